@@ -1,0 +1,189 @@
+/*
+ * qc_eloc.h -- C ABI of libqc_eloc: sample-batched local energies on one GB300 GPU.
+ *
+ * The operation (arxiv 2506.23809, Sec. III-B, Eq. 5):
+ *
+ *     E_loc(x) = sum_x' <x|H|x'> psi(x') / psi(x)
+ *
+ * for every unique sampled occupation bitstring x, with H the second-quantized
+ * Hamiltonian of Eq. 2 (Sec. II-A) built from real one-electron integrals h_pq and
+ * two-electron integrals (pq|rs), and x' running over x itself and every single and
+ * double excitation of x that conserves S_z.  Then (Eq. 1) the count-weighted mean
+ *
+ *     Ebar = sum_i c_i E_loc(x_i) / W,   W = sum_i c_i,
+ *
+ * and the weighted variance  var = sum_i c_i |E_loc(x_i) - Ebar|^2 / W  (two-pass).
+ *
+ * Two modes, after the two energies of Sec. IV-C-4:
+ *   QC_SAMPLE  "sample-space energy": x' contributes only if it is in the table of
+ *              unique samples (the lookup table of Sec. IV-C-4); others contribute 0.
+ *   QC_FULL    "accurate energy": the caller supplies psi for every connected x' in a
+ *              table; an x' missing from it is an error for that sample.
+ *
+ * Bitstrings (the occupation-number vector of Sec. II-A, interleaved spin orbitals
+ * n_1a, n_1b, ..., n_Ka, n_Kb): spin orbital i is spatial orbital i/2 with spin alpha
+ * when i is even; it is bit (i % 64) of 64-bit word i/64.  A key is two uint64 words
+ * {w0, w1}; a table is sorted ascending as the unsigned 128-bit number w1*2^64 + w0,
+ * with no duplicates.  n_orb <= 128.
+ *
+ * Fermionic sign convention: |x> = a+_{i1} a+_{i2} ... |0> with i1 < i2 < ...
+ *
+ * Integrals: h is K x K row-major FP64 (K = n_orb/2), symmetric; eri is K^4 row-major
+ * FP64 in chemist notation, eri[((p*K+q)*K+r)*K+s] = (pq|rs), with the 8-fold symmetry
+ * of real orbitals.  <pq|rs> = (pr|qs) between spin orbitals of matching spins.
+ *
+ * Memory ownership: pointers passed to qc_eloc_create are read during the call only
+ * (the library copies the integrals to the device).  Array pointers passed to
+ * qc_eloc_eval are caller-owned DEVICE memory, 16-byte aligned, and must stay valid
+ * until the stream has passed the call.  The handle owns its device workspace.
+ *
+ * Errors: no C++ exception crosses this ABI.  Functions return QC_OK (0) or a negative
+ * qc_status; qc_eloc_last_error() gives a message.  Conditions found on the device
+ * (unsorted or duplicate keys, wrong electron counts, psi(x) = 0, a missing x' in FULL
+ * mode, a bounded wait that ran out) are reported in qc_eloc_summary.status / .flags
+ * once the stream reaches the end of the call; the affected samples get E_loc = NaN
+ * and are left out of the reduction.
+ *
+ * Threads and streams: a handle may be used from one host thread at a time, and its
+ * evaluations must not overlap on the device (they share the handle's workspace).
+ * Different handles are independent.
+ */
+#ifndef QC_ELOC_H
+#define QC_ELOC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int qc_status;
+
+#define QC_OK              0
+#define QC_PENDING         1   /* qc_eloc_poll: job not finished within the timeout */
+#define QC_ERR_ARG        -1   /* bad argument (null pointer, size, alignment, n_orb) */
+#define QC_ERR_UNSORTED   -2   /* table keys not ascending */
+#define QC_ERR_DUP        -3   /* duplicate key */
+#define QC_ERR_NELEC      -4   /* key with wrong alpha/beta electron count or bits >= n_orb */
+#define QC_ERR_OOM        -5   /* device allocation failed */
+#define QC_ERR_BUDGET     -6   /* serving: job can never fit the memory budget */
+#define QC_ERR_CUDA       -7   /* CUDA runtime error (message in qc_eloc_last_error) */
+#define QC_ERR_ZERO_PSI   -8   /* psi(x) == 0 for some sample */
+#define QC_ERR_MISSING    -9   /* FULL mode: a connected x' is absent from the table */
+#define QC_ERR_TIMEOUT   -10   /* a bounded device wait ran out */
+#define QC_ERR_CAPACITY  -11   /* size beyond a compiled or reserved limit */
+#define QC_ERR_COUNTS    -12   /* negative count */
+
+/* device-detected condition bits in qc_eloc_summary.flags */
+#define QC_FLAG_UNSORTED   0x01u
+#define QC_FLAG_DUP        0x02u
+#define QC_FLAG_NELEC      0x04u
+#define QC_FLAG_ZERO_PSI   0x08u
+#define QC_FLAG_MISSING    0x10u
+#define QC_FLAG_NEG_COUNT  0x20u
+#define QC_FLAG_TABLE_FULL 0x40u
+#define QC_FLAG_TIMEOUT    0x80u
+
+/* precision */
+#define QC_FP64        0   /* every floating-point step in FP64 */
+#define QC_FP32_COMP   1   /* matrix elements x psi ratios in FP32 with compensated
+                              (TwoSum) accumulation per sample; diagonal energy,
+                              1/psi(x) and the reduction over samples in FP64 */
+/* mode */
+#define QC_SAMPLE      0
+#define QC_FULL        1
+
+/* options for qc_eloc_set_option */
+#define QC_OPT_TIMING        1  /* 1: record per-phase CUDA events (qc_eloc_timings) */
+#define QC_OPT_KERNEL        2  /* 0 auto, 1 direct probe of every x', 2 filtered */
+#define QC_OPT_FILTER_LOG2W  3  /* 0 auto, else log2 of filter 32-bit words (5..15) */
+#define QC_OPT_WARPS         4  /* 0 auto, else warps per CTA of the main kernel */
+#define QC_OPT_UNROLL        5  /* 0 auto, else outer entries per inner pass (1,2,4,8) */
+#define QC_OPT_GRID          6  /* 0 auto, else CTAs of the main kernel */
+
+typedef struct qc_eloc qc_eloc;
+
+/* Result summary (written to host memory at the end of an evaluation). */
+typedef struct {
+    double   e_re, e_im;        /* Ebar (Eq. 1) over samples with finite E_loc */
+    double   var;               /* sum c |E - Ebar|^2 / W */
+    double   w;                 /* W = sum c over those samples */
+    double   sum_ce_re, sum_ce_im; /* sum c E (for combining shards) */
+    uint64_t n_used;            /* samples entering the reduction */
+    uint64_t n_pairs;           /* connected (x, x') pairs enumerated, diagonal excluded */
+    uint64_t n_hits;            /* pairs whose x' was found in the table */
+    uint64_t n_missing;         /* FULL mode: pairs whose x' was absent */
+    uint64_t n_bad;             /* samples with E_loc = NaN */
+    uint32_t flags;             /* QC_FLAG_* */
+    int32_t  status;            /* QC_OK or the most severe device-detected error */
+} qc_eloc_summary;
+
+/* Outputs of one evaluation.  eloc is required; the rest may be NULL.
+ *   eloc        device complex128[n_u] (re, im interleaved)
+ *   summary     host memory; page-locked memory keeps qc_eloc_eval asynchronous
+ *   hit_count   device uint32[n_u]: table hits per sample (diagnostics)
+ *   hit_rowsum  device uint64[n_u]: sum over hits of (table row + 1)
+ *   hit_signsum device int64[n_u]:  sum over hits of phase * (table row + 1), where the
+ *               phase is <x'| a+_i a+_j a_b a_a |x> with a < b the spin orbitals emptied
+ *               and i < j those filled (+-1; for a single, <x'| a+_i a_a |x>). */
+typedef struct {
+    double*          eloc;
+    qc_eloc_summary* summary;
+    uint32_t*        hit_count;
+    uint64_t*        hit_rowsum;
+    int64_t*         hit_signsum;
+} qc_eloc_out;
+
+/* Create a handle for one Hamiltonian.  n_orb: even, 2..128.  n_elec: even, S_z = 0
+ * (n_elec/2 electrons of each spin), 0 < n_elec < n_orb.  h, eri: host FP64 (layout
+ * above), copied to the device.  e_core: constant added to every diagonal element.
+ * precision: QC_FP64 | QC_FP32_COMP.  mode: QC_SAMPLE | QC_FULL.  Uses the current CUDA
+ * device.  Returns QC_ERR_ARG on bad sizes, QC_ERR_OOM / QC_ERR_CUDA on device errors. */
+qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int n_orb,
+                         int n_elec, int precision, int mode, qc_eloc** out);
+
+qc_status qc_eloc_destroy(qc_eloc* handle);
+
+/* Message for the last error on this handle (or on handle creation when handle is NULL). */
+const char* qc_eloc_last_error(const qc_eloc* handle);
+
+/* Pre-size the workspace for up to n_u_max samples and n_table_max table rows, so that
+ * later evaluations within those sizes allocate nothing (and can be graph-captured). */
+qc_status qc_eloc_reserve(qc_eloc* handle, int64_t n_u_max, int64_t n_table_max);
+
+qc_status qc_eloc_set_option(qc_eloc* handle, int option, int64_t value);
+
+/* Structural pair count per sample: sum over spins of o v + C(o,2) C(v,2), plus
+ * o_a v_a o_b v_b (o occupied, v empty spatial orbitals per spin). */
+int64_t qc_eloc_pairs_per_sample(const qc_eloc* handle);
+
+/* Evaluate E_loc for n_u samples on `stream` (a cudaStream_t, NULL = legacy default).
+ *   samples  device uint64[n_u][2]   bitstrings to evaluate
+ *   counts   device int64[n_u]       sample counts (>= 0)
+ *   psi      device complex128[n_u]  psi(x), (re, im) interleaved
+ *   table_keys, table_psi, n_table   the lookup table: sorted unique keys and their psi.
+ *            QC_SAMPLE with table_keys == NULL: the table is the sample set itself
+ *            (samples must then be sorted and unique).  A separate table lets one
+ *            evaluate a shard of the samples against the whole sample set.
+ *            QC_FULL: required; must hold every connected x' of every sample.
+ * Asynchronous: returns after enqueueing.  Host-detectable argument errors return
+ * synchronously.  May allocate device workspace on first use or growth (see
+ * qc_eloc_reserve). */
+qc_status qc_eloc_eval(qc_eloc* handle, const uint64_t* samples, const int64_t* counts,
+                       const double* psi, int64_t n_u, const uint64_t* table_keys,
+                       const double* table_psi, int64_t n_table, qc_eloc_out* out,
+                       void* stream);
+
+/* Per-phase device times of the last evaluation in ms: {table build, main kernel,
+ * reduction}.  Needs QC_OPT_TIMING = 1; synchronizes on the recorded events. */
+qc_status qc_eloc_timings(qc_eloc* handle, float* ms3);
+
+/* Launch shape of the last evaluation on this handle: {kernel (1 direct, 2 filtered),
+ * grid CTAs, warps per CTA, unroll, dynamic shared memory bytes, log2 filter words}. */
+qc_status qc_eloc_last_config(const qc_eloc* handle, int64_t* cfg6);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QC_ELOC_H */

@@ -1,0 +1,217 @@
+"""Thin ctypes binding of libqc_eloc (include/qc_eloc.h), same names as the C ABI.
+
+Argument marshalling only: tensors are passed as device pointers, the stream as
+``torch.cuda.current_stream().cuda_stream``; every step of the computation runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library is missing, loading
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqc_eloc.so")
+
+QC_OK, QC_PENDING = 0, 1
+QC_FP64, QC_FP32_COMP = 0, 1
+QC_SAMPLE, QC_FULL = 0, 1
+QC_OPT_TIMING, QC_OPT_KERNEL, QC_OPT_FILTER_LOG2W, QC_OPT_WARPS, QC_OPT_UNROLL, QC_OPT_GRID = 1, 2, 3, 4, 5, 6
+STATUS_NAMES = {0: "QC_OK", 1: "QC_PENDING", -1: "QC_ERR_ARG", -2: "QC_ERR_UNSORTED", -3: "QC_ERR_DUP",
+                -4: "QC_ERR_NELEC", -5: "QC_ERR_OOM", -6: "QC_ERR_BUDGET", -7: "QC_ERR_CUDA",
+                -8: "QC_ERR_ZERO_PSI", -9: "QC_ERR_MISSING", -10: "QC_ERR_TIMEOUT",
+                -11: "QC_ERR_CAPACITY", -12: "QC_ERR_COUNTS"}
+
+
+class QcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class qc_eloc_summary(ctypes.Structure):
+    _fields_ = [("e_re", ctypes.c_double), ("e_im", ctypes.c_double), ("var", ctypes.c_double),
+                ("w", ctypes.c_double), ("sum_ce_re", ctypes.c_double), ("sum_ce_im", ctypes.c_double),
+                ("n_used", ctypes.c_uint64), ("n_pairs", ctypes.c_uint64), ("n_hits", ctypes.c_uint64),
+                ("n_missing", ctypes.c_uint64), ("n_bad", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("status", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["energy"] = complex(self.e_re, self.e_im)
+        return d
+
+
+class qc_eloc_out(ctypes.Structure):
+    _fields_ = [("eloc", ctypes.c_void_p), ("summary", ctypes.c_void_p), ("hit_count", ctypes.c_void_p),
+                ("hit_rowsum", ctypes.c_void_p), ("hit_signsum", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libqc_eloc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libqc_eloc.so not found at {path}: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.qc_eloc_create.argtypes = [P, P, f64, i32, i32, i32, i32, ctypes.POINTER(P)]
+    lib.qc_eloc_create.restype = i32
+    lib.qc_eloc_destroy.argtypes = [P]
+    lib.qc_eloc_destroy.restype = i32
+    lib.qc_eloc_last_error.argtypes = [P]
+    lib.qc_eloc_last_error.restype = ctypes.c_char_p
+    lib.qc_eloc_reserve.argtypes = [P, i64, i64]
+    lib.qc_eloc_reserve.restype = i32
+    lib.qc_eloc_set_option.argtypes = [P, i32, i64]
+    lib.qc_eloc_set_option.restype = i32
+    lib.qc_eloc_pairs_per_sample.argtypes = [P]
+    lib.qc_eloc_pairs_per_sample.restype = i64
+    lib.qc_eloc_eval.argtypes = [P, P, P, P, i64, P, P, i64, ctypes.POINTER(qc_eloc_out), P]
+    lib.qc_eloc_eval.restype = i32
+    lib.qc_eloc_timings.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+    lib.qc_eloc_timings.restype = i32
+    lib.qc_eloc_last_config.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.qc_eloc_last_config.restype = i32
+    _lib = lib
+    return lib
+
+
+def _check(st, handle=None):
+    if st != QC_OK:
+        lib = load_library()
+        msg = lib.qc_eloc_last_error(handle).decode() if lib else ""
+        raise QcError(st, msg)
+
+
+@dataclass
+class QcHandle:
+    """A qc_eloc* plus a page-locked summary buffer reused by every evaluation."""
+    ptr: ctypes.c_void_p
+    n_orb: int
+    n_elec: int
+    precision: int
+    mode: int
+    summary_buf: object  # torch pinned uint8 tensor
+
+    def summary_struct(self) -> qc_eloc_summary:
+        return qc_eloc_summary.from_address(self.summary_buf.data_ptr())
+
+
+def qc_eloc_create(h, eri, e_core: float, n_orb: int, n_elec: int, precision: int = QC_FP64,
+                   mode: int = QC_SAMPLE) -> QcHandle:
+    import torch
+    lib = load_library()
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    out = ctypes.c_void_p()
+    st = lib.qc_eloc_create(h.ctypes.data_as(ctypes.c_void_p), eri.ctypes.data_as(ctypes.c_void_p),
+                            float(e_core), int(n_orb), int(n_elec), int(precision), int(mode),
+                            ctypes.byref(out))
+    _check(st, None)
+    buf = torch.zeros(ctypes.sizeof(qc_eloc_summary), dtype=torch.uint8, pin_memory=True)
+    return QcHandle(out, n_orb, n_elec, precision, mode, buf)
+
+
+def qc_eloc_destroy(handle: QcHandle):
+    if handle.ptr:
+        load_library().qc_eloc_destroy(handle.ptr)
+        handle.ptr = ctypes.c_void_p()
+
+
+def qc_eloc_reserve(handle: QcHandle, n_u_max: int, n_table_max: int = 0):
+    _check(load_library().qc_eloc_reserve(handle.ptr, int(n_u_max), int(n_table_max)), handle.ptr)
+
+
+def qc_eloc_set_option(handle: QcHandle, option: int, value: int):
+    _check(load_library().qc_eloc_set_option(handle.ptr, int(option), int(value)), handle.ptr)
+
+
+def qc_eloc_pairs_per_sample(handle: QcHandle) -> int:
+    return int(load_library().qc_eloc_pairs_per_sample(handle.ptr))
+
+
+def qc_eloc_timings(handle: QcHandle):
+    ms = (ctypes.c_float * 3)()
+    _check(load_library().qc_eloc_timings(handle.ptr, ms), handle.ptr)
+    return tuple(float(v) for v in ms)
+
+
+def qc_eloc_last_config(handle: QcHandle) -> dict:
+    c = (ctypes.c_int64 * 6)()
+    _check(load_library().qc_eloc_last_config(handle.ptr, c), handle.ptr)
+    return dict(kernel=int(c[0]), grid=int(c[1]), warps=int(c[2]), unroll=int(c[3]), smem=int(c[4]),
+                filter_log2w=int(c[5]))
+
+
+def _dptr(t, name, dtype_ok, shape_last=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.dtype not in dtype_ok:
+        raise ValueError(f"{name}: dtype {t.dtype} not in {dtype_ok}")
+    if shape_last is not None and (t.dim() != 2 or t.shape[-1] != shape_last):
+        raise ValueError(f"{name} must have shape (n, {shape_last})")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def qc_eloc_eval(handle: QcHandle, samples, counts, psi, table_keys=None, table_psi=None,
+                 eloc=None, diagnostics: bool = False, summary: bool = True, stream=None):
+    """Enqueue one evaluation.  Returns (eloc complex128[n_u], diag) where diag is None or
+    a dict of per-sample hit_count / hit_rowsum / hit_signsum tensors.  The summary is
+    written into ``handle.summary_buf``; read it with ``qc_eloc_summary_read`` after the
+    stream has passed the call."""
+    import torch
+    lib = load_library()
+    key_types = (torch.int64, torch.uint64)
+    psi_types = (torch.complex128, torch.float64)
+    n_u = samples.shape[0]
+    if eloc is None:
+        eloc = torch.empty(n_u, dtype=torch.complex128, device=samples.device)
+    diag = None
+    out = qc_eloc_out()
+    out.eloc = eloc.data_ptr()
+    out.summary = handle.summary_buf.data_ptr() if summary else None
+    if diagnostics:
+        diag = dict(hit_count=torch.empty(n_u, dtype=torch.int32, device=samples.device),
+                    hit_rowsum=torch.empty(n_u, dtype=torch.int64, device=samples.device),
+                    hit_signsum=torch.empty(n_u, dtype=torch.int64, device=samples.device))
+        out.hit_count = diag["hit_count"].data_ptr()
+        out.hit_rowsum = diag["hit_rowsum"].data_ptr()
+        out.hit_signsum = diag["hit_signsum"].data_ptr()
+    s = _dptr(samples, "samples", key_types, 2)
+    c = _dptr(counts, "counts", (torch.int64,))
+    p = _dptr(psi, "psi", psi_types)
+    tk = _dptr(table_keys, "table_keys", key_types, 2)
+    tp = _dptr(table_psi, "table_psi", psi_types)
+    n_t = 0 if table_keys is None else table_keys.shape[0]
+    if stream is None:
+        stream = torch.cuda.current_stream(samples.device)
+    st = lib.qc_eloc_eval(handle.ptr, s, c, p, int(n_u), tk, tp, int(n_t), ctypes.byref(out),
+                          ctypes.c_void_p(stream.cuda_stream))
+    _check(st, handle.ptr)
+    return eloc, diag
+
+
+def qc_eloc_summary_read(handle: QcHandle, stream=None) -> dict:
+    """Synchronize the stream and return the last summary as a dict."""
+    import torch
+    (stream or torch.cuda.current_stream()).synchronize()
+    return handle.summary_struct().as_dict()
+
+
+def keys_to_tensor(keys: np.ndarray, device="cuda"):
+    """uint64[n, 2] numpy keys -> int64 CUDA tensor with the same bits."""
+    import torch
+    k = np.ascontiguousarray(keys, dtype=np.uint64).view(np.int64)
+    return torch.from_numpy(k).to(device)

@@ -1,0 +1,477 @@
+// qc_api.cu -- host side of the libqc_eloc C ABI (declared in include/qc_eloc.h).
+//
+// A handle holds one Hamiltonian (Eq. 2: h_pq and (pq|rs)) on the device plus the
+// workspace of an evaluation: the bucket hash index and Bloom filter over the lookup
+// table (the sample-space lookup table of Sec. IV-C-4), the reduction partials of Eq. 1,
+// counters and the device copy of the summary.  qc_eloc_eval only enqueues work on the
+// caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qc_eloc.h"
+#include "qc_internal.h"
+
+struct qc_eloc {
+    int device = 0;
+    int n_orb = 0, n_elec = 0, K = 0, na = 0, nb = 0, precision = 0, mode = 0;
+    double e_core = 0.0;
+    qc::SysParams sp{};
+    double* d_h = nullptr;
+    double* d_eri = nullptr;
+    double* d_J = nullptr;
+    double* d_X = nullptr;
+    float* d_h32 = nullptr;
+    float* d_eri32 = nullptr;
+    unsigned long long* d_T = nullptr;
+    unsigned long long* d_slots = nullptr;
+    size_t slots_cap = 0;  // 64-bit entries
+    uint32_t* d_filter = nullptr;
+    size_t filter_cap = 0;  // 32-bit words
+    double* d_part = nullptr;
+    int part_cap = 0;  // reduction blocks
+    qc::Counters* d_ctr = nullptr;
+    qc_eloc_summary* d_sum = nullptr;
+    int opt_timing = 0, opt_kernel = 0, opt_fw = 0, opt_warps = 0, opt_unroll = 0, opt_grid = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool ev_recorded = false;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    qc::LaunchCfg last_cfg{};
+    int last_fw = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+qc_status fail(qc_eloc* h, qc_status st, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+qc_status cuda_fail(qc_eloc* h, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? QC_ERR_OOM : QC_ERR_CUDA, m);
+}
+
+long long comb2(long long n) { return n < 2 ? 0 : n * (n - 1) / 2; }
+
+// splitmix64 (Vigna): seeds the 128 entries of the linear key hash.
+unsigned long long splitmix64(unsigned long long& s) {
+    unsigned long long z = (s += 0x9e3779b97f4a7c15ULL);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+unsigned long long next_pow2(unsigned long long v) {
+    unsigned long long p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+int ceil_log2(unsigned long long v) {
+    int l = 0;
+    while ((1ULL << l) < v) ++l;
+    return l;
+}
+
+template <typename T>
+void free_dev(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+bool prepared_devices[64] = {};
+
+}  // namespace
+
+extern "C" {
+
+const char* qc_eloc_last_error(const qc_eloc* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int n_orb, int n_elec,
+                         int precision, int mode, qc_eloc** out) {
+    if (!out) return fail(nullptr, QC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!h || !eri) return fail(nullptr, QC_ERR_ARG, "h or eri is NULL");
+    if (n_orb < 2 || n_orb > qc::kMaxOrb || (n_orb & 1))
+        return fail(nullptr, QC_ERR_ARG, "n_orb must be even, 2..128");
+    if (n_elec <= 0 || n_elec >= n_orb || (n_elec & 1))
+        return fail(nullptr, QC_ERR_ARG, "n_elec must be even with 0 < n_elec < n_orb (S_z = 0)");
+    if (precision != QC_FP64 && precision != QC_FP32_COMP)
+        return fail(nullptr, QC_ERR_ARG, "precision must be QC_FP64 or QC_FP32_COMP");
+    if (mode != QC_SAMPLE && mode != QC_FULL)
+        return fail(nullptr, QC_ERR_ARG, "mode must be QC_SAMPLE or QC_FULL");
+
+    qc_eloc* H = new (std::nothrow) qc_eloc();
+    if (!H) return fail(nullptr, QC_ERR_OOM, "host allocation failed");
+    H->n_orb = n_orb;
+    H->n_elec = n_elec;
+    H->K = n_orb / 2;
+    H->na = H->nb = n_elec / 2;
+    H->precision = precision;
+    H->mode = mode;
+    H->e_core = e_core;
+    const int K = H->K;
+    cudaError_t e = cudaGetDevice(&H->device);
+    if (e != cudaSuccess) { qc_status s = cuda_fail(nullptr, e, "cudaGetDevice"); delete H; return s; }
+    int smc = 0, optin = 0;
+    cudaDeviceGetAttribute(&smc, cudaDevAttrMultiProcessorCount, H->device);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, H->device);
+    H->sm_count = smc;
+    H->smem_optin = static_cast<size_t>(optin);
+
+    const size_t KK = static_cast<size_t>(K) * K, K4 = KK * KK;
+    std::vector<double> J(KK), X(KK);
+    for (int k = 0; k < K; ++k)
+        for (int l = 0; l < K; ++l) {
+            J[k * K + l] = eri[((static_cast<size_t>(k) * K + k) * K + l) * K + l];  // (kk|ll)
+            X[k * K + l] = eri[((static_cast<size_t>(k) * K + l) * K + l) * K + k];  // (kl|lk)
+        }
+    std::vector<unsigned long long> T(128);
+    unsigned long long seed = 0x51c0de5eedULL;
+    for (auto& t : T) t = splitmix64(seed);
+
+    auto cleanup = [&](qc_status s) { qc_eloc_destroy(H); return s; };
+#define QC_TRY(call, what)                                          \
+    do {                                                            \
+        cudaError_t r_ = (call);                                    \
+        if (r_ != cudaSuccess) return cleanup(cuda_fail(nullptr, r_, what)); \
+    } while (0)
+    QC_TRY(cudaMalloc(&H->d_h, KK * sizeof(double)), "cudaMalloc h");
+    QC_TRY(cudaMemcpy(H->d_h, h, KK * sizeof(double), cudaMemcpyHostToDevice), "copy h");
+    QC_TRY(cudaMalloc(&H->d_J, KK * sizeof(double)), "cudaMalloc J");
+    QC_TRY(cudaMemcpy(H->d_J, J.data(), KK * sizeof(double), cudaMemcpyHostToDevice), "copy J");
+    QC_TRY(cudaMalloc(&H->d_X, KK * sizeof(double)), "cudaMalloc X");
+    QC_TRY(cudaMemcpy(H->d_X, X.data(), KK * sizeof(double), cudaMemcpyHostToDevice), "copy X");
+    if (precision == QC_FP64) {
+        QC_TRY(cudaMalloc(&H->d_eri, K4 * sizeof(double)), "cudaMalloc eri");
+        QC_TRY(cudaMemcpy(H->d_eri, eri, K4 * sizeof(double), cudaMemcpyHostToDevice), "copy eri");
+    } else {
+        std::vector<float> h32(KK), e32(K4);
+        for (size_t i = 0; i < KK; ++i) h32[i] = static_cast<float>(h[i]);
+        for (size_t i = 0; i < K4; ++i) e32[i] = static_cast<float>(eri[i]);
+        QC_TRY(cudaMalloc(&H->d_h32, KK * sizeof(float)), "cudaMalloc h32");
+        QC_TRY(cudaMemcpy(H->d_h32, h32.data(), KK * sizeof(float), cudaMemcpyHostToDevice), "copy h32");
+        QC_TRY(cudaMalloc(&H->d_eri32, K4 * sizeof(float)), "cudaMalloc eri32");
+        QC_TRY(cudaMemcpy(H->d_eri32, e32.data(), K4 * sizeof(float), cudaMemcpyHostToDevice), "copy eri32");
+    }
+    QC_TRY(cudaMalloc(&H->d_T, 128 * sizeof(unsigned long long)), "cudaMalloc T");
+    QC_TRY(cudaMemcpy(H->d_T, T.data(), 128 * sizeof(unsigned long long), cudaMemcpyHostToDevice), "copy T");
+    QC_TRY(cudaMalloc(&H->d_ctr, sizeof(qc::Counters)), "cudaMalloc counters");
+    QC_TRY(cudaMemset(H->d_ctr, 0, sizeof(qc::Counters)), "memset counters");
+    QC_TRY(cudaMalloc(&H->d_sum, sizeof(qc_eloc_summary)), "cudaMalloc summary");
+    if (H->device >= 0 && H->device < 64 && !prepared_devices[H->device]) {
+        QC_TRY(qc::prepare_kernels(H->smem_optin), "cudaFuncSetAttribute");
+        prepared_devices[H->device] = true;
+    }
+#undef QC_TRY
+
+    qc::SysParams& sp = H->sp;
+    sp.n_orb = n_orb;
+    sp.K = K;
+    sp.na = H->na;
+    sp.nb = H->nb;
+    sp.oa = H->na;
+    sp.va = K - H->na;
+    sp.ob = H->nb;
+    sp.vb = K - H->nb;
+    sp.nsa = sp.oa * sp.va;
+    sp.nsb = sp.ob * sp.vb;
+    sp.npoa = static_cast<int>(comb2(sp.oa));
+    sp.npva = static_cast<int>(comb2(sp.va));
+    sp.npob = static_cast<int>(comb2(sp.ob));
+    sp.npvb = static_cast<int>(comb2(sp.vb));
+    sp.pairs = static_cast<long long>(sp.nsa) + sp.nsb + static_cast<long long>(sp.npoa) * sp.npva +
+               static_cast<long long>(sp.npob) * sp.npvb + static_cast<long long>(sp.nsa) * sp.nsb;
+    sp.e_core = e_core;
+    sp.precision = precision;
+    sp.h = H->d_h;
+    sp.eri = H->d_eri;
+    sp.h32 = H->d_h32;
+    sp.eri32 = H->d_eri32;
+    sp.J = H->d_J;
+    sp.X = H->d_X;
+    *out = H;
+    return QC_OK;
+}
+
+qc_status qc_eloc_destroy(qc_eloc* H) {
+    if (!H) return QC_OK;
+    free_dev(H->d_h);
+    free_dev(H->d_eri);
+    free_dev(H->d_J);
+    free_dev(H->d_X);
+    free_dev(H->d_h32);
+    free_dev(H->d_eri32);
+    free_dev(H->d_T);
+    free_dev(H->d_slots);
+    free_dev(H->d_filter);
+    free_dev(H->d_part);
+    free_dev(H->d_ctr);
+    free_dev(H->d_sum);
+    for (auto& ev : H->ev)
+        if (ev) cudaEventDestroy(ev);
+    delete H;
+    return QC_OK;
+}
+
+int64_t qc_eloc_pairs_per_sample(const qc_eloc* H) { return H ? H->sp.pairs : -1; }
+
+qc_status qc_eloc_set_option(qc_eloc* H, int option, int64_t value) {
+    if (!H) return QC_ERR_ARG;
+    switch (option) {
+        case QC_OPT_TIMING: H->opt_timing = value ? 1 : 0; return QC_OK;
+        case QC_OPT_KERNEL:
+            if (value < 0 || value > 2) return fail(H, QC_ERR_ARG, "QC_OPT_KERNEL: 0, 1 or 2");
+            H->opt_kernel = static_cast<int>(value);
+            return QC_OK;
+        case QC_OPT_FILTER_LOG2W:
+            if (value != 0 && (value < 5 || value > 15)) return fail(H, QC_ERR_ARG, "QC_OPT_FILTER_LOG2W: 0 or 5..15");
+            H->opt_fw = static_cast<int>(value);
+            return QC_OK;
+        case QC_OPT_WARPS:
+            if (value < 0 || value > 32) return fail(H, QC_ERR_ARG, "QC_OPT_WARPS: 0..32");
+            H->opt_warps = static_cast<int>(value);
+            return QC_OK;
+        case QC_OPT_UNROLL:
+            if (!(value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
+                return fail(H, QC_ERR_ARG, "QC_OPT_UNROLL: 0, 1, 2, 4 or 8");
+            H->opt_unroll = static_cast<int>(value);
+            return QC_OK;
+        case QC_OPT_GRID:
+            if (value < 0 || value > (1 << 20)) return fail(H, QC_ERR_ARG, "QC_OPT_GRID: 0..2^20");
+            H->opt_grid = static_cast<int>(value);
+            return QC_OK;
+        default: return fail(H, QC_ERR_ARG, "unknown option");
+    }
+}
+
+}  // extern "C"
+
+namespace {
+
+// Workspace growth: bucket table for n_table keys, filter of 2^fw words, partials.
+qc_status ensure_workspace(qc_eloc* H, long long n_u, long long n_table, int fw) {
+    const size_t entries = 2 * static_cast<size_t>(next_pow2(static_cast<unsigned long long>(std::max<long long>(n_table, 1))));
+    if (entries > H->slots_cap) {
+        free_dev(H->d_slots);
+        H->slots_cap = 0;
+        cudaError_t e = cudaMalloc(&H->d_slots, entries * sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(H, e, "cudaMalloc hash table");
+        H->slots_cap = entries;
+    }
+    const size_t words = fw > 0 ? (static_cast<size_t>(1) << fw) : 0;
+    if (words > H->filter_cap) {
+        free_dev(H->d_filter);
+        H->filter_cap = 0;
+        cudaError_t e = cudaMalloc(&H->d_filter, words * sizeof(uint32_t));
+        if (e != cudaSuccess) return cuda_fail(H, e, "cudaMalloc filter");
+        H->filter_cap = words;
+    }
+    const int nblk = qc::reduce_blocks(n_u);
+    if (nblk > H->part_cap) {
+        free_dev(H->d_part);
+        H->part_cap = 0;
+        cudaError_t e = cudaMalloc(&H->d_part, static_cast<size_t>(nblk) * 4 * sizeof(double));
+        if (e != cudaSuccess) return cuda_fail(H, e, "cudaMalloc partials");
+        H->part_cap = nblk;
+    }
+    return QC_OK;
+}
+
+// Kernel choice and launch shape (the defaults the autotuner can override).
+qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::LaunchCfg& c, int& fw) {
+    const qc::SysParams& sp = H->sp;
+    int kernel = H->opt_kernel;
+    if (H->mode == QC_FULL) kernel = 1;  // every x' must be looked up: no filter
+    if (kernel == 0) kernel = 2;
+    fw = 0;
+    int warps = 0;
+    if (kernel == 2) {
+        // filter sized for ~16 bits per key, 2^10..2^15 words
+        int want = H->opt_fw;
+        if (want == 0) {
+            want = ceil_log2(static_cast<unsigned long long>(std::max<long long>(n_table, 1)) / 2 + 1);
+            want = std::min(15, std::max(10, want));
+        }
+        const size_t wb = qc::filtered_smem_bytes(sp, 1, want) - qc::filtered_smem_bytes(sp, 0, want);
+        for (fw = want; fw >= 5; --fw) {
+            const size_t base = qc::filtered_smem_bytes(sp, 0, fw);
+            if (base + wb > H->smem_optin) continue;
+            const int fit = static_cast<int>((H->smem_optin - base) / wb);
+            warps = H->opt_warps ? H->opt_warps : std::min(32, fit);
+            if (warps > fit) continue;
+            if (H->opt_fw == 0 && warps < 8 && fw > 10) continue;  // prefer occupancy
+            break;
+        }
+        if (fw < 5 || warps < 1) {
+            if (H->opt_kernel == 2) return fail(H, QC_ERR_CAPACITY, "filtered kernel does not fit shared memory");
+            kernel = 1;
+            fw = 0;
+        }
+    }
+    c.kernel = kernel;
+    c.unroll = H->opt_unroll ? H->opt_unroll : 4;
+    if (kernel == 2) {
+        c.warps = warps;
+        c.smem = qc::filtered_smem_bytes(sp, warps, fw);
+    } else {
+        c.warps = H->opt_warps ? H->opt_warps : 16;
+        c.smem = qc::direct_smem_bytes(c.warps);
+    }
+    int per_sm = qc::max_active_ctas(c.kernel, H->precision, c.unroll, 32 * c.warps, c.smem);
+    if (per_sm < 1) return fail(H, QC_ERR_CAPACITY, "main kernel cannot be resident with this shape");
+    long long grid = H->opt_grid ? H->opt_grid : static_cast<long long>(per_sm) * H->sm_count;
+    const long long need = (n_u + c.warps - 1) / c.warps;
+    grid = std::max<long long>(1, std::min(grid, need));
+    c.grid = static_cast<int>(grid);
+    return QC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qc_status qc_eloc_reserve(qc_eloc* H, int64_t n_u_max, int64_t n_table_max) {
+    if (!H) return QC_ERR_ARG;
+    if (n_u_max < 0 || n_table_max < 0) return fail(H, QC_ERR_ARG, "negative size");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != H->device) return fail(H, QC_ERR_ARG, "handle belongs to another device");
+    qc::LaunchCfg c{};
+    int fw = 0;
+    const long long nt = std::max<long long>(n_table_max, n_u_max);
+    qc_status s = choose_config(H, std::max<long long>(n_u_max, 1), nt, c, fw);
+    if (s != QC_OK) return s;
+    return ensure_workspace(H, n_u_max, nt, fw);
+}
+
+qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* counts, const double* psi,
+                       int64_t n_u, const uint64_t* table_keys, const double* table_psi,
+                       int64_t n_table, qc_eloc_out* out, void* stream) {
+    if (!H) return QC_ERR_ARG;
+    if (!out || (!out->eloc && n_u > 0)) return fail(H, QC_ERR_ARG, "out or out->eloc is NULL");
+    if (n_u < 0 || n_table < 0) return fail(H, QC_ERR_ARG, "negative size");
+    if (n_u > 0 && (!samples || !counts || !psi)) return fail(H, QC_ERR_ARG, "samples, counts or psi is NULL");
+    if (n_u >= (1LL << 31)) return fail(H, QC_ERR_CAPACITY, "n_u >= 2^31");
+    const bool own_table = (table_keys == nullptr);
+    if (H->mode == QC_FULL && own_table) return fail(H, QC_ERR_ARG, "QC_FULL needs table_keys/table_psi");
+    if (!own_table && !table_psi) return fail(H, QC_ERR_ARG, "table_psi is NULL");
+    const ulonglong2* tk = reinterpret_cast<const ulonglong2*>(own_table ? samples : table_keys);
+    const double2* tpsi = reinterpret_cast<const double2*>(own_table ? psi : table_psi);
+    const long long nt = own_table ? n_u : n_table;
+    if (nt >= 0xfffffffeLL) return fail(H, QC_ERR_CAPACITY, "table larger than 2^32 - 2 rows");
+    auto misaligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; };
+    if ((n_u > 0 && (misaligned(samples) || misaligned(psi) || misaligned(out->eloc))) ||
+        (nt > 0 && (misaligned(tk) || misaligned(tpsi))))
+        return fail(H, QC_ERR_ARG, "device arrays must be 16-byte aligned");
+    if (counts && (reinterpret_cast<uintptr_t>(counts) & 7u)) return fail(H, QC_ERR_ARG, "counts must be 8-byte aligned");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != H->device) return fail(H, QC_ERR_ARG, "handle belongs to another device");
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    qc::LaunchCfg cfg{};
+    int fw = 0;
+    qc_status st = choose_config(H, n_u, nt, cfg, fw);
+    if (st != QC_OK) return st;
+    st = ensure_workspace(H, n_u, nt, fw);
+    if (st != QC_OK) return st;
+    H->last_cfg = cfg;
+    H->last_fw = fw;
+
+    if (H->opt_timing) {
+        for (auto& ev : H->ev)
+            if (!ev) {
+                cudaError_t e = cudaEventCreate(&ev);
+                if (e != cudaSuccess) return cuda_fail(H, e, "cudaEventCreate");
+            }
+    }
+    cudaError_t e;
+#define QC_CHK(call, what)                              \
+    do {                                                \
+        e = (call);                                     \
+        if (e != cudaSuccess) return cuda_fail(H, e, what); \
+    } while (0)
+    if (H->opt_timing) QC_CHK(cudaEventRecord(H->ev[0], s), "cudaEventRecord");
+    QC_CHK(cudaMemsetAsync(H->d_ctr, 0, sizeof(qc::Counters), s), "memset counters");
+
+    qc::TableParams tp{};
+    tp.keys = tk;
+    tp.psi = tpsi;
+    tp.n = nt;
+    tp.slots = H->d_slots;
+    tp.nb_mask = static_cast<unsigned>(next_pow2(static_cast<unsigned long long>(std::max<long long>(nt, 1))) - 1);
+    tp.filter = (cfg.kernel == 2) ? H->d_filter : nullptr;
+    tp.fw = (cfg.kernel == 2) ? fw : 0;
+    const size_t nbuckets = static_cast<size_t>(tp.nb_mask) + 1;
+    QC_CHK(cudaMemsetAsync(H->d_slots, 0, 2 * nbuckets * sizeof(unsigned long long), s), "memset table");
+    if (cfg.kernel == 2) QC_CHK(cudaMemsetAsync(H->d_filter, 0, (static_cast<size_t>(4) << fw), s), "memset filter");
+    QC_CHK(qc::launch_build_table(tp, H->n_orb, H->na, H->nb, H->d_T, H->d_slots, H->d_filter, H->d_ctr, s),
+           "build_table launch");
+    if (H->opt_timing) QC_CHK(cudaEventRecord(H->ev[1], s), "cudaEventRecord");
+
+    qc::EvalParams ep{};
+    ep.samples = reinterpret_cast<const ulonglong2*>(samples);
+    ep.psi = reinterpret_cast<const double2*>(psi);
+    ep.counts = reinterpret_cast<const long long*>(counts);
+    ep.n_u = n_u;
+    ep.eloc = reinterpret_cast<double2*>(out->eloc);
+    ep.hit_count = out->hit_count;
+    ep.hit_rowsum = reinterpret_cast<unsigned long long*>(out->hit_rowsum);
+    ep.hit_signsum = reinterpret_cast<long long*>(out->hit_signsum);
+    ep.ctr = H->d_ctr;
+    ep.T = H->d_T;
+    ep.mode = H->mode;
+    QC_CHK(qc::launch_eloc_main(H->sp, tp, ep, cfg, s), "main kernel launch");
+    if (H->opt_timing) QC_CHK(cudaEventRecord(H->ev[2], s), "cudaEventRecord");
+    QC_CHK(qc::launch_reduce(ep, H->d_part, qc::reduce_blocks(n_u), H->d_sum, H->sp.pairs, s),
+           "reduce launch");
+    if (H->opt_timing) QC_CHK(cudaEventRecord(H->ev[3], s), "cudaEventRecord");
+    if (out->summary)
+        QC_CHK(cudaMemcpyAsync(out->summary, H->d_sum, sizeof(qc_eloc_summary), cudaMemcpyDeviceToHost, s),
+               "summary copy");
+#undef QC_CHK
+    H->ev_recorded = H->opt_timing != 0;
+    return QC_OK;
+}
+
+qc_status qc_eloc_timings(qc_eloc* H, float* ms3) {
+    if (!H || !ms3) return QC_ERR_ARG;
+    if (!H->ev_recorded) return fail(H, QC_ERR_ARG, "no timed evaluation (set QC_OPT_TIMING first)");
+    cudaError_t e = cudaEventSynchronize(H->ev[3]);
+    if (e != cudaSuccess) return cuda_fail(H, e, "cudaEventSynchronize");
+    for (int i = 0; i < 3; ++i) {
+        e = cudaEventElapsedTime(&ms3[i], H->ev[i], H->ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(H, e, "cudaEventElapsedTime");
+    }
+    return QC_OK;
+}
+
+// Launch shape of the last evaluation: {kernel, grid, warps, unroll, smem bytes, filter log2 words}.
+qc_status qc_eloc_last_config(const qc_eloc* H, int64_t* cfg6) {
+    if (!H || !cfg6) return QC_ERR_ARG;
+    cfg6[0] = H->last_cfg.kernel;
+    cfg6[1] = H->last_cfg.grid;
+    cfg6[2] = H->last_cfg.warps;
+    cfg6[3] = H->last_cfg.unroll;
+    cfg6[4] = static_cast<int64_t>(H->last_cfg.smem);
+    cfg6[5] = H->last_fw;
+    return QC_OK;
+}
+
+}  // extern "C"

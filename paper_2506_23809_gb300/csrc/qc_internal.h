@@ -1,0 +1,93 @@
+// qc_internal.h -- device-side parameter blocks shared by the host API and the kernels
+// of libqc_eloc (not part of the public ABI; see include/qc_eloc.h for that).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qc {
+
+constexpr int kMaxOrb = 128;     // spin orbitals (two 64-bit words)
+constexpr int kMaxSpatial = 64;  // spatial orbitals per spin
+constexpr int kPairLut = 2016;   // C(64, 2): colex pair index -> (i, j), i < j < 64
+
+// One Hamiltonian (Eq. 2) resident on the device.
+struct SysParams {
+    int n_orb, K;        // spin / spatial orbitals
+    int na, nb;          // electrons per spin
+    int oa, va, ob, vb;  // occupied / empty spatial orbitals per spin
+    int nsa, nsb;        // singles per spin: o*v
+    int npoa, npva, npob, npvb;  // C(o,2), C(v,2) per spin
+    long long pairs;     // structural connected pairs per sample
+    double e_core;
+    int precision;       // 0 FP64, 1 FP32 compensated
+    const double* h;     // K*K  FP64
+    const double* eri;   // K^4  FP64 (FP64 precision)
+    const float* h32;    // K*K  FP32 (FP32 precision)
+    const float* eri32;  // K^4  FP32 (FP32 precision)
+    const double* J;     // K*K  (kk|ll)  FP64
+    const double* X;     // K*K  (kl|lk)  FP64
+};
+
+// The lookup table: sorted unique keys, their psi, and the device hash index over them.
+struct TableParams {
+    const ulonglong2* keys;
+    const double2* psi;
+    long long n;
+    const unsigned long long* slots;  // 2 entries per 16-byte bucket
+    unsigned nb_mask;                 // buckets - 1 (power of two)
+    const uint32_t* filter;           // blocked Bloom filter, (1 << fw) 32-bit words
+    int fw;
+};
+
+// Counters and flags of one evaluation (device memory, zeroed at the start of a call).
+struct Counters {
+    unsigned long long hits;
+    unsigned long long missing;
+    unsigned long long bad;
+    unsigned long long invalid;   // samples with a wrong electron count (not evaluated)
+    unsigned int flags;
+    unsigned int ticket;     // last-block ticket of the reduction passes
+    double mean_re, mean_im;  // Ebar from pass 1
+    long long w;              // sum of counts (pass 1)
+    double sce_re, sce_im;
+    unsigned long long used;
+};
+
+struct EvalParams {
+    const ulonglong2* samples;
+    const double2* psi;
+    const long long* counts;
+    long long n_u;
+    double2* eloc;
+    uint32_t* hit_count;
+    unsigned long long* hit_rowsum;
+    long long* hit_signsum;
+    Counters* ctr;
+    const unsigned long long* T;  // 128 entries of the linear key hash
+    int mode;                     // 0 SAMPLE, 1 FULL
+};
+
+struct LaunchCfg {
+    int kernel;   // 1 direct, 2 filtered
+    int grid;
+    int warps;
+    int unroll;
+    size_t smem;
+};
+
+// host-side launchers (qc_kernels.cu)
+cudaError_t launch_build_table(const TableParams& tp, int n_orb, int na, int nb,
+                               const unsigned long long* T, unsigned long long* slots,
+                               uint32_t* filter, Counters* ctr, cudaStream_t s);
+cudaError_t launch_eloc_main(const SysParams& sp, const TableParams& tp, const EvalParams& ep,
+                             const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk,
+                          void* summary_dev, long long pairs_per_sample, cudaStream_t s);
+int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem);
+cudaError_t prepare_kernels(size_t max_smem);
+size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw);
+size_t direct_smem_bytes(int warps);
+int reduce_blocks(long long n);
+
+}  // namespace qc

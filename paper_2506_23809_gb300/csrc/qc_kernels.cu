@@ -1,0 +1,990 @@
+// qc_kernels.cu -- sm_103a kernels of libqc_eloc.
+//
+// The method (arxiv 2506.23809, Sec. III-B, Eq. 5 and Alg. 3): for every unique sample x,
+// E_loc(x) = <x|H|x> + sum over single and double excitations x' of x of
+// <x|H|x'> psi(x')/psi(x), with H of Eq. 2 and, in sample-space mode, x' restricted to the
+// table of unique samples (the lookup table of Sec. IV-C-4).  Alg. 3 spreads the sum as
+// processes -> threads -> SIMD lanes; here it is grid -> warp per sample -> lanes over
+// excitations.  Its three SIMD devices map as follows:
+//   * qubit packing    -> a key is one 128-bit word pair (ulonglong2 loads);
+//   * branch elimination -> excitations are enumerated class by class (singles, same-spin
+//     and opposite-spin doubles) as products of two short per-sample lists, so no lane
+//     ever tests the excitation degree;
+//   * SIMD parity      -> the fermionic phase is a sum of four prefix popcounts.
+//
+// Lookup: every key k has a linear hash H(k) = XOR of T[b] over its set bits b, so the hash
+// of x' = x ^ {i, j, a, b} is H(x) ^ T[i] ^ T[j] ^ T[a] ^ T[b] -- four XORs, no key walk.
+// The low 32 bits of H index a blocked Bloom filter (two bits in one 32-bit word) that
+// every CTA holds in shared memory (loaded by a 1-D bulk async copy); lanes whose x' passes
+// are compacted into a per-warp queue and resolved 32 at a time against an open-addressing
+// bucket table in global memory (L2 resident), keyed by a mix of the full 64-bit H and
+// checked against the stored 128-bit key.  Only then are the matrix element (Slater-Condon)
+// and psi(x') read.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qc_internal.h"
+#include "qc_eloc.h"
+
+namespace qc {
+
+#define QC_FULLMASK 0xffffffffu
+
+// ------------------------------------------------------------------------------------
+// small device helpers
+// ------------------------------------------------------------------------------------
+// MurmurHash3's 64-bit finalizer (Appleby, public domain): a bijective bit mixer.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdULL;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ULL;
+    k ^= k >> 33;
+    return k;
+}
+
+// occupied spin orbitals of x strictly below spin orbital k (0 <= k < 128)
+__device__ __forceinline__ int below(ulonglong2 x, int k) {
+    unsigned long long m0 = (k >= 64) ? ~0ULL : ((1ULL << k) - 1ULL);
+    unsigned long long m1 = (k > 64) ? ((1ULL << (k - 64)) - 1ULL) : 0ULL;
+    return __popcll(x.x & m0) + __popcll(x.y & m1);
+}
+
+__device__ __forceinline__ void flip(ulonglong2& x, int k) {
+    unsigned long long bit = 1ULL << (k & 63);
+    if (k < 64) x.x ^= bit; else x.y ^= bit;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(QC_FULLMASK, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(QC_FULLMASK, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_xor_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v ^= __shfl_xor_sync(QC_FULLMASK, v, o);
+    return v;
+}
+
+// Knuth's TwoSum accumulation in FP32: (s, c) holds the running sum and its error.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+    float t = __fadd_rn(s, x);
+    float bp = __fsub_rn(t, s);
+    float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    s = t;
+    c = __fadd_rn(c, e);
+}
+
+// ------------------------------------------------------------------------------------
+// mbarrier + 1-D bulk async copy (global -> shared), bounded waits
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+constexpr unsigned kWaitLimit = 1u << 24;  // bounded spin on the filter copy
+
+// ------------------------------------------------------------------------------------
+// lookup in the bucket table
+// ------------------------------------------------------------------------------------
+// Returns the table row of key, or -1.  Buckets hold two 64-bit entries
+// (fingerprint << 32 | row + 1); an empty entry ends the probe sequence.
+__device__ __forceinline__ long long table_find(const TableParams& tp, ulonglong2 key,
+                                                unsigned long long h) {
+    const unsigned long long m = mix64(h);
+    const unsigned fp = static_cast<unsigned>(m >> 32);
+    unsigned b = static_cast<unsigned>(m) & tp.nb_mask;
+    const ulonglong2* buckets = reinterpret_cast<const ulonglong2*>(tp.slots);
+    for (unsigned it = 0; it <= tp.nb_mask; ++it) {
+        const ulonglong2 e = __ldg(buckets + b);
+        if (e.x == 0ULL) return -1;
+        if (static_cast<unsigned>(e.x >> 32) == fp) {
+            const long long r = static_cast<long long>(static_cast<unsigned>(e.x)) - 1;
+            const ulonglong2 k = __ldg(tp.keys + r);
+            if (k.x == key.x && k.y == key.y) return r;
+        }
+        if (e.y == 0ULL) return -1;
+        if (static_cast<unsigned>(e.y >> 32) == fp) {
+            const long long r = static_cast<long long>(static_cast<unsigned>(e.y)) - 1;
+            const ulonglong2 k = __ldg(tp.keys + r);
+            if (k.x == key.x && k.y == key.y) return r;
+        }
+        b = (b + 1u) & tp.nb_mask;
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------------------------------
+// K0: table build (hash index + Bloom filter + validation)
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) build_table_kernel(TableParams tp, int n_orb, int na, int nb,
+                                                          const unsigned long long* __restrict__ T,
+                                                          unsigned long long* slots,
+                                                          uint32_t* filter, Counters* ctr) {
+    const long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= tp.n) return;
+    const ulonglong2 key = tp.keys[r];
+    unsigned flags = 0;
+    if (r > 0) {
+        const ulonglong2 prev = tp.keys[r - 1];
+        const bool eq = prev.x == key.x && prev.y == key.y;
+        const bool gt = (prev.y > key.y) || (prev.y == key.y && prev.x > key.x);
+        if (eq) flags |= QC_FLAG_DUP;
+        if (gt) flags |= QC_FLAG_UNSORTED;
+    }
+    const unsigned long long even = 0x5555555555555555ULL;
+    const int ea = __popcll(key.x & even) + __popcll(key.y & even);
+    const int eb = __popcll(key.x & ~even) + __popcll(key.y & ~even);
+    bool high = false;
+    if (n_orb < 128) {
+        if (n_orb <= 64) high = (key.y != 0ULL) || (n_orb < 64 && (key.x >> n_orb) != 0ULL);
+        else high = (key.y >> (n_orb - 64)) != 0ULL;
+    }
+    if (ea != na || eb != nb || high) flags |= QC_FLAG_NELEC;
+
+    unsigned long long h = 0;
+    for (unsigned long long w = key.x; w; w &= w - 1ULL) h ^= __ldg(T + (__ffsll(w) - 1));
+    for (unsigned long long w = key.y; w; w &= w - 1ULL) h ^= __ldg(T + 64 + (__ffsll(w) - 1));
+
+    if (tp.filter != nullptr) {
+        const unsigned g = static_cast<unsigned>(h);
+        const unsigned wmask = (1u << tp.fw) - 1u;
+        atomicOr(filter + ((g >> 5) & wmask), (1u << (g & 31u)) | (1u << (g >> 27)));
+    }
+    const unsigned long long m = mix64(h);
+    const unsigned long long entry =
+        (static_cast<unsigned long long>(static_cast<unsigned>(m >> 32)) << 32) |
+        static_cast<unsigned long long>(static_cast<unsigned>(r + 1));
+    unsigned b = static_cast<unsigned>(m) & tp.nb_mask;
+    bool placed = false;
+    for (unsigned it = 0; it <= tp.nb_mask && !placed; ++it) {
+        if (atomicCAS(slots + 2 * b, 0ULL, entry) == 0ULL) { placed = true; break; }
+        if (atomicCAS(slots + 2 * b + 1, 0ULL, entry) == 0ULL) { placed = true; break; }
+        b = (b + 1u) & tp.nb_mask;
+    }
+    if (!placed) flags |= QC_FLAG_TABLE_FULL;
+    if (flags) atomicOr(&ctr->flags, flags);
+}
+
+// ------------------------------------------------------------------------------------
+// per-sample state of the main kernels
+// ------------------------------------------------------------------------------------
+struct WarpLists {  // per-warp shared memory
+    unsigned char* occA;
+    unsigned char* virA;
+    unsigned char* occB;
+    unsigned char* virB;
+};
+
+struct Acc {
+    double re, im;       // FP64 accumulation of sum H psi(x')
+    float sr, cr, si, ci;  // FP32 TwoSum accumulation of sum H psi(x')/psi(x)
+    unsigned hits;
+    unsigned long long rowsum;
+    long long signsum;
+    unsigned long long missing;
+};
+
+// Decode a candidate (class, u, w) into spin orbitals: i -> a, and j -> b for doubles
+// (j = b = -1 for singles).  Classes: 0 alpha single (w), 1 beta single (w), 2 alpha-alpha
+// double (u: occupied pair, w: empty pair), 3 beta-beta double, 4 alpha-beta double
+// (u: alpha single, w: beta single).  Same-spin doubles have i < j and a < b.
+__device__ __forceinline__ void decode(unsigned code, const SysParams& sp, const WarpLists& L,
+                                       const unsigned short* __restrict__ lut, int& i, int& a,
+                                       int& j, int& b) {
+    const int cls = static_cast<int>(code >> 24);
+    const int u = static_cast<int>((code >> 12) & 4095u);
+    const int w = static_cast<int>(code & 4095u);
+    j = -1;
+    b = -1;
+    if (cls == 0) {
+        const int io = w / sp.va, av = w - io * sp.va;
+        i = 2 * L.occA[io];
+        a = 2 * L.virA[av];
+    } else if (cls == 1) {
+        const int io = w / sp.vb, av = w - io * sp.vb;
+        i = 2 * L.occB[io] + 1;
+        a = 2 * L.virB[av] + 1;
+    } else if (cls == 2) {
+        const unsigned po = lut[u], pv = lut[w];
+        i = 2 * L.occA[po & 255u];
+        j = 2 * L.occA[po >> 8];
+        a = 2 * L.virA[pv & 255u];
+        b = 2 * L.virA[pv >> 8];
+    } else if (cls == 3) {
+        const unsigned po = lut[u], pv = lut[w];
+        i = 2 * L.occB[po & 255u] + 1;
+        j = 2 * L.occB[po >> 8] + 1;
+        a = 2 * L.virB[pv & 255u] + 1;
+        b = 2 * L.virB[pv >> 8] + 1;
+    } else {
+        const int io = u / sp.va, av = u - io * sp.va;
+        const int jo = w / sp.vb, bv = w - jo * sp.vb;
+        i = 2 * L.occA[io];
+        a = 2 * L.virA[av];
+        j = 2 * L.occB[jo] + 1;
+        b = 2 * L.virB[bv] + 1;
+    }
+}
+
+// Resolve one candidate: look x' up; on a hit add <x|H|x'> psi(x') (FP64) or
+// <x|H|x'> psi(x')/psi(x) (FP32, TwoSum) to the lane accumulator.
+template <int PREC>
+__device__ __forceinline__ void resolve(unsigned code, bool valid, const SysParams& sp,
+                                        const TableParams& tp, int mode, const WarpLists& L,
+                                        const unsigned short* __restrict__ lut,
+                                        const unsigned long long* __restrict__ T64, ulonglong2 x,
+                                        unsigned long long hx, float2 invpsi32, Acc& acc) {
+    if (!valid) return;
+    int i, a, j, b;
+    decode(code, sp, L, lut, i, a, j, b);
+    ulonglong2 xp = x;
+    flip(xp, i);
+    flip(xp, a);
+    unsigned long long h = hx ^ T64[i] ^ T64[a];
+    if (j >= 0) {
+        flip(xp, j);
+        flip(xp, b);
+        h ^= T64[j] ^ T64[b];
+    }
+    const long long row = table_find(tp, xp, h);
+    if (row < 0) {
+        if (mode == QC_FULL) acc.missing++;
+        return;
+    }
+    const int K = sp.K;
+    const int ki = i >> 1, ka = a >> 1;
+    double elem64 = 0.0;
+    float elem32 = 0.f;
+    int par;
+    int sorted_flip = 0;
+    if (j < 0) {
+        // single i -> a:  h_ai + sum_k occ (ai|kk) - sum_k occ, same spin (ak|ki)
+        const int s = i & 1;
+        const size_t row_ai = (static_cast<size_t>(ka) * K + ki) * K;
+        if (PREC == QC_FP64) {
+            double f = sp.h[ka * K + ki];
+            for (int q = 0; q < sp.oa; ++q) {
+                const int k = L.occA[q];
+                f += sp.eri[(row_ai + k) * K + k];
+                if (s == 0) f -= sp.eri[((static_cast<size_t>(ka) * K + k) * K + k) * K + ki];
+            }
+            for (int q = 0; q < sp.ob; ++q) {
+                const int k = L.occB[q];
+                f += sp.eri[(row_ai + k) * K + k];
+                if (s == 1) f -= sp.eri[((static_cast<size_t>(ka) * K + k) * K + k) * K + ki];
+            }
+            elem64 = f;
+        } else {
+            float f = sp.h32[ka * K + ki];
+            for (int q = 0; q < sp.oa; ++q) {
+                const int k = L.occA[q];
+                f += sp.eri32[(row_ai + k) * K + k];
+                if (s == 0) f -= sp.eri32[((static_cast<size_t>(ka) * K + k) * K + k) * K + ki];
+            }
+            for (int q = 0; q < sp.ob; ++q) {
+                const int k = L.occB[q];
+                f += sp.eri32[(row_ai + k) * K + k];
+                if (s == 1) f -= sp.eri32[((static_cast<size_t>(ka) * K + k) * K + k) * K + ki];
+            }
+            elem32 = f;
+        }
+        par = below(x, i) + below(x, a) + (i < a);
+    } else {
+        const int kj = j >> 1, kb = b >> 1;
+        const size_t d = ((static_cast<size_t>(ka) * K + ki) * K + kb) * K + kj;  // (ai|bj)
+        par = below(x, i) + below(x, j) + below(x, a) + below(x, b) + (i < j) + (i < b) +
+              (j < b) + (i < a) + (j < a) + (b < a);
+        if ((i & 1) == (j & 1)) {
+            const size_t e = ((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki;  // (aj|bi)
+            if (PREC == QC_FP64) elem64 = sp.eri[d] - sp.eri[e];
+            else elem32 = sp.eri32[d] - sp.eri32[e];
+        } else {
+            if (PREC == QC_FP64) elem64 = sp.eri[d];
+            else elem32 = sp.eri32[d];
+            sorted_flip = (i > j) + (a > b);
+        }
+    }
+    const bool neg = (par & 1) != 0;
+    const double2 pp = __ldg(tp.psi + row);
+    if (PREC == QC_FP64) {
+        const double hv = neg ? -elem64 : elem64;
+        acc.re = fma(hv, pp.x, acc.re);
+        acc.im = fma(hv, pp.y, acc.im);
+    } else {
+        const float hv = neg ? -elem32 : elem32;
+        const float px = static_cast<float>(pp.x), py = static_cast<float>(pp.y);
+        const float rr = __fsub_rn(__fmul_rn(px, invpsi32.x), __fmul_rn(py, invpsi32.y));
+        const float ri = __fadd_rn(__fmul_rn(px, invpsi32.y), __fmul_rn(py, invpsi32.x));
+        two_sum_acc(acc.sr, acc.cr, __fmul_rn(hv, rr));
+        two_sum_acc(acc.si, acc.ci, __fmul_rn(hv, ri));
+    }
+    acc.hits++;
+    acc.rowsum += static_cast<unsigned long long>(row + 1);
+    const bool sneg = neg != ((sorted_flip & 1) != 0);
+    acc.signsum += sneg ? -(row + 1) : (row + 1);
+}
+
+// Per-sample set-up shared by both main kernels.  Returns false when x does not hold
+// na alpha and nb beta electrons below n_orb (then nothing is written to the lists).
+__device__ __forceinline__ bool sample_setup(const SysParams& sp, ulonglong2 x, int lane,
+                                             const WarpLists& L,
+                                             const unsigned long long* __restrict__ T64,
+                                             unsigned long long& hx, double& ediag) {
+    const unsigned long long even = 0x5555555555555555ULL;
+    const int ea = __popcll(x.x & even) + __popcll(x.y & even);
+    const int eb = __popcll(x.x & ~even) + __popcll(x.y & ~even);
+    bool high = false;
+    if (sp.n_orb < 128) {
+        if (sp.n_orb <= 64) high = (x.y != 0ULL) || (sp.n_orb < 64 && (x.x >> sp.n_orb) != 0ULL);
+        else high = (x.y >> (sp.n_orb - 64)) != 0ULL;
+    }
+    if (ea != sp.na || eb != sp.nb || high) return false;
+    // spatial occupation strings: lane l owns spatial orbitals l and l + 32
+    const unsigned alo = __ballot_sync(QC_FULLMASK, (x.x >> (2 * lane)) & 1ULL);
+    const unsigned ahi = __ballot_sync(QC_FULLMASK, (x.y >> (2 * lane)) & 1ULL);
+    const unsigned blo = __ballot_sync(QC_FULLMASK, (x.x >> (2 * lane + 1)) & 1ULL);
+    const unsigned bhi = __ballot_sync(QC_FULLMASK, (x.y >> (2 * lane + 1)) & 1ULL);
+    const unsigned long long A = static_cast<unsigned long long>(alo) |
+                                 (static_cast<unsigned long long>(ahi) << 32);
+    const unsigned long long B = static_cast<unsigned long long>(blo) |
+                                 (static_cast<unsigned long long>(bhi) << 32);
+    for (int k = lane; k < sp.K; k += 32) {
+        const unsigned long long lowm = (1ULL << k) - 1ULL;
+        const int ca = __popcll(A & lowm), cb = __popcll(B & lowm);
+        if ((A >> k) & 1ULL) L.occA[ca] = static_cast<unsigned char>(k);
+        else L.virA[k - ca] = static_cast<unsigned char>(k);
+        if ((B >> k) & 1ULL) L.occB[cb] = static_cast<unsigned char>(k);
+        else L.virB[k - cb] = static_cast<unsigned char>(k);
+    }
+    // linear hash of x: XOR of T over set bits (lane l: bits l, l+32, l+64, l+96)
+    unsigned long long hv = 0;
+    if ((x.x >> lane) & 1ULL) hv ^= T64[lane];
+    if ((x.x >> (lane + 32)) & 1ULL) hv ^= T64[lane + 32];
+    if ((x.y >> lane) & 1ULL) hv ^= T64[lane + 64];
+    if ((x.y >> (lane + 32)) & 1ULL) hv ^= T64[lane + 96];
+    hx = warp_xor_u64(hv);
+    __syncwarp();
+    // diagonal: sum_p h_pp + 1/2 sum_{p,q occ} [(pp|qq) - d(sp,sq) (pq|qp)]  (FP64)
+    const int K = sp.K;
+    double ed = 0.0;
+    for (int idx = lane; idx < sp.oa + sp.ob; idx += 32) {
+        const bool isA = idx < sp.oa;
+        const int k = isA ? L.occA[idx] : L.occB[idx - sp.oa];
+        double sj = 0.0, sx = 0.0;
+        for (int q = 0; q < sp.oa; ++q) {
+            const int l = L.occA[q];
+            sj += sp.J[k * K + l];
+            if (isA) sx += sp.X[k * K + l];
+        }
+        for (int q = 0; q < sp.ob; ++q) {
+            const int l = L.occB[q];
+            sj += sp.J[k * K + l];
+            if (!isA) sx += sp.X[k * K + l];
+        }
+        ed += sp.h[k * K + k] + 0.5 * (sj - sx);
+    }
+    ediag = warp_sum(ed) + sp.e_core;
+    return true;
+}
+
+// Per-sample finish: reduce the lane accumulators and write the outputs.
+template <int PREC>
+__device__ __forceinline__ void sample_finish(const EvalParams& ep, long long s, int lane,
+                                              double ediag, double2 psix, Acc& acc) {
+    double sre, sim;
+    if (PREC == QC_FP64) {
+        sre = warp_sum(acc.re);
+        sim = warp_sum(acc.im);
+    } else {
+        sre = warp_sum(static_cast<double>(acc.sr) + static_cast<double>(acc.cr));
+        sim = warp_sum(static_cast<double>(acc.si) + static_cast<double>(acc.ci));
+    }
+    const unsigned long long hits = warp_sum_u64(acc.hits);
+    const unsigned long long rows = warp_sum_u64(acc.rowsum);
+    const long long sgn = static_cast<long long>(warp_sum_u64(static_cast<unsigned long long>(acc.signsum)));
+    const unsigned long long miss = warp_sum_u64(acc.missing);
+    if (lane == 0) {
+        double2 e;
+        const double n2 = psix.x * psix.x + psix.y * psix.y;
+        unsigned flags = 0;
+        bool bad = false;
+        if (n2 == 0.0) {
+            flags |= QC_FLAG_ZERO_PSI;
+            bad = true;
+        }
+        if (miss) {
+            flags |= QC_FLAG_MISSING;
+            bad = true;
+        }
+        if (bad) {
+            e.x = __longlong_as_double(0x7ff8000000000000LL);
+            e.y = e.x;
+        } else if (PREC == QC_FP64) {
+            // sum H psi(x') / psi(x) = S conj(psi) / |psi|^2
+            const double inv = 1.0 / n2;
+            e.x = ediag + (sre * psix.x + sim * psix.y) * inv;
+            e.y = (sim * psix.x - sre * psix.y) * inv;
+        } else {
+            e.x = ediag + sre;
+            e.y = sim;
+        }
+        ep.eloc[s] = e;
+        if (ep.hit_count) ep.hit_count[s] = static_cast<uint32_t>(hits);
+        if (ep.hit_rowsum) ep.hit_rowsum[s] = rows;
+        if (ep.hit_signsum) ep.hit_signsum[s] = sgn;
+        if (hits) atomicAdd(&ep.ctr->hits, hits);
+        if (miss) atomicAdd(&ep.ctr->missing, miss);
+        if (bad) atomicAdd(&ep.ctr->bad, 1ULL);
+        if (flags) atomicOr(&ep.ctr->flags, flags);
+    }
+}
+
+__device__ __forceinline__ void invalid_sample(const EvalParams& ep, long long s, int lane) {
+    if (lane == 0) {
+        double2 e;
+        e.x = __longlong_as_double(0x7ff8000000000000LL);
+        e.y = e.x;
+        ep.eloc[s] = e;
+        if (ep.hit_count) ep.hit_count[s] = 0;
+        if (ep.hit_rowsum) ep.hit_rowsum[s] = 0;
+        if (ep.hit_signsum) ep.hit_signsum[s] = 0;
+        atomicAdd(&ep.ctr->bad, 1ULL);
+        atomicAdd(&ep.ctr->invalid, 1ULL);
+        atomicOr(&ep.ctr->flags, QC_FLAG_NELEC);
+    }
+}
+
+__device__ __forceinline__ float2 inv_psi32(double2 p) {
+    const double n2 = p.x * p.x + p.y * p.y;
+    const double inv = n2 > 0.0 ? 1.0 / n2 : 0.0;
+    return make_float2(static_cast<float>(p.x * inv), static_cast<float>(-p.y * inv));
+}
+
+// colex pair table: p = C(hi, 2) + lo  ->  lo | hi << 8
+__device__ void fill_pair_lut(unsigned short* lut) {
+    for (int p = threadIdx.x; p < kPairLut; p += blockDim.x) {
+        int hi = static_cast<int>((1.0f + sqrtf(1.0f + 8.0f * static_cast<float>(p))) * 0.5f);
+        while (hi * (hi - 1) / 2 > p) --hi;
+        while ((hi + 1) * hi / 2 <= p) ++hi;
+        const int lo = p - hi * (hi - 1) / 2;
+        lut[p] = static_cast<unsigned short>(lo | (hi << 8));
+    }
+}
+
+// shared-memory layout common to both main kernels
+constexpr size_t kOffBar = 0;
+constexpr size_t kOffT = 16;
+constexpr size_t kOffLut = kOffT + 128 * 8;
+constexpr size_t kOffVar = ((kOffLut + kPairLut * 2 + 127) / 128) * 128;  // 5120
+constexpr size_t kWarpFixed = 4 * 64 + 64 * 4;  // occ/vir lists + candidate queue
+
+__host__ __device__ inline size_t list_words(const SysParams& sp) {
+    return static_cast<size_t>(sp.nsa + sp.nsb + sp.npoa + sp.npva + sp.npob + sp.npvb + 4);
+}
+__host__ __device__ inline size_t filtered_warp_bytes(const SysParams& sp) {
+    return ((kWarpFixed + 4 * list_words(sp)) + 15) / 16 * 16;
+}
+
+size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw) {
+    return kOffVar + (static_cast<size_t>(4) << fw) + static_cast<size_t>(warps) * filtered_warp_bytes(sp);
+}
+size_t direct_smem_bytes(int warps) { return kOffVar + static_cast<size_t>(warps) * kWarpFixed; }
+
+// ------------------------------------------------------------------------------------
+// K2a: direct kernel -- every connected x' is looked up (FULL mode; SAMPLE without filter)
+// ------------------------------------------------------------------------------------
+template <int PREC>
+__global__ void __launch_bounds__(1024) eloc_direct_kernel(SysParams sp, TableParams tp,
+                                                           EvalParams ep) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned long long* T64 = reinterpret_cast<unsigned long long*>(smem + kOffT);
+    unsigned short* lut = reinterpret_cast<unsigned short*>(smem + kOffLut);
+    for (int t = threadIdx.x; t < 128; t += blockDim.x) T64[t] = ep.T[t];
+    fill_pair_lut(lut);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned char* wbase = smem + kOffVar + static_cast<size_t>(warp) * kWarpFixed;
+    WarpLists L{wbase, wbase + 64, wbase + 128, wbase + 192};
+    const unsigned c0 = sp.nsa, c1 = c0 + sp.nsb;
+    const unsigned c2 = c1 + static_cast<unsigned>(sp.npoa) * sp.npva;
+    const unsigned c3 = c2 + static_cast<unsigned>(sp.npob) * sp.npvb;
+    const unsigned npairs = static_cast<unsigned>(sp.pairs);
+    for (long long s = static_cast<long long>(blockIdx.x) * nw + warp; s < ep.n_u;
+         s += static_cast<long long>(gridDim.x) * nw) {
+        const ulonglong2 x = ep.samples[s];
+        unsigned long long hx;
+        double ediag;
+        if (!sample_setup(sp, x, lane, L, T64, hx, ediag)) {
+            invalid_sample(ep, s, lane);
+            continue;
+        }
+        const double2 psix = ep.psi[s];
+        const float2 ip32 = inv_psi32(psix);
+        Acc acc{};
+        for (unsigned t = lane; t < npairs; t += 32) {
+            unsigned code;
+            if (t < c0) {
+                code = t;
+            } else if (t < c1) {
+                code = (1u << 24) | (t - c0);
+            } else if (t < c2) {
+                const unsigned r = t - c1, u = r / sp.npva, w = r - u * sp.npva;
+                code = (2u << 24) | (u << 12) | w;
+            } else if (t < c3) {
+                const unsigned r = t - c2, u = r / sp.npvb, w = r - u * sp.npvb;
+                code = (3u << 24) | (u << 12) | w;
+            } else {
+                const unsigned r = t - c3, u = r / sp.nsb, w = r - u * sp.nsb;
+                code = (4u << 24) | (u << 12) | w;
+            }
+            resolve<PREC>(code, true, sp, tp, ep.mode, L, lut, T64, x, hx, ip32, acc);
+        }
+        sample_finish<PREC>(ep, s, lane, ediag, psix, acc);
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// K2b: filtered kernel -- Bloom filter in shared memory in front of the bucket table
+// ------------------------------------------------------------------------------------
+template <int U>
+struct FilterLoop {
+    // One class of excitations as the product outer x inner of two per-sample hash
+    // lists; lanes walk the inner list, U outer entries per pass.
+    template <int PREC>
+    __device__ __forceinline__ static void run(const uint32_t* O, int n1, const uint32_t* In, int n2,
+                                               unsigned cls, uint32_t hx32,
+                                               const uint32_t* __restrict__ filt, uint32_t wmask,
+                                               uint32_t* q, int& qn, int lane, const SysParams& sp,
+                                               const TableParams& tp, const WarpLists& L,
+                                               const unsigned short* lut,
+                                               const unsigned long long* T64, ulonglong2 x,
+                                               unsigned long long hx, float2 ip32, Acc& acc) {
+        const unsigned ltmask = lanemask_lt();
+        for (int u0 = 0; u0 < n1; u0 += U) {
+            uint32_t hu[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) hu[k] = hx32 ^ ((u0 + k < n1) ? O[u0 + k] : 0u);
+            for (int w0 = 0; w0 < n2; w0 += 32) {
+                const int w = w0 + lane;
+                const bool wv = w < n2;
+                const uint32_t hw = wv ? In[w] : 0u;
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    const uint32_t g = hu[k] ^ hw;
+                    const uint32_t word = filt[(g >> 5) & wmask];
+                    const uint32_t t = __funnelshift_r(word, word, g) & __funnelshift_r(word, word, g >> 27);
+                    const bool pass = wv && (u0 + k < n1) && (t & 1u);
+                    const unsigned m = __ballot_sync(QC_FULLMASK, pass);
+                    if (m) {
+                        if (pass)
+                            q[qn + __popc(m & ltmask)] =
+                                (cls << 24) | (static_cast<unsigned>(u0 + k) << 12) | static_cast<unsigned>(w);
+                        qn += __popc(m);
+                        if (qn >= 32) {
+                            __syncwarp();
+                            const unsigned code = q[lane];
+                            __syncwarp();
+                            const int rem = qn - 32;
+                            if (lane < rem) q[lane] = q[32 + lane];
+                            qn = rem;
+                            __syncwarp();
+                            resolve<PREC>(code, true, sp, tp, QC_SAMPLE, L, lut, T64, x, hx, ip32, acc);
+                        }
+                    }
+                }
+            }
+        }
+    }
+};
+
+template <int PREC, int U>
+__global__ void __launch_bounds__(1024) eloc_filtered_kernel(SysParams sp, TableParams tp,
+                                                             EvalParams ep) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + kOffBar);
+    unsigned long long* T64 = reinterpret_cast<unsigned long long*>(smem + kOffT);
+    unsigned short* lut = reinterpret_cast<unsigned short*>(smem + kOffLut);
+    uint32_t* filt = reinterpret_cast<uint32_t*>(smem + kOffVar);
+    const unsigned fbytes = 4u << tp.fw;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, fbytes);
+        constexpr unsigned kChunk = 32768;
+        for (unsigned off = 0; off < fbytes; off += kChunk) {
+            const unsigned n = (fbytes - off < kChunk) ? (fbytes - off) : kChunk;
+            bulk_g2s(reinterpret_cast<unsigned char*>(filt) + off,
+                     reinterpret_cast<const unsigned char*>(tp.filter) + off, n, bar);
+        }
+    }
+    for (int t = threadIdx.x; t < 128; t += blockDim.x) T64[t] = ep.T[t];
+    fill_pair_lut(lut);
+    bool ready = false;
+    for (unsigned it = 0; it < kWaitLimit; ++it) {
+        if (mbar_try_wait(bar, 0)) {
+            ready = true;
+            break;
+        }
+    }
+    if (!__syncthreads_and(ready ? 1 : 0)) {
+        // the copy did not land in time: report, give it one more bounded wait, leave
+        // (the whole CTA leaves together: the decision above is CTA-uniform)
+        if (threadIdx.x == 0) atomicOr(&ep.ctr->flags, QC_FLAG_TIMEOUT);
+        if (!ready)
+            for (unsigned it = 0; it < kWaitLimit; ++it)
+                if (mbar_try_wait(bar, 0)) break;
+        return;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned char* wbase = smem + kOffVar + fbytes + static_cast<size_t>(warp) * filtered_warp_bytes(sp);
+    WarpLists L{wbase, wbase + 64, wbase + 128, wbase + 192};
+    uint32_t* q = reinterpret_cast<uint32_t*>(wbase + 256);
+    uint32_t* lists = reinterpret_cast<uint32_t*>(wbase + kWarpFixed);
+    uint32_t* zero = lists;            // one zero word: the outer list of the singles
+    uint32_t* SA = lists + 4;
+    uint32_t* SB = SA + sp.nsa;
+    uint32_t* PAo = SB + sp.nsb;
+    uint32_t* PAv = PAo + sp.npoa;
+    uint32_t* PBo = PAv + sp.npva;
+    uint32_t* PBv = PBo + sp.npob;
+    const uint32_t wmask = (1u << tp.fw) - 1u;
+    if (lane == 0) zero[0] = 0u;
+
+    for (long long s = static_cast<long long>(blockIdx.x) * nw + warp; s < ep.n_u;
+         s += static_cast<long long>(gridDim.x) * nw) {
+        const ulonglong2 x = ep.samples[s];
+        unsigned long long hx;
+        double ediag;
+        if (!sample_setup(sp, x, lane, L, T64, hx, ediag)) {
+            invalid_sample(ep, s, lane);
+            continue;
+        }
+        // per-sample hash lists (low 32 bits of the linear hash contributions)
+        for (int t = lane; t < sp.nsa; t += 32) {
+            const int io = t / sp.va, av = t - io * sp.va;
+            SA[t] = static_cast<uint32_t>(T64[2 * L.occA[io]] ^ T64[2 * L.virA[av]]);
+        }
+        for (int t = lane; t < sp.nsb; t += 32) {
+            const int io = t / sp.vb, av = t - io * sp.vb;
+            SB[t] = static_cast<uint32_t>(T64[2 * L.occB[io] + 1] ^ T64[2 * L.virB[av] + 1]);
+        }
+        for (int t = lane; t < sp.npoa; t += 32) {
+            const unsigned p = lut[t];
+            PAo[t] = static_cast<uint32_t>(T64[2 * L.occA[p & 255u]] ^ T64[2 * L.occA[p >> 8]]);
+        }
+        for (int t = lane; t < sp.npva; t += 32) {
+            const unsigned p = lut[t];
+            PAv[t] = static_cast<uint32_t>(T64[2 * L.virA[p & 255u]] ^ T64[2 * L.virA[p >> 8]]);
+        }
+        for (int t = lane; t < sp.npob; t += 32) {
+            const unsigned p = lut[t];
+            PBo[t] = static_cast<uint32_t>(T64[2 * L.occB[p & 255u] + 1] ^ T64[2 * L.occB[p >> 8] + 1]);
+        }
+        for (int t = lane; t < sp.npvb; t += 32) {
+            const unsigned p = lut[t];
+            PBv[t] = static_cast<uint32_t>(T64[2 * L.virB[p & 255u] + 1] ^ T64[2 * L.virB[p >> 8] + 1]);
+        }
+        __syncwarp();
+        const double2 psix = ep.psi[s];
+        const float2 ip32 = inv_psi32(psix);
+        const uint32_t hx32 = static_cast<uint32_t>(hx);
+        Acc acc{};
+        int qn = 0;
+        FilterLoop<1>::template run<PREC>(zero, 1, SA, sp.nsa, 0u, hx32, filt, wmask, q, qn, lane, sp, tp, L, lut, T64, x, hx, ip32, acc);
+        FilterLoop<1>::template run<PREC>(zero, 1, SB, sp.nsb, 1u, hx32, filt, wmask, q, qn, lane, sp, tp, L, lut, T64, x, hx, ip32, acc);
+        FilterLoop<U>::template run<PREC>(PAo, sp.npoa, PAv, sp.npva, 2u, hx32, filt, wmask, q, qn, lane, sp, tp, L, lut, T64, x, hx, ip32, acc);
+        FilterLoop<U>::template run<PREC>(PBo, sp.npob, PBv, sp.npvb, 3u, hx32, filt, wmask, q, qn, lane, sp, tp, L, lut, T64, x, hx, ip32, acc);
+        FilterLoop<U>::template run<PREC>(SA, sp.nsa, SB, sp.nsb, 4u, hx32, filt, wmask, q, qn, lane, sp, tp, L, lut, T64, x, hx, ip32, acc);
+        __syncwarp();
+        const unsigned code = q[lane];
+        const bool v = lane < qn;
+        __syncwarp();
+        resolve<PREC>(code, v, sp, tp, QC_SAMPLE, L, lut, T64, x, hx, ip32, acc);
+        sample_finish<PREC>(ep, s, lane, ediag, psix, acc);
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// K3: Eq. 1 reduction (two passes, deterministic order, last-block finish)
+// ------------------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+
+int reduce_blocks(long long n) {
+    long long b = (n + kRedThreads * 8 - 1) / (kRedThreads * 8);
+    if (b < 1) b = 1;
+    if (b > 1024) b = 1024;
+    return static_cast<int>(b);
+}
+
+template <typename Tv>
+__device__ __forceinline__ Tv block_sum(Tv v, Tv* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = sh[threadIdx.x] + sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    Tv r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kRedThreads) reduce_pass1(EvalParams ep, double* part) {
+    __shared__ double shd[kRedThreads];
+    __shared__ long long shl[kRedThreads];
+    __shared__ bool last;
+    long long w = 0, used = 0;
+    double sr = 0.0, si = 0.0;
+    bool neg = false;
+    for (long long i = static_cast<long long>(blockIdx.x) * kRedThreads + threadIdx.x; i < ep.n_u;
+         i += static_cast<long long>(gridDim.x) * kRedThreads) {
+        const double2 e = ep.eloc[i];
+        const long long c = ep.counts[i];
+        if (c < 0) {
+            neg = true;
+            continue;
+        }
+        if (isfinite(e.x) && isfinite(e.y)) {
+            w += c;
+            sr += static_cast<double>(c) * e.x;
+            si += static_cast<double>(c) * e.y;
+            used++;
+        }
+    }
+    if (neg) atomicOr(&ep.ctr->flags, QC_FLAG_NEG_COUNT);
+    const long long bw = block_sum<long long>(w, shl);
+    const long long bu = block_sum<long long>(used, shl);
+    const double bsr = block_sum<double>(sr, shd);
+    const double bsi = block_sum<double>(si, shd);
+    if (threadIdx.x == 0) {
+        part[4 * blockIdx.x + 0] = bsr;
+        part[4 * blockIdx.x + 1] = bsi;
+        part[4 * blockIdx.x + 2] = __longlong_as_double(bw);
+        part[4 * blockIdx.x + 3] = __longlong_as_double(bu);
+        __threadfence();
+        last = (atomicAdd(&ep.ctr->ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double tr = 0.0, ti = 0.0;
+        long long tw = 0, tu = 0;
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            tr += __ldcg(part + 4 * b + 0);
+            ti += __ldcg(part + 4 * b + 1);
+            tw += __double_as_longlong(__ldcg(part + 4 * b + 2));
+            tu += __double_as_longlong(__ldcg(part + 4 * b + 3));
+        }
+        Counters* c = ep.ctr;
+        c->w = tw;
+        c->used = static_cast<unsigned long long>(tu);
+        c->sce_re = tr;
+        c->sce_im = ti;
+        c->mean_re = tr / static_cast<double>(tw);
+        c->mean_im = ti / static_cast<double>(tw);
+        c->ticket = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) reduce_pass2(EvalParams ep, double* part,
+                                                            qc_eloc_summary* out, long long pairs_per_sample) {
+    __shared__ double shd[kRedThreads];
+    __shared__ bool last;
+    const double mr = ep.ctr->mean_re, mi = ep.ctr->mean_im;
+    double v = 0.0;
+    for (long long i = static_cast<long long>(blockIdx.x) * kRedThreads + threadIdx.x; i < ep.n_u;
+         i += static_cast<long long>(gridDim.x) * kRedThreads) {
+        const double2 e = ep.eloc[i];
+        const long long c = ep.counts[i];
+        if (c < 0 || !isfinite(e.x) || !isfinite(e.y)) continue;
+        const double dr = e.x - mr, di = e.y - mi;
+        v += static_cast<double>(c) * (dr * dr + di * di);
+    }
+    const double bv = block_sum<double>(v, shd);
+    if (threadIdx.x == 0) {
+        part[4 * blockIdx.x] = bv;
+        __threadfence();
+        last = (atomicAdd(&ep.ctr->ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double tv = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) tv += __ldcg(part + 4 * b);
+        Counters* c = ep.ctr;
+        const unsigned f = c->flags;
+        int st = QC_OK;
+        if (f & QC_FLAG_UNSORTED) st = QC_ERR_UNSORTED;
+        else if (f & QC_FLAG_DUP) st = QC_ERR_DUP;
+        else if (f & QC_FLAG_NELEC) st = QC_ERR_NELEC;
+        else if (f & QC_FLAG_NEG_COUNT) st = QC_ERR_COUNTS;
+        else if (f & QC_FLAG_TABLE_FULL) st = QC_ERR_CAPACITY;
+        else if (f & QC_FLAG_TIMEOUT) st = QC_ERR_TIMEOUT;
+        else if (f & QC_FLAG_MISSING) st = QC_ERR_MISSING;
+        else if (f & QC_FLAG_ZERO_PSI) st = QC_ERR_ZERO_PSI;
+        const double w = static_cast<double>(c->w);
+        out->e_re = c->mean_re;
+        out->e_im = c->mean_im;
+        out->var = tv / w;
+        out->w = w;
+        out->sum_ce_re = c->sce_re;
+        out->sum_ce_im = c->sce_im;
+        out->n_used = c->used;
+        out->n_pairs = static_cast<unsigned long long>(ep.n_u - static_cast<long long>(c->invalid)) *
+                       static_cast<unsigned long long>(pairs_per_sample);
+        out->n_hits = c->hits;
+        out->n_missing = c->missing;
+        out->n_bad = c->bad;
+        out->flags = f;
+        out->status = st;
+        c->ticket = 0u;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// host launchers
+// ------------------------------------------------------------------------------------
+cudaError_t launch_build_table(const TableParams& tp, int n_orb, int na, int nb,
+                               const unsigned long long* T, unsigned long long* slots,
+                               uint32_t* filter, Counters* ctr, cudaStream_t s) {
+    if (tp.n <= 0) return cudaSuccess;
+    const long long blocks = (tp.n + 255) / 256;
+    build_table_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(tp, n_orb, na, nb, T, slots,
+                                                                      filter, ctr);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t launch_filtered_u(const SysParams& sp, const TableParams& tp,
+                                     const EvalParams& ep, const LaunchCfg& c, cudaStream_t s) {
+    const dim3 grid(c.grid), block(32 * c.warps);
+    switch (c.unroll) {
+        case 1: eloc_filtered_kernel<PREC, 1><<<grid, block, c.smem, s>>>(sp, tp, ep); break;
+        case 2: eloc_filtered_kernel<PREC, 2><<<grid, block, c.smem, s>>>(sp, tp, ep); break;
+        case 8: eloc_filtered_kernel<PREC, 8><<<grid, block, c.smem, s>>>(sp, tp, ep); break;
+        default: eloc_filtered_kernel<PREC, 4><<<grid, block, c.smem, s>>>(sp, tp, ep); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eloc_main(const SysParams& sp, const TableParams& tp, const EvalParams& ep,
+                             const LaunchCfg& c, cudaStream_t s) {
+    if (ep.n_u <= 0) return cudaSuccess;
+    if (c.kernel == 2) {
+        return sp.precision == QC_FP64 ? launch_filtered_u<QC_FP64>(sp, tp, ep, c, s)
+                                       : launch_filtered_u<QC_FP32_COMP>(sp, tp, ep, c, s);
+    }
+    const dim3 grid(c.grid), block(32 * c.warps);
+    if (sp.precision == QC_FP64)
+        eloc_direct_kernel<QC_FP64><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    else
+        eloc_direct_kernel<QC_FP32_COMP><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk, void* summary_dev,
+                          long long pairs_per_sample, cudaStream_t s) {
+    reduce_pass1<<<nblk, kRedThreads, 0, s>>>(ep, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_pass2<<<nblk, kRedThreads, 0, s>>>(ep, partials,
+                                              static_cast<qc_eloc_summary*>(summary_dev), pairs_per_sample);
+    return cudaGetLastError();
+}
+
+int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem) {
+    int n = 0;
+    cudaError_t e;
+    if (kernel == 2) {
+        const void* f = nullptr;
+        if (precision == QC_FP64) {
+            f = unroll == 1 ? (const void*)eloc_filtered_kernel<QC_FP64, 1>
+              : unroll == 2 ? (const void*)eloc_filtered_kernel<QC_FP64, 2>
+              : unroll == 8 ? (const void*)eloc_filtered_kernel<QC_FP64, 8>
+                            : (const void*)eloc_filtered_kernel<QC_FP64, 4>;
+        } else {
+            f = unroll == 1 ? (const void*)eloc_filtered_kernel<QC_FP32_COMP, 1>
+              : unroll == 2 ? (const void*)eloc_filtered_kernel<QC_FP32_COMP, 2>
+              : unroll == 8 ? (const void*)eloc_filtered_kernel<QC_FP32_COMP, 8>
+                            : (const void*)eloc_filtered_kernel<QC_FP32_COMP, 4>;
+        }
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem);
+    } else {
+        const void* f = precision == QC_FP64 ? (const void*)eloc_direct_kernel<QC_FP64>
+                                             : (const void*)eloc_direct_kernel<QC_FP32_COMP>;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem);
+    }
+    return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t prepare_kernels(size_t max_smem) {
+    const int v = static_cast<int>(max_smem);
+    cudaError_t e = cudaSuccess;
+#define QC_ATTR(k)                                                                    \
+    do {                                                                              \
+        cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, v); \
+        if (r != cudaSuccess) e = r;                                                  \
+    } while (0)
+    QC_ATTR(eloc_direct_kernel<QC_FP64>);
+    QC_ATTR(eloc_direct_kernel<QC_FP32_COMP>);
+    QC_ATTR((eloc_filtered_kernel<QC_FP64, 1>));
+    QC_ATTR((eloc_filtered_kernel<QC_FP64, 2>));
+    QC_ATTR((eloc_filtered_kernel<QC_FP64, 4>));
+    QC_ATTR((eloc_filtered_kernel<QC_FP64, 8>));
+    QC_ATTR((eloc_filtered_kernel<QC_FP32_COMP, 1>));
+    QC_ATTR((eloc_filtered_kernel<QC_FP32_COMP, 2>));
+    QC_ATTR((eloc_filtered_kernel<QC_FP32_COMP, 4>));
+    QC_ATTR((eloc_filtered_kernel<QC_FP32_COMP, 8>));
+#undef QC_ATTR
+    return e;
+}
+
+}  // namespace qc

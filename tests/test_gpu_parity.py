@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar (Eq. 5 / Eq. 1): connected sets, table rows and fermionic phases bit-exact (per-sample
+hit count, sum of rows, phase-weighted sum of rows); E_loc within 1e-6 relative for the
+FP64 path; |Delta E| <= 1e-5 Ha on the count-weighted energy for the FP32-compensated path.
+"""
+import numpy as np
+import pytest
+
+from paper_2506_23809_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+RTOL_FP64 = 1e-6     # relative, per-sample E_loc and energy (FP64 path)
+ATOL_FP32C = 1e-5    # Ha, count-weighted energy (FP32-compensated path)
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_23809_gb300 import binding, build
+    build.build()
+    binding.load_library()
+    return binding
+
+
+def run_gpu(B, ints, n_orb, n_elec, keys, counts, psi, table=None, prec=0, mode=0, opts=None,
+            diag=True, e_core=0.0):
+    import torch
+    h = B.qc_eloc_create(ints.h, ints.eri, e_core, n_orb, n_elec, prec, mode)
+    try:
+        for k, v in (opts or {}).items():
+            B.qc_eloc_set_option(h, k, v)
+        kt = B.keys_to_tensor(keys)
+        ct = torch.from_numpy(np.ascontiguousarray(counts, dtype=np.int64)).cuda()
+        pt = torch.from_numpy(np.ascontiguousarray(psi, dtype=np.complex128)).cuda()
+        tk = tp = None
+        if table is not None:
+            tk = B.keys_to_tensor(table[0])
+            tp = torch.from_numpy(np.ascontiguousarray(table[1], dtype=np.complex128)).cuda()
+        eloc, d = B.qc_eloc_eval(h, kt, ct, pt, tk, tp, diagnostics=diag)
+        summ = B.qc_eloc_summary_read(h)
+        cfg = B.qc_eloc_last_config(h)
+        out = dict(eloc=eloc.cpu().numpy(), summary=summ, cfg=cfg)
+        if diag:
+            out["hits"] = d["hit_count"].cpu().numpy().view(np.uint32)
+            out["rowsum"] = d["hit_rowsum"].cpu().numpy().view(np.uint64)
+            out["signsum"] = d["hit_signsum"].cpu().numpy()
+        return out
+    finally:
+        B.qc_eloc_destroy(h)
+
+
+def assert_sets_equal(g, det, rows=None):
+    sel = slice(None) if rows is None else rows
+    assert np.array_equal(g["hits"][sel], det["hits"]), "connected sets differ"
+    assert np.array_equal(g["rowsum"][sel], det["rowsum"]), "table rows differ"
+    assert np.array_equal(g["signsum"][sel], det["signsum"]), "fermionic phases differ"
+
+
+def assert_eloc_close(got, want, rtol=RTOL_FP64):
+    ok = np.isfinite(want)
+    assert np.array_equal(np.isfinite(got), ok)
+    err = np.abs(got[ok] - want[ok]) / np.maximum(1.0, np.abs(want[ok]))
+    assert err.max(initial=0.0) <= rtol, f"max rel err {err.max():.3e}"
+    return err.max(initial=0.0)
+
+
+KERNELS = [dict(), {2: 1}, {2: 2, 5: 1}, {2: 2, 5: 2}, {2: 2, 5: 4}, {2: 2, 5: 8}, {2: 2, 4: 3, 6: 5}]
+
+
+@pytest.mark.parametrize("opts", KERNELS, ids=["auto", "direct", "filt_u1", "filt_u2", "filt_u4",
+                                                "filt_u8", "filt_w3_g5"])
+def test_tiny_sample_mode(B, orc, opts):
+    """N=14, 6 electrons, 1,000 uniform samples (204 pairs each), every kernel variant."""
+    ints, s = I.make_workload("n14_e6_u1k")
+    g = run_gpu(B, ints, 14, 6, s.keys, s.counts, s.psi, opts=opts)
+    want, det = orc.eloc(ints.h, ints.eri, 0.0, 14, s.keys, s.psi, details=True)
+    assert_sets_equal(g, det)
+    assert_eloc_close(g["eloc"], want)
+    m, var, w, n = orc.reduce(want, s.counts)
+    sm = g["summary"]
+    assert sm["status"] == 0 and sm["flags"] == 0
+    assert sm["n_pairs"] == 1000 * 204 and sm["n_hits"] == int(det["hits"].sum())
+    assert sm["w"] == 100_000 and sm["n_used"] == 1000
+    assert abs(sm["energy"] - m) <= RTOL_FP64 * abs(m)
+    assert abs(sm["var"] - var) <= RTOL_FP64 * max(1.0, var)
+    # the all-pairs scan (no enumeration) finds the same connected set
+    _, pdet = orc.eloc_pairwise(ints.h, ints.eri, 0.0, 14, s.keys, s.psi, details=True)
+    assert np.array_equal(g["hits"], pdet["hits"]) and np.array_equal(g["signsum"], pdet["signsum"])
+
+
+def test_exact_ground_state_constant_eloc(B, orc):
+    """N=8, 4 electrons, psi = exact ground state of the sector: E_loc = E0 everywhere
+    psi is not negligible (FP64 path)."""
+    ints = I.make_integrals(4, 8, 808)
+    basis = orc.sector(8, 2, 2)
+    H = orc.h_definition(ints.h, ints.eri, 0.0, 8, basis)
+    w, v = np.linalg.eigh(H)
+    psi = v[:, 0].astype(complex) * np.exp(0.3j)
+    g = run_gpu(B, ints, 8, 4, basis, np.ones(len(basis), np.int64), psi)
+    big = np.abs(psi) > 1e-8 * np.abs(psi).max()
+    assert np.abs(g["eloc"][big] - w[0]).max() < 1e-9
+    assert np.linalg.norm(g["eloc"] * psi - w[0] * psi) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_mode(B, orc, prec):
+    """Accurate energy: a caller table covering every connected x' (the whole sector)."""
+    ints = I.make_integrals(6, 12, 61)
+    basis = orc.sector(12, 3, 3)
+    tpsi = I.lognormal_psi(len(basis), 62)
+    rng = np.random.default_rng(63)
+    pick = np.sort(rng.choice(len(basis), 120, replace=False))
+    keys, psi = basis[pick], tpsi[pick]
+    counts = I.multinomial_counts(120, 10_000, 64)
+    g = run_gpu(B, ints, 12, 6, keys, counts, psi, table=(basis, tpsi), prec=prec, mode=1)
+    want, det = orc.eloc(ints.h, ints.eri, 0.0, 12, keys, psi, basis, tpsi, mode=orc.FULL, details=True)
+    assert_sets_equal(g, det)
+    assert np.all(det["hits"] == det["pairs"])
+    if prec == 0:
+        assert_eloc_close(g["eloc"], want)
+    m, var, w, n = orc.reduce(want, counts)
+    tol = RTOL_FP64 * abs(m) if prec == 0 else ATOL_FP32C
+    assert abs(g["summary"]["energy"] - m) <= tol
+    assert g["summary"]["status"] == 0
+
+
+def test_full_mode_reports_missing(B, orc):
+    ints = I.make_integrals(5, 10, 71)
+    basis = orc.sector(10, 2, 2)
+    tpsi = I.lognormal_psi(len(basis), 72)
+    keep = np.ones(len(basis), bool)
+    keep[[3, 40]] = False
+    keys, psi = basis[:30], tpsi[:30]
+    g = run_gpu(B, ints, 10, 4, keys, np.ones(30, np.int64), psi, table=(basis[keep], tpsi[keep]), mode=1)
+    want = orc.eloc(ints.h, ints.eri, 0.0, 10, keys, psi, basis[keep], tpsi[keep], mode=orc.FULL)
+    assert np.array_equal(np.isnan(g["eloc"].real), np.isnan(want.real))
+    assert np.isnan(want.real).any()
+    sm = g["summary"]
+    assert sm["status"] == -9 and sm["n_missing"] > 0 and sm["n_bad"] == int(np.isnan(want.real).sum())
+
+
+def test_medium_n52_and_shards(B, orc):
+    """N=52, 14 electrons, 3,000 rank-weighted samples: full oracle comparison; then two
+    shards evaluated against the whole table combine to the same energy."""
+    ints = I.make_integrals(26, 52, 5201)
+    keys = I.rank_weighted_samples(26, 7, 7, 3000, seed=5202)
+    counts = I.zipf_counts(3000, 300_000, 5203)
+    psi = I.lognormal_psi(3000, 5204)
+    g = run_gpu(B, ints, 52, 14, keys, counts, psi)
+    want, det = orc.eloc(ints.h, ints.eri, 0.0, 52, keys, psi, details=True)
+    assert_sets_equal(g, det)
+    assert_eloc_close(g["eloc"], want)
+    assert g["summary"]["n_pairs"] == 3000 * 25137
+    m, var, w, n = orc.reduce(want, counts)
+    assert abs(g["summary"]["energy"] - m) <= RTOL_FP64 * abs(m)
+    parts = []
+    for lo, hi in ((0, 1234), (1234, 3000)):
+        gs = run_gpu(B, ints, 52, 14, keys[lo:hi], counts[lo:hi], psi[lo:hi], table=(keys, psi))
+        assert_sets_equal(gs, {k: v[lo:hi] for k, v in det.items()})
+        assert_eloc_close(gs["eloc"], want[lo:hi])
+        parts.append(gs["summary"])
+    W = sum(p["w"] for p in parts)
+    E = sum(complex(p["sum_ce_re"], p["sum_ce_im"]) for p in parts) / W
+    assert W == w and abs(E - m) <= RTOL_FP64 * abs(m)
+
+
+def test_full_size_n52_sampled(B, orc):
+    """The benchmark workload (N=52, 14 e, 1e5 samples, Zipf counts summing to 1e7) in the
+    launch configuration the benchmark uses: 512 sampled rows checked against the oracle
+    (which looks x' up in the whole table), plus exact structural totals and run-to-run
+    determinism."""
+    ints, s = I.make_workload("n52_e14_u100k")
+    g = run_gpu(B, ints, 52, 14, s.keys, s.counts, s.psi)
+    g2 = run_gpu(B, ints, 52, 14, s.keys, s.counts, s.psi)
+    assert np.array_equal(g["eloc"].view(np.uint64), g2["eloc"].view(np.uint64))
+    rows = np.sort(np.random.default_rng(7).choice(s.n_u, 512, replace=False))
+    want, det = orc.eloc(ints.h, ints.eri, 0.0, 52, s.keys[rows], s.psi[rows], s.keys, s.psi, details=True)
+    assert_sets_equal(g, det, rows)
+    assert_eloc_close(g["eloc"][rows], want)
+    sm = g["summary"]
+    assert sm["n_pairs"] == 100_000 * 25137 and sm["w"] == 10_000_000 and sm["status"] == 0
+    # the energy of the GPU E_loc array reduced by the oracle's reduction
+    m, var, w, n = orc.reduce(g["eloc"], s.counts)
+    assert abs(sm["energy"] - m) <= 1e-12 * abs(m) and abs(sm["var"] - var) <= 1e-10 * var
+
+
+def test_precision_form_n76(B, orc):
+    """FP32 integrals and FP32 x FP32 terms with TwoSum accumulation; diagonal and the
+    reduction in FP64.  N=76, 20 electrons, 4,000 samples: error against the FP64 oracle
+    per sample (reported) and on the total (<= 1e-5 Ha)."""
+    ints = I.make_integrals(38, 76, 7601)
+    keys = I.rank_weighted_samples(38, 10, 10, 4000, seed=7602)
+    counts = I.zipf_counts(4000, 400_000, 7603)
+    psi = I.lognormal_psi(4000, 7604)
+    g = run_gpu(B, ints, 76, 20, keys, counts, psi, prec=1)
+    want, det = orc.eloc(ints.h, ints.eri, 0.0, 76, keys, psi, details=True)
+    assert_sets_equal(g, det)
+    m, var, w, n = orc.reduce(want, counts)
+    err_total = abs(g["summary"]["energy"] - m)
+    per = np.abs(g["eloc"] - want)
+    print(f"FP32-comp N=76: |dE| total {err_total:.2e} Ha, per-sample max {per.max():.2e}, rms {np.sqrt((per**2).mean()):.2e}")
+    assert err_total <= ATOL_FP32C
+    assert g["summary"]["n_pairs"] == 4000 * 112980
+
+
+@pytest.mark.parametrize("K,ne,n_u", [(2, 2, 4), (64, 4, 300), (64, 64, 24), (20, 20, 500)])
+def test_shapes_edge(B, orc, K, ne, n_u):
+    """Smallest system (N=4), the largest spin-orbital count (N=128) at low and at half
+    filling (1.54 M pairs per sample), and N=40 at half filling."""
+    ints = I.make_integrals(K, min(2 * K, 16), 100 + K + ne)
+    if K == 2:
+        keys = orc.sector(4, 1, 1)
+    else:
+        keys = I.rank_weighted_samples(K, ne // 2, ne // 2, n_u, seed=200 + K)
+    n = len(keys)
+    psi = I.lognormal_psi(n, 300 + K)
+    counts = I.multinomial_counts(n, 50 * n, 400 + K)
+    for opts in ({}, {2: 1}):
+        g = run_gpu(B, ints, 2 * K, ne, keys, counts, psi, opts=opts)
+        want, det = orc.eloc(ints.h, ints.eri, 0.0, 2 * K, keys, psi, details=True)
+        assert_sets_equal(g, det)
+        assert_eloc_close(g["eloc"], want)
+
+
+def test_degenerate_inputs(B, orc):
+    import torch
+    ints, s = I.make_workload("n14_e6_u1k")
+    # n_u = 0
+    g = run_gpu(B, ints, 14, 6, s.keys[:0], s.counts[:0], s.psi[:0])
+    assert g["eloc"].shape == (0,) and g["summary"]["n_used"] == 0 and g["summary"]["n_pairs"] == 0
+    # n_u = 1: no other sample in the table, E_loc = diagonal
+    g = run_gpu(B, ints, 14, 6, s.keys[:1], s.counts[:1], s.psi[:1])
+    v, _ = orc.slater_condon(ints.h, ints.eri, 0.0, 14, s.keys[0], s.keys[0])
+    assert abs(g["eloc"][0] - v) <= 1e-12 * abs(v) and g["hits"][0] == 0
+    # e_core shifts every E_loc
+    g1 = run_gpu(B, ints, 14, 6, s.keys, s.counts, s.psi, e_core=2.5)
+    g0 = run_gpu(B, ints, 14, 6, s.keys, s.counts, s.psi)
+    assert np.abs(g1["eloc"] - g0["eloc"] - 2.5).max() < 1e-12
+    # psi(x) = 0 -> NaN for that sample, excluded, status QC_ERR_ZERO_PSI
+    psi = s.psi.copy()
+    psi[5] = 0
+    g = run_gpu(B, ints, 14, 6, s.keys, s.counts, psi)
+    assert np.isnan(g["eloc"][5].real) and g["summary"]["status"] == -8 and g["summary"]["n_used"] == 999
+    # duplicate key
+    keys = s.keys.copy()
+    keys[11] = keys[10]
+    assert run_gpu(B, ints, 14, 6, keys, s.counts, s.psi)["summary"]["status"] == -3
+    # unsorted keys
+    keys = s.keys.copy()
+    keys[[20, 21]] = keys[[21, 20]]
+    assert run_gpu(B, ints, 14, 6, keys, s.counts, s.psi)["summary"]["status"] == -2
+    # wrong electron count / bits beyond n_orb: sample skipped with NaN
+    keys = s.keys.copy()
+    keys[-1, 0] |= np.uint64(1) << np.uint64(20)
+    g = run_gpu(B, ints, 14, 6, keys, s.counts, s.psi)
+    assert g["summary"]["status"] == -4 and np.isnan(g["eloc"][-1].real)
+    assert g["summary"]["n_pairs"] == 999 * 204
+    # negative count
+    c = s.counts.copy()
+    c[3] = -1
+    assert run_gpu(B, ints, 14, 6, s.keys, c, s.psi)["summary"]["status"] == -12
+    # misaligned device pointer is rejected synchronously
+    h = B.qc_eloc_create(ints.h, ints.eri, 0.0, 14, 6)
+    try:
+        kt = B.keys_to_tensor(s.keys)
+        raw = torch.empty(2 * len(s.keys) + 1, dtype=torch.int64, device="cuda")
+        mis = raw[1:].view(-1, 2)
+        with pytest.raises(B.QcError):
+            B.qc_eloc_eval(h, mis, torch.from_numpy(s.counts).cuda(), torch.from_numpy(s.psi).cuda())
+        with pytest.raises(B.QcError):   # FULL mode needs a table; this handle is SAMPLE: table psi missing
+            B.qc_eloc_eval(h, kt, torch.from_numpy(s.counts).cuda(), torch.from_numpy(s.psi).cuda(), kt, None)
+    finally:
+        B.qc_eloc_destroy(h)
