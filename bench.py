@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark of the sample-space local-energy step (Eq. 5) and its reduction (Eq. 1).
+
+One step = one qc_eloc_eval over the whole workload: hash-index + Bloom-filter build over
+the unique-sample table, the local-energy kernel (every single and double excitation of
+every sample, looked up in the table), and the two-pass count-weighted reduction.
+
+Workload (default): N = 52 spin orbitals, 14 electrons, 1e5 unique rank-weighted samples
+with Zipf(1.2) counts summing to 1e7, complex FP64 psi, FP64 arithmetic; synthetic seeded
+integrals (h: -U(1,5) diagonal, N(0, 0.1 e^{-|p-q|/2}) off-diagonal; (pq|rs) from a rank-52
+Cholesky-like factor).  25,137 connected pairs per sample, 2.51e9 per step.
+
+With N GPUs (torchrun) the unique-sample set grows to N x 1e5 (weak scaling); rank r
+evaluates rows [r*1e5, (r+1)*1e5) against the whole table, and the per-rank partial sums
+of Eq. 1 are combined on the host (the MPI_Allreduce of Alg. 3).
+
+``--impl reference`` times the CPU oracle instead (rank 0 only), on bounded samples of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "connected matrix elements/sec and E_loc samples/sec vs L2/HBM roofline; serve p50/p99"
+UNIT = "connected matrix elements/s"
+# Algorithmic integer operations per enumerated pair in the main kernel: form the
+# excitation's hash (1 XOR), derive the filter word index (1), read the filter word (1),
+# test its two bits (3), compact the survivors (1).
+OPS_PER_PAIR = 7
+PROFILE_JSON = os.path.join(ROOT, "profiles", "eloc_filtered_n52_e14_u100k.json")
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="n52_e14_u100k")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32c"])
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    for f in ("qc_kernels.cu", "qc_internal.h"):
+        with open(os.path.join(ROOT, "paper_2506_23809_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the GPU runs."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                sm.append(float(f[2]))
+                mx = float(f[3])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        busy = [v for v in sm if mx is None or v >= 0.3 * mx] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _make_workload(name, world):
+    from paper_2506_23809_gb300 import inputs as I
+    spec = dict(I.WORKLOADS[name])
+    kind, total = spec["counts"]
+    return spec, I.make_workload(n_orb=spec["n_orb"], n_elec=spec["n_elec"], rank=spec["rank"],
+                                 n_u=spec["n_u"] * world, sampler=spec["sampler"],
+                                 counts=(kind, total * world), seed=spec["seed"])
+
+
+def _cpu_baseline(ints, s, spec, target_s, pairs_per_sample):
+    """The oracle, as it stands, on a bounded seeded sample of rows (each looks its
+    excitations up in the whole table), all host cores."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(12345)
+    perm = rng.permutation(s.n_u)
+
+    def run(rows):
+        sel = np.sort(perm[:rows])
+        t = time.perf_counter()
+        oracle.eloc(ints.h, ints.eri, 0.0, spec["n_orb"], s.keys[sel], s.psi[sel], s.keys, s.psi,
+                    nthreads=cores)
+        return time.perf_counter() - t
+
+    probe = min(s.n_u, 4 * cores)
+    t0 = run(probe)
+    rows = int(min(s.n_u, max(probe, probe * target_s / max(t0, 1e-6))))
+    t1 = run(rows)
+    return {"value": rows * pairs_per_sample / t1, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{rows} seeded random rows of the {s.n_u}-row table (all rows looked up in the "
+                      f"whole table), {t1:.1f} s on {cores} threads",
+            "samples_per_s": rows / t1}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    oracle.build()
+    spec, (ints, s) = _make_workload(args.workload, 1)
+    K, N = spec["n_orb"] // 2, spec["n_elec"] // 2
+    o, v = N, K - N
+    pairs = 2 * o * v + 2 * (o * (o - 1) // 2) * (v * (v - 1) // 2) + (o * v) ** 2
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(777)
+    # size one step to ~2 s of oracle work
+    probe = 4 * cores
+    sel = np.sort(rng.choice(s.n_u, probe, replace=False))
+    t = time.perf_counter()
+    oracle.eloc(ints.h, ints.eri, 0.0, spec["n_orb"], s.keys[sel], s.psi[sel], s.keys, s.psi, nthreads=cores)
+    dt = time.perf_counter() - t
+    rows = int(min(s.n_u, max(probe, probe * 2.0 / max(dt, 1e-6))))
+    steps = []
+    for i in range(args.warmup + args.steps):
+        sel = np.sort(rng.choice(s.n_u, rows, replace=False))
+        t = time.perf_counter()
+        el = oracle.eloc(ints.h, ints.eri, 0.0, spec["n_orb"], s.keys[sel], s.psi[sel], s.keys, s.psi,
+                         nthreads=cores)
+        oracle.reduce(el, s.counts[sel])
+        if i >= args.warmup:
+            steps.append(time.perf_counter() - t)
+    total = sum(steps)
+    value = rows * pairs * len(steps) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": args.workload, "n_orb": spec["n_orb"], "n_elec": spec["n_elec"],
+                       "n_u": spec["n_u"], "pairs_per_sample": pairs, "rows_per_step": rows,
+                       "mode": "sample"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{rows} seeded random rows per step of the {s.n_u}-row table"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2506_23809_gb300 import binding as B
+    from paper_2506_23809_gb300 import build
+
+    world, rank, local = _dist()
+    build.build()
+    B.load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    spec, (ints, s) = _make_workload(args.workload, world)
+    n_rank = spec["n_u"]
+    lo, hi = rank * n_rank, (rank + 1) * n_rank
+    prec = B.QC_FP64 if args.precision == "fp64" else B.QC_FP32_COMP
+    h = B.qc_eloc_create(ints.h, ints.eri, 0.0, spec["n_orb"], spec["n_elec"], prec, B.QC_SAMPLE)
+    B.qc_eloc_set_option(h, B.QC_OPT_TIMING, 1)
+    pairs_per_sample = B.qc_eloc_pairs_per_sample(h)
+
+    keys_all = B.keys_to_tensor(s.keys, dev)
+    psi_all = torch.from_numpy(s.psi).to(dev)
+    cnt_all = torch.from_numpy(s.counts).to(dev)
+    keys, psi, cnt = keys_all[lo:hi], psi_all[lo:hi], cnt_all[lo:hi]
+    tk, tp = (keys_all, psi_all) if world > 1 else (None, None)
+    eloc = torch.empty(n_rank, dtype=torch.complex128, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+    B.qc_eloc_reserve(h, n_rank, s.n_u)
+
+    def step():
+        B.qc_eloc_eval(h, keys, cnt, psi, tk, tp, eloc=eloc, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    step_ms, main_ms, table_ms, red_ms = [], [], [], []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        t3 = B.qc_eloc_timings(h)
+        table_ms.append(t3[0])
+        main_ms.append(t3[1])
+        red_ms.append(t3[2])
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    wall = time.perf_counter() - t_wall
+    sampler.stop()
+    summ = B.qc_eloc_summary_read(h, stream)
+    cfg = B.qc_eloc_last_config(h)
+
+    total_s = sum(step_ms) / 1e3
+    pairs_rank = int(summ["n_pairs"])
+    t_max, pairs_all, samples_all = total_s, pairs_rank, n_rank
+    if pg:
+        v = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        pg.all_reduce(v, op=pg.ReduceOp.MAX)
+        t_max = float(v.item())
+        c = torch.tensor([pairs_rank, n_rank], dtype=torch.float64, device=dev)
+        pg.all_reduce(c)
+        pairs_all, samples_all = int(c[0].item()), int(c[1].item())
+        # Eq. 1 across ranks: gather (W, sum cE, W * var) and combine (Chan et al.)
+        part = torch.tensor([summ["w"], summ["sum_ce_re"], summ["sum_ce_im"], summ["w"] * summ["var"]],
+                            dtype=torch.float64, device=dev)
+        allp = [torch.empty_like(part) for _ in range(world)]
+        pg.all_gather(allp, part)
+        allp = torch.stack(allp).cpu().numpy()
+        W = allp[:, 0].sum()
+        Ebar = complex(allp[:, 1].sum(), allp[:, 2].sum()) / W
+        means = (allp[:, 1] + 1j * allp[:, 2]) / allp[:, 0]
+        var = (allp[:, 3].sum() + (allp[:, 0] * np.abs(means - Ebar) ** 2).sum()) / W
+    else:
+        W, Ebar, var = summ["w"], summ["energy"], summ["var"]
+    value = pairs_all * args.steps / t_max
+    samples_per_s = samples_all * args.steps / t_max
+
+    # ---- end to end through the C ABI from page-locked host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        keys_h = torch.from_numpy(s.keys[lo:hi].view(np.int64)).pin_memory()
+        psi_h = torch.from_numpy(s.psi[lo:hi]).pin_memory()
+        cnt_h = torch.from_numpy(s.counts[lo:hi]).pin_memory()
+        eloc_h = torch.empty(n_rank, dtype=torch.complex128).pin_memory()
+        keys_d, psi_d, cnt_d = torch.empty_like(keys), torch.empty_like(psi), torch.empty_like(cnt)
+        h2d = keys_h.numel() * 8 + psi_h.numel() * 16 + cnt_h.numel() * 8
+        if world > 1:
+            tk_h = torch.from_numpy(s.keys.view(np.int64)).pin_memory()
+            tp_h = torch.from_numpy(s.psi).pin_memory()
+            tk_d, tp_d = torch.empty_like(keys_all), torch.empty_like(psi_all)
+            h2d += tk_h.numel() * 8 + tp_h.numel() * 16
+        d2h = eloc_h.numel() * 16 + 96
+
+        def e2e_step():
+            keys_d.copy_(keys_h, non_blocking=True)
+            psi_d.copy_(psi_h, non_blocking=True)
+            cnt_d.copy_(cnt_h, non_blocking=True)
+            a, b = None, None
+            if world > 1:
+                tk_d.copy_(tk_h, non_blocking=True)
+                tp_d.copy_(tp_h, non_blocking=True)
+                a, b = tk_d, tp_d
+            B.qc_eloc_eval(h, keys_d, cnt_d, psi_d, a, b, eloc=eloc, stream=stream)
+            eloc_h.copy_(eloc, non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        e_ms = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev0.record(stream)
+            e2e_step()
+            ev1.record(stream)
+            ev1.synchronize()
+            e_ms.append(ev0.elapsed_time(ev1))
+        et = sum(e_ms) / 1e3
+        if pg:
+            v = torch.tensor([et], dtype=torch.float64, device=dev)
+            pg.all_reduce(v, op=pg.ReduceOp.MAX)
+            et = float(v.item())
+        e2e = {"value": pairs_all * args.steps / et, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * et / args.steps}
+
+    # ---- roofline of the dominant kernel (the local-energy kernel) ----
+    peaks, peak_src = _measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * 4 * 32 * sm_max * 1e6     # integer issue, ops/s
+    main_s = statistics.mean(main_ms) / 1e3
+    achieved = pairs_rank * OPS_PER_PAIR / main_s
+    traffic = None
+    if os.path.exists(PROFILE_JSON):
+        with open(PROFILE_JSON) as f:
+            prof = json.load(f)
+        if prof.get("source_hash") == _source_hash() and prof.get("workload") == args.workload:
+            traffic = prof.get("dram_bytes_per_launch")
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+                "frac": achieved / peak_ops, "traffic": traffic,
+                "kernel": "eloc_filtered_kernel" if cfg["kernel"] == 2 else "eloc_direct_kernel",
+                "ops_per_pair": OPS_PER_PAIR,
+                "peak_basis": f"{props.multi_processor_count} SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz "
+                              f"({peak_src} sm_max_mhz)",
+                "kernel_ms": 1e3 * main_s, "kernel_pairs_per_s": pairs_rank / main_s,
+                "hbm_peak_gbs": peaks.get("hbm_gbs")}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(ints, s, spec, args.cpu_seconds, pairs_per_sample)
+
+    clocks = sampler.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == B.QC_FP64 else "f32+f64",
+            "data": "synthetic (seeded integrals, rank-weighted unique samples, Zipf counts, lognormal psi)",
+            "config": {"workload": args.workload, "n_orb": spec["n_orb"], "n_elec": spec["n_elec"],
+                       "n_u_per_gpu": n_rank, "n_table": int(s.n_u), "pairs_per_sample": pairs_per_sample,
+                       "counts_total": int(s.counts.sum()), "mode": "sample", "precision": args.precision,
+                       "l2": "256 MB buffer written between timed steps", "parallelism": f"samples x{world}",
+                       "launch": cfg},
+            "samples_per_s": samples_per_s,
+            "energy": {"re": Ebar.real, "im": Ebar.imag, "var": var, "w": W},
+            "phase_ms": {"table": statistics.mean(table_ms), "main": statistics.mean(main_ms),
+                         "reduce": statistics.mean(red_ms)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 4 * args.steps, "clocks": clocks, "wall_s_timed": wall,
+            "hits_per_step": int(summ["n_hits"]), "status": int(summ["status"])}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    B.qc_eloc_destroy(h)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

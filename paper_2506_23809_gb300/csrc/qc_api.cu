@@ -28,6 +28,10 @@ struct qc_eloc {
     double* d_eri = nullptr;
     double* d_J = nullptr;
     double* d_X = nullptr;
+    double* d_Jt = nullptr;
+    double* d_Xt = nullptr;
+    float* d_Jt32 = nullptr;
+    float* d_Xt32 = nullptr;
     float* d_h32 = nullptr;
     float* d_eri32 = nullptr;
     unsigned long long* d_T = nullptr;
@@ -141,6 +145,14 @@ qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int 
             J[k * K + l] = eri[((static_cast<size_t>(k) * K + k) * K + l) * K + l];  // (kk|ll)
             X[k * K + l] = eri[((static_cast<size_t>(k) * K + l) * K + l) * K + k];  // (kl|lk)
         }
+    const size_t K3 = KK * K;
+    std::vector<double> Jt(K3), Xt(K3);
+    for (int p = 0; p < K; ++p)
+        for (int i = 0; i < K; ++i)
+            for (int k = 0; k < K; ++k) {
+                Jt[(static_cast<size_t>(p) * K + i) * K + k] = eri[((static_cast<size_t>(p) * K + i) * K + k) * K + k];  // (pi|kk)
+                Xt[(static_cast<size_t>(p) * K + i) * K + k] = eri[((static_cast<size_t>(p) * K + k) * K + k) * K + i];  // (pk|ki)
+            }
     std::vector<unsigned long long> T(128);
     unsigned long long seed = 0x51c0de5eedULL;
     for (auto& t : T) t = splitmix64(seed);
@@ -158,6 +170,10 @@ qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int 
     QC_TRY(cudaMalloc(&H->d_X, KK * sizeof(double)), "cudaMalloc X");
     QC_TRY(cudaMemcpy(H->d_X, X.data(), KK * sizeof(double), cudaMemcpyHostToDevice), "copy X");
     if (precision == QC_FP64) {
+        QC_TRY(cudaMalloc(&H->d_Jt, K3 * sizeof(double)), "cudaMalloc Jt");
+        QC_TRY(cudaMemcpy(H->d_Jt, Jt.data(), K3 * sizeof(double), cudaMemcpyHostToDevice), "copy Jt");
+        QC_TRY(cudaMalloc(&H->d_Xt, K3 * sizeof(double)), "cudaMalloc Xt");
+        QC_TRY(cudaMemcpy(H->d_Xt, Xt.data(), K3 * sizeof(double), cudaMemcpyHostToDevice), "copy Xt");
         QC_TRY(cudaMalloc(&H->d_eri, K4 * sizeof(double)), "cudaMalloc eri");
         QC_TRY(cudaMemcpy(H->d_eri, eri, K4 * sizeof(double), cudaMemcpyHostToDevice), "copy eri");
     } else {
@@ -166,6 +182,15 @@ qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int 
         for (size_t i = 0; i < K4; ++i) e32[i] = static_cast<float>(eri[i]);
         QC_TRY(cudaMalloc(&H->d_h32, KK * sizeof(float)), "cudaMalloc h32");
         QC_TRY(cudaMemcpy(H->d_h32, h32.data(), KK * sizeof(float), cudaMemcpyHostToDevice), "copy h32");
+        std::vector<float> jt32(K3), xt32(K3);
+        for (size_t i = 0; i < K3; ++i) {
+            jt32[i] = static_cast<float>(Jt[i]);
+            xt32[i] = static_cast<float>(Xt[i]);
+        }
+        QC_TRY(cudaMalloc(&H->d_Jt32, K3 * sizeof(float)), "cudaMalloc Jt32");
+        QC_TRY(cudaMemcpy(H->d_Jt32, jt32.data(), K3 * sizeof(float), cudaMemcpyHostToDevice), "copy Jt32");
+        QC_TRY(cudaMalloc(&H->d_Xt32, K3 * sizeof(float)), "cudaMalloc Xt32");
+        QC_TRY(cudaMemcpy(H->d_Xt32, xt32.data(), K3 * sizeof(float), cudaMemcpyHostToDevice), "copy Xt32");
         QC_TRY(cudaMalloc(&H->d_eri32, K4 * sizeof(float)), "cudaMalloc eri32");
         QC_TRY(cudaMemcpy(H->d_eri32, e32.data(), K4 * sizeof(float), cudaMemcpyHostToDevice), "copy eri32");
     }
@@ -205,6 +230,10 @@ qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int 
     sp.eri32 = H->d_eri32;
     sp.J = H->d_J;
     sp.X = H->d_X;
+    sp.Jt = H->d_Jt;
+    sp.Xt = H->d_Xt;
+    sp.Jt32 = H->d_Jt32;
+    sp.Xt32 = H->d_Xt32;
     *out = H;
     return QC_OK;
 }
@@ -215,6 +244,10 @@ qc_status qc_eloc_destroy(qc_eloc* H) {
     free_dev(H->d_eri);
     free_dev(H->d_J);
     free_dev(H->d_X);
+    free_dev(H->d_Jt);
+    free_dev(H->d_Xt);
+    free_dev(H->d_Jt32);
+    free_dev(H->d_Xt32);
     free_dev(H->d_h32);
     free_dev(H->d_eri32);
     free_dev(H->d_T);
@@ -313,7 +346,7 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
             const size_t base = qc::filtered_smem_bytes(sp, 0, fw);
             if (base + wb > H->smem_optin) continue;
             const int fit = static_cast<int>((H->smem_optin - base) / wb);
-            warps = H->opt_warps ? H->opt_warps : std::min(32, fit);
+            warps = std::min(qc::kFilteredMaxWarps, H->opt_warps ? H->opt_warps : fit);
             if (warps > fit) continue;
             if (H->opt_fw == 0 && warps < 8 && fw > 10) continue;  // prefer occupancy
             break;

@@ -10,6 +10,7 @@ namespace qc {
 constexpr int kMaxOrb = 128;     // spin orbitals (two 64-bit words)
 constexpr int kMaxSpatial = 64;  // spatial orbitals per spin
 constexpr int kPairLut = 2016;   // C(64, 2): colex pair index -> (i, j), i < j < 64
+constexpr int kFilteredMaxWarps = 24;  // launch bound of the filtered kernel (768 threads)
 
 // One Hamiltonian (Eq. 2) resident on the device.
 struct SysParams {
@@ -27,6 +28,10 @@ struct SysParams {
     const float* eri32;  // K^4  FP32 (FP32 precision)
     const double* J;     // K*K  (kk|ll)  FP64
     const double* X;     // K*K  (kl|lk)  FP64
+    const double* Jt;    // K^3  [a][i][k] = (ai|kk)  FP64 (single excitations)
+    const double* Xt;    // K^3  [a][i][k] = (ak|ki)  FP64
+    const float* Jt32;   // K^3  FP32 copies (FP32 precision)
+    const float* Xt32;
 };
 
 // The lookup table: sorted unique keys, their psi, and the device hash index over them.

@@ -17,7 +17,7 @@
 // The low 32 bits of H index a blocked Bloom filter (two bits in one 32-bit word) that
 // every CTA holds in shared memory (loaded by a 1-D bulk async copy); lanes whose x' passes
 // are compacted into a per-warp queue and resolved 32 at a time against an open-addressing
-// bucket table in global memory (L2 resident), keyed by a mix of the full 64-bit H and
+// bucket table in global memory (L2 resident), keyed by the high 32 bits of H and
 // checked against the stored 128-bit key.  Only then are the matrix element (Slater-Condon)
 // and psi(x') read.
 #include <cstdint>
@@ -33,16 +33,6 @@ namespace qc {
 // ------------------------------------------------------------------------------------
 // small device helpers
 // ------------------------------------------------------------------------------------
-// MurmurHash3's 64-bit finalizer (Appleby, public domain): a bijective bit mixer.
-__device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
-    k ^= k >> 33;
-    k *= 0xff51afd7ed558ccdULL;
-    k ^= k >> 33;
-    k *= 0xc4ceb9fe1a85ec53ULL;
-    k ^= k >> 33;
-    return k;
-}
-
 // occupied spin orbitals of x strictly below spin orbital k (0 <= k < 128)
 __device__ __forceinline__ int below(ulonglong2 x, int k) {
     unsigned long long m0 = (k >= 64) ? ~0ULL : ((1ULL << k) - 1ULL);
@@ -129,13 +119,19 @@ constexpr unsigned kWaitLimit = 1u << 24;  // bounded spin on the filter copy
 // ------------------------------------------------------------------------------------
 // lookup in the bucket table
 // ------------------------------------------------------------------------------------
+// Bits of the 64-bit linear key hash H:  0..31 feed the shared-memory Bloom filter
+// (bits 0-4 and 27-31 pick the two bits, bits 5.. the word); 32..63 give the bucket
+// (low bits) and the fingerprint stored with each entry.  A random GF(2)-linear map
+// sends any two distinct keys to independent uniform hashes, so the bucket load and the
+// filter false-positive rate are those of a 2-universal hash family.
+__device__ __forceinline__ unsigned bucket_of(unsigned long long h) { return static_cast<unsigned>(h >> 32); }
+
 // Returns the table row of key, or -1.  Buckets hold two 64-bit entries
 // (fingerprint << 32 | row + 1); an empty entry ends the probe sequence.
 __device__ __forceinline__ long long table_find(const TableParams& tp, ulonglong2 key,
                                                 unsigned long long h) {
-    const unsigned long long m = mix64(h);
-    const unsigned fp = static_cast<unsigned>(m >> 32);
-    unsigned b = static_cast<unsigned>(m) & tp.nb_mask;
+    const unsigned fp = bucket_of(h);
+    unsigned b = fp & tp.nb_mask;
     const ulonglong2* buckets = reinterpret_cast<const ulonglong2*>(tp.slots);
     for (unsigned it = 0; it <= tp.nb_mask; ++it) {
         const ulonglong2 e = __ldg(buckets + b);
@@ -193,11 +189,10 @@ __global__ void __launch_bounds__(256) build_table_kernel(TableParams tp, int n_
         const unsigned wmask = (1u << tp.fw) - 1u;
         atomicOr(filter + ((g >> 5) & wmask), (1u << (g & 31u)) | (1u << (g >> 27)));
     }
-    const unsigned long long m = mix64(h);
+    const unsigned fp = bucket_of(h);
     const unsigned long long entry =
-        (static_cast<unsigned long long>(static_cast<unsigned>(m >> 32)) << 32) |
-        static_cast<unsigned long long>(static_cast<unsigned>(r + 1));
-    unsigned b = static_cast<unsigned>(m) & tp.nb_mask;
+        (static_cast<unsigned long long>(fp) << 32) | static_cast<unsigned long long>(static_cast<unsigned>(r + 1));
+    unsigned b = fp & tp.nb_mask;
     bool placed = false;
     for (unsigned it = 0; it <= tp.nb_mask && !placed; ++it) {
         if (atomicCAS(slots + 2 * b, 0ULL, entry) == 0ULL) { placed = true; break; }
@@ -209,77 +204,111 @@ __global__ void __launch_bounds__(256) build_table_kernel(TableParams tp, int n_
 }
 
 // ------------------------------------------------------------------------------------
-// per-sample state of the main kernels
+// shared-memory layout of the main kernels
 // ------------------------------------------------------------------------------------
-struct WarpLists {  // per-warp shared memory
-    unsigned char* occA;
-    unsigned char* virA;
-    unsigned char* occB;
-    unsigned char* virB;
-};
+//   [kOffBar]   mbarrier of the filter copy
+//   [kOffT]     T[128]: the linear key hash, 64-bit entries
+//   [kOffLut]   colex pair table: p = C(hi, 2) + lo  ->  lo | hi << 8   (p < 2016)
+//   [kOffDiv]   single-excitation index -> occupied position, per spin (u8, < 1024 each)
+//   [kOffVar]   filter words (filtered kernel only), then one region per warp:
+//               occA[64] virA[64] occB[64] virB[64] (u8) | queue[64] (u32) | hash lists (u32)
+constexpr size_t kOffBar = 0;
+constexpr size_t kOffT = 16;
+constexpr size_t kOffLut = kOffT + 128 * 8;
+constexpr size_t kOffDiv = kOffLut + kPairLut * 2;
+constexpr size_t kOffVar = ((kOffDiv + 2 * 1024 + 127) / 128) * 128;
+constexpr size_t kWarpFixed = 4 * 64 + 64 * 4;
 
-struct Acc {
-    double re, im;       // FP64 accumulation of sum H psi(x')
-    float sr, cr, si, ci;  // FP32 TwoSum accumulation of sum H psi(x')/psi(x)
-    unsigned hits;
-    unsigned long long rowsum;
-    long long signsum;
-    unsigned long long missing;
+__host__ __device__ inline size_t list_words(const SysParams& sp) {
+    return static_cast<size_t>(1 + sp.nsa + sp.nsb + sp.npoa + sp.npva + sp.npob + sp.npvb);
+}
+__host__ __device__ inline size_t filtered_warp_bytes(const SysParams& sp) {
+    return ((kWarpFixed + 4 * list_words(sp)) + 15) / 16 * 16;
+}
+
+size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw) {
+    return kOffVar + (static_cast<size_t>(4) << fw) + static_cast<size_t>(warps) * filtered_warp_bytes(sp);
+}
+size_t direct_smem_bytes(int warps) { return kOffVar + static_cast<size_t>(warps) * kWarpFixed; }
+
+// CTA-wide tables: T, pair LUT, single-excitation division tables
+__device__ void fill_cta_tables(const SysParams& sp, const unsigned long long* __restrict__ Tg,
+                                unsigned char* smem) {
+    unsigned long long* T64 = reinterpret_cast<unsigned long long*>(smem + kOffT);
+    unsigned short* lut = reinterpret_cast<unsigned short*>(smem + kOffLut);
+    unsigned char* divA = smem + kOffDiv;
+    unsigned char* divB = divA + 1024;
+    for (int t = threadIdx.x; t < 128; t += blockDim.x) T64[t] = Tg[t];
+    for (int p = threadIdx.x; p < kPairLut; p += blockDim.x) {
+        int hi = static_cast<int>((1.0f + sqrtf(1.0f + 8.0f * static_cast<float>(p))) * 0.5f);
+        while (hi * (hi - 1) / 2 > p) --hi;
+        while ((hi + 1) * hi / 2 <= p) ++hi;
+        const int lo = p - hi * (hi - 1) / 2;
+        lut[p] = static_cast<unsigned short>(lo | (hi << 8));
+    }
+    for (int t = threadIdx.x; t < sp.nsa; t += blockDim.x) divA[t] = static_cast<unsigned char>(t / sp.va);
+    for (int t = threadIdx.x; t < sp.nsb; t += blockDim.x) divB[t] = static_cast<unsigned char>(t / sp.vb);
+}
+
+// ------------------------------------------------------------------------------------
+// candidate resolution
+// ------------------------------------------------------------------------------------
+struct Resolved {
+    long long row;  // table row, or -1
+    double h;       // <x|H|x'> with its phase (FP64 path) ...
+    float h32;      // ... or FP32 path
+    int ssign;      // phase in the sorted (exported) convention, +1 / -1
 };
 
 // Decode a candidate (class, u, w) into spin orbitals: i -> a, and j -> b for doubles
 // (j = b = -1 for singles).  Classes: 0 alpha single (w), 1 beta single (w), 2 alpha-alpha
 // double (u: occupied pair, w: empty pair), 3 beta-beta double, 4 alpha-beta double
 // (u: alpha single, w: beta single).  Same-spin doubles have i < j and a < b.
-__device__ __forceinline__ void decode(unsigned code, const SysParams& sp, const WarpLists& L,
-                                       const unsigned short* __restrict__ lut, int& i, int& a,
-                                       int& j, int& b) {
+// Look x' up; on a hit return <x|H|x'> (Slater-Condon rules, Sec. III-B (ii)) with the
+// phase <x'| a+_a a+_b a_j a_i |x> (counts of occupied orbitals below each index).
+template <int PREC>
+__device__ __forceinline__ Resolved resolve(unsigned code, const SysParams* __restrict__ spp,
+                                         const TableParams* __restrict__ tpp,
+                                         const unsigned char* __restrict__ wl, ulonglong2 x,
+                                         unsigned long long hx) {
+    const SysParams& sp = *spp;
+    const TableParams& tp = *tpp;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const unsigned long long* T64 = reinterpret_cast<const unsigned long long*>(smem + kOffT);
+    const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
+    const unsigned char* occA = wl;
+    const unsigned char* virA = wl + 64;
+    const unsigned char* occB = wl + 128;
+    const unsigned char* virB = wl + 192;
     const int cls = static_cast<int>(code >> 24);
     const int u = static_cast<int>((code >> 12) & 4095u);
     const int w = static_cast<int>(code & 4095u);
-    j = -1;
-    b = -1;
+    int i, a, j = -1, b = -1;
     if (cls == 0) {
-        const int io = w / sp.va, av = w - io * sp.va;
-        i = 2 * L.occA[io];
-        a = 2 * L.virA[av];
+        const int io = smem[kOffDiv + w];
+        i = 2 * occA[io];
+        a = 2 * virA[w - io * sp.va];
     } else if (cls == 1) {
-        const int io = w / sp.vb, av = w - io * sp.vb;
-        i = 2 * L.occB[io] + 1;
-        a = 2 * L.virB[av] + 1;
-    } else if (cls == 2) {
-        const unsigned po = lut[u], pv = lut[w];
-        i = 2 * L.occA[po & 255u];
-        j = 2 * L.occA[po >> 8];
-        a = 2 * L.virA[pv & 255u];
-        b = 2 * L.virA[pv >> 8];
-    } else if (cls == 3) {
-        const unsigned po = lut[u], pv = lut[w];
-        i = 2 * L.occB[po & 255u] + 1;
-        j = 2 * L.occB[po >> 8] + 1;
-        a = 2 * L.virB[pv & 255u] + 1;
-        b = 2 * L.virB[pv >> 8] + 1;
+        const int io = smem[kOffDiv + 1024 + w];
+        i = 2 * occB[io] + 1;
+        a = 2 * virB[w - io * sp.vb] + 1;
+    } else if (cls == 4) {
+        const int io = smem[kOffDiv + u];
+        const int jo = smem[kOffDiv + 1024 + w];
+        i = 2 * occA[io];
+        a = 2 * virA[u - io * sp.va];
+        j = 2 * occB[jo] + 1;
+        b = 2 * virB[w - jo * sp.vb] + 1;
     } else {
-        const int io = u / sp.va, av = u - io * sp.va;
-        const int jo = w / sp.vb, bv = w - jo * sp.vb;
-        i = 2 * L.occA[io];
-        a = 2 * L.virA[av];
-        j = 2 * L.occB[jo] + 1;
-        b = 2 * L.virB[bv] + 1;
+        const unsigned po = lut[u], pv = lut[w];
+        const unsigned char* occ = cls == 2 ? occA : occB;
+        const unsigned char* vir = cls == 2 ? virA : virB;
+        const int s = cls == 2 ? 0 : 1;
+        i = 2 * occ[po & 255u] + s;
+        j = 2 * occ[po >> 8] + s;
+        a = 2 * vir[pv & 255u] + s;
+        b = 2 * vir[pv >> 8] + s;
     }
-}
-
-// Resolve one candidate: look x' up; on a hit add <x|H|x'> psi(x') (FP64) or
-// <x|H|x'> psi(x')/psi(x) (FP32, TwoSum) to the lane accumulator.
-template <int PREC>
-__device__ __forceinline__ void resolve(unsigned code, bool valid, const SysParams& sp,
-                                        const TableParams& tp, int mode, const WarpLists& L,
-                                        const unsigned short* __restrict__ lut,
-                                        const unsigned long long* __restrict__ T64, ulonglong2 x,
-                                        unsigned long long hx, float2 invpsi32, Acc& acc) {
-    if (!valid) return;
-    int i, a, j, b;
-    decode(code, sp, L, lut, i, a, j, b);
     ulonglong2 xp = x;
     flip(xp, i);
     flip(xp, a);
@@ -289,47 +318,47 @@ __device__ __forceinline__ void resolve(unsigned code, bool valid, const SysPara
         flip(xp, b);
         h ^= T64[j] ^ T64[b];
     }
-    const long long row = table_find(tp, xp, h);
-    if (row < 0) {
-        if (mode == QC_FULL) acc.missing++;
-        return;
-    }
+    Resolved r;
+    r.row = table_find(tp, xp, h);
+    r.h = 0.0;
+    r.h32 = 0.f;
+    r.ssign = 1;
+    if (r.row < 0) return r;
     const int K = sp.K;
     const int ki = i >> 1, ka = a >> 1;
-    double elem64 = 0.0;
-    float elem32 = 0.f;
-    int par;
-    int sorted_flip = 0;
+    int par, sorted_flip = 0;
+    double e64 = 0.0;
+    float e32 = 0.f;
     if (j < 0) {
-        // single i -> a:  h_ai + sum_k occ (ai|kk) - sum_k occ, same spin (ak|ki)
+        // single i -> a:  h_ai + sum_{k occ} (ai|kk) - sum_{k occ, same spin} (ak|ki)
         const int s = i & 1;
-        const size_t row_ai = (static_cast<size_t>(ka) * K + ki) * K;
+        const size_t rowk = (static_cast<size_t>(ka) * K + ki) * K;
         if (PREC == QC_FP64) {
             double f = sp.h[ka * K + ki];
             for (int q = 0; q < sp.oa; ++q) {
-                const int k = L.occA[q];
-                f += sp.eri[(row_ai + k) * K + k];
-                if (s == 0) f -= sp.eri[((static_cast<size_t>(ka) * K + k) * K + k) * K + ki];
+                const int k = occA[q];
+                f += sp.Jt[rowk + k];
+                if (s == 0) f -= sp.Xt[rowk + k];
             }
             for (int q = 0; q < sp.ob; ++q) {
-                const int k = L.occB[q];
-                f += sp.eri[(row_ai + k) * K + k];
-                if (s == 1) f -= sp.eri[((static_cast<size_t>(ka) * K + k) * K + k) * K + ki];
+                const int k = occB[q];
+                f += sp.Jt[rowk + k];
+                if (s == 1) f -= sp.Xt[rowk + k];
             }
-            elem64 = f;
+            e64 = f;
         } else {
             float f = sp.h32[ka * K + ki];
             for (int q = 0; q < sp.oa; ++q) {
-                const int k = L.occA[q];
-                f += sp.eri32[(row_ai + k) * K + k];
-                if (s == 0) f -= sp.eri32[((static_cast<size_t>(ka) * K + k) * K + k) * K + ki];
+                const int k = occA[q];
+                f += sp.Jt32[rowk + k];
+                if (s == 0) f -= sp.Xt32[rowk + k];
             }
             for (int q = 0; q < sp.ob; ++q) {
-                const int k = L.occB[q];
-                f += sp.eri32[(row_ai + k) * K + k];
-                if (s == 1) f -= sp.eri32[((static_cast<size_t>(ka) * K + k) * K + k) * K + ki];
+                const int k = occB[q];
+                f += sp.Jt32[rowk + k];
+                if (s == 1) f -= sp.Xt32[rowk + k];
             }
-            elem32 = f;
+            e32 = f;
         }
         par = below(x, i) + below(x, a) + (i < a);
     } else {
@@ -339,40 +368,63 @@ __device__ __forceinline__ void resolve(unsigned code, bool valid, const SysPara
               (j < b) + (i < a) + (j < a) + (b < a);
         if ((i & 1) == (j & 1)) {
             const size_t e = ((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki;  // (aj|bi)
-            if (PREC == QC_FP64) elem64 = sp.eri[d] - sp.eri[e];
-            else elem32 = sp.eri32[d] - sp.eri32[e];
+            if (PREC == QC_FP64) e64 = sp.eri[d] - sp.eri[e];
+            else e32 = sp.eri32[d] - sp.eri32[e];
         } else {
-            if (PREC == QC_FP64) elem64 = sp.eri[d];
-            else elem32 = sp.eri32[d];
+            if (PREC == QC_FP64) e64 = sp.eri[d];
+            else e32 = sp.eri32[d];
             sorted_flip = (i > j) + (a > b);
         }
     }
     const bool neg = (par & 1) != 0;
-    const double2 pp = __ldg(tp.psi + row);
+    r.h = neg ? -e64 : e64;
+    r.h32 = neg ? -e32 : e32;
+    r.ssign = (neg != ((sorted_flip & 1) != 0)) ? -1 : 1;
+    return r;
+}
+
+struct Acc {
+    double re, im;         // FP64 accumulation of sum H psi(x')
+    float sr, cr, si, ci;  // FP32 TwoSum accumulation of sum H psi(x')/psi(x)
+    unsigned hits;
+    unsigned long long rowsum;
+    long long signsum;
+    unsigned long long missing;
+};
+
+template <int PREC>
+__device__ __forceinline__ void accumulate(const Resolved& r, const TableParams& tp, int mode,
+                                           float2 ip32, Acc& acc) {
+    if (r.row < 0) {
+        if (mode == QC_FULL) acc.missing++;
+        return;
+    }
+    const double2 pp = __ldg(tp.psi + r.row);
     if (PREC == QC_FP64) {
-        const double hv = neg ? -elem64 : elem64;
-        acc.re = fma(hv, pp.x, acc.re);
-        acc.im = fma(hv, pp.y, acc.im);
+        acc.re = fma(r.h, pp.x, acc.re);
+        acc.im = fma(r.h, pp.y, acc.im);
     } else {
-        const float hv = neg ? -elem32 : elem32;
         const float px = static_cast<float>(pp.x), py = static_cast<float>(pp.y);
-        const float rr = __fsub_rn(__fmul_rn(px, invpsi32.x), __fmul_rn(py, invpsi32.y));
-        const float ri = __fadd_rn(__fmul_rn(px, invpsi32.y), __fmul_rn(py, invpsi32.x));
-        two_sum_acc(acc.sr, acc.cr, __fmul_rn(hv, rr));
-        two_sum_acc(acc.si, acc.ci, __fmul_rn(hv, ri));
+        const float rr = __fsub_rn(__fmul_rn(px, ip32.x), __fmul_rn(py, ip32.y));
+        const float ri = __fadd_rn(__fmul_rn(px, ip32.y), __fmul_rn(py, ip32.x));
+        two_sum_acc(acc.sr, acc.cr, __fmul_rn(r.h32, rr));
+        two_sum_acc(acc.si, acc.ci, __fmul_rn(r.h32, ri));
     }
     acc.hits++;
-    acc.rowsum += static_cast<unsigned long long>(row + 1);
-    const bool sneg = neg != ((sorted_flip & 1) != 0);
-    acc.signsum += sneg ? -(row + 1) : (row + 1);
+    acc.rowsum += static_cast<unsigned long long>(r.row + 1);
+    acc.signsum += r.ssign < 0 ? -(r.row + 1) : (r.row + 1);
 }
 
 // Per-sample set-up shared by both main kernels.  Returns false when x does not hold
 // na alpha and nb beta electrons below n_orb (then nothing is written to the lists).
 __device__ __forceinline__ bool sample_setup(const SysParams& sp, ulonglong2 x, int lane,
-                                             const WarpLists& L,
+                                             unsigned char* wl,
                                              const unsigned long long* __restrict__ T64,
                                              unsigned long long& hx, double& ediag) {
+    unsigned char* occA = wl;
+    unsigned char* virA = wl + 64;
+    unsigned char* occB = wl + 128;
+    unsigned char* virB = wl + 192;
     const unsigned long long even = 0x5555555555555555ULL;
     const int ea = __popcll(x.x & even) + __popcll(x.y & even);
     const int eb = __popcll(x.x & ~even) + __popcll(x.y & ~even);
@@ -394,10 +446,10 @@ __device__ __forceinline__ bool sample_setup(const SysParams& sp, ulonglong2 x, 
     for (int k = lane; k < sp.K; k += 32) {
         const unsigned long long lowm = (1ULL << k) - 1ULL;
         const int ca = __popcll(A & lowm), cb = __popcll(B & lowm);
-        if ((A >> k) & 1ULL) L.occA[ca] = static_cast<unsigned char>(k);
-        else L.virA[k - ca] = static_cast<unsigned char>(k);
-        if ((B >> k) & 1ULL) L.occB[cb] = static_cast<unsigned char>(k);
-        else L.virB[k - cb] = static_cast<unsigned char>(k);
+        if ((A >> k) & 1ULL) occA[ca] = static_cast<unsigned char>(k);
+        else virA[k - ca] = static_cast<unsigned char>(k);
+        if ((B >> k) & 1ULL) occB[cb] = static_cast<unsigned char>(k);
+        else virB[k - cb] = static_cast<unsigned char>(k);
     }
     // linear hash of x: XOR of T over set bits (lane l: bits l, l+32, l+64, l+96)
     unsigned long long hv = 0;
@@ -412,15 +464,15 @@ __device__ __forceinline__ bool sample_setup(const SysParams& sp, ulonglong2 x, 
     double ed = 0.0;
     for (int idx = lane; idx < sp.oa + sp.ob; idx += 32) {
         const bool isA = idx < sp.oa;
-        const int k = isA ? L.occA[idx] : L.occB[idx - sp.oa];
+        const int k = isA ? occA[idx] : occB[idx - sp.oa];
         double sj = 0.0, sx = 0.0;
         for (int q = 0; q < sp.oa; ++q) {
-            const int l = L.occA[q];
+            const int l = occA[q];
             sj += sp.J[k * K + l];
             if (isA) sx += sp.X[k * K + l];
         }
         for (int q = 0; q < sp.ob; ++q) {
-            const int l = L.occB[q];
+            const int l = occB[q];
             sj += sp.J[k * K + l];
             if (!isA) sx += sp.X[k * K + l];
         }
@@ -503,51 +555,19 @@ __device__ __forceinline__ float2 inv_psi32(double2 p) {
     return make_float2(static_cast<float>(p.x * inv), static_cast<float>(-p.y * inv));
 }
 
-// colex pair table: p = C(hi, 2) + lo  ->  lo | hi << 8
-__device__ void fill_pair_lut(unsigned short* lut) {
-    for (int p = threadIdx.x; p < kPairLut; p += blockDim.x) {
-        int hi = static_cast<int>((1.0f + sqrtf(1.0f + 8.0f * static_cast<float>(p))) * 0.5f);
-        while (hi * (hi - 1) / 2 > p) --hi;
-        while ((hi + 1) * hi / 2 <= p) ++hi;
-        const int lo = p - hi * (hi - 1) / 2;
-        lut[p] = static_cast<unsigned short>(lo | (hi << 8));
-    }
-}
-
-// shared-memory layout common to both main kernels
-constexpr size_t kOffBar = 0;
-constexpr size_t kOffT = 16;
-constexpr size_t kOffLut = kOffT + 128 * 8;
-constexpr size_t kOffVar = ((kOffLut + kPairLut * 2 + 127) / 128) * 128;  // 5120
-constexpr size_t kWarpFixed = 4 * 64 + 64 * 4;  // occ/vir lists + candidate queue
-
-__host__ __device__ inline size_t list_words(const SysParams& sp) {
-    return static_cast<size_t>(sp.nsa + sp.nsb + sp.npoa + sp.npva + sp.npob + sp.npvb + 4);
-}
-__host__ __device__ inline size_t filtered_warp_bytes(const SysParams& sp) {
-    return ((kWarpFixed + 4 * list_words(sp)) + 15) / 16 * 16;
-}
-
-size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw) {
-    return kOffVar + (static_cast<size_t>(4) << fw) + static_cast<size_t>(warps) * filtered_warp_bytes(sp);
-}
-size_t direct_smem_bytes(int warps) { return kOffVar + static_cast<size_t>(warps) * kWarpFixed; }
-
 // ------------------------------------------------------------------------------------
 // K2a: direct kernel -- every connected x' is looked up (FULL mode; SAMPLE without filter)
 // ------------------------------------------------------------------------------------
 template <int PREC>
-__global__ void __launch_bounds__(1024) eloc_direct_kernel(SysParams sp, TableParams tp,
-                                                           EvalParams ep) {
+__global__ void __launch_bounds__(1024) eloc_direct_kernel(const __grid_constant__ SysParams sp,
+                                                           const __grid_constant__ TableParams tp,
+                                                           const __grid_constant__ EvalParams ep) {
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned long long* T64 = reinterpret_cast<unsigned long long*>(smem + kOffT);
-    unsigned short* lut = reinterpret_cast<unsigned short*>(smem + kOffLut);
-    for (int t = threadIdx.x; t < 128; t += blockDim.x) T64[t] = ep.T[t];
-    fill_pair_lut(lut);
+    const unsigned long long* T64 = reinterpret_cast<const unsigned long long*>(smem + kOffT);
+    fill_cta_tables(sp, ep.T, smem);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned char* wbase = smem + kOffVar + static_cast<size_t>(warp) * kWarpFixed;
-    WarpLists L{wbase, wbase + 64, wbase + 128, wbase + 192};
+    unsigned char* wl = smem + kOffVar + static_cast<size_t>(warp) * kWarpFixed;
     const unsigned c0 = sp.nsa, c1 = c0 + sp.nsb;
     const unsigned c2 = c1 + static_cast<unsigned>(sp.npoa) * sp.npva;
     const unsigned c3 = c2 + static_cast<unsigned>(sp.npob) * sp.npvb;
@@ -557,7 +577,7 @@ __global__ void __launch_bounds__(1024) eloc_direct_kernel(SysParams sp, TablePa
         const ulonglong2 x = ep.samples[s];
         unsigned long long hx;
         double ediag;
-        if (!sample_setup(sp, x, lane, L, T64, hx, ediag)) {
+        if (!sample_setup(sp, x, lane, wl, T64, hx, ediag)) {
             invalid_sample(ep, s, lane);
             continue;
         }
@@ -580,7 +600,8 @@ __global__ void __launch_bounds__(1024) eloc_direct_kernel(SysParams sp, TablePa
                 const unsigned r = t - c3, u = r / sp.nsb, w = r - u * sp.nsb;
                 code = (4u << 24) | (u << 12) | w;
             }
-            resolve<PREC>(code, true, sp, tp, ep.mode, L, lut, T64, x, hx, ip32, acc);
+            const Resolved r = resolve<PREC>(code, &sp, &tp, wl, x, hx);
+            accumulate<PREC>(r, tp, ep.mode, ip32, acc);
         }
         sample_finish<PREC>(ep, s, lane, ediag, psix, acc);
         __syncwarp();
@@ -590,64 +611,14 @@ __global__ void __launch_bounds__(1024) eloc_direct_kernel(SysParams sp, TablePa
 // ------------------------------------------------------------------------------------
 // K2b: filtered kernel -- Bloom filter in shared memory in front of the bucket table
 // ------------------------------------------------------------------------------------
-template <int U>
-struct FilterLoop {
-    // One class of excitations as the product outer x inner of two per-sample hash
-    // lists; lanes walk the inner list, U outer entries per pass.
-    template <int PREC>
-    __device__ __forceinline__ static void run(const uint32_t* O, int n1, const uint32_t* In, int n2,
-                                               unsigned cls, uint32_t hx32,
-                                               const uint32_t* __restrict__ filt, uint32_t wmask,
-                                               uint32_t* q, int& qn, int lane, const SysParams& sp,
-                                               const TableParams& tp, const WarpLists& L,
-                                               const unsigned short* lut,
-                                               const unsigned long long* T64, ulonglong2 x,
-                                               unsigned long long hx, float2 ip32, Acc& acc) {
-        const unsigned ltmask = lanemask_lt();
-        for (int u0 = 0; u0 < n1; u0 += U) {
-            uint32_t hu[U];
-#pragma unroll
-            for (int k = 0; k < U; ++k) hu[k] = hx32 ^ ((u0 + k < n1) ? O[u0 + k] : 0u);
-            for (int w0 = 0; w0 < n2; w0 += 32) {
-                const int w = w0 + lane;
-                const bool wv = w < n2;
-                const uint32_t hw = wv ? In[w] : 0u;
-#pragma unroll
-                for (int k = 0; k < U; ++k) {
-                    const uint32_t g = hu[k] ^ hw;
-                    const uint32_t word = filt[(g >> 5) & wmask];
-                    const uint32_t t = __funnelshift_r(word, word, g) & __funnelshift_r(word, word, g >> 27);
-                    const bool pass = wv && (u0 + k < n1) && (t & 1u);
-                    const unsigned m = __ballot_sync(QC_FULLMASK, pass);
-                    if (m) {
-                        if (pass)
-                            q[qn + __popc(m & ltmask)] =
-                                (cls << 24) | (static_cast<unsigned>(u0 + k) << 12) | static_cast<unsigned>(w);
-                        qn += __popc(m);
-                        if (qn >= 32) {
-                            __syncwarp();
-                            const unsigned code = q[lane];
-                            __syncwarp();
-                            const int rem = qn - 32;
-                            if (lane < rem) q[lane] = q[32 + lane];
-                            qn = rem;
-                            __syncwarp();
-                            resolve<PREC>(code, true, sp, tp, QC_SAMPLE, L, lut, T64, x, hx, ip32, acc);
-                        }
-                    }
-                }
-            }
-        }
-    }
-};
-
 template <int PREC, int U>
-__global__ void __launch_bounds__(1024) eloc_filtered_kernel(SysParams sp, TableParams tp,
-                                                             EvalParams ep) {
+__global__ void __launch_bounds__(768) eloc_filtered_kernel(const __grid_constant__ SysParams sp,
+                                                             const __grid_constant__ TableParams tp,
+                                                             const __grid_constant__ EvalParams ep) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + kOffBar);
-    unsigned long long* T64 = reinterpret_cast<unsigned long long*>(smem + kOffT);
-    unsigned short* lut = reinterpret_cast<unsigned short*>(smem + kOffLut);
+    const unsigned long long* T64 = reinterpret_cast<const unsigned long long*>(smem + kOffT);
+    const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
     uint32_t* filt = reinterpret_cast<uint32_t*>(smem + kOffVar);
     const unsigned fbytes = 4u << tp.fw;
     if (threadIdx.x == 0) {
@@ -664,8 +635,7 @@ __global__ void __launch_bounds__(1024) eloc_filtered_kernel(SysParams sp, Table
                      reinterpret_cast<const unsigned char*>(tp.filter) + off, n, bar);
         }
     }
-    for (int t = threadIdx.x; t < 128; t += blockDim.x) T64[t] = ep.T[t];
-    fill_pair_lut(lut);
+    fill_cta_tables(sp, ep.T, smem);
     bool ready = false;
     for (unsigned it = 0; it < kWaitLimit; ++it) {
         if (mbar_try_wait(bar, 0)) {
@@ -683,53 +653,55 @@ __global__ void __launch_bounds__(1024) eloc_filtered_kernel(SysParams sp, Table
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned char* wbase = smem + kOffVar + fbytes + static_cast<size_t>(warp) * filtered_warp_bytes(sp);
-    WarpLists L{wbase, wbase + 64, wbase + 128, wbase + 192};
-    uint32_t* q = reinterpret_cast<uint32_t*>(wbase + 256);
-    uint32_t* lists = reinterpret_cast<uint32_t*>(wbase + kWarpFixed);
-    uint32_t* zero = lists;            // one zero word: the outer list of the singles
-    uint32_t* SA = lists + 4;
-    uint32_t* SB = SA + sp.nsa;
-    uint32_t* PAo = SB + sp.nsb;
-    uint32_t* PAv = PAo + sp.npoa;
-    uint32_t* PBo = PAv + sp.npva;
-    uint32_t* PBv = PBo + sp.npob;
+    unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * filtered_warp_bytes(sp);
+    uint32_t* q = reinterpret_cast<uint32_t*>(wl + 256);
+    uint32_t* H = reinterpret_cast<uint32_t*>(wl + kWarpFixed);
+    // list offsets inside H: 0 zero | SA | SB | PAo | PAv | PBo | PBv
+    const int oSA = 1, oSB = oSA + sp.nsa, oPAo = oSB + sp.nsb, oPAv = oPAo + sp.npoa;
+    const int oPBo = oPAv + sp.npva, oPBv = oPBo + sp.npob;
     const uint32_t wmask = (1u << tp.fw) - 1u;
-    if (lane == 0) zero[0] = 0u;
+    const unsigned ltmask = lanemask_lt();
+    const unsigned char* divA = smem + kOffDiv;
+    const unsigned char* divB = divA + 1024;
+    if (lane == 0) H[0] = 0u;
 
     for (long long s = static_cast<long long>(blockIdx.x) * nw + warp; s < ep.n_u;
          s += static_cast<long long>(gridDim.x) * nw) {
         const ulonglong2 x = ep.samples[s];
         unsigned long long hx;
         double ediag;
-        if (!sample_setup(sp, x, lane, L, T64, hx, ediag)) {
+        if (!sample_setup(sp, x, lane, wl, T64, hx, ediag)) {
             invalid_sample(ep, s, lane);
             continue;
         }
+        const unsigned char* occA = wl;
+        const unsigned char* virA = wl + 64;
+        const unsigned char* occB = wl + 128;
+        const unsigned char* virB = wl + 192;
         // per-sample hash lists (low 32 bits of the linear hash contributions)
         for (int t = lane; t < sp.nsa; t += 32) {
-            const int io = t / sp.va, av = t - io * sp.va;
-            SA[t] = static_cast<uint32_t>(T64[2 * L.occA[io]] ^ T64[2 * L.virA[av]]);
+            const int io = divA[t];
+            H[oSA + t] = static_cast<uint32_t>(T64[2 * occA[io]] ^ T64[2 * virA[t - io * sp.va]]);
         }
         for (int t = lane; t < sp.nsb; t += 32) {
-            const int io = t / sp.vb, av = t - io * sp.vb;
-            SB[t] = static_cast<uint32_t>(T64[2 * L.occB[io] + 1] ^ T64[2 * L.virB[av] + 1]);
+            const int io = divB[t];
+            H[oSB + t] = static_cast<uint32_t>(T64[2 * occB[io] + 1] ^ T64[2 * virB[t - io * sp.vb] + 1]);
         }
         for (int t = lane; t < sp.npoa; t += 32) {
             const unsigned p = lut[t];
-            PAo[t] = static_cast<uint32_t>(T64[2 * L.occA[p & 255u]] ^ T64[2 * L.occA[p >> 8]]);
+            H[oPAo + t] = static_cast<uint32_t>(T64[2 * occA[p & 255u]] ^ T64[2 * occA[p >> 8]]);
         }
         for (int t = lane; t < sp.npva; t += 32) {
             const unsigned p = lut[t];
-            PAv[t] = static_cast<uint32_t>(T64[2 * L.virA[p & 255u]] ^ T64[2 * L.virA[p >> 8]]);
+            H[oPAv + t] = static_cast<uint32_t>(T64[2 * virA[p & 255u]] ^ T64[2 * virA[p >> 8]]);
         }
         for (int t = lane; t < sp.npob; t += 32) {
             const unsigned p = lut[t];
-            PBo[t] = static_cast<uint32_t>(T64[2 * L.occB[p & 255u] + 1] ^ T64[2 * L.occB[p >> 8] + 1]);
+            H[oPBo + t] = static_cast<uint32_t>(T64[2 * occB[p & 255u] + 1] ^ T64[2 * occB[p >> 8] + 1]);
         }
         for (int t = lane; t < sp.npvb; t += 32) {
             const unsigned p = lut[t];
-            PBv[t] = static_cast<uint32_t>(T64[2 * L.virB[p & 255u] + 1] ^ T64[2 * L.virB[p >> 8] + 1]);
+            H[oPBv + t] = static_cast<uint32_t>(T64[2 * virB[p & 255u] + 1] ^ T64[2 * virB[p >> 8] + 1]);
         }
         __syncwarp();
         const double2 psix = ep.psi[s];
@@ -737,16 +709,64 @@ __global__ void __launch_bounds__(1024) eloc_filtered_kernel(SysParams sp, Table
         const uint32_t hx32 = static_cast<uint32_t>(hx);
         Acc acc{};
         int qn = 0;
-        FilterLoop<1>::template run<PREC>(zero, 1, SA, sp.nsa, 0u, hx32, filt, wmask, q, qn, lane, sp, tp, L, lut, T64, x, hx, ip32, acc);
-        FilterLoop<1>::template run<PREC>(zero, 1, SB, sp.nsb, 1u, hx32, filt, wmask, q, qn, lane, sp, tp, L, lut, T64, x, hx, ip32, acc);
-        FilterLoop<U>::template run<PREC>(PAo, sp.npoa, PAv, sp.npva, 2u, hx32, filt, wmask, q, qn, lane, sp, tp, L, lut, T64, x, hx, ip32, acc);
-        FilterLoop<U>::template run<PREC>(PBo, sp.npob, PBv, sp.npvb, 3u, hx32, filt, wmask, q, qn, lane, sp, tp, L, lut, T64, x, hx, ip32, acc);
-        FilterLoop<U>::template run<PREC>(SA, sp.nsa, SB, sp.nsb, 4u, hx32, filt, wmask, q, qn, lane, sp, tp, L, lut, T64, x, hx, ip32, acc);
+        // one loop for the five classes: outer list x inner list, lanes over the inner
+        for (int cls = 0; cls < 5; ++cls) {
+            int oo, n1, io, n2;
+            if (cls == 0) { oo = 0; n1 = 1; io = oSA; n2 = sp.nsa; }
+            else if (cls == 1) { oo = 0; n1 = 1; io = oSB; n2 = sp.nsb; }
+            else if (cls == 2) { oo = oPAo; n1 = sp.npoa; io = oPAv; n2 = sp.npva; }
+            else if (cls == 3) { oo = oPBo; n1 = sp.npob; io = oPBv; n2 = sp.npvb; }
+            else { oo = oSA; n1 = sp.nsa; io = oSB; n2 = sp.nsb; }
+            const unsigned ccode = static_cast<unsigned>(cls) << 24;
+            for (int u0 = 0; u0 < n1; u0 += U) {
+                uint32_t hu[U];
+                unsigned umask = 0;
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    const bool v = u0 + k < n1;
+                    hu[k] = hx32 ^ (v ? H[oo + u0 + k] : 0u);
+                    umask |= (v ? 1u : 0u) << k;
+                }
+                for (int w0 = 0; w0 < n2; w0 += 32) {
+                    const int w = w0 + lane;
+                    const bool wv = w < n2;
+                    const uint32_t hw = wv ? H[io + w] : 0u;
+                    const unsigned vm = wv ? umask : 0u;
+#pragma unroll
+                    for (int k = 0; k < U; ++k) {
+                        const uint32_t g = hu[k] ^ hw;
+                        const uint32_t word = filt[(g >> 5) & wmask];
+                        const uint32_t t = __funnelshift_r(word, word, g) &
+                                           __funnelshift_r(word, word, g >> 27) & (vm >> k);
+                        const bool pass = (t & 1u) != 0u;
+                        const unsigned m = __ballot_sync(QC_FULLMASK, pass);
+                        if (m) {
+                            if (pass)
+                                q[qn + __popc(m & ltmask)] =
+                                    ccode | (static_cast<unsigned>(u0 + k) << 12) | static_cast<unsigned>(w);
+                            qn += __popc(m);
+                            if (qn >= 32) {
+                                __syncwarp();
+                                const unsigned code = q[lane];
+                                __syncwarp();
+                                const int rem = qn - 32;
+                                if (lane < rem) q[lane] = q[32 + lane];
+                                qn = rem;
+                                __syncwarp();
+                                const Resolved r = resolve<PREC>(code, &sp, &tp, wl, x, hx);
+                                accumulate<PREC>(r, tp, QC_SAMPLE, ip32, acc);
+                            }
+                        }
+                    }
+                }
+            }
+        }
         __syncwarp();
-        const unsigned code = q[lane];
-        const bool v = lane < qn;
+        if (lane < qn) {
+            const Resolved r = resolve<PREC>(q[lane], &sp, &tp, wl, x, hx);
+            accumulate<PREC>(r, tp, QC_SAMPLE, ip32, acc);
+        }
         __syncwarp();
-        resolve<PREC>(code, v, sp, tp, QC_SAMPLE, L, lut, T64, x, hx, ip32, acc);
         sample_finish<PREC>(ep, s, lane, ediag, psix, acc);
         __syncwarp();
     }

@@ -150,12 +150,14 @@ def uniform_samples(n_spatial: int, n_alpha: int, n_beta: int, n_u: int, seed: i
 
 
 def _random_subset_mask(rng, M: int, n: int, k: np.ndarray) -> np.ndarray:
-    """Row-wise uniformly random subsets of size k[m] out of n positions."""
+    """Row-wise uniformly random subsets of size k[m] out of n positions: the k[m]
+    smallest of n i.i.d. uniforms in each row."""
     if n == 0:
         return np.zeros((M, 0), dtype=bool)
     r = rng.random((M, n))
-    order = np.argsort(np.argsort(r, axis=1), axis=1)
-    return order < k[:, None]
+    srt = np.sort(r, axis=1)
+    thr = np.where(k > 0, srt[np.arange(M), np.maximum(k, 1) - 1], -1.0)
+    return r <= thr[:, None]
 
 
 def rank_weighted_samples(n_spatial: int, n_alpha: int, n_beta: int, n_u: int, seed: int,
@@ -183,9 +185,14 @@ def rank_weighted_samples(n_spatial: int, n_alpha: int, n_beta: int, n_u: int, s
     total_dets = sum(nd for (_, _, nd) in splits)
     if n_u > total_dets:
         raise ValueError("n_u exceeds the sector dimension")
-    seen: dict = {}
-    order_keys = []
-    while len(order_keys) < n_u:
+    # keep the first n_u distinct draws: dedupe every batch against the distinct keys so
+    # far, remembering each key's first draw index
+    aufbau = aufbau_key(K, n_alpha, n_beta)
+    u_lo = np.empty(0, dtype=np.uint64)
+    u_hi = np.empty(0, dtype=np.uint64)
+    first = np.empty(0, dtype=np.int64)
+    drawn = 0
+    while len(first) < n_u:
         ranks = rng.choice(kmax + 1, size=batch, p=rank_w)
         ka = np.empty(batch, dtype=np.int64)
         kb = np.empty(batch, dtype=np.int64)
@@ -199,21 +206,29 @@ def rank_weighted_samples(n_spatial: int, n_alpha: int, n_beta: int, n_u: int, s
             pick = rng.choice(len(opts), size=sel.size, p=w)
             ka[sel] = np.array([o[0] for o in opts])[pick]
             kb[sel] = np.array([o[1] for o in opts])[pick]
-        holes_a = _random_subset_mask(rng, batch, oa, ka)
-        parts_a = _random_subset_mask(rng, batch, va, ka)
-        holes_b = _random_subset_mask(rng, batch, ob, kb)
-        parts_b = _random_subset_mask(rng, batch, vb, kb)
-        occ_a = np.concatenate([~holes_a, parts_a], axis=1)
-        occ_b = np.concatenate([~holes_b, parts_b], axis=1)
-        keys = pack_occupations(occ_a, occ_b)
-        for lo, hi in zip(keys[:, 0].tolist(), keys[:, 1].tolist()):
-            t = (hi << 64) | lo
-            if t not in seen:
-                seen[t] = len(order_keys)
-                order_keys.append((lo, hi))
-                if len(order_keys) == n_u:
-                    break
-    keys = np.array(order_keys, dtype=np.uint64).reshape(-1, 2)
+        keys = np.empty((batch, 2), dtype=np.uint64)
+        keys[:] = aufbau
+        ex = np.nonzero(ranks > 0)[0]          # rank 0 is the Aufbau determinant itself
+        m = ex.size
+        if m:
+            holes_a = _random_subset_mask(rng, m, oa, ka[ex])
+            parts_a = _random_subset_mask(rng, m, va, ka[ex])
+            holes_b = _random_subset_mask(rng, m, ob, kb[ex])
+            parts_b = _random_subset_mask(rng, m, vb, kb[ex])
+            occ_a = np.concatenate([~holes_a, parts_a], axis=1)
+            occ_b = np.concatenate([~holes_b, parts_b], axis=1)
+            keys[ex] = pack_occupations(occ_a, occ_b)
+        lo = np.concatenate([u_lo, keys[:, 0]])
+        hi = np.concatenate([u_hi, keys[:, 1]])
+        fi = np.concatenate([first, drawn + np.arange(batch, dtype=np.int64)])
+        order = np.lexsort((fi, lo, hi))
+        lo, hi, fi = lo[order], hi[order], fi[order]
+        keep = np.ones(len(lo), dtype=bool)
+        keep[1:] = (lo[1:] != lo[:-1]) | (hi[1:] != hi[:-1])
+        u_lo, u_hi, first = lo[keep], hi[keep], fi[keep]
+        drawn += batch
+    sel = np.argsort(first, kind="stable")[:n_u]
+    keys = np.stack([u_lo[sel], u_hi[sel]], axis=1)
     return np.ascontiguousarray(keys[sort_keys(keys)])
 
 
