@@ -281,8 +281,8 @@ qc_status qc_eloc_set_option(qc_eloc* H, int option, int64_t value) {
             H->opt_warps = static_cast<int>(value);
             return QC_OK;
         case QC_OPT_UNROLL:
-            if (!(value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
-                return fail(H, QC_ERR_ARG, "QC_OPT_UNROLL: 0, 1, 2, 4 or 8");
+            if (!(value == 0 || value == 1 || value == 2 || value == 4))
+                return fail(H, QC_ERR_ARG, "QC_OPT_UNROLL: 0, 1, 2 or 4");
             H->opt_unroll = static_cast<int>(value);
             return QC_OK;
         case QC_OPT_GRID:
@@ -363,8 +363,8 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
         c.warps = warps;
         c.smem = qc::filtered_smem_bytes(sp, warps, fw);
     } else {
-        c.warps = H->opt_warps ? H->opt_warps : 16;
-        c.smem = qc::direct_smem_bytes(c.warps);
+        c.warps = std::min(qc::kFilteredMaxWarps, H->opt_warps ? H->opt_warps : 16);
+        c.smem = qc::direct_smem_bytes(sp, c.warps);
     }
     int per_sm = qc::max_active_ctas(c.kernel, H->precision, c.unroll, 32 * c.warps, c.smem);
     if (per_sm < 1) return fail(H, QC_ERR_CAPACITY, "main kernel cannot be resident with this shape");

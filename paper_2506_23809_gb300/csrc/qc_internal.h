@@ -10,7 +10,7 @@ namespace qc {
 constexpr int kMaxOrb = 128;     // spin orbitals (two 64-bit words)
 constexpr int kMaxSpatial = 64;  // spatial orbitals per spin
 constexpr int kPairLut = 2016;   // C(64, 2): colex pair index -> (i, j), i < j < 64
-constexpr int kFilteredMaxWarps = 24;  // launch bound of the filtered kernel (768 threads)
+constexpr int kFilteredMaxWarps = 24;  // launch bound of the main kernel (768 threads)
 
 // One Hamiltonian (Eq. 2) resident on the device.
 struct SysParams {
@@ -92,7 +92,7 @@ cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk,
 int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem);
 cudaError_t prepare_kernels(size_t max_smem);
 size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw);
-size_t direct_smem_bytes(int warps);
+size_t direct_smem_bytes(const SysParams& sp, int warps);
 int reduce_blocks(long long n);
 
 }  // namespace qc

@@ -211,25 +211,18 @@ __global__ void __launch_bounds__(256) build_table_kernel(TableParams tp, int n_
 //   [kOffLut]   colex pair table: p = C(hi, 2) + lo  ->  lo | hi << 8   (p < 2016)
 //   [kOffDiv]   single-excitation index -> occupied position, per spin (u8, < 1024 each)
 //   [kOffVar]   filter words (filtered kernel only), then one region per warp:
-//               occA[64] virA[64] occB[64] virB[64] (u8) | queue[64] (u32) | hash lists (u32)
+//               occA[64] virA[64] occB[64] virB[64] (u8) | candidate queue (u32) |
+//               single-hit and double-hit queues (uint2) | hash lists (u32, filtered only)
 constexpr size_t kOffBar = 0;
 constexpr size_t kOffT = 16;
 constexpr size_t kOffLut = kOffT + 128 * 8;
 constexpr size_t kOffDiv = kOffLut + kPairLut * 2;
 constexpr size_t kOffVar = ((kOffDiv + 2 * 1024 + 127) / 128) * 128;
-constexpr size_t kWarpFixed = 4 * 64 + 64 * 4;
 
 __host__ __device__ inline size_t list_words(const SysParams& sp) {
     return static_cast<size_t>(1 + sp.nsa + sp.nsb + sp.npoa + sp.npva + sp.npob + sp.npvb);
 }
-__host__ __device__ inline size_t filtered_warp_bytes(const SysParams& sp) {
-    return ((kWarpFixed + 4 * list_words(sp)) + 15) / 16 * 16;
-}
 
-size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw) {
-    return kOffVar + (static_cast<size_t>(4) << fw) + static_cast<size_t>(warps) * filtered_warp_bytes(sp);
-}
-size_t direct_smem_bytes(int warps) { return kOffVar + static_cast<size_t>(warps) * kWarpFixed; }
 
 // CTA-wide tables: T, pair LUT, single-excitation division tables
 __device__ void fill_cta_tables(const SysParams& sp, const unsigned long long* __restrict__ Tg,
@@ -251,138 +244,8 @@ __device__ void fill_cta_tables(const SysParams& sp, const unsigned long long* _
 }
 
 // ------------------------------------------------------------------------------------
-// candidate resolution
+// accumulators and the three batch stages of candidate resolution
 // ------------------------------------------------------------------------------------
-struct Resolved {
-    long long row;  // table row, or -1
-    double h;       // <x|H|x'> with its phase (FP64 path) ...
-    float h32;      // ... or FP32 path
-    int ssign;      // phase in the sorted (exported) convention, +1 / -1
-};
-
-// Decode a candidate (class, u, w) into spin orbitals: i -> a, and j -> b for doubles
-// (j = b = -1 for singles).  Classes: 0 alpha single (w), 1 beta single (w), 2 alpha-alpha
-// double (u: occupied pair, w: empty pair), 3 beta-beta double, 4 alpha-beta double
-// (u: alpha single, w: beta single).  Same-spin doubles have i < j and a < b.
-// Look x' up; on a hit return <x|H|x'> (Slater-Condon rules, Sec. III-B (ii)) with the
-// phase <x'| a+_a a+_b a_j a_i |x> (counts of occupied orbitals below each index).
-template <int PREC>
-__device__ __forceinline__ Resolved resolve(unsigned code, const SysParams* __restrict__ spp,
-                                         const TableParams* __restrict__ tpp,
-                                         const unsigned char* __restrict__ wl, ulonglong2 x,
-                                         unsigned long long hx) {
-    const SysParams& sp = *spp;
-    const TableParams& tp = *tpp;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const unsigned long long* T64 = reinterpret_cast<const unsigned long long*>(smem + kOffT);
-    const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
-    const unsigned char* occA = wl;
-    const unsigned char* virA = wl + 64;
-    const unsigned char* occB = wl + 128;
-    const unsigned char* virB = wl + 192;
-    const int cls = static_cast<int>(code >> 24);
-    const int u = static_cast<int>((code >> 12) & 4095u);
-    const int w = static_cast<int>(code & 4095u);
-    int i, a, j = -1, b = -1;
-    if (cls == 0) {
-        const int io = smem[kOffDiv + w];
-        i = 2 * occA[io];
-        a = 2 * virA[w - io * sp.va];
-    } else if (cls == 1) {
-        const int io = smem[kOffDiv + 1024 + w];
-        i = 2 * occB[io] + 1;
-        a = 2 * virB[w - io * sp.vb] + 1;
-    } else if (cls == 4) {
-        const int io = smem[kOffDiv + u];
-        const int jo = smem[kOffDiv + 1024 + w];
-        i = 2 * occA[io];
-        a = 2 * virA[u - io * sp.va];
-        j = 2 * occB[jo] + 1;
-        b = 2 * virB[w - jo * sp.vb] + 1;
-    } else {
-        const unsigned po = lut[u], pv = lut[w];
-        const unsigned char* occ = cls == 2 ? occA : occB;
-        const unsigned char* vir = cls == 2 ? virA : virB;
-        const int s = cls == 2 ? 0 : 1;
-        i = 2 * occ[po & 255u] + s;
-        j = 2 * occ[po >> 8] + s;
-        a = 2 * vir[pv & 255u] + s;
-        b = 2 * vir[pv >> 8] + s;
-    }
-    ulonglong2 xp = x;
-    flip(xp, i);
-    flip(xp, a);
-    unsigned long long h = hx ^ T64[i] ^ T64[a];
-    if (j >= 0) {
-        flip(xp, j);
-        flip(xp, b);
-        h ^= T64[j] ^ T64[b];
-    }
-    Resolved r;
-    r.row = table_find(tp, xp, h);
-    r.h = 0.0;
-    r.h32 = 0.f;
-    r.ssign = 1;
-    if (r.row < 0) return r;
-    const int K = sp.K;
-    const int ki = i >> 1, ka = a >> 1;
-    int par, sorted_flip = 0;
-    double e64 = 0.0;
-    float e32 = 0.f;
-    if (j < 0) {
-        // single i -> a:  h_ai + sum_{k occ} (ai|kk) - sum_{k occ, same spin} (ak|ki)
-        const int s = i & 1;
-        const size_t rowk = (static_cast<size_t>(ka) * K + ki) * K;
-        if (PREC == QC_FP64) {
-            double f = sp.h[ka * K + ki];
-            for (int q = 0; q < sp.oa; ++q) {
-                const int k = occA[q];
-                f += sp.Jt[rowk + k];
-                if (s == 0) f -= sp.Xt[rowk + k];
-            }
-            for (int q = 0; q < sp.ob; ++q) {
-                const int k = occB[q];
-                f += sp.Jt[rowk + k];
-                if (s == 1) f -= sp.Xt[rowk + k];
-            }
-            e64 = f;
-        } else {
-            float f = sp.h32[ka * K + ki];
-            for (int q = 0; q < sp.oa; ++q) {
-                const int k = occA[q];
-                f += sp.Jt32[rowk + k];
-                if (s == 0) f -= sp.Xt32[rowk + k];
-            }
-            for (int q = 0; q < sp.ob; ++q) {
-                const int k = occB[q];
-                f += sp.Jt32[rowk + k];
-                if (s == 1) f -= sp.Xt32[rowk + k];
-            }
-            e32 = f;
-        }
-        par = below(x, i) + below(x, a) + (i < a);
-    } else {
-        const int kj = j >> 1, kb = b >> 1;
-        const size_t d = ((static_cast<size_t>(ka) * K + ki) * K + kb) * K + kj;  // (ai|bj)
-        par = below(x, i) + below(x, j) + below(x, a) + below(x, b) + (i < j) + (i < b) +
-              (j < b) + (i < a) + (j < a) + (b < a);
-        if ((i & 1) == (j & 1)) {
-            const size_t e = ((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki;  // (aj|bi)
-            if (PREC == QC_FP64) e64 = sp.eri[d] - sp.eri[e];
-            else e32 = sp.eri32[d] - sp.eri32[e];
-        } else {
-            if (PREC == QC_FP64) e64 = sp.eri[d];
-            else e32 = sp.eri32[d];
-            sorted_flip = (i > j) + (a > b);
-        }
-    }
-    const bool neg = (par & 1) != 0;
-    r.h = neg ? -e64 : e64;
-    r.h32 = neg ? -e32 : e32;
-    r.ssign = (neg != ((sorted_flip & 1) != 0)) ? -1 : 1;
-    return r;
-}
-
 struct Acc {
     double re, im;         // FP64 accumulation of sum H psi(x')
     float sr, cr, si, ci;  // FP32 TwoSum accumulation of sum H psi(x')/psi(x)
@@ -392,27 +255,156 @@ struct Acc {
     unsigned long long missing;
 };
 
+// Add one hit: <x|H|x'> (phase included) times psi(x') [FP64], or times psi(x')/psi(x)
+// [FP32, compensated], plus the diagnostics of the exported phase convention.
 template <int PREC>
-__device__ __forceinline__ void accumulate(const Resolved& r, const TableParams& tp, int mode,
-                                           float2 ip32, Acc& acc) {
-    if (r.row < 0) {
-        if (mode == QC_FULL) acc.missing++;
-        return;
-    }
-    const double2 pp = __ldg(tp.psi + r.row);
+__device__ __forceinline__ void add_hit(double h64, float h32, long long row, bool sneg,
+                                        const TableParams& tp, float2 ip32, Acc& acc) {
+    const double2 pp = __ldg(tp.psi + row);
     if (PREC == QC_FP64) {
-        acc.re = fma(r.h, pp.x, acc.re);
-        acc.im = fma(r.h, pp.y, acc.im);
+        acc.re = fma(h64, pp.x, acc.re);
+        acc.im = fma(h64, pp.y, acc.im);
     } else {
         const float px = static_cast<float>(pp.x), py = static_cast<float>(pp.y);
         const float rr = __fsub_rn(__fmul_rn(px, ip32.x), __fmul_rn(py, ip32.y));
         const float ri = __fadd_rn(__fmul_rn(px, ip32.y), __fmul_rn(py, ip32.x));
-        two_sum_acc(acc.sr, acc.cr, __fmul_rn(r.h32, rr));
-        two_sum_acc(acc.si, acc.ci, __fmul_rn(r.h32, ri));
+        two_sum_acc(acc.sr, acc.cr, __fmul_rn(h32, rr));
+        two_sum_acc(acc.si, acc.ci, __fmul_rn(h32, ri));
     }
     acc.hits++;
-    acc.rowsum += static_cast<unsigned long long>(r.row + 1);
-    acc.signsum += r.ssign < 0 ? -(r.row + 1) : (r.row + 1);
+    acc.rowsum += static_cast<unsigned long long>(row + 1);
+    acc.signsum += sneg ? -(row + 1) : (row + 1);
+}
+
+// Stage 1 -- decode a candidate (class, u, w) into the spin orbitals it empties (i, j)
+// and fills (a, b); j = b = 255 for singles.  Classes: 0 alpha single (w), 1 beta single
+// (w), 2 alpha-alpha double (u: occupied pair, w: empty pair), 3 beta-beta double,
+// 4 alpha-beta double (u: alpha single, w: beta single).  Same-spin doubles come out with
+// i < j and a < b.  Returns the packed orbitals i | a << 8 | j << 16 | b << 24.
+__device__ __forceinline__ unsigned decode(unsigned code, const SysParams& sp,
+                                           const unsigned char* __restrict__ wl,
+                                           const unsigned char* __restrict__ smem) {
+    const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
+    const unsigned char* divA = smem + kOffDiv;
+    const unsigned char* divB = divA + 1024;
+    const unsigned char* occA = wl;
+    const unsigned char* virA = wl + 64;
+    const unsigned char* occB = wl + 128;
+    const unsigned char* virB = wl + 192;
+    const unsigned cls = code >> 24;
+    const int u = static_cast<int>((code >> 12) & 4095u);
+    const int w = static_cast<int>(code & 4095u);
+    unsigned i, a, j = 255u, b = 255u;
+    if (cls == 4u) {
+        const int io = divA[u], jo = divB[w];
+        i = 2u * occA[io];
+        a = 2u * virA[u - io * sp.va];
+        j = 2u * occB[jo] + 1u;
+        b = 2u * virB[w - jo * sp.vb] + 1u;
+    } else if (cls >= 2u) {
+        const unsigned po = lut[u], pv = lut[w];
+        const unsigned char* occ = cls == 2u ? occA : occB;
+        const unsigned char* vir = cls == 2u ? virA : virB;
+        const unsigned s = cls - 2u;
+        i = 2u * occ[po & 255u] + s;
+        j = 2u * occ[po >> 8] + s;
+        a = 2u * vir[pv & 255u] + s;
+        b = 2u * vir[pv >> 8] + s;
+    } else {
+        const unsigned char* dv = cls == 0u ? divA : divB;
+        const unsigned char* occ = cls == 0u ? occA : occB;
+        const unsigned char* vir = cls == 0u ? virA : virB;
+        const int vv = cls == 0u ? sp.va : sp.vb;
+        const int io = dv[w];
+        i = 2u * occ[io] + cls;
+        a = 2u * vir[w - io * vv] + cls;
+    }
+    return i | (a << 8) | (j << 16) | (b << 24);
+}
+
+// Stage 1 -- look x' = x with orbitals (i, j) emptied and (a, b) filled up in the table.
+__device__ __forceinline__ long long probe(unsigned orbs, ulonglong2 x, unsigned long long hx,
+                                          const TableParams& tp,
+                                          const unsigned long long* __restrict__ T64) {
+    const int i = orbs & 255u, a = (orbs >> 8) & 255u, j = (orbs >> 16) & 255u, b = orbs >> 24;
+    ulonglong2 xp = x;
+    flip(xp, i);
+    flip(xp, a);
+    unsigned long long h = hx ^ T64[i] ^ T64[a];
+    if (j != 255) {
+        flip(xp, j);
+        flip(xp, b);
+        h ^= T64[j] ^ T64[b];
+    }
+    return table_find(tp, xp, h);
+}
+
+// Stage 2 -- single i -> a (Slater-Condon): h_ai + sum_{k occ} (ai|kk) - sum_{k occ, same
+// spin} (ak|ki), phase <x'| a+_a a_i |x> = (-1)^{P(i) + P(a) + [i < a]}, P = occupied below.
+template <int PREC>
+__device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 x, const SysParams& sp,
+                                               const unsigned char* __restrict__ wl, double& h64,
+                                               float& h32, bool& sneg) {
+    const int i = orbs & 255u, a = (orbs >> 8) & 255u;
+    const int K = sp.K, ki = i >> 1, ka = a >> 1, s = i & 1;
+    const size_t rowk = (static_cast<size_t>(ka) * K + ki) * K;
+    const unsigned char* occA = wl;
+    const unsigned char* occB = wl + 128;
+    const bool neg = ((below(x, i) + below(x, a) + (i < a)) & 1) != 0;
+    if (PREC == QC_FP64) {
+        double f = sp.h[ka * K + ki];
+        for (int q = 0; q < sp.oa; ++q) {
+            const int k = occA[q];
+            f += sp.Jt[rowk + k];
+            if (s == 0) f -= sp.Xt[rowk + k];
+        }
+        for (int q = 0; q < sp.ob; ++q) {
+            const int k = occB[q];
+            f += sp.Jt[rowk + k];
+            if (s == 1) f -= sp.Xt[rowk + k];
+        }
+        h64 = neg ? -f : f;
+    } else {
+        float f = sp.h32[ka * K + ki];
+        for (int q = 0; q < sp.oa; ++q) {
+            const int k = occA[q];
+            f += sp.Jt32[rowk + k];
+            if (s == 0) f -= sp.Xt32[rowk + k];
+        }
+        for (int q = 0; q < sp.ob; ++q) {
+            const int k = occB[q];
+            f += sp.Jt32[rowk + k];
+            if (s == 1) f -= sp.Xt32[rowk + k];
+        }
+        h32 = neg ? -f : f;
+    }
+    sneg = neg;
+}
+
+// Stage 2 -- double (i, j) -> (a, b): <ab||ij> = (ai|bj) - (aj|bi) for equal spins,
+// (ai|bj) for alpha i, a and beta j, b; phase <x'| a+_a a+_b a_j a_i |x> =
+// (-1)^{P(i)+P(j)+P(a)+P(b) + [i<j]+[i<b]+[j<b]+[i<a]+[j<a]+[b<a]}.
+template <int PREC>
+__device__ __forceinline__ void double_element(unsigned orbs, ulonglong2 x, const SysParams& sp,
+                                               double& h64, float& h32, bool& sneg) {
+    const int i = orbs & 255u, a = (orbs >> 8) & 255u, j = (orbs >> 16) & 255u, b = orbs >> 24;
+    const int K = sp.K, ki = i >> 1, ka = a >> 1, kj = j >> 1, kb = b >> 1;
+    const size_t d = ((static_cast<size_t>(ka) * K + ki) * K + kb) * K + kj;  // (ai|bj)
+    const int par = below(x, i) + below(x, j) + below(x, a) + below(x, b) + (i < j) + (i < b) +
+                    (j < b) + (i < a) + (j < a) + (b < a);
+    const bool neg = (par & 1) != 0;
+    const bool same = (i & 1) == (j & 1);
+    if (PREC == QC_FP64) {
+        double e = sp.eri[d];
+        if (same) e -= sp.eri[((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki];  // (aj|bi)
+        h64 = neg ? -e : e;
+    } else {
+        float e = sp.eri32[d];
+        if (same) e -= sp.eri32[((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki];
+        h32 = neg ? -e : e;
+    }
+    // exported convention sorts the emptied and the filled pair
+    sneg = neg != ((((i > j) ? 1 : 0) + ((a > b) ? 1 : 0)) & 1);
 }
 
 // Per-sample set-up shared by both main kernels.  Returns false when x does not hold
@@ -556,114 +548,93 @@ __device__ __forceinline__ float2 inv_psi32(double2 p) {
 }
 
 // ------------------------------------------------------------------------------------
-// K2a: direct kernel -- every connected x' is looked up (FULL mode; SAMPLE without filter)
+// K2: the local-energy kernel
 // ------------------------------------------------------------------------------------
-template <int PREC>
-__global__ void __launch_bounds__(1024) eloc_direct_kernel(const __grid_constant__ SysParams sp,
-                                                           const __grid_constant__ TableParams tp,
-                                                           const __grid_constant__ EvalParams ep) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const unsigned long long* T64 = reinterpret_cast<const unsigned long long*>(smem + kOffT);
-    fill_cta_tables(sp, ep.T, smem);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned char* wl = smem + kOffVar + static_cast<size_t>(warp) * kWarpFixed;
-    const unsigned c0 = sp.nsa, c1 = c0 + sp.nsb;
-    const unsigned c2 = c1 + static_cast<unsigned>(sp.npoa) * sp.npva;
-    const unsigned c3 = c2 + static_cast<unsigned>(sp.npob) * sp.npvb;
-    const unsigned npairs = static_cast<unsigned>(sp.pairs);
-    for (long long s = static_cast<long long>(blockIdx.x) * nw + warp; s < ep.n_u;
-         s += static_cast<long long>(gridDim.x) * nw) {
-        const ulonglong2 x = ep.samples[s];
-        unsigned long long hx;
-        double ediag;
-        if (!sample_setup(sp, x, lane, wl, T64, hx, ediag)) {
-            invalid_sample(ep, s, lane);
-            continue;
-        }
-        const double2 psix = ep.psi[s];
-        const float2 ip32 = inv_psi32(psix);
-        Acc acc{};
-        for (unsigned t = lane; t < npairs; t += 32) {
-            unsigned code;
-            if (t < c0) {
-                code = t;
-            } else if (t < c1) {
-                code = (1u << 24) | (t - c0);
-            } else if (t < c2) {
-                const unsigned r = t - c1, u = r / sp.npva, w = r - u * sp.npva;
-                code = (2u << 24) | (u << 12) | w;
-            } else if (t < c3) {
-                const unsigned r = t - c2, u = r / sp.npvb, w = r - u * sp.npvb;
-                code = (3u << 24) | (u << 12) | w;
-            } else {
-                const unsigned r = t - c3, u = r / sp.nsb, w = r - u * sp.nsb;
-                code = (4u << 24) | (u << 12) | w;
-            }
-            const Resolved r = resolve<PREC>(code, &sp, &tp, wl, x, hx);
-            accumulate<PREC>(r, tp, ep.mode, ip32, acc);
-        }
-        sample_finish<PREC>(ep, s, lane, ediag, psix, acc);
-        __syncwarp();
-    }
+// One warp per sample (persistent grid).  The five excitation classes are walked as
+// outer x inner products of per-sample hash lists by a flat state machine; each step
+// tests U x 32 excitations.  With FILTER, an excitation becomes a candidate only if its
+// two bits are set in the shared-memory Bloom filter; without it (accurate-energy mode,
+// or the unfiltered variant) every excitation is a candidate.  Candidates queue up per
+// warp and are resolved 32 at a time in three full-warp stages: probe the bucket table,
+// then compute the matrix elements of single hits and of double hits in separate
+// batches (so lanes of one batch follow the same path).  All three stages sit at one
+// place in the loop; the end of a sample flushes the partial batches through the same code.
+constexpr int kCandCap = 160;  // >= 31 + 32 * 4 (the largest U with a single flush site)
+constexpr size_t kWarpQueues = 4 * kCandCap + 2 * 64 * 8;  // candidate + two hit queues
+
+__host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filter) {
+    const size_t lists = filter ? 4 * list_words(sp) : 0;
+    return (256 + kWarpQueues + lists + 15) / 16 * 16;
 }
 
-// ------------------------------------------------------------------------------------
-// K2b: filtered kernel -- Bloom filter in shared memory in front of the bucket table
-// ------------------------------------------------------------------------------------
-template <int PREC, int U>
-__global__ void __launch_bounds__(768) eloc_filtered_kernel(const __grid_constant__ SysParams sp,
-                                                             const __grid_constant__ TableParams tp,
-                                                             const __grid_constant__ EvalParams ep) {
+size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw) {
+    return kOffVar + (static_cast<size_t>(4) << fw) + static_cast<size_t>(warps) * main_warp_bytes(sp, true);
+}
+size_t direct_smem_bytes(const SysParams& sp, int warps) {
+    return kOffVar + static_cast<size_t>(warps) * main_warp_bytes(sp, false);
+}
+
+template <int PREC, int U, bool FILTER>
+__global__ void __launch_bounds__(768) eloc_main_kernel(const __grid_constant__ SysParams sp,
+                                                        const __grid_constant__ TableParams tp,
+                                                        const __grid_constant__ EvalParams ep) {
+    static_assert(31 + 32 * U <= kCandCap, "candidate queue too small for U");
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + kOffBar);
     const unsigned long long* T64 = reinterpret_cast<const unsigned long long*>(smem + kOffT);
     const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
     uint32_t* filt = reinterpret_cast<uint32_t*>(smem + kOffVar);
-    const unsigned fbytes = 4u << tp.fw;
-    if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_expect_tx(bar, fbytes);
-        constexpr unsigned kChunk = 32768;
-        for (unsigned off = 0; off < fbytes; off += kChunk) {
-            const unsigned n = (fbytes - off < kChunk) ? (fbytes - off) : kChunk;
-            bulk_g2s(reinterpret_cast<unsigned char*>(filt) + off,
-                     reinterpret_cast<const unsigned char*>(tp.filter) + off, n, bar);
+    const unsigned fbytes = FILTER ? (4u << tp.fw) : 0u;
+    if constexpr (FILTER) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(bar, fbytes);
+            constexpr unsigned kChunk = 32768;
+            for (unsigned off = 0; off < fbytes; off += kChunk) {
+                const unsigned n = (fbytes - off < kChunk) ? (fbytes - off) : kChunk;
+                bulk_g2s(reinterpret_cast<unsigned char*>(filt) + off,
+                         reinterpret_cast<const unsigned char*>(tp.filter) + off, n, bar);
+            }
         }
     }
     fill_cta_tables(sp, ep.T, smem);
-    bool ready = false;
-    for (unsigned it = 0; it < kWaitLimit; ++it) {
-        if (mbar_try_wait(bar, 0)) {
-            ready = true;
-            break;
+    if constexpr (FILTER) {
+        bool ready = false;
+        for (unsigned it = 0; it < kWaitLimit; ++it) {
+            if (mbar_try_wait(bar, 0)) {
+                ready = true;
+                break;
+            }
         }
-    }
-    if (!__syncthreads_and(ready ? 1 : 0)) {
-        // the copy did not land in time: report, give it one more bounded wait, leave
-        // (the whole CTA leaves together: the decision above is CTA-uniform)
-        if (threadIdx.x == 0) atomicOr(&ep.ctr->flags, QC_FLAG_TIMEOUT);
-        if (!ready)
-            for (unsigned it = 0; it < kWaitLimit; ++it)
-                if (mbar_try_wait(bar, 0)) break;
-        return;
+        if (!__syncthreads_and(ready ? 1 : 0)) {
+            // the copy did not land in time: report, give it one more bounded wait, leave
+            // (the whole CTA leaves together: the decision above is CTA-uniform)
+            if (threadIdx.x == 0) atomicOr(&ep.ctr->flags, QC_FLAG_TIMEOUT);
+            if (!ready)
+                for (unsigned it = 0; it < kWaitLimit; ++it)
+                    if (mbar_try_wait(bar, 0)) break;
+            return;
+        }
+    } else {
+        __syncthreads();
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * filtered_warp_bytes(sp);
+    unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * main_warp_bytes(sp, FILTER);
     uint32_t* q = reinterpret_cast<uint32_t*>(wl + 256);
-    uint32_t* H = reinterpret_cast<uint32_t*>(wl + kWarpFixed);
+    uint2* sq = reinterpret_cast<uint2*>(wl + 256 + 4 * kCandCap);
+    uint2* dq = sq + 64;
+    uint32_t* H = reinterpret_cast<uint32_t*>(wl + 256 + kWarpQueues);
     // list offsets inside H: 0 zero | SA | SB | PAo | PAv | PBo | PBv
     const int oSA = 1, oSB = oSA + sp.nsa, oPAo = oSB + sp.nsb, oPAv = oPAo + sp.npoa;
     const int oPBo = oPAv + sp.npva, oPBv = oPBo + sp.npob;
-    const uint32_t wmask = (1u << tp.fw) - 1u;
+    const uint32_t wmask = FILTER ? (1u << tp.fw) - 1u : 0u;
     const unsigned ltmask = lanemask_lt();
     const unsigned char* divA = smem + kOffDiv;
     const unsigned char* divB = divA + 1024;
-    if (lane == 0) H[0] = 0u;
 
     for (long long s = static_cast<long long>(blockIdx.x) * nw + warp; s < ep.n_u;
          s += static_cast<long long>(gridDim.x) * nw) {
@@ -674,99 +645,171 @@ __global__ void __launch_bounds__(768) eloc_filtered_kernel(const __grid_constan
             invalid_sample(ep, s, lane);
             continue;
         }
-        const unsigned char* occA = wl;
-        const unsigned char* virA = wl + 64;
-        const unsigned char* occB = wl + 128;
-        const unsigned char* virB = wl + 192;
-        // per-sample hash lists (low 32 bits of the linear hash contributions)
-        for (int t = lane; t < sp.nsa; t += 32) {
-            const int io = divA[t];
-            H[oSA + t] = static_cast<uint32_t>(T64[2 * occA[io]] ^ T64[2 * virA[t - io * sp.va]]);
+        if (FILTER) {
+            const unsigned char* occA = wl;
+            const unsigned char* virA = wl + 64;
+            const unsigned char* occB = wl + 128;
+            const unsigned char* virB = wl + 192;
+            if (lane == 0) H[0] = 0u;
+            // per-sample hash lists (low 32 bits of the linear hash contributions)
+            for (int t = lane; t < sp.nsa; t += 32) {
+                const int io = divA[t];
+                H[oSA + t] = static_cast<uint32_t>(T64[2 * occA[io]] ^ T64[2 * virA[t - io * sp.va]]);
+            }
+            for (int t = lane; t < sp.nsb; t += 32) {
+                const int io = divB[t];
+                H[oSB + t] = static_cast<uint32_t>(T64[2 * occB[io] + 1] ^ T64[2 * virB[t - io * sp.vb] + 1]);
+            }
+            for (int t = lane; t < sp.npoa; t += 32) {
+                const unsigned p = lut[t];
+                H[oPAo + t] = static_cast<uint32_t>(T64[2 * occA[p & 255u]] ^ T64[2 * occA[p >> 8]]);
+            }
+            for (int t = lane; t < sp.npva; t += 32) {
+                const unsigned p = lut[t];
+                H[oPAv + t] = static_cast<uint32_t>(T64[2 * virA[p & 255u]] ^ T64[2 * virA[p >> 8]]);
+            }
+            for (int t = lane; t < sp.npob; t += 32) {
+                const unsigned p = lut[t];
+                H[oPBo + t] = static_cast<uint32_t>(T64[2 * occB[p & 255u] + 1] ^ T64[2 * occB[p >> 8] + 1]);
+            }
+            for (int t = lane; t < sp.npvb; t += 32) {
+                const unsigned p = lut[t];
+                H[oPBv + t] = static_cast<uint32_t>(T64[2 * virB[p & 255u] + 1] ^ T64[2 * virB[p >> 8] + 1]);
+            }
+            __syncwarp();
         }
-        for (int t = lane; t < sp.nsb; t += 32) {
-            const int io = divB[t];
-            H[oSB + t] = static_cast<uint32_t>(T64[2 * occB[io] + 1] ^ T64[2 * virB[t - io * sp.vb] + 1]);
-        }
-        for (int t = lane; t < sp.npoa; t += 32) {
-            const unsigned p = lut[t];
-            H[oPAo + t] = static_cast<uint32_t>(T64[2 * occA[p & 255u]] ^ T64[2 * occA[p >> 8]]);
-        }
-        for (int t = lane; t < sp.npva; t += 32) {
-            const unsigned p = lut[t];
-            H[oPAv + t] = static_cast<uint32_t>(T64[2 * virA[p & 255u]] ^ T64[2 * virA[p >> 8]]);
-        }
-        for (int t = lane; t < sp.npob; t += 32) {
-            const unsigned p = lut[t];
-            H[oPBo + t] = static_cast<uint32_t>(T64[2 * occB[p & 255u] + 1] ^ T64[2 * occB[p >> 8] + 1]);
-        }
-        for (int t = lane; t < sp.npvb; t += 32) {
-            const unsigned p = lut[t];
-            H[oPBv + t] = static_cast<uint32_t>(T64[2 * virB[p & 255u] + 1] ^ T64[2 * virB[p >> 8] + 1]);
-        }
-        __syncwarp();
         const double2 psix = ep.psi[s];
         const float2 ip32 = inv_psi32(psix);
         const uint32_t hx32 = static_cast<uint32_t>(hx);
         Acc acc{};
-        int qn = 0;
-        // one loop for the five classes: outer list x inner list, lanes over the inner
-        for (int cls = 0; cls < 5; ++cls) {
-            int oo, n1, io, n2;
-            if (cls == 0) { oo = 0; n1 = 1; io = oSA; n2 = sp.nsa; }
-            else if (cls == 1) { oo = 0; n1 = 1; io = oSB; n2 = sp.nsb; }
-            else if (cls == 2) { oo = oPAo; n1 = sp.npoa; io = oPAv; n2 = sp.npva; }
-            else if (cls == 3) { oo = oPBo; n1 = sp.npob; io = oPBv; n2 = sp.npvb; }
-            else { oo = oSA; n1 = sp.nsa; io = oSB; n2 = sp.nsb; }
-            const unsigned ccode = static_cast<unsigned>(cls) << 24;
-            for (int u0 = 0; u0 < n1; u0 += U) {
-                uint32_t hu[U];
-                unsigned umask = 0;
+        int qn = 0, nsq = 0, ndq = 0;
+        // iterator over (class, outer block u0, inner block w0)
+        int cls = -1, oo = 0, n1 = 0, io = 0, n2 = 0, u0 = 0, w0 = 0;
+        bool done = false, need_class = true, need_outer = true;
+        uint32_t hu[U];
+        unsigned umask = 0;
 #pragma unroll
-                for (int k = 0; k < U; ++k) {
-                    const bool v = u0 + k < n1;
-                    hu[k] = hx32 ^ (v ? H[oo + u0 + k] : 0u);
-                    umask |= (v ? 1u : 0u) << k;
+        for (int k = 0; k < U; ++k) hu[k] = 0u;
+        while (true) {
+            if (!done) {
+                if (need_class) {
+                    do {
+                        ++cls;
+                        if (cls == 0) { oo = 0; n1 = 1; io = oSA; n2 = sp.nsa; }
+                        else if (cls == 1) { oo = 0; n1 = 1; io = oSB; n2 = sp.nsb; }
+                        else if (cls == 2) { oo = oPAo; n1 = sp.npoa; io = oPAv; n2 = sp.npva; }
+                        else if (cls == 3) { oo = oPBo; n1 = sp.npob; io = oPBv; n2 = sp.npvb; }
+                        else if (cls == 4) { oo = oSA; n1 = sp.nsa; io = oSB; n2 = sp.nsb; }
+                    } while (cls < 5 && (n1 == 0 || n2 == 0));
+                    done = cls >= 5;
+                    u0 = 0;
+                    w0 = 0;
+                    need_class = false;
+                    need_outer = true;
                 }
-                for (int w0 = 0; w0 < n2; w0 += 32) {
+                if (!done) {
+                    if (need_outer) {
+                        umask = 0;
+#pragma unroll
+                        for (int k = 0; k < U; ++k) {
+                            const bool v = u0 + k < n1;
+                            if (FILTER) hu[k] = hx32 ^ (v ? H[oo + u0 + k] : 0u);
+                            umask |= (v ? 1u : 0u) << k;
+                        }
+                        need_outer = false;
+                    }
                     const int w = w0 + lane;
                     const bool wv = w < n2;
-                    const uint32_t hw = wv ? H[io + w] : 0u;
                     const unsigned vm = wv ? umask : 0u;
+                    const uint32_t hw = (FILTER && wv) ? H[io + w] : 0u;
+                    const unsigned ccode = (static_cast<unsigned>(cls) << 24) | static_cast<unsigned>(w);
 #pragma unroll
                     for (int k = 0; k < U; ++k) {
-                        const uint32_t g = hu[k] ^ hw;
-                        const uint32_t word = filt[(g >> 5) & wmask];
-                        const uint32_t t = __funnelshift_r(word, word, g) &
-                                           __funnelshift_r(word, word, g >> 27) & (vm >> k);
-                        const bool pass = (t & 1u) != 0u;
-                        const unsigned m = __ballot_sync(QC_FULLMASK, pass);
-                        if (m) {
-                            if (pass)
-                                q[qn + __popc(m & ltmask)] =
-                                    ccode | (static_cast<unsigned>(u0 + k) << 12) | static_cast<unsigned>(w);
-                            qn += __popc(m);
-                            if (qn >= 32) {
-                                __syncwarp();
-                                const unsigned code = q[lane];
-                                __syncwarp();
-                                const int rem = qn - 32;
-                                if (lane < rem) q[lane] = q[32 + lane];
-                                qn = rem;
-                                __syncwarp();
-                                const Resolved r = resolve<PREC>(code, &sp, &tp, wl, x, hx);
-                                accumulate<PREC>(r, tp, QC_SAMPLE, ip32, acc);
-                            }
+                        bool pass;
+                        if (FILTER) {
+                            const uint32_t g = hu[k] ^ hw;
+                            const uint32_t word = filt[(g >> 5) & wmask];
+                            pass = ((__funnelshift_r(word, word, g) & __funnelshift_r(word, word, g >> 27) &
+                                     (vm >> k)) & 1u) != 0u;
+                        } else {
+                            pass = ((vm >> k) & 1u) != 0u;
                         }
+                        const unsigned m = __ballot_sync(QC_FULLMASK, pass);
+                        if (pass) q[qn + __popc(m & ltmask)] = ccode | (static_cast<unsigned>(u0 + k) << 12);
+                        qn += __popc(m);
+                    }
+                    w0 += 32;
+                    if (w0 >= n2) {
+                        w0 = 0;
+                        u0 += U;
+                        need_outer = true;
+                        if (u0 >= n1) need_class = true;
                     }
                 }
             }
+            __syncwarp();
+            // resolution stages (hit queues first, so neither can exceed 63 entries)
+            while (true) {
+                if (nsq >= 32 || (done && qn == 0 && nsq > 0)) {
+                    const int n = nsq < 32 ? nsq : 32;
+                    const bool v = lane < n;
+                    const uint2 e = v ? sq[lane] : make_uint2(0u, 0u);
+                    __syncwarp();
+                    if (lane < nsq - n) sq[lane] = sq[n + lane];
+                    nsq -= n;
+                    __syncwarp();
+                    if (v) {
+                        double h64 = 0.0;
+                        float h32 = 0.f;
+                        bool sneg;
+                        single_element<PREC>(e.x, x, sp, wl, h64, h32, sneg);
+                        add_hit<PREC>(h64, h32, e.y, sneg, tp, ip32, acc);
+                    }
+                } else if (ndq >= 32 || (done && qn == 0 && ndq > 0)) {
+                    const int n = ndq < 32 ? ndq : 32;
+                    const bool v = lane < n;
+                    const uint2 e = v ? dq[lane] : make_uint2(0u, 0u);
+                    __syncwarp();
+                    if (lane < ndq - n) dq[lane] = dq[n + lane];
+                    ndq -= n;
+                    __syncwarp();
+                    if (v) {
+                        double h64 = 0.0;
+                        float h32 = 0.f;
+                        bool sneg;
+                        double_element<PREC>(e.x, x, sp, h64, h32, sneg);
+                        add_hit<PREC>(h64, h32, e.y, sneg, tp, ip32, acc);
+                    }
+                } else if (qn >= 32 || (done && qn > 0)) {
+                    const int n = qn < 32 ? qn : 32;
+                    const bool v = lane < n;
+                    const unsigned code = v ? q[lane] : 0u;
+                    __syncwarp();
+                    for (int t = lane; t < qn - n; t += 32) q[t] = q[n + t];
+                    qn -= n;
+                    __syncwarp();
+                    unsigned orbs = 0u;
+                    long long row = -1;
+                    if (v) {
+                        orbs = decode(code, sp, wl, smem);
+                        row = probe(orbs, x, hx, tp, T64);
+                        if (row < 0 && ep.mode == QC_FULL) acc.missing++;
+                    }
+                    const bool hit = row >= 0;
+                    const bool single = (orbs >> 16) == 0xFFFFu;
+                    const unsigned ms = __ballot_sync(QC_FULLMASK, hit && single);
+                    const unsigned md = __ballot_sync(QC_FULLMASK, hit && !single);
+                    if (hit && single) sq[nsq + __popc(ms & ltmask)] = make_uint2(orbs, static_cast<unsigned>(row));
+                    if (hit && !single) dq[ndq + __popc(md & ltmask)] = make_uint2(orbs, static_cast<unsigned>(row));
+                    nsq += __popc(ms);
+                    ndq += __popc(md);
+                    __syncwarp();
+                } else {
+                    break;
+                }
+            }
+            if (done) break;
         }
-        __syncwarp();
-        if (lane < qn) {
-            const Resolved r = resolve<PREC>(q[lane], &sp, &tp, wl, x, hx);
-            accumulate<PREC>(r, tp, QC_SAMPLE, ip32, acc);
-        }
-        __syncwarp();
         sample_finish<PREC>(ep, s, lane, ediag, psix, acc);
         __syncwarp();
     }
@@ -923,14 +966,17 @@ cudaError_t launch_build_table(const TableParams& tp, int n_orb, int na, int nb,
 }
 
 template <int PREC>
-static cudaError_t launch_filtered_u(const SysParams& sp, const TableParams& tp,
-                                     const EvalParams& ep, const LaunchCfg& c, cudaStream_t s) {
+static cudaError_t launch_main_p(const SysParams& sp, const TableParams& tp, const EvalParams& ep,
+                                 const LaunchCfg& c, cudaStream_t s) {
     const dim3 grid(c.grid), block(32 * c.warps);
-    switch (c.unroll) {
-        case 1: eloc_filtered_kernel<PREC, 1><<<grid, block, c.smem, s>>>(sp, tp, ep); break;
-        case 2: eloc_filtered_kernel<PREC, 2><<<grid, block, c.smem, s>>>(sp, tp, ep); break;
-        case 8: eloc_filtered_kernel<PREC, 8><<<grid, block, c.smem, s>>>(sp, tp, ep); break;
-        default: eloc_filtered_kernel<PREC, 4><<<grid, block, c.smem, s>>>(sp, tp, ep); break;
+    if (c.kernel != 2) {
+        eloc_main_kernel<PREC, 1, false><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    } else if (c.unroll == 1) {
+        eloc_main_kernel<PREC, 1, true><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    } else if (c.unroll == 2) {
+        eloc_main_kernel<PREC, 2, true><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    } else {
+        eloc_main_kernel<PREC, 4, true><<<grid, block, c.smem, s>>>(sp, tp, ep);
     }
     return cudaGetLastError();
 }
@@ -938,16 +984,8 @@ static cudaError_t launch_filtered_u(const SysParams& sp, const TableParams& tp,
 cudaError_t launch_eloc_main(const SysParams& sp, const TableParams& tp, const EvalParams& ep,
                              const LaunchCfg& c, cudaStream_t s) {
     if (ep.n_u <= 0) return cudaSuccess;
-    if (c.kernel == 2) {
-        return sp.precision == QC_FP64 ? launch_filtered_u<QC_FP64>(sp, tp, ep, c, s)
-                                       : launch_filtered_u<QC_FP32_COMP>(sp, tp, ep, c, s);
-    }
-    const dim3 grid(c.grid), block(32 * c.warps);
-    if (sp.precision == QC_FP64)
-        eloc_direct_kernel<QC_FP64><<<grid, block, c.smem, s>>>(sp, tp, ep);
-    else
-        eloc_direct_kernel<QC_FP32_COMP><<<grid, block, c.smem, s>>>(sp, tp, ep);
-    return cudaGetLastError();
+    return sp.precision == QC_FP64 ? launch_main_p<QC_FP64>(sp, tp, ep, c, s)
+                                   : launch_main_p<QC_FP32_COMP>(sp, tp, ep, c, s);
 }
 
 cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk, void* summary_dev,
@@ -960,50 +998,32 @@ cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk, void
     return cudaGetLastError();
 }
 
+template <int PREC>
+static const void* main_kernel_ptr(int kernel, int unroll) {
+    if (kernel != 2) return (const void*)eloc_main_kernel<PREC, 1, false>;
+    if (unroll == 1) return (const void*)eloc_main_kernel<PREC, 1, true>;
+    if (unroll == 2) return (const void*)eloc_main_kernel<PREC, 2, true>;
+    return (const void*)eloc_main_kernel<PREC, 4, true>;
+}
+
 int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem) {
+    const void* f = precision == QC_FP64 ? main_kernel_ptr<QC_FP64>(kernel, unroll)
+                                         : main_kernel_ptr<QC_FP32_COMP>(kernel, unroll);
     int n = 0;
-    cudaError_t e;
-    if (kernel == 2) {
-        const void* f = nullptr;
-        if (precision == QC_FP64) {
-            f = unroll == 1 ? (const void*)eloc_filtered_kernel<QC_FP64, 1>
-              : unroll == 2 ? (const void*)eloc_filtered_kernel<QC_FP64, 2>
-              : unroll == 8 ? (const void*)eloc_filtered_kernel<QC_FP64, 8>
-                            : (const void*)eloc_filtered_kernel<QC_FP64, 4>;
-        } else {
-            f = unroll == 1 ? (const void*)eloc_filtered_kernel<QC_FP32_COMP, 1>
-              : unroll == 2 ? (const void*)eloc_filtered_kernel<QC_FP32_COMP, 2>
-              : unroll == 8 ? (const void*)eloc_filtered_kernel<QC_FP32_COMP, 8>
-                            : (const void*)eloc_filtered_kernel<QC_FP32_COMP, 4>;
-        }
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem);
-    } else {
-        const void* f = precision == QC_FP64 ? (const void*)eloc_direct_kernel<QC_FP64>
-                                             : (const void*)eloc_direct_kernel<QC_FP32_COMP>;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem);
-    }
-    return e == cudaSuccess ? n : 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) == cudaSuccess ? n : 0;
 }
 
 cudaError_t prepare_kernels(size_t max_smem) {
     const int v = static_cast<int>(max_smem);
     cudaError_t e = cudaSuccess;
-#define QC_ATTR(k)                                                                    \
-    do {                                                                              \
-        cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, v); \
-        if (r != cudaSuccess) e = r;                                                  \
-    } while (0)
-    QC_ATTR(eloc_direct_kernel<QC_FP64>);
-    QC_ATTR(eloc_direct_kernel<QC_FP32_COMP>);
-    QC_ATTR((eloc_filtered_kernel<QC_FP64, 1>));
-    QC_ATTR((eloc_filtered_kernel<QC_FP64, 2>));
-    QC_ATTR((eloc_filtered_kernel<QC_FP64, 4>));
-    QC_ATTR((eloc_filtered_kernel<QC_FP64, 8>));
-    QC_ATTR((eloc_filtered_kernel<QC_FP32_COMP, 1>));
-    QC_ATTR((eloc_filtered_kernel<QC_FP32_COMP, 2>));
-    QC_ATTR((eloc_filtered_kernel<QC_FP32_COMP, 4>));
-    QC_ATTR((eloc_filtered_kernel<QC_FP32_COMP, 8>));
-#undef QC_ATTR
+    for (int prec = 0; prec < 2; ++prec)
+        for (int kernel = 1; kernel <= 2; ++kernel)
+            for (int unroll : {1, 2, 4}) {
+                const void* f = prec == QC_FP64 ? main_kernel_ptr<QC_FP64>(kernel, unroll)
+                                                : main_kernel_ptr<QC_FP32_COMP>(kernel, unroll);
+                const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+                if (r != cudaSuccess) e = r;
+            }
     return e;
 }
 

@@ -68,11 +68,11 @@ def assert_eloc_close(got, want, rtol=RTOL_FP64):
     return err.max(initial=0.0)
 
 
-KERNELS = [dict(), {2: 1}, {2: 2, 5: 1}, {2: 2, 5: 2}, {2: 2, 5: 4}, {2: 2, 5: 8}, {2: 2, 4: 3, 6: 5}]
+KERNELS = [dict(), {2: 1}, {2: 2, 5: 1}, {2: 2, 5: 2}, {2: 2, 5: 4}, {2: 2, 4: 3, 6: 5}, {2: 1, 4: 1, 6: 7}]
 
 
 @pytest.mark.parametrize("opts", KERNELS, ids=["auto", "direct", "filt_u1", "filt_u2", "filt_u4",
-                                                "filt_u8", "filt_w3_g5"])
+                                                "filt_w3_g5", "direct_w1_g7"])
 def test_tiny_sample_mode(B, orc, opts):
     """N=14, 6 electrons, 1,000 uniform samples (204 pairs each), every kernel variant."""
     ints, s = I.make_workload("n14_e6_u1k")
