@@ -84,6 +84,12 @@ unsigned long long next_pow2(unsigned long long v) {
     return p;
 }
 
+// Buckets of two entries, at most a quarter of the slots filled: most probes of an
+// absent key end at the first bucket.
+unsigned long long table_buckets(long long n) {
+    return next_pow2(2ULL * static_cast<unsigned long long>(std::max<long long>(n, 1)));
+}
+
 int ceil_log2(unsigned long long v) {
     int l = 0;
     while ((1ULL << l) < v) ++l;
@@ -299,7 +305,7 @@ namespace {
 
 // Workspace growth: bucket table for n_table keys, filter of 2^fw words, partials.
 qc_status ensure_workspace(qc_eloc* H, long long n_u, long long n_table, int fw) {
-    const size_t entries = 2 * static_cast<size_t>(next_pow2(static_cast<unsigned long long>(std::max<long long>(n_table, 1))));
+    const size_t entries = 2 * static_cast<size_t>(table_buckets(n_table));
     if (entries > H->slots_cap) {
         free_dev(H->d_slots);
         H->slots_cap = 0;
@@ -448,7 +454,7 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     tp.psi = tpsi;
     tp.n = nt;
     tp.slots = H->d_slots;
-    tp.nb_mask = static_cast<unsigned>(next_pow2(static_cast<unsigned long long>(std::max<long long>(nt, 1))) - 1);
+    tp.nb_mask = static_cast<unsigned>(table_buckets(nt) - 1);
     tp.filter = (cfg.kernel == 2) ? H->d_filter : nullptr;
     tp.fw = (cfg.kernel == 2) ? fw : 0;
     const size_t nbuckets = static_cast<size_t>(tp.nb_mask) + 1;

@@ -10,7 +10,7 @@ namespace qc {
 constexpr int kMaxOrb = 128;     // spin orbitals (two 64-bit words)
 constexpr int kMaxSpatial = 64;  // spatial orbitals per spin
 constexpr int kPairLut = 2016;   // C(64, 2): colex pair index -> (i, j), i < j < 64
-constexpr int kFilteredMaxWarps = 24;  // launch bound of the main kernel (768 threads)
+constexpr int kFilteredMaxWarps = 20;  // launch bound of the main kernel (640 threads)
 
 // One Hamiltonian (Eq. 2) resident on the device.
 struct SysParams {

@@ -41,8 +41,9 @@ __device__ __forceinline__ int below(ulonglong2 x, int k) {
 }
 
 __device__ __forceinline__ void flip(ulonglong2& x, int k) {
-    unsigned long long bit = 1ULL << (k & 63);
-    if (k < 64) x.x ^= bit; else x.y ^= bit;
+    const unsigned long long bit = 1ULL << (k & 63);
+    x.x ^= (k < 64) ? bit : 0ULL;
+    x.y ^= (k < 64) ? 0ULL : bit;
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -257,10 +258,45 @@ struct Acc {
 
 // Add one hit: <x|H|x'> (phase included) times psi(x') [FP64], or times psi(x')/psi(x)
 // [FP32, compensated], plus the diagnostics of the exported phase convention.
+__device__ __forceinline__ ulonglong2 excite(unsigned orbs, ulonglong2 x, unsigned long long hx,
+                                             const unsigned long long* __restrict__ T64,
+                                             unsigned long long& h) {
+    const int i = orbs & 255u, a = (orbs >> 8) & 255u, j = (orbs >> 16) & 255u, b = orbs >> 24;
+    ulonglong2 xp = x;
+    flip(xp, i);
+    flip(xp, a);
+    h = hx ^ T64[i] ^ T64[a];
+    if (j != 255) {
+        flip(xp, j);
+        flip(xp, b);
+        h ^= T64[j] ^ T64[b];
+    }
+    return xp;
+}
+
+// Stage 1 -- probe the home bucket of x' = x with orbitals (i, j) emptied and (a, b)
+// filled.  Returns the row of the first entry whose fingerprint matches (the key itself
+// is checked in stage 2, together with the loads of psi and the integrals), -1 when the
+// bucket shows x' is absent, or the exact result of the full probe walk when the home
+// bucket is full without a fingerprint match.
+__device__ __forceinline__ long long probe(unsigned orbs, ulonglong2 x, unsigned long long hx,
+                                          const TableParams& tp,
+                                          const unsigned long long* __restrict__ T64) {
+    unsigned long long h;
+    const ulonglong2 xp = excite(orbs, x, hx, T64, h);
+    const unsigned fp = bucket_of(h);
+    const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(tp.slots) + (fp & tp.nb_mask));
+    if (e.x != 0ULL && static_cast<unsigned>(e.x >> 32) == fp)
+        return static_cast<long long>(static_cast<unsigned>(e.x)) - 1;
+    if (e.y != 0ULL && static_cast<unsigned>(e.y >> 32) == fp)
+        return static_cast<long long>(static_cast<unsigned>(e.y)) - 1;
+    if (e.x == 0ULL || e.y == 0ULL) return -1;
+    return table_find(tp, xp, h);
+}
+
 template <int PREC>
-__device__ __forceinline__ void add_hit(double h64, float h32, long long row, bool sneg,
-                                        const TableParams& tp, float2 ip32, Acc& acc) {
-    const double2 pp = __ldg(tp.psi + row);
+__device__ __forceinline__ void add_hit(double h64, float h32, long long row, bool sneg, double2 pp,
+                                        float2 ip32, Acc& acc) {
     if (PREC == QC_FP64) {
         acc.re = fma(h64, pp.x, acc.re);
         acc.im = fma(h64, pp.y, acc.im);
@@ -274,6 +310,31 @@ __device__ __forceinline__ void add_hit(double h64, float h32, long long row, bo
     acc.hits++;
     acc.rowsum += static_cast<unsigned long long>(row + 1);
     acc.signsum += sneg ? -(row + 1) : (row + 1);
+}
+
+// Stage 2 common part: issue the loads of the stored key and psi of a stage-1 row, let
+// `element` load the integrals meanwhile, then confirm the key (exact walk on a
+// fingerprint collision) and add the hit.
+template <int PREC, typename Element>
+__device__ __forceinline__ void verify_and_add(uint2 e, ulonglong2 x, unsigned long long hx,
+                                               const TableParams& tp, int mode,
+                                               const unsigned long long* __restrict__ T64,
+                                               float2 ip32, Acc& acc, Element element) {
+    unsigned long long h;
+    const ulonglong2 xp = excite(e.x, x, hx, T64, h);
+    const ulonglong2 key = __ldg(tp.keys + e.y);
+    double2 pp = __ldg(tp.psi + e.y);
+    double h64 = 0.0;
+    float h32 = 0.f;
+    bool sneg = false;
+    element(h64, h32, sneg);
+    long long row = e.y;
+    if (key.x != xp.x || key.y != xp.y) {
+        row = table_find(tp, xp, h);
+        if (row >= 0) pp = __ldg(tp.psi + row);
+        else if (mode == QC_FULL) acc.missing++;
+    }
+    if (row >= 0) add_hit<PREC>(h64, h32, row, sneg, pp, ip32, acc);
 }
 
 // Stage 1 -- decode a candidate (class, u, w) into the spin orbitals it empties (i, j)
@@ -322,23 +383,6 @@ __device__ __forceinline__ unsigned decode(unsigned code, const SysParams& sp,
     return i | (a << 8) | (j << 16) | (b << 24);
 }
 
-// Stage 1 -- look x' = x with orbitals (i, j) emptied and (a, b) filled up in the table.
-__device__ __forceinline__ long long probe(unsigned orbs, ulonglong2 x, unsigned long long hx,
-                                          const TableParams& tp,
-                                          const unsigned long long* __restrict__ T64) {
-    const int i = orbs & 255u, a = (orbs >> 8) & 255u, j = (orbs >> 16) & 255u, b = orbs >> 24;
-    ulonglong2 xp = x;
-    flip(xp, i);
-    flip(xp, a);
-    unsigned long long h = hx ^ T64[i] ^ T64[a];
-    if (j != 255) {
-        flip(xp, j);
-        flip(xp, b);
-        h ^= T64[j] ^ T64[b];
-    }
-    return table_find(tp, xp, h);
-}
-
 // Stage 2 -- single i -> a (Slater-Condon): h_ai + sum_{k occ} (ai|kk) - sum_{k occ, same
 // spin} (ak|ki), phase <x'| a+_a a_i |x> = (-1)^{P(i) + P(a) + [i < a]}, P = occupied below.
 template <int PREC>
@@ -351,31 +395,38 @@ __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 x, cons
     const unsigned char* occA = wl;
     const unsigned char* occB = wl + 128;
     const bool neg = ((below(x, i) + below(x, a) + (i < a)) & 1) != 0;
+    // sum over the occupied orbitals of both spins, four independent partial sums
     if (PREC == QC_FP64) {
-        double f = sp.h[ka * K + ki];
-        for (int q = 0; q < sp.oa; ++q) {
-            const int k = occA[q];
-            f += sp.Jt[rowk + k];
-            if (s == 0) f -= sp.Xt[rowk + k];
-        }
-        for (int q = 0; q < sp.ob; ++q) {
-            const int k = occB[q];
-            f += sp.Jt[rowk + k];
-            if (s == 1) f -= sp.Xt[rowk + k];
-        }
+        double f0 = sp.h[ka * K + ki], f1 = 0.0, f2 = 0.0, f3 = 0.0;
+        const double* jt = sp.Jt + rowk;
+        const double* xt = sp.Xt + rowk;
+        const unsigned char* occS = s == 0 ? occA : occB;
+        const int os = s == 0 ? sp.oa : sp.ob;
+        int q = 0;
+        for (; q + 1 < sp.oa; q += 2) { f0 += jt[occA[q]]; f1 += jt[occA[q + 1]]; }
+        if (q < sp.oa) f0 += jt[occA[q]];
+        for (q = 0; q + 1 < sp.ob; q += 2) { f2 += jt[occB[q]]; f3 += jt[occB[q + 1]]; }
+        if (q < sp.ob) f2 += jt[occB[q]];
+        double g0 = 0.0, g1 = 0.0;
+        for (q = 0; q + 1 < os; q += 2) { g0 += xt[occS[q]]; g1 += xt[occS[q + 1]]; }
+        if (q < os) g0 += xt[occS[q]];
+        const double f = ((f0 + f1) + (f2 + f3)) - (g0 + g1);
         h64 = neg ? -f : f;
     } else {
-        float f = sp.h32[ka * K + ki];
-        for (int q = 0; q < sp.oa; ++q) {
-            const int k = occA[q];
-            f += sp.Jt32[rowk + k];
-            if (s == 0) f -= sp.Xt32[rowk + k];
-        }
-        for (int q = 0; q < sp.ob; ++q) {
-            const int k = occB[q];
-            f += sp.Jt32[rowk + k];
-            if (s == 1) f -= sp.Xt32[rowk + k];
-        }
+        float f0 = sp.h32[ka * K + ki], f1 = 0.f, f2 = 0.f, f3 = 0.f;
+        const float* jt = sp.Jt32 + rowk;
+        const float* xt = sp.Xt32 + rowk;
+        const unsigned char* occS = s == 0 ? occA : occB;
+        const int os = s == 0 ? sp.oa : sp.ob;
+        int q = 0;
+        for (; q + 1 < sp.oa; q += 2) { f0 += jt[occA[q]]; f1 += jt[occA[q + 1]]; }
+        if (q < sp.oa) f0 += jt[occA[q]];
+        for (q = 0; q + 1 < sp.ob; q += 2) { f2 += jt[occB[q]]; f3 += jt[occB[q + 1]]; }
+        if (q < sp.ob) f2 += jt[occB[q]];
+        float g0 = 0.f, g1 = 0.f;
+        for (q = 0; q + 1 < os; q += 2) { g0 += xt[occS[q]]; g1 += xt[occS[q + 1]]; }
+        if (q < os) g0 += xt[occS[q]];
+        const float f = ((f0 + f1) + (f2 + f3)) - (g0 + g1);
         h32 = neg ? -f : f;
     }
     sneg = neg;
@@ -575,7 +626,7 @@ size_t direct_smem_bytes(const SysParams& sp, int warps) {
 }
 
 template <int PREC, int U, bool FILTER>
-__global__ void __launch_bounds__(768) eloc_main_kernel(const __grid_constant__ SysParams sp,
+__global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ SysParams sp,
                                                         const __grid_constant__ TableParams tp,
                                                         const __grid_constant__ EvalParams ep) {
     static_assert(31 + 32 * U <= kCandCap, "candidate queue too small for U");
@@ -758,13 +809,11 @@ __global__ void __launch_bounds__(768) eloc_main_kernel(const __grid_constant__ 
                     if (lane < nsq - n) sq[lane] = sq[n + lane];
                     nsq -= n;
                     __syncwarp();
-                    if (v) {
-                        double h64 = 0.0;
-                        float h32 = 0.f;
-                        bool sneg;
-                        single_element<PREC>(e.x, x, sp, wl, h64, h32, sneg);
-                        add_hit<PREC>(h64, h32, e.y, sneg, tp, ip32, acc);
-                    }
+                    if (v)
+                        verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc,
+                                             [&](double& h64, float& h32, bool& sneg) {
+                                                 single_element<PREC>(e.x, x, sp, wl, h64, h32, sneg);
+                                             });
                 } else if (ndq >= 32 || (done && qn == 0 && ndq > 0)) {
                     const int n = ndq < 32 ? ndq : 32;
                     const bool v = lane < n;
@@ -773,13 +822,11 @@ __global__ void __launch_bounds__(768) eloc_main_kernel(const __grid_constant__ 
                     if (lane < ndq - n) dq[lane] = dq[n + lane];
                     ndq -= n;
                     __syncwarp();
-                    if (v) {
-                        double h64 = 0.0;
-                        float h32 = 0.f;
-                        bool sneg;
-                        double_element<PREC>(e.x, x, sp, h64, h32, sneg);
-                        add_hit<PREC>(h64, h32, e.y, sneg, tp, ip32, acc);
-                    }
+                    if (v)
+                        verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc,
+                                             [&](double& h64, float& h32, bool& sneg) {
+                                                 double_element<PREC>(e.x, x, sp, h64, h32, sneg);
+                                             });
                 } else if (qn >= 32 || (done && qn > 0)) {
                     const int n = qn < 32 ? qn : 32;
                     const bool v = lane < n;
