@@ -275,10 +275,12 @@ __device__ __forceinline__ ulonglong2 excite(unsigned orbs, ulonglong2 x, unsign
 }
 
 // Stage 1 -- probe the home bucket of x' = x with orbitals (i, j) emptied and (a, b)
-// filled.  Returns the row of the first entry whose fingerprint matches (the key itself
-// is checked in stage 2, together with the loads of psi and the integrals), -1 when the
-// bucket shows x' is absent, or the exact result of the full probe walk when the home
-// bucket is full without a fingerprint match.
+// filled.  A bucket with a free entry holds every key whose home it is (a key only moves
+// on when its home bucket is full), so its content does not depend on the order of
+// insertion: its fingerprint-matching entry (at most one) is returned as a candidate row,
+// to be checked against the stored key in stage 2 beside the loads of psi and the
+// integrals.  A full home bucket takes the exact probe walk instead, so the outcome of
+// this stage -- and with it the order of accumulation -- is the same on every run.
 __device__ __forceinline__ long long probe(unsigned orbs, ulonglong2 x, unsigned long long hx,
                                           const TableParams& tp,
                                           const unsigned long long* __restrict__ T64) {
@@ -286,12 +288,10 @@ __device__ __forceinline__ long long probe(unsigned orbs, ulonglong2 x, unsigned
     const ulonglong2 xp = excite(orbs, x, hx, T64, h);
     const unsigned fp = bucket_of(h);
     const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(tp.slots) + (fp & tp.nb_mask));
+    if (e.x != 0ULL && e.y != 0ULL) return table_find(tp, xp, h);
     if (e.x != 0ULL && static_cast<unsigned>(e.x >> 32) == fp)
         return static_cast<long long>(static_cast<unsigned>(e.x)) - 1;
-    if (e.y != 0ULL && static_cast<unsigned>(e.y >> 32) == fp)
-        return static_cast<long long>(static_cast<unsigned>(e.y)) - 1;
-    if (e.x == 0ULL || e.y == 0ULL) return -1;
-    return table_find(tp, xp, h);
+    return -1;
 }
 
 template <int PREC>
