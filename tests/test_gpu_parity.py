@@ -157,6 +157,12 @@ def test_medium_n52_and_shards(B, orc):
     assert g["summary"]["n_pairs"] == 3000 * 25137
     m, var, w, n = orc.reduce(want, counts)
     assert abs(g["summary"]["energy"] - m) <= RTOL_FP64 * abs(m)
+    # run-to-run bitwise determinism of every kernel variant and precision
+    for opts, prec in (({2: 1}, 0), ({2: 2, 5: 2}, 0), ({}, 1)):
+        r1 = run_gpu(B, ints, 52, 14, keys, counts, psi, opts=opts, prec=prec)
+        r2 = run_gpu(B, ints, 52, 14, keys, counts, psi, opts=opts, prec=prec)
+        assert np.array_equal(r1["eloc"].view(np.uint64), r2["eloc"].view(np.uint64)), (opts, prec)
+        assert_sets_equal(r1, det)
     parts = []
     for lo, hi in ((0, 1234), (1234, 3000)):
         gs = run_gpu(B, ints, 52, 14, keys[lo:hi], counts[lo:hi], psi[lo:hi], table=(keys, psi))
