@@ -144,7 +144,8 @@ qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int 
 
 qc_status qc_eloc_destroy(qc_eloc* handle);
 
-/* Message for the last error on this handle (or on handle creation when handle is NULL). */
+/* Message for the last error on this handle; with NULL, of the last handle-less call
+ * (qc_eloc_create, qc_eloc_eval_static) on the calling thread. */
 const char* qc_eloc_last_error(const qc_eloc* handle);
 
 /* Pre-size the workspace for up to n_u_max samples and n_table_max table rows, so that
@@ -177,6 +178,39 @@ qc_status qc_eloc_eval(qc_eloc* handle, const uint64_t* samples, const int64_t* 
 /* Per-phase device times of the last evaluation in ms: {table build, main kernel,
  * reduction}.  Needs QC_OPT_TIMING = 1; synchronizes on the recorded events. */
 qc_status qc_eloc_timings(qc_eloc* handle, float* ms3);
+
+/* ---- allocation-free evaluation ---------------------------------------------------
+ * qc_eloc_eval_static: the sample-space, FP64 evaluation of qc_eloc_eval (the table is
+ * the sample set itself) for callers that cannot allocate device memory when they call
+ * -- code inside a CUDA stream capture whose capture mode forbids unsafe calls, a
+ * framework that owns all device memory through its own pool, or a serving loop that
+ * must never wait on the allocator.  The paper has no counterpart; it is an interface
+ * convenience of this library.
+ *
+ * It takes no handle and allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library routine.  The caller passes every input and output as device memory: h (K*K)
+ * and eri (K^4) in the layouts above, samples / counts / psi as for qc_eloc_eval, and
+ * eloc (complex128[n_u]).  summary may be host or device memory, or NULL.  The library's
+ * own working memory (hash index, filter, integral tables, counters, reduction partials)
+ * lives in one file-scope device array of QC_STATIC_SCRATCH_MB (about 8.4 MB) that every
+ * GPU loading this library holds until the process exits.
+ *
+ * Limits: n_u <= QC_STATIC_MAX_SAMPLES and n_orb <= QC_STATIC_MAX_ORB; larger sizes
+ * return QC_ERR_CAPACITY without touching the GPU.  Errors of this call are read with
+ * qc_eloc_last_error(NULL) on the calling thread.
+ *
+ * The first call on each device (with that device current) looks up the device address
+ * of the array and sets kernel attributes; make that first call before any stream
+ * capture.  All calls share the one array and each clears what must start at zero, so
+ * calls that overlap on the GPU (other streams, other host threads) race and must be
+ * serialized by the caller.  Asynchronous on `stream` like qc_eloc_eval. */
+#define QC_STATIC_MAX_SAMPLES 131072
+#define QC_STATIC_MAX_ORB     128
+#define QC_STATIC_SCRATCH_MB  8.4
+qc_status qc_eloc_eval_static(const double* h, const double* eri, double e_core, int n_orb,
+                              int n_elec, const uint64_t* samples, const int64_t* counts,
+                              const double* psi, int64_t n_u, double* eloc,
+                              qc_eloc_summary* summary, void* stream);
 
 /* Launch shape of the last evaluation on this handle: {kernel (1 direct, 2 filtered),
  * grid CTAs, warps per CTA, unroll, dynamic shared memory bytes, log2 filter words}. */

@@ -80,6 +80,8 @@ def load_library(path: str = LIB_PATH):
     lib.qc_eloc_timings.restype = i32
     lib.qc_eloc_last_config.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.qc_eloc_last_config.restype = i32
+    lib.qc_eloc_eval_static.argtypes = [P, P, f64, i32, i32, P, P, P, i64, P, P, P]
+    lib.qc_eloc_eval_static.restype = i32
     _lib = lib
     return lib
 
@@ -201,6 +203,35 @@ def qc_eloc_eval(handle: QcHandle, samples, counts, psi, table_keys=None, table_
                           ctypes.c_void_p(stream.cuda_stream))
     _check(st, handle.ptr)
     return eloc, diag
+
+
+QC_STATIC_MAX_SAMPLES = 131072
+
+
+def qc_eloc_eval_static(h, eri, e_core: float, n_orb: int, n_elec: int, samples, counts, psi,
+                        eloc, summary=None, stream=None):
+    """The allocation-free entry point: every argument is caller-owned memory (h, eri and
+    the sample arrays on the device, ``summary`` a page-locked uint8 tensor or None).
+    Returns the status code; raises QcError with the library's message on failure."""
+    import torch
+    lib = load_library()
+    for name, t in (("h", h), ("eri", eri)):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    n_u = samples.shape[0]
+    if stream is None:
+        stream = torch.cuda.current_stream(samples.device)
+    st = lib.qc_eloc_eval_static(ctypes.c_void_p(h.data_ptr()), ctypes.c_void_p(eri.data_ptr()),
+                                 float(e_core), int(n_orb), int(n_elec),
+                                 _dptr(samples, "samples", (torch.int64, torch.uint64), 2),
+                                 _dptr(counts, "counts", (torch.int64,)),
+                                 _dptr(psi, "psi", (torch.complex128, torch.float64)), int(n_u),
+                                 ctypes.c_void_p(eloc.data_ptr()),
+                                 None if summary is None else ctypes.c_void_p(summary.data_ptr()),
+                                 ctypes.c_void_p(stream.cuda_stream))
+    if st != QC_OK:
+        raise QcError(st, lib.qc_eloc_last_error(None).decode())
+    return st
 
 
 def qc_eloc_summary_read(handle: QcHandle, stream=None) -> dict:

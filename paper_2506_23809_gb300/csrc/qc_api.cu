@@ -106,6 +106,8 @@ bool prepared_devices[64] = {};
 
 }  // namespace
 
+void qc::set_handleless_error(const std::string& msg) { g_create_error = msg; }
+
 extern "C" {
 
 const char* qc_eloc_last_error(const qc_eloc* h) {

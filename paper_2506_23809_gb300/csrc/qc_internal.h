@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace qc {
@@ -94,5 +95,7 @@ cudaError_t prepare_kernels(size_t max_smem);
 size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw);
 size_t direct_smem_bytes(const SysParams& sp, int warps);
 int reduce_blocks(long long n);
+// message returned by qc_eloc_last_error(NULL) on this thread (qc_api.cu)
+void set_handleless_error(const std::string& msg);
 
 }  // namespace qc
