@@ -216,7 +216,7 @@ def run_ours(args):
     import torch
 
     from paper_2506_23809_gb300 import binding as B
-    from paper_2506_23809_gb300 import build
+    from paper_2506_23809_gb300 import build, shards
 
     world, rank, local = _dist()
     build.build()
@@ -230,8 +230,8 @@ def run_ours(args):
         pg = dist
 
     spec, (ints, s) = _make_workload(args.workload, world)
-    n_rank = spec["n_u"]
-    lo, hi = rank * n_rank, (rank + 1) * n_rank
+    lo, hi = shards.shard_rows(s.n_u, world, rank)
+    n_rank = hi - lo
     prec = B.QC_FP64 if args.precision == "fp64" else B.QC_FP32_COMP
     h = B.qc_eloc_create(ints.h, ints.eri, 0.0, spec["n_orb"], spec["n_elec"], prec, B.QC_SAMPLE)
     B.qc_eloc_set_option(h, B.QC_OPT_TIMING, 1)
@@ -292,16 +292,8 @@ def run_ours(args):
         c = torch.tensor([pairs_rank, n_rank], dtype=torch.float64, device=dev)
         pg.all_reduce(c)
         pairs_all, samples_all = int(c[0].item()), int(c[1].item())
-        # Eq. 1 across ranks: gather (W, sum cE, W * var) and combine (Chan et al.)
-        part = torch.tensor([summ["w"], summ["sum_ce_re"], summ["sum_ce_im"], summ["w"] * summ["var"]],
-                            dtype=torch.float64, device=dev)
-        allp = [torch.empty_like(part) for _ in range(world)]
-        pg.all_gather(allp, part)
-        allp = torch.stack(allp).cpu().numpy()
-        W = allp[:, 0].sum()
-        Ebar = complex(allp[:, 1].sum(), allp[:, 2].sum()) / W
-        means = (allp[:, 1] + 1j * allp[:, 2]) / allp[:, 0]
-        var = (allp[:, 3].sum() + (allp[:, 0] * np.abs(means - Ebar) ** 2).sum()) / W
+        # Eq. 1 across ranks: gather (W, sum cE, W * var) and combine
+        W, Ebar, var = shards.allgather_combine(shards.partials(summ), pg, device=dev)
     else:
         W, Ebar, var = summ["w"], summ["energy"], summ["var"]
     value = pairs_all * args.steps / t_max

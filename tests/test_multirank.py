@@ -1,0 +1,84 @@
+"""The N-rank path without a GPU: two gloo ranks each evaluate a block of rows against the
+whole table (with the CPU oracle standing in for the device kernel) and combine their Eq. 1
+partials with the exchange step of the package; the result equals the single-rank
+reduction over all rows."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_2506_23809_gb300 import shards
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out_path):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    from paper_2506_23809_gb300 import inputs as I
+    ints, s = I.make_workload("n14_e6_u1k")
+    lo, hi = shards.shard_rows(s.n_u, world, rank)
+    el = oracle.eloc(ints.h, ints.eri, 0.0, 14, s.keys[lo:hi], s.psi[lo:hi], s.keys, s.psi, nthreads=1)
+    m, var, w, n = oracle.reduce(el, s.counts[lo:hi])
+    part = np.array([w, w * m.real, w * m.imag, w * var])
+    W, E, V = shards.allgather_combine(part, dist)
+    if rank == 0:
+        np.save(out_path, np.array([W, E.real, E.imag, V]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_shard_rows_cover_everything():
+    for n in (0, 1, 7, 1000, 1001):
+        for world in (1, 2, 3, 8):
+            blocks = [shards.shard_rows(n, world, r) for r in range(world)]
+            assert blocks[0][0] == 0 and blocks[-1][1] == n
+            assert all(blocks[i][1] == blocks[i + 1][0] for i in range(world - 1))
+            sizes = [b - a for a, b in blocks]
+            assert max(sizes) - min(sizes) <= 1
+
+
+def test_combine_matches_pooled_moments():
+    rng = np.random.default_rng(3)
+    e = rng.normal(size=300) + 1j * rng.normal(size=300)
+    c = rng.integers(1, 9, size=300).astype(float)
+    W = c.sum()
+    m = (c * e).sum() / W
+    v = (c * np.abs(e - m) ** 2).sum() / W
+    parts = []
+    for lo, hi in ((0, 50), (50, 51), (51, 300)):
+        w = c[lo:hi].sum()
+        mr = (c[lo:hi] * e[lo:hi]).sum() / w
+        vr = (c[lo:hi] * np.abs(e[lo:hi] - mr) ** 2).sum() / w
+        parts.append([w, w * mr.real, w * mr.imag, w * vr])
+    parts.append([0.0, 0.0, 0.0, 0.0])  # an empty shard
+    W2, m2, v2 = shards.combine(parts)
+    assert W2 == W and abs(m2 - m) < 1e-12 and abs(v2 - v) < 1e-12
+
+
+def test_two_gloo_ranks_equal_one(tmp_path, orc):
+    import multiprocessing as mp
+    from paper_2506_23809_gb300 import inputs as I
+    port = _free_port()
+    out = str(tmp_path / "r0.npy")
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    W, er, ei, V = np.load(out)
+    ints, s = I.make_workload("n14_e6_u1k")
+    el = orc.eloc(ints.h, ints.eri, 0.0, 14, s.keys, s.psi)
+    m, var, w, n = orc.reduce(el, s.counts)
+    assert W == w and abs(complex(er, ei) - m) <= 1e-12 * abs(m) and abs(V - var) <= 1e-10 * var
