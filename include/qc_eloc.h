@@ -100,6 +100,8 @@ typedef int qc_status;
 #define QC_OPT_WARPS         4  /* 0 auto, else warps per CTA of the main kernel (<= 20) */
 #define QC_OPT_UNROLL        5  /* 0 auto, else outer entries per inner pass (1, 2, 4) */
 #define QC_OPT_GRID          6  /* 0 auto, else CTAs of the main kernel */
+#define QC_OPT_PREFILTER     7  /* 1 (default): drop single excitations whose new spin string no
+                                   table key has, and the doubles built on them; 0: off */
 
 typedef struct qc_eloc qc_eloc;
 

@@ -39,11 +39,14 @@ struct qc_eloc {
     size_t slots_cap = 0;  // 64-bit entries
     uint32_t* d_filter = nullptr;
     size_t filter_cap = 0;  // 32-bit words
+    unsigned long long* d_sets = nullptr;  // alpha set | beta set
+    size_t sets_cap = 0;                   // entries per set
     double* d_part = nullptr;
     int part_cap = 0;  // reduction blocks
     qc::Counters* d_ctr = nullptr;
     qc_eloc_summary* d_sum = nullptr;
     int opt_timing = 0, opt_kernel = 0, opt_fw = 0, opt_warps = 0, opt_unroll = 0, opt_grid = 0;
+    int opt_prefilter = 1;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool ev_recorded = false;
     int sm_count = 0;
@@ -261,6 +264,7 @@ qc_status qc_eloc_destroy(qc_eloc* H) {
     free_dev(H->d_T);
     free_dev(H->d_slots);
     free_dev(H->d_filter);
+    free_dev(H->d_sets);
     free_dev(H->d_part);
     free_dev(H->d_ctr);
     free_dev(H->d_sum);
@@ -293,6 +297,7 @@ qc_status qc_eloc_set_option(qc_eloc* H, int option, int64_t value) {
                 return fail(H, QC_ERR_ARG, "QC_OPT_UNROLL: 0, 1, 2 or 4");
             H->opt_unroll = static_cast<int>(value);
             return QC_OK;
+        case QC_OPT_PREFILTER: H->opt_prefilter = value ? 1 : 0; return QC_OK;
         case QC_OPT_GRID:
             if (value < 0 || value > (1 << 20)) return fail(H, QC_ERR_ARG, "QC_OPT_GRID: 0..2^20");
             H->opt_grid = static_cast<int>(value);
@@ -314,6 +319,16 @@ qc_status ensure_workspace(qc_eloc* H, long long n_u, long long n_table, int fw)
         cudaError_t e = cudaMalloc(&H->d_slots, entries * sizeof(unsigned long long));
         if (e != cudaSuccess) return cuda_fail(H, e, "cudaMalloc hash table");
         H->slots_cap = entries;
+    }
+    if (fw > 0 && H->opt_prefilter) {
+        const size_t se = static_cast<size_t>(table_buckets(n_table));
+        if (se > H->sets_cap) {
+            free_dev(H->d_sets);
+            H->sets_cap = 0;
+            cudaError_t e = cudaMalloc(&H->d_sets, 2 * se * sizeof(unsigned long long));
+            if (e != cudaSuccess) return cuda_fail(H, e, "cudaMalloc spin-string sets");
+            H->sets_cap = se;
+        }
     }
     const size_t words = fw > 0 ? (static_cast<size_t>(1) << fw) : 0;
     if (words > H->filter_cap) {
@@ -460,9 +475,20 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     tp.filter = (cfg.kernel == 2) ? H->d_filter : nullptr;
     tp.fw = (cfg.kernel == 2) ? fw : 0;
     const size_t nbuckets = static_cast<size_t>(tp.nb_mask) + 1;
+    unsigned long long* aset = nullptr;
+    unsigned long long* bset = nullptr;
+    if (cfg.kernel == 2 && H->opt_prefilter) {
+        aset = H->d_sets;
+        bset = H->d_sets + nbuckets;
+        tp.aset = aset;
+        tp.bset = bset;
+        tp.set_mask = tp.nb_mask;
+        QC_CHK(cudaMemsetAsync(H->d_sets, 0, 2 * nbuckets * sizeof(unsigned long long), s), "memset sets");
+    }
     QC_CHK(cudaMemsetAsync(H->d_slots, 0, 2 * nbuckets * sizeof(unsigned long long), s), "memset table");
     if (cfg.kernel == 2) QC_CHK(cudaMemsetAsync(H->d_filter, 0, (static_cast<size_t>(4) << fw), s), "memset filter");
-    QC_CHK(qc::launch_build_table(tp, H->n_orb, H->na, H->nb, H->d_T, H->d_slots, H->d_filter, H->d_ctr, s),
+    QC_CHK(qc::launch_build_table(tp, H->n_orb, H->na, H->nb, H->d_T, H->d_slots, H->d_filter, aset, bset,
+                                  H->d_ctr, s),
            "build_table launch");
     if (H->opt_timing) QC_CHK(cudaEventRecord(H->ev[1], s), "cudaEventRecord");
 

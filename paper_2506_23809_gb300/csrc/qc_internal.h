@@ -44,6 +44,11 @@ struct TableParams {
     unsigned nb_mask;                 // buckets - 1 (power of two)
     const uint32_t* filter;           // blocked Bloom filter, (1 << fw) 32-bit words
     int fw;
+    // exact sets of the alpha and beta spatial strings of the table keys (open addressing,
+    // 0 = empty); NULL disables the spin-string prefilter
+    const unsigned long long* aset;
+    const unsigned long long* bset;
+    unsigned set_mask;
 };
 
 // Counters and flags of one evaluation (device memory, zeroed at the start of a call).
@@ -85,7 +90,8 @@ struct LaunchCfg {
 // host-side launchers (qc_kernels.cu)
 cudaError_t launch_build_table(const TableParams& tp, int n_orb, int na, int nb,
                                const unsigned long long* T, unsigned long long* slots,
-                               uint32_t* filter, Counters* ctr, cudaStream_t s);
+                               uint32_t* filter, unsigned long long* aset,
+                               unsigned long long* bset, Counters* ctr, cudaStream_t s);
 cudaError_t launch_eloc_main(const SysParams& sp, const TableParams& tp, const EvalParams& ep,
                              const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk,

@@ -156,10 +156,40 @@ __device__ __forceinline__ long long table_find(const TableParams& tp, ulonglong
 // ------------------------------------------------------------------------------------
 // K0: table build (hash index + Bloom filter + validation)
 // ------------------------------------------------------------------------------------
+// Filter bits of a 32-bit hash g: word (g >> 5) & wmask, bits g & 31, (g >> 27) and
+// (g >> 22) & 31 of that word.
+__device__ __forceinline__ unsigned filter_bits(unsigned g) {
+    return (1u << (g & 31u)) | (1u << (g >> 27)) | (1u << ((g >> 22) & 31u));
+}
+
+// Insert a spin string into an exact set (open addressing on the high hash bits).
+__device__ __forceinline__ void set_insert(unsigned long long* set, unsigned mask, unsigned long long v,
+                                           unsigned long long h) {
+    unsigned b = static_cast<unsigned>(h >> 32) & mask;
+    for (unsigned it = 0; it <= mask; ++it) {
+        const unsigned long long old = atomicCAS(set + b, 0ULL, v);
+        if (old == 0ULL || old == v) return;
+        b = (b + 1u) & mask;
+    }
+}
+
+__device__ __forceinline__ bool set_contains(const unsigned long long* __restrict__ set, unsigned mask,
+                                             unsigned long long v, unsigned long long h) {
+    unsigned b = static_cast<unsigned>(h >> 32) & mask;
+    for (unsigned it = 0; it <= mask; ++it) {
+        const unsigned long long e = __ldg(set + b);
+        if (e == v) return true;
+        if (e == 0ULL) return false;
+        b = (b + 1u) & mask;
+    }
+    return false;
+}
+
 __global__ void __launch_bounds__(256) build_table_kernel(TableParams tp, int n_orb, int na, int nb,
                                                           const unsigned long long* __restrict__ T,
                                                           unsigned long long* slots,
-                                                          uint32_t* filter, Counters* ctr) {
+                                                          uint32_t* filter, unsigned long long* aset,
+                                                          unsigned long long* bset, Counters* ctr) {
     const long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= tp.n) return;
     const ulonglong2 key = tp.keys[r];
@@ -181,15 +211,27 @@ __global__ void __launch_bounds__(256) build_table_kernel(TableParams tp, int n_
     }
     if (ea != na || eb != nb || high) flags |= QC_FLAG_NELEC;
 
-    unsigned long long h = 0;
-    for (unsigned long long w = key.x; w; w &= w - 1ULL) h ^= __ldg(T + (__ffsll(w) - 1));
-    for (unsigned long long w = key.y; w; w &= w - 1ULL) h ^= __ldg(T + 64 + (__ffsll(w) - 1));
+    // key hash, and its alpha / beta parts with the spatial strings they belong to
+    unsigned long long ha = 0, hb = 0, sa = 0, sb = 0;
+    for (unsigned long long w = key.x; w; w &= w - 1ULL) {
+        const int bit = __ffsll(w) - 1;
+        if (bit & 1) { hb ^= __ldg(T + bit); sb |= 1ULL << (bit >> 1); }
+        else { ha ^= __ldg(T + bit); sa |= 1ULL << (bit >> 1); }
+    }
+    for (unsigned long long w = key.y; w; w &= w - 1ULL) {
+        const int bit = __ffsll(w) - 1;
+        if (bit & 1) { hb ^= __ldg(T + 64 + bit); sb |= 1ULL << ((64 + bit) >> 1); }
+        else { ha ^= __ldg(T + 64 + bit); sa |= 1ULL << ((64 + bit) >> 1); }
+    }
+    const unsigned long long h = ha ^ hb;
 
     if (tp.filter != nullptr) {
         const unsigned g = static_cast<unsigned>(h);
         const unsigned wmask = (1u << tp.fw) - 1u;
-        atomicOr(filter + ((g >> 5) & wmask), (1u << (g & 31u)) | (1u << (g >> 27)));
+        atomicOr(filter + ((g >> 5) & wmask), filter_bits(g));
     }
+    if (aset != nullptr && sa != 0ULL) set_insert(aset, tp.set_mask, sa, ha);
+    if (bset != nullptr && sb != 0ULL) set_insert(bset, tp.set_mask, sb, hb);
     const unsigned fp = bucket_of(h);
     const unsigned long long entry =
         (static_cast<unsigned long long>(fp) << 32) | static_cast<unsigned long long>(static_cast<unsigned>(r + 1));
@@ -341,10 +383,13 @@ __device__ __forceinline__ void verify_and_add(uint2 e, ulonglong2 x, unsigned l
 // and fills (a, b); j = b = 255 for singles.  Classes: 0 alpha single (w), 1 beta single
 // (w), 2 alpha-alpha double (u: occupied pair, w: empty pair), 3 beta-beta double,
 // 4 alpha-beta double (u: alpha single, w: beta single).  Same-spin doubles come out with
-// i < j and a < b.  Returns the packed orbitals i | a << 8 | j << 16 | b << 24.
+// i < j and a < b.  Single indices go through IA / IB (the compacted single lists of the
+// filtered kernel) when given.  Returns the packed orbitals i | a << 8 | j << 16 | b << 24.
 __device__ __forceinline__ unsigned decode(unsigned code, const SysParams& sp,
                                            const unsigned char* __restrict__ wl,
-                                           const unsigned char* __restrict__ smem) {
+                                           const unsigned char* __restrict__ smem,
+                                           const unsigned short* __restrict__ IA,
+                                           const unsigned short* __restrict__ IB) {
     const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
     const unsigned char* divA = smem + kOffDiv;
     const unsigned char* divB = divA + 1024;
@@ -353,8 +398,14 @@ __device__ __forceinline__ unsigned decode(unsigned code, const SysParams& sp,
     const unsigned char* occB = wl + 128;
     const unsigned char* virB = wl + 192;
     const unsigned cls = code >> 24;
-    const int u = static_cast<int>((code >> 12) & 4095u);
-    const int w = static_cast<int>(code & 4095u);
+    int u = static_cast<int>((code >> 12) & 4095u);
+    int w = static_cast<int>(code & 4095u);
+    // singles lists may be compacted by the spin-string prefilter: map back
+    if (IA != nullptr) {
+        if (cls == 4u) { u = IA[u]; w = IB[w]; }
+        else if (cls == 0u) w = IA[w];
+        else if (cls == 1u) w = IB[w];
+    }
     unsigned i, a, j = 255u, b = 255u;
     if (cls == 4u) {
         const int io = divA[u], jo = divB[w];
@@ -463,7 +514,9 @@ __device__ __forceinline__ void double_element(unsigned orbs, ulonglong2 x, cons
 __device__ __forceinline__ bool sample_setup(const SysParams& sp, ulonglong2 x, int lane,
                                              unsigned char* wl,
                                              const unsigned long long* __restrict__ T64,
-                                             unsigned long long& hx, double& ediag) {
+                                             unsigned long long& hx, double& ediag,
+                                             unsigned long long& As, unsigned long long& Bs,
+                                             unsigned long long& hxa) {
     unsigned char* occA = wl;
     unsigned char* virA = wl + 64;
     unsigned char* occB = wl + 128;
@@ -501,6 +554,9 @@ __device__ __forceinline__ bool sample_setup(const SysParams& sp, ulonglong2 x, 
     if ((x.y >> lane) & 1ULL) hv ^= T64[lane + 64];
     if ((x.y >> (lane + 32)) & 1ULL) hv ^= T64[lane + 96];
     hx = warp_xor_u64(hv);
+    hxa = warp_xor_u64((lane & 1) ? 0ULL : hv);  // even spin orbitals: the alpha part
+    As = A;
+    Bs = B;
     __syncwarp();
     // diagonal: sum_p h_pp + 1/2 sum_{p,q occ} [(pp|qq) - d(sp,sq) (pq|qp)]  (FP64)
     const int K = sp.K;
@@ -614,7 +670,8 @@ constexpr int kCandCap = 160;  // >= 31 + 32 * 4 (the largest U with a single fl
 constexpr size_t kWarpQueues = 4 * kCandCap + 2 * 64 * 8;  // candidate + two hit queues
 
 __host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filter) {
-    const size_t lists = filter ? 4 * list_words(sp) : 0;
+    // hash lists (u32) and, for the two single lists, their compaction maps (u16)
+    const size_t lists = filter ? 4 * list_words(sp) + 2 * static_cast<size_t>(sp.nsa + sp.nsb) : 0;
     return (256 + kWarpQueues + lists + 15) / 16 * 16;
 }
 
@@ -682,7 +739,10 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
     // list offsets inside H: 0 zero | SA | SB | PAo | PAv | PBo | PBv
     const int oSA = 1, oSB = oSA + sp.nsa, oPAo = oSB + sp.nsb, oPAv = oPAo + sp.npoa;
     const int oPBo = oPAv + sp.npva, oPBv = oPBo + sp.npob;
-    const uint32_t wmask = FILTER ? (1u << tp.fw) - 1u : 0u;
+    unsigned short* IA = FILTER ? reinterpret_cast<unsigned short*>(H + list_words(sp)) : nullptr;
+    unsigned short* IB = FILTER ? IA + sp.nsa : nullptr;
+    int nsa2 = sp.nsa, nsb2 = sp.nsb;  // single-list lengths after the spin-string prefilter
+    const uint32_t wmask4 = FILTER ? ((1u << tp.fw) - 1u) << 2 : 0u;
     const unsigned ltmask = lanemask_lt();
     const unsigned char* divA = smem + kOffDiv;
     const unsigned char* divB = divA + 1024;
@@ -690,9 +750,9 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
     for (long long s = static_cast<long long>(blockIdx.x) * nw + warp; s < ep.n_u;
          s += static_cast<long long>(gridDim.x) * nw) {
         const ulonglong2 x = ep.samples[s];
-        unsigned long long hx;
+        unsigned long long hx, As, Bs, hxa;
         double ediag;
-        if (!sample_setup(sp, x, lane, wl, T64, hx, ediag)) {
+        if (!sample_setup(sp, x, lane, wl, T64, hx, ediag, As, Bs, hxa)) {
             invalid_sample(ep, s, lane);
             continue;
         }
@@ -702,14 +762,52 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
             const unsigned char* occB = wl + 128;
             const unsigned char* virB = wl + 192;
             if (lane == 0) H[0] = 0u;
-            // per-sample hash lists (low 32 bits of the linear hash contributions)
-            for (int t = lane; t < sp.nsa; t += 32) {
-                const int io = divA[t];
-                H[oSA + t] = static_cast<uint32_t>(T64[2 * occA[io]] ^ T64[2 * virA[t - io * sp.va]]);
+            // per-sample hash lists (low 32 bits of the linear hash contributions).  A single
+            // excitation whose new spin string is absent from every table key can take part in
+            // no hit (nor can any alpha-beta double built on it): the spin-string prefilter
+            // drops it, compacting the single lists (IA / IB map back to the full index).
+            const unsigned long long hxb = hx ^ hxa;
+            nsa2 = 0;
+            for (int t0 = 0; t0 < sp.nsa; t0 += 32) {
+                const int t = t0 + lane;
+                bool keep = false;
+                uint32_t hv32 = 0u;
+                if (t < sp.nsa) {
+                    const int io = divA[t];
+                    const int ki = occA[io], ka = virA[t - io * sp.va];
+                    const unsigned long long tm = T64[2 * ki] ^ T64[2 * ka];
+                    hv32 = static_cast<uint32_t>(tm);
+                    keep = tp.aset == nullptr ||
+                           set_contains(tp.aset, tp.set_mask, As ^ (1ULL << ki) ^ (1ULL << ka), hxa ^ tm);
+                }
+                const unsigned m = __ballot_sync(QC_FULLMASK, keep);
+                if (keep) {
+                    const int pos = nsa2 + __popc(m & ltmask);
+                    H[oSA + pos] = hv32;
+                    IA[pos] = static_cast<unsigned short>(t);
+                }
+                nsa2 += __popc(m);
             }
-            for (int t = lane; t < sp.nsb; t += 32) {
-                const int io = divB[t];
-                H[oSB + t] = static_cast<uint32_t>(T64[2 * occB[io] + 1] ^ T64[2 * virB[t - io * sp.vb] + 1]);
+            nsb2 = 0;
+            for (int t0 = 0; t0 < sp.nsb; t0 += 32) {
+                const int t = t0 + lane;
+                bool keep = false;
+                uint32_t hv32 = 0u;
+                if (t < sp.nsb) {
+                    const int io = divB[t];
+                    const int ki = occB[io], ka = virB[t - io * sp.vb];
+                    const unsigned long long tm = T64[2 * ki + 1] ^ T64[2 * ka + 1];
+                    hv32 = static_cast<uint32_t>(tm);
+                    keep = tp.bset == nullptr ||
+                           set_contains(tp.bset, tp.set_mask, Bs ^ (1ULL << ki) ^ (1ULL << ka), hxb ^ tm);
+                }
+                const unsigned m = __ballot_sync(QC_FULLMASK, keep);
+                if (keep) {
+                    const int pos = nsb2 + __popc(m & ltmask);
+                    H[oSB + pos] = hv32;
+                    IB[pos] = static_cast<unsigned short>(t);
+                }
+                nsb2 += __popc(m);
             }
             for (int t = lane; t < sp.npoa; t += 32) {
                 const unsigned p = lut[t];
@@ -737,20 +835,22 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
         // iterator over (class, outer block u0, inner block w0)
         int cls = -1, oo = 0, n1 = 0, io = 0, n2 = 0, u0 = 0, w0 = 0;
         bool done = false, need_class = true, need_outer = true;
-        uint32_t hu[U];
+        // outer hash values with their shifted copies: filter word offset (>> 3), bit 2 (>> 27),
+        // bit 3 (>> 22); XOR commutes with the shifts, so each test needs no shift of its own
+        uint32_t hu[U], hu3[U], hu22[U], hu27[U];
         unsigned umask = 0;
 #pragma unroll
-        for (int k = 0; k < U; ++k) hu[k] = 0u;
+        for (int k = 0; k < U; ++k) hu[k] = hu3[k] = hu22[k] = hu27[k] = 0u;
         while (true) {
             if (!done) {
                 if (need_class) {
                     do {
                         ++cls;
-                        if (cls == 0) { oo = 0; n1 = 1; io = oSA; n2 = sp.nsa; }
-                        else if (cls == 1) { oo = 0; n1 = 1; io = oSB; n2 = sp.nsb; }
+                        if (cls == 0) { oo = 0; n1 = 1; io = oSA; n2 = nsa2; }
+                        else if (cls == 1) { oo = 0; n1 = 1; io = oSB; n2 = nsb2; }
                         else if (cls == 2) { oo = oPAo; n1 = sp.npoa; io = oPAv; n2 = sp.npva; }
                         else if (cls == 3) { oo = oPBo; n1 = sp.npob; io = oPBv; n2 = sp.npvb; }
-                        else if (cls == 4) { oo = oSA; n1 = sp.nsa; io = oSB; n2 = sp.nsb; }
+                        else if (cls == 4) { oo = oSA; n1 = nsa2; io = oSB; n2 = nsb2; }
                     } while (cls < 5 && (n1 == 0 || n2 == 0));
                     done = cls >= 5;
                     u0 = 0;
@@ -764,7 +864,12 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
 #pragma unroll
                         for (int k = 0; k < U; ++k) {
                             const bool v = u0 + k < n1;
-                            if (FILTER) hu[k] = hx32 ^ (v ? H[oo + u0 + k] : 0u);
+                            if (FILTER) {
+                                hu[k] = hx32 ^ (v ? H[oo + u0 + k] : 0u);
+                                hu3[k] = hu[k] >> 3;
+                                hu22[k] = hu[k] >> 22;
+                                hu27[k] = hu[k] >> 27;
+                            }
                             umask |= (v ? 1u : 0u) << k;
                         }
                         need_outer = false;
@@ -773,15 +878,18 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
                     const bool wv = w < n2;
                     const unsigned vm = wv ? umask : 0u;
                     const uint32_t hw = (FILTER && wv) ? H[io + w] : 0u;
+                    const uint32_t hw3 = hw >> 3, hw22 = hw >> 22, hw27 = hw >> 27;
                     const unsigned ccode = (static_cast<unsigned>(cls) << 24) | static_cast<unsigned>(w);
 #pragma unroll
                     for (int k = 0; k < U; ++k) {
                         bool pass;
                         if (FILTER) {
-                            const uint32_t g = hu[k] ^ hw;
-                            const uint32_t word = filt[(g >> 5) & wmask];
-                            pass = ((__funnelshift_r(word, word, g) & __funnelshift_r(word, word, g >> 27) &
-                                     (vm >> k)) & 1u) != 0u;
+                            const uint32_t word = *reinterpret_cast<const uint32_t*>(
+                                reinterpret_cast<const unsigned char*>(filt) + ((hu3[k] ^ hw3) & wmask4));
+                            const uint32_t t = __funnelshift_r(word, word, hu[k] ^ hw) &
+                                               __funnelshift_r(word, word, hu27[k] ^ hw27) &
+                                               __funnelshift_r(word, word, hu22[k] ^ hw22);
+                            pass = ((t & (vm >> k)) & 1u) != 0u;
                         } else {
                             pass = ((vm >> k) & 1u) != 0u;
                         }
@@ -838,7 +946,7 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
                     unsigned orbs = 0u;
                     long long row = -1;
                     if (v) {
-                        orbs = decode(code, sp, wl, smem);
+                        orbs = decode(code, sp, wl, smem, IA, IB);
                         row = probe(orbs, x, hx, tp, T64);
                         if (row < 0 && ep.mode == QC_FULL) acc.missing++;
                     }
@@ -1004,11 +1112,12 @@ __global__ void __launch_bounds__(kRedThreads) reduce_pass2(EvalParams ep, doubl
 // ------------------------------------------------------------------------------------
 cudaError_t launch_build_table(const TableParams& tp, int n_orb, int na, int nb,
                                const unsigned long long* T, unsigned long long* slots,
-                               uint32_t* filter, Counters* ctr, cudaStream_t s) {
+                               uint32_t* filter, unsigned long long* aset,
+                               unsigned long long* bset, Counters* ctr, cudaStream_t s) {
     if (tp.n <= 0) return cudaSuccess;
     const long long blocks = (tp.n + 255) / 256;
     build_table_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(tp, n_orb, na, nb, T, slots,
-                                                                      filter, ctr);
+                                                                      filter, aset, bset, ctr);
     return cudaGetLastError();
 }
 

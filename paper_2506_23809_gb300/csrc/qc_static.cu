@@ -223,7 +223,8 @@ extern "C" qc_status qc_eloc_eval_static(const double* h, const double* eri, dou
     QC_S(cudaMemsetAsync(slots, 0, 2 * (static_cast<size_t>(tp.nb_mask) + 1) * sizeof(unsigned long long), s),
          "memset table");
     if (cfg.kernel == 2) QC_S(cudaMemsetAsync(filter, 0, static_cast<size_t>(4) << fw, s), "memset filter");
-    QC_S(launch_build_table(tp, n_orb, sp.na, sp.nb, T, slots, filter, ctr, s), "build_table launch");
+    QC_S(launch_build_table(tp, n_orb, sp.na, sp.nb, T, slots, filter, nullptr, nullptr, ctr, s),
+         "build_table launch");
     QC_S(launch_eloc_main(sp, tp, ep, cfg, s), "main kernel launch");
     QC_S(launch_reduce(ep, part, reduce_blocks(n_u), sum_dev, sp.pairs, s), "reduce launch");
     if (summary)
