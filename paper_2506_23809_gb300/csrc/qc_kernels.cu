@@ -33,11 +33,25 @@ namespace qc {
 // ------------------------------------------------------------------------------------
 // small device helpers
 // ------------------------------------------------------------------------------------
-// occupied spin orbitals of x strictly below spin orbital k (0 <= k < 128)
-__device__ __forceinline__ int below(ulonglong2 x, int k) {
-    unsigned long long m0 = (k >= 64) ? ~0ULL : ((1ULL << k) - 1ULL);
-    unsigned long long m1 = (k > 64) ? ((1ULL << (k - 64)) - 1ULL) : 0ULL;
-    return __popcll(x.x & m0) + __popcll(x.y & m1);
+// Exclusive prefix parity of a 128-bit occupation: bit k is the parity of the number of
+// occupied spin orbitals below k (doubling prefix XOR within each word, then the low
+// word's total parity carried into the high word).
+__device__ __forceinline__ ulonglong2 prefix_parity(ulonglong2 x) {
+    unsigned long long lo = x.x, hi = x.y;
+#pragma unroll
+    for (int sh = 1; sh < 64; sh <<= 1) {
+        lo ^= lo << sh;
+        hi ^= hi << sh;
+    }
+    ulonglong2 p;
+    p.x = lo ^ x.x;
+    p.y = (hi ^ x.y) ^ ((__popcll(x.x) & 1) ? ~0ULL : 0ULL);
+    return p;
+}
+
+__device__ __forceinline__ int pbit(ulonglong2 p, int k) {
+    const unsigned long long w = (k < 64) ? p.x : p.y;
+    return static_cast<int>((w >> (k & 63)) & 1ULL);
 }
 
 __device__ __forceinline__ void flip(ulonglong2& x, int k) {
@@ -435,9 +449,10 @@ __device__ __forceinline__ unsigned decode(unsigned code, const SysParams& sp,
 }
 
 // Stage 2 -- single i -> a (Slater-Condon): h_ai + sum_{k occ} (ai|kk) - sum_{k occ, same
-// spin} (ak|ki), phase <x'| a+_a a_i |x> = (-1)^{P(i) + P(a) + [i < a]}, P = occupied below.
+// spin} (ak|ki), phase <x'| a+_a a_i |x> = (-1)^{P(i) + P(a) + [i < a]}, P = occupied below
+// (read from the prefix-parity mask px).
 template <int PREC>
-__device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 x, const SysParams& sp,
+__device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 px, const SysParams& sp,
                                                const unsigned char* __restrict__ wl, double& h64,
                                                float& h32, bool& sneg) {
     const int i = orbs & 255u, a = (orbs >> 8) & 255u;
@@ -445,7 +460,7 @@ __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 x, cons
     const size_t rowk = (static_cast<size_t>(ka) * K + ki) * K;
     const unsigned char* occA = wl;
     const unsigned char* occB = wl + 128;
-    const bool neg = ((below(x, i) + below(x, a) + (i < a)) & 1) != 0;
+    const bool neg = (pbit(px, i) ^ pbit(px, a) ^ (i < a ? 1 : 0)) != 0;
     // sum over the occupied orbitals of both spins, four independent partial sums
     if (PREC == QC_FP64) {
         double f0 = sp.h[ka * K + ki], f1 = 0.0, f2 = 0.0, f3 = 0.0;
@@ -487,12 +502,12 @@ __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 x, cons
 // (ai|bj) for alpha i, a and beta j, b; phase <x'| a+_a a+_b a_j a_i |x> =
 // (-1)^{P(i)+P(j)+P(a)+P(b) + [i<j]+[i<b]+[j<b]+[i<a]+[j<a]+[b<a]}.
 template <int PREC>
-__device__ __forceinline__ void double_element(unsigned orbs, ulonglong2 x, const SysParams& sp,
+__device__ __forceinline__ void double_element(unsigned orbs, ulonglong2 px, const SysParams& sp,
                                                double& h64, float& h32, bool& sneg) {
     const int i = orbs & 255u, a = (orbs >> 8) & 255u, j = (orbs >> 16) & 255u, b = orbs >> 24;
     const int K = sp.K, ki = i >> 1, ka = a >> 1, kj = j >> 1, kb = b >> 1;
     const size_t d = ((static_cast<size_t>(ka) * K + ki) * K + kb) * K + kj;  // (ai|bj)
-    const int par = below(x, i) + below(x, j) + below(x, a) + below(x, b) + (i < j) + (i < b) +
+    const int par = (pbit(px, i) ^ pbit(px, j) ^ pbit(px, a) ^ pbit(px, b)) + (i < j) + (i < b) +
                     (j < b) + (i < a) + (j < a) + (b < a);
     const bool neg = (par & 1) != 0;
     const bool same = (i & 1) == (j & 1);
@@ -835,12 +850,12 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
         // iterator over (class, outer block u0, inner block w0)
         int cls = -1, oo = 0, n1 = 0, io = 0, n2 = 0, u0 = 0, w0 = 0;
         bool done = false, need_class = true, need_outer = true;
-        // outer hash values with their shifted copies: filter word offset (>> 3), bit 2 (>> 27),
-        // bit 3 (>> 22); XOR commutes with the shifts, so each test needs no shift of its own
-        uint32_t hu[U], hu3[U], hu22[U], hu27[U];
+        // outer hash values and their copies shifted for the filter word offset (>> 3): XOR
+        // commutes with the shift, so the offset costs one LOP3 per test
+        uint32_t hu[U], hu3[U];
         unsigned umask = 0;
 #pragma unroll
-        for (int k = 0; k < U; ++k) hu[k] = hu3[k] = hu22[k] = hu27[k] = 0u;
+        for (int k = 0; k < U; ++k) hu[k] = hu3[k] = 0u;
         while (true) {
             if (!done) {
                 if (need_class) {
@@ -867,8 +882,6 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
                             if (FILTER) {
                                 hu[k] = hx32 ^ (v ? H[oo + u0 + k] : 0u);
                                 hu3[k] = hu[k] >> 3;
-                                hu22[k] = hu[k] >> 22;
-                                hu27[k] = hu[k] >> 27;
                             }
                             umask |= (v ? 1u : 0u) << k;
                         }
@@ -878,7 +891,7 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
                     const bool wv = w < n2;
                     const unsigned vm = wv ? umask : 0u;
                     const uint32_t hw = (FILTER && wv) ? H[io + w] : 0u;
-                    const uint32_t hw3 = hw >> 3, hw22 = hw >> 22, hw27 = hw >> 27;
+                    const uint32_t hw3 = hw >> 3;
                     const unsigned ccode = (static_cast<unsigned>(cls) << 24) | static_cast<unsigned>(w);
 #pragma unroll
                     for (int k = 0; k < U; ++k) {
@@ -886,9 +899,10 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
                         if (FILTER) {
                             const uint32_t word = *reinterpret_cast<const uint32_t*>(
                                 reinterpret_cast<const unsigned char*>(filt) + ((hu3[k] ^ hw3) & wmask4));
-                            const uint32_t t = __funnelshift_r(word, word, hu[k] ^ hw) &
-                                               __funnelshift_r(word, word, hu27[k] ^ hw27) &
-                                               __funnelshift_r(word, word, hu22[k] ^ hw22);
+                            const uint32_t g = hu[k] ^ hw;
+                            const uint32_t t = __funnelshift_r(word, word, g) &
+                                               __funnelshift_r(word, word, g >> 27) &
+                                               __funnelshift_r(word, word, g >> 22);
                             pass = ((t & (vm >> k)) & 1u) != 0u;
                         } else {
                             pass = ((vm >> k) & 1u) != 0u;
@@ -920,7 +934,7 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
                     if (v)
                         verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc,
                                              [&](double& h64, float& h32, bool& sneg) {
-                                                 single_element<PREC>(e.x, x, sp, wl, h64, h32, sneg);
+                                                 single_element<PREC>(e.x, prefix_parity(x), sp, wl, h64, h32, sneg);
                                              });
                 } else if (ndq >= 32 || (done && qn == 0 && ndq > 0)) {
                     const int n = ndq < 32 ? ndq : 32;
@@ -933,7 +947,7 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
                     if (v)
                         verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc,
                                              [&](double& h64, float& h32, bool& sneg) {
-                                                 double_element<PREC>(e.x, x, sp, h64, h32, sneg);
+                                                 double_element<PREC>(e.x, prefix_parity(x), sp, h64, h32, sneg);
                                              });
                 } else if (qn >= 32 || (done && qn > 0)) {
                     const int n = qn < 32 ? qn : 32;
