@@ -38,7 +38,7 @@ UNIT = "connected matrix elements/s"
 # excitation's hash (1 XOR), derive the filter word index (1), read the filter word (1),
 # test its two bits (3), compact the survivors (1).
 OPS_PER_PAIR = 7
-PROFILE_JSON = os.path.join(ROOT, "profiles", "eloc_filtered_n52_e14_u100k.json")
+PROFILE_JSON = os.path.join(ROOT, "profiles", "eloc_main_n52_e14_u100k.json")
 
 
 def _args():
@@ -361,7 +361,7 @@ def run_ours(args):
             traffic = prof.get("dram_bytes_per_launch")
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
                 "frac": achieved / peak_ops, "traffic": traffic,
-                "kernel": "eloc_filtered_kernel" if cfg["kernel"] == 2 else "eloc_direct_kernel",
+                "kernel": "eloc_main_kernel (filtered)" if cfg["kernel"] == 2 else "eloc_main_kernel (unfiltered)",
                 "ops_per_pair": OPS_PER_PAIR,
                 "peak_basis": f"{props.multi_processor_count} SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz "
                               f"({peak_src} sm_max_mhz)",
