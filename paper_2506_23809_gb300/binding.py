@@ -83,6 +83,20 @@ def load_library(path: str = LIB_PATH):
     lib.qc_eloc_last_config.restype = i32
     lib.qc_eloc_eval_static.argtypes = [P, P, f64, i32, i32, P, P, P, i64, P, P, P]
     lib.qc_eloc_eval_static.restype = i32
+    lib.qc_batch_create.argtypes = [P, i32, ctypes.POINTER(P)]
+    lib.qc_batch_destroy.argtypes = [P]
+    lib.qc_batch_last_error.argtypes = [P]
+    lib.qc_batch_last_error.restype = ctypes.c_char_p
+    lib.qc_batch_set_inputs.argtypes = [P, i32, P, P, P, i64, P]
+    lib.qc_batch_set_config.argtypes = [P, i32, i32, i32]
+    lib.qc_batch_config.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.qc_batch_eval.argtypes = [P, P, P]
+    lib.qc_batch_graph_launch.argtypes = [P, P, P]
+    lib.qc_batch_timings.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+    lib.qc_batch_autotune.argtypes = [P, P, i32, ctypes.POINTER(ctypes.c_int64)]
+    for f in ("qc_batch_create", "qc_batch_destroy", "qc_batch_set_inputs", "qc_batch_set_config",
+              "qc_batch_config", "qc_batch_eval", "qc_batch_graph_launch", "qc_batch_timings", "qc_batch_autotune"):
+        getattr(lib, f).restype = i32
     _lib = lib
     return lib
 
@@ -247,3 +261,92 @@ def keys_to_tensor(keys: np.ndarray, device="cuda"):
     import torch
     k = np.ascontiguousarray(keys, dtype=np.uint64).view(np.int64)
     return torch.from_numpy(k).to(device)
+
+
+# ----------------------------------------------------------------------------------
+# the batched form
+# ----------------------------------------------------------------------------------
+@dataclass
+class QcBatch:
+    ptr: ctypes.c_void_p
+    n_mol: int
+    summary_buf: object  # page-locked uint8 tensor, one qc_eloc_summary per molecule
+    keep: list           # handles and tensors that must outlive the batch's use
+
+
+def _bcheck(st, batch):
+    if st != QC_OK:
+        raise QcError(st, load_library().qc_batch_last_error(batch.ptr if batch else None).decode())
+
+
+def qc_batch_create(handles) -> QcBatch:
+    import torch
+    lib = load_library()
+    arr = (ctypes.c_void_p * len(handles))(*[h.ptr.value for h in handles])
+    out = ctypes.c_void_p()
+    st = lib.qc_batch_create(arr, len(handles), ctypes.byref(out))
+    if st != QC_OK:
+        raise QcError(st, "qc_batch_create failed")
+    buf = torch.zeros(len(handles) * ctypes.sizeof(qc_eloc_summary), dtype=torch.uint8, pin_memory=True)
+    return QcBatch(out, len(handles), buf, list(handles))
+
+
+def qc_batch_destroy(batch: QcBatch):
+    if batch.ptr:
+        load_library().qc_batch_destroy(batch.ptr)
+        batch.ptr = ctypes.c_void_p()
+
+
+def qc_batch_set_inputs(batch: QcBatch, mol: int, samples, counts, psi, eloc):
+    import torch
+    st = load_library().qc_batch_set_inputs(
+        batch.ptr, int(mol), _dptr(samples, "samples", (torch.int64, torch.uint64), 2),
+        _dptr(counts, "counts", (torch.int64,)), _dptr(psi, "psi", (torch.complex128, torch.float64)),
+        int(samples.shape[0]), _dptr(eloc, "eloc", (torch.complex128, torch.float64)))
+    _bcheck(st, batch)
+    batch.keep += [samples, counts, psi, eloc]
+
+
+def qc_batch_set_config(batch: QcBatch, unroll=0, warps=0, units_per_cta=0):
+    _bcheck(load_library().qc_batch_set_config(batch.ptr, int(unroll), int(warps), int(units_per_cta)), batch)
+
+
+def qc_batch_config(batch: QcBatch) -> dict:
+    c = (ctypes.c_int64 * 6)()
+    _bcheck(load_library().qc_batch_config(batch.ptr, c), batch)
+    return dict(unroll=int(c[0]), warps=int(c[1]), units_per_cta=int(c[2]), grid=int(c[3]),
+                units=int(c[4]), smem=int(c[5]))
+
+
+def qc_batch_eval(batch: QcBatch, stream=None):
+    import torch
+    s = stream or torch.cuda.current_stream()
+    _bcheck(load_library().qc_batch_eval(batch.ptr, ctypes.c_void_p(batch.summary_buf.data_ptr()),
+                                         ctypes.c_void_p(s.cuda_stream)), batch)
+
+
+def qc_batch_graph_launch(batch: QcBatch, stream):
+    _bcheck(load_library().qc_batch_graph_launch(batch.ptr, ctypes.c_void_p(batch.summary_buf.data_ptr()),
+                                                 ctypes.c_void_p(stream.cuda_stream)), batch)
+
+
+def qc_batch_summaries(batch: QcBatch, stream=None) -> list:
+    import torch
+    (stream or torch.cuda.current_stream()).synchronize()
+    base = batch.summary_buf.data_ptr()
+    sz = ctypes.sizeof(qc_eloc_summary)
+    return [qc_eloc_summary.from_address(base + m * sz).as_dict() for m in range(batch.n_mol)]
+
+
+def qc_batch_timings(batch: QcBatch):
+    ms = (ctypes.c_float * 3)()
+    _bcheck(load_library().qc_batch_timings(batch.ptr, ms), batch)
+    return tuple(float(v) for v in ms)
+
+
+def qc_batch_autotune(batch: QcBatch, stream=None, iters: int = 2):
+    import torch
+    s = stream or torch.cuda.current_stream()
+    best = (ctypes.c_int64 * 3)()
+    _bcheck(load_library().qc_batch_autotune(batch.ptr, ctypes.c_void_p(s.cuda_stream), int(iters), best), batch)
+    return dict(unroll=int(best[0]), warps=int(best[1]), units_per_cta=int(best[2]))

@@ -1,0 +1,480 @@
+// qc_batch.cu -- the batched form: many molecules (each a qc_eloc handle, its integrals
+// already resident on the device) evaluated together.  One step is five device
+// operations whatever the number of molecules -- a memset of the batch arena, one table
+// build over every molecule's keys, one persistent local-energy launch over work units of
+// all molecules, and the two reduction passes -- and it can be captured once as a CUDA
+// graph.  The launch shape (unroll, warps per CTA, work-unit size) is picked by an
+// autotuner that times candidates on the batch itself.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qc_eloc.h"
+#include "qc_handle.h"
+#include "qc_internal.h"
+
+namespace {
+
+struct BatchInput {
+    const uint64_t* samples = nullptr;
+    const int64_t* counts = nullptr;
+    const double* psi = nullptr;
+    int64_t n_u = 0;
+    double* eloc = nullptr;
+};
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+unsigned long long next_pow2(unsigned long long v) {
+    unsigned long long p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+struct qc_batch {
+    int device = 0;
+    int precision = 0;
+    int n_mol = 0;
+    int sm_count = 0;
+    size_t dyn_limit = 0;
+    std::vector<qc_eloc*> handles;
+    std::vector<BatchInput> in;
+    qc::MolParams* d_mols = nullptr;
+    qc::MolWork* d_work = nullptr;
+    long long* d_key_off = nullptr;
+    qc::WorkUnit* d_units = nullptr;
+    size_t units_cap = 0;
+    unsigned* d_counter = nullptr;
+    unsigned char* d_arena = nullptr;
+    size_t arena_cap = 0, arena_bytes = 0;
+    qc_eloc_summary* d_sums = nullptr;
+    // launch shape
+    int unroll = 4, warps = 0, units_per_cta = 8;
+    int warps_used = 0, grid = 0, n_units = 0;
+    long long n_keys = 0;
+    size_t smem = 0;
+    unsigned filter_bytes = 0, warp_stride = 0;
+    bool dirty = true;
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    qc_eloc_summary* graph_sums = nullptr;
+    // timing of the last eager evaluation
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool timed = false;
+    std::string err;
+};
+
+namespace {
+
+qc_status bfail(qc_batch* b, qc_status st, const std::string& m) {
+    if (b) b->err = m;
+    return st;
+}
+qc_status bcuda(qc_batch* b, cudaError_t e, const char* what) {
+    return bfail(b, e == cudaErrorMemoryAllocation ? QC_ERR_OOM : QC_ERR_CUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int filter_log2(long long n) {
+    int fw = 10;
+    while (fw < 15 && (1LL << fw) < n / 2 + 1) ++fw;
+    return fw;
+}
+
+// Lay out every molecule's workspace in one arena, fill the parameter blocks, cut the
+// samples into work units of similar estimated cost and order them longest first.
+qc_status prepare(qc_batch* B) {
+    const int M = B->n_mol;
+    std::vector<qc::MolParams> mp(M);
+    std::vector<qc::MolWork> mw(M);
+    std::vector<long long> key_off(M + 1, 0);
+    size_t off = 0;
+    unsigned fbytes_max = 0, stride_max = 0;
+    struct Lay { size_t slots, filter, sets, ctr, part, sum; unsigned long long nb; int fw; };
+    std::vector<Lay> lay(M);
+    for (int m = 0; m < M; ++m) {
+        const long long n = std::max<long long>(B->in[m].n_u, 1);
+        Lay& L = lay[m];
+        L.nb = next_pow2(2ULL * static_cast<unsigned long long>(n));
+        L.fw = filter_log2(n);
+        L.slots = off; off = align256(off + 2 * L.nb * 8);
+        L.sets = off; off = align256(off + 2 * L.nb * 8);
+        L.filter = off; off = align256(off + (static_cast<size_t>(4) << L.fw));
+        L.ctr = off; off = align256(off + sizeof(qc::Counters));
+        L.part = off; off = align256(off + qc::kBatchRedBlocks * 4 * sizeof(double));
+        L.sum = 0;
+        fbytes_max = std::max(fbytes_max, 4u << L.fw);
+        stride_max = std::max(stride_max, static_cast<unsigned>(qc::batch_warp_bytes(B->handles[m]->sp)));
+        key_off[m + 1] = key_off[m] + B->in[m].n_u;
+    }
+    if (off > B->arena_cap) {
+        if (B->d_arena) cudaFree(B->d_arena);
+        B->d_arena = nullptr;
+        B->arena_cap = 0;
+        cudaError_t e = cudaMalloc(&B->d_arena, off);
+        if (e != cudaSuccess) return bcuda(B, e, "cudaMalloc batch arena");
+        B->arena_cap = off;
+    }
+    B->arena_bytes = off;
+    unsigned char* A = B->d_arena;
+    for (int m = 0; m < M; ++m) {
+        const Lay& L = lay[m];
+        const BatchInput& I = B->in[m];
+        qc_eloc* H = B->handles[m];
+        qc::MolWork& W = mw[m];
+        W.slots = reinterpret_cast<unsigned long long*>(A + L.slots);
+        W.aset = reinterpret_cast<unsigned long long*>(A + L.sets);
+        W.bset = W.aset + L.nb;
+        W.filter = reinterpret_cast<uint32_t*>(A + L.filter);
+        W.ctr = reinterpret_cast<qc::Counters*>(A + L.ctr);
+        W.part = reinterpret_cast<double*>(A + L.part);
+        W.sum = B->d_sums + m;
+        qc::MolParams& P = mp[m];
+        P.sp = H->sp;
+        P.tp = qc::TableParams{};
+        P.tp.keys = reinterpret_cast<const ulonglong2*>(I.samples);
+        P.tp.psi = reinterpret_cast<const double2*>(I.psi);
+        P.tp.n = I.n_u;
+        P.tp.slots = W.slots;
+        P.tp.nb_mask = static_cast<unsigned>(L.nb - 1);
+        P.tp.filter = W.filter;
+        P.tp.fw = L.fw;
+        P.tp.aset = W.aset;
+        P.tp.bset = W.bset;
+        P.tp.set_mask = static_cast<unsigned>(L.nb - 1);
+        P.ep = qc::EvalParams{};
+        P.ep.samples = reinterpret_cast<const ulonglong2*>(I.samples);
+        P.ep.psi = reinterpret_cast<const double2*>(I.psi);
+        P.ep.counts = reinterpret_cast<const long long*>(I.counts);
+        P.ep.n_u = I.n_u;
+        P.ep.eloc = reinterpret_cast<double2*>(I.eloc);
+        P.ep.ctr = W.ctr;
+        P.ep.T = H->d_T;
+        P.ep.mode = QC_SAMPLE;
+    }
+    B->filter_bytes = fbytes_max;
+    B->warp_stride = (stride_max + 15) / 16 * 16;
+    // launch shape
+    const size_t fixed = qc::smem_fixed_bytes() + B->filter_bytes;
+    if (fixed + B->warp_stride > B->dyn_limit) return bfail(B, QC_ERR_CAPACITY, "batch does not fit shared memory");
+    const int fit = static_cast<int>((B->dyn_limit - fixed) / B->warp_stride);
+    int warps = B->warps > 0 ? B->warps : 20;
+    warps = std::min(std::min(warps, fit), qc::kFilteredMaxWarps);
+    if (warps < 1) return bfail(B, QC_ERR_CAPACITY, "batch does not fit shared memory");
+    B->smem = fixed + static_cast<size_t>(warps) * B->warp_stride;
+    const int per_sm = qc::max_active_batch(B->precision, B->unroll, 32 * warps, B->smem);
+    if (per_sm < 1) return bfail(B, QC_ERR_CAPACITY, "batch kernel cannot be resident with this shape");
+    B->grid = per_sm * B->sm_count;
+    // work units: ~units_per_cta units per CTA, each a block of samples of one molecule
+    double total = 0.0;
+    for (int m = 0; m < M; ++m) total += static_cast<double>(B->in[m].n_u) * static_cast<double>(mp[m].sp.pairs);
+    const double target = std::max(1.0, total / (static_cast<double>(B->grid) * B->units_per_cta));
+    std::vector<qc::WorkUnit> units;
+    std::vector<double> cost;
+    for (int m = 0; m < M; ++m) {
+        const long long n = B->in[m].n_u;
+        if (n <= 0) continue;
+        long long chunk = static_cast<long long>(target / std::max<double>(1.0, static_cast<double>(mp[m].sp.pairs)));
+        chunk = std::max<long long>(chunk, warps);
+        chunk = (chunk + warps - 1) / warps * warps;
+        for (long long s0 = 0; s0 < n; s0 += chunk) {
+            qc::WorkUnit u{};
+            u.mol = m;
+            u.s0 = s0;
+            u.s1 = std::min(n, s0 + chunk);
+            units.push_back(u);
+            cost.push_back(static_cast<double>(u.s1 - u.s0) * static_cast<double>(mp[m].sp.pairs));
+        }
+    }
+    std::vector<size_t> order(units.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<qc::WorkUnit> sorted(units.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = units[order[i]];
+    B->n_units = static_cast<int>(sorted.size());
+    B->n_keys = key_off[M];
+    if (sorted.size() > B->units_cap) {
+        if (B->d_units) cudaFree(B->d_units);
+        B->d_units = nullptr;
+        B->units_cap = 0;
+        cudaError_t e = cudaMalloc(&B->d_units, std::max<size_t>(1, sorted.size()) * sizeof(qc::WorkUnit));
+        if (e != cudaSuccess) return bcuda(B, e, "cudaMalloc work units");
+        B->units_cap = sorted.size();
+    }
+    cudaError_t e;
+    if (!sorted.empty()) {
+        e = cudaMemcpy(B->d_units, sorted.data(), sorted.size() * sizeof(qc::WorkUnit), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bcuda(B, e, "copy work units");
+    }
+    e = cudaMemcpy(B->d_mols, mp.data(), M * sizeof(qc::MolParams), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bcuda(B, e, "copy molecule parameters");
+    e = cudaMemcpy(B->d_work, mw.data(), M * sizeof(qc::MolWork), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bcuda(B, e, "copy molecule workspaces");
+    e = cudaMemcpy(B->d_key_off, key_off.data(), (M + 1) * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bcuda(B, e, "copy key offsets");
+    B->dirty = false;
+    B->warps_used = warps;
+    return QC_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// One batched step on stream s (eager or under capture).
+qc_status enqueue(qc_batch* B, qc_eloc_summary* sums_host, cudaStream_t s, bool timed) {
+    cudaError_t e;
+#define QB(call, what)                                   \
+    do {                                                 \
+        e = (call);                                      \
+        if (e != cudaSuccess) return bcuda(B, e, what);  \
+    } while (0)
+    if (timed) QB(cudaEventRecord(B->ev[0], s), "cudaEventRecord");
+    QB(cudaMemsetAsync(B->d_arena, 0, B->arena_bytes, s), "memset arena");
+    QB(cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned), s), "memset counter");
+    QB(qc::launch_build_batch(B->d_mols, B->d_work, B->d_key_off, B->n_mol, B->n_keys, s), "batch build");
+    if (timed) QB(cudaEventRecord(B->ev[1], s), "cudaEventRecord");
+    if (B->n_units > 0) {
+        qc::BatchParams bp{};
+        bp.mols = B->d_mols;
+        bp.units = B->d_units;
+        bp.n_units = B->n_units;
+        bp.counter = B->d_counter;
+        bp.filter_bytes = B->filter_bytes;
+        bp.warp_stride = B->warp_stride;
+        QB(qc::launch_eloc_batch(bp, B->precision, B->unroll, B->grid, B->warps_used, B->smem, s), "batch kernel");
+    }
+    if (timed) QB(cudaEventRecord(B->ev[2], s), "cudaEventRecord");
+    QB(qc::launch_reduce_batch(B->d_mols, B->d_work, B->n_mol, s), "batch reduce");
+    if (timed) QB(cudaEventRecord(B->ev[3], s), "cudaEventRecord");
+    if (sums_host)
+        QB(cudaMemcpyAsync(sums_host, B->d_sums, B->n_mol * sizeof(qc_eloc_summary), cudaMemcpyDeviceToHost, s),
+           "summary copy");
+#undef QB
+    return QC_OK;
+}
+
+void drop_graph(qc_batch* B) {
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    B->exec = nullptr;
+    B->graph = nullptr;
+    B->graph_sums = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+qc_status qc_batch_create(qc_eloc* const* handles, int n_mol, qc_batch** out) {
+    if (!out) return QC_ERR_ARG;
+    *out = nullptr;
+    if (!handles || n_mol <= 0 || n_mol > 65535) return QC_ERR_ARG;
+    qc_batch* B = new (std::nothrow) qc_batch();
+    if (!B) return QC_ERR_OOM;
+    B->n_mol = n_mol;
+    B->handles.assign(handles, handles + n_mol);
+    B->in.resize(n_mol);
+    for (int m = 0; m < n_mol; ++m) {
+        qc_eloc* H = handles[m];
+        if (!H || H->mode != QC_SAMPLE || H->precision != handles[0]->precision || H->device != handles[0]->device) {
+            delete B;
+            return QC_ERR_ARG;
+        }
+    }
+    B->device = handles[0]->device;
+    B->precision = handles[0]->precision;
+    B->sm_count = handles[0]->sm_count;
+    cudaError_t e = qc::prepare_batch_kernels(handles[0]->smem_optin, &B->dyn_limit);
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_mols, n_mol * sizeof(qc::MolParams));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_work, n_mol * sizeof(qc::MolWork));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_key_off, (n_mol + 1) * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_counter, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_sums, n_mol * sizeof(qc_eloc_summary));
+    for (auto& ev : B->ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) {
+        qc_batch_destroy(B);
+        return e == cudaErrorMemoryAllocation ? QC_ERR_OOM : QC_ERR_CUDA;
+    }
+    *out = B;
+    return QC_OK;
+}
+
+qc_status qc_batch_destroy(qc_batch* B) {
+    if (!B) return QC_OK;
+    drop_graph(B);
+    for (void* p : {static_cast<void*>(B->d_mols), static_cast<void*>(B->d_work), static_cast<void*>(B->d_key_off),
+                    static_cast<void*>(B->d_units), static_cast<void*>(B->d_counter), static_cast<void*>(B->d_arena),
+                    static_cast<void*>(B->d_sums)})
+        if (p) cudaFree(p);
+    for (auto& ev : B->ev)
+        if (ev) cudaEventDestroy(ev);
+    delete B;
+    return QC_OK;
+}
+
+const char* qc_batch_last_error(const qc_batch* B) { return B ? B->err.c_str() : ""; }
+
+qc_status qc_batch_set_inputs(qc_batch* B, int mol, const uint64_t* samples, const int64_t* counts,
+                              const double* psi, int64_t n_u, double* eloc) {
+    if (!B) return QC_ERR_ARG;
+    if (mol < 0 || mol >= B->n_mol) return bfail(B, QC_ERR_ARG, "molecule index out of range");
+    if (n_u < 0 || n_u >= (1LL << 31)) return bfail(B, QC_ERR_ARG, "bad n_u");
+    if (n_u > 0 && (!samples || !counts || !psi || !eloc)) return bfail(B, QC_ERR_ARG, "NULL pointer");
+    auto mis = [](const void* p, unsigned a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; };
+    if (n_u > 0 && (mis(samples, 16) || mis(psi, 16) || mis(eloc, 16) || mis(counts, 8)))
+        return bfail(B, QC_ERR_ARG, "device arrays must be 16-byte aligned (counts: 8)");
+    BatchInput& I = B->in[mol];
+    I.samples = samples;
+    I.counts = counts;
+    I.psi = psi;
+    I.n_u = n_u;
+    I.eloc = eloc;
+    B->dirty = true;
+    drop_graph(B);
+    return QC_OK;
+}
+
+qc_status qc_batch_set_config(qc_batch* B, int unroll, int warps, int units_per_cta) {
+    if (!B) return QC_ERR_ARG;
+    if (unroll != 0 && unroll != 2 && unroll != 4) return bfail(B, QC_ERR_ARG, "unroll: 0, 2 or 4");
+    if (warps < 0 || warps > qc::kFilteredMaxWarps) return bfail(B, QC_ERR_ARG, "warps: 0..20");
+    if (units_per_cta < 0 || units_per_cta > 1024) return bfail(B, QC_ERR_ARG, "units_per_cta: 0..1024");
+    B->unroll = unroll ? unroll : 4;
+    B->warps = warps;
+    B->units_per_cta = units_per_cta ? units_per_cta : 8;
+    B->dirty = true;
+    drop_graph(B);
+    return QC_OK;
+}
+
+qc_status qc_batch_eval(qc_batch* B, qc_eloc_summary* sums, void* stream) {
+    if (!B) return QC_ERR_ARG;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != B->device) return bfail(B, QC_ERR_ARG, "batch belongs to another device");
+    if (B->dirty) {
+        qc_status st = prepare(B);
+        if (st != QC_OK) return st;
+    }
+    qc_status st = enqueue(B, sums, static_cast<cudaStream_t>(stream), true);
+    B->timed = (st == QC_OK);
+    return st;
+}
+
+qc_status qc_batch_graph_launch(qc_batch* B, qc_eloc_summary* sums, void* stream) {
+    if (!B) return QC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!s) return bfail(B, QC_ERR_ARG, "graph capture needs a non-default stream");
+    if (B->dirty) {
+        drop_graph(B);
+        qc_status st = prepare(B);
+        if (st != QC_OK) return st;
+    }
+    if (!B->exec || B->graph_sums != sums) {
+        drop_graph(B);
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return bcuda(B, e, "cudaStreamBeginCapture");
+        qc_status st = enqueue(B, sums, s, false);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(s, &g);
+        if (st != QC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return bcuda(B, e, "cudaStreamEndCapture");
+        B->graph = g;
+        e = cudaGraphInstantiate(&B->exec, g, 0);
+        if (e != cudaSuccess) {
+            drop_graph(B);
+            return bcuda(B, e, "cudaGraphInstantiate");
+        }
+        B->graph_sums = sums;
+    }
+    cudaError_t e = cudaGraphLaunch(B->exec, s);
+    if (e != cudaSuccess) return bcuda(B, e, "cudaGraphLaunch");
+    B->timed = false;
+    return QC_OK;
+}
+
+qc_status qc_batch_timings(qc_batch* B, float* ms3) {
+    if (!B || !ms3) return QC_ERR_ARG;
+    if (!B->timed) return bfail(B, QC_ERR_ARG, "no eager evaluation to time");
+    cudaError_t e = cudaEventSynchronize(B->ev[3]);
+    if (e != cudaSuccess) return bcuda(B, e, "cudaEventSynchronize");
+    for (int i = 0; i < 3; ++i) {
+        e = cudaEventElapsedTime(&ms3[i], B->ev[i], B->ev[i + 1]);
+        if (e != cudaSuccess) return bcuda(B, e, "cudaEventElapsedTime");
+    }
+    return QC_OK;
+}
+
+qc_status qc_batch_config(const qc_batch* B, int64_t* cfg6) {
+    if (!B || !cfg6) return QC_ERR_ARG;
+    cfg6[0] = B->unroll;
+    cfg6[1] = B->warps_used;
+    cfg6[2] = B->units_per_cta;
+    cfg6[3] = B->grid;
+    cfg6[4] = B->n_units;
+    cfg6[5] = static_cast<int64_t>(B->smem);
+    return QC_OK;
+}
+
+// Time every candidate shape on this batch (eager evaluations on `stream`, main kernel
+// only, best of `iters`) and keep the fastest.  best3 (optional): {unroll, warps, units_per_cta}.
+qc_status qc_batch_autotune(qc_batch* B, void* stream, int iters, int64_t* best3) {
+    if (!B) return QC_ERR_ARG;
+    if (iters < 1) iters = 1;
+    const int warps_c[] = {8, 12, 16, 20};
+    const int units_c[] = {4, 8, 16};
+    const int unroll_c[] = {2, 4};
+    float best = 3.0e38f;
+    int bu = 4, bw = 0, bp = 8;
+    for (int ur : unroll_c)
+        for (int w : warps_c)
+            for (int up : units_c) {
+                qc_status st = qc_batch_set_config(B, ur, w, up);
+                if (st != QC_OK) return st;
+                st = prepare(B);
+                if (st == QC_ERR_CAPACITY) continue;
+                if (st != QC_OK) return st;
+                if (B->warps_used != w) continue;  // shape clipped by shared memory: tried already
+                float t_best = 3.0e38f;
+                for (int it = 0; it < iters + 1; ++it) {
+                    st = enqueue(B, nullptr, static_cast<cudaStream_t>(stream), true);
+                    if (st != QC_OK) return st;
+                    float ms3[3];
+                    B->timed = true;
+                    st = qc_batch_timings(B, ms3);
+                    if (st != QC_OK) return st;
+                    if (it > 0) t_best = std::min(t_best, ms3[1]);
+                }
+                if (t_best < best) {
+                    best = t_best;
+                    bu = ur;
+                    bw = w;
+                    bp = up;
+                }
+            }
+    qc_status st = qc_batch_set_config(B, bu, bw, bp);
+    if (st != QC_OK) return st;
+    st = prepare(B);
+    if (st != QC_OK) return st;
+    if (best3) {
+        best3[0] = bu;
+        best3[1] = bw;
+        best3[2] = bp;
+    }
+    return QC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// qc_batch_kernels.cu -- many molecules in one launch (sm_103a): batched table build,
+// the persistent multi-molecule local-energy kernel, and the batched reduction.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qc_device.cuh"
+
+namespace qc {
+
+// Every molecule of a batch: thread -> (molecule, row) through the prefix of table sizes.
+__global__ void __launch_bounds__(256) build_batch_kernel(const MolParams* __restrict__ mols,
+                                                          const MolWork* __restrict__ work,
+                                                          const long long* __restrict__ key_off,
+                                                          int n_mol, long long n_keys) {
+    const long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= n_keys) return;
+    int lo = 0, hi = n_mol;  // largest m with key_off[m] <= g
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (key_off[mid] <= g) lo = mid; else hi = mid;
+    }
+    const MolParams& P = mols[lo];
+    const MolWork& W = work[lo];
+    build_one(P.tp, P.sp.n_orb, P.sp.na, P.sp.nb, P.ep.T, W.slots, W.filter, W.aset, W.bset, W.ctr,
+              g - key_off[lo]);
+}
+
+// batch: blockIdx.y is the molecule
+__global__ void __launch_bounds__(kRedThreads) reduce_batch_pass1(const MolParams* __restrict__ mols,
+                                                                  const MolWork* __restrict__ work) {
+    reduce_pass1_body(mols[blockIdx.y].ep, work[blockIdx.y].part, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kRedThreads) reduce_batch_pass2(const MolParams* __restrict__ mols,
+                                                                  const MolWork* __restrict__ work) {
+    const MolParams& P = mols[blockIdx.y];
+    reduce_pass2_body(P.ep, work[blockIdx.y].part, static_cast<qc_eloc_summary*>(work[blockIdx.y].sum),
+                      P.sp.pairs, blockIdx.x, gridDim.x);
+}
+
+// K4: many molecules in one persistent launch.  CTAs take work units (a block of samples
+// of one molecule) from a global counter, longest units first (the host orders them by
+// estimated cost).  For each unit the CTA loads that molecule's parameters and Bloom
+// filter into shared memory and rebuilds the CTA tables; its warps then run the unit's
+// samples with the same per-sample code as the single-molecule kernel.
+template <int PREC, int U>
+__global__ void __launch_bounds__(640) eloc_batch_kernel(const __grid_constant__ BatchParams bp) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ MolParams mp;
+    __shared__ int unit_id;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + kOffBar);
+    uint32_t* filt = reinterpret_cast<uint32_t*>(smem + kOffVar);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned char* wl = smem + kOffVar + bp.filter_bytes + static_cast<size_t>(warp) * bp.warp_stride;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    while (true) {
+        if (threadIdx.x == 0) unit_id = static_cast<int>(atomicAdd(bp.counter, 1u));
+        __syncthreads();
+        const int u = unit_id;
+        if (u >= bp.n_units) break;
+        const WorkUnit wu = bp.units[u];
+        const unsigned* src = reinterpret_cast<const unsigned*>(bp.mols + wu.mol);
+        unsigned* dst = reinterpret_cast<unsigned*>(&mp);
+        for (int t = threadIdx.x; t < static_cast<int>(sizeof(MolParams) / 4); t += blockDim.x) dst[t] = src[t];
+        __syncthreads();
+        const unsigned fbytes = 4u << mp.tp.fw;
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(bar, fbytes);
+            constexpr unsigned kChunk = 32768;
+            for (unsigned off = 0; off < fbytes; off += kChunk) {
+                const unsigned n = (fbytes - off < kChunk) ? (fbytes - off) : kChunk;
+                bulk_g2s(reinterpret_cast<unsigned char*>(filt) + off,
+                         reinterpret_cast<const unsigned char*>(mp.tp.filter) + off, n, bar);
+            }
+        }
+        fill_cta_tables(mp.sp, mp.ep.T, smem);
+        bool ready = false;
+        for (unsigned it = 0; it < kWaitLimit; ++it) {
+            if (mbar_try_wait(bar, phase)) {
+                ready = true;
+                break;
+            }
+        }
+        if (!__syncthreads_and(ready ? 1 : 0)) {
+            // the copy did not land in time: report, one more bounded wait, leave together
+            if (threadIdx.x == 0) atomicOr(&mp.ep.ctr->flags, QC_FLAG_TIMEOUT);
+            if (!ready)
+                for (unsigned it = 0; it < kWaitLimit; ++it)
+                    if (mbar_try_wait(bar, phase)) break;
+            return;
+        }
+        phase ^= 1u;
+        for (long long s = wu.s0 + warp; s < wu.s1; s += nw)
+            run_sample<PREC, U, true>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt);
+        __syncthreads();  // every warp done before the next unit replaces parameters and filter
+    }
+}
+
+size_t batch_warp_bytes(const SysParams& sp) { return main_warp_bytes(sp, true); }
+
+cudaError_t launch_build_batch(const MolParams* mols, const MolWork* work, const long long* key_off,
+                               int n_mol, long long n_keys, cudaStream_t s) {
+    if (n_keys <= 0) return cudaSuccess;
+    build_batch_kernel<<<static_cast<unsigned>((n_keys + 255) / 256), 256, 0, s>>>(mols, work, key_off, n_mol,
+                                                                                    n_keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_batch(const MolParams* mols, const MolWork* work, int n_mol, cudaStream_t s) {
+    const dim3 grid(kBatchRedBlocks, n_mol);
+    reduce_batch_pass1<<<grid, kRedThreads, 0, s>>>(mols, work);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_batch_pass2<<<grid, kRedThreads, 0, s>>>(mols, work);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static const void* batch_kernel_ptr(int unroll) {
+    if (unroll == 2) return (const void*)eloc_batch_kernel<PREC, 2>;
+    return (const void*)eloc_batch_kernel<PREC, 4>;
+}
+
+cudaError_t launch_eloc_batch(const BatchParams& bp, int precision, int unroll, int grid, int warps,
+                              size_t smem, cudaStream_t s) {
+    const dim3 g(grid), b(32 * warps);
+    if (precision == QC_FP64) {
+        if (unroll == 2) eloc_batch_kernel<QC_FP64, 2><<<g, b, smem, s>>>(bp);
+        else eloc_batch_kernel<QC_FP64, 4><<<g, b, smem, s>>>(bp);
+    } else {
+        if (unroll == 2) eloc_batch_kernel<QC_FP32_COMP, 2><<<g, b, smem, s>>>(bp);
+        else eloc_batch_kernel<QC_FP32_COMP, 4><<<g, b, smem, s>>>(bp);
+    }
+    return cudaGetLastError();
+}
+
+int max_active_batch(int precision, int unroll, int threads, size_t smem) {
+    const void* f = precision == QC_FP64 ? batch_kernel_ptr<QC_FP64>(unroll) : batch_kernel_ptr<QC_FP32_COMP>(unroll);
+    int n = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) == cudaSuccess ? n : 0;
+}
+
+// Dynamic shared memory of the batch kernels: the opt-in limit less their static share.
+cudaError_t prepare_batch_kernels(size_t max_smem, size_t* dyn_limit) {
+    cudaError_t e = cudaSuccess;
+    size_t lim = max_smem;
+    for (int prec = 0; prec < 2; ++prec)
+        for (int unroll : {2, 4}) {
+            const void* f = prec == QC_FP64 ? batch_kernel_ptr<QC_FP64>(unroll) : batch_kernel_ptr<QC_FP32_COMP>(unroll);
+            cudaFuncAttributes a{};
+            cudaError_t r = cudaFuncGetAttributes(&a, f);
+            if (r != cudaSuccess) { e = r; continue; }
+            const size_t dyn = max_smem - a.sharedSizeBytes;
+            if (dyn < lim) lim = dyn;
+            r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+            if (r != cudaSuccess) e = r;
+        }
+    if (dyn_limit) *dyn_limit = lim;
+    return e;
+}
+
+}  // namespace qc

@@ -1,0 +1,1077 @@
+// qc_device.cuh -- device code shared by the sm_103a kernels of libqc_eloc.
+//
+// The method (arxiv 2506.23809, Sec. III-B, Eq. 5 and Alg. 3): for every unique sample x,
+// E_loc(x) = <x|H|x> + sum over single and double excitations x' of x of
+// <x|H|x'> psi(x')/psi(x), with H of Eq. 2 and, in sample-space mode, x' restricted to the
+// table of unique samples (the lookup table of Sec. IV-C-4).  Alg. 3 spreads the sum as
+// processes -> threads -> SIMD lanes; here it is grid -> warp per sample -> lanes over
+// excitations.  Its three SIMD devices map as follows:
+//   * qubit packing    -> a key is one 128-bit word pair (ulonglong2 loads);
+//   * branch elimination -> excitations are enumerated class by class (singles, same-spin
+//     and opposite-spin doubles) as products of two short per-sample lists, so no lane
+//     ever tests the excitation degree;
+//   * SIMD parity      -> the fermionic phase is a sum of four prefix popcounts.
+//
+// Lookup: every key k has a linear hash H(k) = XOR of T[b] over its set bits b, so the hash
+// of x' = x ^ {i, j, a, b} is H(x) ^ T[i] ^ T[j] ^ T[a] ^ T[b] -- four XORs, no key walk.
+// The low 32 bits of H index a blocked Bloom filter (two bits in one 32-bit word) that
+// every CTA holds in shared memory (loaded by a 1-D bulk async copy); lanes whose x' passes
+// are compacted into a per-warp queue and resolved 32 at a time against an open-addressing
+// bucket table in global memory (L2 resident), keyed by the high 32 bits of H and
+// checked against the stored 128-bit key.  Only then are the matrix element (Slater-Condon)
+// and psi(x') read.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qc_internal.h"
+#include "qc_eloc.h"
+
+namespace qc {
+
+#define QC_FULLMASK 0xffffffffu
+
+// ------------------------------------------------------------------------------------
+// small device helpers
+// ------------------------------------------------------------------------------------
+// Exclusive prefix parity of a 128-bit occupation: bit k is the parity of the number of
+// occupied spin orbitals below k (doubling prefix XOR within each word, then the low
+// word's total parity carried into the high word).
+__device__ __forceinline__ ulonglong2 prefix_parity(ulonglong2 x) {
+    unsigned long long lo = x.x, hi = x.y;
+#pragma unroll
+    for (int sh = 1; sh < 64; sh <<= 1) {
+        lo ^= lo << sh;
+        hi ^= hi << sh;
+    }
+    ulonglong2 p;
+    p.x = lo ^ x.x;
+    p.y = (hi ^ x.y) ^ ((__popcll(x.x) & 1) ? ~0ULL : 0ULL);
+    return p;
+}
+
+__device__ __forceinline__ int pbit(ulonglong2 p, int k) {
+    const unsigned long long w = (k < 64) ? p.x : p.y;
+    return static_cast<int>((w >> (k & 63)) & 1ULL);
+}
+
+__device__ __forceinline__ void flip(ulonglong2& x, int k) {
+    const unsigned long long bit = 1ULL << (k & 63);
+    x.x ^= (k < 64) ? bit : 0ULL;
+    x.y ^= (k < 64) ? 0ULL : bit;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(QC_FULLMASK, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(QC_FULLMASK, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_xor_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v ^= __shfl_xor_sync(QC_FULLMASK, v, o);
+    return v;
+}
+
+// Knuth's TwoSum accumulation in FP32: (s, c) holds the running sum and its error.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+    float t = __fadd_rn(s, x);
+    float bp = __fsub_rn(t, s);
+    float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    s = t;
+    c = __fadd_rn(c, e);
+}
+
+// ------------------------------------------------------------------------------------
+// mbarrier + 1-D bulk async copy (global -> shared), bounded waits
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+constexpr unsigned kWaitLimit = 1u << 24;  // bounded spin on the filter copy
+
+// ------------------------------------------------------------------------------------
+// lookup in the bucket table
+// ------------------------------------------------------------------------------------
+// Bits of the 64-bit linear key hash H:  0..31 feed the shared-memory Bloom filter
+// (bits 0-4 and 27-31 pick the two bits, bits 5.. the word); 32..63 give the bucket
+// (low bits) and the fingerprint stored with each entry.  A random GF(2)-linear map
+// sends any two distinct keys to independent uniform hashes, so the bucket load and the
+// filter false-positive rate are those of a 2-universal hash family.
+__device__ __forceinline__ unsigned bucket_of(unsigned long long h) { return static_cast<unsigned>(h >> 32); }
+
+// Returns the table row of key, or -1.  Buckets hold two 64-bit entries
+// (fingerprint << 32 | row + 1); an empty entry ends the probe sequence.
+__device__ __forceinline__ long long table_find(const TableParams& tp, ulonglong2 key,
+                                                unsigned long long h) {
+    const unsigned fp = bucket_of(h);
+    unsigned b = fp & tp.nb_mask;
+    const ulonglong2* buckets = reinterpret_cast<const ulonglong2*>(tp.slots);
+    for (unsigned it = 0; it <= tp.nb_mask; ++it) {
+        const ulonglong2 e = __ldg(buckets + b);
+        if (e.x == 0ULL) return -1;
+        if (static_cast<unsigned>(e.x >> 32) == fp) {
+            const long long r = static_cast<long long>(static_cast<unsigned>(e.x)) - 1;
+            const ulonglong2 k = __ldg(tp.keys + r);
+            if (k.x == key.x && k.y == key.y) return r;
+        }
+        if (e.y == 0ULL) return -1;
+        if (static_cast<unsigned>(e.y >> 32) == fp) {
+            const long long r = static_cast<long long>(static_cast<unsigned>(e.y)) - 1;
+            const ulonglong2 k = __ldg(tp.keys + r);
+            if (k.x == key.x && k.y == key.y) return r;
+        }
+        b = (b + 1u) & tp.nb_mask;
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------------------------------
+// K0: table build (hash index + Bloom filter + validation)
+// ------------------------------------------------------------------------------------
+// Filter bits of a 32-bit hash g: word (g >> 5) & wmask, bits g & 31, (g >> 27) and
+// (g >> 22) & 31 of that word.
+__device__ __forceinline__ unsigned filter_bits(unsigned g) {
+    return (1u << (g & 31u)) | (1u << (g >> 27)) | (1u << ((g >> 22) & 31u));
+}
+
+// Insert a spin string into an exact set (open addressing on the high hash bits).
+__device__ __forceinline__ void set_insert(unsigned long long* set, unsigned mask, unsigned long long v,
+                                           unsigned long long h) {
+    unsigned b = static_cast<unsigned>(h >> 32) & mask;
+    for (unsigned it = 0; it <= mask; ++it) {
+        const unsigned long long old = atomicCAS(set + b, 0ULL, v);
+        if (old == 0ULL || old == v) return;
+        b = (b + 1u) & mask;
+    }
+}
+
+__device__ __forceinline__ bool set_contains(const unsigned long long* __restrict__ set, unsigned mask,
+                                             unsigned long long v, unsigned long long h) {
+    unsigned b = static_cast<unsigned>(h >> 32) & mask;
+    for (unsigned it = 0; it <= mask; ++it) {
+        const unsigned long long e = __ldg(set + b);
+        if (e == v) return true;
+        if (e == 0ULL) return false;
+        b = (b + 1u) & mask;
+    }
+    return false;
+}
+
+// Insert row r of the table: validation, filter bits, spin-string sets, bucket entry.
+__device__ __forceinline__ void build_one(const TableParams& tp, int n_orb, int na, int nb,
+                                          const unsigned long long* __restrict__ T,
+                                          unsigned long long* slots, uint32_t* filter,
+                                          unsigned long long* aset, unsigned long long* bset,
+                                          Counters* ctr, long long r) {
+    const ulonglong2 key = tp.keys[r];
+    unsigned flags = 0;
+    if (r > 0) {
+        const ulonglong2 prev = tp.keys[r - 1];
+        const bool eq = prev.x == key.x && prev.y == key.y;
+        const bool gt = (prev.y > key.y) || (prev.y == key.y && prev.x > key.x);
+        if (eq) flags |= QC_FLAG_DUP;
+        if (gt) flags |= QC_FLAG_UNSORTED;
+    }
+    const unsigned long long even = 0x5555555555555555ULL;
+    const int ea = __popcll(key.x & even) + __popcll(key.y & even);
+    const int eb = __popcll(key.x & ~even) + __popcll(key.y & ~even);
+    bool high = false;
+    if (n_orb < 128) {
+        if (n_orb <= 64) high = (key.y != 0ULL) || (n_orb < 64 && (key.x >> n_orb) != 0ULL);
+        else high = (key.y >> (n_orb - 64)) != 0ULL;
+    }
+    if (ea != na || eb != nb || high) flags |= QC_FLAG_NELEC;
+
+    // key hash, and its alpha / beta parts with the spatial strings they belong to
+    unsigned long long ha = 0, hb = 0, sa = 0, sb = 0;
+    for (unsigned long long w = key.x; w; w &= w - 1ULL) {
+        const int bit = __ffsll(w) - 1;
+        if (bit & 1) { hb ^= __ldg(T + bit); sb |= 1ULL << (bit >> 1); }
+        else { ha ^= __ldg(T + bit); sa |= 1ULL << (bit >> 1); }
+    }
+    for (unsigned long long w = key.y; w; w &= w - 1ULL) {
+        const int bit = __ffsll(w) - 1;
+        if (bit & 1) { hb ^= __ldg(T + 64 + bit); sb |= 1ULL << ((64 + bit) >> 1); }
+        else { ha ^= __ldg(T + 64 + bit); sa |= 1ULL << ((64 + bit) >> 1); }
+    }
+    const unsigned long long h = ha ^ hb;
+
+    if (tp.filter != nullptr) {
+        const unsigned g = static_cast<unsigned>(h);
+        const unsigned wmask = (1u << tp.fw) - 1u;
+        atomicOr(filter + ((g >> 5) & wmask), filter_bits(g));
+    }
+    if (aset != nullptr && sa != 0ULL) set_insert(aset, tp.set_mask, sa, ha);
+    if (bset != nullptr && sb != 0ULL) set_insert(bset, tp.set_mask, sb, hb);
+    const unsigned fp = bucket_of(h);
+    const unsigned long long entry =
+        (static_cast<unsigned long long>(fp) << 32) | static_cast<unsigned long long>(static_cast<unsigned>(r + 1));
+    unsigned b = fp & tp.nb_mask;
+    bool placed = false;
+    for (unsigned it = 0; it <= tp.nb_mask && !placed; ++it) {
+        if (atomicCAS(slots + 2 * b, 0ULL, entry) == 0ULL) { placed = true; break; }
+        if (atomicCAS(slots + 2 * b + 1, 0ULL, entry) == 0ULL) { placed = true; break; }
+        b = (b + 1u) & tp.nb_mask;
+    }
+    if (!placed) flags |= QC_FLAG_TABLE_FULL;
+    if (flags) atomicOr(&ctr->flags, flags);
+}
+
+
+
+// ------------------------------------------------------------------------------------
+// shared-memory layout of the main kernels
+// ------------------------------------------------------------------------------------
+//   [kOffBar]   mbarrier of the filter copy
+//   [kOffT]     T[128]: the linear key hash, 64-bit entries
+//   [kOffLut]   colex pair table: p = C(hi, 2) + lo  ->  lo | hi << 8   (p < 2016)
+//   [kOffDiv]   single-excitation index -> occupied position, per spin (u8, < 1024 each)
+//   [kOffVar]   filter words (filtered kernel only), then one region per warp:
+//               occA[64] virA[64] occB[64] virB[64] (u8) | candidate queue (u32) |
+//               single-hit and double-hit queues (uint2) | hash lists (u32, filtered only)
+constexpr size_t kOffBar = 0;
+constexpr size_t kOffT = 16;
+constexpr size_t kOffLut = kOffT + 128 * 8;
+constexpr size_t kOffDiv = kOffLut + kPairLut * 2;
+constexpr size_t kOffVar = ((kOffDiv + 2 * 1024 + 127) / 128) * 128;
+
+__host__ __device__ inline size_t list_words(const SysParams& sp) {
+    return static_cast<size_t>(1 + sp.nsa + sp.nsb + sp.npoa + sp.npva + sp.npob + sp.npvb);
+}
+
+
+// CTA-wide tables: T, pair LUT, single-excitation division tables
+__device__ inline void fill_cta_tables(const SysParams& sp, const unsigned long long* __restrict__ Tg,
+                                unsigned char* smem) {
+    unsigned long long* T64 = reinterpret_cast<unsigned long long*>(smem + kOffT);
+    unsigned short* lut = reinterpret_cast<unsigned short*>(smem + kOffLut);
+    unsigned char* divA = smem + kOffDiv;
+    unsigned char* divB = divA + 1024;
+    for (int t = threadIdx.x; t < 128; t += blockDim.x) T64[t] = Tg[t];
+    for (int p = threadIdx.x; p < kPairLut; p += blockDim.x) {
+        int hi = static_cast<int>((1.0f + sqrtf(1.0f + 8.0f * static_cast<float>(p))) * 0.5f);
+        while (hi * (hi - 1) / 2 > p) --hi;
+        while ((hi + 1) * hi / 2 <= p) ++hi;
+        const int lo = p - hi * (hi - 1) / 2;
+        lut[p] = static_cast<unsigned short>(lo | (hi << 8));
+    }
+    for (int t = threadIdx.x; t < sp.nsa; t += blockDim.x) divA[t] = static_cast<unsigned char>(t / sp.va);
+    for (int t = threadIdx.x; t < sp.nsb; t += blockDim.x) divB[t] = static_cast<unsigned char>(t / sp.vb);
+}
+
+// ------------------------------------------------------------------------------------
+// accumulators and the three batch stages of candidate resolution
+// ------------------------------------------------------------------------------------
+struct Acc {
+    double re, im;         // FP64 accumulation of sum H psi(x')
+    float sr, cr, si, ci;  // FP32 TwoSum accumulation of sum H psi(x')/psi(x)
+    unsigned hits;
+    unsigned long long rowsum;
+    long long signsum;
+    unsigned long long missing;
+};
+
+// Add one hit: <x|H|x'> (phase included) times psi(x') [FP64], or times psi(x')/psi(x)
+// [FP32, compensated], plus the diagnostics of the exported phase convention.
+__device__ __forceinline__ ulonglong2 excite(unsigned orbs, ulonglong2 x, unsigned long long hx,
+                                             const unsigned long long* __restrict__ T64,
+                                             unsigned long long& h) {
+    const int i = orbs & 255u, a = (orbs >> 8) & 255u, j = (orbs >> 16) & 255u, b = orbs >> 24;
+    ulonglong2 xp = x;
+    flip(xp, i);
+    flip(xp, a);
+    h = hx ^ T64[i] ^ T64[a];
+    if (j != 255) {
+        flip(xp, j);
+        flip(xp, b);
+        h ^= T64[j] ^ T64[b];
+    }
+    return xp;
+}
+
+// Stage 1 -- probe the home bucket of x' = x with orbitals (i, j) emptied and (a, b)
+// filled.  A bucket with a free entry holds every key whose home it is (a key only moves
+// on when its home bucket is full), so its content does not depend on the order of
+// insertion: its fingerprint-matching entry (at most one) is returned as a candidate row,
+// to be checked against the stored key in stage 2 beside the loads of psi and the
+// integrals.  A full home bucket takes the exact probe walk instead, so the outcome of
+// this stage -- and with it the order of accumulation -- is the same on every run.
+__device__ __forceinline__ long long probe(unsigned orbs, ulonglong2 x, unsigned long long hx,
+                                          const TableParams& tp,
+                                          const unsigned long long* __restrict__ T64) {
+    unsigned long long h;
+    const ulonglong2 xp = excite(orbs, x, hx, T64, h);
+    const unsigned fp = bucket_of(h);
+    const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(tp.slots) + (fp & tp.nb_mask));
+    if (e.x != 0ULL && e.y != 0ULL) return table_find(tp, xp, h);
+    if (e.x != 0ULL && static_cast<unsigned>(e.x >> 32) == fp)
+        return static_cast<long long>(static_cast<unsigned>(e.x)) - 1;
+    return -1;
+}
+
+template <int PREC>
+__device__ __forceinline__ void add_hit(double h64, float h32, long long row, bool sneg, double2 pp,
+                                        float2 ip32, Acc& acc) {
+    if (PREC == QC_FP64) {
+        acc.re = fma(h64, pp.x, acc.re);
+        acc.im = fma(h64, pp.y, acc.im);
+    } else {
+        const float px = static_cast<float>(pp.x), py = static_cast<float>(pp.y);
+        const float rr = __fsub_rn(__fmul_rn(px, ip32.x), __fmul_rn(py, ip32.y));
+        const float ri = __fadd_rn(__fmul_rn(px, ip32.y), __fmul_rn(py, ip32.x));
+        two_sum_acc(acc.sr, acc.cr, __fmul_rn(h32, rr));
+        two_sum_acc(acc.si, acc.ci, __fmul_rn(h32, ri));
+    }
+    acc.hits++;
+    acc.rowsum += static_cast<unsigned long long>(row + 1);
+    acc.signsum += sneg ? -(row + 1) : (row + 1);
+}
+
+// Stage 2 common part: issue the loads of the stored key and psi of a stage-1 row, let
+// `element` load the integrals meanwhile, then confirm the key (exact walk on a
+// fingerprint collision) and add the hit.
+template <int PREC, typename Element>
+__device__ __forceinline__ void verify_and_add(uint2 e, ulonglong2 x, unsigned long long hx,
+                                               const TableParams& tp, int mode,
+                                               const unsigned long long* __restrict__ T64,
+                                               float2 ip32, Acc& acc, Element element) {
+    unsigned long long h;
+    const ulonglong2 xp = excite(e.x, x, hx, T64, h);
+    const ulonglong2 key = __ldg(tp.keys + e.y);
+    double2 pp = __ldg(tp.psi + e.y);
+    double h64 = 0.0;
+    float h32 = 0.f;
+    bool sneg = false;
+    element(h64, h32, sneg);
+    long long row = e.y;
+    if (key.x != xp.x || key.y != xp.y) {
+        row = table_find(tp, xp, h);
+        if (row >= 0) pp = __ldg(tp.psi + row);
+        else if (mode == QC_FULL) acc.missing++;
+    }
+    if (row >= 0) add_hit<PREC>(h64, h32, row, sneg, pp, ip32, acc);
+}
+
+// Stage 1 -- decode a candidate (class, u, w) into the spin orbitals it empties (i, j)
+// and fills (a, b); j = b = 255 for singles.  Classes: 0 alpha single (w), 1 beta single
+// (w), 2 alpha-alpha double (u: occupied pair, w: empty pair), 3 beta-beta double,
+// 4 alpha-beta double (u: alpha single, w: beta single).  Same-spin doubles come out with
+// i < j and a < b.  Single indices go through IA / IB (the compacted single lists of the
+// filtered kernel) when given.  Returns the packed orbitals i | a << 8 | j << 16 | b << 24.
+__device__ __forceinline__ unsigned decode(unsigned code, const SysParams& sp,
+                                           const unsigned char* __restrict__ wl,
+                                           const unsigned char* __restrict__ smem,
+                                           const unsigned short* __restrict__ IA,
+                                           const unsigned short* __restrict__ IB) {
+    const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
+    const unsigned char* divA = smem + kOffDiv;
+    const unsigned char* divB = divA + 1024;
+    const unsigned char* occA = wl;
+    const unsigned char* virA = wl + 64;
+    const unsigned char* occB = wl + 128;
+    const unsigned char* virB = wl + 192;
+    const unsigned cls = code >> 24;
+    int u = static_cast<int>((code >> 12) & 4095u);
+    int w = static_cast<int>(code & 4095u);
+    // singles lists may be compacted by the spin-string prefilter: map back
+    if (IA != nullptr) {
+        if (cls == 4u) { u = IA[u]; w = IB[w]; }
+        else if (cls == 0u) w = IA[w];
+        else if (cls == 1u) w = IB[w];
+    }
+    unsigned i, a, j = 255u, b = 255u;
+    if (cls == 4u) {
+        const int io = divA[u], jo = divB[w];
+        i = 2u * occA[io];
+        a = 2u * virA[u - io * sp.va];
+        j = 2u * occB[jo] + 1u;
+        b = 2u * virB[w - jo * sp.vb] + 1u;
+    } else if (cls >= 2u) {
+        const unsigned po = lut[u], pv = lut[w];
+        const unsigned char* occ = cls == 2u ? occA : occB;
+        const unsigned char* vir = cls == 2u ? virA : virB;
+        const unsigned s = cls - 2u;
+        i = 2u * occ[po & 255u] + s;
+        j = 2u * occ[po >> 8] + s;
+        a = 2u * vir[pv & 255u] + s;
+        b = 2u * vir[pv >> 8] + s;
+    } else {
+        const unsigned char* dv = cls == 0u ? divA : divB;
+        const unsigned char* occ = cls == 0u ? occA : occB;
+        const unsigned char* vir = cls == 0u ? virA : virB;
+        const int vv = cls == 0u ? sp.va : sp.vb;
+        const int io = dv[w];
+        i = 2u * occ[io] + cls;
+        a = 2u * vir[w - io * vv] + cls;
+    }
+    return i | (a << 8) | (j << 16) | (b << 24);
+}
+
+// Stage 2 -- single i -> a (Slater-Condon): h_ai + sum_{k occ} (ai|kk) - sum_{k occ, same
+// spin} (ak|ki), phase <x'| a+_a a_i |x> = (-1)^{P(i) + P(a) + [i < a]}, P = occupied below
+// (read from the prefix-parity mask px).
+template <int PREC>
+__device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 px, const SysParams& sp,
+                                               const unsigned char* __restrict__ wl, double& h64,
+                                               float& h32, bool& sneg) {
+    const int i = orbs & 255u, a = (orbs >> 8) & 255u;
+    const int K = sp.K, ki = i >> 1, ka = a >> 1, s = i & 1;
+    const size_t rowk = (static_cast<size_t>(ka) * K + ki) * K;
+    const unsigned char* occA = wl;
+    const unsigned char* occB = wl + 128;
+    const bool neg = (pbit(px, i) ^ pbit(px, a) ^ (i < a ? 1 : 0)) != 0;
+    // sum over the occupied orbitals of both spins, four independent partial sums
+    if (PREC == QC_FP64) {
+        double f0 = sp.h[ka * K + ki], f1 = 0.0, f2 = 0.0, f3 = 0.0;
+        const double* jt = sp.Jt + rowk;
+        const double* xt = sp.Xt + rowk;
+        const unsigned char* occS = s == 0 ? occA : occB;
+        const int os = s == 0 ? sp.oa : sp.ob;
+        int q = 0;
+        for (; q + 1 < sp.oa; q += 2) { f0 += jt[occA[q]]; f1 += jt[occA[q + 1]]; }
+        if (q < sp.oa) f0 += jt[occA[q]];
+        for (q = 0; q + 1 < sp.ob; q += 2) { f2 += jt[occB[q]]; f3 += jt[occB[q + 1]]; }
+        if (q < sp.ob) f2 += jt[occB[q]];
+        double g0 = 0.0, g1 = 0.0;
+        for (q = 0; q + 1 < os; q += 2) { g0 += xt[occS[q]]; g1 += xt[occS[q + 1]]; }
+        if (q < os) g0 += xt[occS[q]];
+        const double f = ((f0 + f1) + (f2 + f3)) - (g0 + g1);
+        h64 = neg ? -f : f;
+    } else {
+        float f0 = sp.h32[ka * K + ki], f1 = 0.f, f2 = 0.f, f3 = 0.f;
+        const float* jt = sp.Jt32 + rowk;
+        const float* xt = sp.Xt32 + rowk;
+        const unsigned char* occS = s == 0 ? occA : occB;
+        const int os = s == 0 ? sp.oa : sp.ob;
+        int q = 0;
+        for (; q + 1 < sp.oa; q += 2) { f0 += jt[occA[q]]; f1 += jt[occA[q + 1]]; }
+        if (q < sp.oa) f0 += jt[occA[q]];
+        for (q = 0; q + 1 < sp.ob; q += 2) { f2 += jt[occB[q]]; f3 += jt[occB[q + 1]]; }
+        if (q < sp.ob) f2 += jt[occB[q]];
+        float g0 = 0.f, g1 = 0.f;
+        for (q = 0; q + 1 < os; q += 2) { g0 += xt[occS[q]]; g1 += xt[occS[q + 1]]; }
+        if (q < os) g0 += xt[occS[q]];
+        const float f = ((f0 + f1) + (f2 + f3)) - (g0 + g1);
+        h32 = neg ? -f : f;
+    }
+    sneg = neg;
+}
+
+// Stage 2 -- double (i, j) -> (a, b): <ab||ij> = (ai|bj) - (aj|bi) for equal spins,
+// (ai|bj) for alpha i, a and beta j, b; phase <x'| a+_a a+_b a_j a_i |x> =
+// (-1)^{P(i)+P(j)+P(a)+P(b) + [i<j]+[i<b]+[j<b]+[i<a]+[j<a]+[b<a]}.
+template <int PREC>
+__device__ __forceinline__ void double_element(unsigned orbs, ulonglong2 px, const SysParams& sp,
+                                               double& h64, float& h32, bool& sneg) {
+    const int i = orbs & 255u, a = (orbs >> 8) & 255u, j = (orbs >> 16) & 255u, b = orbs >> 24;
+    const int K = sp.K, ki = i >> 1, ka = a >> 1, kj = j >> 1, kb = b >> 1;
+    const size_t d = ((static_cast<size_t>(ka) * K + ki) * K + kb) * K + kj;  // (ai|bj)
+    const int par = (pbit(px, i) ^ pbit(px, j) ^ pbit(px, a) ^ pbit(px, b)) + (i < j) + (i < b) +
+                    (j < b) + (i < a) + (j < a) + (b < a);
+    const bool neg = (par & 1) != 0;
+    const bool same = (i & 1) == (j & 1);
+    if (PREC == QC_FP64) {
+        double e = sp.eri[d];
+        if (same) e -= sp.eri[((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki];  // (aj|bi)
+        h64 = neg ? -e : e;
+    } else {
+        float e = sp.eri32[d];
+        if (same) e -= sp.eri32[((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki];
+        h32 = neg ? -e : e;
+    }
+    // exported convention sorts the emptied and the filled pair
+    sneg = neg != ((((i > j) ? 1 : 0) + ((a > b) ? 1 : 0)) & 1);
+}
+
+// Per-sample set-up shared by both main kernels.  Returns false when x does not hold
+// na alpha and nb beta electrons below n_orb (then nothing is written to the lists).
+__device__ __forceinline__ bool sample_setup(const SysParams& sp, ulonglong2 x, int lane,
+                                             unsigned char* wl,
+                                             const unsigned long long* __restrict__ T64,
+                                             unsigned long long& hx, double& ediag,
+                                             unsigned long long& As, unsigned long long& Bs,
+                                             unsigned long long& hxa) {
+    unsigned char* occA = wl;
+    unsigned char* virA = wl + 64;
+    unsigned char* occB = wl + 128;
+    unsigned char* virB = wl + 192;
+    const unsigned long long even = 0x5555555555555555ULL;
+    const int ea = __popcll(x.x & even) + __popcll(x.y & even);
+    const int eb = __popcll(x.x & ~even) + __popcll(x.y & ~even);
+    bool high = false;
+    if (sp.n_orb < 128) {
+        if (sp.n_orb <= 64) high = (x.y != 0ULL) || (sp.n_orb < 64 && (x.x >> sp.n_orb) != 0ULL);
+        else high = (x.y >> (sp.n_orb - 64)) != 0ULL;
+    }
+    if (ea != sp.na || eb != sp.nb || high) return false;
+    // spatial occupation strings: lane l owns spatial orbitals l and l + 32
+    const unsigned alo = __ballot_sync(QC_FULLMASK, (x.x >> (2 * lane)) & 1ULL);
+    const unsigned ahi = __ballot_sync(QC_FULLMASK, (x.y >> (2 * lane)) & 1ULL);
+    const unsigned blo = __ballot_sync(QC_FULLMASK, (x.x >> (2 * lane + 1)) & 1ULL);
+    const unsigned bhi = __ballot_sync(QC_FULLMASK, (x.y >> (2 * lane + 1)) & 1ULL);
+    const unsigned long long A = static_cast<unsigned long long>(alo) |
+                                 (static_cast<unsigned long long>(ahi) << 32);
+    const unsigned long long B = static_cast<unsigned long long>(blo) |
+                                 (static_cast<unsigned long long>(bhi) << 32);
+    for (int k = lane; k < sp.K; k += 32) {
+        const unsigned long long lowm = (1ULL << k) - 1ULL;
+        const int ca = __popcll(A & lowm), cb = __popcll(B & lowm);
+        if ((A >> k) & 1ULL) occA[ca] = static_cast<unsigned char>(k);
+        else virA[k - ca] = static_cast<unsigned char>(k);
+        if ((B >> k) & 1ULL) occB[cb] = static_cast<unsigned char>(k);
+        else virB[k - cb] = static_cast<unsigned char>(k);
+    }
+    // linear hash of x: XOR of T over set bits (lane l: bits l, l+32, l+64, l+96)
+    unsigned long long hv = 0;
+    if ((x.x >> lane) & 1ULL) hv ^= T64[lane];
+    if ((x.x >> (lane + 32)) & 1ULL) hv ^= T64[lane + 32];
+    if ((x.y >> lane) & 1ULL) hv ^= T64[lane + 64];
+    if ((x.y >> (lane + 32)) & 1ULL) hv ^= T64[lane + 96];
+    hx = warp_xor_u64(hv);
+    hxa = warp_xor_u64((lane & 1) ? 0ULL : hv);  // even spin orbitals: the alpha part
+    As = A;
+    Bs = B;
+    __syncwarp();
+    // diagonal: sum_p h_pp + 1/2 sum_{p,q occ} [(pp|qq) - d(sp,sq) (pq|qp)]  (FP64)
+    const int K = sp.K;
+    double ed = 0.0;
+    for (int idx = lane; idx < sp.oa + sp.ob; idx += 32) {
+        const bool isA = idx < sp.oa;
+        const int k = isA ? occA[idx] : occB[idx - sp.oa];
+        double sj = 0.0, sx = 0.0;
+        for (int q = 0; q < sp.oa; ++q) {
+            const int l = occA[q];
+            sj += sp.J[k * K + l];
+            if (isA) sx += sp.X[k * K + l];
+        }
+        for (int q = 0; q < sp.ob; ++q) {
+            const int l = occB[q];
+            sj += sp.J[k * K + l];
+            if (!isA) sx += sp.X[k * K + l];
+        }
+        ed += sp.h[k * K + k] + 0.5 * (sj - sx);
+    }
+    ediag = warp_sum(ed) + sp.e_core;
+    return true;
+}
+
+// Per-sample finish: reduce the lane accumulators and write the outputs.
+template <int PREC>
+__device__ __forceinline__ void sample_finish(const EvalParams& ep, long long s, int lane,
+                                              double ediag, double2 psix, Acc& acc) {
+    double sre, sim;
+    if (PREC == QC_FP64) {
+        sre = warp_sum(acc.re);
+        sim = warp_sum(acc.im);
+    } else {
+        sre = warp_sum(static_cast<double>(acc.sr) + static_cast<double>(acc.cr));
+        sim = warp_sum(static_cast<double>(acc.si) + static_cast<double>(acc.ci));
+    }
+    const unsigned long long hits = warp_sum_u64(acc.hits);
+    const unsigned long long rows = warp_sum_u64(acc.rowsum);
+    const long long sgn = static_cast<long long>(warp_sum_u64(static_cast<unsigned long long>(acc.signsum)));
+    const unsigned long long miss = warp_sum_u64(acc.missing);
+    if (lane == 0) {
+        double2 e;
+        const double n2 = psix.x * psix.x + psix.y * psix.y;
+        unsigned flags = 0;
+        bool bad = false;
+        if (n2 == 0.0) {
+            flags |= QC_FLAG_ZERO_PSI;
+            bad = true;
+        }
+        if (miss) {
+            flags |= QC_FLAG_MISSING;
+            bad = true;
+        }
+        if (bad) {
+            e.x = __longlong_as_double(0x7ff8000000000000LL);
+            e.y = e.x;
+        } else if (PREC == QC_FP64) {
+            // sum H psi(x') / psi(x) = S conj(psi) / |psi|^2
+            const double inv = 1.0 / n2;
+            e.x = ediag + (sre * psix.x + sim * psix.y) * inv;
+            e.y = (sim * psix.x - sre * psix.y) * inv;
+        } else {
+            e.x = ediag + sre;
+            e.y = sim;
+        }
+        ep.eloc[s] = e;
+        if (ep.hit_count) ep.hit_count[s] = static_cast<uint32_t>(hits);
+        if (ep.hit_rowsum) ep.hit_rowsum[s] = rows;
+        if (ep.hit_signsum) ep.hit_signsum[s] = sgn;
+        if (hits) atomicAdd(&ep.ctr->hits, hits);
+        if (miss) atomicAdd(&ep.ctr->missing, miss);
+        if (bad) atomicAdd(&ep.ctr->bad, 1ULL);
+        if (flags) atomicOr(&ep.ctr->flags, flags);
+    }
+}
+
+__device__ __forceinline__ void invalid_sample(const EvalParams& ep, long long s, int lane) {
+    if (lane == 0) {
+        double2 e;
+        e.x = __longlong_as_double(0x7ff8000000000000LL);
+        e.y = e.x;
+        ep.eloc[s] = e;
+        if (ep.hit_count) ep.hit_count[s] = 0;
+        if (ep.hit_rowsum) ep.hit_rowsum[s] = 0;
+        if (ep.hit_signsum) ep.hit_signsum[s] = 0;
+        atomicAdd(&ep.ctr->bad, 1ULL);
+        atomicAdd(&ep.ctr->invalid, 1ULL);
+        atomicOr(&ep.ctr->flags, QC_FLAG_NELEC);
+    }
+}
+
+__device__ __forceinline__ float2 inv_psi32(double2 p) {
+    const double n2 = p.x * p.x + p.y * p.y;
+    const double inv = n2 > 0.0 ? 1.0 / n2 : 0.0;
+    return make_float2(static_cast<float>(p.x * inv), static_cast<float>(-p.y * inv));
+}
+
+// ------------------------------------------------------------------------------------
+// K2: the local-energy kernel
+// ------------------------------------------------------------------------------------
+// One warp per sample (persistent grid).  The five excitation classes are walked as
+// outer x inner products of per-sample hash lists by a flat state machine; each step
+// tests U x 32 excitations.  With FILTER, an excitation becomes a candidate only if its
+// two bits are set in the shared-memory Bloom filter; without it (accurate-energy mode,
+// or the unfiltered variant) every excitation is a candidate.  Candidates queue up per
+// warp and are resolved 32 at a time in three full-warp stages: probe the bucket table,
+// then compute the matrix elements of single hits and of double hits in separate
+// batches (so lanes of one batch follow the same path).  All three stages sit at one
+// place in the loop; the end of a sample flushes the partial batches through the same code.
+constexpr int kCandCap = 160;  // >= 31 + 32 * 4 (the largest U with a single flush site)
+constexpr size_t kWarpQueues = 4 * kCandCap + 2 * 64 * 8;  // candidate + two hit queues
+
+__host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filter) {
+    // hash lists (u32) and, for the two single lists, their compaction maps (u16)
+    const size_t lists = filter ? 4 * list_words(sp) + 2 * static_cast<size_t>(sp.nsa + sp.nsb) : 0;
+    return (256 + kWarpQueues + lists + 15) / 16 * 16;
+}
+
+
+
+// One sample, one warp: set-up, the filtered (or unfiltered) walk over its excitations,
+// resolution of the candidates and the per-sample outputs.  wl is the warp's region of
+// shared memory, filt the CTA's copy of the Bloom filter.
+template <int PREC, int U, bool FILTER>
+__device__ __forceinline__ void run_sample(const SysParams& sp, const TableParams& tp,
+                                           const EvalParams& ep, long long s, int lane,
+                                           unsigned char* smem, unsigned char* wl,
+                                           const uint32_t* filt) {
+    const unsigned long long* T64 = reinterpret_cast<const unsigned long long*>(smem + kOffT);
+    const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
+    uint32_t* q = reinterpret_cast<uint32_t*>(wl + 256);
+    uint2* sq = reinterpret_cast<uint2*>(wl + 256 + 4 * kCandCap);
+    uint2* dq = sq + 64;
+    uint32_t* H = reinterpret_cast<uint32_t*>(wl + 256 + kWarpQueues);
+    // list offsets inside H: 0 zero | SA | SB | PAo | PAv | PBo | PBv
+    const int oSA = 1, oSB = oSA + sp.nsa, oPAo = oSB + sp.nsb, oPAv = oPAo + sp.npoa;
+    const int oPBo = oPAv + sp.npva, oPBv = oPBo + sp.npob;
+    unsigned short* IA = FILTER ? reinterpret_cast<unsigned short*>(H + list_words(sp)) : nullptr;
+    unsigned short* IB = FILTER ? IA + sp.nsa : nullptr;
+    int nsa2 = sp.nsa, nsb2 = sp.nsb;  // single-list lengths after the spin-string prefilter
+    const uint32_t wmask4 = FILTER ? ((1u << tp.fw) - 1u) << 2 : 0u;
+    const unsigned ltmask = lanemask_lt();
+    const unsigned char* divA = smem + kOffDiv;
+    const unsigned char* divB = divA + 1024;
+
+
+    const ulonglong2 x = ep.samples[s];
+    unsigned long long hx, As, Bs, hxa;
+    double ediag;
+    if (!sample_setup(sp, x, lane, wl, T64, hx, ediag, As, Bs, hxa)) {
+        invalid_sample(ep, s, lane);
+        return;
+    }
+    if (FILTER) {
+        const unsigned char* occA = wl;
+        const unsigned char* virA = wl + 64;
+        const unsigned char* occB = wl + 128;
+        const unsigned char* virB = wl + 192;
+        if (lane == 0) H[0] = 0u;
+        // per-sample hash lists (low 32 bits of the linear hash contributions).  A single
+        // excitation whose new spin string is absent from every table key can take part in
+        // no hit (nor can any alpha-beta double built on it): the spin-string prefilter
+        // drops it, compacting the single lists (IA / IB map back to the full index).
+        const unsigned long long hxb = hx ^ hxa;
+        nsa2 = 0;
+        for (int t0 = 0; t0 < sp.nsa; t0 += 32) {
+            const int t = t0 + lane;
+            bool keep = false;
+            uint32_t hv32 = 0u;
+            if (t < sp.nsa) {
+                const int io = divA[t];
+                const int ki = occA[io], ka = virA[t - io * sp.va];
+                const unsigned long long tm = T64[2 * ki] ^ T64[2 * ka];
+                hv32 = static_cast<uint32_t>(tm);
+                keep = tp.aset == nullptr ||
+                       set_contains(tp.aset, tp.set_mask, As ^ (1ULL << ki) ^ (1ULL << ka), hxa ^ tm);
+            }
+            const unsigned m = __ballot_sync(QC_FULLMASK, keep);
+            if (keep) {
+                const int pos = nsa2 + __popc(m & ltmask);
+                H[oSA + pos] = hv32;
+                IA[pos] = static_cast<unsigned short>(t);
+            }
+            nsa2 += __popc(m);
+        }
+        nsb2 = 0;
+        for (int t0 = 0; t0 < sp.nsb; t0 += 32) {
+            const int t = t0 + lane;
+            bool keep = false;
+            uint32_t hv32 = 0u;
+            if (t < sp.nsb) {
+                const int io = divB[t];
+                const int ki = occB[io], ka = virB[t - io * sp.vb];
+                const unsigned long long tm = T64[2 * ki + 1] ^ T64[2 * ka + 1];
+                hv32 = static_cast<uint32_t>(tm);
+                keep = tp.bset == nullptr ||
+                       set_contains(tp.bset, tp.set_mask, Bs ^ (1ULL << ki) ^ (1ULL << ka), hxb ^ tm);
+            }
+            const unsigned m = __ballot_sync(QC_FULLMASK, keep);
+            if (keep) {
+                const int pos = nsb2 + __popc(m & ltmask);
+                H[oSB + pos] = hv32;
+                IB[pos] = static_cast<unsigned short>(t);
+            }
+            nsb2 += __popc(m);
+        }
+        for (int t = lane; t < sp.npoa; t += 32) {
+            const unsigned p = lut[t];
+            H[oPAo + t] = static_cast<uint32_t>(T64[2 * occA[p & 255u]] ^ T64[2 * occA[p >> 8]]);
+        }
+        for (int t = lane; t < sp.npva; t += 32) {
+            const unsigned p = lut[t];
+            H[oPAv + t] = static_cast<uint32_t>(T64[2 * virA[p & 255u]] ^ T64[2 * virA[p >> 8]]);
+        }
+        for (int t = lane; t < sp.npob; t += 32) {
+            const unsigned p = lut[t];
+            H[oPBo + t] = static_cast<uint32_t>(T64[2 * occB[p & 255u] + 1] ^ T64[2 * occB[p >> 8] + 1]);
+        }
+        for (int t = lane; t < sp.npvb; t += 32) {
+            const unsigned p = lut[t];
+            H[oPBv + t] = static_cast<uint32_t>(T64[2 * virB[p & 255u] + 1] ^ T64[2 * virB[p >> 8] + 1]);
+        }
+        __syncwarp();
+    }
+    const double2 psix = ep.psi[s];
+    const float2 ip32 = inv_psi32(psix);
+    const uint32_t hx32 = static_cast<uint32_t>(hx);
+    Acc acc{};
+    int qn = 0, nsq = 0, ndq = 0;
+    // iterator over (class, outer block u0, inner block w0)
+    int cls = -1, oo = 0, n1 = 0, io = 0, n2 = 0, u0 = 0, w0 = 0;
+    bool done = false, need_class = true, need_outer = true;
+    // outer hash values and their copies shifted for the filter word offset (>> 3): XOR
+    // commutes with the shift, so the offset costs one LOP3 per test
+    uint32_t hu[U], hu3[U];
+    unsigned umask = 0;
+#pragma unroll
+    for (int k = 0; k < U; ++k) hu[k] = hu3[k] = 0u;
+    while (true) {
+        if (!done) {
+            if (need_class) {
+                do {
+                    ++cls;
+                    if (cls == 0) { oo = 0; n1 = 1; io = oSA; n2 = nsa2; }
+                    else if (cls == 1) { oo = 0; n1 = 1; io = oSB; n2 = nsb2; }
+                    else if (cls == 2) { oo = oPAo; n1 = sp.npoa; io = oPAv; n2 = sp.npva; }
+                    else if (cls == 3) { oo = oPBo; n1 = sp.npob; io = oPBv; n2 = sp.npvb; }
+                    else if (cls == 4) { oo = oSA; n1 = nsa2; io = oSB; n2 = nsb2; }
+                } while (cls < 5 && (n1 == 0 || n2 == 0));
+                done = cls >= 5;
+                u0 = 0;
+                w0 = 0;
+                need_class = false;
+                need_outer = true;
+            }
+            if (!done) {
+                if (need_outer) {
+                    umask = 0;
+#pragma unroll
+                    for (int k = 0; k < U; ++k) {
+                        const bool v = u0 + k < n1;
+                        if (FILTER) {
+                            hu[k] = hx32 ^ (v ? H[oo + u0 + k] : 0u);
+                            hu3[k] = hu[k] >> 3;
+                        }
+                        umask |= (v ? 1u : 0u) << k;
+                    }
+                    need_outer = false;
+                }
+                const int w = w0 + lane;
+                const bool wv = w < n2;
+                const unsigned vm = wv ? umask : 0u;
+                const uint32_t hw = (FILTER && wv) ? H[io + w] : 0u;
+                const uint32_t hw3 = hw >> 3;
+                const unsigned ccode = (static_cast<unsigned>(cls) << 24) | static_cast<unsigned>(w);
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    bool pass;
+                    if (FILTER) {
+                        const uint32_t word = *reinterpret_cast<const uint32_t*>(
+                            reinterpret_cast<const unsigned char*>(filt) + ((hu3[k] ^ hw3) & wmask4));
+                        const uint32_t g = hu[k] ^ hw;
+                        const uint32_t t = __funnelshift_r(word, word, g) &
+                                           __funnelshift_r(word, word, g >> 27) &
+                                           __funnelshift_r(word, word, g >> 22);
+                        pass = ((t & (vm >> k)) & 1u) != 0u;
+                    } else {
+                        pass = ((vm >> k) & 1u) != 0u;
+                    }
+                    const unsigned m = __ballot_sync(QC_FULLMASK, pass);
+                    if (pass) q[qn + __popc(m & ltmask)] = ccode | (static_cast<unsigned>(u0 + k) << 12);
+                    qn += __popc(m);
+                }
+                w0 += 32;
+                if (w0 >= n2) {
+                    w0 = 0;
+                    u0 += U;
+                    need_outer = true;
+                    if (u0 >= n1) need_class = true;
+                }
+            }
+        }
+        __syncwarp();
+        // resolution stages (hit queues first, so neither can exceed 63 entries)
+        while (true) {
+            if (nsq >= 32 || (done && qn == 0 && nsq > 0)) {
+                const int n = nsq < 32 ? nsq : 32;
+                const bool v = lane < n;
+                const uint2 e = v ? sq[lane] : make_uint2(0u, 0u);
+                __syncwarp();
+                if (lane < nsq - n) sq[lane] = sq[n + lane];
+                nsq -= n;
+                __syncwarp();
+                if (v)
+                    verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc,
+                                         [&](double& h64, float& h32, bool& sneg) {
+                                             single_element<PREC>(e.x, prefix_parity(x), sp, wl, h64, h32, sneg);
+                                         });
+            } else if (ndq >= 32 || (done && qn == 0 && ndq > 0)) {
+                const int n = ndq < 32 ? ndq : 32;
+                const bool v = lane < n;
+                const uint2 e = v ? dq[lane] : make_uint2(0u, 0u);
+                __syncwarp();
+                if (lane < ndq - n) dq[lane] = dq[n + lane];
+                ndq -= n;
+                __syncwarp();
+                if (v)
+                    verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc,
+                                         [&](double& h64, float& h32, bool& sneg) {
+                                             double_element<PREC>(e.x, prefix_parity(x), sp, h64, h32, sneg);
+                                         });
+            } else if (qn >= 32 || (done && qn > 0)) {
+                const int n = qn < 32 ? qn : 32;
+                const bool v = lane < n;
+                const unsigned code = v ? q[lane] : 0u;
+                __syncwarp();
+                for (int t = lane; t < qn - n; t += 32) q[t] = q[n + t];
+                qn -= n;
+                __syncwarp();
+                unsigned orbs = 0u;
+                long long row = -1;
+                if (v) {
+                    orbs = decode(code, sp, wl, smem, IA, IB);
+                    row = probe(orbs, x, hx, tp, T64);
+                    if (row < 0 && ep.mode == QC_FULL) acc.missing++;
+                }
+                const bool hit = row >= 0;
+                const bool single = (orbs >> 16) == 0xFFFFu;
+                const unsigned ms = __ballot_sync(QC_FULLMASK, hit && single);
+                const unsigned md = __ballot_sync(QC_FULLMASK, hit && !single);
+                if (hit && single) sq[nsq + __popc(ms & ltmask)] = make_uint2(orbs, static_cast<unsigned>(row));
+                if (hit && !single) dq[ndq + __popc(md & ltmask)] = make_uint2(orbs, static_cast<unsigned>(row));
+                nsq += __popc(ms);
+                ndq += __popc(md);
+                __syncwarp();
+            } else {
+                break;
+            }
+        }
+        if (done) break;
+    }
+    sample_finish<PREC>(ep, s, lane, ediag, psix, acc);
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------------------------
+// K3: Eq. 1 reduction (two passes, deterministic order, last-block finish)
+// ------------------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+
+
+template <typename Tv>
+__device__ __forceinline__ Tv block_sum(Tv v, Tv* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = sh[threadIdx.x] + sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    Tv r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Pass 1 of one molecule, as block `bid` of `nblk`: W, sum c E and the count of finite
+// samples; the last block to finish writes the mean.
+__device__ __forceinline__ void reduce_pass1_body(const EvalParams& ep, double* part, unsigned bid,
+                                                  unsigned nblk) {
+    __shared__ double shd[kRedThreads];
+    __shared__ long long shl[kRedThreads];
+    __shared__ bool last;
+    long long w = 0, used = 0;
+    double sr = 0.0, si = 0.0;
+    bool neg = false;
+    for (long long i = static_cast<long long>(bid) * kRedThreads + threadIdx.x; i < ep.n_u;
+         i += static_cast<long long>(nblk) * kRedThreads) {
+        const double2 e = ep.eloc[i];
+        const long long c = ep.counts[i];
+        if (c < 0) {
+            neg = true;
+            continue;
+        }
+        if (isfinite(e.x) && isfinite(e.y)) {
+            w += c;
+            sr += static_cast<double>(c) * e.x;
+            si += static_cast<double>(c) * e.y;
+            used++;
+        }
+    }
+    if (neg) atomicOr(&ep.ctr->flags, QC_FLAG_NEG_COUNT);
+    const long long bw = block_sum<long long>(w, shl);
+    const long long bu = block_sum<long long>(used, shl);
+    const double bsr = block_sum<double>(sr, shd);
+    const double bsi = block_sum<double>(si, shd);
+    if (threadIdx.x == 0) {
+        part[4 * bid + 0] = bsr;
+        part[4 * bid + 1] = bsi;
+        part[4 * bid + 2] = __longlong_as_double(bw);
+        part[4 * bid + 3] = __longlong_as_double(bu);
+        __threadfence();
+        last = (atomicAdd(&ep.ctr->ticket, 1u) == nblk - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double tr = 0.0, ti = 0.0;
+        long long tw = 0, tu = 0;
+        for (unsigned b = 0; b < nblk; ++b) {
+            tr += __ldcg(part + 4 * b + 0);
+            ti += __ldcg(part + 4 * b + 1);
+            tw += __double_as_longlong(__ldcg(part + 4 * b + 2));
+            tu += __double_as_longlong(__ldcg(part + 4 * b + 3));
+        }
+        Counters* c = ep.ctr;
+        c->w = tw;
+        c->used = static_cast<unsigned long long>(tu);
+        c->sce_re = tr;
+        c->sce_im = ti;
+        c->mean_re = tr / static_cast<double>(tw);
+        c->mean_im = ti / static_cast<double>(tw);
+        c->ticket = 0u;
+    }
+}
+
+// Pass 2 of one molecule: sum c |E - Ebar|^2; the last block writes the summary.
+__device__ __forceinline__ void reduce_pass2_body(const EvalParams& ep, double* part, qc_eloc_summary* out,
+                                                  long long pairs_per_sample, unsigned bid, unsigned nblk) {
+    __shared__ double shd[kRedThreads];
+    __shared__ bool last;
+    const double mr = ep.ctr->mean_re, mi = ep.ctr->mean_im;
+    double v = 0.0;
+    for (long long i = static_cast<long long>(bid) * kRedThreads + threadIdx.x; i < ep.n_u;
+         i += static_cast<long long>(nblk) * kRedThreads) {
+        const double2 e = ep.eloc[i];
+        const long long c = ep.counts[i];
+        if (c < 0 || !isfinite(e.x) || !isfinite(e.y)) continue;
+        const double dr = e.x - mr, di = e.y - mi;
+        v += static_cast<double>(c) * (dr * dr + di * di);
+    }
+    const double bv = block_sum<double>(v, shd);
+    if (threadIdx.x == 0) {
+        part[4 * bid] = bv;
+        __threadfence();
+        last = (atomicAdd(&ep.ctr->ticket, 1u) == nblk - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double tv = 0.0;
+        for (unsigned b = 0; b < nblk; ++b) tv += __ldcg(part + 4 * b);
+        Counters* c = ep.ctr;
+        const unsigned f = c->flags;
+        int st = QC_OK;
+        if (f & QC_FLAG_UNSORTED) st = QC_ERR_UNSORTED;
+        else if (f & QC_FLAG_DUP) st = QC_ERR_DUP;
+        else if (f & QC_FLAG_NELEC) st = QC_ERR_NELEC;
+        else if (f & QC_FLAG_NEG_COUNT) st = QC_ERR_COUNTS;
+        else if (f & QC_FLAG_TABLE_FULL) st = QC_ERR_CAPACITY;
+        else if (f & QC_FLAG_TIMEOUT) st = QC_ERR_TIMEOUT;
+        else if (f & QC_FLAG_MISSING) st = QC_ERR_MISSING;
+        else if (f & QC_FLAG_ZERO_PSI) st = QC_ERR_ZERO_PSI;
+        const double w = static_cast<double>(c->w);
+        out->e_re = c->mean_re;
+        out->e_im = c->mean_im;
+        out->var = tv / w;
+        out->w = w;
+        out->sum_ce_re = c->sce_re;
+        out->sum_ce_im = c->sce_im;
+        out->n_used = c->used;
+        out->n_pairs = static_cast<unsigned long long>(ep.n_u - static_cast<long long>(c->invalid)) *
+                       static_cast<unsigned long long>(pairs_per_sample);
+        out->n_hits = c->hits;
+        out->n_missing = c->missing;
+        out->n_bad = c->bad;
+        out->flags = f;
+        out->status = st;
+        c->ticket = 0u;
+    }
+}
+
+}  // namespace qc

@@ -1,0 +1,54 @@
+// qc_handle.h -- the handle of the C ABI (opaque to callers) and host helpers shared by
+// the handle API (qc_api.cu) and the many-molecule batch (qc_batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "qc_eloc.h"
+#include "qc_internal.h"
+
+struct qc_eloc {
+    int device = 0;
+    int n_orb = 0, n_elec = 0, K = 0, na = 0, nb = 0, precision = 0, mode = 0;
+    double e_core = 0.0;
+    qc::SysParams sp{};
+    double* d_h = nullptr;
+    double* d_eri = nullptr;
+    double* d_J = nullptr;
+    double* d_X = nullptr;
+    double* d_Jt = nullptr;
+    double* d_Xt = nullptr;
+    float* d_Jt32 = nullptr;
+    float* d_Xt32 = nullptr;
+    float* d_h32 = nullptr;
+    float* d_eri32 = nullptr;
+    unsigned long long* d_T = nullptr;
+    unsigned long long* d_slots = nullptr;
+    size_t slots_cap = 0;  // 64-bit entries
+    uint32_t* d_filter = nullptr;
+    size_t filter_cap = 0;  // 32-bit words
+    unsigned long long* d_sets = nullptr;  // alpha set | beta set
+    size_t sets_cap = 0;                   // entries per set
+    double* d_part = nullptr;
+    int part_cap = 0;  // reduction blocks
+    qc::Counters* d_ctr = nullptr;
+    qc_eloc_summary* d_sum = nullptr;
+    int opt_timing = 0, opt_kernel = 0, opt_fw = 0, opt_warps = 0, opt_unroll = 0, opt_grid = 0;
+    int opt_prefilter = 1;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool ev_recorded = false;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    qc::LaunchCfg last_cfg{};
+    int last_fw = 0;
+    std::string err;
+};
+
+namespace qc {
+// grow the handle's workspace for n_u samples, an n_table-row table and 2^fw filter words
+qc_status ensure_workspace(qc_eloc* H, long long n_u, long long n_table, int fw);
+// kernel choice and launch shape for n_u samples against an n_table-row table
+qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, LaunchCfg& c, int& fw);
+}  // namespace qc

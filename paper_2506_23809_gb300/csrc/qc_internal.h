@@ -79,6 +79,36 @@ struct EvalParams {
     int mode;                     // 0 SAMPLE, 1 FULL
 };
 
+// A batch of molecules evaluated in one persistent launch.
+struct MolWork {  // writable workspace of one molecule of a batch
+    unsigned long long* slots;
+    uint32_t* filter;
+    unsigned long long* aset;
+    unsigned long long* bset;
+    Counters* ctr;
+    double* part;  // kBatchRedBlocks x 4 doubles
+    void* sum;     // qc_eloc_summary (device)
+};
+struct MolParams {
+    SysParams sp;
+    TableParams tp;
+    EvalParams ep;
+};
+struct WorkUnit {  // samples [s0, s1) of molecule mol
+    int mol;
+    int pad;
+    long long s0, s1;
+};
+struct BatchParams {
+    const MolParams* mols;
+    const WorkUnit* units;
+    int n_units;
+    unsigned* counter;         // next unit to hand out (zeroed before the launch)
+    unsigned filter_bytes;     // shared-memory filter region (largest filter of the batch)
+    unsigned warp_stride;      // per-warp shared-memory region (largest of the batch)
+};
+constexpr int kBatchRedBlocks = 16;  // reduction blocks per molecule in a batch
+
 struct LaunchCfg {
     int kernel;   // 1 direct, 2 filtered
     int grid;
@@ -97,9 +127,19 @@ cudaError_t launch_eloc_main(const SysParams& sp, const TableParams& tp, const E
 cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk,
                           void* summary_dev, long long pairs_per_sample, cudaStream_t s);
 int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem);
+// batch: build every molecule's table in one launch (key_off: prefix of table sizes, device)
+cudaError_t launch_build_batch(const MolParams* mols, const MolWork* work, const long long* key_off,
+                               int n_mol, long long n_keys, cudaStream_t s);
+cudaError_t launch_eloc_batch(const BatchParams& bp, int precision, int unroll, int grid, int warps,
+                              size_t smem, cudaStream_t s);
+cudaError_t launch_reduce_batch(const MolParams* mols, const MolWork* work, int n_mol, cudaStream_t s);
+int max_active_batch(int precision, int unroll, int threads, size_t smem);
+size_t batch_warp_bytes(const SysParams& sp);
+cudaError_t prepare_batch_kernels(size_t max_smem, size_t* dyn_limit);
 cudaError_t prepare_kernels(size_t max_smem);
 size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw);
 size_t direct_smem_bytes(const SysParams& sp, int warps);
+size_t smem_fixed_bytes();  // CTA tables at the head of the main kernels' dynamic shared memory
 int reduce_blocks(long long n);
 // message returned by qc_eloc_last_error(NULL) on this thread (qc_api.cu)
 void set_handleless_error(const std::string& msg);
