@@ -57,7 +57,7 @@ struct qc_batch {
     qc_eloc_summary* d_sums = nullptr;
     // launch shape
     int unroll = 4, warps = 0, units_per_cta = 8;
-    int warps_used = 0, grid = 0, n_units = 0;
+    int warps_used = 0, grid = 0, n_units = 0, red_blocks = 1;
     long long n_keys = 0;
     size_t smem = 0;
     unsigned filter_bytes = 0, warp_stride = 0;
@@ -93,6 +93,7 @@ int filter_log2(long long n) {
 // samples into work units of similar estimated cost and order them longest first.
 qc_status prepare(qc_batch* B) {
     const int M = B->n_mol;
+    B->red_blocks = 1;
     std::vector<qc::MolParams> mp(M);
     std::vector<qc::MolWork> mw(M);
     std::vector<long long> key_off(M + 1, 0);
@@ -109,7 +110,7 @@ qc_status prepare(qc_batch* B) {
         L.sets = off; off = align256(off + 2 * L.nb * 8);
         L.filter = off; off = align256(off + (static_cast<size_t>(4) << L.fw));
         L.ctr = off; off = align256(off + sizeof(qc::Counters));
-        L.part = off; off = align256(off + qc::kBatchRedBlocks * 4 * sizeof(double));
+        L.part = off; off = align256(off + static_cast<size_t>(qc::reduce_blocks(B->in[m].n_u)) * 4 * sizeof(double));
         L.sum = 0;
         fbytes_max = std::max(fbytes_max, 4u << L.fw);
         stride_max = std::max(stride_max, static_cast<unsigned>(qc::batch_warp_bytes(B->handles[m]->sp)));
@@ -137,6 +138,8 @@ qc_status prepare(qc_batch* B) {
         W.ctr = reinterpret_cast<qc::Counters*>(A + L.ctr);
         W.part = reinterpret_cast<double*>(A + L.part);
         W.sum = B->d_sums + m;
+        W.nblk = qc::reduce_blocks(I.n_u);
+        B->red_blocks = std::max(B->red_blocks, W.nblk);
         qc::MolParams& P = mp[m];
         P.sp = H->sp;
         P.tp = qc::TableParams{};
@@ -253,7 +256,7 @@ qc_status enqueue(qc_batch* B, qc_eloc_summary* sums_host, cudaStream_t s, bool 
         QB(qc::launch_eloc_batch(bp, B->precision, B->unroll, B->grid, B->warps_used, B->smem, s), "batch kernel");
     }
     if (timed) QB(cudaEventRecord(B->ev[2], s), "cudaEventRecord");
-    QB(qc::launch_reduce_batch(B->d_mols, B->d_work, B->n_mol, s), "batch reduce");
+    QB(qc::launch_reduce_batch(B->d_mols, B->d_work, B->n_mol, B->red_blocks, s), "batch reduce");
     if (timed) QB(cudaEventRecord(B->ev[3], s), "cudaEventRecord");
     if (sums_host)
         QB(cudaMemcpyAsync(sums_host, B->d_sums, B->n_mol * sizeof(qc_eloc_summary), cudaMemcpyDeviceToHost, s),

@@ -28,13 +28,16 @@ __global__ void __launch_bounds__(256) build_batch_kernel(const MolParams* __res
 // batch: blockIdx.y is the molecule
 __global__ void __launch_bounds__(kRedThreads) reduce_batch_pass1(const MolParams* __restrict__ mols,
                                                                   const MolWork* __restrict__ work) {
-    reduce_pass1_body(mols[blockIdx.y].ep, work[blockIdx.y].part, blockIdx.x, gridDim.x);
+    const MolWork& W = work[blockIdx.y];
+    if (blockIdx.x >= static_cast<unsigned>(W.nblk)) return;  // block-uniform
+    reduce_pass1_body(mols[blockIdx.y].ep, W.part, blockIdx.x, W.nblk);
 }
 __global__ void __launch_bounds__(kRedThreads) reduce_batch_pass2(const MolParams* __restrict__ mols,
                                                                   const MolWork* __restrict__ work) {
     const MolParams& P = mols[blockIdx.y];
-    reduce_pass2_body(P.ep, work[blockIdx.y].part, static_cast<qc_eloc_summary*>(work[blockIdx.y].sum),
-                      P.sp.pairs, blockIdx.x, gridDim.x);
+    const MolWork& W = work[blockIdx.y];
+    if (blockIdx.x >= static_cast<unsigned>(W.nblk)) return;  // block-uniform
+    reduce_pass2_body(P.ep, W.part, static_cast<qc_eloc_summary*>(W.sum), P.sp.pairs, blockIdx.x, W.nblk);
 }
 
 // K4: many molecules in one persistent launch.  CTAs take work units (a block of samples
@@ -110,8 +113,9 @@ cudaError_t launch_build_batch(const MolParams* mols, const MolWork* work, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_batch(const MolParams* mols, const MolWork* work, int n_mol, cudaStream_t s) {
-    const dim3 grid(kBatchRedBlocks, n_mol);
+cudaError_t launch_reduce_batch(const MolParams* mols, const MolWork* work, int n_mol, int max_blocks,
+                                cudaStream_t s) {
+    const dim3 grid(max_blocks, n_mol);
     reduce_batch_pass1<<<grid, kRedThreads, 0, s>>>(mols, work);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

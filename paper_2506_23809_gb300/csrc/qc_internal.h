@@ -86,8 +86,10 @@ struct MolWork {  // writable workspace of one molecule of a batch
     unsigned long long* aset;
     unsigned long long* bset;
     Counters* ctr;
-    double* part;  // kBatchRedBlocks x 4 doubles
+    double* part;  // nblk x 4 doubles
     void* sum;     // qc_eloc_summary (device)
+    int nblk;      // reduction blocks: the single-molecule path's count, so results match it bitwise
+    int pad;
 };
 struct MolParams {
     SysParams sp;
@@ -107,7 +109,6 @@ struct BatchParams {
     unsigned filter_bytes;     // shared-memory filter region (largest filter of the batch)
     unsigned warp_stride;      // per-warp shared-memory region (largest of the batch)
 };
-constexpr int kBatchRedBlocks = 16;  // reduction blocks per molecule in a batch
 
 struct LaunchCfg {
     int kernel;   // 1 direct, 2 filtered
@@ -132,7 +133,8 @@ cudaError_t launch_build_batch(const MolParams* mols, const MolWork* work, const
                                int n_mol, long long n_keys, cudaStream_t s);
 cudaError_t launch_eloc_batch(const BatchParams& bp, int precision, int unroll, int grid, int warps,
                               size_t smem, cudaStream_t s);
-cudaError_t launch_reduce_batch(const MolParams* mols, const MolWork* work, int n_mol, cudaStream_t s);
+cudaError_t launch_reduce_batch(const MolParams* mols, const MolWork* work, int n_mol, int max_blocks,
+                                cudaStream_t s);
 int max_active_batch(int precision, int unroll, int threads, size_t smem);
 size_t batch_warp_bytes(const SysParams& sp);
 cudaError_t prepare_batch_kernels(size_t max_smem, size_t* dyn_limit);
