@@ -243,6 +243,45 @@ qc_status qc_batch_timings(qc_batch* batch, float* ms3);
  * fastest; best3 (may be NULL) receives {unroll, warps, units_per_cta} */
 qc_status qc_batch_autotune(qc_batch* batch, void* stream, int iters, int64_t* best3);
 
+/* ---- the serving form: asynchronous requests, continuous batching -----------------
+ * qc_server_create starts a scheduler thread on `device`.  qc_eloc_submit queues one
+ * sample-space request and returns a ticket at once; the scheduler admits requests in
+ * arrival order while their device footprint fits `budget_bytes` and fewer than
+ * `max_slots` are in flight, keeps each molecule's Hamiltonian resident for later requests
+ * with the same nonzero mol_key (least-recently-used eviction when the budget needs
+ * room), and launches every admitted request whose inputs are on the device as one batch
+ * ("wave") on one of `n_streams` streams, so waves overlap on the GPU.  A request that can
+ * never fit the budget is refused with QC_ERR_BUDGET at submit.  qc_eloc_poll waits up to
+ * timeout_us for a ticket and returns QC_PENDING if it is not done; a finished ticket is
+ * released by the poll that returns it.  A request's E_loc is bitwise the same alone and
+ * in any mix (the batch runs the single-molecule per-sample code). */
+typedef struct qc_server qc_server;
+typedef struct {
+    const double* h;       /* host FP64 integrals as for qc_eloc_create: copied at submit   */
+    const double* eri;     /* unless the molecule (mol_key) is resident                     */
+    double e_core;
+    int n_orb, n_elec, precision;  /* QC_FP64 | QC_FP32_COMP; sample-space mode             */
+    int pad;
+    uint64_t mol_key;      /* nonzero: keep this Hamiltonian resident under this key        */
+    const uint64_t* samples;  /* host uint64[n_u][2], sorted unique; with counts and psi,   */
+    const int64_t* counts;    /* valid until the ticket is polled done                      */
+    const double* psi;
+    int64_t n_u;
+    double* eloc_out;      /* host complex128[n_u] written when done, or NULL               */
+} qc_eloc_job;
+typedef struct {
+    qc_eloc_summary summary;
+    int32_t status, pad;
+    double t_submit, t_admit, t_start, t_done;  /* seconds on the steady clock              */
+} qc_eloc_result;
+qc_status qc_server_create(int device, uint64_t budget_bytes, int max_slots, int n_streams,
+                           qc_server** out);
+qc_status qc_eloc_submit(qc_server* server, const qc_eloc_job* job, uint64_t* ticket);
+qc_status qc_eloc_poll(qc_server* server, uint64_t ticket, qc_eloc_result* result, int timeout_us);
+/* {device bytes in use, requests in flight, requests waiting, resident molecules} */
+qc_status qc_server_stats(qc_server* server, uint64_t* stats4);
+qc_status qc_server_destroy(qc_server* server);  /* finishes queued work first */
+
 /* Launch shape of the last evaluation on this handle: {kernel (1 direct, 2 filtered),
  * grid CTAs, warps per CTA, unroll, dynamic shared memory bytes, log2 filter words}. */
 qc_status qc_eloc_last_config(const qc_eloc* handle, int64_t* cfg6);

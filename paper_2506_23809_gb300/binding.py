@@ -350,3 +350,98 @@ def qc_batch_autotune(batch: QcBatch, stream=None, iters: int = 2):
     best = (ctypes.c_int64 * 3)()
     _bcheck(load_library().qc_batch_autotune(batch.ptr, ctypes.c_void_p(s.cuda_stream), int(iters), best), batch)
     return dict(unroll=int(best[0]), warps=int(best[1]), units_per_cta=int(best[2]))
+
+
+# ----------------------------------------------------------------------------------
+# the serving form
+# ----------------------------------------------------------------------------------
+class qc_eloc_job(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p), ("eri", ctypes.c_void_p), ("e_core", ctypes.c_double),
+                ("n_orb", ctypes.c_int), ("n_elec", ctypes.c_int), ("precision", ctypes.c_int),
+                ("pad", ctypes.c_int), ("mol_key", ctypes.c_uint64), ("samples", ctypes.c_void_p),
+                ("counts", ctypes.c_void_p), ("psi", ctypes.c_void_p), ("n_u", ctypes.c_int64),
+                ("eloc_out", ctypes.c_void_p)]
+
+
+class qc_eloc_result(ctypes.Structure):
+    _fields_ = [("summary", qc_eloc_summary), ("status", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+@dataclass
+class QcServer:
+    ptr: ctypes.c_void_p
+    keep: dict  # ticket -> host arrays that must outlive the request
+
+
+def _server_lib():
+    lib = load_library()
+    if not getattr(lib, "_qc_server_typed", False):
+        P = ctypes.c_void_p
+        lib.qc_server_create.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)]
+        lib.qc_eloc_submit.argtypes = [P, ctypes.POINTER(qc_eloc_job), ctypes.POINTER(ctypes.c_uint64)]
+        lib.qc_eloc_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(qc_eloc_result), ctypes.c_int]
+        lib.qc_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
+        lib.qc_server_destroy.argtypes = [P]
+        for f in ("qc_server_create", "qc_eloc_submit", "qc_eloc_poll", "qc_server_stats", "qc_server_destroy"):
+            getattr(lib, f).restype = ctypes.c_int
+        lib._qc_server_typed = True
+    return lib
+
+
+def qc_server_create(device: int = 0, budget_bytes: int = 160 << 30, max_slots: int = 64,
+                     n_streams: int = 2) -> QcServer:
+    out = ctypes.c_void_p()
+    st = _server_lib().qc_server_create(int(device), int(budget_bytes), int(max_slots), int(n_streams),
+                                        ctypes.byref(out))
+    if st != QC_OK:
+        raise QcError(st, "qc_server_create failed")
+    return QcServer(out, {})
+
+
+def qc_eloc_submit(server: QcServer, h, eri, e_core: float, n_orb: int, n_elec: int, keys, counts, psi,
+                   precision: int = QC_FP64, mol_key: int = 0, want_eloc: bool = True) -> int:
+    """Queue one request (host numpy inputs); returns its ticket."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    counts = np.ascontiguousarray(counts, dtype=np.int64)
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    out = np.empty(len(keys), dtype=np.complex128) if want_eloc else None
+    j = qc_eloc_job(h=h.ctypes.data, eri=eri.ctypes.data, e_core=float(e_core), n_orb=int(n_orb),
+                    n_elec=int(n_elec), precision=int(precision), pad=0, mol_key=int(mol_key),
+                    samples=keys.ctypes.data, counts=counts.ctypes.data, psi=psi.ctypes.data, n_u=len(keys),
+                    eloc_out=None if out is None else out.ctypes.data)
+    t = ctypes.c_uint64()
+    st = _server_lib().qc_eloc_submit(server.ptr, ctypes.byref(j), ctypes.byref(t))
+    if st != QC_OK:
+        raise QcError(st, "qc_eloc_submit refused the request")
+    server.keep[t.value] = (keys, counts, psi, out)
+    return t.value
+
+
+def qc_eloc_poll(server: QcServer, ticket: int, timeout_us: int = 0):
+    """None while pending; else (result dict, E_loc numpy array or None)."""
+    r = qc_eloc_result()
+    st = _server_lib().qc_eloc_poll(server.ptr, int(ticket), ctypes.byref(r), int(timeout_us))
+    if st == QC_PENDING:
+        return None
+    if st != QC_OK:
+        raise QcError(st, "qc_eloc_poll")
+    arrays = server.keep.pop(ticket)
+    d = r.summary.as_dict()
+    d.update(status=r.status, t_submit=r.t_submit, t_admit=r.t_admit, t_start=r.t_start, t_done=r.t_done)
+    return d, arrays[3]
+
+
+def qc_server_stats(server: QcServer) -> dict:
+    s = (ctypes.c_uint64 * 4)()
+    _server_lib().qc_server_stats(server.ptr, s)
+    return dict(bytes_in_use=int(s[0]), in_flight=int(s[1]), waiting=int(s[2]), resident=int(s[3]))
+
+
+def qc_server_destroy(server: QcServer):
+    if server.ptr:
+        _server_lib().qc_server_destroy(server.ptr)
+        server.ptr = ctypes.c_void_p()

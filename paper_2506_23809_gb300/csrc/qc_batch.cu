@@ -42,6 +42,7 @@ struct qc_batch {
     int device = 0;
     int precision = 0;
     int n_mol = 0;
+    int mol_cap = 0;
     int sm_count = 0;
     size_t dyn_limit = 0;
     std::vector<qc_eloc*> handles;
@@ -277,6 +278,49 @@ void drop_graph(qc_batch* B) {
 
 extern "C" {
 
+}  // extern "C"
+
+namespace {
+// (Re)size the per-molecule device arrays for n_mol molecules.
+cudaError_t batch_alloc(qc_batch* B, int n_mol) {
+    if (n_mol <= B->mol_cap) return cudaSuccess;
+    for (void* p : {static_cast<void*>(B->d_mols), static_cast<void*>(B->d_work), static_cast<void*>(B->d_key_off),
+                    static_cast<void*>(B->d_sums)})
+        if (p) cudaFree(p);
+    B->d_mols = nullptr;
+    B->d_work = nullptr;
+    B->d_key_off = nullptr;
+    B->d_sums = nullptr;
+    B->mol_cap = 0;
+    cudaError_t e = cudaMalloc(&B->d_mols, n_mol * sizeof(qc::MolParams));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_work, n_mol * sizeof(qc::MolWork));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_key_off, (n_mol + 1) * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_sums, n_mol * sizeof(qc_eloc_summary));
+    if (e == cudaSuccess) B->mol_cap = n_mol;
+    return e;
+}
+}  // namespace
+
+// Point an existing batch at another set of handles (same precision and device), keeping
+// its device allocations when they are large enough; inputs must be set again.
+qc_status qc::batch_retarget(qc_batch* B, qc_eloc* const* handles, int n_mol) {
+    if (!B || !handles || n_mol <= 0 || n_mol > 65535) return QC_ERR_ARG;
+    for (int m = 0; m < n_mol; ++m)
+        if (!handles[m] || handles[m]->mode != QC_SAMPLE || handles[m]->precision != B->precision ||
+            handles[m]->device != B->device)
+            return QC_ERR_ARG;
+    cudaError_t e = batch_alloc(B, n_mol);
+    if (e != cudaSuccess) return bcuda(B, e, "cudaMalloc batch arrays");
+    B->n_mol = n_mol;
+    B->handles.assign(handles, handles + n_mol);
+    B->in.assign(n_mol, BatchInput{});
+    B->dirty = true;
+    drop_graph(B);
+    return QC_OK;
+}
+
+extern "C" {
+
 qc_status qc_batch_create(qc_eloc* const* handles, int n_mol, qc_batch** out) {
     if (!out) return QC_ERR_ARG;
     *out = nullptr;
@@ -297,11 +341,8 @@ qc_status qc_batch_create(qc_eloc* const* handles, int n_mol, qc_batch** out) {
     B->precision = handles[0]->precision;
     B->sm_count = handles[0]->sm_count;
     cudaError_t e = qc::prepare_batch_kernels(handles[0]->smem_optin, &B->dyn_limit);
-    if (e == cudaSuccess) e = cudaMalloc(&B->d_mols, n_mol * sizeof(qc::MolParams));
-    if (e == cudaSuccess) e = cudaMalloc(&B->d_work, n_mol * sizeof(qc::MolWork));
-    if (e == cudaSuccess) e = cudaMalloc(&B->d_key_off, (n_mol + 1) * sizeof(long long));
+    if (e == cudaSuccess) e = batch_alloc(B, n_mol);
     if (e == cudaSuccess) e = cudaMalloc(&B->d_counter, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&B->d_sums, n_mol * sizeof(qc_eloc_summary));
     for (auto& ev : B->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
     if (e != cudaSuccess) {

@@ -51,4 +51,6 @@ namespace qc {
 qc_status ensure_workspace(qc_eloc* H, long long n_u, long long n_table, int fw);
 // kernel choice and launch shape for n_u samples against an n_table-row table
 qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, LaunchCfg& c, int& fw);
+// point a batch at another set of handles, reusing its device allocations
+qc_status batch_retarget(qc_batch* B, qc_eloc* const* handles, int n_mol);
 }  // namespace qc
