@@ -84,13 +84,13 @@ def test_alone_equals_in_the_mix_and_handle_api(B, orc):
 
 def test_budget_refusal_and_eviction(B):
     ints, keys, counts, psi = _mol(24, 8, 500, 1701)
-    srv = B.qc_server_create(0, 64 << 20, max_slots=4, n_streams=1)
+    srv = B.qc_server_create(0, 1 << 20, max_slots=4, n_streams=1)
     try:
         big = _mol(64, 16, 300, 1801)
-        with pytest.raises(B.QcError) as ex:   # K^4 FP64 integrals alone exceed 64 MB
+        with pytest.raises(B.QcError) as ex:   # K^4 FP64 integrals alone exceed 1 MB
             B.qc_eloc_submit(srv, big[0].h, big[0].eri, 0.0, 64, 16, big[1], big[2], big[3])
         assert ex.value.status == -6
-        # many small molecules through a small budget: residents get evicted, all finish
+        # six molecules through a budget that holds about two: residents get evicted, all finish
         ts = [B.qc_eloc_submit(srv, ints.h, ints.eri, 0.1 * k, 24, 8, keys, counts, psi, mol_key=100 + k)
               for k in range(6)]
         outs = [_wait(B, srv, t) for t in ts]
