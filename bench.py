@@ -52,6 +52,12 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--form", default="plain", choices=["plain", "batched", "serve"],
+                   help="plain: one molecule per step (the default benchmark); batched: many "
+                        "molecules in one persistent launch; serve: Poisson request arrivals")
+    p.add_argument("--n-mol", type=int, default=64, help="batched form: molecules")
+    p.add_argument("--requests", type=int, default=48, help="serve form: requests")
+    p.add_argument("--rate", type=float, default=20.0, help="serve form: arrivals per second")
     return p.parse_args()
 
 
@@ -397,10 +403,173 @@ def run_ours(args):
     return 0
 
 
+def _pairs(n_orb, n_elec):
+    K, o = n_orb // 2, n_elec // 2
+    v = K - o
+    return 2 * o * v + 2 * (o * (o - 1) // 2) * (v * (v - 1) // 2) + (o * v) ** 2
+
+
+def run_batched(args):
+    """64 synthetic molecules (N even in 24..120, FP32-compensated): plain per-molecule
+    launches against one batched step, eager and as an autotuned CUDA graph."""
+    import numpy as np
+    import torch
+
+    from paper_2506_23809_gb300 import binding as B
+    from paper_2506_23809_gb300 import build
+    from paper_2506_23809_gb300 import inputs as I
+    build.build()
+    B.load_library()
+    torch.cuda.set_device(0)
+    specs = I.batched_molecule_specs(args.n_mol)
+    # the batched form computes in the precision form (FP32 terms, compensated sums, FP64
+    # diagonal and reduction) unless --precision fp64 is given explicitly
+    prec = B.QC_FP64 if "--precision" in sys.argv and args.precision == "fp64" else B.QC_FP32_COMP
+    handles, dev, outs = [], [], []
+    total_pairs = 0
+    for sp in specs:
+        K = sp["n_orb"] // 2
+        ints = I.make_integrals(K, sp["n_orb"], sp["seed"])
+        keys = I.rank_weighted_samples(K, sp["n_elec"] // 2, sp["n_elec"] // 2, sp["n_u"], seed=sp["seed"] + 1)
+        counts = I.zipf_counts(sp["n_u"], 100 * sp["n_u"], sp["seed"] + 2)
+        psi = I.lognormal_psi(sp["n_u"], sp["seed"] + 3)
+        h = B.qc_eloc_create(ints.h, ints.eri, 0.0, sp["n_orb"], sp["n_elec"], prec)
+        B.qc_eloc_set_option(h, B.QC_OPT_TIMING, 1)
+        handles.append(h)
+        dev.append((B.keys_to_tensor(keys), torch.from_numpy(counts).cuda(), torch.from_numpy(psi).cuda()))
+        outs.append(torch.empty(sp["n_u"], dtype=torch.complex128, device="cuda"))
+        total_pairs += sp["n_u"] * _pairs(sp["n_orb"], sp["n_elec"])
+    stream = torch.cuda.Stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        stream.synchronize()
+        ts = []
+        for _ in range(reps):
+            ev0.record(stream)
+            fn()
+            ev1.record(stream)
+            ev1.synchronize()
+            ts.append(ev0.elapsed_time(ev1))
+        return statistics.median(ts)
+
+    def plain():
+        for h, (k, c, p), o in zip(handles, dev, outs):
+            B.qc_eloc_eval(h, k, c, p, eloc=o, stream=stream)
+    with torch.cuda.stream(stream):
+        t_plain = timed(plain, args.steps)
+        ref = [o.cpu().numpy().copy() for o in outs]
+        batch = B.qc_batch_create(handles)
+        for m, ((k, c, p), o) in enumerate(zip(dev, outs)):
+            B.qc_batch_set_inputs(batch, m, k, c, p, o)
+        t_eager = timed(lambda: B.qc_batch_eval(batch, stream), args.steps)
+        best = B.qc_batch_autotune(batch, stream, iters=2)
+        t_tuned = timed(lambda: B.qc_batch_eval(batch, stream), args.steps)
+        t_graph = timed(lambda: B.qc_batch_graph_launch(batch, stream), args.steps)
+        same = all(np.array_equal(o.cpu().numpy().view(np.uint64), r.view(np.uint64)) for o, r in zip(outs, ref))
+        cfg = B.qc_batch_config(batch)
+    B.qc_batch_destroy(batch)
+    for h in handles:
+        B.qc_eloc_destroy(h)
+    line = {"metric": METRIC, "form": "batched", "value": total_pairs / (t_graph / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_graph,
+            "higher_is_better": True, "dtype": "f32+f64" if prec == B.QC_FP32_COMP else "f64",
+            "config": {"workload": f"batched_{args.n_mol}_molecules", "n_mol": args.n_mol,
+                       "total_samples": int(sum(sp["n_u"] for sp in specs)), "pairs_per_step": int(total_pairs),
+                       "n_orb_range": [min(sp["n_orb"] for sp in specs), max(sp["n_orb"] for sp in specs)],
+                       "autotuned": best, "launch": cfg},
+            "ms": {"plain_per_molecule_launches": t_plain, "batched_eager": t_eager,
+                   "batched_eager_autotuned": t_tuned, "batched_graph_autotuned": t_graph},
+            "speedup_vs_plain": t_plain / t_graph, "results_bitwise_equal_to_plain": bool(same)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson arrivals of requests with their own molecules (N 28..128) and sample sets;
+    latency percentiles and throughput of the server against plain sequential launches."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2506_23809_gb300 import binding as B
+    from paper_2506_23809_gb300 import build
+    from paper_2506_23809_gb300 import inputs as I
+    build.build()
+    B.load_library()
+    torch.cuda.set_device(0)
+    specs = I.serving_request_specs(args.requests, args.rate)
+    reqs = []
+    for sp in specs:
+        n_u = min(sp["n_u"], 200_000)   # generation cost on the host bounds the largest sets
+        K = sp["n_orb"] // 2
+        ints = I.make_integrals(K, min(sp["n_orb"], 64), sp["seed"])
+        keys = I.rank_weighted_samples(K, sp["n_elec"] // 2, sp["n_elec"] // 2, n_u, seed=sp["seed"] + 1)
+        reqs.append(dict(t=sp["t_arrive"], n_orb=sp["n_orb"], n_elec=sp["n_elec"], ints=ints, keys=keys,
+                         counts=I.zipf_counts(n_u, 100 * n_u, sp["seed"] + 2), psi=I.lognormal_psi(n_u, sp["seed"] + 3),
+                         pairs=n_u * _pairs(sp["n_orb"], sp["n_elec"])))
+    total_pairs = sum(r["pairs"] for r in reqs)
+    # plain: one handle and one evaluation per request, back to back (integral upload included)
+    t0 = time.perf_counter()
+    for r in reqs:
+        h = B.qc_eloc_create(r["ints"].h, r["ints"].eri, 0.0, r["n_orb"], r["n_elec"])
+        e, _ = B.qc_eloc_eval(h, B.keys_to_tensor(r["keys"]), torch.from_numpy(r["counts"]).cuda(),
+                              torch.from_numpy(r["psi"]).cuda())
+        e.cpu()
+        B.qc_eloc_destroy(h)
+    t_plain = time.perf_counter() - t0
+    srv = B.qc_server_create(0, 160 << 30, max_slots=64, n_streams=3)
+    done = {}
+    tickets = [None] * len(reqs)
+    start = time.perf_counter()
+
+    def client():
+        for i, r in enumerate(reqs):
+            delay = r["t"] - (time.perf_counter() - start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = B.qc_eloc_submit(srv, r["ints"].h, r["ints"].eri, 0.0, r["n_orb"], r["n_elec"],
+                                          r["keys"], r["counts"], r["psi"], mol_key=i + 1)
+    th = threading.Thread(target=client)
+    th.start()
+    while len(done) < len(reqs):
+        for i, t in enumerate(tickets):
+            if t is not None and i not in done:
+                out = B.qc_eloc_poll(srv, t, 1000)
+                if out is not None:
+                    done[i] = out[0]
+        time.sleep(0.0005)
+    th.join()
+    t_all = time.perf_counter() - start
+    B.qc_server_destroy(srv)
+    lat = np.array([done[i]["t_done"] - done[i]["t_submit"] for i in range(len(reqs))]) * 1e3
+    ok = all(done[i]["status"] == 0 for i in done)
+    line = {"metric": METRIC, "form": "serve", "value": total_pairs / t_all, "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f64",
+            "config": {"workload": f"serve_{args.requests}_requests_poisson_{args.rate}_per_s",
+                       "requests": len(reqs), "rate_per_s": args.rate, "budget_gb": 160,
+                       "n_orb_range": [min(r["n_orb"] for r in reqs), max(r["n_orb"] for r in reqs)],
+                       "max_samples": int(max(len(r["keys"]) for r in reqs)), "pairs_total": int(total_pairs)},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "wall_s": {"served_including_arrival_gaps": t_all, "plain_sequential": t_plain,
+                       "arrival_span": reqs[-1]["t"]},
+            "all_ok": bool(ok)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.form == "batched":
+        return run_batched(args)
+    if args.form == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

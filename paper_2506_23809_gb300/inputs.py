@@ -319,7 +319,7 @@ def batched_molecule_specs(n_mol: int = 64, seed: int = 6400):
     """Per-molecule (n_orb, n_elec, n_u, seed) for the many-molecule batched form:
     N even uniform in 24..120, n_elec = N/2 - 2*U{0..N/4}, rounded down to even (S_z = 0)
     and clamped to >= 2,
-    n_u log-uniform in [1e3, 1e5]."""
+    n_u log-uniform in [1e3, 1e5] (at most a quarter of a small sector)."""
     rng = _rng(seed)
     specs = []
     for m in range(n_mol):
@@ -328,6 +328,7 @@ def batched_molecule_specs(n_mol: int = 64, seed: int = 6400):
         ne -= ne % 2          # S_z = 0 needs an even count: round an odd N/2 down
         ne = max(ne, 2)
         n_u = int(round(10 ** rng.uniform(3.0, 5.0)))
+        n_u = min(n_u, math.comb(N // 2, ne // 2) ** 2 // 4)  # small sectors: a quarter at most
         specs.append(dict(n_orb=N, n_elec=ne, n_u=n_u, seed=seed + 17 * (m + 1)))
     return specs
 

@@ -78,7 +78,7 @@ def test_batched_and_serving_specs():
     for s in specs:
         assert s["n_orb"] % 2 == 0 and 24 <= s["n_orb"] <= 120
         assert 2 <= s["n_elec"] <= s["n_orb"] // 2 and s["n_elec"] % 2 == 0
-        assert 1000 <= s["n_u"] <= 100_000
+        assert 1 <= s["n_u"] <= 100_000
     reqs = I.serving_request_specs(50, 10.0)
     assert all(28 <= r["n_orb"] <= 128 for r in reqs)
     assert all(abs(r["n_elec"] - r["n_orb"] // 2) <= 4 for r in reqs)
