@@ -468,7 +468,10 @@ def run_batched(args):
         best = B.qc_batch_autotune(batch, stream, iters=2)
         t_tuned = timed(lambda: B.qc_batch_eval(batch, stream), args.steps)
         t_graph = timed(lambda: B.qc_batch_graph_launch(batch, stream), args.steps)
-        same = all(np.array_equal(o.cpu().numpy().view(np.uint64), r.view(np.uint64)) for o, r in zip(outs, ref))
+        # the two paths may pick different filter sizes, which changes the order hits are
+        # summed in: compare within the precision form's tolerance
+        diff = max(float(np.max(np.abs(o.cpu().numpy() - r) / np.maximum(1.0, np.abs(r)), initial=0.0))
+                   for o, r in zip(outs, ref))
         cfg = B.qc_batch_config(batch)
     B.qc_batch_destroy(batch)
     for h in handles:
@@ -482,7 +485,7 @@ def run_batched(args):
                        "autotuned": best, "launch": cfg},
             "ms": {"plain_per_molecule_launches": t_plain, "batched_eager": t_eager,
                    "batched_eager_autotuned": t_tuned, "batched_graph_autotuned": t_graph},
-            "speedup_vs_plain": t_plain / t_graph, "results_bitwise_equal_to_plain": bool(same)}
+            "speedup_vs_plain": t_plain / t_graph, "max_rel_diff_vs_plain": diff}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -512,15 +515,24 @@ def run_serve(args):
                          counts=I.zipf_counts(n_u, 100 * n_u, sp["seed"] + 2), psi=I.lognormal_psi(n_u, sp["seed"] + 3),
                          pairs=n_u * _pairs(sp["n_orb"], sp["n_elec"])))
     total_pairs = sum(r["pairs"] for r in reqs)
-    # plain: one handle and one evaluation per request, back to back (integral upload included)
+    # plain: one handle and one evaluation per request, back to back (integral upload
+    # included); its latencies under the same arrivals follow from FIFO service times
+    service = []
     t0 = time.perf_counter()
     for r in reqs:
+        ts = time.perf_counter()
         h = B.qc_eloc_create(r["ints"].h, r["ints"].eri, 0.0, r["n_orb"], r["n_elec"])
         e, _ = B.qc_eloc_eval(h, B.keys_to_tensor(r["keys"]), torch.from_numpy(r["counts"]).cuda(),
                               torch.from_numpy(r["psi"]).cuda())
         e.cpu()
         B.qc_eloc_destroy(h)
+        service.append(time.perf_counter() - ts)
     t_plain = time.perf_counter() - t0
+    free_at, plain_lat = 0.0, []
+    for r, sv in zip(reqs, service):
+        begin = max(free_at, r["t"])
+        free_at = begin + sv
+        plain_lat.append(1e3 * (free_at - r["t"]))
     srv = B.qc_server_create(0, 160 << 30, max_slots=64, n_streams=3)
     done = {}
     tickets = [None] * len(reqs)
@@ -555,6 +567,8 @@ def run_serve(args):
                        "max_samples": int(max(len(r["keys"]) for r in reqs)), "pairs_total": int(total_pairs)},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
+            "plain_fifo_latency_ms": {"p50": float(np.percentile(plain_lat, 50)),
+                                      "p99": float(np.percentile(plain_lat, 99))},
             "wall_s": {"served_including_arrival_gaps": t_all, "plain_sequential": t_plain,
                        "arrival_span": reqs[-1]["t"]},
             "all_ok": bool(ok)}

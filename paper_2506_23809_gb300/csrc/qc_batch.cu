@@ -61,7 +61,6 @@ struct qc_batch {
     int warps_used = 0, grid = 0, n_units = 0, red_blocks = 1;
     long long n_keys = 0;
     size_t smem = 0;
-    unsigned filter_bytes = 0, warp_stride = 0;
     bool dirty = true;
     // graph
     cudaGraph_t graph = nullptr;
@@ -99,22 +98,36 @@ qc_status prepare(qc_batch* B) {
     std::vector<qc::MolWork> mw(M);
     std::vector<long long> key_off(M + 1, 0);
     size_t off = 0;
-    unsigned fbytes_max = 0, stride_max = 0;
     struct Lay { size_t slots, filter, sets, ctr, part, sum; unsigned long long nb; int fw; };
     std::vector<Lay> lay(M);
+    const size_t fixed0 = qc::smem_fixed_bytes();
+    const int wcap = B->warps > 0 ? std::min(B->warps, qc::kFilteredMaxWarps) : qc::kFilteredMaxWarps;
+    std::vector<int> act(M);
+    std::vector<unsigned> stride(M);
     for (int m = 0; m < M; ++m) {
         const long long n = std::max<long long>(B->in[m].n_u, 1);
         Lay& L = lay[m];
         L.nb = next_pow2(2ULL * static_cast<unsigned long long>(n));
-        L.fw = filter_log2(n);
+        stride[m] = static_cast<unsigned>((qc::batch_warp_bytes(B->handles[m]->sp) + 15) / 16 * 16);
+        // the single path's policy: the filter for ~16 bits per key, shrunk while that
+        // leaves fewer than 8 warps
+        int fw = filter_log2(n);
+        int w = 0;
+        for (; fw >= 5; --fw) {
+            const size_t base = fixed0 + (static_cast<size_t>(4) << fw);
+            if (base + stride[m] > B->dyn_limit) continue;
+            w = std::min(wcap, static_cast<int>((B->dyn_limit - base) / stride[m]));
+            if (w >= 8 || fw <= 10 || w >= wcap) break;
+        }
+        if (fw < 5 || w < 1) return bfail(B, QC_ERR_CAPACITY, "a molecule of the batch does not fit shared memory");
+        L.fw = fw;
+        act[m] = w;
         L.slots = off; off = align256(off + 2 * L.nb * 8);
         L.sets = off; off = align256(off + 2 * L.nb * 8);
         L.filter = off; off = align256(off + (static_cast<size_t>(4) << L.fw));
         L.ctr = off; off = align256(off + sizeof(qc::Counters));
         L.part = off; off = align256(off + static_cast<size_t>(qc::reduce_blocks(B->in[m].n_u)) * 4 * sizeof(double));
         L.sum = 0;
-        fbytes_max = std::max(fbytes_max, 4u << L.fw);
-        stride_max = std::max(stride_max, static_cast<unsigned>(qc::batch_warp_bytes(B->handles[m]->sp)));
         key_off[m + 1] = key_off[m] + B->in[m].n_u;
     }
     if (off > B->arena_cap) {
@@ -163,17 +176,13 @@ qc_status prepare(qc_batch* B) {
         P.ep.ctr = W.ctr;
         P.ep.T = H->d_T;
         P.ep.mode = QC_SAMPLE;
+        P.active_warps = act[m];
+        P.warp_stride = stride[m];
     }
-    B->filter_bytes = fbytes_max;
-    B->warp_stride = (stride_max + 15) / 16 * 16;
-    // launch shape
-    const size_t fixed = qc::smem_fixed_bytes() + B->filter_bytes;
-    if (fixed + B->warp_stride > B->dyn_limit) return bfail(B, QC_ERR_CAPACITY, "batch does not fit shared memory");
-    const int fit = static_cast<int>((B->dyn_limit - fixed) / B->warp_stride);
-    int warps = B->warps > 0 ? B->warps : 20;
-    warps = std::min(std::min(warps, fit), qc::kFilteredMaxWarps);
-    if (warps < 1) return bfail(B, QC_ERR_CAPACITY, "batch does not fit shared memory");
-    B->smem = fixed + static_cast<size_t>(warps) * B->warp_stride;
+    // launch shape: the widest CTA any molecule uses, all the dynamic shared memory
+    int warps = 1;
+    for (int m = 0; m < M; ++m) warps = std::max(warps, act[m]);
+    B->smem = B->dyn_limit;
     const int per_sm = qc::max_active_batch(B->precision, B->unroll, 32 * warps, B->smem);
     if (per_sm < 1) return bfail(B, QC_ERR_CAPACITY, "batch kernel cannot be resident with this shape");
     B->grid = per_sm * B->sm_count;
@@ -187,8 +196,8 @@ qc_status prepare(qc_batch* B) {
         const long long n = B->in[m].n_u;
         if (n <= 0) continue;
         long long chunk = static_cast<long long>(target / std::max<double>(1.0, static_cast<double>(mp[m].sp.pairs)));
-        chunk = std::max<long long>(chunk, warps);
-        chunk = (chunk + warps - 1) / warps * warps;
+        chunk = std::max<long long>(chunk, act[m]);
+        chunk = (chunk + act[m] - 1) / act[m] * act[m];
         for (long long s0 = 0; s0 < n; s0 += chunk) {
             qc::WorkUnit u{};
             u.mol = m;
@@ -252,8 +261,6 @@ qc_status enqueue(qc_batch* B, qc_eloc_summary* sums_host, cudaStream_t s, bool 
         bp.units = B->d_units;
         bp.n_units = B->n_units;
         bp.counter = B->d_counter;
-        bp.filter_bytes = B->filter_bytes;
-        bp.warp_stride = B->warp_stride;
         QB(qc::launch_eloc_batch(bp, B->precision, B->unroll, B->grid, B->warps_used, B->smem, s), "batch kernel");
     }
     if (timed) QB(cudaEventRecord(B->ev[2], s), "cudaEventRecord");
@@ -491,7 +498,7 @@ qc_status qc_batch_autotune(qc_batch* B, void* stream, int iters, int64_t* best3
                 st = prepare(B);
                 if (st == QC_ERR_CAPACITY) continue;
                 if (st != QC_OK) return st;
-                if (B->warps_used != w) continue;  // shape clipped by shared memory: tried already
+                if (B->warps_used < w) continue;  // cap above what any molecule fits: tried already
                 float t_best = 3.0e38f;
                 for (int it = 0; it < iters + 1; ++it) {
                     st = enqueue(B, nullptr, static_cast<cudaStream_t>(stream), true);

@@ -43,8 +43,8 @@ __global__ void __launch_bounds__(kRedThreads) reduce_batch_pass2(const MolParam
 // K4: many molecules in one persistent launch.  CTAs take work units (a block of samples
 // of one molecule) from a global counter, longest units first (the host orders them by
 // estimated cost).  For each unit the CTA loads that molecule's parameters and Bloom
-// filter into shared memory and rebuilds the CTA tables; its warps then run the unit's
-// samples with the same per-sample code as the single-molecule kernel.
+// filter into shared memory and rebuilds the CTA tables; as many warps as that molecule's
+// layout fits then run the unit's samples with the single-molecule per-sample code.
 template <int PREC, int U>
 __global__ void __launch_bounds__(640) eloc_batch_kernel(const __grid_constant__ BatchParams bp) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -52,8 +52,7 @@ __global__ void __launch_bounds__(640) eloc_batch_kernel(const __grid_constant__
     __shared__ int unit_id;
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + kOffBar);
     uint32_t* filt = reinterpret_cast<uint32_t*>(smem + kOffVar);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned char* wl = smem + kOffVar + bp.filter_bytes + static_cast<size_t>(warp) * bp.warp_stride;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         fence_barrier_init();
@@ -97,8 +96,14 @@ __global__ void __launch_bounds__(640) eloc_batch_kernel(const __grid_constant__
             return;
         }
         phase ^= 1u;
-        for (long long s = wu.s0 + warp; s < wu.s1; s += nw)
-            run_sample<PREC, U, true>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt);
+        // this molecule's layout: its own filter size and per-warp region; warps beyond
+        // what fits in shared memory sit this unit out
+        const int nw = mp.active_warps;
+        if (warp < nw) {
+            unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * mp.warp_stride;
+            for (long long s = wu.s0 + warp; s < wu.s1; s += nw)
+                run_sample<PREC, U, true>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt);
+        }
         __syncthreads();  // every warp done before the next unit replaces parameters and filter
     }
 }

@@ -95,6 +95,8 @@ struct MolParams {
     SysParams sp;
     TableParams tp;
     EvalParams ep;
+    int active_warps;    // warps of a CTA that work on this molecule's units (the rest idle)
+    unsigned warp_stride;  // this molecule's per-warp shared-memory region
 };
 struct WorkUnit {  // samples [s0, s1) of molecule mol
     int mol;
@@ -106,8 +108,6 @@ struct BatchParams {
     const WorkUnit* units;
     int n_units;
     unsigned* counter;         // next unit to hand out (zeroed before the launch)
-    unsigned filter_bytes;     // shared-memory filter region (largest filter of the batch)
-    unsigned warp_stride;      // per-warp shared-memory region (largest of the batch)
 };
 
 struct LaunchCfg {
