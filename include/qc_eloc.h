@@ -217,8 +217,9 @@ qc_status qc_eloc_eval_static(const double* h, const double* eri, double e_core,
 /* ---- the batched form: many molecules, one persistent launch ---------------------
  * A batch groups sample-space handles (same precision, same device); each keeps its
  * Hamiltonian resident.  One batched step is: a memset of the batch's workspace, one table
- * build over every molecule's keys, one persistent local-energy launch whose CTAs take
- * work units (blocks of samples of one molecule, longest first), and the two reduction
+ * build over every molecule's keys, one persistent local-energy launch that runs the
+ * molecules one after another (longest estimated time first; every CTA takes samples of
+ * the current molecule from a cursor and moves on when none are left), and the two reduction
  * passes -- five device operations for any number of molecules.  The per-sample
  * arithmetic is the single-molecule kernel's, so a molecule's results are bitwise the
  * same alone and in a batch.  Inputs are caller-owned device arrays, as for qc_eloc_eval.
@@ -231,16 +232,17 @@ qc_status qc_batch_destroy(qc_batch* batch);
 const char* qc_batch_last_error(const qc_batch* batch);
 qc_status qc_batch_set_inputs(qc_batch* batch, int mol, const uint64_t* samples, const int64_t* counts,
                               const double* psi, int64_t n_u, double* eloc);
-/* launch shape: unroll 0|2|4 (0 = 4), warps 0..20 (0 = as many as fit), units per CTA (0 = 8) */
-qc_status qc_batch_set_config(qc_batch* batch, int unroll, int warps, int units_per_cta);
-/* {unroll, warps, units_per_cta, grid, work units, dynamic shared memory bytes} */
+/* launch shape: unroll 0|2|4 (0 = 4), warps 0..20 (0 = as many as fit), samples a warp
+ * takes per fetch 0..1024 (0 = 1) */
+qc_status qc_batch_set_config(qc_batch* batch, int unroll, int warps, int chunk);
+/* {unroll, warps, chunk, grid, molecules with samples, dynamic shared memory bytes} */
 qc_status qc_batch_config(const qc_batch* batch, int64_t* cfg6);
 qc_status qc_batch_eval(qc_batch* batch, qc_eloc_summary* summaries, void* stream);
 qc_status qc_batch_graph_launch(qc_batch* batch, qc_eloc_summary* summaries, void* stream);
 /* device ms of the last eager step: {table build, local-energy kernel, reduction} */
 qc_status qc_batch_timings(qc_batch* batch, float* ms3);
 /* autotuner: times every candidate shape on this batch (best of `iters`), keeps the
- * fastest; best3 (may be NULL) receives {unroll, warps, units_per_cta} */
+ * fastest; best3 (may be NULL) receives {unroll, warps, chunk} */
 qc_status qc_batch_autotune(qc_batch* batch, void* stream, int iters, int64_t* best3);
 
 /* ---- the serving form: asynchronous requests, continuous batching -----------------

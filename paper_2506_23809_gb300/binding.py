@@ -307,15 +307,15 @@ def qc_batch_set_inputs(batch: QcBatch, mol: int, samples, counts, psi, eloc):
     batch.keep += [samples, counts, psi, eloc]
 
 
-def qc_batch_set_config(batch: QcBatch, unroll=0, warps=0, units_per_cta=0):
-    _bcheck(load_library().qc_batch_set_config(batch.ptr, int(unroll), int(warps), int(units_per_cta)), batch)
+def qc_batch_set_config(batch: QcBatch, unroll=0, warps=0, chunk=0):
+    _bcheck(load_library().qc_batch_set_config(batch.ptr, int(unroll), int(warps), int(chunk)), batch)
 
 
 def qc_batch_config(batch: QcBatch) -> dict:
     c = (ctypes.c_int64 * 6)()
     _bcheck(load_library().qc_batch_config(batch.ptr, c), batch)
-    return dict(unroll=int(c[0]), warps=int(c[1]), units_per_cta=int(c[2]), grid=int(c[3]),
-                units=int(c[4]), smem=int(c[5]))
+    return dict(unroll=int(c[0]), warps=int(c[1]), chunk=int(c[2]), grid=int(c[3]),
+                molecules=int(c[4]), smem=int(c[5]))
 
 
 def qc_batch_eval(batch: QcBatch, stream=None):
@@ -349,7 +349,7 @@ def qc_batch_autotune(batch: QcBatch, stream=None, iters: int = 2):
     s = stream or torch.cuda.current_stream()
     best = (ctypes.c_int64 * 3)()
     _bcheck(load_library().qc_batch_autotune(batch.ptr, ctypes.c_void_p(s.cuda_stream), int(iters), best), batch)
-    return dict(unroll=int(best[0]), warps=int(best[1]), units_per_cta=int(best[2]))
+    return dict(unroll=int(best[0]), warps=int(best[1]), chunk=int(best[2]))
 
 
 # ----------------------------------------------------------------------------------

@@ -1,10 +1,11 @@
 // qc_batch.cu -- the batched form: many molecules (each a qc_eloc handle, its integrals
 // already resident on the device) evaluated together.  One step is five device
 // operations whatever the number of molecules -- a memset of the batch arena, one table
-// build over every molecule's keys, one persistent local-energy launch over work units of
-// all molecules, and the two reduction passes -- and it can be captured once as a CUDA
-// graph.  The launch shape (unroll, warps per CTA, work-unit size) is picked by an
-// autotuner that times candidates on the batch itself.
+// build over every molecule's keys, one persistent local-energy launch that runs the
+// molecules one after another (largest first, every CTA taking samples of the current
+// molecule from its cursor), and the two reduction passes -- and it can be captured once
+// as a CUDA graph.  The launch shape (unroll, warps per CTA, samples per fetch) is picked
+// by an autotuner that times candidates on the batch itself.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,15 +51,13 @@ struct qc_batch {
     qc::MolParams* d_mols = nullptr;
     qc::MolWork* d_work = nullptr;
     long long* d_key_off = nullptr;
-    qc::WorkUnit* d_units = nullptr;
-    size_t units_cap = 0;
-    unsigned* d_counter = nullptr;
+    int* d_order = nullptr;  // molecules in run order
     unsigned char* d_arena = nullptr;
     size_t arena_cap = 0, arena_bytes = 0;
     qc_eloc_summary* d_sums = nullptr;
     // launch shape
-    int unroll = 4, warps = 0, units_per_cta = 8;
-    int warps_used = 0, grid = 0, n_units = 0, red_blocks = 1;
+    int unroll = 4, warps = 0, chunk = 1;
+    int warps_used = 0, grid = 0, n_run = 0, red_blocks = 1;
     long long n_keys = 0;
     size_t smem = 0;
     bool dirty = true;
@@ -89,15 +88,16 @@ int filter_log2(long long n) {
     return fw;
 }
 
-// Lay out every molecule's workspace in one arena, fill the parameter blocks, cut the
-// samples into work units of similar estimated cost and order them longest first.
+// Lay out every molecule's workspace in one arena (after the per-molecule sample cursors),
+// fill the parameter blocks and order the molecules by estimated running time, longest
+// first, so that the small ones fill the tail of the launch.
 qc_status prepare(qc_batch* B) {
     const int M = B->n_mol;
     B->red_blocks = 1;
     std::vector<qc::MolParams> mp(M);
     std::vector<qc::MolWork> mw(M);
     std::vector<long long> key_off(M + 1, 0);
-    size_t off = 0;
+    size_t off = align256(static_cast<size_t>(M) * sizeof(unsigned long long));  // sample cursors
     struct Lay { size_t slots, filter, sets, ctr, part, sum; unsigned long long nb; int fw; };
     std::vector<Lay> lay(M);
     const size_t fixed0 = qc::smem_fixed_bytes();
@@ -186,46 +186,21 @@ qc_status prepare(qc_batch* B) {
     const int per_sm = qc::max_active_batch(B->precision, B->unroll, 32 * warps, B->smem);
     if (per_sm < 1) return bfail(B, QC_ERR_CAPACITY, "batch kernel cannot be resident with this shape");
     B->grid = per_sm * B->sm_count;
-    // work units: ~units_per_cta units per CTA, each a block of samples of one molecule
-    double total = 0.0;
-    for (int m = 0; m < M; ++m) total += static_cast<double>(B->in[m].n_u) * static_cast<double>(mp[m].sp.pairs);
-    const double target = std::max(1.0, total / (static_cast<double>(B->grid) * B->units_per_cta));
-    std::vector<qc::WorkUnit> units;
-    std::vector<double> cost;
+    // run order: estimated time n_u * pairs / active warps, longest first
+    std::vector<int> order;
+    std::vector<double> cost(M, 0.0);
     for (int m = 0; m < M; ++m) {
-        const long long n = B->in[m].n_u;
-        if (n <= 0) continue;
-        long long chunk = static_cast<long long>(target / std::max<double>(1.0, static_cast<double>(mp[m].sp.pairs)));
-        chunk = std::max<long long>(chunk, act[m]);
-        chunk = (chunk + act[m] - 1) / act[m] * act[m];
-        for (long long s0 = 0; s0 < n; s0 += chunk) {
-            qc::WorkUnit u{};
-            u.mol = m;
-            u.s0 = s0;
-            u.s1 = std::min(n, s0 + chunk);
-            units.push_back(u);
-            cost.push_back(static_cast<double>(u.s1 - u.s0) * static_cast<double>(mp[m].sp.pairs));
-        }
+        if (B->in[m].n_u <= 0) continue;
+        order.push_back(m);
+        cost[m] = static_cast<double>(B->in[m].n_u) * static_cast<double>(mp[m].sp.pairs) / act[m];
     }
-    std::vector<size_t> order(units.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
-    std::vector<qc::WorkUnit> sorted(units.size());
-    for (size_t i = 0; i < order.size(); ++i) sorted[i] = units[order[i]];
-    B->n_units = static_cast<int>(sorted.size());
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    B->n_run = static_cast<int>(order.size());
     B->n_keys = key_off[M];
-    if (sorted.size() > B->units_cap) {
-        if (B->d_units) cudaFree(B->d_units);
-        B->d_units = nullptr;
-        B->units_cap = 0;
-        cudaError_t e = cudaMalloc(&B->d_units, std::max<size_t>(1, sorted.size()) * sizeof(qc::WorkUnit));
-        if (e != cudaSuccess) return bcuda(B, e, "cudaMalloc work units");
-        B->units_cap = sorted.size();
-    }
     cudaError_t e;
-    if (!sorted.empty()) {
-        e = cudaMemcpy(B->d_units, sorted.data(), sorted.size() * sizeof(qc::WorkUnit), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return bcuda(B, e, "copy work units");
+    if (!order.empty()) {
+        e = cudaMemcpy(B->d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bcuda(B, e, "copy run order");
     }
     e = cudaMemcpy(B->d_mols, mp.data(), M * sizeof(qc::MolParams), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bcuda(B, e, "copy molecule parameters");
@@ -252,15 +227,15 @@ qc_status enqueue(qc_batch* B, qc_eloc_summary* sums_host, cudaStream_t s, bool 
     } while (0)
     if (timed) QB(cudaEventRecord(B->ev[0], s), "cudaEventRecord");
     QB(cudaMemsetAsync(B->d_arena, 0, B->arena_bytes, s), "memset arena");
-    QB(cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned), s), "memset counter");
     QB(qc::launch_build_batch(B->d_mols, B->d_work, B->d_key_off, B->n_mol, B->n_keys, s), "batch build");
     if (timed) QB(cudaEventRecord(B->ev[1], s), "cudaEventRecord");
-    if (B->n_units > 0) {
+    if (B->n_run > 0) {
         qc::BatchParams bp{};
         bp.mols = B->d_mols;
-        bp.units = B->d_units;
-        bp.n_units = B->n_units;
-        bp.counter = B->d_counter;
+        bp.order = B->d_order;
+        bp.next = reinterpret_cast<unsigned long long*>(B->d_arena);  // cursors lead the arena
+        bp.n_mol = B->n_run;
+        bp.chunk = B->chunk;
         QB(qc::launch_eloc_batch(bp, B->precision, B->unroll, B->grid, B->warps_used, B->smem, s), "batch kernel");
     }
     if (timed) QB(cudaEventRecord(B->ev[2], s), "cudaEventRecord");
@@ -292,8 +267,9 @@ namespace {
 cudaError_t batch_alloc(qc_batch* B, int n_mol) {
     if (n_mol <= B->mol_cap) return cudaSuccess;
     for (void* p : {static_cast<void*>(B->d_mols), static_cast<void*>(B->d_work), static_cast<void*>(B->d_key_off),
-                    static_cast<void*>(B->d_sums)})
+                    static_cast<void*>(B->d_sums), static_cast<void*>(B->d_order)})
         if (p) cudaFree(p);
+    B->d_order = nullptr;
     B->d_mols = nullptr;
     B->d_work = nullptr;
     B->d_key_off = nullptr;
@@ -303,6 +279,7 @@ cudaError_t batch_alloc(qc_batch* B, int n_mol) {
     if (e == cudaSuccess) e = cudaMalloc(&B->d_work, n_mol * sizeof(qc::MolWork));
     if (e == cudaSuccess) e = cudaMalloc(&B->d_key_off, (n_mol + 1) * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&B->d_sums, n_mol * sizeof(qc_eloc_summary));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_order, n_mol * sizeof(int));
     if (e == cudaSuccess) B->mol_cap = n_mol;
     return e;
 }
@@ -349,7 +326,6 @@ qc_status qc_batch_create(qc_eloc* const* handles, int n_mol, qc_batch** out) {
     B->sm_count = handles[0]->sm_count;
     cudaError_t e = qc::prepare_batch_kernels(handles[0]->smem_optin, &B->dyn_limit);
     if (e == cudaSuccess) e = batch_alloc(B, n_mol);
-    if (e == cudaSuccess) e = cudaMalloc(&B->d_counter, sizeof(unsigned));
     for (auto& ev : B->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
     if (e != cudaSuccess) {
@@ -364,7 +340,7 @@ qc_status qc_batch_destroy(qc_batch* B) {
     if (!B) return QC_OK;
     drop_graph(B);
     for (void* p : {static_cast<void*>(B->d_mols), static_cast<void*>(B->d_work), static_cast<void*>(B->d_key_off),
-                    static_cast<void*>(B->d_units), static_cast<void*>(B->d_counter), static_cast<void*>(B->d_arena),
+                    static_cast<void*>(B->d_order), static_cast<void*>(B->d_arena),
                     static_cast<void*>(B->d_sums)})
         if (p) cudaFree(p);
     for (auto& ev : B->ev)
@@ -395,14 +371,14 @@ qc_status qc_batch_set_inputs(qc_batch* B, int mol, const uint64_t* samples, con
     return QC_OK;
 }
 
-qc_status qc_batch_set_config(qc_batch* B, int unroll, int warps, int units_per_cta) {
+qc_status qc_batch_set_config(qc_batch* B, int unroll, int warps, int chunk) {
     if (!B) return QC_ERR_ARG;
     if (unroll != 0 && unroll != 2 && unroll != 4) return bfail(B, QC_ERR_ARG, "unroll: 0, 2 or 4");
     if (warps < 0 || warps > qc::kFilteredMaxWarps) return bfail(B, QC_ERR_ARG, "warps: 0..20");
-    if (units_per_cta < 0 || units_per_cta > 1024) return bfail(B, QC_ERR_ARG, "units_per_cta: 0..1024");
+    if (chunk < 0 || chunk > 1024) return bfail(B, QC_ERR_ARG, "chunk: 0..1024");
     B->unroll = unroll ? unroll : 4;
     B->warps = warps;
-    B->units_per_cta = units_per_cta ? units_per_cta : 8;
+    B->chunk = chunk ? chunk : 1;
     B->dirty = true;
     drop_graph(B);
     return QC_OK;
@@ -473,23 +449,23 @@ qc_status qc_batch_config(const qc_batch* B, int64_t* cfg6) {
     if (!B || !cfg6) return QC_ERR_ARG;
     cfg6[0] = B->unroll;
     cfg6[1] = B->warps_used;
-    cfg6[2] = B->units_per_cta;
+    cfg6[2] = B->chunk;
     cfg6[3] = B->grid;
-    cfg6[4] = B->n_units;
+    cfg6[4] = B->n_run;
     cfg6[5] = static_cast<int64_t>(B->smem);
     return QC_OK;
 }
 
 // Time every candidate shape on this batch (eager evaluations on `stream`, main kernel
-// only, best of `iters`) and keep the fastest.  best3 (optional): {unroll, warps, units_per_cta}.
+// only, best of `iters`) and keep the fastest.  best3 (optional): {unroll, warps, chunk}.
 qc_status qc_batch_autotune(qc_batch* B, void* stream, int iters, int64_t* best3) {
     if (!B) return QC_ERR_ARG;
     if (iters < 1) iters = 1;
     const int warps_c[] = {8, 12, 16, 20};
-    const int units_c[] = {4, 8, 16};
+    const int units_c[] = {1, 4};  // samples per fetch
     const int unroll_c[] = {2, 4};
     float best = 3.0e38f;
-    int bu = 4, bw = 0, bp = 8;
+    int bu = 4, bw = 0, bp = 1;
     for (int ur : unroll_c)
         for (int w : warps_c)
             for (int up : units_c) {

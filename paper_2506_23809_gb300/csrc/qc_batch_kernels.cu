@@ -40,16 +40,19 @@ __global__ void __launch_bounds__(kRedThreads) reduce_batch_pass2(const MolParam
     reduce_pass2_body(P.ep, W.part, static_cast<qc_eloc_summary*>(W.sum), P.sp.pairs, blockIdx.x, W.nblk);
 }
 
-// K4: many molecules in one persistent launch.  CTAs take work units (a block of samples
-// of one molecule) from a global counter, longest units first (the host orders them by
-// estimated cost).  For each unit the CTA loads that molecule's parameters and Bloom
-// filter into shared memory and rebuilds the CTA tables; as many warps as that molecule's
-// layout fits then run the unit's samples with the single-molecule per-sample code.
+// K4: many molecules in one persistent launch, one molecule after another.  Every CTA
+// walks the molecules in the host's order (largest estimated cost first); for each one
+// that still has samples it loads the molecule's parameters and Bloom filter into shared
+// memory and rebuilds the CTA tables, then its warps take samples of that molecule from
+// the molecule's global cursor until none are left.  All CTAs therefore work on one or two
+// molecules at a time: their integral tables stay in L2 as in one plain launch, while
+// CTAs that run out of a molecule's samples start the next molecule without waiting for
+// the rest of the grid.
 template <int PREC, int U>
 __global__ void __launch_bounds__(640) eloc_batch_kernel(const __grid_constant__ BatchParams bp) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ MolParams mp;
-    __shared__ int unit_id;
+    __shared__ int skip;
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + kOffBar);
     uint32_t* filt = reinterpret_cast<uint32_t*>(smem + kOffVar);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -57,18 +60,18 @@ __global__ void __launch_bounds__(640) eloc_batch_kernel(const __grid_constant__
         mbar_init(bar, 1);
         fence_barrier_init();
     }
-    __syncthreads();
     unsigned phase = 0;
-    while (true) {
-        if (threadIdx.x == 0) unit_id = static_cast<int>(atomicAdd(bp.counter, 1u));
-        __syncthreads();
-        const int u = unit_id;
-        if (u >= bp.n_units) break;
-        const WorkUnit wu = bp.units[u];
-        const unsigned* src = reinterpret_cast<const unsigned*>(bp.mols + wu.mol);
+    for (int k = 0; k < bp.n_mol; ++k) {
+        __syncthreads();  // every warp is done with the previous molecule's shared data
+        const int m = bp.order[k];
+        const unsigned* src = reinterpret_cast<const unsigned*>(bp.mols + m);
         unsigned* dst = reinterpret_cast<unsigned*>(&mp);
         for (int t = threadIdx.x; t < static_cast<int>(sizeof(MolParams) / 4); t += blockDim.x) dst[t] = src[t];
+        if (threadIdx.x == 0)
+            skip = *reinterpret_cast<volatile unsigned long long*>(bp.next + k) >=
+                   static_cast<unsigned long long>(bp.mols[m].ep.n_u);
         __syncthreads();
+        if (skip) continue;  // other CTAs took all of this molecule's samples
         const unsigned fbytes = 4u << mp.tp.fw;
         if (threadIdx.x == 0) {
             mbar_expect_tx(bar, fbytes);
@@ -97,14 +100,21 @@ __global__ void __launch_bounds__(640) eloc_batch_kernel(const __grid_constant__
         }
         phase ^= 1u;
         // this molecule's layout: its own filter size and per-warp region; warps beyond
-        // what fits in shared memory sit this unit out
+        // what fits in shared memory sit it out
         const int nw = mp.active_warps;
         if (warp < nw) {
             unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * mp.warp_stride;
-            for (long long s = wu.s0 + warp; s < wu.s1; s += nw)
-                run_sample<PREC, U, true>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt);
+            const unsigned long long n_u = static_cast<unsigned long long>(mp.ep.n_u);
+            while (true) {
+                unsigned long long s0 = 0;
+                if (lane == 0) s0 = atomicAdd(bp.next + k, static_cast<unsigned long long>(bp.chunk));
+                s0 = __shfl_sync(0xffffffffu, s0, 0);
+                if (s0 >= n_u) break;
+                const unsigned long long s1 = s0 + bp.chunk < n_u ? s0 + bp.chunk : n_u;
+                for (unsigned long long s = s0; s < s1; ++s)
+                    run_sample<PREC, U, true>(mp.sp, mp.tp, mp.ep, static_cast<long long>(s), lane, smem, wl, filt);
+            }
         }
-        __syncthreads();  // every warp done before the next unit replaces parameters and filter
     }
 }
 

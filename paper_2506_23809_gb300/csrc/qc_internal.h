@@ -95,19 +95,15 @@ struct MolParams {
     SysParams sp;
     TableParams tp;
     EvalParams ep;
-    int active_warps;    // warps of a CTA that work on this molecule's units (the rest idle)
+    int active_warps;    // warps of a CTA that work on this molecule's samples (the rest idle)
     unsigned warp_stride;  // this molecule's per-warp shared-memory region
-};
-struct WorkUnit {  // samples [s0, s1) of molecule mol
-    int mol;
-    int pad;
-    long long s0, s1;
 };
 struct BatchParams {
     const MolParams* mols;
-    const WorkUnit* units;
-    int n_units;
-    unsigned* counter;         // next unit to hand out (zeroed before the launch)
+    const int* order;          // molecules in the order they are run (largest estimated cost first)
+    unsigned long long* next;  // per position in `order`: next sample to hand out (zeroed before the launch)
+    int n_mol;
+    int chunk;                 // samples a warp takes per fetch
 };
 
 struct LaunchCfg {
