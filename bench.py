@@ -70,7 +70,7 @@ def _dist():
 
 def _source_hash():
     h = hashlib.sha256()
-    for f in ("qc_kernels.cu", "qc_internal.h"):
+    for f in ("qc_kernels.cu", "qc_device.cuh", "qc_internal.h"):
         with open(os.path.join(ROOT, "paper_2506_23809_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

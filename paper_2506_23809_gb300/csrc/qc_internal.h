@@ -63,6 +63,7 @@ struct Counters {
     long long w;              // sum of counts (pass 1)
     double sce_re, sce_im;
     unsigned long long used;
+    unsigned long long next;  // next sample a warp of the local-energy kernel takes
 };
 
 struct EvalParams {

@@ -79,11 +79,18 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
     } else {
         __syncthreads();
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * main_warp_bytes(sp, FILTER);
-    for (long long s = static_cast<long long>(blockIdx.x) * nw + warp; s < ep.n_u;
-         s += static_cast<long long>(gridDim.x) * nw)
-        run_sample<PREC, U, FILTER>(sp, tp, ep, s, lane, smem, wl, filt);
+    // samples go to warps as they come free: one cursor for the grid, so a warp that drew
+    // cheap samples takes more of them and the launch ends with little tail
+    const unsigned long long n_u = static_cast<unsigned long long>(ep.n_u);
+    while (true) {
+        unsigned long long s = 0;
+        if (lane == 0) s = atomicAdd(&ep.ctr->next, 1ULL);
+        s = __shfl_sync(0xffffffffu, s, 0);
+        if (s >= n_u) break;
+        run_sample<PREC, U, FILTER>(sp, tp, ep, static_cast<long long>(s), lane, smem, wl, filt);
+    }
 }
 
 __global__ void __launch_bounds__(kRedThreads) reduce_pass1(EvalParams ep, double* part) {
