@@ -34,10 +34,16 @@ if ROOT not in sys.path:
 
 METRIC = "connected matrix elements/sec and E_loc samples/sec vs L2/HBM roofline; serve p50/p99"
 UNIT = "connected matrix elements/s"
-# Algorithmic integer operations per enumerated pair in the main kernel: form the
-# excitation's hash (1 XOR), derive the filter word index (1), read the filter word (1),
-# test its two bits (3), compact the survivors (1).
+# Algorithmic integer (ALU-pipe) operations per enumerated pair in the main kernel: form
+# the excitation's hash (1 XOR), derive the filter word offset (1), shift the filter word to
+# its three bit positions (3), combine them (1) and test the result (1).  The word itself
+# is read through the load/store pipe and is not counted.
 OPS_PER_PAIR = 7
+# Lanes of the integer ALU pipe per SM sub-partition.  ncu reports the ALU pipe at 61.4 %
+# of its peak while the SM issues 2.44 of 4 instructions per cycle: a 32-lane pipe would
+# need more ALU instructions than were issued in total, so the pipe is 16 lanes wide
+# (a warp instruction every other cycle).
+ALU_LANES = 16
 PROFILE_JSON = os.path.join(ROOT, "profiles", "eloc_main_n52_e14_u100k.json")
 
 
@@ -58,6 +64,10 @@ def _args():
     p.add_argument("--n-mol", type=int, default=64, help="batched form: molecules")
     p.add_argument("--requests", type=int, default=48, help="serve form: requests")
     p.add_argument("--rate", type=float, default=20.0, help="serve form: arrivals per second")
+    p.add_argument("--quantum", type=float, default=1e10,
+                   help="serve form: enumerated pairs per wave (0: one wave takes every ready request)")
+    p.add_argument("--oldest-pct", type=int, default=50,
+                   help="serve form: percent of a wave guaranteed to the oldest request")
     return p.parse_args()
 
 
@@ -356,7 +366,7 @@ def run_ours(args):
     peaks, peak_src = _measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = props.multi_processor_count * 4 * 32 * sm_max * 1e6     # integer issue, ops/s
+    peak_ops = props.multi_processor_count * 4 * ALU_LANES * sm_max * 1e6  # ALU pipe, ops/s
     main_s = statistics.mean(main_ms) / 1e3
     achieved = pairs_rank * OPS_PER_PAIR / main_s
     traffic = None
@@ -369,7 +379,7 @@ def run_ours(args):
                 "frac": achieved / peak_ops, "traffic": traffic,
                 "kernel": "eloc_main_kernel (filtered)" if cfg["kernel"] == 2 else "eloc_main_kernel (unfiltered)",
                 "ops_per_pair": OPS_PER_PAIR,
-                "peak_basis": f"{props.multi_processor_count} SMs x 4 schedulers x 32 lanes x {sm_max:.0f} MHz "
+                "peak_basis": f"{props.multi_processor_count} SMs x 4 sub-partitions x {ALU_LANES} ALU lanes x {sm_max:.0f} MHz "
                               f"({peak_src} sm_max_mhz)",
                 "kernel_ms": 1e3 * main_s, "kernel_pairs_per_s": pairs_rank / main_s,
                 "hbm_peak_gbs": peaks.get("hbm_gbs")}
@@ -533,7 +543,9 @@ def run_serve(args):
         begin = max(free_at, r["t"])
         free_at = begin + sv
         plain_lat.append(1e3 * (free_at - r["t"]))
-    srv = B.qc_server_create(0, 160 << 30, max_slots=64, n_streams=3)
+    srv = B.qc_server_create(0, 160 << 30, max_slots=64, n_streams=2)
+    B.qc_server_set_option(srv, B.QC_SRV_OPT_QUANTUM, int(args.quantum))
+    B.qc_server_set_option(srv, B.QC_SRV_OPT_OLDEST_PCT, int(args.oldest_pct))
     done = {}
     tickets = [None] * len(reqs)
     start = time.perf_counter()
@@ -563,6 +575,8 @@ def run_serve(args):
             "higher_is_better": True, "dtype": "f64",
             "config": {"workload": f"serve_{args.requests}_requests_poisson_{args.rate}_per_s",
                        "requests": len(reqs), "rate_per_s": args.rate, "budget_gb": 160,
+                       "wave_quantum_pairs": int(args.quantum), "oldest_share_pct": int(args.oldest_pct),
+                       "streams": 2,
                        "n_orb_range": [min(r["n_orb"] for r in reqs), max(r["n_orb"] for r in reqs)],
                        "max_samples": int(max(len(r["keys"]) for r in reqs)), "pairs_total": int(total_pairs)},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

@@ -232,7 +232,7 @@ qc_status qc_batch_destroy(qc_batch* batch);
 const char* qc_batch_last_error(const qc_batch* batch);
 qc_status qc_batch_set_inputs(qc_batch* batch, int mol, const uint64_t* samples, const int64_t* counts,
                               const double* psi, int64_t n_u, double* eloc);
-/* launch shape: unroll 0|2|4 (0 = 4), warps 0..20 (0 = as many as fit), samples a warp
+/* launch shape: unroll 0|2|4 (0 = 4), warps 0..20 (0 = 16, the widest CTA without register spills), samples a warp
  * takes per fetch 0..1024 (0 = 1) */
 qc_status qc_batch_set_config(qc_batch* batch, int unroll, int warps, int chunk);
 /* {unroll, warps, chunk, grid, molecules with samples, dynamic shared memory bytes} */
@@ -251,12 +251,18 @@ qc_status qc_batch_autotune(qc_batch* batch, void* stream, int iters, int64_t* b
  * arrival order while their device footprint fits `budget_bytes` and fewer than
  * `max_slots` are in flight, keeps each molecule's Hamiltonian resident for later requests
  * with the same nonzero mol_key (least-recently-used eviction when the budget needs
- * room), and launches every admitted request whose inputs are on the device as one batch
- * ("wave") on one of `n_streams` streams, so waves overlap on the GPU.  A request that can
- * never fit the budget is refused with QC_ERR_BUDGET at submit.  qc_eloc_poll waits up to
- * timeout_us for a ticket and returns QC_PENDING if it is not done; a finished ticket is
- * released by the poll that returns it.  A request's E_loc is bitwise the same alone and
- * in any mix (the batch runs the single-molecule per-sample code). */
+ * room), and launches admitted requests whose inputs are on the device as batches
+ * ("waves") on `n_streams` streams.  A wave holds about `quantum` enumerated pairs
+ * (QC_SRV_OPT_QUANTUM, default 1e10): the oldest request with a guaranteed share of it
+ * (QC_SRV_OPT_OLDEST_PCT, default half), the
+ * others least remaining work first; a request that does not fit whole runs a slice of its
+ * rows (against its whole sample table) and joins the next wave, so requests that arrive
+ * while a long one runs are served between its slices.  A request that can never fit the
+ * budget is refused with QC_ERR_BUDGET at submit.  qc_eloc_poll waits up to timeout_us for
+ * a ticket and returns QC_PENDING if it is not done; a finished ticket is released by the
+ * poll that returns it.  A request's E_loc and energy are bitwise the same alone and in
+ * any mix: the batch runs the single-molecule per-sample code, and a sliced request's
+ * Eq. 1 reduction runs once, over all of its rows, with its last slice. */
 typedef struct qc_server qc_server;
 typedef struct {
     const double* h;       /* host FP64 integrals as for qc_eloc_create: copied at submit   */
@@ -282,6 +288,9 @@ qc_status qc_eloc_submit(qc_server* server, const qc_eloc_job* job, uint64_t* ti
 qc_status qc_eloc_poll(qc_server* server, uint64_t ticket, qc_eloc_result* result, int timeout_us);
 /* {device bytes in use, requests in flight, requests waiting, resident molecules} */
 qc_status qc_server_stats(qc_server* server, uint64_t* stats4);
+#define QC_SRV_OPT_QUANTUM    1  /* enumerated pairs per wave, >= 0 (0: no slicing, one wave takes all) */
+#define QC_SRV_OPT_OLDEST_PCT 2  /* percent of a wave guaranteed to the oldest request, 1..100 (50) */
+qc_status qc_server_set_option(qc_server* server, int option, int64_t value);
 qc_status qc_server_destroy(qc_server* server);  /* finishes queued work first */
 
 /* Launch shape of the last evaluation on this handle: {kernel (1 direct, 2 filtered),

@@ -21,6 +21,8 @@ QC_FP64, QC_FP32_COMP = 0, 1
 QC_SAMPLE, QC_FULL = 0, 1
 QC_OPT_TIMING, QC_OPT_KERNEL, QC_OPT_FILTER_LOG2W, QC_OPT_WARPS, QC_OPT_UNROLL, QC_OPT_GRID = 1, 2, 3, 4, 5, 6
 QC_OPT_PREFILTER = 7
+QC_SRV_OPT_QUANTUM = 1
+QC_SRV_OPT_OLDEST_PCT = 2
 STATUS_NAMES = {0: "QC_OK", 1: "QC_PENDING", -1: "QC_ERR_ARG", -2: "QC_ERR_UNSORTED", -3: "QC_ERR_DUP",
                 -4: "QC_ERR_NELEC", -5: "QC_ERR_OOM", -6: "QC_ERR_BUDGET", -7: "QC_ERR_CUDA",
                 -8: "QC_ERR_ZERO_PSI", -9: "QC_ERR_MISSING", -10: "QC_ERR_TIMEOUT",
@@ -384,7 +386,9 @@ def _server_lib():
         lib.qc_eloc_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(qc_eloc_result), ctypes.c_int]
         lib.qc_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
         lib.qc_server_destroy.argtypes = [P]
-        for f in ("qc_server_create", "qc_eloc_submit", "qc_eloc_poll", "qc_server_stats", "qc_server_destroy"):
+        lib.qc_server_set_option.argtypes = [P, ctypes.c_int, ctypes.c_int64]
+        for f in ("qc_server_create", "qc_eloc_submit", "qc_eloc_poll", "qc_server_stats", "qc_server_destroy",
+                  "qc_server_set_option"):
             getattr(lib, f).restype = ctypes.c_int
         lib._qc_server_typed = True
     return lib
@@ -439,6 +443,12 @@ def qc_server_stats(server: QcServer) -> dict:
     s = (ctypes.c_uint64 * 4)()
     _server_lib().qc_server_stats(server.ptr, s)
     return dict(bytes_in_use=int(s[0]), in_flight=int(s[1]), waiting=int(s[2]), resident=int(s[3]))
+
+
+def qc_server_set_option(server: QcServer, option: int, value: int):
+    st = _server_lib().qc_server_set_option(server.ptr, int(option), int(value))
+    if st != QC_OK:
+        raise QcError(st, "qc_server_set_option failed")
 
 
 def qc_server_destroy(server: QcServer):

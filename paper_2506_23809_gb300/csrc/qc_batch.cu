@@ -27,6 +27,12 @@ struct BatchInput {
     const double* psi = nullptr;
     int64_t n_u = 0;
     double* eloc = nullptr;
+    // a slice of a long request (serving): rows [r0, r1) are evaluated against the whole
+    // table, counters accumulate in caller memory across slices, and the Eq. 1 reduction
+    // runs over all rows only with the last slice
+    int64_t r0 = 0, r1 = -1;  // r1 < 0: all rows
+    bool reduce = true;
+    qc::Counters* ctr = nullptr;  // null: the batch's own counters, zeroed every step
 };
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -101,7 +107,7 @@ qc_status prepare(qc_batch* B) {
     struct Lay { size_t slots, filter, sets, ctr, part, sum; unsigned long long nb; int fw; };
     std::vector<Lay> lay(M);
     const size_t fixed0 = qc::smem_fixed_bytes();
-    const int wcap = B->warps > 0 ? std::min(B->warps, qc::kFilteredMaxWarps) : qc::kFilteredMaxWarps;
+    const int wcap = B->warps > 0 ? std::min(B->warps, qc::kFilteredMaxWarps) : 16;  // 16: the spill-free bound
     std::vector<int> act(M);
     std::vector<unsigned> stride(M);
     for (int m = 0; m < M; ++m) {
@@ -131,12 +137,14 @@ qc_status prepare(qc_batch* B) {
         key_off[m + 1] = key_off[m] + B->in[m].n_u;
     }
     if (off > B->arena_cap) {
+        // grow with headroom: a reallocation (cudaFree) waits for the whole device
         if (B->d_arena) cudaFree(B->d_arena);
         B->d_arena = nullptr;
         B->arena_cap = 0;
-        cudaError_t e = cudaMalloc(&B->d_arena, off);
+        const size_t cap = align256(off + off / 2);
+        cudaError_t e = cudaMalloc(&B->d_arena, cap);
         if (e != cudaSuccess) return bcuda(B, e, "cudaMalloc batch arena");
-        B->arena_cap = off;
+        B->arena_cap = cap;
     }
     B->arena_bytes = off;
     unsigned char* A = B->d_arena;
@@ -149,10 +157,10 @@ qc_status prepare(qc_batch* B) {
         W.aset = reinterpret_cast<unsigned long long*>(A + L.sets);
         W.bset = W.aset + L.nb;
         W.filter = reinterpret_cast<uint32_t*>(A + L.filter);
-        W.ctr = reinterpret_cast<qc::Counters*>(A + L.ctr);
+        W.ctr = I.ctr ? I.ctr : reinterpret_cast<qc::Counters*>(A + L.ctr);
         W.part = reinterpret_cast<double*>(A + L.part);
         W.sum = B->d_sums + m;
-        W.nblk = qc::reduce_blocks(I.n_u);
+        W.nblk = I.reduce ? qc::reduce_blocks(I.n_u) : 0;
         B->red_blocks = std::max(B->red_blocks, W.nblk);
         qc::MolParams& P = mp[m];
         P.sp = H->sp;
@@ -178,6 +186,8 @@ qc_status prepare(qc_batch* B) {
         P.ep.mode = QC_SAMPLE;
         P.active_warps = act[m];
         P.warp_stride = stride[m];
+        P.r0 = I.r0;
+        P.r1 = I.r1 < 0 ? I.n_u : I.r1;
     }
     // launch shape: the widest CTA any molecule uses, all the dynamic shared memory
     int warps = 1;
@@ -190,9 +200,10 @@ qc_status prepare(qc_batch* B) {
     std::vector<int> order;
     std::vector<double> cost(M, 0.0);
     for (int m = 0; m < M; ++m) {
-        if (B->in[m].n_u <= 0) continue;
+        const long long rows = mp[m].r1 - mp[m].r0;
+        if (rows <= 0) continue;
         order.push_back(m);
-        cost[m] = static_cast<double>(B->in[m].n_u) * static_cast<double>(mp[m].sp.pairs) / act[m];
+        cost[m] = static_cast<double>(rows) * static_cast<double>(mp[m].sp.pairs) / act[m];
     }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     B->n_run = static_cast<int>(order.size());
@@ -266,6 +277,7 @@ namespace {
 // (Re)size the per-molecule device arrays for n_mol molecules.
 cudaError_t batch_alloc(qc_batch* B, int n_mol) {
     if (n_mol <= B->mol_cap) return cudaSuccess;
+    n_mol = std::max(n_mol, 64);  // room for a typical batch without reallocating
     for (void* p : {static_cast<void*>(B->d_mols), static_cast<void*>(B->d_work), static_cast<void*>(B->d_key_off),
                     static_cast<void*>(B->d_sums), static_cast<void*>(B->d_order)})
         if (p) cudaFree(p);
@@ -298,6 +310,22 @@ qc_status qc::batch_retarget(qc_batch* B, qc_eloc* const* handles, int n_mol) {
     B->n_mol = n_mol;
     B->handles.assign(handles, handles + n_mol);
     B->in.assign(n_mol, BatchInput{});
+    B->dirty = true;
+    drop_graph(B);
+    return QC_OK;
+}
+
+// Evaluate only rows [r0, r1) of molecule `mol` (set after its inputs), accumulate its
+// counters in `ctr` (device memory that the caller zeroes before the first slice), and run
+// its Eq. 1 reduction over all rows only when `reduce` is set.
+qc_status qc::batch_set_slice(qc_batch* B, int mol, long long r0, long long r1, bool reduce, qc::Counters* ctr) {
+    if (!B || mol < 0 || mol >= B->n_mol) return QC_ERR_ARG;
+    BatchInput& I = B->in[mol];
+    if (r0 < 0 || r1 < r0 || r1 > I.n_u) return bfail(B, QC_ERR_ARG, "bad row slice");
+    I.r0 = r0;
+    I.r1 = r1;
+    I.reduce = reduce;
+    I.ctr = ctr;
     B->dirty = true;
     drop_graph(B);
     return QC_OK;
@@ -361,6 +389,7 @@ qc_status qc_batch_set_inputs(qc_batch* B, int mol, const uint64_t* samples, con
     if (n_u > 0 && (mis(samples, 16) || mis(psi, 16) || mis(eloc, 16) || mis(counts, 8)))
         return bfail(B, QC_ERR_ARG, "device arrays must be 16-byte aligned (counts: 8)");
     BatchInput& I = B->in[mol];
+    I = BatchInput{};
     I.samples = samples;
     I.counts = counts;
     I.psi = psi;

@@ -48,8 +48,12 @@ __global__ void __launch_bounds__(kRedThreads) reduce_batch_pass2(const MolParam
 // molecules at a time: their integral tables stay in L2 as in one plain launch, while
 // CTAs that run out of a molecule's samples start the next molecule without waiting for
 // the rest of the grid.
-template <int PREC, int U>
-__global__ void __launch_bounds__(640) eloc_batch_kernel(const __grid_constant__ BatchParams bp) {
+// MAXT: the launch bound.  The per-molecule parameters live in shared memory, not in the
+// constant bank, so the sample code needs more registers than in the single-molecule
+// kernel: 512 threads (16 warps, 128 registers) keep it free of spills, 640 threads (20
+// warps, 96 registers) trade a few spills for more warps.
+template <int PREC, int U, int MAXT>
+__global__ void __launch_bounds__(MAXT) eloc_batch_kernel(const __grid_constant__ BatchParams bp) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ MolParams mp;
     __shared__ int skip;
@@ -69,7 +73,7 @@ __global__ void __launch_bounds__(640) eloc_batch_kernel(const __grid_constant__
         for (int t = threadIdx.x; t < static_cast<int>(sizeof(MolParams) / 4); t += blockDim.x) dst[t] = src[t];
         if (threadIdx.x == 0)
             skip = *reinterpret_cast<volatile unsigned long long*>(bp.next + k) >=
-                   static_cast<unsigned long long>(bp.mols[m].ep.n_u);
+                   static_cast<unsigned long long>(bp.mols[m].r1 - bp.mols[m].r0);
         __syncthreads();
         if (skip) continue;  // other CTAs took all of this molecule's samples
         const unsigned fbytes = 4u << mp.tp.fw;
@@ -104,15 +108,17 @@ __global__ void __launch_bounds__(640) eloc_batch_kernel(const __grid_constant__
         const int nw = mp.active_warps;
         if (warp < nw) {
             unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * mp.warp_stride;
-            const unsigned long long n_u = static_cast<unsigned long long>(mp.ep.n_u);
+            // rows [r0, r1) of this molecule: all of them, or one slice of a long request
+            const unsigned long long n_run = static_cast<unsigned long long>(mp.r1 - mp.r0);
+            const long long r0 = mp.r0;
             while (true) {
                 unsigned long long s0 = 0;
                 if (lane == 0) s0 = atomicAdd(bp.next + k, static_cast<unsigned long long>(bp.chunk));
                 s0 = __shfl_sync(0xffffffffu, s0, 0);
-                if (s0 >= n_u) break;
-                const unsigned long long s1 = s0 + bp.chunk < n_u ? s0 + bp.chunk : n_u;
+                if (s0 >= n_run) break;
+                const unsigned long long s1 = s0 + bp.chunk < n_run ? s0 + bp.chunk : n_run;
                 for (unsigned long long s = s0; s < s1; ++s)
-                    run_sample<PREC, U, true>(mp.sp, mp.tp, mp.ep, static_cast<long long>(s), lane, smem, wl, filt);
+                    run_sample<PREC, U, true>(mp.sp, mp.tp, mp.ep, r0 + static_cast<long long>(s), lane, smem, wl, filt);
             }
         }
     }
@@ -139,26 +145,33 @@ cudaError_t launch_reduce_batch(const MolParams* mols, const MolWork* work, int 
 }
 
 template <int PREC>
-static const void* batch_kernel_ptr(int unroll) {
-    if (unroll == 2) return (const void*)eloc_batch_kernel<PREC, 2>;
-    return (const void*)eloc_batch_kernel<PREC, 4>;
+static const void* batch_kernel_ptr(int unroll, int warps) {
+    if (warps > 16) return unroll == 2 ? (const void*)eloc_batch_kernel<PREC, 2, 640> : (const void*)eloc_batch_kernel<PREC, 4, 640>;
+    return unroll == 2 ? (const void*)eloc_batch_kernel<PREC, 2, 512> : (const void*)eloc_batch_kernel<PREC, 4, 512>;
+}
+
+template <int PREC, int U>
+static void launch_batch_u(const BatchParams& bp, int grid, int warps, size_t smem, cudaStream_t s) {
+    const dim3 g(grid), b(32 * warps);
+    if (warps > 16) eloc_batch_kernel<PREC, U, 640><<<g, b, smem, s>>>(bp);
+    else eloc_batch_kernel<PREC, U, 512><<<g, b, smem, s>>>(bp);
 }
 
 cudaError_t launch_eloc_batch(const BatchParams& bp, int precision, int unroll, int grid, int warps,
                               size_t smem, cudaStream_t s) {
-    const dim3 g(grid), b(32 * warps);
     if (precision == QC_FP64) {
-        if (unroll == 2) eloc_batch_kernel<QC_FP64, 2><<<g, b, smem, s>>>(bp);
-        else eloc_batch_kernel<QC_FP64, 4><<<g, b, smem, s>>>(bp);
+        if (unroll == 2) launch_batch_u<QC_FP64, 2>(bp, grid, warps, smem, s);
+        else launch_batch_u<QC_FP64, 4>(bp, grid, warps, smem, s);
     } else {
-        if (unroll == 2) eloc_batch_kernel<QC_FP32_COMP, 2><<<g, b, smem, s>>>(bp);
-        else eloc_batch_kernel<QC_FP32_COMP, 4><<<g, b, smem, s>>>(bp);
+        if (unroll == 2) launch_batch_u<QC_FP32_COMP, 2>(bp, grid, warps, smem, s);
+        else launch_batch_u<QC_FP32_COMP, 4>(bp, grid, warps, smem, s);
     }
     return cudaGetLastError();
 }
 
 int max_active_batch(int precision, int unroll, int threads, size_t smem) {
-    const void* f = precision == QC_FP64 ? batch_kernel_ptr<QC_FP64>(unroll) : batch_kernel_ptr<QC_FP32_COMP>(unroll);
+    const int w = threads / 32;
+    const void* f = precision == QC_FP64 ? batch_kernel_ptr<QC_FP64>(unroll, w) : batch_kernel_ptr<QC_FP32_COMP>(unroll, w);
     int n = 0;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) == cudaSuccess ? n : 0;
 }
@@ -168,8 +181,9 @@ cudaError_t prepare_batch_kernels(size_t max_smem, size_t* dyn_limit) {
     cudaError_t e = cudaSuccess;
     size_t lim = max_smem;
     for (int prec = 0; prec < 2; ++prec)
-        for (int unroll : {2, 4}) {
-            const void* f = prec == QC_FP64 ? batch_kernel_ptr<QC_FP64>(unroll) : batch_kernel_ptr<QC_FP32_COMP>(unroll);
+        for (int k = 0; k < 4; ++k) {
+            const int unroll = (k & 1) ? 4 : 2, w = (k & 2) ? 20 : 16;
+            const void* f = prec == QC_FP64 ? batch_kernel_ptr<QC_FP64>(unroll, w) : batch_kernel_ptr<QC_FP32_COMP>(unroll, w);
             cudaFuncAttributes a{};
             cudaError_t r = cudaFuncGetAttributes(&a, f);
             if (r != cudaSuccess) { e = r; continue; }

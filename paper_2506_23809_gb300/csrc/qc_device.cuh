@@ -843,31 +843,37 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     }
                     need_outer = false;
                 }
-                const int w = w0 + lane;
-                const bool wv = w < n2;
-                const unsigned vm = wv ? umask : 0u;
-                const uint32_t hw = (FILTER && wv) ? H[io + w] : 0u;
-                const uint32_t hw3 = hw >> 3;
-                const unsigned ccode = (static_cast<unsigned>(cls) << 24) | static_cast<unsigned>(w);
+                // steps over this block of U outer entries until its inner list ends or the
+                // candidate queue holds a batch for the resolution stages (a step adds at
+                // most 32 U entries, so the queue never exceeds 31 + 32 U)
+                const unsigned cbase = (static_cast<unsigned>(cls) << 24) | (static_cast<unsigned>(u0) << 12);
+                do {
+                    const int w = w0 + lane;
+                    const bool wv = w < n2;
+                    const unsigned vm = wv ? umask : 0u;
+                    const uint32_t hw = (FILTER && wv) ? H[io + w] : 0u;
+                    const uint32_t hw3 = hw >> 3;
+                    const unsigned ccode = cbase | static_cast<unsigned>(w);
 #pragma unroll
-                for (int k = 0; k < U; ++k) {
-                    bool pass;
-                    if (FILTER) {
-                        const uint32_t word = *reinterpret_cast<const uint32_t*>(
-                            reinterpret_cast<const unsigned char*>(filt) + ((hu3[k] ^ hw3) & wmask4));
-                        const uint32_t g = hu[k] ^ hw;
-                        const uint32_t t = __funnelshift_r(word, word, g) &
-                                           __funnelshift_r(word, word, g >> 27) &
-                                           __funnelshift_r(word, word, g >> 22);
-                        pass = ((t & (vm >> k)) & 1u) != 0u;
-                    } else {
-                        pass = ((vm >> k) & 1u) != 0u;
+                    for (int k = 0; k < U; ++k) {
+                        bool pass;
+                        if (FILTER) {
+                            const uint32_t word = *reinterpret_cast<const uint32_t*>(
+                                reinterpret_cast<const unsigned char*>(filt) + ((hu3[k] ^ hw3) & wmask4));
+                            const uint32_t g = hu[k] ^ hw;
+                            const uint32_t t = __funnelshift_r(word, word, g) &
+                                               __funnelshift_r(word, word, g >> 27) &
+                                               __funnelshift_r(word, word, g >> 22);
+                            pass = ((t & (vm >> k)) & 1u) != 0u;
+                        } else {
+                            pass = ((vm >> k) & 1u) != 0u;
+                        }
+                        const unsigned m = __ballot_sync(QC_FULLMASK, pass);
+                        if (pass) q[qn + __popc(m & ltmask)] = ccode + (static_cast<unsigned>(k) << 12);
+                        qn += __popc(m);
                     }
-                    const unsigned m = __ballot_sync(QC_FULLMASK, pass);
-                    if (pass) q[qn + __popc(m & ltmask)] = ccode | (static_cast<unsigned>(u0 + k) << 12);
-                    qn += __popc(m);
-                }
-                w0 += 32;
+                    w0 += 32;
+                } while (w0 < n2 && qn < 32);
                 if (w0 >= n2) {
                     w0 = 0;
                     u0 += U;

@@ -53,4 +53,6 @@ qc_status ensure_workspace(qc_eloc* H, long long n_u, long long n_table, int fw)
 qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, LaunchCfg& c, int& fw);
 // point a batch at another set of handles, reusing its device allocations
 qc_status batch_retarget(qc_batch* B, qc_eloc* const* handles, int n_mol);
+// one slice of a molecule's rows per step (the serving form's long requests)
+qc_status batch_set_slice(qc_batch* B, int mol, long long r0, long long r1, bool reduce, Counters* ctr);
 }  // namespace qc

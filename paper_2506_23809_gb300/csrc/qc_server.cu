@@ -6,13 +6,17 @@
 //   * residency -- a molecule's Hamiltonian (a qc_eloc handle) stays on the device for
 //     later requests with the same molecule key, evicted least-recently-used when the
 //     budget needs the room;
-//   * waves -- every admitted request whose inputs are on the device joins the next wave,
-//     one qc_batch launch on one of several streams; new waves start while earlier ones
-//     are still running, so their work overlaps on the GPU;
+//   * waves -- admitted requests whose inputs are on the device join the next wave, one
+//     qc_batch launch on one of several streams; a wave holds about `quantum` enumerated
+//     pairs: the oldest request first (a guaranteed share of the quantum), then the others with
+//     the least remaining work first.  A request too long for the room left runs a slice of
+//     its rows against its whole sample table and comes back for the next wave, so a long
+//     request never holds the GPU for more than a wave while short ones wait;
 //   * completion -- found by polling CUDA events (no blocking device waits); results are
 //     copied to the caller's host buffers and the request's memory is released.
-// Because a batch runs the single-molecule per-sample code, a request's E_loc is bitwise
-// the same alone and in any mix.
+// Because a batch runs the single-molecule per-sample code, and a sliced request's Eq. 1
+// reduction runs once over all of its rows in its last wave, a request's E_loc and energy
+// are bitwise the same alone and in any mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -59,6 +63,10 @@ struct Request {
     int64_t* d_counts = nullptr;
     double* d_psi = nullptr;
     double* d_eloc = nullptr;
+    qc::Counters* d_ctr = nullptr;  // accumulates over the request's slices
+    long long next_row = 0;         // rows [0, next_row) are evaluated
+    long long slice_end = 0;        // end of the slice in flight
+    long long pairs_per_row = 1;
     qc_eloc_result result{};
     bool done = false;
 };
@@ -108,6 +116,8 @@ struct qc_server {
     std::map<uint64_t, std::unique_ptr<Resident>> residents;  // by molecule key
     uint64_t next_ticket = 1;
     int active = 0;                      // admitted and not finished
+    long long quantum = 10000000000LL;   // enumerated pairs per wave (0: no slicing)
+    int oldest_pct = 50;                 // share of a wave guaranteed to the oldest request
     bool stop = false;
     std::thread worker;
     cudaError_t fatal = cudaSuccess;
@@ -121,6 +131,8 @@ void finish_request(qc_server* S, Request* r, cudaStream_t s) {
     if (r->d_counts) cudaFreeAsync(r->d_counts, s);
     if (r->d_psi) cudaFreeAsync(r->d_psi, s);
     if (r->d_eloc) cudaFreeAsync(r->d_eloc, s);
+    if (r->d_ctr) cudaFreeAsync(r->d_ctr, s);
+    r->d_ctr = nullptr;
     r->d_keys = nullptr;
     r->d_counts = nullptr;
     r->d_psi = nullptr;
@@ -199,11 +211,13 @@ void admit(qc_server* S) {
         S->used += r->bytes;
         S->active++;
         const size_t n = static_cast<size_t>(j.n_u);
-        cudaError_t e = cudaSuccess;
+        r->pairs_per_row = std::max<long long>(1, qc_eloc_pairs_per_sample(res->handle));
         cudaStream_t up = S->upload;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_ctr), sizeof(qc::Counters), up);
+        if (e == cudaSuccess) e = cudaMemsetAsync(r->d_ctr, 0, sizeof(qc::Counters), up);
         if (n > 0) {
             // stream-ordered allocations: no device-wide synchronisation while waves run
-            e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_keys), n * 16, up);
+            if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_keys), n * 16, up);
             if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_counts), n * 8, up);
             if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_psi), n * 16, up);
             if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_eloc), n * 16, up);
@@ -222,11 +236,49 @@ void admit(qc_server* S) {
     }
 }
 
-// Launch the ready requests of one precision as one wave (one batch) on a free lane.
+// Launch one wave on a free lane: requests of one precision, about `quantum` enumerated
+// pairs in all -- the oldest request first with at least `oldest_pct` percent of it, then
+// the others by least remaining work; a request that does not fit whole runs a slice of
+// its rows.
 void launch_wave(qc_server* S, Lane& L, int lane_index) {
-    std::vector<Request*> take, keep;
     const int prec = S->ready.front()->job.precision;
-    for (Request* r : S->ready) (r->job.precision == prec ? take : keep).push_back(r);
+    std::vector<Request*> cand, keep;
+    for (Request* r : S->ready) (r->job.precision == prec ? cand : keep).push_back(r);
+    auto rows_left = [](const Request* r) { return r->job.n_u - r->next_row; };
+    auto work_left = [&](const Request* r) {
+        return static_cast<double>(rows_left(r)) * static_cast<double>(r->pairs_per_row);
+    };
+    std::stable_sort(cand.begin(), cand.end(), [](const Request* a, const Request* b) { return a->ticket < b->ticket; });
+    if (cand.size() > 1)
+        std::stable_sort(cand.begin() + 1, cand.end(),
+                         [&](const Request* a, const Request* b) { return work_left(a) < work_left(b); });
+    // the oldest request is guaranteed its share of the quantum (no request starves); the others
+    // fill the rest, least remaining work first; room left over goes back to the oldest
+    const double Q = S->quantum > 0 ? static_cast<double>(S->quantum) : 1e300;
+    Request* oldest = cand.front();
+    const double reserve = std::min(work_left(oldest), 0.01 * S->oldest_pct * Q);
+    double room = Q - reserve;
+    std::vector<Request*> take{oldest};
+    for (size_t i = 1; i < cand.size(); ++i) {
+        Request* r = cand[i];
+        long long rows = rows_left(r);
+        if (rows > 0 && work_left(r) > room)
+            rows = std::max<long long>(0, static_cast<long long>(room / static_cast<double>(r->pairs_per_row)));
+        if (rows == 0 && rows_left(r) > 0) {
+            keep.push_back(r);  // no room left in this wave
+            continue;
+        }
+        r->slice_end = r->next_row + rows;
+        room -= static_cast<double>(rows) * static_cast<double>(r->pairs_per_row);
+        take.push_back(r);
+    }
+    {
+        long long rows = rows_left(oldest);
+        const double share = reserve + std::max(room, 0.0);
+        if (work_left(oldest) > share)
+            rows = std::max<long long>(1, static_cast<long long>(share / static_cast<double>(oldest->pairs_per_row)));
+        oldest->slice_end = oldest->next_row + rows;
+    }
     S->ready.swap(keep);
     std::vector<qc_eloc*> hs;
     for (Request* r : take) hs.push_back(r->res->handle);
@@ -237,6 +289,9 @@ void launch_wave(qc_server* S, Lane& L, int lane_index) {
     for (size_t m = 0; m < take.size() && st == QC_OK; ++m) {
         Request* r = take[m];
         st = qc_batch_set_inputs(B, static_cast<int>(m), r->d_keys, r->d_counts, r->d_psi, r->job.n_u, r->d_eloc);
+        if (st == QC_OK)
+            st = qc::batch_set_slice(B, static_cast<int>(m), r->next_row, r->slice_end, r->slice_end == r->job.n_u,
+                                     r->d_ctr);
     }
     const double t0 = now_s();
     // the wave's stream waits for the uploads of its requests
@@ -252,7 +307,8 @@ void launch_wave(qc_server* S, Lane& L, int lane_index) {
         S->cv_done.notify_all();
         return;
     }
-    for (Request* r : take) r->result.t_start = t0;
+    for (Request* r : take)
+        if (r->result.t_start == 0.0) r->result.t_start = t0;
     Wave w;
     w.reqs = take;
     w.stream = lane_index;
@@ -273,6 +329,11 @@ bool retire(qc_server* S) {
         const double t = now_s();
         for (size_t m = 0; m < it->reqs.size(); ++m) {
             Request* r = it->reqs[m];
+            if (q == cudaSuccess && r->slice_end < r->job.n_u) {  // more slices to go
+                r->next_row = r->slice_end;
+                S->ready.push_back(r);
+                continue;
+            }
             cudaError_t e = q;
             if (e == cudaSuccess && r->job.eloc_out && r->job.n_u > 0) {
                 e = cudaMemcpyAsync(r->job.eloc_out, r->d_eloc, static_cast<size_t>(r->job.n_u) * 16,
@@ -388,6 +449,15 @@ qc_status qc_eloc_poll(qc_server* S, uint64_t ticket, qc_eloc_result* result, in
     *result = r->result;
     S->all.erase(it);
     delete r;
+    return QC_OK;
+}
+
+qc_status qc_server_set_option(qc_server* S, int option, int64_t value) {
+    if (!S) return QC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (option == QC_SRV_OPT_QUANTUM && value >= 0) S->quantum = value;
+    else if (option == QC_SRV_OPT_OLDEST_PCT && value >= 1 && value <= 100) S->oldest_pct = static_cast<int>(value);
+    else return QC_ERR_ARG;
     return QC_OK;
 }
 

@@ -1,7 +1,8 @@
 """The serving form: requests submitted at any time, continuous batching on several
-streams.  A request's result must be the same alone and in a mix of other molecules
-(bitwise, since batches run the single-molecule per-sample code), and equal to the
-handle API's; a request that can never fit the memory budget is refused."""
+streams.  A request's result must be the same alone, in a mix of other molecules and cut
+into row slices over many waves (bitwise, since batches run the single-molecule per-sample
+code and the Eq. 1 reduction runs once over all rows), and equal to the handle API's; a
+request that can never fit the memory budget is refused."""
 import time
 
 import numpy as np
@@ -97,5 +98,36 @@ def test_budget_refusal_and_eviction(B):
         for k, (r, e) in enumerate(outs):
             assert r["status"] == 0
             assert np.allclose(e - outs[0][1], 0.1 * k, rtol=0, atol=1e-12)   # e_core shifts E_loc
+    finally:
+        B.qc_server_destroy(srv)
+
+
+def test_sliced_requests_equal_whole(B):
+    """With a small wave quantum every request runs as many row slices in many waves (and
+    mixes with the others slice by slice); E_loc and the Eq. 1 energy stay bitwise those of
+    one whole evaluation through the handle API."""
+    import torch
+    specs = [(40, 12, 3000, 2101), (52, 14, 2000, 2201), (28, 10, 1500, 2301)]
+    mols = [_mol(*sp) for sp in specs]
+    srv = B.qc_server_create(0, 8 << 30, max_slots=16, n_streams=2)
+    try:
+        with pytest.raises(B.QcError):
+            B.qc_server_set_option(srv, B.QC_SRV_OPT_QUANTUM, -1)
+        B.qc_server_set_option(srv, B.QC_SRV_OPT_QUANTUM, 2_000_000)   # a few hundred rows per wave
+        tickets = [B.qc_eloc_submit(srv, m[0].h, m[0].eri, 0.0, sp[0], sp[1], m[1], m[2], m[3], mol_key=k + 1)
+                   for k, (sp, m) in enumerate(zip(specs, mols))]
+        res = [_wait(B, srv, t) for t in tickets]
+        for sp, m, (r, e) in zip(specs, mols, res):
+            assert r["status"] == 0
+            h = B.qc_eloc_create(m[0].h, m[0].eri, 0.0, sp[0], sp[1])
+            try:
+                e1, _ = B.qc_eloc_eval(h, B.keys_to_tensor(m[1]), torch.from_numpy(m[2]).cuda(),
+                                       torch.from_numpy(m[3]).cuda())
+                s1 = B.qc_eloc_summary_read(h)
+                assert np.array_equal(e.view(np.uint64), e1.cpu().numpy().view(np.uint64)), sp
+                for f in ("e_re", "e_im", "var", "w", "n_hits", "n_pairs", "n_missing"):
+                    assert r[f] == s1[f], (sp, f)
+            finally:
+                B.qc_eloc_destroy(h)
     finally:
         B.qc_server_destroy(srv)
