@@ -684,7 +684,7 @@ __device__ __forceinline__ float2 inv_psi32(double2 p) {
 // batches (so lanes of one batch follow the same path).  All three stages sit at one
 // place in the loop; the end of a sample flushes the partial batches through the same code.
 constexpr int kCandCap = 160;  // >= 31 + 32 * 4 (the largest U with a single flush site)
-constexpr size_t kWarpQueues = 4 * kCandCap + 2 * 64 * 8;  // candidate + two hit queues
+constexpr size_t kWarpQueues = 4 * kCandCap + 64 * 8;  // candidate queue + hit queue
 
 __host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filter) {
     // hash lists (u32) and, for the two single lists, their compaction maps (u16)
@@ -705,8 +705,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     const unsigned long long* T64 = reinterpret_cast<const unsigned long long*>(smem + kOffT);
     const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
     uint32_t* q = reinterpret_cast<uint32_t*>(wl + 256);
-    uint2* sq = reinterpret_cast<uint2*>(wl + 256 + 4 * kCandCap);
-    uint2* dq = sq + 64;
+    uint2* hq = reinterpret_cast<uint2*>(wl + 256 + 4 * kCandCap);
     uint32_t* H = reinterpret_cast<uint32_t*>(wl + 256 + kWarpQueues);
     // list offsets inside H: 0 zero | SA | SB | PAo | PAv | PBo | PBv
     const int oSA = 1, oSB = oSA + sp.nsa, oPAo = oSB + sp.nsb, oPAv = oPAo + sp.npoa;
@@ -802,7 +801,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     const float2 ip32 = inv_psi32(psix);
     const uint32_t hx32 = static_cast<uint32_t>(hx);
     Acc acc{};
-    int qn = 0, nsq = 0, ndq = 0;
+    int qn = 0, nh = 0;
     // iterator over (class, outer block u0, inner block w0)
     int cls = -1, oo = 0, n1 = 0, io = 0, n2 = 0, u0 = 0, w0 = 0;
     bool done = false, need_class = true, need_outer = true;
@@ -883,33 +882,25 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
             }
         }
         __syncwarp();
-        // resolution stages (hit queues first, so neither can exceed 63 entries)
+        // resolution stages (the hit queue first, so it never exceeds 63 entries)
         while (true) {
-            if (nsq >= 32 || (done && qn == 0 && nsq > 0)) {
-                const int n = nsq < 32 ? nsq : 32;
+            if (nh >= 32 || (done && qn == 0 && nh > 0)) {
+                // hits: key check, psi(x') and integrals, then the element.  Singles are
+                // found only in the first two classes, so a batch rarely mixes the kinds.
+                const int n = nh < 32 ? nh : 32;
                 const bool v = lane < n;
-                const uint2 e = v ? sq[lane] : make_uint2(0u, 0u);
+                const uint2 e = v ? hq[lane] : make_uint2(0u, 0u);
                 __syncwarp();
-                if (lane < nsq - n) sq[lane] = sq[n + lane];
-                nsq -= n;
+                if (lane < nh - n) hq[lane] = hq[n + lane];
+                nh -= n;
                 __syncwarp();
                 if (v)
                     verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc,
                                          [&](double& h64, float& h32, bool& sneg) {
-                                             single_element<PREC>(e.x, prefix_parity(x), sp, wl, h64, h32, sneg);
-                                         });
-            } else if (ndq >= 32 || (done && qn == 0 && ndq > 0)) {
-                const int n = ndq < 32 ? ndq : 32;
-                const bool v = lane < n;
-                const uint2 e = v ? dq[lane] : make_uint2(0u, 0u);
-                __syncwarp();
-                if (lane < ndq - n) dq[lane] = dq[n + lane];
-                ndq -= n;
-                __syncwarp();
-                if (v)
-                    verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc,
-                                         [&](double& h64, float& h32, bool& sneg) {
-                                             double_element<PREC>(e.x, prefix_parity(x), sp, h64, h32, sneg);
+                                             if ((e.x >> 16) == 0xFFFFu)
+                                                 single_element<PREC>(e.x, prefix_parity(x), sp, wl, h64, h32, sneg);
+                                             else
+                                                 double_element<PREC>(e.x, prefix_parity(x), sp, h64, h32, sneg);
                                          });
             } else if (qn >= 32 || (done && qn > 0)) {
                 const int n = qn < 32 ? qn : 32;
@@ -927,13 +918,9 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     if (row < 0 && ep.mode == QC_FULL) acc.missing++;
                 }
                 const bool hit = row >= 0;
-                const bool single = (orbs >> 16) == 0xFFFFu;
-                const unsigned ms = __ballot_sync(QC_FULLMASK, hit && single);
-                const unsigned md = __ballot_sync(QC_FULLMASK, hit && !single);
-                if (hit && single) sq[nsq + __popc(ms & ltmask)] = make_uint2(orbs, static_cast<unsigned>(row));
-                if (hit && !single) dq[ndq + __popc(md & ltmask)] = make_uint2(orbs, static_cast<unsigned>(row));
-                nsq += __popc(ms);
-                ndq += __popc(md);
+                const unsigned mh = __ballot_sync(QC_FULLMASK, hit);
+                if (hit) hq[nh + __popc(mh & ltmask)] = make_uint2(orbs, static_cast<unsigned>(row));
+                nh += __popc(mh);
                 __syncwarp();
             } else {
                 break;
