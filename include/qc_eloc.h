@@ -256,8 +256,9 @@ qc_status qc_batch_autotune(qc_batch* batch, void* stream, int iters, int64_t* b
  * (QC_SRV_OPT_QUANTUM, default 1e10): the oldest request with a guaranteed share of it
  * (QC_SRV_OPT_OLDEST_PCT, default half), the
  * others least remaining work first; a request that does not fit whole runs a slice of its
- * rows (against its whole sample table) and joins the next wave, so requests that arrive
- * while a long one runs are served between its slices.  A request that can never fit the
+ * rows (against its whole sample table) and joins the next wave, and after a wave that ran
+ * a slice the ready short requests (at most half a quantum) get a wave of their own, so
+ * requests that arrive while a long one runs are served between its slices.  A request that can never fit the
  * budget is refused with QC_ERR_BUDGET at submit.  qc_eloc_poll waits up to timeout_us for
  * a ticket and returns QC_PENDING if it is not done; a finished ticket is released by the
  * poll that returns it.  A request's E_loc and energy are bitwise the same alone and in

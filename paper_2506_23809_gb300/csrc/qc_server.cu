@@ -11,7 +11,9 @@
 //     pairs: the oldest request first (a guaranteed share of the quantum), then the others with
 //     the least remaining work first.  A request too long for the room left runs a slice of
 //     its rows against its whole sample table and comes back for the next wave, so a long
-//     request never holds the GPU for more than a wave while short ones wait;
+//     request never holds the GPU for more than a wave while short ones wait; after a wave
+//     that ran a slice, the short requests that are ready (at most half a quantum each) get
+//     a wave of their own before the next slice;
 //   * completion -- found by polling CUDA events (no blocking device waits); results are
 //     copied to the caller's host buffers and the request's memory is released.
 // Because a batch runs the single-molecule per-sample code, and a sliced request's Eq. 1
@@ -118,6 +120,7 @@ struct qc_server {
     int active = 0;                      // admitted and not finished
     long long quantum = 10000000000LL;   // enumerated pairs per wave (0: no slicing)
     int oldest_pct = 50;                 // share of a wave guaranteed to the oldest request
+    bool last_wave_sliced = false;       // the last wave ran a slice of a long request
     bool stop = false;
     std::thread worker;
     cudaError_t fatal = cudaSuccess;
@@ -236,6 +239,8 @@ void admit(qc_server* S) {
     }
 }
 
+void run_wave(qc_server* S, Lane& L, int lane_index, int prec, const std::vector<Request*>& take);
+
 // Launch one wave on a free lane: requests of one precision, about `quantum` enumerated
 // pairs in all -- the oldest request first with at least `oldest_pct` percent of it, then
 // the others by least remaining work; a request that does not fit whole runs a slice of
@@ -252,9 +257,35 @@ void launch_wave(qc_server* S, Lane& L, int lane_index) {
     if (cand.size() > 1)
         std::stable_sort(cand.begin() + 1, cand.end(),
                          [&](const Request* a, const Request* b) { return work_left(a) < work_left(b); });
+    const double Q = S->quantum > 0 ? static_cast<double>(S->quantum) : 1e300;
+    // after a wave that ran a slice of a long request, short requests that are ready get a
+    // wave of their own first: they wait for at most one slice, never for a whole long job
+    if (S->quantum > 0 && S->last_wave_sliced) {
+        std::vector<Request*> small, rest;
+        for (Request* r : cand) (r->next_row == 0 && work_left(r) <= 0.5 * Q ? small : rest).push_back(r);
+        if (!small.empty()) {
+            std::stable_sort(small.begin(), small.end(),
+                             [&](const Request* a, const Request* b) { return work_left(a) < work_left(b); });
+            std::vector<Request*> take;
+            double room = Q;
+            for (Request* r : small) {
+                if (!take.empty() && work_left(r) > room) {
+                    rest.push_back(r);
+                    continue;
+                }
+                r->slice_end = r->job.n_u;
+                room -= work_left(r);
+                take.push_back(r);
+            }
+            for (Request* r : rest) keep.push_back(r);
+            S->ready.swap(keep);
+            S->last_wave_sliced = false;
+            run_wave(S, L, lane_index, prec, take);
+            return;
+        }
+    }
     // the oldest request is guaranteed its share of the quantum (no request starves); the others
     // fill the rest, least remaining work first; room left over goes back to the oldest
-    const double Q = S->quantum > 0 ? static_cast<double>(S->quantum) : 1e300;
     Request* oldest = cand.front();
     const double reserve = std::min(work_left(oldest), 0.01 * S->oldest_pct * Q);
     double room = Q - reserve;
@@ -280,6 +311,14 @@ void launch_wave(qc_server* S, Lane& L, int lane_index) {
         oldest->slice_end = oldest->next_row + rows;
     }
     S->ready.swap(keep);
+    bool sliced = false;
+    for (Request* r : take) sliced = sliced || r->slice_end < r->job.n_u || r->next_row > 0;
+    S->last_wave_sliced = sliced;
+    run_wave(S, L, lane_index, prec, take);
+}
+
+// Launch `take` (with their row slices set) as one batch on lane L.
+void run_wave(qc_server* S, Lane& L, int lane_index, int prec, const std::vector<Request*>& take) {
     std::vector<qc_eloc*> hs;
     for (Request* r : take) hs.push_back(r->res->handle);
     qc_status st = QC_OK;
