@@ -102,6 +102,9 @@ typedef int qc_status;
 #define QC_OPT_GRID          6  /* 0 auto, else CTAs of the main kernel */
 #define QC_OPT_PREFILTER     7  /* 1 (default): drop single excitations whose new spin string no
                                    table key has, and the doubles built on them; 0: off */
+#define QC_OPT_LEAN          8  /* filtered kernel's per-warp lists: 0 auto (the layout that fits
+                                   more warps), 1 stored pair lists, 2 pair lists formed on the
+                                   fly from per-orbital values (same results, less shared memory) */
 
 typedef struct qc_eloc qc_eloc;
 
@@ -294,8 +297,9 @@ qc_status qc_server_stats(qc_server* server, uint64_t* stats4);
 qc_status qc_server_set_option(qc_server* server, int option, int64_t value);
 qc_status qc_server_destroy(qc_server* server);  /* finishes queued work first */
 
-/* Launch shape of the last evaluation on this handle: {kernel (1 direct, 2 filtered),
- * grid CTAs, warps per CTA, unroll, dynamic shared memory bytes, log2 filter words}. */
+/* Launch shape of the last evaluation on this handle: {kernel (1 direct, 2 filtered,
+ * 3 filtered with pair lists formed on the fly), grid CTAs, warps per CTA, unroll, dynamic
+ * shared memory bytes, log2 filter words}. */
 qc_status qc_eloc_last_config(const qc_eloc* handle, int64_t* cfg6);
 
 #ifdef __cplusplus

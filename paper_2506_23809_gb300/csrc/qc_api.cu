@@ -263,6 +263,10 @@ qc_status qc_eloc_set_option(qc_eloc* H, int option, int64_t value) {
             H->opt_unroll = static_cast<int>(value);
             return QC_OK;
         case QC_OPT_PREFILTER: H->opt_prefilter = value ? 1 : 0; return QC_OK;
+        case QC_OPT_LEAN:
+            if (value < 0 || value > 2) return fail(H, QC_ERR_ARG, "QC_OPT_LEAN: 0, 1 or 2");
+            H->opt_lean = static_cast<int>(value);
+            return QC_OK;
         case QC_OPT_GRID:
             if (value < 0 || value > (1 << 20)) return fail(H, QC_ERR_ARG, "QC_OPT_GRID: 0..2^20");
             H->opt_grid = static_cast<int>(value);
@@ -322,39 +326,58 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
     if (kernel == 0) kernel = 2;
     fw = 0;
     int warps = 0;
+    int lean = 0;
     if (kernel == 2) {
-        // filter sized for ~16 bits per key, 2^10..2^15 words
+        // filter sized for ~16 bits per key, 2^10..2^15 words; then as many warps as fit,
+        // shrinking the filter while that leaves fewer than 8.  Both list layouts are tried
+        // (unless forced) and the one that fits more warps is taken (stored lists on a tie).
         int want = H->opt_fw;
         if (want == 0) {
             want = ceil_log2(static_cast<unsigned long long>(std::max<long long>(n_table, 1)) / 2 + 1);
             want = std::min(15, std::max(10, want));
         }
-        const size_t wb = qc::filtered_smem_bytes(sp, 1, want) - qc::filtered_smem_bytes(sp, 0, want);
-        for (fw = want; fw >= 5; --fw) {
-            const size_t base = qc::filtered_smem_bytes(sp, 0, fw);
-            if (base + wb > H->smem_optin) continue;
-            const int fit = static_cast<int>((H->smem_optin - base) / wb);
-            warps = std::min(qc::kFilteredMaxWarps, H->opt_warps ? H->opt_warps : fit);
-            if (warps > fit) continue;
-            if (H->opt_fw == 0 && warps < 8 && fw > 10) continue;  // prefer occupancy
-            break;
+        int best_fw = 0, best_w = 0, best_lean = 0;
+        for (int ln = 0; ln < 2; ++ln) {
+            if ((H->opt_lean == 1 && ln == 1) || (H->opt_lean == 2 && ln == 0)) continue;
+            const size_t wb = qc::filtered_smem_bytes(sp, 1, want, ln) - qc::filtered_smem_bytes(sp, 0, want, ln);
+            int f = want, w = 0;
+            for (; f >= 5; --f) {
+                const size_t base = qc::filtered_smem_bytes(sp, 0, f, ln);
+                if (base + wb > H->smem_optin) continue;
+                const int fit = static_cast<int>((H->smem_optin - base) / wb);
+                w = std::min(qc::kFilteredMaxWarps, H->opt_warps ? H->opt_warps : fit);
+                if (w > fit) continue;
+                if (H->opt_fw == 0 && w < 8 && f > 10) continue;  // prefer occupancy
+                break;
+            }
+            if (f < 5 || w < 1) continue;
+            if (w > best_w || (w == best_w && f > best_fw)) {
+                best_fw = f;
+                best_w = w;
+                best_lean = ln;
+            }
         }
-        if (fw < 5 || warps < 1) {
+        fw = best_fw;
+        warps = best_w;
+        lean = best_lean;
+        if (warps < 1) {
             if (H->opt_kernel == 2) return fail(H, QC_ERR_CAPACITY, "filtered kernel does not fit shared memory");
             kernel = 1;
             fw = 0;
+            lean = 0;
         }
     }
     c.kernel = kernel;
+    c.lean = lean;
     c.unroll = H->opt_unroll ? H->opt_unroll : 4;
     if (kernel == 2) {
         c.warps = warps;
-        c.smem = qc::filtered_smem_bytes(sp, warps, fw);
+        c.smem = qc::filtered_smem_bytes(sp, warps, fw, lean);
     } else {
         c.warps = std::min(qc::kFilteredMaxWarps, H->opt_warps ? H->opt_warps : 16);
         c.smem = qc::direct_smem_bytes(sp, c.warps);
     }
-    int per_sm = qc::max_active_ctas(c.kernel, H->precision, c.unroll, 32 * c.warps, c.smem);
+    int per_sm = qc::max_active_ctas(c.kernel, H->precision, c.unroll, 32 * c.warps, c.smem, c.lean);
     if (per_sm < 1) return fail(H, QC_ERR_CAPACITY, "main kernel cannot be resident with this shape");
     long long grid = H->opt_grid ? H->opt_grid : static_cast<long long>(per_sm) * H->sm_count;
     const long long need = (n_u + c.warps - 1) / c.warps;
@@ -472,6 +495,7 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     ep.ctr = H->d_ctr;
     ep.T = H->d_T;
     ep.mode = H->mode;
+    ep.lean = cfg.lean;
     QC_CHK(qc::launch_eloc_main(H->sp, tp, ep, cfg, s), "main kernel launch");
     if (H->opt_timing) QC_CHK(cudaEventRecord(H->ev[2], s), "cudaEventRecord");
     QC_CHK(qc::launch_reduce(ep, H->d_part, qc::reduce_blocks(n_u), H->d_sum, H->sp.pairs, s),
@@ -500,7 +524,7 @@ qc_status qc_eloc_timings(qc_eloc* H, float* ms3) {
 // Launch shape of the last evaluation: {kernel, grid, warps, unroll, smem bytes, filter log2 words}.
 qc_status qc_eloc_last_config(const qc_eloc* H, int64_t* cfg6) {
     if (!H || !cfg6) return QC_ERR_ARG;
-    cfg6[0] = H->last_cfg.kernel;
+    cfg6[0] = H->last_cfg.kernel == 2 && H->last_cfg.lean ? 3 : H->last_cfg.kernel;
     cfg6[1] = H->last_cfg.grid;
     cfg6[2] = H->last_cfg.warps;
     cfg6[3] = H->last_cfg.unroll;

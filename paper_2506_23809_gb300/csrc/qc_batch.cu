@@ -108,24 +108,34 @@ qc_status prepare(qc_batch* B) {
     std::vector<Lay> lay(M);
     const size_t fixed0 = qc::smem_fixed_bytes();
     const int wcap = B->warps > 0 ? std::min(B->warps, qc::kFilteredMaxWarps) : 16;  // 16: the spill-free bound
-    std::vector<int> act(M);
+    std::vector<int> act(M), lean(M);
     std::vector<unsigned> stride(M);
     for (int m = 0; m < M; ++m) {
         const long long n = std::max<long long>(B->in[m].n_u, 1);
         Lay& L = lay[m];
         L.nb = next_pow2(2ULL * static_cast<unsigned long long>(n));
-        stride[m] = static_cast<unsigned>((qc::batch_warp_bytes(B->handles[m]->sp) + 15) / 16 * 16);
         // the single path's policy: the filter for ~16 bits per key, shrunk while that
-        // leaves fewer than 8 warps
-        int fw = filter_log2(n);
-        int w = 0;
-        for (; fw >= 5; --fw) {
-            const size_t base = fixed0 + (static_cast<size_t>(4) << fw);
-            if (base + stride[m] > B->dyn_limit) continue;
-            w = std::min(wcap, static_cast<int>((B->dyn_limit - base) / stride[m]));
-            if (w >= 8 || fw <= 10 || w >= wcap) break;
+        // leaves fewer than 8 warps, in the list layout that fits more warps
+        int fw = 0, w = 0;
+        lean[m] = 0;
+        for (int ln = 0; ln < 2; ++ln) {
+            const unsigned st = static_cast<unsigned>((qc::batch_warp_bytes(B->handles[m]->sp, ln) + 15) / 16 * 16);
+            int f = filter_log2(n), ww = 0;
+            for (; f >= 5; --f) {
+                const size_t base = fixed0 + (static_cast<size_t>(4) << f);
+                if (base + st > B->dyn_limit) continue;
+                ww = std::min(wcap, static_cast<int>((B->dyn_limit - base) / st));
+                if (ww >= 8 || f <= 10 || ww >= wcap) break;
+            }
+            if (f < 5 || ww < 1) continue;
+            if (ww > w || (ww == w && f > fw)) {
+                fw = f;
+                w = ww;
+                lean[m] = ln;
+                stride[m] = st;
+            }
         }
-        if (fw < 5 || w < 1) return bfail(B, QC_ERR_CAPACITY, "a molecule of the batch does not fit shared memory");
+        if (w < 1) return bfail(B, QC_ERR_CAPACITY, "a molecule of the batch does not fit shared memory");
         L.fw = fw;
         act[m] = w;
         L.slots = off; off = align256(off + 2 * L.nb * 8);
@@ -184,6 +194,7 @@ qc_status prepare(qc_batch* B) {
         P.ep.ctr = W.ctr;
         P.ep.T = H->d_T;
         P.ep.mode = QC_SAMPLE;
+        P.ep.lean = lean[m];
         P.active_warps = act[m];
         P.warp_stride = stride[m];
         P.r0 = I.r0;

@@ -117,14 +117,18 @@ __global__ void __launch_bounds__(MAXT) eloc_batch_kernel(const __grid_constant_
                 s0 = __shfl_sync(0xffffffffu, s0, 0);
                 if (s0 >= n_run) break;
                 const unsigned long long s1 = s0 + bp.chunk < n_run ? s0 + bp.chunk : n_run;
-                for (unsigned long long s = s0; s < s1; ++s)
-                    run_sample<PREC, U, true>(mp.sp, mp.tp, mp.ep, r0 + static_cast<long long>(s), lane, smem, wl, filt);
+                for (unsigned long long s = s0; s < s1; ++s) {
+                    if (mp.ep.lean)
+                        run_sample<PREC, U, true, 1>(mp.sp, mp.tp, mp.ep, r0 + static_cast<long long>(s), lane, smem, wl, filt);
+                    else
+                        run_sample<PREC, U, true, 0>(mp.sp, mp.tp, mp.ep, r0 + static_cast<long long>(s), lane, smem, wl, filt);
+                }
             }
         }
     }
 }
 
-size_t batch_warp_bytes(const SysParams& sp) { return main_warp_bytes(sp, true); }
+size_t batch_warp_bytes(const SysParams& sp, bool lean) { return main_warp_bytes(sp, true, lean); }
 
 cudaError_t launch_build_batch(const MolParams* mols, const MolWork* work, const long long* key_off,
                                int n_mol, long long n_keys, cudaStream_t s) {

@@ -278,8 +278,12 @@ constexpr size_t kOffLut = kOffT + 128 * 8;
 constexpr size_t kOffDiv = kOffLut + kPairLut * 2;
 constexpr size_t kOffVar = ((kOffDiv + 2 * 1024 + 127) / 128) * 128;
 
-__host__ __device__ inline size_t list_words(const SysParams& sp) {
-    return static_cast<size_t>(1 + sp.nsa + sp.nsb + sp.npoa + sp.npva + sp.npob + sp.npvb);
+// u32 words of a warp's hash lists: the zero entry, the two single lists, then either the
+// four pair lists (occupied and empty pairs per spin) or, in the lean layout, only the
+// per-orbital values they are built from (a pair's value is the XOR of two of them).
+__host__ __device__ inline size_t list_words(const SysParams& sp, bool lean = false) {
+    return static_cast<size_t>(1 + sp.nsa + sp.nsb) +
+           static_cast<size_t>(lean ? sp.oa + sp.va + sp.ob + sp.vb : sp.npoa + sp.npva + sp.npob + sp.npvb);
 }
 
 
@@ -686,9 +690,9 @@ __device__ __forceinline__ float2 inv_psi32(double2 p) {
 constexpr int kCandCap = 160;  // >= 31 + 32 * 4 (the largest U with a single flush site)
 constexpr size_t kWarpQueues = 4 * kCandCap + 64 * 8;  // candidate queue + hit queue
 
-__host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filter) {
+__host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filter, bool lean = false) {
     // hash lists (u32) and, for the two single lists, their compaction maps (u16)
-    const size_t lists = filter ? 4 * list_words(sp) + 2 * static_cast<size_t>(sp.nsa + sp.nsb) : 0;
+    const size_t lists = filter ? 4 * list_words(sp, lean) + 2 * static_cast<size_t>(sp.nsa + sp.nsb) : 0;
     return (256 + kWarpQueues + lists + 15) / 16 * 16;
 }
 
@@ -696,8 +700,11 @@ __host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filt
 
 // One sample, one warp: set-up, the filtered (or unfiltered) walk over its excitations,
 // resolution of the candidates and the per-sample outputs.  wl is the warp's region of
-// shared memory, filt the CTA's copy of the Bloom filter.
-template <int PREC, int U, bool FILTER>
+// shared memory, filt the CTA's copy of the Bloom filter.  LEAN: 0 the pair lists are
+// stored, 1 they are formed on the fly from per-orbital values (less shared memory per
+// warp, so more warps fit for large orbital counts), 2 as ep.lean says.  Both layouts give
+// the same hash values in the same order, so the same results.
+template <int PREC, int U, bool FILTER, int LEAN>
 __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParams& tp,
                                            const EvalParams& ep, long long s, int lane,
                                            unsigned char* smem, unsigned char* wl,
@@ -707,10 +714,14 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     uint32_t* q = reinterpret_cast<uint32_t*>(wl + 256);
     uint2* hq = reinterpret_cast<uint2*>(wl + 256 + 4 * kCandCap);
     uint32_t* H = reinterpret_cast<uint32_t*>(wl + 256 + kWarpQueues);
-    // list offsets inside H: 0 zero | SA | SB | PAo | PAv | PBo | PBv
-    const int oSA = 1, oSB = oSA + sp.nsa, oPAo = oSB + sp.nsb, oPAv = oPAo + sp.npoa;
-    const int oPBo = oPAv + sp.npva, oPBv = oPBo + sp.npob;
-    unsigned short* IA = FILTER ? reinterpret_cast<unsigned short*>(H + list_words(sp)) : nullptr;
+    const bool lean = FILTER && (LEAN == 1 || (LEAN == 2 && ep.lean != 0));
+    // list offsets inside H: 0 zero | SA | SB | PAo | PAv | PBo | PBv, or in the lean layout
+    // 0 zero | SA | SB | occupied alpha | empty alpha | occupied beta | empty beta
+    const int oSA = 1, oSB = oSA + sp.nsa, oPAo = oSB + sp.nsb;
+    const int oPAv = oPAo + (lean ? sp.oa : sp.npoa);
+    const int oPBo = oPAv + (lean ? sp.va : sp.npva);
+    const int oPBv = oPBo + (lean ? sp.ob : sp.npob);
+    unsigned short* IA = FILTER ? reinterpret_cast<unsigned short*>(H + list_words(sp, lean)) : nullptr;
     unsigned short* IB = FILTER ? IA + sp.nsa : nullptr;
     int nsa2 = sp.nsa, nsb2 = sp.nsb;  // single-list lengths after the spin-string prefilter
     const uint32_t wmask4 = FILTER ? ((1u << tp.fw) - 1u) << 2 : 0u;
@@ -779,21 +790,28 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
             }
             nsb2 += __popc(m);
         }
-        for (int t = lane; t < sp.npoa; t += 32) {
-            const unsigned p = lut[t];
-            H[oPAo + t] = static_cast<uint32_t>(T64[2 * occA[p & 255u]] ^ T64[2 * occA[p >> 8]]);
-        }
-        for (int t = lane; t < sp.npva; t += 32) {
-            const unsigned p = lut[t];
-            H[oPAv + t] = static_cast<uint32_t>(T64[2 * virA[p & 255u]] ^ T64[2 * virA[p >> 8]]);
-        }
-        for (int t = lane; t < sp.npob; t += 32) {
-            const unsigned p = lut[t];
-            H[oPBo + t] = static_cast<uint32_t>(T64[2 * occB[p & 255u] + 1] ^ T64[2 * occB[p >> 8] + 1]);
-        }
-        for (int t = lane; t < sp.npvb; t += 32) {
-            const unsigned p = lut[t];
-            H[oPBv + t] = static_cast<uint32_t>(T64[2 * virB[p & 255u] + 1] ^ T64[2 * virB[p >> 8] + 1]);
+        if (lean) {
+            for (int t = lane; t < sp.oa; t += 32) H[oPAo + t] = static_cast<uint32_t>(T64[2 * occA[t]]);
+            for (int t = lane; t < sp.va; t += 32) H[oPAv + t] = static_cast<uint32_t>(T64[2 * virA[t]]);
+            for (int t = lane; t < sp.ob; t += 32) H[oPBo + t] = static_cast<uint32_t>(T64[2 * occB[t] + 1]);
+            for (int t = lane; t < sp.vb; t += 32) H[oPBv + t] = static_cast<uint32_t>(T64[2 * virB[t] + 1]);
+        } else {
+            for (int t = lane; t < sp.npoa; t += 32) {
+                const unsigned p = lut[t];
+                H[oPAo + t] = static_cast<uint32_t>(T64[2 * occA[p & 255u]] ^ T64[2 * occA[p >> 8]]);
+            }
+            for (int t = lane; t < sp.npva; t += 32) {
+                const unsigned p = lut[t];
+                H[oPAv + t] = static_cast<uint32_t>(T64[2 * virA[p & 255u]] ^ T64[2 * virA[p >> 8]]);
+            }
+            for (int t = lane; t < sp.npob; t += 32) {
+                const unsigned p = lut[t];
+                H[oPBo + t] = static_cast<uint32_t>(T64[2 * occB[p & 255u] + 1] ^ T64[2 * occB[p >> 8] + 1]);
+            }
+            for (int t = lane; t < sp.npvb; t += 32) {
+                const unsigned p = lut[t];
+                H[oPBv + t] = static_cast<uint32_t>(T64[2 * virB[p & 255u] + 1] ^ T64[2 * virB[p >> 8] + 1]);
+            }
         }
         __syncwarp();
     }
@@ -805,6 +823,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     // iterator over (class, outer block u0, inner block w0)
     int cls = -1, oo = 0, n1 = 0, io = 0, n2 = 0, u0 = 0, w0 = 0;
     bool done = false, need_class = true, need_outer = true;
+    bool pairs = false;  // lean layout, same-spin doubles: list entries are formed from pairs
     // outer hash values and their copies shifted for the filter word offset (>> 3): XOR
     // commutes with the shift, so the offset costs one LOP3 per test
     uint32_t hu[U], hu3[U];
@@ -823,6 +842,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     else if (cls == 4) { oo = oSA; n1 = nsa2; io = oSB; n2 = nsb2; }
                 } while (cls < 5 && (n1 == 0 || n2 == 0));
                 done = cls >= 5;
+                pairs = lean && (cls == 2 || cls == 3);
                 u0 = 0;
                 w0 = 0;
                 need_class = false;
@@ -835,7 +855,16 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     for (int k = 0; k < U; ++k) {
                         const bool v = u0 + k < n1;
                         if (FILTER) {
-                            hu[k] = hx32 ^ (v ? H[oo + u0 + k] : 0u);
+                            uint32_t e = 0u;
+                            if (v) {
+                                if (pairs) {
+                                    const unsigned pp = lut[u0 + k];
+                                    e = H[oo + (pp & 255u)] ^ H[oo + (pp >> 8)];
+                                } else {
+                                    e = H[oo + u0 + k];
+                                }
+                            }
+                            hu[k] = hx32 ^ e;
                             hu3[k] = hu[k] >> 3;
                         }
                         umask |= (v ? 1u : 0u) << k;
@@ -850,7 +879,15 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     const int w = w0 + lane;
                     const bool wv = w < n2;
                     const unsigned vm = wv ? umask : 0u;
-                    const uint32_t hw = (FILTER && wv) ? H[io + w] : 0u;
+                    uint32_t hw = 0u;
+                    if (FILTER && wv) {
+                        if (LEAN != 0 && pairs) {
+                            const unsigned pp = lut[w];
+                            hw = H[io + (pp & 255u)] ^ H[io + (pp >> 8)];
+                        } else {
+                            hw = H[io + w];
+                        }
+                    }
                     const uint32_t hw3 = hw >> 3;
                     const unsigned ccode = cbase | static_cast<unsigned>(w);
 #pragma unroll

@@ -37,6 +37,7 @@ struct qc_eloc {
     qc_eloc_summary* d_sum = nullptr;
     int opt_timing = 0, opt_kernel = 0, opt_fw = 0, opt_warps = 0, opt_unroll = 0, opt_grid = 0;
     int opt_prefilter = 1;
+    int opt_lean = 0;  // 0 auto, 1 stored pair lists, 2 formed on the fly
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool ev_recorded = false;
     int sm_count = 0;

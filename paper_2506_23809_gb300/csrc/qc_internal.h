@@ -78,6 +78,7 @@ struct EvalParams {
     Counters* ctr;
     const unsigned long long* T;  // 128 entries of the linear key hash
     int mode;                     // 0 SAMPLE, 1 FULL
+    int lean;                     // pair hash lists formed on the fly (batch kernel)
 };
 
 // A batch of molecules evaluated in one persistent launch.
@@ -114,6 +115,7 @@ struct LaunchCfg {
     int warps;
     int unroll;
     size_t smem;
+    int lean;     // filtered kernel: pair hash lists formed on the fly
 };
 
 // host-side launchers (qc_kernels.cu)
@@ -125,7 +127,7 @@ cudaError_t launch_eloc_main(const SysParams& sp, const TableParams& tp, const E
                              const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk,
                           void* summary_dev, long long pairs_per_sample, cudaStream_t s);
-int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem);
+int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem, int lean = 0);
 // batch: build every molecule's table in one launch (key_off: prefix of table sizes, device)
 cudaError_t launch_build_batch(const MolParams* mols, const MolWork* work, const long long* key_off,
                                int n_mol, long long n_keys, cudaStream_t s);
@@ -134,10 +136,10 @@ cudaError_t launch_eloc_batch(const BatchParams& bp, int precision, int unroll, 
 cudaError_t launch_reduce_batch(const MolParams* mols, const MolWork* work, int n_mol, int max_blocks,
                                 cudaStream_t s);
 int max_active_batch(int precision, int unroll, int threads, size_t smem);
-size_t batch_warp_bytes(const SysParams& sp);
+size_t batch_warp_bytes(const SysParams& sp, bool lean);
 cudaError_t prepare_batch_kernels(size_t max_smem, size_t* dyn_limit);
 cudaError_t prepare_kernels(size_t max_smem);
-size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw);
+size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw, bool lean = false);
 size_t direct_smem_bytes(const SysParams& sp, int warps);
 size_t smem_fixed_bytes();  // CTA tables at the head of the main kernels' dynamic shared memory
 int reduce_blocks(long long n);

@@ -17,8 +17,8 @@ int reduce_blocks(long long n) {
 
 size_t smem_fixed_bytes() { return kOffVar; }
 
-size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw) {
-    return kOffVar + (static_cast<size_t>(4) << fw) + static_cast<size_t>(warps) * main_warp_bytes(sp, true);
+size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw, bool lean) {
+    return kOffVar + (static_cast<size_t>(4) << fw) + static_cast<size_t>(warps) * main_warp_bytes(sp, true, lean);
 }
 size_t direct_smem_bytes(const SysParams& sp, int warps) {
     return kOffVar + static_cast<size_t>(warps) * main_warp_bytes(sp, false);
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256) build_table_kernel(TableParams tp, int n_
     if (r < tp.n) build_one(tp, n_orb, na, nb, T, slots, filter, aset, bset, ctr, r);
 }
 
-template <int PREC, int U, bool FILTER>
+template <int PREC, int U, bool FILTER, int LEAN>
 __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ SysParams sp,
                                                         const __grid_constant__ TableParams tp,
                                                         const __grid_constant__ EvalParams ep) {
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
         __syncthreads();
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * main_warp_bytes(sp, FILTER);
+    unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * main_warp_bytes(sp, FILTER, LEAN == 1);
     // samples go to warps as they come free: one cursor for the grid, so a warp that drew
     // cheap samples takes more of them and the launch ends with little tail
     const unsigned long long n_u = static_cast<unsigned long long>(ep.n_u);
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
         if (lane == 0) s = atomicAdd(&ep.ctr->next, 1ULL);
         s = __shfl_sync(0xffffffffu, s, 0);
         if (s >= n_u) break;
-        run_sample<PREC, U, FILTER>(sp, tp, ep, static_cast<long long>(s), lane, smem, wl, filt);
+        run_sample<PREC, U, FILTER, LEAN>(sp, tp, ep, static_cast<long long>(s), lane, smem, wl, filt);
     }
 }
 
@@ -115,18 +115,24 @@ cudaError_t launch_build_table(const TableParams& tp, int n_orb, int na, int nb,
     return cudaGetLastError();
 }
 
+template <int PREC, int LEAN>
+static void launch_filtered(const SysParams& sp, const TableParams& tp, const EvalParams& ep, const LaunchCfg& c,
+                            cudaStream_t s) {
+    const dim3 grid(c.grid), block(32 * c.warps);
+    if (c.unroll == 1) eloc_main_kernel<PREC, 1, true, LEAN><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    else if (c.unroll == 2) eloc_main_kernel<PREC, 2, true, LEAN><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    else eloc_main_kernel<PREC, 4, true, LEAN><<<grid, block, c.smem, s>>>(sp, tp, ep);
+}
+
 template <int PREC>
 static cudaError_t launch_main_p(const SysParams& sp, const TableParams& tp, const EvalParams& ep,
                                  const LaunchCfg& c, cudaStream_t s) {
-    const dim3 grid(c.grid), block(32 * c.warps);
     if (c.kernel != 2) {
-        eloc_main_kernel<PREC, 1, false><<<grid, block, c.smem, s>>>(sp, tp, ep);
-    } else if (c.unroll == 1) {
-        eloc_main_kernel<PREC, 1, true><<<grid, block, c.smem, s>>>(sp, tp, ep);
-    } else if (c.unroll == 2) {
-        eloc_main_kernel<PREC, 2, true><<<grid, block, c.smem, s>>>(sp, tp, ep);
+        eloc_main_kernel<PREC, 1, false, 0><<<dim3(c.grid), dim3(32 * c.warps), c.smem, s>>>(sp, tp, ep);
+    } else if (c.lean) {
+        launch_filtered<PREC, 1>(sp, tp, ep, c, s);
     } else {
-        eloc_main_kernel<PREC, 4, true><<<grid, block, c.smem, s>>>(sp, tp, ep);
+        launch_filtered<PREC, 0>(sp, tp, ep, c, s);
     }
     return cudaGetLastError();
 }
@@ -149,16 +155,21 @@ cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk, void
 }
 
 template <int PREC>
-static const void* main_kernel_ptr(int kernel, int unroll) {
-    if (kernel != 2) return (const void*)eloc_main_kernel<PREC, 1, false>;
-    if (unroll == 1) return (const void*)eloc_main_kernel<PREC, 1, true>;
-    if (unroll == 2) return (const void*)eloc_main_kernel<PREC, 2, true>;
-    return (const void*)eloc_main_kernel<PREC, 4, true>;
+static const void* main_kernel_ptr(int kernel, int unroll, int lean) {
+    if (kernel != 2) return (const void*)eloc_main_kernel<PREC, 1, false, 0>;
+    if (lean) {
+        if (unroll == 1) return (const void*)eloc_main_kernel<PREC, 1, true, 1>;
+        if (unroll == 2) return (const void*)eloc_main_kernel<PREC, 2, true, 1>;
+        return (const void*)eloc_main_kernel<PREC, 4, true, 1>;
+    }
+    if (unroll == 1) return (const void*)eloc_main_kernel<PREC, 1, true, 0>;
+    if (unroll == 2) return (const void*)eloc_main_kernel<PREC, 2, true, 0>;
+    return (const void*)eloc_main_kernel<PREC, 4, true, 0>;
 }
 
-int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem) {
-    const void* f = precision == QC_FP64 ? main_kernel_ptr<QC_FP64>(kernel, unroll)
-                                         : main_kernel_ptr<QC_FP32_COMP>(kernel, unroll);
+int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem, int lean) {
+    const void* f = precision == QC_FP64 ? main_kernel_ptr<QC_FP64>(kernel, unroll, lean)
+                                         : main_kernel_ptr<QC_FP32_COMP>(kernel, unroll, lean);
     int n = 0;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) == cudaSuccess ? n : 0;
 }
@@ -168,12 +179,13 @@ cudaError_t prepare_kernels(size_t max_smem) {
     cudaError_t e = cudaSuccess;
     for (int prec = 0; prec < 2; ++prec)
         for (int kernel = 1; kernel <= 2; ++kernel)
-            for (int unroll : {1, 2, 4}) {
-                const void* f = prec == QC_FP64 ? main_kernel_ptr<QC_FP64>(kernel, unroll)
-                                                : main_kernel_ptr<QC_FP32_COMP>(kernel, unroll);
-                const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
-                if (r != cudaSuccess) e = r;
-            }
+            for (int unroll : {1, 2, 4})
+                for (int lean = 0; lean < 2; ++lean) {
+                    const void* f = prec == QC_FP64 ? main_kernel_ptr<QC_FP64>(kernel, unroll, lean)
+                                                    : main_kernel_ptr<QC_FP32_COMP>(kernel, unroll, lean);
+                    const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+                    if (r != cudaSuccess) e = r;
+                }
     return e;
 }
 

@@ -68,11 +68,12 @@ def assert_eloc_close(got, want, rtol=RTOL_FP64):
     return err.max(initial=0.0)
 
 
-KERNELS = [dict(), {2: 1}, {2: 2, 5: 1}, {2: 2, 5: 2}, {2: 2, 5: 4}, {2: 2, 4: 3, 6: 5}, {2: 1, 4: 1, 6: 7}]
+KERNELS = [dict(), {2: 1}, {2: 2, 5: 1}, {2: 2, 5: 2}, {2: 2, 5: 4}, {2: 2, 4: 3, 6: 5}, {2: 1, 4: 1, 6: 7},
+           {2: 2, 8: 2}, {2: 2, 8: 2, 5: 1}]
 
 
 @pytest.mark.parametrize("opts", KERNELS, ids=["auto", "direct", "filt_u1", "filt_u2", "filt_u4",
-                                                "filt_w3_g5", "direct_w1_g7"])
+                                                "filt_w3_g5", "direct_w1_g7", "lean", "lean_u1"])
 def test_tiny_sample_mode(B, orc, opts):
     """N=14, 6 electrons, 1,000 uniform samples (204 pairs each), every kernel variant."""
     ints, s = I.make_workload("n14_e6_u1k")
@@ -90,6 +91,28 @@ def test_tiny_sample_mode(B, orc, opts):
     # the all-pairs scan (no enumeration) finds the same connected set
     _, pdet = orc.eloc_pairwise(ints.h, ints.eri, 0.0, 14, s.keys, s.psi, details=True)
     assert np.array_equal(g["hits"], pdet["hits"]) and np.array_equal(g["signsum"], pdet["signsum"])
+
+
+@pytest.mark.parametrize("n,ne,nu,prec", [(76, 20, 3000, 1), (128, 64, 24, 0), (52, 14, 2000, 0)])
+def test_lean_lists_equal_stored(B, orc, n, ne, nu, prec):
+    """Pair hash lists formed on the fly (QC_OPT_LEAN 2) give the same hashes in the same
+    order as the stored lists (QC_OPT_LEAN 1): E_loc bitwise equal, with at least as many
+    warps; and both match the oracle."""
+    K = n // 2
+    ints = I.make_integrals(K, min(n, 52), 990 + n)
+    keys = I.rank_weighted_samples(K, ne // 2, ne // 2, nu, seed=991 + n)
+    counts = I.zipf_counts(nu, 40 * nu, 992 + n)
+    psi = I.lognormal_psi(nu, 993 + n)
+    a = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={8: 1})
+    b = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={8: 2})
+    assert a["cfg"]["kernel"] == 2 and b["cfg"]["kernel"] == 3
+    assert b["cfg"]["warps"] >= a["cfg"]["warps"] and b["cfg"]["filter_log2w"] == a["cfg"]["filter_log2w"]
+    assert np.array_equal(a["eloc"].view(np.uint64), b["eloc"].view(np.uint64))
+    assert np.array_equal(a["hits"], b["hits"]) and np.array_equal(a["signsum"], b["signsum"])
+    want, det = orc.eloc(ints.h, ints.eri, 0.0, n, keys, psi, details=True)
+    assert_sets_equal(b, det)
+    if prec == 0:
+        assert_eloc_close(b["eloc"], want)
 
 
 def test_exact_ground_state_constant_eloc(B, orc):
