@@ -12,7 +12,8 @@ function names the paper passage it follows:
   * ``h_slater_condon``/``slater_condon`` -- Slater-Condon rules (Sec. III-B (ii));
   * ``eloc``           -- Eq. 5 by excitation enumeration + binary search in the table;
   * ``eloc_pairwise``  -- Eq. 5 by an all-pairs scan of the table (no enumeration);
-  * ``reduce``         -- Eq. 1 count-weighted mean and variance (two-pass).
+  * ``reduce``         -- Eq. 1 count-weighted mean and variance (two-pass);
+  * ``grad``           -- Eq. 4 gradient weights and 2 Re contraction with d ln Psi* rows.
 
 Parity pins: every function is checked in ``tests/test_oracle_pins.py`` against exact
 diagonalisation, closed forms and invariants; none is pinned only against itself.
@@ -55,6 +56,8 @@ def _load():
     lib = ctypes.CDLL(_LIB)
     P = ctypes.c_void_p
     i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.orc_grad.argtypes = [P, P, i64, P, i64, P, P]
+    lib.orc_grad.restype = i32
     lib.orc_h_definition.argtypes = [P, P, f64, i32, P, i64, P]
     lib.orc_h_definition.restype = i32
     lib.orc_h_slater_condon.argtypes = [P, P, f64, i32, P, i64, P]
@@ -205,6 +208,27 @@ def reduce(eloc_vals, counts):
     out = np.zeros(5)
     _load().orc_reduce(_p(e), _p(c), e.shape[0], _p(out))
     return complex(out[0], out[1]), float(out[2]), float(out[3]), int(out[4])
+
+
+def grad(eloc_vals, counts, dconj=None):
+    """Eq. 4: (w, g) with w_i = c_i (E_loc,i - Ebar)/W (complex) and, when the rows
+    D_ip = d/d theta_p ln Psi*(n_i) are given (complex, n x P), g_p = 2 Re sum_i w_i D_ip."""
+    e = _cplx(eloc_vals)
+    c = np.ascontiguousarray(counts, dtype=np.int64)
+    n = e.shape[0]
+    w = np.zeros(n, dtype=np.complex128)
+    g = None
+    P = 0
+    d = None
+    if dconj is not None:
+        d = np.ascontiguousarray(dconj, dtype=np.complex128)
+        P = d.shape[1]
+        g = np.zeros(P)
+    st = _load().orc_grad(_p(e), _p(c), n, _p(d) if d is not None else None, P, _p(w),
+                          _p(g) if g is not None else None)
+    if st != 0:
+        raise ValueError("orc_grad failed (no finite E_loc with positive count?)")
+    return w, g
 
 
 def connected_union(n_orb, samples, cap=None) -> np.ndarray:

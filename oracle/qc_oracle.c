@@ -27,6 +27,8 @@
  *   - orc_pairwise: the same sum found by scanning every (n, m) pair of the table and
  *     keeping those that differ by one or two electrons (no enumeration).
  *   - orc_reduce: Eq. 1, the count-weighted mean of E_loc, and its weighted variance.
+ *   - orc_grad: Eq. 4, the energy gradient 2 Re < d_theta ln Psi*(n) (E_loc - <E>) >_n as
+ *     a count-weighted sample average, given the rows d_theta ln Psi*(n_i).
  *
  * Sign convention: |n> = a+_{i1} a+_{i2} ... |0> with i1 < i2 < ...; hence
  * a_q |n> = (-1)^{#occupied below q} |n - q>, and a+_p |n> = (-1)^{#occupied below p} |n + p>.
@@ -420,6 +422,47 @@ int orc_reduce(const double *eloc, const int64_t *counts, int64_t n, double *out
     }
     out[0] = (double)mr; out[1] = (double)mi; out[2] = (double)(v / w);
     out[3] = (double)w; out[4] = (double)used;
+    return 0;
+}
+
+/* Eq. 4 over the unique samples: with W = sum c_i and Ebar the Eq. 1 mean (complex),
+ *   w_i = c_i (E_loc,i - Ebar) / W      (0 for a sample whose E_loc is not finite)
+ *   g_p = 2 Re sum_i w_i D_ip,          D_ip = d/d theta_p ln Psi*(n_i)  (complex, row-major)
+ * Written as two plain loops in long double.  w_out (complex, n) or g_out (P) may be NULL. */
+int orc_grad(const double *eloc, const int64_t *counts, int64_t n, const double *dconj, int64_t P,
+             double *w_out, double *g_out) {
+    long double W = 0, sr = 0, si = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double er = eloc[2 * i], ei = eloc[2 * i + 1];
+        if (!isfinite(er) || !isfinite(ei)) continue;
+        W += (long double)counts[i];
+        sr += (long double)counts[i] * er;
+        si += (long double)counts[i] * ei;
+    }
+    if (W <= 0) return -1;
+    const long double mr = sr / W, mi = si / W;
+    long double *wr = (long double *)calloc((size_t)(n > 0 ? n : 1), sizeof(long double));
+    long double *wi = (long double *)calloc((size_t)(n > 0 ? n : 1), sizeof(long double));
+    if (!wr || !wi) { free(wr); free(wi); return -2; }
+    for (int64_t i = 0; i < n; ++i) {
+        double er = eloc[2 * i], ei = eloc[2 * i + 1];
+        if (!isfinite(er) || !isfinite(ei)) continue;
+        wr[i] = (long double)counts[i] * (er - mr) / W;
+        wi[i] = (long double)counts[i] * (ei - mi) / W;
+    }
+    if (w_out)
+        for (int64_t i = 0; i < n; ++i) { w_out[2 * i] = (double)wr[i]; w_out[2 * i + 1] = (double)wi[i]; }
+    if (g_out && dconj)
+        for (int64_t p = 0; p < P; ++p) {
+            long double g = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                const double dr = dconj[2 * (i * P + p)], di = dconj[2 * (i * P + p) + 1];
+                g += wr[i] * dr - wi[i] * di;   /* Re(w D) */
+            }
+            g_out[p] = (double)(2 * g);
+        }
+    free(wr);
+    free(wi);
     return 0;
 }
 
