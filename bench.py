@@ -44,6 +44,8 @@ OPS_PER_PAIR = 7
 # need more ALU instructions than were issued in total, so the pipe is 16 lanes wide
 # (a warp instruction every other cycle).
 ALU_LANES = 16
+# Nominal dense FP64 rate of the part, GFLOP/s (the gradient contraction's bound).
+FP64_NOMINAL_GFLOPS = 1250.0
 PROFILE_JSON = os.path.join(ROOT, "profiles", "eloc_main_n52_e14_u100k.json")
 
 
@@ -58,10 +60,11 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--form", default="plain", choices=["plain", "batched", "serve"],
+    p.add_argument("--form", default="plain", choices=["plain", "batched", "serve", "grad"],
                    help="plain: one molecule per step (the default benchmark); batched: many "
                         "molecules in one persistent launch; serve: Poisson request arrivals")
     p.add_argument("--n-mol", type=int, default=64, help="batched form: molecules")
+    p.add_argument("--n-par", type=int, default=4096, help="grad form: parameters (columns of d ln Psi*)")
     p.add_argument("--requests", type=int, default=48, help="serve form: requests")
     p.add_argument("--rate", type=float, default=20.0, help="serve form: arrivals per second")
     p.add_argument("--quantum", type=float, default=1e10,
@@ -590,6 +593,68 @@ def run_serve(args):
     return 0
 
 
+def run_grad(args):
+    """Eq. 4 gradient on the bench workload: after one evaluation, each step forms the
+    weights and contracts them with n_u x P complex d ln Psi* rows (synthetic, resident in
+    HBM, larger than L2).  Bound by HBM: the rows are read once, 16 B per element."""
+    import numpy as np
+    import torch
+
+    from paper_2506_23809_gb300 import binding as B
+    from paper_2506_23809_gb300 import build
+    build.build()
+    B.load_library()
+    torch.cuda.set_device(0)
+    spec, (ints, s) = _make_workload(args.workload, 1)
+    h = B.qc_eloc_create(ints.h, ints.eri, 0.0, spec["n_orb"], spec["n_elec"])
+    keys = B.keys_to_tensor(s.keys)
+    ct = torch.from_numpy(s.counts).cuda()
+    e, _ = B.qc_eloc_eval(h, keys, ct, torch.from_numpy(s.psi).cuda())
+    n_u, P = len(s.keys), int(args.n_par)
+    g = torch.Generator(device="cuda").manual_seed(4401)
+    D = torch.randn(n_u, P, dtype=torch.complex128, device="cuda", generator=g)
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for _ in range(args.warmup):
+        B.qc_eloc_grad(h, e, ct, D, weights=True)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for a, b in evs:
+        a.record(stream)
+        B.qc_eloc_grad(h, e, ct, D, weights=True)
+        b.record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = t0.elapsed_time(t1)
+    B.qc_eloc_destroy(h)
+    peaks, peak_src = _measured_peaks()
+    bytes_step = n_u * P * 16 + n_u * (16 + 8) * 2 + n_u * 16 + P * 8
+    mean_s = statistics.mean(ms) / 1e3
+    line = {"metric": "Eq. 4 gradient: d ln Psi* rows contracted per second", "form": "grad",
+            "value": n_u * P / mean_s, "unit": "row elements/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic (Gaussian complex d ln Psi* rows, bench workload E_loc)",
+            "config": {"workload": args.workload, "n_u": n_u, "n_par": P, "rows_bytes": n_u * P * 16,
+                       "l2": "rows larger than L2 (read once per step)"},
+            # two FP64 fused multiply-adds (4 flops) per element against the nominal FP64
+            # rate of the part (no measured FP64 peak exists); HBM fraction beside it
+            "roofline": {"bound": "fp64", "achieved": 4.0 * n_u * P / mean_s / 1e9, "peak": FP64_NOMINAL_GFLOPS,
+                         "unit": "GFLOP/s", "frac": 4.0 * n_u * P / mean_s / 1e9 / FP64_NOMINAL_GFLOPS,
+                         "traffic": None, "peak_source": "nominal FP64 rate (no measured FP64 peak)",
+                         "hbm": {"achieved_gbs": bytes_step / mean_s / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
+                                 "frac": bytes_step / mean_s / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                                 "peak_source": peak_src, "algorithmic_bytes_per_step": bytes_step}},
+            "gpu_launches": 3 * args.steps, "clocks": sampler.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -598,6 +663,8 @@ def main():
         return run_batched(args)
     if args.form == "serve":
         return run_serve(args)
+    if args.form == "grad":
+        return run_grad(args)
     return run_ours(args)
 
 

@@ -184,6 +184,25 @@ qc_status qc_eloc_eval(qc_eloc* handle, const uint64_t* samples, const int64_t* 
  * reduction}.  Needs QC_OPT_TIMING = 1; synchronizes on the recorded events. */
 qc_status qc_eloc_timings(qc_eloc* handle, float* ms3);
 
+/* ---- Eq. 4: the energy gradient ----------------------------------------------------
+ * d<E>/d theta_p = 2 Re < d_theta_p ln Psi*(n) (E_loc(n) - <E>) >_n (Sec. II-A, Eq. 4), the
+ * average taken over the unique samples of the last qc_eloc_eval on this handle with their
+ * counts: with W and Ebar that evaluation's Eq. 1 sums (read on the device, so this call
+ * is asynchronous on the same stream after it),
+ *   w_i = c_i (E_loc,i - Ebar) / W       (0 for a sample whose E_loc is not finite)
+ *   g_p = 2 Re sum_i w_i dconj_ip
+ * Arguments (device memory, caller-owned):
+ *   eloc    complex128[n_u]: the E_loc written by that evaluation (same order, same n_u)
+ *   counts  int64[n_u]
+ *   dconj   complex128[n_u][n_par], row-major: d/d theta_p ln Psi*(n_i); NULL if g_out is
+ *   w_out   complex128[n_u] or NULL
+ *   g_out   double[n_par] or NULL
+ * The contraction reads dconj once (HBM-bound) in a fixed summation order (deterministic).
+ * Errors: QC_ERR_ARG (sizes, NULL, alignment: 16 bytes, counts and g_out 8), QC_ERR_OOM
+ * for the handle's n_par x (<= 512) partials buffer. */
+qc_status qc_eloc_grad(qc_eloc* handle, const double* eloc, const int64_t* counts, int64_t n_u,
+                       const double* dconj, int64_t n_par, double* w_out, double* g_out, void* stream);
+
 /* ---- allocation-free evaluation ---------------------------------------------------
  * qc_eloc_eval_static: the sample-space, FP64 evaluation of qc_eloc_eval (the table is
  * the sample set itself) for callers that cannot allocate device memory when they call

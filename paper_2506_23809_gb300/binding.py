@@ -86,6 +86,8 @@ def load_library(path: str = LIB_PATH):
     lib.qc_eloc_last_config.restype = i32
     lib.qc_eloc_eval_static.argtypes = [P, P, f64, i32, i32, P, P, P, i64, P, P, P]
     lib.qc_eloc_eval_static.restype = i32
+    lib.qc_eloc_grad.argtypes = [P, P, P, i64, P, i64, P, P, P]
+    lib.qc_eloc_grad.restype = i32
     lib.qc_batch_create.argtypes = [P, i32, ctypes.POINTER(P)]
     lib.qc_batch_destroy.argtypes = [P]
     lib.qc_batch_last_error.argtypes = [P]
@@ -221,6 +223,35 @@ def qc_eloc_eval(handle: QcHandle, samples, counts, psi, table_keys=None, table_
                           ctypes.c_void_p(stream.cuda_stream))
     _check(st, handle.ptr)
     return eloc, diag
+
+
+def qc_eloc_grad(handle: QcHandle, eloc, counts, dconj=None, weights: bool = True, stream=None):
+    """Eq. 4 on the device after the handle's last evaluation (same stream): returns
+    (w complex128[n_u] or None, g float64[n_par] or None) with w_i = c_i (E_loc,i - Ebar)/W
+    and g_p = 2 Re sum_i w_i dconj[i, p] (dconj: complex128 [n_u, n_par], d ln Psi* rows)."""
+    import torch
+    lib = load_library()
+    n_u = eloc.shape[0]
+    e = _dptr(eloc, "eloc", (torch.complex128,))
+    c = _dptr(counts, "counts", (torch.int64,))
+    d = None
+    n_par = 0
+    g = None
+    if dconj is not None:
+        if dconj.dim() != 2 or dconj.shape[0] != n_u:
+            raise ValueError("dconj must be [n_u, n_par]")
+        d = _dptr(dconj, "dconj", (torch.complex128,))
+        n_par = dconj.shape[1]
+        g = torch.empty(n_par, dtype=torch.float64, device=eloc.device)
+    w = torch.empty(n_u, dtype=torch.complex128, device=eloc.device) if weights else None
+    if stream is None:
+        stream = torch.cuda.current_stream(eloc.device)
+    st = lib.qc_eloc_grad(handle.ptr, e, c, int(n_u), d, int(n_par),
+                          None if w is None else ctypes.c_void_p(w.data_ptr()),
+                          None if g is None else ctypes.c_void_p(g.data_ptr()),
+                          ctypes.c_void_p(stream.cuda_stream))
+    _check(st, handle.ptr)
+    return w, g
 
 
 QC_STATIC_MAX_SAMPLES = 131072

@@ -233,6 +233,7 @@ qc_status qc_eloc_destroy(qc_eloc* H) {
     free_dev(H->d_part);
     free_dev(H->d_ctr);
     free_dev(H->d_sum);
+    free_dev(H->d_gpart);
     for (auto& ev : H->ev)
         if (ev) cudaEventDestroy(ev);
     delete H;

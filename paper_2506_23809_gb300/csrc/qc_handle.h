@@ -35,6 +35,8 @@ struct qc_eloc {
     int part_cap = 0;  // reduction blocks
     qc::Counters* d_ctr = nullptr;
     qc_eloc_summary* d_sum = nullptr;
+    double* d_gpart = nullptr;  // Eq. 4 contraction partials
+    size_t gpart_cap = 0;       // doubles
     int opt_timing = 0, opt_kernel = 0, opt_fw = 0, opt_warps = 0, opt_unroll = 0, opt_grid = 0;
     int opt_prefilter = 1;
     int opt_lean = 0;  // 0 auto, 1 stored pair lists, 2 formed on the fly
