@@ -13,7 +13,9 @@ function names the paper passage it follows:
   * ``eloc``           -- Eq. 5 by excitation enumeration + binary search in the table;
   * ``eloc_pairwise``  -- Eq. 5 by an all-pairs scan of the table (no enumeration);
   * ``reduce``         -- Eq. 1 count-weighted mean and variance (two-pass);
-  * ``grad``           -- Eq. 4 gradient weights and 2 Re contraction with d ln Psi* rows.
+  * ``grad``           -- Eq. 4 gradient weights and 2 Re contraction with d ln Psi* rows;
+  * ``dedup``          -- the unique-sample table of Sec. IV-C-4 (sorted unique keys with
+                          their multiplicities) from a raw stream of sampled bitstrings.
 
 Parity pins: every function is checked in ``tests/test_oracle_pins.py`` against exact
 diagonalisation, closed forms and invariants; none is pinned only against itself.
@@ -229,6 +231,22 @@ def grad(eloc_vals, counts, dconj=None):
     if st != 0:
         raise ValueError("orc_grad failed (no finite E_loc with positive count?)")
     return w, g
+
+
+def dedup(raw):
+    """The sample table (unique sorted keys, multiplicities) of a raw stream of sampled
+    bitstrings uint64[n, 2]: a library sort of the 128-bit keys (hi = word 1 first, then
+    word 0), then run lengths of equal neighbours -- the plain definition, no other steps."""
+    raw = np.ascontiguousarray(raw, dtype=np.uint64).reshape(-1, 2)
+    if raw.shape[0] == 0:
+        return raw.copy(), np.zeros(0, dtype=np.int64)
+    order = np.lexsort((raw[:, 0], raw[:, 1]))      # last key is primary: word 1, then word 0
+    srt = raw[order]
+    head = np.ones(srt.shape[0], dtype=bool)
+    head[1:] = np.any(srt[1:] != srt[:-1], axis=1)
+    starts = np.flatnonzero(head)
+    counts = np.diff(np.append(starts, srt.shape[0])).astype(np.int64)
+    return srt[starts].copy(), counts
 
 
 def connected_union(n_orb, samples, cap=None) -> np.ndarray:
