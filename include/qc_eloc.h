@@ -51,6 +51,7 @@
 #ifndef QC_ELOC_H
 #define QC_ELOC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -183,6 +184,27 @@ qc_status qc_eloc_eval(qc_eloc* handle, const uint64_t* samples, const int64_t* 
 /* Per-phase device times of the last evaluation in ms: {table build, main kernel,
  * reduction}.  Needs QC_OPT_TIMING = 1; synchronizes on the recorded events. */
 qc_status qc_eloc_timings(qc_eloc* handle, float* ms3);
+
+/* ---- the sample table from a raw sample stream --------------------------------------
+ * Sec. IV-C-4 builds a lookup table over the unique samples and names its construction as
+ * what limits scaling.  qc_dedup turns a raw stream of sampled bitstrings (any order,
+ * repeats) into the table qc_eloc_eval takes: ascending unique keys (unsigned 128-bit order,
+ * word 1 most significant) and their multiplicities, on the device, asynchronously.
+ *   raw        device uint64[n_raw][2], read only, 16-byte aligned; n_raw < 2^31
+ *   n_orb      significant bits (1..128); every bit >= n_orb must be 0
+ *   keys_out   device uint64[n_raw][2]: the first *n_unique rows are written
+ *   counts_out device int64[n_raw]: the first *n_unique entries are written
+ *   n_unique   device int64: the number of unique keys, or -1 if a key had a bit >= n_orb
+ *              set (keys_out and counts_out are then not a table)
+ *   work       device scratch of qc_dedup_workspace_bytes(n_raw) bytes, 256-byte aligned,
+ *              not shared with a concurrent call
+ * A stable radix sort over ceil(n_orb / 8) 8-bit digits, then run lengths; exact (integer
+ * work), so the result is bit-identical to any correct sort.  Errors (QC_ERR_ARG,
+ * QC_ERR_CAPACITY for a short workspace, QC_ERR_CUDA) return synchronously; the message
+ * is qc_eloc_last_error(NULL). */
+int64_t qc_dedup_workspace_bytes(int64_t n_raw);
+qc_status qc_dedup(const uint64_t* raw, int64_t n_raw, int n_orb, uint64_t* keys_out, int64_t* counts_out,
+                   int64_t* n_unique, void* work, size_t work_bytes, void* stream);
 
 /* ---- Eq. 4: the energy gradient ----------------------------------------------------
  * d<E>/d theta_p = 2 Re < d_theta_p ln Psi*(n) (E_loc(n) - <E>) >_n (Sec. II-A, Eq. 4), the

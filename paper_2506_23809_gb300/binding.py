@@ -88,6 +88,10 @@ def load_library(path: str = LIB_PATH):
     lib.qc_eloc_eval_static.restype = i32
     lib.qc_eloc_grad.argtypes = [P, P, P, i64, P, i64, P, P, P]
     lib.qc_eloc_grad.restype = i32
+    lib.qc_dedup_workspace_bytes.argtypes = [i64]
+    lib.qc_dedup_workspace_bytes.restype = i64
+    lib.qc_dedup.argtypes = [P, i64, i32, P, P, P, P, ctypes.c_size_t, P]
+    lib.qc_dedup.restype = i32
     lib.qc_batch_create.argtypes = [P, i32, ctypes.POINTER(P)]
     lib.qc_batch_destroy.argtypes = [P]
     lib.qc_batch_last_error.argtypes = [P]
@@ -252,6 +256,39 @@ def qc_eloc_grad(handle: QcHandle, eloc, counts, dconj=None, weights: bool = Tru
                           ctypes.c_void_p(stream.cuda_stream))
     _check(st, handle.ptr)
     return w, g
+
+
+def qc_dedup_workspace_bytes(n_raw: int) -> int:
+    return int(load_library().qc_dedup_workspace_bytes(int(n_raw)))
+
+
+def qc_dedup(raw, n_orb: int, keys_out=None, counts_out=None, n_unique=None, work=None, stream=None):
+    """The sample table of a raw stream on the device: returns (keys_out, counts_out,
+    n_unique) tensors -- the first int(n_unique) rows are the table (read n_unique after the
+    stream has passed the call; -1 means a key had a bit >= n_orb set)."""
+    import torch
+    lib = load_library()
+    n = raw.shape[0]
+    dev = raw.device
+    if keys_out is None:
+        keys_out = torch.empty((max(n, 1), 2), dtype=torch.int64, device=dev)
+    if counts_out is None:
+        counts_out = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+    if n_unique is None:
+        n_unique = torch.empty(1, dtype=torch.int64, device=dev)
+    need = qc_dedup_workspace_bytes(n)
+    if work is None or work.numel() < need:
+        work = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+    wp = work.data_ptr()
+    wp += (-wp) % 256
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    st = lib.qc_dedup(_dptr(raw, "raw", (torch.int64, torch.uint64), 2) if n else None, int(n), int(n_orb),
+                      ctypes.c_void_p(keys_out.data_ptr()), ctypes.c_void_p(counts_out.data_ptr()),
+                      ctypes.c_void_p(n_unique.data_ptr()), ctypes.c_void_p(wp), int(need),
+                      ctypes.c_void_p(stream.cuda_stream))
+    _check(st, None)
+    return keys_out, counts_out, n_unique
 
 
 QC_STATIC_MAX_SAMPLES = 131072
