@@ -185,6 +185,34 @@ qc_status qc_eloc_eval(qc_eloc* handle, const uint64_t* samples, const int64_t* 
  * reduction}.  Needs QC_OPT_TIMING = 1; synchronizes on the recorded events. */
 qc_status qc_eloc_timings(qc_eloc* handle, float* ms3);
 
+/* ---- the accurate energy at scale: export the connected set, apply psi --------------
+ * Sec. IV-C-4's "accurate energy" sums Eq. 5 over every x' connected to a sample, with psi
+ * from the network.  For large systems the connected set is far larger than any table, so
+ * it is exported in chunks of samples, the caller evaluates psi on it, and Eq. 5 is then
+ * reduced against those values.  Every sample has exactly P = qc_eloc_pairs_per_sample()
+ * connected x', written in a fixed order (position = class offset + u * n2 + w): alpha
+ * singles, beta singles (w = occupied index * empty count + empty index over the spin's
+ * ascending occupied / empty lists), alpha-alpha then beta-beta doubles (u an occupied
+ * pair, w an empty pair; pair (p < q) has index q (q - 1) / 2 + p), alpha-beta doubles
+ * (u an alpha single, w a beta single).
+ *   qc_eloc_export: samples device uint64[n_u][2] (sorted order not required); outputs
+ *     (device, any may be NULL) keys_out uint64[n_u * P][2], elems_out double[n_u * P]
+ *     (the signed elements <x|H|x'> of Eq. 2 by the Slater-Condon rules, in the handle's
+ *     precision), diag_out double[n_u] (<x|H|x> with e_core).  A sample with a wrong
+ *     electron count gets NaN diagonal and elements and zero keys.
+ *   qc_eloc_apply: E_loc(x_i) = diag_i + sum_j elems_ij psi_conn_ij / psi_i (FP64, fixed
+ *     order), then the Eq. 1 reduction over the chunk into the handle's device summary and,
+ *     if `summary` is given (host memory, page-locked keeps it asynchronous), a copy.
+ *     psi device complex128[n_u], counts int64[n_u], elems / diag as exported, psi_conn
+ *     complex128[n_u * P] in the export order, eloc_out complex128[n_u].  psi(x) = 0 gives
+ *     NaN and QC_ERR_ZERO_PSI in the summary; n_hits is 0 (nothing is looked up).
+ * Both are asynchronous on `stream`; errors as for qc_eloc_eval. */
+qc_status qc_eloc_export(qc_eloc* handle, const uint64_t* samples, int64_t n_u, uint64_t* keys_out,
+                         double* elems_out, double* diag_out, void* stream);
+qc_status qc_eloc_apply(qc_eloc* handle, const double* psi, const int64_t* counts, int64_t n_u,
+                        const double* elems, const double* diag, const double* psi_conn, double* eloc_out,
+                        qc_eloc_summary* summary, void* stream);
+
 /* ---- the sample table from a raw sample stream --------------------------------------
  * Sec. IV-C-4 builds a lookup table over the unique samples and names its construction as
  * what limits scaling.  qc_dedup turns a raw stream of sampled bitstrings (any order,

@@ -88,6 +88,10 @@ def load_library(path: str = LIB_PATH):
     lib.qc_eloc_eval_static.restype = i32
     lib.qc_eloc_grad.argtypes = [P, P, P, i64, P, i64, P, P, P]
     lib.qc_eloc_grad.restype = i32
+    lib.qc_eloc_export.argtypes = [P, P, i64, P, P, P, P]
+    lib.qc_eloc_export.restype = i32
+    lib.qc_eloc_apply.argtypes = [P, P, P, i64, P, P, P, P, P, P]
+    lib.qc_eloc_apply.restype = i32
     lib.qc_dedup_workspace_bytes.argtypes = [i64]
     lib.qc_dedup_workspace_bytes.restype = i64
     lib.qc_dedup.argtypes = [P, i64, i32, P, P, P, P, ctypes.c_size_t, P]
@@ -256,6 +260,46 @@ def qc_eloc_grad(handle: QcHandle, eloc, counts, dconj=None, weights: bool = Tru
                           ctypes.c_void_p(stream.cuda_stream))
     _check(st, handle.ptr)
     return w, g
+
+
+def qc_eloc_export(handle: QcHandle, samples, keys=True, elems=True, diag=True, stream=None):
+    """The connected set of every sample in the export order: returns (keys int64[n_u * P, 2]
+    or None, elems float64[n_u * P] or None, diag float64[n_u] or None)."""
+    import torch
+    lib = load_library()
+    n_u = samples.shape[0]
+    P = qc_eloc_pairs_per_sample(handle)
+    dev = samples.device
+    k = torch.empty((n_u * P, 2), dtype=torch.int64, device=dev) if keys else None
+    e = torch.empty(n_u * P, dtype=torch.float64, device=dev) if elems else None
+    d = torch.empty(n_u, dtype=torch.float64, device=dev) if diag else None
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    vp = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    st = lib.qc_eloc_export(handle.ptr, _dptr(samples, "samples", (torch.int64, torch.uint64), 2), int(n_u),
+                            vp(k), vp(e), vp(d), ctypes.c_void_p(stream.cuda_stream))
+    _check(st, handle.ptr)
+    return k, e, d
+
+
+def qc_eloc_apply(handle: QcHandle, psi, counts, elems, diag, psi_conn, eloc=None, summary: bool = True,
+                  stream=None):
+    """E_loc against psi on the exported connected set; returns eloc (complex128[n_u]) and
+    writes the Eq. 1 summary into handle.summary_buf (read with qc_eloc_summary_read)."""
+    import torch
+    lib = load_library()
+    n_u = psi.shape[0]
+    if eloc is None:
+        eloc = torch.empty(n_u, dtype=torch.complex128, device=psi.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(psi.device)
+    st = lib.qc_eloc_apply(handle.ptr, _dptr(psi, "psi", (torch.complex128,)), _dptr(counts, "counts", (torch.int64,)),
+                           int(n_u), _dptr(elems, "elems", (torch.float64,)), _dptr(diag, "diag", (torch.float64,)),
+                           _dptr(psi_conn, "psi_conn", (torch.complex128,)), ctypes.c_void_p(eloc.data_ptr()),
+                           ctypes.c_void_p(handle.summary_buf.data_ptr()) if summary else None,
+                           ctypes.c_void_p(stream.cuda_stream))
+    _check(st, handle.ptr)
+    return eloc
 
 
 def qc_dedup_workspace_bytes(n_raw: int) -> int:
