@@ -64,29 +64,33 @@ __global__ void __launch_bounds__(32 * kExpWarps) eloc_export_kernel(const __gri
             const int n1 = cls < 2 ? 1 : cls == 2 ? sp.npoa : cls == 3 ? sp.npob : sp.nsa;
             const int n2 = cls == 0 ? sp.nsa : cls == 1 ? sp.nsb : cls == 2 ? sp.npva : cls == 3 ? sp.npvb : sp.nsb;
             for (int u = 0; u < n1; ++u) {
-                for (int w0 = 0; w0 < n2; w0 += 32) {
-                    const int w = w0 + lane;
-                    if (w >= n2) continue;
-                    const long long pos = off + static_cast<long long>(u) * n2 + w;
-                    if (!ok) {  // not a determinant of this system: no connected set
-                        if (out.keys) out.keys[pos] = make_ulonglong2(0ULL, 0ULL);
-                        if (out.elems) out.elems[pos] = nan;
-                        continue;
-                    }
-                    const unsigned code = (static_cast<unsigned>(cls) << 24) | (static_cast<unsigned>(u) << 12) |
-                                          static_cast<unsigned>(w);
-                    const unsigned orbs = decode(code, sp, wl, smem, nullptr, nullptr);
-                    if (out.keys) {
-                        unsigned long long h;
-                        out.keys[pos] = excite(orbs, x, hx, T64, h);
-                    }
-                    if (out.elems) {
-                        double h64 = 0.0;
-                        float h32 = 0.f;
-                        bool sneg = false;
-                        if (cls < 2) single_element<PREC>(orbs, px, sp, wl, h64, h32, sneg);
-                        else double_element<PREC>(orbs, px, sp, h64, h32, sneg);
-                        out.elems[pos] = PREC == QC_FP64 ? h64 : static_cast<double>(h32);
+                // two excitations per lane per step (w and w + 32): independent loads in flight
+                for (int w0 = 0; w0 < n2; w0 += 64) {
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        const int w = w0 + 32 * half + lane;
+                        if (w >= n2) continue;
+                        const long long pos = off + static_cast<long long>(u) * n2 + w;
+                        if (!ok) {  // not a determinant of this system: no connected set
+                            if (out.keys) __stcs(out.keys + pos, make_ulonglong2(0ULL, 0ULL));
+                            if (out.elems) __stcs(out.elems + pos, nan);
+                            continue;
+                        }
+                        const unsigned code = (static_cast<unsigned>(cls) << 24) |
+                                              (static_cast<unsigned>(u) << 12) | static_cast<unsigned>(w);
+                        const unsigned orbs = decode(code, sp, wl, smem, nullptr, nullptr);
+                        if (out.keys) {
+                            unsigned long long h;
+                            __stcs(out.keys + pos, excite(orbs, x, hx, T64, h));
+                        }
+                        if (out.elems) {
+                            double h64 = 0.0;
+                            float h32 = 0.f;
+                            bool sneg = false;
+                            if (cls < 2) single_element<PREC>(orbs, px, sp, wl, h64, h32, sneg);
+                            else double_element<PREC>(orbs, px, sp, h64, h32, sneg);
+                            __stcs(out.elems + pos, PREC == QC_FP64 ? h64 : static_cast<double>(h32));
+                        }
                     }
                 }
             }
@@ -110,15 +114,25 @@ __global__ void __launch_bounds__(256) eloc_apply_kernel(const double* __restric
          s += warps) {
         const double* e = elems + s * P;
         const double2* q = psi_conn + s * P;
-        double re = 0.0, im = 0.0;
-        for (long long j = lane; j < P; j += 32) {
-            const double h = __ldcs(e + j);
-            const double2 v = __ldcs(q + j);
-            re = fma(h, v.x, re);
-            im = fma(h, v.y, im);
+        // two independent partial sums per lane (j and j + 32 of each 64), added at the end
+        double re = 0.0, im = 0.0, re2 = 0.0, im2 = 0.0;
+        long long j = lane;
+        for (; j + 32 < P; j += 64) {
+            const double h0 = __ldcs(e + j), h1 = __ldcs(e + j + 32);
+            const double2 v0 = __ldcs(q + j), v1 = __ldcs(q + j + 32);
+            re = fma(h0, v0.x, re);
+            im = fma(h0, v0.y, im);
+            re2 = fma(h1, v1.x, re2);
+            im2 = fma(h1, v1.y, im2);
         }
-        re = warp_sum(re);
-        im = warp_sum(im);
+        if (j < P) {
+            const double h0 = __ldcs(e + j);
+            const double2 v0 = __ldcs(q + j);
+            re = fma(h0, v0.x, re);
+            im = fma(h0, v0.y, im);
+        }
+        re = warp_sum(re + re2);
+        im = warp_sum(im + im2);
         if (lane == 0) {
             const double2 p = psi[s];
             const double n2 = p.x * p.x + p.y * p.y;
