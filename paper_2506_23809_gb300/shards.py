@@ -46,3 +46,60 @@ def allgather_combine(part: np.ndarray, dist, device=None) -> tuple[float, compl
     out = [torch.empty_like(t) for _ in range(dist.get_world_size())]
     dist.all_gather(out, t)
     return combine(torch.stack(out).cpu().numpy())
+
+
+# ---------------------------------------------------------------------------------------
+# Cost-weighted plans across replicas (many molecules, uneven sizes)
+# ---------------------------------------------------------------------------------------
+def job_cost(n_rows: int, pairs_per_sample: int, per_sample: float = 4096.0) -> float:
+    """Estimated work of n_rows samples of one molecule: every sample enumerates the same
+    number of connected pairs, plus a per-sample set-up share (in pair equivalents)."""
+    return float(n_rows) * (float(pairs_per_sample) + per_sample)
+
+
+def plan_replicas(jobs, n_replicas: int, per_sample: float = 4096.0, min_rows: int = 1):
+    """Split jobs [(n_rows, pairs_per_sample), ...] over replicas so that the estimated
+    work of each is about equal.  Whole jobs go longest first to the least-loaded replica;
+    a job larger than a fair share is cut into row ranges first, so no replica waits on one
+    long molecule.  Returns, per replica, a list of (job index, row0, row1)."""
+    if n_replicas < 1:
+        raise ValueError("n_replicas >= 1")
+    costs = [job_cost(n, p, per_sample) for n, p in jobs]
+    total = sum(costs)
+    share = total / n_replicas if total > 0 else 0.0
+    pieces = []           # (cost, job, r0, r1)
+    for j, ((n, p), c) in enumerate(zip(jobs, costs)):
+        if n <= 0:
+            continue
+        if share > 0 and c > share and n > min_rows:
+            k = min(n, max(2, int(np.ceil(c / share))))
+            for q in range(k):
+                r0, r1 = (n * q) // k, (n * (q + 1)) // k
+                if r1 > r0:
+                    pieces.append((job_cost(r1 - r0, p, per_sample), j, r0, r1))
+        else:
+            pieces.append((c, j, 0, n))
+    pieces.sort(key=lambda t: (-t[0], t[1], t[2]))
+    load = [0.0] * n_replicas
+    plan = [[] for _ in range(n_replicas)]
+    for c, j, r0, r1 in pieces:
+        r = min(range(n_replicas), key=lambda i: (load[i], i))
+        load[r] += c
+        plan[r].append((j, r0, r1))
+    for p in plan:
+        p.sort()
+    return plan
+
+
+def predicted_unique(sample_counts, density_prev) -> np.ndarray:
+    """The density-aware estimate of Alg. 2: the unique samples a partition will hold is its
+    sample count times the unique-to-sample ratio d = unique / counts measured for it in the
+    previous iteration (the sample distribution changes slowly between iterations)."""
+    return np.asarray(sample_counts, dtype=np.float64) * np.asarray(density_prev, dtype=np.float64)
+
+
+def density(n_unique, n_counts) -> np.ndarray:
+    """Alg. 2's density metric d = unique / counts (0 where nothing was drawn)."""
+    u = np.asarray(n_unique, dtype=np.float64)
+    c = np.asarray(n_counts, dtype=np.float64)
+    return np.divide(u, c, out=np.zeros_like(u), where=c > 0)

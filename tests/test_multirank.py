@@ -82,3 +82,37 @@ def test_two_gloo_ranks_equal_one(tmp_path, orc):
     el = orc.eloc(ints.h, ints.eri, 0.0, 14, s.keys, s.psi)
     m, var, w, n = orc.reduce(el, s.counts)
     assert W == w and abs(complex(er, ei) - m) <= 1e-12 * abs(m) and abs(V - var) <= 1e-10 * var
+
+
+def test_plan_replicas_balances_and_covers():
+    from paper_2506_23809_gb300 import inputs as I
+    from paper_2506_23809_gb300.shards import job_cost, plan_replicas
+    specs = I.batched_molecule_specs(64)
+
+    def pairs(n_orb, ne):
+        K, o = n_orb // 2, ne // 2
+        v = K - o
+        s = o * v
+        return 2 * s + 2 * (o * (o - 1) // 2) * (v * (v - 1) // 2) + s * s
+    jobs = [(sp["n_u"], pairs(sp["n_orb"], sp["n_elec"])) for sp in specs]
+    for n_rep in (1, 2, 3, 8):
+        plan = plan_replicas(jobs, n_rep)
+        # every row of every job exactly once
+        seen = {j: [] for j in range(len(jobs))}
+        for rep in plan:
+            for j, r0, r1 in rep:
+                seen[j].append((r0, r1))
+        for j, (n, _) in enumerate(jobs):
+            rs = sorted(seen[j])
+            assert rs[0][0] == 0 and rs[-1][1] == n and all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
+        loads = [sum(job_cost(r1 - r0, jobs[j][1]) for j, r0, r1 in rep) for rep in plan]
+        total = sum(job_cost(n, p) for n, p in jobs)
+        # within 10 % of a fair share (the largest molecule is cut into row ranges)
+        assert max(loads) <= 1.10 * total / n_rep + 1e-9
+
+
+def test_density_prediction():
+    from paper_2506_23809_gb300.shards import density, predicted_unique
+    d = density([50, 0, 30], [100, 0, 30])
+    assert np.allclose(d, [0.5, 0.0, 1.0])
+    assert np.allclose(predicted_unique([200, 10, 60], d), [100.0, 0.0, 60.0])
