@@ -387,6 +387,14 @@ def run_ours(args):
                               f"({peak_src} sm_max_mhz)",
                 "kernel_ms": 1e3 * main_s, "kernel_pairs_per_s": pairs_rank / main_s,
                 "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    try:  # measured ceilings beside the derived one (probes of the library, after the timed region)
+        probe = B.qc_probe_peaks()
+        roofline["alu_probe_gops"] = probe["alu_ops_per_s"] / 1e9
+        roofline["alu_probe_frac_of_peak"] = probe["alu_ops_per_s"] / peak_ops
+        roofline["l2_gather_probe_gbs"] = probe["l2_gather_gbs"]
+        # the candidates that reach the bucket table: 16 B each, per launch
+    except Exception as ex:  # noqa: BLE001 -- a probe failure must not lose the bench line
+        roofline["probe_error"] = str(ex)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -366,6 +366,14 @@ qc_status qc_server_stats(qc_server* server, uint64_t* stats4);
 qc_status qc_server_set_option(qc_server* server, int option, int64_t value);
 qc_status qc_server_destroy(qc_server* server);  /* finishes queued work first */
 
+/* Measurement probes (no counterpart in the paper; used by the benchmark to report measured
+ * ceilings beside the derived ones).  On the current device, synchronously:
+ *   alu_ops_per_s  integer throughput of the filter test's operation mix (shift, funnel
+ *                  shift, shift, XOR; independent chains, 2,048 threads per SM), or NULL
+ *   l2_gather_gbs  random 16-byte loads from a 4 MB table resident in L2, GB/s, or NULL
+ * Allocates and frees about 4 MB of device memory. */
+qc_status qc_probe_peaks(double* alu_ops_per_s, double* l2_gather_gbs, void* stream);
+
 /* Launch shape of the last evaluation on this handle: {kernel (1 direct, 2 filtered,
  * 3 filtered with pair lists formed on the fly), grid CTAs, warps per CTA, unroll, dynamic
  * shared memory bytes, log2 filter words}. */

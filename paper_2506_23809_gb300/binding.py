@@ -92,6 +92,8 @@ def load_library(path: str = LIB_PATH):
     lib.qc_eloc_export.restype = i32
     lib.qc_eloc_apply.argtypes = [P, P, P, i64, P, P, P, P, P, P]
     lib.qc_eloc_apply.restype = i32
+    lib.qc_probe_peaks.argtypes = [P, P, P]
+    lib.qc_probe_peaks.restype = i32
     lib.qc_dedup_workspace_bytes.argtypes = [i64]
     lib.qc_dedup_workspace_bytes.restype = i64
     lib.qc_dedup.argtypes = [P, i64, i32, P, P, P, P, ctypes.c_size_t, P]
@@ -300,6 +302,16 @@ def qc_eloc_apply(handle: QcHandle, psi, counts, elems, diag, psi_conn, eloc=Non
                            ctypes.c_void_p(stream.cuda_stream))
     _check(st, handle.ptr)
     return eloc
+
+
+def qc_probe_peaks(stream=None) -> dict:
+    """Measured ceilings on the current device: {'alu_ops_per_s', 'l2_gather_gbs'}."""
+    import torch
+    a, g = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(load_library().qc_probe_peaks(ctypes.byref(a), ctypes.byref(g), ctypes.c_void_p(stream.cuda_stream)), None)
+    return dict(alu_ops_per_s=a.value, l2_gather_gbs=g.value)
 
 
 def qc_dedup_workspace_bytes(n_raw: int) -> int:
