@@ -49,7 +49,8 @@ double now_s() {
 }
 
 struct Resident {  // a molecule's Hamiltonian kept on the device
-    qc_eloc* handle = nullptr;
+    qc_eloc* handle = nullptr;  // null while the scheduler creates it (outside the lock)
+    qc_status failed = QC_OK;   // creation failed: requests pinned to it fail the same way
     size_t bytes = 0;
     int users = 0;        // requests in flight using it
     double last_use = 0.0;
@@ -167,9 +168,12 @@ bool make_room(qc_server* S, size_t need) {
     return true;
 }
 
-// Admit pending requests in arrival order while memory and slots allow.  Called with the
-// lock held; uploads happen here too (the scheduler thread owns the device work).
-void admit(qc_server* S) {
+// Admit pending requests in arrival order while memory and slots allow.  Called by the
+// scheduler thread with the lock held; the lock is released while a new Hamiltonian is
+// created and while a request's inputs are copied to the device, so submit and poll do not
+// wait for those copies.  Only the scheduler thread admits, so a molecule created here is
+// complete before a later request for it is admitted.
+void admit(qc_server* S, std::unique_lock<std::mutex>& lk) {
     while (!S->pending.empty() && S->active < S->max_slots) {
         Request* r = S->pending.front();
         const qc_eloc_job& j = r->job;
@@ -183,20 +187,22 @@ void admit(qc_server* S) {
                 r->res = res;
             }
         }
+        if (res && !res->handle && res->failed != QC_OK) {  // its Hamiltonian could not be created
+            S->pending.pop_front();
+            r->result.status = res->failed;
+            res->users--;
+            r->res = nullptr;
+            r->done = true;
+            S->cv_done.notify_all();
+            continue;
+        }
         const size_t ham = res ? 0 : hamiltonian_bytes(j.n_orb, j.precision);
         if (!make_room(S, r->bytes + ham)) break;  // wait for memory to free up
         S->pending.pop_front();
         r->result.t_admit = now_s();
-        if (!res) {
+        const bool create = (res == nullptr);
+        if (create) {
             auto fresh = std::make_unique<Resident>();
-            qc_status st = qc_eloc_create(r->h.data(), r->eri.data(), j.e_core, j.n_orb, j.n_elec, j.precision,
-                                          QC_SAMPLE, &fresh->handle);
-            if (st != QC_OK) {
-                r->result.status = st;
-                r->done = true;
-                S->cv_done.notify_all();
-                continue;
-            }
             fresh->bytes = ham;
             fresh->users = 1;
             S->used += ham;
@@ -206,35 +212,50 @@ void admit(qc_server* S) {
             const uint64_t k = key ? key : (0x8000000000000000ULL | r->ticket);
             S->residents[k] = std::move(fresh);
         }
+        S->used += r->bytes;
+        S->active++;
+        lk.unlock();
+        // ---- outside the lock: the Hamiltonian and the inputs go to the device ----
+        qc_status st = QC_OK;
+        qc_eloc* made = nullptr;
+        if (create)
+            st = qc_eloc_create(r->h.data(), r->eri.data(), j.e_core, j.n_orb, j.n_elec, j.precision, QC_SAMPLE,
+                                &made);
         r->h.clear();
         r->h.shrink_to_fit();
         r->eri.clear();
         r->eri.shrink_to_fit();
-        res->last_use = now_s();
-        S->used += r->bytes;
-        S->active++;
         const size_t n = static_cast<size_t>(j.n_u);
-        r->pairs_per_row = std::max<long long>(1, qc_eloc_pairs_per_sample(res->handle));
         cudaStream_t up = S->upload;
-        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_ctr), sizeof(qc::Counters), up);
-        if (e == cudaSuccess) e = cudaMemsetAsync(r->d_ctr, 0, sizeof(qc::Counters), up);
-        if (n > 0) {
-            // stream-ordered allocations: no device-wide synchronisation while waves run
-            if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_keys), n * 16, up);
-            if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_counts), n * 8, up);
-            if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_psi), n * 16, up);
-            if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_eloc), n * 16, up);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(r->d_keys, j.samples, n * 16, cudaMemcpyHostToDevice, up);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(r->d_counts, j.counts, n * 8, cudaMemcpyHostToDevice, up);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(r->d_psi, j.psi, n * 16, cudaMemcpyHostToDevice, up);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(up);
+        cudaError_t e = cudaSuccess;
+        if (st == QC_OK) {
+            e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_ctr), sizeof(qc::Counters), up);
+            if (e == cudaSuccess) e = cudaMemsetAsync(r->d_ctr, 0, sizeof(qc::Counters), up);
+            if (n > 0) {
+                // stream-ordered allocations: no device-wide synchronisation while waves run
+                if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_keys), n * 16, up);
+                if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_counts), n * 8, up);
+                if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_psi), n * 16, up);
+                if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&r->d_eloc), n * 16, up);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(r->d_keys, j.samples, n * 16, cudaMemcpyHostToDevice, up);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(r->d_counts, j.counts, n * 8, cudaMemcpyHostToDevice, up);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(r->d_psi, j.psi, n * 16, cudaMemcpyHostToDevice, up);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(up);
+            }
         }
-        if (e != cudaSuccess) {
-            r->result.status = e == cudaErrorMemoryAllocation ? QC_ERR_OOM : QC_ERR_CUDA;
+        lk.lock();
+        if (create) {
+            if (st == QC_OK) res->handle = made;
+            else res->failed = st;
+        }
+        res->last_use = now_s();
+        if (st != QC_OK || e != cudaSuccess) {
+            r->result.status = st != QC_OK ? st : (e == cudaErrorMemoryAllocation ? QC_ERR_OOM : QC_ERR_CUDA);
             finish_request(S, r, up);
             S->cv_done.notify_all();
             continue;
         }
+        r->pairs_per_row = std::max<long long>(1, qc_eloc_pairs_per_sample(res->handle));
         S->ready.push_back(r);
     }
 }
@@ -397,7 +418,7 @@ void scheduler(qc_server* S) {
     std::unique_lock<std::mutex> lk(S->mu);
     while (true) {
         if (retire(S)) S->cv_done.notify_all();
-        admit(S);
+        admit(S, lk);
         // continuous batching: every free lane takes the requests that are ready now
         for (size_t i = 0; i < S->lanes.size() && !S->ready.empty(); ++i)
             if (!S->lanes[i].busy) launch_wave(S, S->lanes[i], static_cast<int>(i));
