@@ -169,21 +169,24 @@ def _cpu_baseline(ints, s, spec, target_s, pairs_per_sample):
     rng = np.random.default_rng(12345)
     perm = rng.permutation(s.n_u)
 
-    def run(rows):
+    def run(rows, threads):
         sel = np.sort(perm[:rows])
         t = time.perf_counter()
         oracle.eloc(ints.h, ints.eri, 0.0, spec["n_orb"], s.keys[sel], s.psi[sel], s.keys, s.psi,
-                    nthreads=cores)
+                    nthreads=threads)
         return time.perf_counter() - t
 
     probe = min(s.n_u, 4 * cores)
-    t0 = run(probe)
+    t0 = run(probe, cores)
     rows = int(min(s.n_u, max(probe, probe * target_s / max(t0, 1e-6))))
-    t1 = run(rows)
+    t1 = run(rows, cores)
+    # one thread, on a sample sized for about a tenth of the all-core time
+    rows1 = int(min(s.n_u, max(4, rows * 0.1 / cores)))
+    t2 = run(rows1, 1)
     return {"value": rows * pairs_per_sample / t1, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{rows} seeded random rows of the {s.n_u}-row table (all rows looked up in the "
-                      f"whole table), {t1:.1f} s on {cores} threads",
-            "samples_per_s": rows / t1}
+                      f"whole table), {t1:.1f} s on {cores} threads; single thread: {rows1} rows, {t2:.2f} s",
+            "samples_per_s": rows / t1, "value_1_thread": rows1 * pairs_per_sample / t2}
 
 
 def run_reference(args):
