@@ -103,6 +103,10 @@ typedef int qc_status;
 #define QC_OPT_GRID          6  /* 0 auto, else CTAs of the main kernel */
 #define QC_OPT_PREFILTER     7  /* 1 (default): drop single excitations whose new spin string no
                                    table key has, and the doubles built on them; 0: off */
+#define QC_OPT_CHUNK_PAIRS   9  /* excitation chunks: a sample's doubles are split over
+                                   ceil(pairs / value) warps (at most 8), each adding its share
+                                   and the last to finish combining them in chunk order; 0 or -1
+                                   (the default) one warp per sample */
 #define QC_OPT_LEAN          8  /* filtered kernel's per-warp lists: 0 auto (the layout that fits
                                    more warps), 1 stored pair lists, 2 pair lists formed on the
                                    fly from per-orbital values (same results, less shared memory) */
@@ -313,9 +317,13 @@ qc_status qc_batch_eval(qc_batch* batch, qc_eloc_summary* summaries, void* strea
 qc_status qc_batch_graph_launch(qc_batch* batch, qc_eloc_summary* summaries, void* stream);
 /* device ms of the last eager step: {table build, local-energy kernel, reduction} */
 qc_status qc_batch_timings(qc_batch* batch, float* ms3);
+/* excitation chunks of the batch's molecules (as QC_OPT_CHUNK_PAIRS of a handle: pairs
+ * per chunk, 0 or -1 one warp per sample, the default) */
+qc_status qc_batch_set_chunk_pairs(qc_batch* batch, int64_t chunk_pairs);
 /* autotuner: times every candidate shape on this batch (best of `iters`), keeps the
- * fastest; best3 (may be NULL) receives {unroll, warps, chunk} */
-qc_status qc_batch_autotune(qc_batch* batch, void* stream, int iters, int64_t* best3);
+ * fastest, then the excitation-chunk size at that shape; best4 (may be NULL) receives
+ * {unroll, warps, samples per fetch, pairs per chunk (-1: one warp per sample)} */
+qc_status qc_batch_autotune(qc_batch* batch, void* stream, int iters, int64_t* best4);
 
 /* ---- the serving form: asynchronous requests, continuous batching -----------------
  * qc_server_create starts a scheduler thread on `device`.  qc_eloc_submit queues one
@@ -376,8 +384,8 @@ qc_status qc_probe_peaks(double* alu_ops_per_s, double* l2_gather_gbs, void* str
 
 /* Launch shape of the last evaluation on this handle: {kernel (1 direct, 2 filtered,
  * 3 filtered with pair lists formed on the fly), grid CTAs, warps per CTA, unroll, dynamic
- * shared memory bytes, log2 filter words}. */
-qc_status qc_eloc_last_config(const qc_eloc* handle, int64_t* cfg6);
+ * shared memory bytes, log2 filter words, excitation chunks per sample}. */
+qc_status qc_eloc_last_config(const qc_eloc* handle, int64_t* cfg7);
 
 #ifdef __cplusplus
 }

@@ -22,6 +22,7 @@ QC_SAMPLE, QC_FULL = 0, 1
 QC_OPT_TIMING, QC_OPT_KERNEL, QC_OPT_FILTER_LOG2W, QC_OPT_WARPS, QC_OPT_UNROLL, QC_OPT_GRID = 1, 2, 3, 4, 5, 6
 QC_OPT_PREFILTER = 7
 QC_OPT_LEAN = 8
+QC_OPT_CHUNK_PAIRS = 9
 QC_SRV_OPT_QUANTUM = 1
 QC_SRV_OPT_OLDEST_PCT = 2
 STATUS_NAMES = {0: "QC_OK", 1: "QC_PENDING", -1: "QC_ERR_ARG", -2: "QC_ERR_UNSORTED", -3: "QC_ERR_DUP",
@@ -109,8 +110,10 @@ def load_library(path: str = LIB_PATH):
     lib.qc_batch_graph_launch.argtypes = [P, P, P]
     lib.qc_batch_timings.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
     lib.qc_batch_autotune.argtypes = [P, P, i32, ctypes.POINTER(ctypes.c_int64)]
+    lib.qc_batch_set_chunk_pairs.argtypes = [P, i64]
     for f in ("qc_batch_create", "qc_batch_destroy", "qc_batch_set_inputs", "qc_batch_set_config",
-              "qc_batch_config", "qc_batch_eval", "qc_batch_graph_launch", "qc_batch_timings", "qc_batch_autotune"):
+              "qc_batch_config", "qc_batch_eval", "qc_batch_graph_launch", "qc_batch_timings", "qc_batch_autotune",
+              "qc_batch_set_chunk_pairs"):
         getattr(lib, f).restype = i32
     _lib = lib
     return lib
@@ -177,10 +180,10 @@ def qc_eloc_timings(handle: QcHandle):
 
 
 def qc_eloc_last_config(handle: QcHandle) -> dict:
-    c = (ctypes.c_int64 * 6)()
+    c = (ctypes.c_int64 * 7)()
     _check(load_library().qc_eloc_last_config(handle.ptr, c), handle.ptr)
     return dict(kernel=int(c[0]), grid=int(c[1]), warps=int(c[2]), unroll=int(c[3]), smem=int(c[4]),
-                filter_log2w=int(c[5]))
+                filter_log2w=int(c[5]), chunks=int(c[6]))
 
 
 def _dptr(t, name, dtype_ok, shape_last=None):
@@ -474,9 +477,13 @@ def qc_batch_timings(batch: QcBatch):
 def qc_batch_autotune(batch: QcBatch, stream=None, iters: int = 2):
     import torch
     s = stream or torch.cuda.current_stream()
-    best = (ctypes.c_int64 * 3)()
+    best = (ctypes.c_int64 * 4)()
     _bcheck(load_library().qc_batch_autotune(batch.ptr, ctypes.c_void_p(s.cuda_stream), int(iters), best), batch)
-    return dict(unroll=int(best[0]), warps=int(best[1]), chunk=int(best[2]))
+    return dict(unroll=int(best[0]), warps=int(best[1]), chunk=int(best[2]), chunk_pairs=int(best[3]))
+
+
+def qc_batch_set_chunk_pairs(batch: QcBatch, chunk_pairs: int):
+    _bcheck(load_library().qc_batch_set_chunk_pairs(batch.ptr, int(chunk_pairs)), batch)
 
 
 # ----------------------------------------------------------------------------------

@@ -234,6 +234,8 @@ qc_status qc_eloc_destroy(qc_eloc* H) {
     free_dev(H->d_ctr);
     free_dev(H->d_sum);
     free_dev(H->d_gpart);
+    free_dev(H->d_cpart);
+    free_dev(H->d_cticket);
     for (auto& ev : H->ev)
         if (ev) cudaEventDestroy(ev);
     delete H;
@@ -264,6 +266,10 @@ qc_status qc_eloc_set_option(qc_eloc* H, int option, int64_t value) {
             H->opt_unroll = static_cast<int>(value);
             return QC_OK;
         case QC_OPT_PREFILTER: H->opt_prefilter = value ? 1 : 0; return QC_OK;
+        case QC_OPT_CHUNK_PAIRS:
+            if (value < -1) return fail(H, QC_ERR_ARG, "QC_OPT_CHUNK_PAIRS: -1, 0 or pairs per chunk");
+            H->opt_chunk_pairs = value;
+            return QC_OK;
         case QC_OPT_LEAN:
             if (value < 0 || value > 2) return fail(H, QC_ERR_ARG, "QC_OPT_LEAN: 0, 1 or 2");
             H->opt_lean = static_cast<int>(value);
@@ -381,7 +387,9 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
     int per_sm = qc::max_active_ctas(c.kernel, H->precision, c.unroll, 32 * c.warps, c.smem, c.lean);
     if (per_sm < 1) return fail(H, QC_ERR_CAPACITY, "main kernel cannot be resident with this shape");
     long long grid = H->opt_grid ? H->opt_grid : static_cast<long long>(per_sm) * H->sm_count;
-    const long long need = (n_u + c.warps - 1) / c.warps;
+    const long long cp = H->opt_chunk_pairs == 0 ? qc::kDefaultChunkPairs : H->opt_chunk_pairs;
+    c.chunks = qc::exc_chunks(sp.pairs, cp);
+    const long long need = (n_u * c.chunks + c.warps - 1) / c.warps;
     grid = std::max<long long>(1, std::min(grid, need));
     c.grid = static_cast<int>(grid);
     return QC_OK;
@@ -497,6 +505,25 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     ep.T = H->d_T;
     ep.mode = H->mode;
     ep.lean = cfg.lean;
+    ep.chunks = cfg.chunks;
+    if (cfg.chunks > 1 && n_u > 0) {
+        const size_t recs = static_cast<size_t>(n_u) * cfg.chunks;
+        if (recs > H->cpart_cap) {
+            free_dev(H->d_cpart);
+            H->cpart_cap = 0;
+            QC_CHK(cudaMalloc(&H->d_cpart, recs * sizeof(qc::ChunkRec)), "cudaMalloc chunk records");
+            H->cpart_cap = recs;
+        }
+        if (static_cast<size_t>(n_u) > H->cticket_cap) {
+            free_dev(H->d_cticket);
+            H->cticket_cap = 0;
+            QC_CHK(cudaMalloc(&H->d_cticket, static_cast<size_t>(n_u) * sizeof(unsigned)), "cudaMalloc chunk tickets");
+            H->cticket_cap = static_cast<size_t>(n_u);
+        }
+        QC_CHK(cudaMemsetAsync(H->d_cticket, 0, static_cast<size_t>(n_u) * sizeof(unsigned), s), "memset tickets");
+        ep.cpart = H->d_cpart;
+        ep.cticket = H->d_cticket;
+    }
     QC_CHK(qc::launch_eloc_main(H->sp, tp, ep, cfg, s), "main kernel launch");
     if (H->opt_timing) QC_CHK(cudaEventRecord(H->ev[2], s), "cudaEventRecord");
     QC_CHK(qc::launch_reduce(ep, H->d_part, qc::reduce_blocks(n_u), H->d_sum, H->sp.pairs, s),
@@ -523,14 +550,15 @@ qc_status qc_eloc_timings(qc_eloc* H, float* ms3) {
 }
 
 // Launch shape of the last evaluation: {kernel, grid, warps, unroll, smem bytes, filter log2 words}.
-qc_status qc_eloc_last_config(const qc_eloc* H, int64_t* cfg6) {
-    if (!H || !cfg6) return QC_ERR_ARG;
-    cfg6[0] = H->last_cfg.kernel == 2 && H->last_cfg.lean ? 3 : H->last_cfg.kernel;
-    cfg6[1] = H->last_cfg.grid;
-    cfg6[2] = H->last_cfg.warps;
-    cfg6[3] = H->last_cfg.unroll;
-    cfg6[4] = static_cast<int64_t>(H->last_cfg.smem);
-    cfg6[5] = H->last_fw;
+qc_status qc_eloc_last_config(const qc_eloc* H, int64_t* cfg7) {
+    if (!H || !cfg7) return QC_ERR_ARG;
+    cfg7[0] = H->last_cfg.kernel == 2 && H->last_cfg.lean ? 3 : H->last_cfg.kernel;
+    cfg7[1] = H->last_cfg.grid;
+    cfg7[2] = H->last_cfg.warps;
+    cfg7[3] = H->last_cfg.unroll;
+    cfg7[4] = static_cast<int64_t>(H->last_cfg.smem);
+    cfg7[5] = H->last_fw;
+    cfg7[6] = H->last_cfg.chunks > 1 ? H->last_cfg.chunks : 1;
     return QC_OK;
 }
 

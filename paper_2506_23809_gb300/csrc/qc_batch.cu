@@ -63,6 +63,7 @@ struct qc_batch {
     qc_eloc_summary* d_sums = nullptr;
     // launch shape
     int unroll = 4, warps = 0, chunk = 1;
+    long long chunk_pairs = qc::kDefaultChunkPairs;  // excitation chunks (<= 0: one warp per sample)
     int warps_used = 0, grid = 0, n_run = 0, red_blocks = 1;
     long long n_keys = 0;
     size_t smem = 0;
@@ -104,7 +105,7 @@ qc_status prepare(qc_batch* B) {
     std::vector<qc::MolWork> mw(M);
     std::vector<long long> key_off(M + 1, 0);
     size_t off = align256(static_cast<size_t>(M) * sizeof(unsigned long long));  // sample cursors
-    struct Lay { size_t slots, filter, sets, ctr, part, sum; unsigned long long nb; int fw; };
+    struct Lay { size_t slots, filter, sets, ctr, part, sum, cpart, ctick; unsigned long long nb; int fw, chunks; };
     std::vector<Lay> lay(M);
     const size_t fixed0 = qc::smem_fixed_bytes();
     const int wcap = B->warps > 0 ? std::min(B->warps, qc::kFilteredMaxWarps) : 16;  // 16: the spill-free bound
@@ -142,6 +143,13 @@ qc_status prepare(qc_batch* B) {
         L.sets = off; off = align256(off + 2 * L.nb * 8);
         L.filter = off; off = align256(off + (static_cast<size_t>(4) << L.fw));
         L.ctr = off; off = align256(off + sizeof(qc::Counters));
+        L.chunks = qc::exc_chunks(B->handles[m]->sp.pairs, B->chunk_pairs);
+        L.cpart = L.ctick = 0;
+        if (L.chunks > 1 && B->in[m].n_u > 0) {
+            const size_t nu = static_cast<size_t>(B->in[m].n_u);
+            L.cpart = off; off = align256(off + nu * L.chunks * sizeof(qc::ChunkRec));
+            L.ctick = off; off = align256(off + nu * sizeof(unsigned));  // zeroed with the arena
+        }
         L.part = off; off = align256(off + static_cast<size_t>(qc::reduce_blocks(B->in[m].n_u)) * 4 * sizeof(double));
         L.sum = 0;
         key_off[m + 1] = key_off[m] + B->in[m].n_u;
@@ -195,6 +203,10 @@ qc_status prepare(qc_batch* B) {
         P.ep.T = H->d_T;
         P.ep.mode = QC_SAMPLE;
         P.ep.lean = lean[m];
+        P.ep.chunks = L.chunks;
+        P.ep.cpart = L.cpart ? static_cast<void*>(A + L.cpart) : nullptr;
+        P.ep.cticket = L.ctick ? reinterpret_cast<unsigned*>(A + L.ctick) : nullptr;
+        if (P.ep.chunks > 1 && !P.ep.cpart) P.ep.chunks = 1;
         P.active_warps = act[m];
         P.warp_stride = stride[m];
         P.r0 = I.r0;
@@ -424,6 +436,15 @@ qc_status qc_batch_set_config(qc_batch* B, int unroll, int warps, int chunk) {
     return QC_OK;
 }
 
+qc_status qc_batch_set_chunk_pairs(qc_batch* B, int64_t chunk_pairs) {
+    if (!B) return QC_ERR_ARG;
+    if (chunk_pairs < -1) return bfail(B, QC_ERR_ARG, "chunk_pairs: -1, 0 or pairs per chunk");
+    B->chunk_pairs = chunk_pairs == 0 ? qc::kDefaultChunkPairs : (chunk_pairs < 0 ? 0 : chunk_pairs);
+    B->dirty = true;
+    drop_graph(B);
+    return QC_OK;
+}
+
 qc_status qc_batch_eval(qc_batch* B, qc_eloc_summary* sums, void* stream) {
     if (!B) return QC_ERR_ARG;
     int dev = 0;
@@ -497,49 +518,78 @@ qc_status qc_batch_config(const qc_batch* B, int64_t* cfg6) {
 }
 
 // Time every candidate shape on this batch (eager evaluations on `stream`, main kernel
-// only, best of `iters`) and keep the fastest.  best3 (optional): {unroll, warps, chunk}.
-qc_status qc_batch_autotune(qc_batch* B, void* stream, int iters, int64_t* best3) {
+// only, best of `iters`) and keep the fastest, then the excitation-chunk size at that
+// shape.  best4 (optional): {unroll, warps, samples per fetch, pairs per chunk (-1: none)}.
+qc_status qc_batch_autotune(qc_batch* B, void* stream, int iters, int64_t* best4) {
     if (!B) return QC_ERR_ARG;
     if (iters < 1) iters = 1;
+    // best of `iters` timed steps (after one untimed) of the current shape; capacity -> skip
+    auto time_shape = [&](float& t_best) -> qc_status {
+        qc_status st = prepare(B);
+        if (st != QC_OK) return st;
+        t_best = 3.0e38f;
+        for (int it = 0; it < iters + 1; ++it) {
+            st = enqueue(B, nullptr, static_cast<cudaStream_t>(stream), true);
+            if (st != QC_OK) return st;
+            float ms3[3];
+            B->timed = true;
+            st = qc_batch_timings(B, ms3);
+            if (st != QC_OK) return st;
+            if (it > 0) t_best = std::min(t_best, ms3[1]);
+        }
+        return QC_OK;
+    };
     const int warps_c[] = {8, 12, 16, 20};
     const int units_c[] = {1, 4};  // samples per fetch
     const int unroll_c[] = {2, 4};
     float best = 3.0e38f;
     int bu = 4, bw = 0, bp = 1;
+    const long long keep_cp = B->chunk_pairs;
     for (int ur : unroll_c)
         for (int w : warps_c)
             for (int up : units_c) {
                 qc_status st = qc_batch_set_config(B, ur, w, up);
                 if (st != QC_OK) return st;
-                st = prepare(B);
+                B->chunk_pairs = keep_cp;
+                float t = 0.f;
+                st = time_shape(t);
                 if (st == QC_ERR_CAPACITY) continue;
                 if (st != QC_OK) return st;
                 if (B->warps_used < w) continue;  // cap above what any molecule fits: tried already
-                float t_best = 3.0e38f;
-                for (int it = 0; it < iters + 1; ++it) {
-                    st = enqueue(B, nullptr, static_cast<cudaStream_t>(stream), true);
-                    if (st != QC_OK) return st;
-                    float ms3[3];
-                    B->timed = true;
-                    st = qc_batch_timings(B, ms3);
-                    if (st != QC_OK) return st;
-                    if (it > 0) t_best = std::min(t_best, ms3[1]);
-                }
-                if (t_best < best) {
-                    best = t_best;
+                if (t < best) {
+                    best = t;
                     bu = ur;
                     bw = w;
                     bp = up;
                 }
             }
+    // then the excitation-chunk size at that shape (0: one warp per sample)
+    long long bc = keep_cp;
+    const long long cp_c[] = {qc::kChunkPairsProbe / 2, qc::kChunkPairsProbe, qc::kChunkPairsProbe * 2, 0};
     qc_status st = qc_batch_set_config(B, bu, bw, bp);
     if (st != QC_OK) return st;
+    for (long long cp : cp_c) {
+        if (cp == keep_cp) continue;
+        B->chunk_pairs = cp;
+        B->dirty = true;
+        float t = 0.f;
+        st = time_shape(t);
+        if (st == QC_ERR_CAPACITY) continue;
+        if (st != QC_OK) return st;
+        if (t < best) {
+            best = t;
+            bc = cp;
+        }
+    }
+    B->chunk_pairs = bc;
+    B->dirty = true;
     st = prepare(B);
     if (st != QC_OK) return st;
-    if (best3) {
-        best3[0] = bu;
-        best3[1] = bw;
-        best3[2] = bp;
+    if (best4) {
+        best4[0] = bu;
+        best4[1] = bw;
+        best4[2] = bp;
+        best4[3] = bc > 0 ? bc : -1;
     }
     return QC_OK;
 }

@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(MAXT) eloc_batch_kernel(const __grid_constant_
         for (int t = threadIdx.x; t < static_cast<int>(sizeof(MolParams) / 4); t += blockDim.x) dst[t] = src[t];
         if (threadIdx.x == 0)
             skip = *reinterpret_cast<volatile unsigned long long*>(bp.next + k) >=
-                   static_cast<unsigned long long>(bp.mols[m].r1 - bp.mols[m].r0);
+                   static_cast<unsigned long long>(bp.mols[m].r1 - bp.mols[m].r0) *
+                       static_cast<unsigned long long>(bp.mols[m].ep.chunks > 1 ? bp.mols[m].ep.chunks : 1);
         __syncthreads();
         if (skip) continue;  // other CTAs took all of this molecule's samples
         const unsigned fbytes = 4u << mp.tp.fw;
@@ -108,20 +109,25 @@ __global__ void __launch_bounds__(MAXT) eloc_batch_kernel(const __grid_constant_
         const int nw = mp.active_warps;
         if (warp < nw) {
             unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * mp.warp_stride;
-            // rows [r0, r1) of this molecule: all of them, or one slice of a long request
-            const unsigned long long n_run = static_cast<unsigned long long>(mp.r1 - mp.r0);
+            // rows [r0, r1) of this molecule: all of them, or one slice of a long request;
+            // with C excitation chunks per sample a work item is (row, chunk)
+            const unsigned long long C = static_cast<unsigned long long>(mp.ep.chunks > 1 ? mp.ep.chunks : 1);
+            const unsigned long long n_run = static_cast<unsigned long long>(mp.r1 - mp.r0) * C;
             const long long r0 = mp.r0;
             while (true) {
-                unsigned long long s0 = 0;
-                if (lane == 0) s0 = atomicAdd(bp.next + k, static_cast<unsigned long long>(bp.chunk));
-                s0 = __shfl_sync(0xffffffffu, s0, 0);
-                if (s0 >= n_run) break;
-                const unsigned long long s1 = s0 + bp.chunk < n_run ? s0 + bp.chunk : n_run;
-                for (unsigned long long s = s0; s < s1; ++s) {
+                unsigned long long i0 = 0;
+                if (lane == 0) i0 = atomicAdd(bp.next + k, static_cast<unsigned long long>(bp.chunk));
+                i0 = __shfl_sync(0xffffffffu, i0, 0);
+                if (i0 >= n_run) break;
+                const unsigned long long i1 = i0 + bp.chunk < n_run ? i0 + bp.chunk : n_run;
+                for (unsigned long long it = i0; it < i1; ++it) {
+                    const unsigned long long q = it / C;
+                    const long long s = r0 + static_cast<long long>(q);
+                    const int c = static_cast<int>(it - q * C);
                     if (mp.ep.lean)
-                        run_sample<PREC, U, true, 1>(mp.sp, mp.tp, mp.ep, r0 + static_cast<long long>(s), lane, smem, wl, filt);
+                        run_sample<PREC, U, true, 1>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));
                     else
-                        run_sample<PREC, U, true, 0>(mp.sp, mp.tp, mp.ep, r0 + static_cast<long long>(s), lane, smem, wl, filt);
+                        run_sample<PREC, U, true, 0>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));
                 }
             }
         }

@@ -602,10 +602,52 @@ __device__ __forceinline__ bool sample_setup(const SysParams& sp, ulonglong2 x, 
     return true;
 }
 
-// Per-sample finish: reduce the lane accumulators and write the outputs.
+// Lane 0's part of a sample's finish: E_loc from the warp sums and the outputs.
+template <int PREC>
+__device__ __forceinline__ void write_sample(const EvalParams& ep, long long s, double ediag, double2 psix,
+                                             double sre, double sim, unsigned long long hits,
+                                             unsigned long long rows, long long sgn, unsigned long long miss) {
+    double2 e;
+    const double n2 = psix.x * psix.x + psix.y * psix.y;
+    unsigned flags = 0;
+    bool bad = false;
+    if (n2 == 0.0) {
+        flags |= QC_FLAG_ZERO_PSI;
+        bad = true;
+    }
+    if (miss) {
+        flags |= QC_FLAG_MISSING;
+        bad = true;
+    }
+    if (bad) {
+        e.x = __longlong_as_double(0x7ff8000000000000LL);
+        e.y = e.x;
+    } else if (PREC == QC_FP64) {
+        // sum H psi(x') / psi(x) = S conj(psi) / |psi|^2
+        const double inv = 1.0 / n2;
+        e.x = ediag + (sre * psix.x + sim * psix.y) * inv;
+        e.y = (sim * psix.x - sre * psix.y) * inv;
+    } else {
+        e.x = ediag + sre;
+        e.y = sim;
+    }
+    ep.eloc[s] = e;
+    if (ep.hit_count) ep.hit_count[s] = static_cast<uint32_t>(hits);
+    if (ep.hit_rowsum) ep.hit_rowsum[s] = rows;
+    if (ep.hit_signsum) ep.hit_signsum[s] = sgn;
+    if (hits) atomicAdd(&ep.ctr->hits, hits);
+    if (miss) atomicAdd(&ep.ctr->missing, miss);
+    if (bad) atomicAdd(&ep.ctr->bad, 1ULL);
+    if (flags) atomicOr(&ep.ctr->flags, flags);
+}
+
+// Per-sample finish: reduce the lane accumulators and write the outputs.  With several
+// excitation chunks per sample (C > 1) each chunk stores its warp sums; the warp that
+// finishes the last chunk of the sample adds the C records in chunk order (the result does
+// not depend on which warp finishes last) and writes the outputs.
 template <int PREC>
 __device__ __forceinline__ void sample_finish(const EvalParams& ep, long long s, int lane,
-                                              double ediag, double2 psix, Acc& acc) {
+                                              double ediag, double2 psix, Acc& acc, int c = 0, int C = 1) {
     double sre, sim;
     if (PREC == QC_FP64) {
         sre = warp_sum(acc.re);
@@ -618,40 +660,36 @@ __device__ __forceinline__ void sample_finish(const EvalParams& ep, long long s,
     const unsigned long long rows = warp_sum_u64(acc.rowsum);
     const long long sgn = static_cast<long long>(warp_sum_u64(static_cast<unsigned long long>(acc.signsum)));
     const unsigned long long miss = warp_sum_u64(acc.missing);
-    if (lane == 0) {
-        double2 e;
-        const double n2 = psix.x * psix.x + psix.y * psix.y;
-        unsigned flags = 0;
-        bool bad = false;
-        if (n2 == 0.0) {
-            flags |= QC_FLAG_ZERO_PSI;
-            bad = true;
-        }
-        if (miss) {
-            flags |= QC_FLAG_MISSING;
-            bad = true;
-        }
-        if (bad) {
-            e.x = __longlong_as_double(0x7ff8000000000000LL);
-            e.y = e.x;
-        } else if (PREC == QC_FP64) {
-            // sum H psi(x') / psi(x) = S conj(psi) / |psi|^2
-            const double inv = 1.0 / n2;
-            e.x = ediag + (sre * psix.x + sim * psix.y) * inv;
-            e.y = (sim * psix.x - sre * psix.y) * inv;
-        } else {
-            e.x = ediag + sre;
-            e.y = sim;
-        }
-        ep.eloc[s] = e;
-        if (ep.hit_count) ep.hit_count[s] = static_cast<uint32_t>(hits);
-        if (ep.hit_rowsum) ep.hit_rowsum[s] = rows;
-        if (ep.hit_signsum) ep.hit_signsum[s] = sgn;
-        if (hits) atomicAdd(&ep.ctr->hits, hits);
-        if (miss) atomicAdd(&ep.ctr->missing, miss);
-        if (bad) atomicAdd(&ep.ctr->bad, 1ULL);
-        if (flags) atomicOr(&ep.ctr->flags, flags);
+    if (lane != 0) return;
+    if (C <= 1) {
+        write_sample<PREC>(ep, s, ediag, psix, sre, sim, hits, rows, sgn, miss);
+        return;
     }
+    ChunkRec* rec = static_cast<ChunkRec*>(ep.cpart) + s * C;
+    ChunkRec mine;
+    mine.re = sre;
+    mine.im = sim;
+    mine.hits = hits;
+    mine.rowsum = rows;
+    mine.signsum = sgn;
+    mine.missing = miss;
+    rec[c] = mine;
+    __threadfence();
+    if (atomicAdd(ep.cticket + s, 1u) != static_cast<unsigned>(C - 1)) return;
+    __threadfence();
+    double re = 0.0, im = 0.0;
+    unsigned long long th = 0, tr = 0, tm = 0;
+    long long ts = 0;
+    for (int k = 0; k < C; ++k) {
+        const volatile ChunkRec* r = rec + k;
+        re += r->re;
+        im += r->im;
+        th += r->hits;
+        tr += r->rowsum;
+        ts += r->signsum;
+        tm += r->missing;
+    }
+    write_sample<PREC>(ep, s, ediag, psix, re, im, th, tr, ts, tm);
 }
 
 __device__ __forceinline__ void invalid_sample(const EvalParams& ep, long long s, int lane) {
@@ -708,7 +746,7 @@ template <int PREC, int U, bool FILTER, int LEAN>
 __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParams& tp,
                                            const EvalParams& ep, long long s, int lane,
                                            unsigned char* smem, unsigned char* wl,
-                                           const uint32_t* filt) {
+                                           const uint32_t* filt, int c = 0, int C = 1) {
     const unsigned long long* T64 = reinterpret_cast<const unsigned long long*>(smem + kOffT);
     const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
     uint32_t* q = reinterpret_cast<uint32_t*>(wl + 256);
@@ -734,7 +772,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     unsigned long long hx, As, Bs, hxa;
     double ediag;
     if (!sample_setup(sp, x, lane, wl, T64, hx, ediag, As, Bs, hxa)) {
-        invalid_sample(ep, s, lane);
+        if (c == 0) invalid_sample(ep, s, lane);  // reported once, by the first chunk
         return;
     }
     if (FILTER) {
@@ -840,10 +878,11 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     else if (cls == 2) { oo = oPAo; n1 = sp.npoa; io = oPAv; n2 = sp.npva; }
                     else if (cls == 3) { oo = oPBo; n1 = sp.npob; io = oPBv; n2 = sp.npvb; }
                     else if (cls == 4) { oo = oSA; n1 = nsa2; io = oSB; n2 = nsb2; }
-                } while (cls < 5 && (n1 == 0 || n2 == 0));
+                } while (cls < 5 && (n1 == 0 || n2 == 0 || (cls < 2 ? c != 0 : c * U >= n1)));
                 done = cls >= 5;
                 pairs = lean && (cls == 2 || cls == 3);
-                u0 = 0;
+                // excitation chunk c of C: the singles in chunk 0, outer blocks c, c + C, ...
+                u0 = cls >= 2 ? c * U : 0;
                 w0 = 0;
                 need_class = false;
                 need_outer = true;
@@ -912,7 +951,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 } while (w0 < n2 && qn < 32);
                 if (w0 >= n2) {
                     w0 = 0;
-                    u0 += U;
+                    u0 += cls >= 2 ? U * C : U;
                     need_outer = true;
                     if (u0 >= n1) need_class = true;
                 }
@@ -965,7 +1004,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         }
         if (done) break;
     }
-    sample_finish<PREC>(ep, s, lane, ediag, psix, acc);
+    sample_finish<PREC>(ep, s, lane, ediag, psix, acc, c, C);
     __syncwarp();
 }
 

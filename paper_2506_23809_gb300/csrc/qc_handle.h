@@ -37,6 +37,11 @@ struct qc_eloc {
     qc_eloc_summary* d_sum = nullptr;
     double* d_gpart = nullptr;  // Eq. 4 contraction partials
     size_t gpart_cap = 0;       // doubles
+    void* d_cpart = nullptr;    // excitation-chunk records
+    size_t cpart_cap = 0;       // records
+    unsigned* d_cticket = nullptr;
+    size_t cticket_cap = 0;     // samples
+    long long opt_chunk_pairs = 0;  // 0 default, < 0 one chunk per sample, else pairs per chunk
     int opt_timing = 0, opt_kernel = 0, opt_fw = 0, opt_warps = 0, opt_unroll = 0, opt_grid = 0;
     int opt_prefilter = 1;
     int opt_lean = 0;  // 0 auto, 1 stored pair lists, 2 formed on the fly

@@ -79,7 +79,31 @@ struct EvalParams {
     const unsigned long long* T;  // 128 entries of the linear key hash
     int mode;                     // 0 SAMPLE, 1 FULL
     int lean;                     // pair hash lists formed on the fly (batch kernel)
+    int chunks;                   // excitation chunks per sample (1: a warp owns a sample)
+    int pad_;
+    void* cpart;                  // chunks > 1: ChunkRec[n_u * chunks]
+    unsigned* cticket;            // chunks > 1: per-sample count of finished chunks (zeroed)
 };
+
+// One excitation chunk's share of a sample (chunks > 1): the warp sums of its hits.
+struct ChunkRec {
+    double re, im;
+    unsigned long long hits, rowsum;
+    long long signsum;
+    unsigned long long missing;
+};
+
+// Excitation chunks of a sample with `pairs` connected pairs: ceil(pairs / chunk_pairs),
+// 1..8; chunk_pairs <= 0 means one chunk (a warp owns the whole sample).  Off by default:
+// every chunk repeats the sample's set-up, which on the measured workloads costs more than
+// the shorter tails save; the batch autotuner tries sizes around kChunkPairsProbe.
+constexpr long long kDefaultChunkPairs = 0;
+constexpr long long kChunkPairsProbe = 262144;
+inline int exc_chunks(long long pairs, long long chunk_pairs) {
+    if (chunk_pairs <= 0) return 1;
+    const long long c = (pairs + chunk_pairs - 1) / chunk_pairs;
+    return static_cast<int>(c < 1 ? 1 : (c > 8 ? 8 : c));
+}
 
 // A batch of molecules evaluated in one persistent launch.
 struct MolWork {  // writable workspace of one molecule of a batch
@@ -116,6 +140,7 @@ struct LaunchCfg {
     int unroll;
     size_t smem;
     int lean;     // filtered kernel: pair hash lists formed on the fly
+    int chunks;   // excitation chunks per sample
 };
 
 // host-side launchers (qc_kernels.cu)

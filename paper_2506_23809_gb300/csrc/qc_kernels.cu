@@ -83,13 +83,17 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
     unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * main_warp_bytes(sp, FILTER, LEAN == 1);
     // samples go to warps as they come free: one cursor for the grid, so a warp that drew
     // cheap samples takes more of them and the launch ends with little tail
-    const unsigned long long n_u = static_cast<unsigned long long>(ep.n_u);
+    // with C excitation chunks per sample a work item is (sample, chunk): item = s * C + c
+    const unsigned long long C = static_cast<unsigned long long>(ep.chunks > 1 ? ep.chunks : 1);
+    const unsigned long long items = static_cast<unsigned long long>(ep.n_u) * C;
     while (true) {
-        unsigned long long s = 0;
-        if (lane == 0) s = atomicAdd(&ep.ctr->next, 1ULL);
-        s = __shfl_sync(0xffffffffu, s, 0);
-        if (s >= n_u) break;
-        run_sample<PREC, U, FILTER, LEAN>(sp, tp, ep, static_cast<long long>(s), lane, smem, wl, filt);
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(&ep.ctr->next, 1ULL);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= items) break;
+        const unsigned long long s = it / C;
+        run_sample<PREC, U, FILTER, LEAN>(sp, tp, ep, static_cast<long long>(s), lane, smem, wl, filt,
+                                          static_cast<int>(it - s * C), static_cast<int>(C));
     }
 }
 

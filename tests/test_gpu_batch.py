@@ -102,3 +102,37 @@ def test_batch_equals_single_and_oracle(B, orc, prec):
     finally:
         for h in handles:
             B.qc_eloc_destroy(h)
+
+
+def test_batch_excitation_chunks_equal_single(B):
+    """With the same excitation-chunk size the batched evaluation stays bitwise equal to the
+    handle API for every molecule."""
+    import torch
+    mols = _molecules()
+    handles, singles, ins, outs = [], [], [], []
+    try:
+        for n, ne, ints, keys, counts, psi in mols:
+            h = B.qc_eloc_create(ints.h, ints.eri, 0.0, n, ne, 0)
+            B.qc_eloc_set_option(h, 9, 3000)
+            handles.append(h)
+            kt, ct, pt = _dev(B, keys, counts, psi)
+            e, _ = B.qc_eloc_eval(h, kt, ct, pt)
+            singles.append((e.cpu().numpy(), B.qc_eloc_summary_read(h), B.qc_eloc_last_config(h)["chunks"]))
+            ins.append((kt, ct, pt))
+            outs.append(torch.empty(len(keys), dtype=torch.complex128, device="cuda"))
+        assert max(c for _, _, c in singles) > 1
+        batch = B.qc_batch_create(handles)
+        try:
+            B.qc_batch_set_chunk_pairs(batch, 3000)
+            for m, (kt, ct, pt) in enumerate(ins):
+                B.qc_batch_set_inputs(batch, m, kt, ct, pt, outs[m])
+            B.qc_batch_eval(batch)
+            sums = B.qc_batch_summaries(batch)
+            for m, (e1, s1, _) in enumerate(singles):
+                assert np.array_equal(outs[m].cpu().numpy().view(np.uint64), e1.view(np.uint64)), m
+                assert sums[m]["e_re"] == s1["e_re"] and sums[m]["n_hits"] == s1["n_hits"]
+        finally:
+            B.qc_batch_destroy(batch)
+    finally:
+        for h in handles:
+            B.qc_eloc_destroy(h)

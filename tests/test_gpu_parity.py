@@ -304,3 +304,39 @@ def test_degenerate_inputs(B, orc):
             B.qc_eloc_eval(h, kt, torch.from_numpy(s.counts).cuda(), torch.from_numpy(s.psi).cuda(), kt, None)
     finally:
         B.qc_eloc_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_excitation_chunks(B, orc, prec):
+    """A sample's doubles split over C warps (QC_OPT_CHUNK_PAIRS): the connected sets, rows and
+    phases stay bit-exact, E_loc within the parity tolerance of the oracle and of the
+    one-warp evaluation, bitwise the same run to run; an invalid sample and a psi(x) = 0
+    sample are reported once."""
+    ints = I.make_integrals(26, 52, 5401)
+    keys = I.rank_weighted_samples(26, 7, 7, 2000, seed=5402)
+    counts = I.zipf_counts(2000, 100_000, 5403)
+    psi = I.lognormal_psi(2000, 5404)
+    psi[11] = 0.0
+    bad_keys = keys.copy()
+    bad_keys[7, 0] ^= np.uint64(1)             # one electron too many or too few
+    order = np.lexsort((bad_keys[:, 0], bad_keys[:, 1]))
+    bad_keys, psi_b, counts_b = bad_keys[order], psi[order], counts[order]
+    a = run_gpu(B, ints, 52, 14, bad_keys, counts_b, psi_b, prec=prec, opts={9: 4000})
+    b = run_gpu(B, ints, 52, 14, bad_keys, counts_b, psi_b, prec=prec, opts={9: 4000})
+    one = run_gpu(B, ints, 52, 14, bad_keys, counts_b, psi_b, prec=prec, opts={9: -1})
+    assert a["cfg"]["chunks"] == 7 and one["cfg"]["chunks"] == 1
+    assert np.array_equal(a["eloc"].view(np.uint64), b["eloc"].view(np.uint64))
+    assert np.array_equal(a["hits"], one["hits"]) and np.array_equal(a["signsum"], one["signsum"])
+    fin = np.isfinite(one["eloc"])
+    assert np.array_equal(np.isfinite(a["eloc"]), fin) and (~fin).sum() == 2
+    err = np.abs(a["eloc"][fin] - one["eloc"][fin]) / np.maximum(1.0, np.abs(one["eloc"][fin]))
+    assert err.max() <= (1e-12 if prec == 0 else 1e-5)
+    sa, so = a["summary"], one["summary"]
+    assert sa["n_bad"] == so["n_bad"] == 2 and sa["n_used"] == so["n_used"] == 1998
+    assert sa["n_hits"] == so["n_hits"] and sa["n_pairs"] == so["n_pairs"]
+    # against the oracle on the valid samples (it does not check electron counts itself)
+    want, det = orc.eloc(ints.h, ints.eri, 0.0, 52, bad_keys, psi_b, details=True)
+    ok = np.isfinite(want) & fin
+    assert np.array_equal(a["hits"][ok], det["hits"][ok]) and np.array_equal(a["signsum"][ok], det["signsum"][ok])
+    if prec == 0:
+        assert_eloc_close(a["eloc"][ok], want[ok])
