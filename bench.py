@@ -384,7 +384,8 @@ def run_ours(args):
             traffic = prof.get("dram_bytes_per_launch")
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
                 "frac": achieved / peak_ops, "traffic": traffic,
-                "kernel": "eloc_main_kernel (filtered)" if cfg["kernel"] == 2 else "eloc_main_kernel (unfiltered)",
+                "kernel": {1: "eloc_main_kernel (unfiltered)", 2: "eloc_main_kernel (filtered)",
+                           3: "eloc_main_kernel (filtered, lean lists)"}.get(cfg["kernel"], "eloc_main_kernel"),
                 "ops_per_pair": OPS_PER_PAIR,
                 "peak_basis": f"{props.multi_processor_count} SMs x 4 sub-partitions x {ALU_LANES} ALU lanes x {sm_max:.0f} MHz "
                               f"({peak_src} sm_max_mhz)",

@@ -135,34 +135,55 @@ constexpr unsigned kWaitLimit = 1u << 24;  // bounded spin on the filter copy
 // ------------------------------------------------------------------------------------
 // lookup in the bucket table
 // ------------------------------------------------------------------------------------
-// Bits of the 64-bit linear key hash H:  0..31 feed the shared-memory Bloom filter
-// (bits 0-4 and 27-31 pick the two bits, bits 5.. the word); 32..63 give the bucket
-// (low bits) and the fingerprint stored with each entry.  A random GF(2)-linear map
-// sends any two distinct keys to independent uniform hashes, so the bucket load and the
-// filter false-positive rate are those of a 2-universal hash family.
-__device__ __forceinline__ unsigned bucket_of(unsigned long long h) { return static_cast<unsigned>(h >> 32); }
+// Bits of the 64-bit linear key hash H:  the low 32 bits g feed the shared-memory Bloom
+// filter (bits 0-4 and 22-31 pick the bits, bits 5.. the word) and are also the bucket
+// entry's fingerprint; the home bucket comes from g by multiplicative hashing (its top
+// bits after a multiply by an odd constant), so it does not follow the filter word.  A
+// random GF(2)-linear map sends any two distinct keys to independent uniform hashes, so
+// the bucket load, the fingerprint collisions and the filter false-positive rate are those
+// of a 2-universal hash family.  Because every key with fingerprint g has the same home
+// bucket, whether some key of the table has fingerprint g does not depend on the order of
+// insertion, and a probe by fingerprint alone is deterministic.
+__device__ __forceinline__ unsigned home_bucket(unsigned g, unsigned nb_mask) {
+    return __umulhi(g * 0x9E3779B1u, nb_mask + 1u);
+}
 
-// Returns the table row of key, or -1.  Buckets hold two 64-bit entries
+// Returns the table row of key (low hash bits g), or -1.  Buckets hold two 64-bit entries
 // (fingerprint << 32 | row + 1); an empty entry ends the probe sequence.
-__device__ __forceinline__ long long table_find(const TableParams& tp, ulonglong2 key,
-                                                unsigned long long h) {
-    const unsigned fp = bucket_of(h);
-    unsigned b = fp & tp.nb_mask;
+__device__ __forceinline__ long long table_find(const TableParams& tp, ulonglong2 key, unsigned g) {
+    unsigned b = home_bucket(g, tp.nb_mask);
     const ulonglong2* buckets = reinterpret_cast<const ulonglong2*>(tp.slots);
     for (unsigned it = 0; it <= tp.nb_mask; ++it) {
         const ulonglong2 e = __ldg(buckets + b);
         if (e.x == 0ULL) return -1;
-        if (static_cast<unsigned>(e.x >> 32) == fp) {
+        if (static_cast<unsigned>(e.x >> 32) == g) {
             const long long r = static_cast<long long>(static_cast<unsigned>(e.x)) - 1;
             const ulonglong2 k = __ldg(tp.keys + r);
             if (k.x == key.x && k.y == key.y) return r;
         }
         if (e.y == 0ULL) return -1;
-        if (static_cast<unsigned>(e.y >> 32) == fp) {
+        if (static_cast<unsigned>(e.y >> 32) == g) {
             const long long r = static_cast<long long>(static_cast<unsigned>(e.y)) - 1;
             const ulonglong2 k = __ldg(tp.keys + r);
             if (k.x == key.x && k.y == key.y) return r;
         }
+        b = (b + 1u) & tp.nb_mask;
+    }
+    return -1;
+}
+
+// The first row along the probe sequence of g whose entry carries fingerprint g, or -1 if
+// no key of the table has fingerprint g.  Needs only g, not the key: the caller confirms
+// the key of the row (table_find resolves the rare 32-bit fingerprint collision).
+__device__ __forceinline__ long long probe_fp(unsigned g, const TableParams& tp) {
+    unsigned b = home_bucket(g, tp.nb_mask);
+    const ulonglong2* buckets = reinterpret_cast<const ulonglong2*>(tp.slots);
+    for (unsigned it = 0; it <= tp.nb_mask; ++it) {
+        const ulonglong2 e = __ldg(buckets + b);
+        if (e.x == 0ULL) return -1;
+        if (static_cast<unsigned>(e.x >> 32) == g) return static_cast<long long>(static_cast<unsigned>(e.x)) - 1;
+        if (e.y == 0ULL) return -1;
+        if (static_cast<unsigned>(e.y >> 32) == g) return static_cast<long long>(static_cast<unsigned>(e.y)) - 1;
         b = (b + 1u) & tp.nb_mask;
     }
     return -1;
@@ -246,10 +267,10 @@ __device__ __forceinline__ void build_one(const TableParams& tp, int n_orb, int 
     }
     if (aset != nullptr && sa != 0ULL) set_insert(aset, tp.set_mask, sa, ha);
     if (bset != nullptr && sb != 0ULL) set_insert(bset, tp.set_mask, sb, hb);
-    const unsigned fp = bucket_of(h);
+    const unsigned fp = static_cast<unsigned>(h);
     const unsigned long long entry =
         (static_cast<unsigned long long>(fp) << 32) | static_cast<unsigned long long>(static_cast<unsigned>(r + 1));
-    unsigned b = fp & tp.nb_mask;
+    unsigned b = home_bucket(fp, tp.nb_mask);
     bool placed = false;
     for (unsigned it = 0; it <= tp.nb_mask && !placed; ++it) {
         if (atomicCAS(slots + 2 * b, 0ULL, entry) == 0ULL) { placed = true; break; }
@@ -318,8 +339,8 @@ struct Acc {
     unsigned long long missing;
 };
 
-// Add one hit: <x|H|x'> (phase included) times psi(x') [FP64], or times psi(x')/psi(x)
-// [FP32, compensated], plus the diagnostics of the exported phase convention.
+// x' = x with spin orbitals (i, j) emptied and (a, b) filled (j = b = 255: a single), and
+// its linear hash h, updated from that of x by the four orbitals' entries of T.
 __device__ __forceinline__ ulonglong2 excite(unsigned orbs, ulonglong2 x, unsigned long long hx,
                                              const unsigned long long* __restrict__ T64,
                                              unsigned long long& h) {
@@ -336,26 +357,8 @@ __device__ __forceinline__ ulonglong2 excite(unsigned orbs, ulonglong2 x, unsign
     return xp;
 }
 
-// Stage 1 -- probe the home bucket of x' = x with orbitals (i, j) emptied and (a, b)
-// filled.  A bucket with a free entry holds every key whose home it is (a key only moves
-// on when its home bucket is full), so its content does not depend on the order of
-// insertion: its fingerprint-matching entry (at most one) is returned as a candidate row,
-// to be checked against the stored key in stage 2 beside the loads of psi and the
-// integrals.  A full home bucket takes the exact probe walk instead, so the outcome of
-// this stage -- and with it the order of accumulation -- is the same on every run.
-__device__ __forceinline__ long long probe(unsigned orbs, ulonglong2 x, unsigned long long hx,
-                                          const TableParams& tp,
-                                          const unsigned long long* __restrict__ T64) {
-    unsigned long long h;
-    const ulonglong2 xp = excite(orbs, x, hx, T64, h);
-    const unsigned fp = bucket_of(h);
-    const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(tp.slots) + (fp & tp.nb_mask));
-    if (e.x != 0ULL && e.y != 0ULL) return table_find(tp, xp, h);
-    if (e.x != 0ULL && static_cast<unsigned>(e.x >> 32) == fp)
-        return static_cast<long long>(static_cast<unsigned>(e.x)) - 1;
-    return -1;
-}
-
+// Add one hit: <x|H|x'> (phase included) times psi(x') [FP64], or times psi(x')/psi(x)
+// [FP32, compensated], plus the diagnostics of the exported phase convention.
 template <int PREC>
 __device__ __forceinline__ void add_hit(double h64, float h32, long long row, bool sneg, double2 pp,
                                         float2 ip32, Acc& acc) {
@@ -392,7 +395,7 @@ __device__ __forceinline__ void verify_and_add(uint2 e, ulonglong2 x, unsigned l
     element(h64, h32, sneg);
     long long row = e.y;
     if (key.x != xp.x || key.y != xp.y) {
-        row = table_find(tp, xp, h);
+        row = table_find(tp, xp, static_cast<unsigned>(h));
         if (row >= 0) pp = __ldg(tp.psi + row);
         else if (mode == QC_FULL) acc.missing++;
     }
@@ -719,11 +722,12 @@ __device__ __forceinline__ float2 inv_psi32(double2 p) {
 // One warp per sample (persistent grid).  The five excitation classes are walked as
 // outer x inner products of per-sample hash lists by a flat state machine; each step
 // tests U x 32 excitations.  With FILTER, an excitation becomes a candidate only if its
-// two bits are set in the shared-memory Bloom filter; without it (accurate-energy mode,
+// three bits are set in the shared-memory Bloom filter; without it (accurate-energy mode,
 // or the unfiltered variant) every excitation is a candidate.  Candidates queue up per
-// warp and are resolved 32 at a time in three full-warp stages: probe the bucket table,
-// then compute the matrix elements of single hits and of double hits in separate
-// batches (so lanes of one batch follow the same path).  All three stages sit at one
+// warp and are resolved 32 at a time in two full-warp stages: probe the bucket table by
+// the candidate's fingerprint (its low hash bits, rebuilt from two list entries, so most
+// filter false positives are rejected without decoding the excitation), then decode the
+// hits, confirm their keys and compute their matrix elements.  Both stages sit at one
 // place in the loop; the end of a sample flushes the partial batches through the same code.
 constexpr int kCandCap = 160;  // >= 31 + 32 * 4 (the largest U with a single flush site)
 constexpr size_t kWarpQueues = 4 * kCandCap + 64 * 8;  // candidate queue + hit queue
@@ -965,11 +969,13 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 // found only in the first two classes, so a batch rarely mixes the kinds.
                 const int n = nh < 32 ? nh : 32;
                 const bool v = lane < n;
-                const uint2 e = v ? hq[lane] : make_uint2(0u, 0u);
+                uint2 e = v ? hq[lane] : make_uint2(0u, 0u);
                 __syncwarp();
                 if (lane < nh - n) hq[lane] = hq[n + lane];
                 nh -= n;
                 __syncwarp();
+                // the filtered walk queues candidate codes; they are decoded only here
+                if (FILTER && v) e.x = decode(e.x, sp, wl, smem, IA, IB);
                 if (v)
                     verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc,
                                          [&](double& h64, float& h32, bool& sneg) {
@@ -986,16 +992,41 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 for (int t = lane; t < qn - n; t += 32) q[t] = q[n + t];
                 qn -= n;
                 __syncwarp();
-                unsigned orbs = 0u;
+                unsigned item = 0u;
                 long long row = -1;
                 if (v) {
-                    orbs = decode(code, sp, wl, smem, IA, IB);
-                    row = probe(orbs, x, hx, tp, T64);
+                    unsigned g;
+                    if (FILTER) {
+                        // the low hash bits of x' again from the hash lists: g = hx ^ outer
+                        // ^ inner entry of the candidate's class (no decode, no excite)
+                        const unsigned cc = code >> 24;
+                        const int u = static_cast<int>((code >> 12) & 4095u);
+                        const int w = static_cast<int>(code & 4095u);
+                        const int ob = cc == 2u ? oPAo : cc == 3u ? oPBo : cc == 4u ? oSA : 0;
+                        const int ib = cc == 0u ? oSA : cc == 1u ? oSB : cc == 2u ? oPAv : cc == 3u ? oPBv : oSB;
+                        uint32_t ho, hi;
+                        if (LEAN != 0 && lean && (cc == 2u || cc == 3u)) {
+                            const unsigned pu = lut[u], pw = lut[w];
+                            ho = H[ob + (pu & 255u)] ^ H[ob + (pu >> 8)];
+                            hi = H[ib + (pw & 255u)] ^ H[ib + (pw >> 8)];
+                        } else {
+                            ho = H[ob + u];
+                            hi = H[ib + w];
+                        }
+                        g = hx32 ^ ho ^ hi;
+                        item = code;
+                    } else {
+                        item = decode(code, sp, wl, smem, IA, IB);
+                        unsigned long long h;
+                        excite(item, x, hx, T64, h);
+                        g = static_cast<unsigned>(h);
+                    }
+                    row = probe_fp(g, tp);
                     if (row < 0 && ep.mode == QC_FULL) acc.missing++;
                 }
                 const bool hit = row >= 0;
                 const unsigned mh = __ballot_sync(QC_FULLMASK, hit);
-                if (hit) hq[nh + __popc(mh & ltmask)] = make_uint2(orbs, static_cast<unsigned>(row));
+                if (hit) hq[nh + __popc(mh & ltmask)] = make_uint2(item, static_cast<unsigned>(row));
                 nh += __popc(mh);
                 __syncwarp();
             } else {
