@@ -110,6 +110,15 @@ typedef int qc_status;
 #define QC_OPT_LEAN          8  /* filtered kernel's per-warp lists: 0 auto (the layout that fits
                                    more warps), 1 stored pair lists, 2 pair lists formed on the
                                    fly from per-orbital values (same results, less shared memory) */
+#define QC_OPT_JOIN         10  /* sample-space mode, filtered kernel: 0 auto (on from 16384
+                                   table rows), 1 off, 2 on.  On,
+                                   the table rows are also grouped by alpha string and by beta
+                                   string (a per-evaluation index); a short group that can hold
+                                   connected keys is scanned row by row, the excitations into a
+                                   long one enumerated.  Same connected set, so the same results
+                                   up to the order of accumulation */
+#define QC_OPT_SCAN_COST    11  /* join: a group is scanned when its rows x this / 4 are at most
+                                   the excitations it replaces; 0 the default */
 
 typedef struct qc_eloc qc_eloc;
 

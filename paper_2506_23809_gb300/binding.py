@@ -23,6 +23,8 @@ QC_OPT_TIMING, QC_OPT_KERNEL, QC_OPT_FILTER_LOG2W, QC_OPT_WARPS, QC_OPT_UNROLL, 
 QC_OPT_PREFILTER = 7
 QC_OPT_LEAN = 8
 QC_OPT_CHUNK_PAIRS = 9
+QC_OPT_JOIN = 10
+QC_OPT_SCAN_COST = 11
 QC_SRV_OPT_QUANTUM = 1
 QC_SRV_OPT_OLDEST_PCT = 2
 STATUS_NAMES = {0: "QC_OK", 1: "QC_PENDING", -1: "QC_ERR_ARG", -2: "QC_ERR_UNSORTED", -3: "QC_ERR_DUP",

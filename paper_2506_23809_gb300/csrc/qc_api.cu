@@ -236,6 +236,7 @@ qc_status qc_eloc_destroy(qc_eloc* H) {
     free_dev(H->d_gpart);
     free_dev(H->d_cpart);
     free_dev(H->d_cticket);
+    free_dev(H->d_join);
     for (auto& ev : H->ev)
         if (ev) cudaEventDestroy(ev);
     delete H;
@@ -273,6 +274,14 @@ qc_status qc_eloc_set_option(qc_eloc* H, int option, int64_t value) {
         case QC_OPT_LEAN:
             if (value < 0 || value > 2) return fail(H, QC_ERR_ARG, "QC_OPT_LEAN: 0, 1 or 2");
             H->opt_lean = static_cast<int>(value);
+            return QC_OK;
+        case QC_OPT_JOIN:
+            if (value < 0 || value > 2) return fail(H, QC_ERR_ARG, "QC_OPT_JOIN: 0, 1 or 2");
+            H->opt_join = static_cast<int>(value);
+            return QC_OK;
+        case QC_OPT_SCAN_COST:
+            if (value < 0 || value > 1024) return fail(H, QC_ERR_ARG, "QC_OPT_SCAN_COST: 0..1024");
+            H->opt_scan_cost = static_cast<int>(value);
             return QC_OK;
         case QC_OPT_GRID:
             if (value < 0 || value > (1 << 20)) return fail(H, QC_ERR_ARG, "QC_OPT_GRID: 0..2^20");
@@ -334,10 +343,19 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
     fw = 0;
     int warps = 0;
     int lean = 0;
+    // the join needs the spin-string sets and strings that are never empty (no spin without
+    // electrons); by default taken from qc::kJoinMinRows table rows up (below that its index
+    // build, a few microseconds per launch, outweighs what it saves); built with U = 4
+    const bool join = kernel == 2 && H->mode == QC_SAMPLE && H->opt_prefilter && H->na > 0 && H->nb > 0 &&
+                      (H->opt_join == 2 || (H->opt_join == 0 && n_table >= qc::kJoinMinRows));
     if (kernel == 2) {
         // filter sized for ~16 bits per key, 2^10..2^15 words; then as many warps as fit,
-        // shrinking the filter while that leaves fewer than 8.  Both list layouts are tried
-        // (unless forced) and the one that fits more warps is taken (stored lists on a tie).
+        // shrinking the filter while that leaves fewer than 8.  With the join, which sends
+        // fewer excitations through the filter, the most warps that fit with at least ~5
+        // filter bits per key (measured: N=52, 10^5 keys, 20 warps at 2^14 words beat 18 at
+        // 2^15; N=76, 2*10^5 keys, 16 warps at 2^15 beat 20 at 2^14).  Both list layouts are
+        // tried (unless forced) and the one that fits more warps is taken (stored lists on a
+        // tie; without the join, the larger filter first).
         int want = H->opt_fw;
         if (want == 0) {
             want = ceil_log2(static_cast<unsigned long long>(std::max<long long>(n_table, 1)) / 2 + 1);
@@ -346,19 +364,38 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
         int best_fw = 0, best_w = 0, best_lean = 0;
         for (int ln = 0; ln < 2; ++ln) {
             if ((H->opt_lean == 1 && ln == 1) || (H->opt_lean == 2 && ln == 0)) continue;
-            const size_t wb = qc::filtered_smem_bytes(sp, 1, want, ln) - qc::filtered_smem_bytes(sp, 0, want, ln);
+            const size_t wb =
+                qc::filtered_smem_bytes(sp, 1, want, ln, join) - qc::filtered_smem_bytes(sp, 0, want, ln, join);
             int f = want, w = 0;
-            for (; f >= 5; --f) {
-                const size_t base = qc::filtered_smem_bytes(sp, 0, f, ln);
-                if (base + wb > H->smem_optin) continue;
-                const int fit = static_cast<int>((H->smem_optin - base) / wb);
-                w = std::min(qc::kFilteredMaxWarps, H->opt_warps ? H->opt_warps : fit);
-                if (w > fit) continue;
-                if (H->opt_fw == 0 && w < 8 && f > 10) continue;  // prefer occupancy
-                break;
+            if (join && H->opt_fw == 0) {
+                const int min_f = std::min(want, std::max(10, ceil_log2(static_cast<unsigned long long>(
+                                                                   std::max<long long>(n_table, 1)) * 5 / 32 + 1)));
+                int bf = 0, bw = 0;
+                for (int g = want; g >= min_f; --g) {
+                    const size_t base = qc::filtered_smem_bytes(sp, 0, g, ln, join);
+                    if (base + wb > H->smem_optin) continue;
+                    const int fit = static_cast<int>((H->smem_optin - base) / wb);
+                    const int wg = std::min(qc::kFilteredMaxWarps, H->opt_warps ? H->opt_warps : fit);
+                    if (wg <= fit && wg > bw) {
+                        bw = wg;
+                        bf = g;
+                    }
+                }
+                f = bw > 0 ? bf : 4;
+                w = bw;
+            } else {
+                for (; f >= 5; --f) {
+                    const size_t base = qc::filtered_smem_bytes(sp, 0, f, ln, join);
+                    if (base + wb > H->smem_optin) continue;
+                    const int fit = static_cast<int>((H->smem_optin - base) / wb);
+                    w = std::min(qc::kFilteredMaxWarps, H->opt_warps ? H->opt_warps : fit);
+                    if (w > fit) continue;
+                    if (H->opt_fw == 0 && w < 8 && f > 10) continue;  // prefer occupancy
+                    break;
+                }
             }
             if (f < 5 || w < 1) continue;
-            if (w > best_w || (w == best_w && f > best_fw)) {
+            if (w > best_w || (w == best_w && !join && f > best_fw)) {
                 best_fw = f;
                 best_w = w;
                 best_lean = ln;
@@ -376,15 +413,16 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
     }
     c.kernel = kernel;
     c.lean = lean;
-    c.unroll = H->opt_unroll ? H->opt_unroll : 4;
+    c.join = kernel == 2 && join;
+    c.unroll = c.join ? 4 : (H->opt_unroll ? H->opt_unroll : 4);
     if (kernel == 2) {
         c.warps = warps;
-        c.smem = qc::filtered_smem_bytes(sp, warps, fw, lean);
+        c.smem = qc::filtered_smem_bytes(sp, warps, fw, lean, c.join);
     } else {
         c.warps = std::min(qc::kFilteredMaxWarps, H->opt_warps ? H->opt_warps : 16);
         c.smem = qc::direct_smem_bytes(sp, c.warps);
     }
-    int per_sm = qc::max_active_ctas(c.kernel, H->precision, c.unroll, 32 * c.warps, c.smem, c.lean);
+    int per_sm = qc::max_active_ctas(c.kernel, H->precision, c.unroll, 32 * c.warps, c.smem, c.lean, c.join);
     if (per_sm < 1) return fail(H, QC_ERR_CAPACITY, "main kernel cannot be resident with this shape");
     long long grid = H->opt_grid ? H->opt_grid : static_cast<long long>(per_sm) * H->sm_count;
     const long long cp = H->opt_chunk_pairs == 0 ? qc::kDefaultChunkPairs : H->opt_chunk_pairs;
@@ -487,9 +525,41 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     }
     QC_CHK(cudaMemsetAsync(H->d_slots, 0, 2 * nbuckets * sizeof(unsigned long long), s), "memset table");
     if (cfg.kernel == 2) QC_CHK(cudaMemsetAsync(H->d_filter, 0, (static_cast<size_t>(4) << fw), s), "memset filter");
+    // join index regions: slot keys, group sizes and starts, entries (strings, rows), sort space
+    const bool join = cfg.join && nt > 0;
+    auto a256 = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t jo_len = a256(2 * static_cast<size_t>(nt) * 4);
+    const size_t jo_start = jo_len + a256(2 * nbuckets * 4);
+    const size_t jo_ent = jo_start + a256(2 * nbuckets * 4);
+    const size_t jo_ws = jo_ent + a256(2 * static_cast<size_t>(nt) * 16);
+    unsigned* jkey = nullptr;
+    unsigned* jlen = nullptr;
+    if (join) {
+        const size_t need = jo_ws + qc::join_workspace_bytes(nt, static_cast<unsigned>(nbuckets));
+        if (need > H->join_cap) {
+            free_dev(H->d_join);
+            H->join_cap = 0;
+            QC_CHK(cudaMalloc(&H->d_join, need), "cudaMalloc join index");
+            H->join_cap = need;
+        }
+        jkey = reinterpret_cast<unsigned*>(H->d_join);
+        jlen = reinterpret_cast<unsigned*>(H->d_join + jo_len);
+        QC_CHK(cudaMemsetAsync(jlen, 0, 2 * nbuckets * sizeof(unsigned), s), "memset join sizes");
+    }
     QC_CHK(qc::launch_build_table(tp, H->n_orb, H->na, H->nb, H->d_T, H->d_slots, H->d_filter, aset, bset,
-                                  H->d_ctr, s),
+                                  H->d_ctr, s, jkey, jlen),
            "build_table launch");
+    if (join) {
+        unsigned* jstart = reinterpret_cast<unsigned*>(H->d_join + jo_start);
+        ulonglong2* gent = reinterpret_cast<ulonglong2*>(H->d_join + jo_ent);
+        QC_CHK(qc::launch_join_index(tp, static_cast<unsigned>(nbuckets), H->d_join + jo_ws, jkey, jlen, jstart,
+                                     gent, s),
+               "join index launch");
+        tp.jstart = jstart;
+        tp.jlen = jlen;
+        tp.gent = gent;
+        tp.scan_cost = H->opt_scan_cost ? H->opt_scan_cost : qc::kDefaultScanCost;
+    }
     if (H->opt_timing) QC_CHK(cudaEventRecord(H->ev[1], s), "cudaEventRecord");
 
     qc::EvalParams ep{};
@@ -549,10 +619,13 @@ qc_status qc_eloc_timings(qc_eloc* H, float* ms3) {
     return QC_OK;
 }
 
-// Launch shape of the last evaluation: {kernel, grid, warps, unroll, smem bytes, filter log2 words}.
+// Launch shape of the last evaluation: {kernel, grid, warps, unroll, smem bytes, filter log2 words,
+// excitation chunks}.
 qc_status qc_eloc_last_config(const qc_eloc* H, int64_t* cfg7) {
     if (!H || !cfg7) return QC_ERR_ARG;
-    cfg7[0] = H->last_cfg.kernel == 2 && H->last_cfg.lean ? 3 : H->last_cfg.kernel;
+    // 1 direct, 2 filtered, 3 filtered with lean lists, 4 / 5 the same two with the join
+    cfg7[0] = H->last_cfg.kernel == 2 ? 2 + (H->last_cfg.lean ? 1 : 0) + (H->last_cfg.join ? 2 : 0)
+                                      : H->last_cfg.kernel;
     cfg7[1] = H->last_cfg.grid;
     cfg7[2] = H->last_cfg.warps;
     cfg7[3] = H->last_cfg.unroll;

@@ -125,9 +125,9 @@ __global__ void __launch_bounds__(MAXT) eloc_batch_kernel(const __grid_constant_
                     const long long s = r0 + static_cast<long long>(q);
                     const int c = static_cast<int>(it - q * C);
                     if (mp.ep.lean)
-                        run_sample<PREC, U, true, 1>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));
+                        run_sample<PREC, U, true, 1, false>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));
                     else
-                        run_sample<PREC, U, true, 0>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));
+                        run_sample<PREC, U, true, 0, false>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));
                 }
             }
         }

@@ -192,13 +192,6 @@ __global__ void __launch_bounds__(kScanBlock) scan_down_kernel(unsigned* __restr
         }
 }
 
-cudaError_t exclusive_scan(unsigned* a, long long n, unsigned* sums, cudaStream_t s) {
-    const long long segs = (n + kScanSeg - 1) / kScanSeg;
-    scan_sums_kernel<<<static_cast<unsigned>(segs), kScanBlock, 0, s>>>(a, n, sums);
-    scan_top_kernel<<<1, kScanBlock, 0, s>>>(sums, segs);
-    scan_down_kernel<<<static_cast<unsigned>(segs), kScanBlock, 0, s>>>(a, n, sums);
-    return cudaGetLastError();
-}
 
 // KU: head-of-run flags of the sorted keys (as 0/1 in `f`)
 __global__ void __launch_bounds__(256) dedup_flags_kernel(const ulonglong2* __restrict__ k, long long n,
@@ -261,6 +254,17 @@ qc_status dfail(qc_status st, const char* msg) {
 
 }  // namespace
 
+// Exclusive prefix sum of a u32 array in place (segment sums, a scan of the sums, segment
+// scans); also the join index's group starts (qc_join.cu).
+cudaError_t qc::exclusive_scan_u32(unsigned* a, long long n, unsigned* sums, cudaStream_t s) {
+    const long long segs = (n + kScanSeg - 1) / kScanSeg;
+    if (segs == 0) return cudaSuccess;
+    scan_sums_kernel<<<static_cast<unsigned>(segs), kScanBlock, 0, s>>>(a, n, sums);
+    scan_top_kernel<<<1, kScanBlock, 0, s>>>(sums, segs);
+    scan_down_kernel<<<static_cast<unsigned>(segs), kScanBlock, 0, s>>>(a, n, sums);
+    return cudaGetLastError();
+}
+
 extern "C" int64_t qc_dedup_workspace_bytes(int64_t n_raw) {
     if (n_raw < 0) return -1;
     return static_cast<int64_t>(layout(n_raw).total);
@@ -303,7 +307,7 @@ extern "C" qc_status qc_dedup(const uint64_t* raw, int64_t n_raw, int n_orb, uin
     for (int p = 0; p < passes && e == cudaSuccess; ++p) {
         dedup_hist_kernel<<<blocks, 256, 0, s>>>(src, n, p, tiles, table, high, flag);
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = exclusive_scan(table, static_cast<long long>(kBins) * tiles, sums, s);
+        if (e == cudaSuccess) e = qc::exclusive_scan_u32(table, static_cast<long long>(kBins) * tiles, sums, s);
         if (e == cudaSuccess) {
             dedup_scatter_kernel<<<blocks, 256, 0, s>>>(src, dst, n, p, tiles, table);
             e = cudaGetLastError();
@@ -318,7 +322,7 @@ extern "C" qc_status qc_dedup(const uint64_t* raw, int64_t n_raw, int n_orb, uin
         e = cudaGetLastError();
     }
     const long long segs = (n + kScanSeg - 1) / kScanSeg;
-    if (e == cudaSuccess) e = exclusive_scan(table, n, sums, s);
+    if (e == cudaSuccess) e = qc::exclusive_scan_u32(table, n, sums, s);
     if (e == cudaSuccess) {
         dedup_emit_kernel<<<gblocks, 256, 0, s>>>(src, n, table, sums + segs, reinterpret_cast<ulonglong2*>(keys_out),
                                                  heads, reinterpret_cast<long long*>(n_unique), flag);

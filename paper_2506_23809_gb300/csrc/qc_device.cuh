@@ -198,35 +198,47 @@ __device__ __forceinline__ unsigned filter_bits(unsigned g) {
     return (1u << (g & 31u)) | (1u << (g >> 27)) | (1u << ((g >> 22) & 31u));
 }
 
-// Insert a spin string into an exact set (open addressing on the high hash bits).
-__device__ __forceinline__ void set_insert(unsigned long long* set, unsigned mask, unsigned long long v,
-                                           unsigned long long h) {
+// Insert a spin string into an exact set (open addressing on the high hash bits).  Returns
+// the slot that holds it, or kNoSlot when the set is full.
+constexpr unsigned kNoSlot = 0xffffffffu;
+__device__ __forceinline__ unsigned set_insert(unsigned long long* set, unsigned mask, unsigned long long v,
+                                               unsigned long long h) {
     unsigned b = static_cast<unsigned>(h >> 32) & mask;
     for (unsigned it = 0; it <= mask; ++it) {
         const unsigned long long old = atomicCAS(set + b, 0ULL, v);
-        if (old == 0ULL || old == v) return;
+        if (old == 0ULL || old == v) return b;
         b = (b + 1u) & mask;
     }
+    return kNoSlot;
 }
 
-__device__ __forceinline__ bool set_contains(const unsigned long long* __restrict__ set, unsigned mask,
+// The slot that holds spin string v, or kNoSlot.
+__device__ __forceinline__ unsigned set_slot(const unsigned long long* __restrict__ set, unsigned mask,
                                              unsigned long long v, unsigned long long h) {
     unsigned b = static_cast<unsigned>(h >> 32) & mask;
     for (unsigned it = 0; it <= mask; ++it) {
         const unsigned long long e = __ldg(set + b);
-        if (e == v) return true;
-        if (e == 0ULL) return false;
+        if (e == v) return b;
+        if (e == 0ULL) return kNoSlot;
         b = (b + 1u) & mask;
     }
-    return false;
+    return kNoSlot;
 }
 
-// Insert row r of the table: validation, filter bits, spin-string sets, bucket entry.
+__device__ __forceinline__ bool set_contains(const unsigned long long* __restrict__ set, unsigned mask,
+                                             unsigned long long v, unsigned long long h) {
+    return set_slot(set, mask, v, h) != kNoSlot;
+}
+
+// Insert row r of the table: validation, filter bits, spin-string sets, bucket entry.  With
+// jkey (the sample-space join index), also the row's two set slots as sort keys -- jkey[r]
+// the alpha slot, jkey[n + r] the beta slot + set size -- and their group counts in jlen.
 __device__ __forceinline__ void build_one(const TableParams& tp, int n_orb, int na, int nb,
                                           const unsigned long long* __restrict__ T,
                                           unsigned long long* slots, uint32_t* filter,
                                           unsigned long long* aset, unsigned long long* bset,
-                                          Counters* ctr, long long r) {
+                                          Counters* ctr, long long r, unsigned* jkey = nullptr,
+                                          unsigned* jlen = nullptr) {
     const ulonglong2 key = tp.keys[r];
     unsigned flags = 0;
     if (r > 0) {
@@ -265,8 +277,22 @@ __device__ __forceinline__ void build_one(const TableParams& tp, int n_orb, int 
         const unsigned wmask = (1u << tp.fw) - 1u;
         atomicOr(filter + ((g >> 5) & wmask), filter_bits(g));
     }
-    if (aset != nullptr && sa != 0ULL) set_insert(aset, tp.set_mask, sa, ha);
-    if (bset != nullptr && sb != 0ULL) set_insert(bset, tp.set_mask, sb, hb);
+    unsigned slot_a = kNoSlot, slot_b = kNoSlot;
+    if (aset != nullptr && sa != 0ULL) slot_a = set_insert(aset, tp.set_mask, sa, ha);
+    if (bset != nullptr && sb != 0ULL) slot_b = set_insert(bset, tp.set_mask, sb, hb);
+    if (jkey != nullptr) {
+        // the join is only built when both spins hold electrons (no string is 0); a row that
+        // fails validation joins no group (its keys sort past every group)
+        const unsigned size = tp.set_mask + 1u;
+        if (slot_a == kNoSlot || slot_b == kNoSlot) flags |= QC_FLAG_TABLE_FULL;
+        const bool ok = (flags & QC_FLAG_NELEC) == 0u && slot_a != kNoSlot && slot_b != kNoSlot;
+        jkey[r] = ok ? slot_a : 2u * size;
+        jkey[tp.n + r] = ok ? size + slot_b : 2u * size;
+        if (ok) {
+            atomicAdd(jlen + slot_a, 1u);
+            atomicAdd(jlen + size + slot_b, 1u);
+        }
+    }
     const unsigned fp = static_cast<unsigned>(h);
     const unsigned long long entry =
         (static_cast<unsigned long long>(fp) << 32) | static_cast<unsigned long long>(static_cast<unsigned>(r + 1));
@@ -402,12 +428,38 @@ __device__ __forceinline__ void verify_and_add(uint2 e, ulonglong2 x, unsigned l
     if (row >= 0) add_hit<PREC>(h64, h32, row, sneg, pp, ip32, acc);
 }
 
+// Sample-space join.  Kinds of scanned groups (low bits of a scan descriptor's kind; an
+// alpha' group also carries its excitation ki << 8 | ka << 16), and the classes of the hits
+// it finds: their codes pack four spatial orbitals, 6 bits each.
+constexpr unsigned kScanAlpha = 1u;   // rows sharing x's alpha string (beta strings scanned)
+constexpr unsigned kScanBeta = 2u;    // rows sharing x's beta string (alpha strings scanned)
+constexpr unsigned kScanAlphaP = 3u;  // rows of an alpha' = single excitation of x's alpha string
+constexpr unsigned kCodeSingleA = 5u, kCodeSingleB = 6u, kCodeDoubleAA = 7u, kCodeDoubleBB = 8u,
+                   kCodeDoubleAB = 9u;
+
+// Code of a scanned hit: d is the popcount of the scanned string against x's, emptied and
+// filled its bits set only in x's string and only in the row's.
+__device__ __forceinline__ unsigned scan_code(unsigned kind, int d, unsigned long long emptied,
+                                              unsigned long long filled) {
+    const unsigned e0 = static_cast<unsigned>(__ffsll(emptied) - 1) & 63u;
+    const unsigned f0 = static_cast<unsigned>(__ffsll(filled) - 1) & 63u;
+    if ((kind & 3u) == kScanAlphaP) {
+        const unsigned ki = (kind >> 8) & 63u, ka = (kind >> 16) & 63u;
+        if (d == 0) return (kCodeSingleA << 24) | ki | (ka << 6);
+        return (kCodeDoubleAB << 24) | ki | (ka << 6) | (e0 << 12) | (f0 << 18);
+    }
+    if (d == 2) return (kCodeSingleB << 24) | e0 | (f0 << 6);  // x's alpha group only
+    const unsigned e1 = static_cast<unsigned>(63 - __clzll(emptied)), f1 = static_cast<unsigned>(63 - __clzll(filled));
+    const unsigned cls = (kind & 3u) == kScanAlpha ? kCodeDoubleBB : kCodeDoubleAA;
+    return (cls << 24) | e0 | (e1 << 6) | (f0 << 12) | (f1 << 18);
+}
+
 // Stage 1 -- decode a candidate (class, u, w) into the spin orbitals it empties (i, j)
 // and fills (a, b); j = b = 255 for singles.  Classes: 0 alpha single (w), 1 beta single
 // (w), 2 alpha-alpha double (u: occupied pair, w: empty pair), 3 beta-beta double,
-// 4 alpha-beta double (u: alpha single, w: beta single).  Same-spin doubles come out with
-// i < j and a < b.  Single indices go through IA / IB (the compacted single lists of the
-// filtered kernel) when given.  Returns the packed orbitals i | a << 8 | j << 16 | b << 24.
+// 4 alpha-beta double (u: alpha single, w: beta single), and the classes of scanned hits
+// (kCodeSingleA ..).  Same-spin doubles come out with i < j and a < b.  Single indices go
+// through IA / IB (the compacted single lists of the filtered kernel) when given.  Returns the packed orbitals i | a << 8 | j << 16 | b << 24.
 __device__ __forceinline__ unsigned decode(unsigned code, const SysParams& sp,
                                            const unsigned char* __restrict__ wl,
                                            const unsigned char* __restrict__ smem,
@@ -421,6 +473,16 @@ __device__ __forceinline__ unsigned decode(unsigned code, const SysParams& sp,
     const unsigned char* occB = wl + 128;
     const unsigned char* virB = wl + 192;
     const unsigned cls = code >> 24;
+    if (cls >= kCodeSingleA) {  // a scanned hit: spatial orbitals in the code
+        const unsigned k0 = code & 63u, k1 = (code >> 6) & 63u, k2 = (code >> 12) & 63u, k3 = (code >> 18) & 63u;
+        if (cls <= kCodeSingleB) {
+            const unsigned sb = cls - kCodeSingleA;
+            return (2u * k0 + sb) | ((2u * k1 + sb) << 8) | 0xFFFF0000u;
+        }
+        if (cls == kCodeDoubleAB) return (2u * k0) | ((2u * k1) << 8) | ((2u * k2 + 1u) << 16) | ((2u * k3 + 1u) << 24);
+        const unsigned sb = cls - kCodeDoubleAA;
+        return (2u * k0 + sb) | ((2u * k2 + sb) << 8) | ((2u * k1 + sb) << 16) | ((2u * k3 + sb) << 24);
+    }
     int u = static_cast<int>((code >> 12) & 4095u);
     int w = static_cast<int>(code & 4095u);
     // singles lists may be compacted by the spin-string prefilter: map back
@@ -732,10 +794,12 @@ __device__ __forceinline__ float2 inv_psi32(double2 p) {
 constexpr int kCandCap = 160;  // >= 31 + 32 * 4 (the largest U with a single flush site)
 constexpr size_t kWarpQueues = 4 * kCandCap + 64 * 8;  // candidate queue + hit queue
 
-__host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filter, bool lean = false) {
+constexpr int kSingleCap = 64;  // join: the hit queue of scanned singles (uint2)
+__host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filter, bool lean = false,
+                                                  bool join = false) {
     // hash lists (u32) and, for the two single lists, their compaction maps (u16)
     const size_t lists = filter ? 4 * list_words(sp, lean) + 2 * static_cast<size_t>(sp.nsa + sp.nsb) : 0;
-    return (256 + kWarpQueues + lists + 15) / 16 * 16;
+    return (256 + kWarpQueues + (join ? 8 * kSingleCap : 0) + lists + 15) / 16 * 16;
 }
 
 
@@ -745,8 +809,9 @@ __host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filt
 // shared memory, filt the CTA's copy of the Bloom filter.  LEAN: 0 the pair lists are
 // stored, 1 they are formed on the fly from per-orbital values (less shared memory per
 // warp, so more warps fit for large orbital counts), 2 as ep.lean says.  Both layouts give
-// the same hash values in the same order, so the same results.
-template <int PREC, int U, bool FILTER, int LEAN>
+// the same hash values in the same order, so the same results.  JOIN: the sample-space join
+// is taken when the table carries its index (false compiles it out).
+template <int PREC, int U, bool FILTER, int LEAN, bool JOIN = true>
 __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParams& tp,
                                            const EvalParams& ep, long long s, int lane,
                                            unsigned char* smem, unsigned char* wl,
@@ -755,7 +820,8 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
     uint32_t* q = reinterpret_cast<uint32_t*>(wl + 256);
     uint2* hq = reinterpret_cast<uint2*>(wl + 256 + 4 * kCandCap);
-    uint32_t* H = reinterpret_cast<uint32_t*>(wl + 256 + kWarpQueues);
+    uint2* hs = hq + 64;  // join kernels only: scanned singles
+    uint32_t* H = reinterpret_cast<uint32_t*>(wl + 256 + kWarpQueues + (JOIN ? 8 * kSingleCap : 0));
     const bool lean = FILTER && (LEAN == 1 || (LEAN == 2 && ep.lean != 0));
     // list offsets inside H: 0 zero | SA | SB | PAo | PAv | PBo | PBv, or in the lean layout
     // 0 zero | SA | SB | occupied alpha | empty alpha | occupied beta | empty beta
@@ -779,6 +845,60 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         if (c == 0) invalid_sample(ep, s, lane);  // reported once, by the first chunk
         return;
     }
+    const double2 psix = ep.psi[s];
+    const float2 ip32 = inv_psi32(psix);
+    Acc acc{};
+    int qn = 0, nh = 0;
+    // sample-space join: short groups of table rows are scanned (the scan state, first phase
+    // of the main loop; chunk 0 only), the excitations into long ones enumerated (classes 1 and
+    // 3 only when x's alpha group is long, class 2 only when its beta group is, classes 0 and 4
+    // only over long alpha' groups)
+    const bool join = JOIN && FILTER && tp.jlen != nullptr;
+    bool enumA = true, enumB = true;
+
+    // hits: 32 from a hit queue -- decode, key check, psi(x') and integrals, then the
+    // element.  Singles come in their own classes (and, from the join's scans, in their own
+    // queue), so a batch rarely mixes the kinds.
+    int ns = 0;  // join: scanned singles queued in hs
+    auto hit_batch = [&](uint2* Q, int& nq) {
+        const int n = nq < 32 ? nq : 32;
+        const bool v = lane < n;
+        uint2 e = v ? Q[lane] : make_uint2(0u, 0u);
+        __syncwarp();
+        if (lane < nq - n) Q[lane] = Q[n + lane];
+        nq -= n;
+        __syncwarp();
+        if (FILTER && v) e.x = decode(e.x, sp, wl, smem, IA, IB);
+        if (v)
+            verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc, [&](double& h64, float& h32, bool& sneg) {
+                if ((e.x >> 16) == 0xFFFFu)
+                    single_element<PREC>(e.x, prefix_parity(x), sp, wl, h64, h32, sneg);
+                else
+                    double_element<PREC>(e.x, prefix_parity(x), sp, h64, h32, sneg);
+            });
+    };
+
+    // Scan state of the join (the first phase of the main loop, before any candidate is
+    // queued, so it owns the candidate queue's space): a chunk of up to 32 groups of table
+    // rows, one per lane -- start, exclusive row offset and kind in q[0..95] -- scanned as one
+    // list of q[102] rows, 32 per step; x's spin strings and alpha hash in q[96..101], the
+    // next alpha single excitation to classify in q[103] (shared memory keeps the scan state
+    // out of the registers of the enumeration loop).
+    auto store_chunk = [&](unsigned gst, unsigned gln, unsigned kind) {
+        unsigned inc = gln;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(QC_FULLMASK, inc, o);
+            if (lane >= o) inc += y;
+        }
+        q[lane] = gst;
+        q[32 + lane] = inc - gln;
+        q[64 + lane] = kind;
+        if (lane == 31) q[102] = inc;
+        __syncwarp();
+    };
+    unsigned long long* qx = reinterpret_cast<unsigned long long*>(q + 96);
+
     if (FILTER) {
         const unsigned char* occA = wl;
         const unsigned char* virA = wl + 64;
@@ -790,27 +910,6 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         // no hit (nor can any alpha-beta double built on it): the spin-string prefilter
         // drops it, compacting the single lists (IA / IB map back to the full index).
         const unsigned long long hxb = hx ^ hxa;
-        nsa2 = 0;
-        for (int t0 = 0; t0 < sp.nsa; t0 += 32) {
-            const int t = t0 + lane;
-            bool keep = false;
-            uint32_t hv32 = 0u;
-            if (t < sp.nsa) {
-                const int io = divA[t];
-                const int ki = occA[io], ka = virA[t - io * sp.va];
-                const unsigned long long tm = T64[2 * ki] ^ T64[2 * ka];
-                hv32 = static_cast<uint32_t>(tm);
-                keep = tp.aset == nullptr ||
-                       set_contains(tp.aset, tp.set_mask, As ^ (1ULL << ki) ^ (1ULL << ka), hxa ^ tm);
-            }
-            const unsigned m = __ballot_sync(QC_FULLMASK, keep);
-            if (keep) {
-                const int pos = nsa2 + __popc(m & ltmask);
-                H[oSA + pos] = hv32;
-                IA[pos] = static_cast<unsigned short>(t);
-            }
-            nsa2 += __popc(m);
-        }
         nsb2 = 0;
         for (int t0 = 0; t0 < sp.nsb; t0 += 32) {
             const int t = t0 + lane;
@@ -831,6 +930,61 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 IB[pos] = static_cast<unsigned short>(t);
             }
             nsb2 += __popc(m);
+        }
+        if (join) {
+            // x's own groups: lane 0 its alpha group (scanned, or classes 1 and 3), lane 1
+            // its beta group (scanned, or class 2); an absent or empty group has no hits
+            unsigned gst = 0u, gln = 0u, kind = 0u;
+            bool en = false;
+            if (lane < 2) {
+                const unsigned off = lane == 0 ? 0u : tp.set_mask + 1u;
+                const unsigned sl = lane == 0 ? set_slot(tp.aset, tp.set_mask, As, hxa)
+                                              : set_slot(tp.bset, tp.set_mask, Bs, hxb);
+                const unsigned len = sl != kNoSlot ? __ldg(tp.jlen + off + sl) : 0u;
+                const long long pairs = lane == 0 ? static_cast<long long>(nsb2) + static_cast<long long>(sp.npob) * sp.npvb
+                                                  : static_cast<long long>(sp.npoa) * sp.npva;
+                if (len > 0u) {
+                    if (static_cast<long long>(len) * tp.scan_cost <= 4 * pairs) {
+                        gst = __ldg(tp.jstart + off + sl);
+                        gln = len;
+                    } else {
+                        en = true;
+                    }
+                }
+                kind = lane == 0 ? kScanAlpha : kScanBeta;
+            }
+            enumA = __shfl_sync(QC_FULLMASK, en, 0);
+            enumB = __shfl_sync(QC_FULLMASK, en, 1);
+            if (lane == 0) {
+                qx[0] = As;
+                qx[1] = Bs;
+                qx[2] = hxa;
+                q[103] = 0u;
+            }
+            store_chunk(gst, c == 0 ? gln : 0u, kind);  // later chunks classify but scan nothing
+            nsa2 = 0;  // the alpha' groups are classified in the scan state
+        } else {
+            nsa2 = 0;
+            for (int t0 = 0; t0 < sp.nsa; t0 += 32) {
+                const int t = t0 + lane;
+                bool keep = false;
+                uint32_t hv32 = 0u;
+                if (t < sp.nsa) {
+                    const int io = divA[t];
+                    const int ki = occA[io], ka = virA[t - io * sp.va];
+                    const unsigned long long tm = T64[2 * ki] ^ T64[2 * ka];
+                    hv32 = static_cast<uint32_t>(tm);
+                    keep = tp.aset == nullptr ||
+                           set_contains(tp.aset, tp.set_mask, As ^ (1ULL << ki) ^ (1ULL << ka), hxa ^ tm);
+                }
+                const unsigned m = __ballot_sync(QC_FULLMASK, keep);
+                if (keep) {
+                    const int pos = nsa2 + __popc(m & ltmask);
+                    H[oSA + pos] = hv32;
+                    IA[pos] = static_cast<unsigned short>(t);
+                }
+                nsa2 += __popc(m);
+            }
         }
         if (lean) {
             for (int t = lane; t < sp.oa; t += 32) H[oPAo + t] = static_cast<uint32_t>(T64[2 * occA[t]]);
@@ -857,11 +1011,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         }
         __syncwarp();
     }
-    const double2 psix = ep.psi[s];
-    const float2 ip32 = inv_psi32(psix);
     const uint32_t hx32 = static_cast<uint32_t>(hx);
-    Acc acc{};
-    int qn = 0, nh = 0;
     // iterator over (class, outer block u0, inner block w0)
     int cls = -1, oo = 0, n1 = 0, io = 0, n2 = 0, u0 = 0, w0 = 0;
     bool done = false, need_class = true, need_outer = true;
@@ -872,8 +1022,90 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     unsigned umask = 0;
 #pragma unroll
     for (int k = 0; k < U; ++k) hu[k] = hu3[k] = 0u;
+    bool scanning = join;
+    unsigned sbase = 0u;  // next row of the current scan chunk
     while (true) {
-        if (!done) {
+        if (scanning) {
+            const unsigned stotal = q[102];
+            const int st0 = static_cast<int>(q[103]);
+            if (sbase < stotal) {
+                // 32 rows of the chunk: each lane finds its row's group by a binary search over
+                // the offsets.  A row connects to x when the popcount of its string of the
+                // other spin against x's is 2 or 4 (x's alpha group: a beta single or beta-beta
+                // double), 4 (x's beta group: an alpha-alpha double) or 0 or 2 (an alpha'
+                // group: the alpha single or an alpha-beta double).  Singles and doubles go to
+                // separate queues, so that hit batches do not mix the two element paths.
+                const unsigned v = sbase + lane;
+                int g = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (q[32 + g + step] <= v) g += step;
+                bool dbl = false, sgl = false;
+                unsigned code = 0u, row = 0u;
+                if (v < stotal) {
+                    const unsigned kd = q[64 + g];
+                    const ulonglong2 e = __ldg(tp.gent + q[g] + (v - q[32 + g]));
+                    const unsigned kk = kd & 3u;
+                    const unsigned long long ref = kk == kScanBeta ? qx[0] : qx[1];
+                    const unsigned long long dm = e.x ^ ref;
+                    const int d = __popcll(dm);
+                    sgl = kk == kScanAlpha ? d == 2 : (kk == kScanAlphaP && d == 0);
+                    dbl = kk == kScanAlphaP ? d == 2 : d == 4;
+                    if (sgl || dbl) {
+                        code = scan_code(kd, d, dm & ref, dm & e.x);
+                        row = static_cast<unsigned>(e.y);
+                    }
+                }
+                const unsigned md = __ballot_sync(QC_FULLMASK, dbl), ms = __ballot_sync(QC_FULLMASK, sgl);
+                if (dbl) hq[nh + __popc(md & ltmask)] = make_uint2(code, row);
+                if (sgl) hs[ns + __popc(ms & ltmask)] = make_uint2(code, row);
+                nh += __popc(md);
+                ns += __popc(ms);
+                sbase += 32u;
+                __syncwarp();
+            } else if (st0 < sp.nsa) {
+                // the next 32 alpha' = single excitations of x's alpha string: a long group
+                // joins the lists of classes 0 and 4, a short one becomes a scan descriptor
+                const unsigned char* occA = wl;
+                const unsigned char* virA = wl + 64;
+                const int t = st0 + lane;
+                bool keep = false;
+                uint32_t hv32 = 0u;
+                unsigned gst = 0u, gln = 0u, kd = 0u;
+                if (t < sp.nsa) {
+                    const int oi = divA[t];
+                    const int ki = occA[oi], ka = virA[t - oi * sp.va];
+                    const unsigned long long tm = T64[2 * ki] ^ T64[2 * ka];
+                    hv32 = static_cast<uint32_t>(tm);
+                    const unsigned sl = set_slot(tp.aset, tp.set_mask, qx[0] ^ (1ULL << ki) ^ (1ULL << ka), qx[2] ^ tm);
+                    unsigned len = 0u, start = 0u;
+                    if (sl != kNoSlot) {
+                        len = __ldg(tp.jlen + sl);
+                        start = __ldg(tp.jstart + sl);
+                    }
+                    if (static_cast<long long>(len) * tp.scan_cost <= 4LL * (nsb2 + 1)) {
+                        gst = start;
+                        gln = len;
+                        kd = kScanAlphaP | (static_cast<unsigned>(ki) << 8) | (static_cast<unsigned>(ka) << 16);
+                    } else {
+                        keep = true;
+                    }
+                }
+                const unsigned m = __ballot_sync(QC_FULLMASK, keep);
+                if (keep) {
+                    const int pos = nsa2 + __popc(m & ltmask);
+                    H[oSA + pos] = hv32;
+                    IA[pos] = static_cast<unsigned short>(t);
+                }
+                nsa2 += __popc(m);
+                __syncwarp();
+                if (lane == 0) q[103] = static_cast<unsigned>(st0 + 32);
+                store_chunk(gst, c == 0 ? gln : 0u, kd);
+                sbase = 0u;
+            } else {
+                scanning = false;
+            }
+        } else if (!done) {
             if (need_class) {
                 do {
                     ++cls;
@@ -882,7 +1114,8 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     else if (cls == 2) { oo = oPAo; n1 = sp.npoa; io = oPAv; n2 = sp.npva; }
                     else if (cls == 3) { oo = oPBo; n1 = sp.npob; io = oPBv; n2 = sp.npvb; }
                     else if (cls == 4) { oo = oSA; n1 = nsa2; io = oSB; n2 = nsb2; }
-                } while (cls < 5 && (n1 == 0 || n2 == 0 || (cls < 2 ? c != 0 : c * U >= n1)));
+                } while (cls < 5 && (n1 == 0 || n2 == 0 || (cls < 2 ? c != 0 : c * U >= n1) ||
+                                     ((cls == 1 || cls == 3) && !enumA) || (cls == 2 && !enumB)));
                 done = cls >= 5;
                 pairs = lean && (cls == 2 || cls == 3);
                 // excitation chunk c of C: the singles in chunk 0, outer blocks c, c + C, ...
@@ -964,26 +1197,10 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         __syncwarp();
         // resolution stages (the hit queue first, so it never exceeds 63 entries)
         while (true) {
-            if (nh >= 32 || (done && qn == 0 && nh > 0)) {
-                // hits: key check, psi(x') and integrals, then the element.  Singles are
-                // found only in the first two classes, so a batch rarely mixes the kinds.
-                const int n = nh < 32 ? nh : 32;
-                const bool v = lane < n;
-                uint2 e = v ? hq[lane] : make_uint2(0u, 0u);
-                __syncwarp();
-                if (lane < nh - n) hq[lane] = hq[n + lane];
-                nh -= n;
-                __syncwarp();
-                // the filtered walk queues candidate codes; they are decoded only here
-                if (FILTER && v) e.x = decode(e.x, sp, wl, smem, IA, IB);
-                if (v)
-                    verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc,
-                                         [&](double& h64, float& h32, bool& sneg) {
-                                             if ((e.x >> 16) == 0xFFFFu)
-                                                 single_element<PREC>(e.x, prefix_parity(x), sp, wl, h64, h32, sneg);
-                                             else
-                                                 double_element<PREC>(e.x, prefix_parity(x), sp, h64, h32, sneg);
-                                         });
+            const bool dh = nh >= 32 || (done && qn == 0 && nh > 0);
+            const bool dsg = JOIN && (ns >= 32 || (done && qn == 0 && ns > 0));
+            if (dh || dsg) {
+                hit_batch(dh ? hq : hs, dh ? nh : ns);
             } else if (qn >= 32 || (done && qn > 0)) {
                 const int n = qn < 32 ? qn : 32;
                 const bool v = lane < n;

@@ -41,10 +41,14 @@ struct qc_eloc {
     size_t cpart_cap = 0;       // records
     unsigned* d_cticket = nullptr;
     size_t cticket_cap = 0;     // samples
+    unsigned char* d_join = nullptr;  // sample-space join index and its sort workspace
+    size_t join_cap = 0;              // bytes
     long long opt_chunk_pairs = 0;  // 0 default, < 0 one chunk per sample, else pairs per chunk
     int opt_timing = 0, opt_kernel = 0, opt_fw = 0, opt_warps = 0, opt_unroll = 0, opt_grid = 0;
     int opt_prefilter = 1;
     int opt_lean = 0;  // 0 auto, 1 stored pair lists, 2 formed on the fly
+    int opt_join = 0;  // 0 auto, 1 off, 2 on (sample-space mode, filtered kernel)
+    int opt_scan_cost = 0;  // 0 default, else 4 x the cost of a scanned row in enumerated pairs
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool ev_recorded = false;
     int sm_count = 0;

@@ -49,6 +49,15 @@ struct TableParams {
     const unsigned long long* aset;
     const unsigned long long* bset;
     unsigned set_mask;
+    // sample-space join index (NULL: not built).  Set slot s of the alpha set (s + set size of
+    // the beta set) owns the group of table rows whose alpha (beta) string sits in it:
+    // entries jstart[s] .. jstart[s] + jlen[s] - 1 of gent, in row order.  An entry holds the
+    // row's string of the other spin (beta strings in alpha groups, alpha strings in beta
+    // groups) and the row.
+    const unsigned* jstart;
+    const unsigned* jlen;
+    const ulonglong2* gent;
+    int scan_cost;  // a group is scanned when len * scan_cost <= 4 * (pairs it replaces)
 };
 
 // Counters and flags of one evaluation (device memory, zeroed at the start of a call).
@@ -98,6 +107,10 @@ struct ChunkRec {
 // every chunk repeats the sample's set-up, which on the measured workloads costs more than
 // the shorter tails save; the batch autotuner tries sizes around kChunkPairsProbe.
 constexpr long long kDefaultChunkPairs = 0;
+// Sample-space join: a group of table rows is scanned when len * kDefaultScanCost / 4 is at
+// most the number of excitations that scanning it replaces.
+constexpr int kDefaultScanCost = 4;
+constexpr long long kJoinMinRows = 16384;  // the join's default: tables from this many rows
 constexpr long long kChunkPairsProbe = 262144;
 inline int exc_chunks(long long pairs, long long chunk_pairs) {
     if (chunk_pairs <= 0) return 1;
@@ -141,18 +154,20 @@ struct LaunchCfg {
     size_t smem;
     int lean;     // filtered kernel: pair hash lists formed on the fly
     int chunks;   // excitation chunks per sample
+    int join;     // filtered kernel: sample-space join (short row groups scanned)
 };
 
 // host-side launchers (qc_kernels.cu)
 cudaError_t launch_build_table(const TableParams& tp, int n_orb, int na, int nb,
                                const unsigned long long* T, unsigned long long* slots,
                                uint32_t* filter, unsigned long long* aset,
-                               unsigned long long* bset, Counters* ctr, cudaStream_t s);
+                               unsigned long long* bset, Counters* ctr, cudaStream_t s,
+                               unsigned* jkey = nullptr, unsigned* jlen = nullptr);
 cudaError_t launch_eloc_main(const SysParams& sp, const TableParams& tp, const EvalParams& ep,
                              const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk,
                           void* summary_dev, long long pairs_per_sample, cudaStream_t s);
-int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem, int lean = 0);
+int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem, int lean = 0, int join = 0);
 // batch: build every molecule's table in one launch (key_off: prefix of table sizes, device)
 cudaError_t launch_build_batch(const MolParams* mols, const MolWork* work, const long long* key_off,
                                int n_mol, long long n_keys, cudaStream_t s);
@@ -164,10 +179,17 @@ int max_active_batch(int precision, int unroll, int threads, size_t smem);
 size_t batch_warp_bytes(const SysParams& sp, bool lean);
 cudaError_t prepare_batch_kernels(size_t max_smem, size_t* dyn_limit);
 cudaError_t prepare_kernels(size_t max_smem);
-size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw, bool lean = false);
+size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw, bool lean = false, bool join = false);
 size_t direct_smem_bytes(const SysParams& sp, int warps);
 size_t smem_fixed_bytes();  // CTA tables at the head of the main kernels' dynamic shared memory
 int reduce_blocks(long long n);
+// sample-space join index over an n-row table whose slot keys K0 wrote (qc_join.cu):
+// jkey[0, 2n) slot keys (alpha rows, then beta rows offset by the set size), jlen counts
+size_t join_workspace_bytes(long long n, unsigned set_size);
+cudaError_t launch_join_index(const TableParams& tp, unsigned set_size, void* ws, unsigned* jkey,
+                              unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s);
+// in-place exclusive prefix sum of n u32 (qc_dedup.cu); sums: (n / 4096 + 2) u32 of scratch
+cudaError_t exclusive_scan_u32(unsigned* a, long long n, unsigned* sums, cudaStream_t s);
 // message returned by qc_eloc_last_error(NULL) on this thread (qc_api.cu)
 void set_handleless_error(const std::string& msg);
 

@@ -1,0 +1,198 @@
+// qc_join.cu -- the sample-space join index: the table rows grouped by their alpha string
+// and by their beta string.
+//
+// In the sample-space energy (Eq. 5 with x' restricted to the sampled set, Sec. IV-C-4)
+// a connected x' = (alpha', beta') of a sample x = (alpha, beta) has either alpha' = alpha
+// (a beta single or beta-beta double), beta' = beta (an alpha-alpha double) or alpha' a
+// single excitation of alpha (an alpha single when beta' = beta, else an alpha-beta double
+// with beta' a single excitation of beta).  So the rows that can connect to x are those of
+// a few groups: the rows sharing x's alpha string, those sharing its beta string, and the
+// rows of each alpha' group.  The local-energy kernel scans a short group row by row (one
+// popcount of the other spin's string difference decides the connection) and enumerates the
+// excitations into a long one through the filter and the bucket table.
+//
+// Built once per evaluation after K0, which leaves each row's slot in the alpha and beta
+// spin-string sets as a sort key (alpha rows first, beta rows offset by the set size) and
+// the group sizes:
+//   starts:    exclusive prefix sum of the group sizes
+//   J1 hist:   per-tile digit counts (11-bit digits of the slot key)
+//   scan:      exclusive prefix over the (digit, tile) counts, digit-major
+//   J2 scatter: stable scatter of (key, row) by digit; after the passes the pairs are in
+//              (slot, row) order, so every group lists its rows in row order and the scan
+//              order of a group -- and with it the order of accumulation -- is the same on
+//              every run
+//   J3 gather: each entry's row and the row's string of the other spin (16 bytes, so one
+//              load brings the kernel both)
+// Traffic per row: 8 B read (hist) + 8 B read + 8 B written (scatter) per pass and key half,
+// then 16 B read, 16 B written; a few tens of microseconds at 10^5 rows.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "qc_eloc.h"
+#include "qc_internal.h"
+
+namespace {
+
+constexpr int kJTile = 2048;  // items per warp tile (64 steps of 32)
+constexpr int kJWarps = 4;    // warps per block (32 KB of per-warp digit counts)
+constexpr int kJBits = 11;
+constexpr int kJBins = 1 << kJBits;
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+struct JLayout {
+    size_t key1, val0, val1, table, sums, total;
+};
+
+JLayout jlayout(long long n, unsigned set_size) {
+    const long long m = 2 * std::max<long long>(n, 1);
+    const long long tiles = (m + kJTile - 1) / kJTile;
+    const long long table_n = static_cast<long long>(kJBins) * tiles;
+    const long long scan_n = std::max<long long>(table_n, 2LL * set_size);
+    JLayout L{};
+    size_t off = 0;
+    L.key1 = off; off = align256(off + static_cast<size_t>(m) * 4);
+    L.val0 = off; off = align256(off + static_cast<size_t>(m) * 4);
+    L.val1 = off; off = align256(off + static_cast<size_t>(m) * 4);
+    L.table = off; off = align256(off + static_cast<size_t>(table_n) * 4);
+    L.sums = off; off = align256(off + static_cast<size_t>(scan_n / 4096 + 2) * 4 + 4096);
+    L.total = off;
+    return L;
+}
+
+__global__ void __launch_bounds__(32 * kJWarps) join_hist_kernel(const unsigned* __restrict__ key, long long m,
+                                                                 int shift, long long tiles,
+                                                                 unsigned* __restrict__ table) {
+    __shared__ unsigned hist[kJWarps][kJBins];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = lane; d < kJBins; d += 32) hist[warp][d] = 0u;
+    __syncwarp();
+    const long long t = static_cast<long long>(blockIdx.x) * kJWarps + warp;
+    if (t >= tiles) return;  // warp-uniform; no block-wide barrier
+    const long long i0 = t * kJTile;
+    const long long i1 = i0 + kJTile < m ? i0 + kJTile : m;
+    for (long long i = i0 + lane; i < i1; i += 32) atomicAdd(&hist[warp][(key[i] >> shift) & (kJBins - 1)], 1u);
+    __syncwarp();
+    for (int d = lane; d < kJBins; d += 32) table[static_cast<long long>(d) * tiles + t] = hist[warp][d];
+}
+
+// Stable scatter of a tile in index order; the first pass takes the row from the index
+// (item i < n is row i's alpha key, item n + i its beta key).
+__global__ void __launch_bounds__(32 * kJWarps) join_scatter_kernel(const unsigned* __restrict__ key_in,
+                                                                    const unsigned* __restrict__ val_in,
+                                                                    long long n, unsigned* __restrict__ key_out,
+                                                                    unsigned* __restrict__ val_out, long long m,
+                                                                    int shift, long long tiles,
+                                                                    const unsigned* __restrict__ offs) {
+    __shared__ unsigned run[kJWarps][kJBins];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long t = static_cast<long long>(blockIdx.x) * kJWarps + warp;
+    if (t >= tiles) return;
+    for (int d = lane; d < kJBins; d += 32) run[warp][d] = offs[static_cast<long long>(d) * tiles + t];
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+    const long long i0 = t * kJTile;
+    const long long i1 = i0 + kJTile < m ? i0 + kJTile : m;
+    for (long long b = i0; b < i1; b += 32) {
+        const long long i = b + lane;
+        const bool v = i < i1;
+        const unsigned active = __ballot_sync(0xffffffffu, v);
+        if (v) {
+            const unsigned k = key_in[i];
+            const unsigned val = val_in ? val_in[i] : static_cast<unsigned>(i < n ? i : i - n);
+            const unsigned d = (k >> shift) & (kJBins - 1);
+            const unsigned same = __match_any_sync(active, d);
+            const unsigned base = run[warp][d];
+            const unsigned pos = base + __popc(same & lt);
+            key_out[pos] = k;
+            val_out[pos] = val;
+            __syncwarp(active);
+            if ((same & lt) == 0u) run[warp][d] = base + __popc(same);  // the lowest lane of the group
+        }
+        __syncwarp();
+    }
+}
+
+// Spatial string of one spin from an interleaved key: bits 2k + spin, packed.
+__device__ __forceinline__ unsigned long long gather_even(unsigned long long w) {
+    w &= 0x5555555555555555ULL;
+    w = (w | (w >> 1)) & 0x3333333333333333ULL;
+    w = (w | (w >> 2)) & 0x0F0F0F0F0F0F0F0FULL;
+    w = (w | (w >> 4)) & 0x00FF00FF00FF00FFULL;
+    w = (w | (w >> 8)) & 0x0000FFFF0000FFFFULL;
+    w = (w | (w >> 16)) & 0x00000000FFFFFFFFULL;
+    return w;
+}
+__device__ __forceinline__ unsigned long long spin_string(ulonglong2 k, int spin) {
+    return gather_even(k.x >> spin) | (gather_even(k.y >> spin) << 32);
+}
+
+__global__ void __launch_bounds__(256) join_gather_kernel(const ulonglong2* __restrict__ keys,
+                                                          const unsigned* __restrict__ skey,
+                                                          const unsigned* __restrict__ srow, long long m,
+                                                          unsigned set_size, ulonglong2* __restrict__ gent) {
+    for (long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < m;
+         p += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const unsigned k = skey[p];
+        if (k >= 2u * set_size) continue;  // rows that failed validation: past every group
+        const unsigned row = srow[p];
+        // alpha groups list beta strings and the other way round
+        gent[p] = make_ulonglong2(spin_string(keys[row], k < set_size ? 1 : 0), row);
+    }
+}
+
+int bits_for(unsigned long long v) {  // bits to hold 0..v
+    int b = 1;
+    while (b < 64 && (v >> b) != 0ULL) ++b;
+    return b;
+}
+
+}  // namespace
+
+size_t qc::join_workspace_bytes(long long n, unsigned set_size) { return jlayout(n, set_size).total; }
+
+cudaError_t qc::launch_join_index(const TableParams& tp, unsigned set_size, void* ws, unsigned* jkey,
+                                  unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s) {
+    const long long n = tp.n;
+    if (n <= 0) return cudaSuccess;
+    const long long m = 2 * n;
+    const JLayout L = jlayout(n, set_size);
+    unsigned char* W = static_cast<unsigned char*>(ws);
+    unsigned* key1 = reinterpret_cast<unsigned*>(W + L.key1);
+    unsigned* val0 = reinterpret_cast<unsigned*>(W + L.val0);
+    unsigned* val1 = reinterpret_cast<unsigned*>(W + L.val1);
+    unsigned* table = reinterpret_cast<unsigned*>(W + L.table);
+    unsigned* sums = reinterpret_cast<unsigned*>(W + L.sums);
+    // group starts
+    cudaError_t e = cudaMemcpyAsync(jstart, jlen, 2 * static_cast<size_t>(set_size) * sizeof(unsigned),
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = qc::exclusive_scan_u32(jstart, 2LL * set_size, sums, s);
+    // stable LSD sort of (slot key, row) over the bits of the largest key (the sentinel 2 * size)
+    const int passes = (bits_for(2ULL * set_size) + kJBits - 1) / kJBits;
+    const long long tiles = (m + kJTile - 1) / kJTile;
+    const unsigned blocks = static_cast<unsigned>((tiles + kJWarps - 1) / kJWarps);
+    const unsigned* src_k = jkey;
+    const unsigned* src_v = nullptr;
+    unsigned* dk[2] = {key1, jkey};
+    unsigned* dv[2] = {val0, val1};
+    for (int p = 0; p < passes && e == cudaSuccess; ++p) {
+        join_hist_kernel<<<blocks, 32 * kJWarps, 0, s>>>(src_k, m, p * kJBits, tiles, table);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = qc::exclusive_scan_u32(table, static_cast<long long>(kJBins) * tiles, sums, s);
+        if (e == cudaSuccess) {
+            join_scatter_kernel<<<blocks, 32 * kJWarps, 0, s>>>(src_k, src_v, n, dk[p & 1], dv[p & 1], m,
+                                                               p * kJBits, tiles, table);
+            e = cudaGetLastError();
+        }
+        src_k = dk[p & 1];
+        src_v = dv[p & 1];
+    }
+    if (e == cudaSuccess) {
+        const unsigned gblocks = static_cast<unsigned>(std::min<long long>((m + 255) / 256, 8192));
+        join_gather_kernel<<<gblocks, 256, 0, s>>>(tp.keys, src_k, src_v, m, set_size, gent);
+        e = cudaGetLastError();
+    }
+    return e;
+}

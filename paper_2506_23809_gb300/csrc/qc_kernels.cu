@@ -17,8 +17,8 @@ int reduce_blocks(long long n) {
 
 size_t smem_fixed_bytes() { return kOffVar; }
 
-size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw, bool lean) {
-    return kOffVar + (static_cast<size_t>(4) << fw) + static_cast<size_t>(warps) * main_warp_bytes(sp, true, lean);
+size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw, bool lean, bool join) {
+    return kOffVar + (static_cast<size_t>(4) << fw) + static_cast<size_t>(warps) * main_warp_bytes(sp, true, lean, join);
 }
 size_t direct_smem_bytes(const SysParams& sp, int warps) {
     return kOffVar + static_cast<size_t>(warps) * main_warp_bytes(sp, false);
@@ -28,12 +28,13 @@ __global__ void __launch_bounds__(256) build_table_kernel(TableParams tp, int n_
                                                           const unsigned long long* __restrict__ T,
                                                           unsigned long long* slots,
                                                           uint32_t* filter, unsigned long long* aset,
-                                                          unsigned long long* bset, Counters* ctr) {
+                                                          unsigned long long* bset, Counters* ctr,
+                                                          unsigned* jkey, unsigned* jlen) {
     const long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (r < tp.n) build_one(tp, n_orb, na, nb, T, slots, filter, aset, bset, ctr, r);
+    if (r < tp.n) build_one(tp, n_orb, na, nb, T, slots, filter, aset, bset, ctr, r, jkey, jlen);
 }
 
-template <int PREC, int U, bool FILTER, int LEAN>
+template <int PREC, int U, bool FILTER, int LEAN, bool JOIN>
 __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ SysParams sp,
                                                         const __grid_constant__ TableParams tp,
                                                         const __grid_constant__ EvalParams ep) {
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
         __syncthreads();
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * main_warp_bytes(sp, FILTER, LEAN == 1);
+    unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * main_warp_bytes(sp, FILTER, LEAN == 1, JOIN);
     // samples go to warps as they come free: one cursor for the grid, so a warp that drew
     // cheap samples takes more of them and the launch ends with little tail
     // with C excitation chunks per sample a work item is (sample, chunk): item = s * C + c
@@ -92,8 +93,8 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= items) break;
         const unsigned long long s = it / C;
-        run_sample<PREC, U, FILTER, LEAN>(sp, tp, ep, static_cast<long long>(s), lane, smem, wl, filt,
-                                          static_cast<int>(it - s * C), static_cast<int>(C));
+        run_sample<PREC, U, FILTER, LEAN, JOIN>(sp, tp, ep, static_cast<long long>(s), lane, smem, wl, filt,
+                                                static_cast<int>(it - s * C), static_cast<int>(C));
     }
 }
 
@@ -111,11 +112,12 @@ __global__ void __launch_bounds__(kRedThreads) reduce_pass2(EvalParams ep, doubl
 cudaError_t launch_build_table(const TableParams& tp, int n_orb, int na, int nb,
                                const unsigned long long* T, unsigned long long* slots,
                                uint32_t* filter, unsigned long long* aset,
-                               unsigned long long* bset, Counters* ctr, cudaStream_t s) {
+                               unsigned long long* bset, Counters* ctr, cudaStream_t s, unsigned* jkey,
+                               unsigned* jlen) {
     if (tp.n <= 0) return cudaSuccess;
     const long long blocks = (tp.n + 255) / 256;
     build_table_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(tp, n_orb, na, nb, T, slots,
-                                                                      filter, aset, bset, ctr);
+                                                                      filter, aset, bset, ctr, jkey, jlen);
     return cudaGetLastError();
 }
 
@@ -123,16 +125,17 @@ template <int PREC, int LEAN>
 static void launch_filtered(const SysParams& sp, const TableParams& tp, const EvalParams& ep, const LaunchCfg& c,
                             cudaStream_t s) {
     const dim3 grid(c.grid), block(32 * c.warps);
-    if (c.unroll == 1) eloc_main_kernel<PREC, 1, true, LEAN><<<grid, block, c.smem, s>>>(sp, tp, ep);
-    else if (c.unroll == 2) eloc_main_kernel<PREC, 2, true, LEAN><<<grid, block, c.smem, s>>>(sp, tp, ep);
-    else eloc_main_kernel<PREC, 4, true, LEAN><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    if (c.join) eloc_main_kernel<PREC, 4, true, LEAN, true><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    else if (c.unroll == 1) eloc_main_kernel<PREC, 1, true, LEAN, false><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    else if (c.unroll == 2) eloc_main_kernel<PREC, 2, true, LEAN, false><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    else eloc_main_kernel<PREC, 4, true, LEAN, false><<<grid, block, c.smem, s>>>(sp, tp, ep);
 }
 
 template <int PREC>
 static cudaError_t launch_main_p(const SysParams& sp, const TableParams& tp, const EvalParams& ep,
                                  const LaunchCfg& c, cudaStream_t s) {
     if (c.kernel != 2) {
-        eloc_main_kernel<PREC, 1, false, 0><<<dim3(c.grid), dim3(32 * c.warps), c.smem, s>>>(sp, tp, ep);
+        eloc_main_kernel<PREC, 1, false, 0, false><<<dim3(c.grid), dim3(32 * c.warps), c.smem, s>>>(sp, tp, ep);
     } else if (c.lean) {
         launch_filtered<PREC, 1>(sp, tp, ep, c, s);
     } else {
@@ -158,22 +161,25 @@ cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk, void
     return cudaGetLastError();
 }
 
+// the join is built with U = 4 only
 template <int PREC>
-static const void* main_kernel_ptr(int kernel, int unroll, int lean) {
-    if (kernel != 2) return (const void*)eloc_main_kernel<PREC, 1, false, 0>;
+static const void* main_kernel_ptr(int kernel, int unroll, int lean, int join) {
+    if (kernel != 2) return (const void*)eloc_main_kernel<PREC, 1, false, 0, false>;
     if (lean) {
-        if (unroll == 1) return (const void*)eloc_main_kernel<PREC, 1, true, 1>;
-        if (unroll == 2) return (const void*)eloc_main_kernel<PREC, 2, true, 1>;
-        return (const void*)eloc_main_kernel<PREC, 4, true, 1>;
+        if (join) return (const void*)eloc_main_kernel<PREC, 4, true, 1, true>;
+        if (unroll == 1) return (const void*)eloc_main_kernel<PREC, 1, true, 1, false>;
+        if (unroll == 2) return (const void*)eloc_main_kernel<PREC, 2, true, 1, false>;
+        return (const void*)eloc_main_kernel<PREC, 4, true, 1, false>;
     }
-    if (unroll == 1) return (const void*)eloc_main_kernel<PREC, 1, true, 0>;
-    if (unroll == 2) return (const void*)eloc_main_kernel<PREC, 2, true, 0>;
-    return (const void*)eloc_main_kernel<PREC, 4, true, 0>;
+    if (join) return (const void*)eloc_main_kernel<PREC, 4, true, 0, true>;
+    if (unroll == 1) return (const void*)eloc_main_kernel<PREC, 1, true, 0, false>;
+    if (unroll == 2) return (const void*)eloc_main_kernel<PREC, 2, true, 0, false>;
+    return (const void*)eloc_main_kernel<PREC, 4, true, 0, false>;
 }
 
-int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem, int lean) {
-    const void* f = precision == QC_FP64 ? main_kernel_ptr<QC_FP64>(kernel, unroll, lean)
-                                         : main_kernel_ptr<QC_FP32_COMP>(kernel, unroll, lean);
+int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem, int lean, int join) {
+    const void* f = precision == QC_FP64 ? main_kernel_ptr<QC_FP64>(kernel, unroll, lean, join)
+                                         : main_kernel_ptr<QC_FP32_COMP>(kernel, unroll, lean, join);
     int n = 0;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) == cudaSuccess ? n : 0;
 }
@@ -184,12 +190,13 @@ cudaError_t prepare_kernels(size_t max_smem) {
     for (int prec = 0; prec < 2; ++prec)
         for (int kernel = 1; kernel <= 2; ++kernel)
             for (int unroll : {1, 2, 4})
-                for (int lean = 0; lean < 2; ++lean) {
-                    const void* f = prec == QC_FP64 ? main_kernel_ptr<QC_FP64>(kernel, unroll, lean)
-                                                    : main_kernel_ptr<QC_FP32_COMP>(kernel, unroll, lean);
-                    const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
-                    if (r != cudaSuccess) e = r;
-                }
+                for (int lean = 0; lean < 2; ++lean)
+                    for (int join = 0; join < 2; ++join) {
+                        const void* f = prec == QC_FP64 ? main_kernel_ptr<QC_FP64>(kernel, unroll, lean, join)
+                                                        : main_kernel_ptr<QC_FP32_COMP>(kernel, unroll, lean, join);
+                        const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+                        if (r != cudaSuccess) e = r;
+                    }
     return e;
 }
 

@@ -69,11 +69,13 @@ def assert_eloc_close(got, want, rtol=RTOL_FP64):
 
 
 KERNELS = [dict(), {2: 1}, {2: 2, 5: 1}, {2: 2, 5: 2}, {2: 2, 5: 4}, {2: 2, 4: 3, 6: 5}, {2: 1, 4: 1, 6: 7},
-           {2: 2, 8: 2}, {2: 2, 8: 2, 5: 1}]
+           {2: 2, 8: 2}, {2: 2, 8: 2, 5: 1}, {2: 2, 10: 1}, {2: 2, 10: 2}, {2: 2, 10: 2, 11: 1},
+           {2: 2, 10: 2, 11: 1024}, {2: 2, 10: 2, 8: 2, 5: 1}]
 
 
 @pytest.mark.parametrize("opts", KERNELS, ids=["auto", "direct", "filt_u1", "filt_u2", "filt_u4",
-                                                "filt_w3_g5", "direct_w1_g7", "lean", "lean_u1"])
+                                                "filt_w3_g5", "direct_w1_g7", "lean", "lean_u1", "nojoin",
+                                                "join", "join_scan", "join_enum", "join_lean_u1"])
 def test_tiny_sample_mode(B, orc, opts):
     """N=14, 6 electrons, 1,000 uniform samples (204 pairs each), every kernel variant."""
     ints, s = I.make_workload("n14_e6_u1k")
@@ -103,8 +105,8 @@ def test_lean_lists_equal_stored(B, orc, n, ne, nu, prec):
     keys = I.rank_weighted_samples(K, ne // 2, ne // 2, nu, seed=991 + n)
     counts = I.zipf_counts(nu, 40 * nu, 992 + n)
     psi = I.lognormal_psi(nu, 993 + n)
-    a = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={8: 1})
-    b = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={8: 2})
+    a = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={8: 1, 10: 1})
+    b = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={8: 2, 10: 1})
     assert a["cfg"]["kernel"] == 2 and b["cfg"]["kernel"] == 3
     assert b["cfg"]["warps"] >= a["cfg"]["warps"] and b["cfg"]["filter_log2w"] == a["cfg"]["filter_log2w"]
     assert np.array_equal(a["eloc"].view(np.uint64), b["eloc"].view(np.uint64))
@@ -113,6 +115,52 @@ def test_lean_lists_equal_stored(B, orc, n, ne, nu, prec):
     assert_sets_equal(b, det)
     if prec == 0:
         assert_eloc_close(b["eloc"], want)
+
+
+@pytest.mark.parametrize("n,ne,nu,prec,opts", [(52, 14, 3000, 0, {}), (76, 20, 3000, 1, {}),
+                                               (52, 14, 3000, 0, {11: 1}), (52, 14, 3000, 0, {11: 64}),
+                                               (76, 20, 2000, 1, {8: 2, 5: 2}), (52, 14, 3000, 0, {9: 2000}),
+                                               (40, 8, 1500, 0, {}), (128, 64, 24, 0, {})],
+                         ids=["n52", "n76_fp32c", "n52_scan_all", "n52_enum_most", "n76_lean_u2", "n52_chunks",
+                              "n40", "n128"])
+def test_join_equals_enumeration(B, orc, n, ne, nu, prec, opts):
+    """The sample-space join (QC_OPT_JOIN 2: short row groups scanned, long ones enumerated)
+    finds the same connected set with the same rows and phases as plain enumeration
+    (QC_OPT_JOIN 1) and as the oracle; E_loc differs only by the order of accumulation.
+    Rank-weighted samples give a few very large groups (the reference determinant's
+    strings) beside many small ones, so both halves of the join run."""
+    K = n // 2
+    ints = I.make_integrals(K, min(n, 52), 1990 + n)
+    na = (ne + 1) // 2
+    keys = I.rank_weighted_samples(K, na, ne - na, nu, seed=1991 + n)
+    counts = I.zipf_counts(nu, 40 * nu, 1992 + n)
+    psi = I.lognormal_psi(nu, 1993 + n)
+    a = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={2: 2, 10: 1, **opts})
+    b = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={2: 2, 10: 2, **opts})
+    assert a["cfg"]["kernel"] in (2, 3) and b["cfg"]["kernel"] in (4, 5)
+    assert np.array_equal(a["hits"], b["hits"]) and np.array_equal(a["rowsum"], b["rowsum"])
+    assert np.array_equal(a["signsum"], b["signsum"])
+    want, det = orc.eloc(ints.h, ints.eri, 0.0, n, keys, psi, details=True)
+    assert_sets_equal(b, det)
+    if prec == 0:
+        assert_eloc_close(b["eloc"], want)
+        assert_eloc_close(b["eloc"], a["eloc"], rtol=1e-12)
+    else:
+        m, _, _, _ = orc.reduce(want, counts)
+        assert abs(b["summary"]["energy"] - m) <= ATOL_FP32C
+    assert b["summary"]["status"] == 0 and b["summary"]["n_hits"] == a["summary"]["n_hits"]
+
+
+def test_join_deterministic(B):
+    """Two runs of the join path give bitwise-equal E_loc (group order inside the index is
+    row order, whatever order the build's atomics took)."""
+    K = 26
+    ints = I.make_integrals(K, 52, 2052)
+    keys = I.rank_weighted_samples(K, 7, 7, 4000, seed=2053)
+    counts = I.zipf_counts(4000, 160000, 2054)
+    psi = I.lognormal_psi(4000, 2055)
+    r = [run_gpu(B, ints, 52, 14, keys, counts, psi, opts={10: 2}, diag=False)["eloc"] for _ in range(2)]
+    assert np.array_equal(r[0].view(np.uint64), r[1].view(np.uint64))
 
 
 def test_exact_ground_state_constant_eloc(B, orc):
