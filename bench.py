@@ -68,7 +68,7 @@ def _args():
     p.add_argument("--chunk", type=int, default=10000, help="full form: samples per export/apply chunk")
     p.add_argument("--requests", type=int, default=48, help="serve form: requests")
     p.add_argument("--rate", type=float, default=20.0, help="serve form: arrivals per second")
-    p.add_argument("--quantum", type=float, default=1e10,
+    p.add_argument("--quantum", type=float, default=1e12,
                    help="serve form: enumerated pairs per wave (0: one wave takes every ready request)")
     p.add_argument("--oldest-pct", type=int, default=50,
                    help="serve form: percent of a wave guaranteed to the oldest request")

@@ -342,7 +342,7 @@ qc_status qc_batch_autotune(qc_batch* batch, void* stream, int iters, int64_t* b
  * with the same nonzero mol_key (least-recently-used eviction when the budget needs
  * room), and launches admitted requests whose inputs are on the device as batches
  * ("waves") on `n_streams` streams.  A wave holds about `quantum` enumerated pairs
- * (QC_SRV_OPT_QUANTUM, default 1e10): the oldest request with a guaranteed share of it
+ * (QC_SRV_OPT_QUANTUM, default 1e12): the oldest request with a guaranteed share of it
  * (QC_SRV_OPT_OLDEST_PCT, default half), the
  * others least remaining work first; a request that does not fit whole runs a slice of its
  * rows (against its whole sample table) and joins the next wave, and after a wave that ran

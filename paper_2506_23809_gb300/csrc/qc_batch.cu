@@ -61,6 +61,15 @@ struct qc_batch {
     unsigned char* d_arena = nullptr;
     size_t arena_cap = 0, arena_bytes = 0;
     qc_eloc_summary* d_sums = nullptr;
+    // sample-space join over every molecule (one index for the batch): sort keys and values,
+    // group starts, entries, sort space and the molecules' first slot keys, outside the
+    // zeroed arena (the group sizes are inside it)
+    bool join = false;
+    unsigned char* d_join = nullptr;
+    size_t join_cap = 0;
+    long long j_items = 0;
+    unsigned long long j_slots = 0;
+    size_t jo_val = 0, jo_start = 0, jo_ent = 0, jo_ws = 0, jo_base = 0, ja_len = 0;
     // launch shape
     int unroll = 4, warps = 0, chunk = 1;
     long long chunk_pairs = qc::kDefaultChunkPairs;  // excitation chunks (<= 0: one warp per sample)
@@ -109,6 +118,17 @@ qc_status prepare(qc_batch* B) {
     std::vector<Lay> lay(M);
     const size_t fixed0 = qc::smem_fixed_bytes();
     const int wcap = B->warps > 0 ? std::min(B->warps, qc::kFilteredMaxWarps) : 16;  // 16: the spill-free bound
+    // the join, per molecule as its handle would decide (so that a molecule's results are
+    // the same in a batch as alone); the batch shares one index build over those molecules
+    std::vector<char> jm(M, 0);
+    bool join = false;
+    for (int m = 0; m < M; ++m) {
+        const qc_eloc* H = B->handles[m];
+        jm[m] = H->opt_prefilter && H->na > 0 && H->nb > 0 &&
+                (H->opt_join == 2 || (H->opt_join == 0 && B->in[m].n_u >= qc::kJoinMinRows));
+        join = join || jm[m];
+    }
+    B->join = join;
     std::vector<int> act(M), lean(M);
     std::vector<unsigned> stride(M);
     for (int m = 0; m < M; ++m) {
@@ -120,7 +140,7 @@ qc_status prepare(qc_batch* B) {
         int fw = 0, w = 0;
         lean[m] = 0;
         for (int ln = 0; ln < 2; ++ln) {
-            const unsigned st = static_cast<unsigned>((qc::batch_warp_bytes(B->handles[m]->sp, ln) + 15) / 16 * 16);
+            const unsigned st = static_cast<unsigned>((qc::batch_warp_bytes(B->handles[m]->sp, ln, join) + 15) / 16 * 16);
             int f = filter_log2(n), ww = 0;
             for (; f >= 5; --f) {
                 const size_t base = fixed0 + (static_cast<size_t>(4) << f);
@@ -154,6 +174,27 @@ qc_status prepare(qc_batch* B) {
         L.sum = 0;
         key_off[m + 1] = key_off[m] + B->in[m].n_u;
     }
+    // join: molecule m's slot keys start at slot_base[m] (two sets of nb slots each)
+    // (molecules without the join take no slots and no items)
+    unsigned long long total_slots = 0;
+    long long total_items = 0;
+    std::vector<long long> item_off(M + 1, 0);
+    for (int m = 0; m < M; ++m) {
+        total_slots += jm[m] ? 2 * lay[m].nb : 0;
+        item_off[m + 1] = item_off[m] + (jm[m] ? 2 * B->in[m].n_u : 0);
+    }
+    total_items = item_off[M];
+    if (join && (total_items >= 0xffffffffLL || total_slots >= 0xffffffffULL)) {
+        join = B->join = false;  // sort keys, values and entry positions are 32-bit
+        std::fill(jm.begin(), jm.end(), 0);
+    }
+    std::vector<unsigned> slot_base(M + 1, 0u);
+    if (join)
+        for (int m = 0; m < M; ++m) slot_base[m + 1] = slot_base[m] + static_cast<unsigned>(jm[m] ? 2 * lay[m].nb : 0);
+    if (join) {
+        B->ja_len = off;
+        off = align256(off + static_cast<size_t>(slot_base[M]) * 4);
+    }
     if (off > B->arena_cap) {
         // grow with headroom: a reallocation (cudaFree) waits for the whole device
         if (B->d_arena) cudaFree(B->d_arena);
@@ -166,6 +207,30 @@ qc_status prepare(qc_batch* B) {
     }
     B->arena_bytes = off;
     unsigned char* A = B->d_arena;
+    if (join) {
+        const long long mi = total_items;
+        const unsigned long long ns = slot_base[M];
+        size_t jo = align256(static_cast<size_t>(std::max<long long>(mi, 1)) * 4);  // keys
+        B->jo_val = jo; jo = align256(jo + static_cast<size_t>(std::max<long long>(mi, 1)) * 4);
+        B->jo_start = jo; jo = align256(jo + static_cast<size_t>(ns) * 4);
+        B->jo_ent = jo; jo = align256(jo + static_cast<size_t>(std::max<long long>(mi, 1)) * 16);
+        B->jo_base = jo; jo = align256(jo + static_cast<size_t>(M + 1) * 4);
+        B->jo_ws = jo; jo = align256(jo + qc::join_batch_workspace_bytes(mi, ns));
+        if (jo > B->join_cap) {
+            if (B->d_join) cudaFree(B->d_join);
+            B->d_join = nullptr;
+            B->join_cap = 0;
+            const size_t cap = align256(jo + jo / 2);
+            cudaError_t e = cudaMalloc(&B->d_join, cap);
+            if (e != cudaSuccess) return bcuda(B, e, "cudaMalloc batch join index");
+            B->join_cap = cap;
+        }
+        B->j_items = mi;
+        B->j_slots = ns;
+        cudaError_t e = cudaMemcpy(B->d_join + B->jo_base, slot_base.data(), (M + 1) * sizeof(unsigned),
+                                   cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bcuda(B, e, "copy join slot bases");
+    }
     for (int m = 0; m < M; ++m) {
         const Lay& L = lay[m];
         const BatchInput& I = B->in[m];
@@ -179,6 +244,15 @@ qc_status prepare(qc_batch* B) {
         W.part = reinterpret_cast<double*>(A + L.part);
         W.sum = B->d_sums + m;
         W.nblk = I.reduce ? qc::reduce_blocks(I.n_u) : 0;
+        W.jkey = W.jval = W.jlen = nullptr;
+        W.jbase = W.jsent = 0u;
+        if (jm[m]) {
+            W.jkey = reinterpret_cast<unsigned*>(B->d_join) + item_off[m];
+            W.jval = reinterpret_cast<unsigned*>(B->d_join + B->jo_val) + item_off[m];
+            W.jlen = reinterpret_cast<unsigned*>(A + B->ja_len);
+            W.jbase = slot_base[m];
+            W.jsent = slot_base[M];
+        }
         B->red_blocks = std::max(B->red_blocks, W.nblk);
         qc::MolParams& P = mp[m];
         P.sp = H->sp;
@@ -193,6 +267,12 @@ qc_status prepare(qc_batch* B) {
         P.tp.aset = W.aset;
         P.tp.bset = W.bset;
         P.tp.set_mask = static_cast<unsigned>(L.nb - 1);
+        if (jm[m]) {
+            P.tp.jstart = reinterpret_cast<const unsigned*>(B->d_join + B->jo_start) + slot_base[m];
+            P.tp.jlen = reinterpret_cast<const unsigned*>(A + B->ja_len) + slot_base[m];
+            P.tp.gent = reinterpret_cast<const ulonglong2*>(B->d_join + B->jo_ent);
+            P.tp.scan_cost = H->opt_scan_cost ? H->opt_scan_cost : qc::kDefaultScanCost;
+        }
         P.ep = qc::EvalParams{};
         P.ep.samples = reinterpret_cast<const ulonglong2*>(I.samples);
         P.ep.psi = reinterpret_cast<const double2*>(I.psi);
@@ -216,7 +296,7 @@ qc_status prepare(qc_batch* B) {
     int warps = 1;
     for (int m = 0; m < M; ++m) warps = std::max(warps, act[m]);
     B->smem = B->dyn_limit;
-    const int per_sm = qc::max_active_batch(B->precision, B->unroll, 32 * warps, B->smem);
+    const int per_sm = qc::max_active_batch(B->precision, B->unroll, 32 * warps, B->smem, join);
     if (per_sm < 1) return bfail(B, QC_ERR_CAPACITY, "batch kernel cannot be resident with this shape");
     B->grid = per_sm * B->sm_count;
     // run order: estimated time n_u * pairs / active warps, longest first
@@ -262,6 +342,14 @@ qc_status enqueue(qc_batch* B, qc_eloc_summary* sums_host, cudaStream_t s, bool 
     if (timed) QB(cudaEventRecord(B->ev[0], s), "cudaEventRecord");
     QB(cudaMemsetAsync(B->d_arena, 0, B->arena_bytes, s), "memset arena");
     QB(qc::launch_build_batch(B->d_mols, B->d_work, B->d_key_off, B->n_mol, B->n_keys, s), "batch build");
+    if (B->join)
+        QB(qc::launch_join_batch(B->d_mols, reinterpret_cast<const unsigned*>(B->d_join + B->jo_base), B->n_mol,
+                                 B->j_items, B->j_slots, B->d_join + B->jo_ws, reinterpret_cast<unsigned*>(B->d_join),
+                                 reinterpret_cast<unsigned*>(B->d_join + B->jo_val),
+                                 reinterpret_cast<unsigned*>(B->d_arena + B->ja_len),
+                                 reinterpret_cast<unsigned*>(B->d_join + B->jo_start),
+                                 reinterpret_cast<ulonglong2*>(B->d_join + B->jo_ent), s),
+           "batch join index");
     if (timed) QB(cudaEventRecord(B->ev[1], s), "cudaEventRecord");
     if (B->n_run > 0) {
         qc::BatchParams bp{};
@@ -270,7 +358,8 @@ qc_status enqueue(qc_batch* B, qc_eloc_summary* sums_host, cudaStream_t s, bool 
         bp.next = reinterpret_cast<unsigned long long*>(B->d_arena);  // cursors lead the arena
         bp.n_mol = B->n_run;
         bp.chunk = B->chunk;
-        QB(qc::launch_eloc_batch(bp, B->precision, B->unroll, B->grid, B->warps_used, B->smem, s), "batch kernel");
+        QB(qc::launch_eloc_batch(bp, B->precision, B->unroll, B->grid, B->warps_used, B->smem, s, B->join),
+           "batch kernel");
     }
     if (timed) QB(cudaEventRecord(B->ev[2], s), "cudaEventRecord");
     QB(qc::launch_reduce_batch(B->d_mols, B->d_work, B->n_mol, B->red_blocks, s), "batch reduce");
@@ -392,7 +481,7 @@ qc_status qc_batch_destroy(qc_batch* B) {
     drop_graph(B);
     for (void* p : {static_cast<void*>(B->d_mols), static_cast<void*>(B->d_work), static_cast<void*>(B->d_key_off),
                     static_cast<void*>(B->d_order), static_cast<void*>(B->d_arena),
-                    static_cast<void*>(B->d_sums)})
+                    static_cast<void*>(B->d_sums), static_cast<void*>(B->d_join)})
         if (p) cudaFree(p);
     for (auto& ev : B->ev)
         if (ev) cudaEventDestroy(ev);

@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(256) build_batch_kernel(const MolParams* __res
     const MolParams& P = mols[lo];
     const MolWork& W = work[lo];
     build_one(P.tp, P.sp.n_orb, P.sp.na, P.sp.nb, P.ep.T, W.slots, W.filter, W.aset, W.bset, W.ctr,
-              g - key_off[lo]);
+              g - key_off[lo], W.jkey, W.jlen, W.jbase, W.jsent, W.jval);
 }
 
 // batch: blockIdx.y is the molecule
@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(kRedThreads) reduce_batch_pass2(const MolParam
 // constant bank, so the sample code needs more registers than in the single-molecule
 // kernel: 512 threads (16 warps, 128 registers) keep it free of spills, 640 threads (20
 // warps, 96 registers) trade a few spills for more warps.
-template <int PREC, int U, int MAXT>
+// JOIN: the molecules' tables carry the sample-space join index (built with U = 4 only).
+template <int PREC, int U, int MAXT, bool JOIN>
 __global__ void __launch_bounds__(MAXT) eloc_batch_kernel(const __grid_constant__ BatchParams bp) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ MolParams mp;
@@ -125,16 +126,16 @@ __global__ void __launch_bounds__(MAXT) eloc_batch_kernel(const __grid_constant_
                     const long long s = r0 + static_cast<long long>(q);
                     const int c = static_cast<int>(it - q * C);
                     if (mp.ep.lean)
-                        run_sample<PREC, U, true, 1, false>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));
+                        run_sample<PREC, U, true, 1, JOIN>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));
                     else
-                        run_sample<PREC, U, true, 0, false>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));
+                        run_sample<PREC, U, true, 0, JOIN>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));
                 }
             }
         }
     }
 }
 
-size_t batch_warp_bytes(const SysParams& sp, bool lean) { return main_warp_bytes(sp, true, lean); }
+size_t batch_warp_bytes(const SysParams& sp, bool lean, bool join) { return main_warp_bytes(sp, true, lean, join); }
 
 cudaError_t launch_build_batch(const MolParams* mols, const MolWork* work, const long long* key_off,
                                int n_mol, long long n_keys, cudaStream_t s) {
@@ -155,33 +156,37 @@ cudaError_t launch_reduce_batch(const MolParams* mols, const MolWork* work, int 
 }
 
 template <int PREC>
-static const void* batch_kernel_ptr(int unroll, int warps) {
-    if (warps > 16) return unroll == 2 ? (const void*)eloc_batch_kernel<PREC, 2, 640> : (const void*)eloc_batch_kernel<PREC, 4, 640>;
-    return unroll == 2 ? (const void*)eloc_batch_kernel<PREC, 2, 512> : (const void*)eloc_batch_kernel<PREC, 4, 512>;
+static const void* batch_kernel_ptr(int unroll, int warps, bool join) {
+    if (join) return warps > 16 ? (const void*)eloc_batch_kernel<PREC, 4, 640, true> : (const void*)eloc_batch_kernel<PREC, 4, 512, true>;
+    if (warps > 16) return unroll == 2 ? (const void*)eloc_batch_kernel<PREC, 2, 640, false> : (const void*)eloc_batch_kernel<PREC, 4, 640, false>;
+    return unroll == 2 ? (const void*)eloc_batch_kernel<PREC, 2, 512, false> : (const void*)eloc_batch_kernel<PREC, 4, 512, false>;
 }
 
-template <int PREC, int U>
+template <int PREC, int U, bool JOIN>
 static void launch_batch_u(const BatchParams& bp, int grid, int warps, size_t smem, cudaStream_t s) {
     const dim3 g(grid), b(32 * warps);
-    if (warps > 16) eloc_batch_kernel<PREC, U, 640><<<g, b, smem, s>>>(bp);
-    else eloc_batch_kernel<PREC, U, 512><<<g, b, smem, s>>>(bp);
+    if (warps > 16) eloc_batch_kernel<PREC, U, 640, JOIN><<<g, b, smem, s>>>(bp);
+    else eloc_batch_kernel<PREC, U, 512, JOIN><<<g, b, smem, s>>>(bp);
 }
 
 cudaError_t launch_eloc_batch(const BatchParams& bp, int precision, int unroll, int grid, int warps,
-                              size_t smem, cudaStream_t s) {
+                              size_t smem, cudaStream_t s, bool join) {
     if (precision == QC_FP64) {
-        if (unroll == 2) launch_batch_u<QC_FP64, 2>(bp, grid, warps, smem, s);
-        else launch_batch_u<QC_FP64, 4>(bp, grid, warps, smem, s);
+        if (join) launch_batch_u<QC_FP64, 4, true>(bp, grid, warps, smem, s);
+        else if (unroll == 2) launch_batch_u<QC_FP64, 2, false>(bp, grid, warps, smem, s);
+        else launch_batch_u<QC_FP64, 4, false>(bp, grid, warps, smem, s);
     } else {
-        if (unroll == 2) launch_batch_u<QC_FP32_COMP, 2>(bp, grid, warps, smem, s);
-        else launch_batch_u<QC_FP32_COMP, 4>(bp, grid, warps, smem, s);
+        if (join) launch_batch_u<QC_FP32_COMP, 4, true>(bp, grid, warps, smem, s);
+        else if (unroll == 2) launch_batch_u<QC_FP32_COMP, 2, false>(bp, grid, warps, smem, s);
+        else launch_batch_u<QC_FP32_COMP, 4, false>(bp, grid, warps, smem, s);
     }
     return cudaGetLastError();
 }
 
-int max_active_batch(int precision, int unroll, int threads, size_t smem) {
+int max_active_batch(int precision, int unroll, int threads, size_t smem, bool join) {
     const int w = threads / 32;
-    const void* f = precision == QC_FP64 ? batch_kernel_ptr<QC_FP64>(unroll, w) : batch_kernel_ptr<QC_FP32_COMP>(unroll, w);
+    const void* f = precision == QC_FP64 ? batch_kernel_ptr<QC_FP64>(unroll, w, join)
+                                         : batch_kernel_ptr<QC_FP32_COMP>(unroll, w, join);
     int n = 0;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) == cudaSuccess ? n : 0;
 }
@@ -191,9 +196,11 @@ cudaError_t prepare_batch_kernels(size_t max_smem, size_t* dyn_limit) {
     cudaError_t e = cudaSuccess;
     size_t lim = max_smem;
     for (int prec = 0; prec < 2; ++prec)
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 8; ++k) {
             const int unroll = (k & 1) ? 4 : 2, w = (k & 2) ? 20 : 16;
-            const void* f = prec == QC_FP64 ? batch_kernel_ptr<QC_FP64>(unroll, w) : batch_kernel_ptr<QC_FP32_COMP>(unroll, w);
+            const bool join = (k & 4) != 0;
+            const void* f = prec == QC_FP64 ? batch_kernel_ptr<QC_FP64>(unroll, w, join)
+                                            : batch_kernel_ptr<QC_FP32_COMP>(unroll, w, join);
             cudaFuncAttributes a{};
             cudaError_t r = cudaFuncGetAttributes(&a, f);
             if (r != cudaSuccess) { e = r; continue; }

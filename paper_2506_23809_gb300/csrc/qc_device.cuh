@@ -232,13 +232,16 @@ __device__ __forceinline__ bool set_contains(const unsigned long long* __restric
 
 // Insert row r of the table: validation, filter bits, spin-string sets, bucket entry.  With
 // jkey (the sample-space join index), also the row's two set slots as sort keys -- jkey[r]
-// the alpha slot, jkey[n + r] the beta slot + set size -- and their group counts in jlen.
+// jbase + the alpha slot, jkey[n + r] jbase + set size + the beta slot (jsent for a row that
+// fails validation) -- their group counts in jlen[key], and with jval the row as the value
+// of both (a batch sorts every molecule's keys together, each with its own jbase).
 __device__ __forceinline__ void build_one(const TableParams& tp, int n_orb, int na, int nb,
                                           const unsigned long long* __restrict__ T,
                                           unsigned long long* slots, uint32_t* filter,
                                           unsigned long long* aset, unsigned long long* bset,
                                           Counters* ctr, long long r, unsigned* jkey = nullptr,
-                                          unsigned* jlen = nullptr) {
+                                          unsigned* jlen = nullptr, unsigned jbase = 0u, unsigned jsent = 0u,
+                                          unsigned* jval = nullptr) {
     const ulonglong2 key = tp.keys[r];
     unsigned flags = 0;
     if (r > 0) {
@@ -286,11 +289,15 @@ __device__ __forceinline__ void build_one(const TableParams& tp, int n_orb, int 
         const unsigned size = tp.set_mask + 1u;
         if (slot_a == kNoSlot || slot_b == kNoSlot) flags |= QC_FLAG_TABLE_FULL;
         const bool ok = (flags & QC_FLAG_NELEC) == 0u && slot_a != kNoSlot && slot_b != kNoSlot;
-        jkey[r] = ok ? slot_a : 2u * size;
-        jkey[tp.n + r] = ok ? size + slot_b : 2u * size;
+        jkey[r] = ok ? jbase + slot_a : jsent;
+        jkey[tp.n + r] = ok ? jbase + size + slot_b : jsent;
+        if (jval != nullptr) {
+            jval[r] = static_cast<unsigned>(r);
+            jval[tp.n + r] = static_cast<unsigned>(r);
+        }
         if (ok) {
-            atomicAdd(jlen + slot_a, 1u);
-            atomicAdd(jlen + size + slot_b, 1u);
+            atomicAdd(jlen + jbase + slot_a, 1u);
+            atomicAdd(jlen + jbase + size + slot_b, 1u);
         }
     }
     const unsigned fp = static_cast<unsigned>(h);

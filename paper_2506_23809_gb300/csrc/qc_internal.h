@@ -127,6 +127,12 @@ struct MolWork {  // writable workspace of one molecule of a batch
     Counters* ctr;
     double* part;  // nblk x 4 doubles
     void* sum;     // qc_eloc_summary (device)
+    // sample-space join (null jkey: none): this molecule's 2n sort keys and values, the
+    // batch's group sizes, the molecule's first slot key and the batch's sentinel key
+    unsigned* jkey;
+    unsigned* jval;
+    unsigned* jlen;
+    unsigned jbase, jsent;
     int nblk;      // reduction blocks: the single-molecule path's count, so results match it bitwise
     int pad;
 };
@@ -172,11 +178,11 @@ int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t s
 cudaError_t launch_build_batch(const MolParams* mols, const MolWork* work, const long long* key_off,
                                int n_mol, long long n_keys, cudaStream_t s);
 cudaError_t launch_eloc_batch(const BatchParams& bp, int precision, int unroll, int grid, int warps,
-                              size_t smem, cudaStream_t s);
+                              size_t smem, cudaStream_t s, bool join = false);
 cudaError_t launch_reduce_batch(const MolParams* mols, const MolWork* work, int n_mol, int max_blocks,
                                 cudaStream_t s);
-int max_active_batch(int precision, int unroll, int threads, size_t smem);
-size_t batch_warp_bytes(const SysParams& sp, bool lean);
+int max_active_batch(int precision, int unroll, int threads, size_t smem, bool join = false);
+size_t batch_warp_bytes(const SysParams& sp, bool lean, bool join = false);
 cudaError_t prepare_batch_kernels(size_t max_smem, size_t* dyn_limit);
 cudaError_t prepare_kernels(size_t max_smem);
 size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw, bool lean = false, bool join = false);
@@ -187,6 +193,12 @@ int reduce_blocks(long long n);
 // jkey[0, 2n) slot keys (alpha rows, then beta rows offset by the set size), jlen counts
 size_t join_workspace_bytes(long long n, unsigned set_size);
 cudaError_t launch_join_index(const TableParams& tp, unsigned set_size, void* ws, unsigned* jkey,
+                              unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s);
+// a batch's join index: m sort items (every molecule's 2n keys, values written by K0),
+// n_slots group sizes (slot_base[M] = n_slots, the sentinel key); entries in one gent array
+size_t join_batch_workspace_bytes(long long m, unsigned long long n_slots);
+cudaError_t launch_join_batch(const MolParams* mols, const unsigned* slot_base, int n_mol, long long m,
+                              unsigned long long n_slots, void* ws, unsigned* jkey, unsigned* jval,
                               unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s);
 // in-place exclusive prefix sum of n u32 (qc_dedup.cu); sums: (n / 4096 + 2) u32 of scratch
 cudaError_t exclusive_scan_u32(unsigned* a, long long n, unsigned* sums, cudaStream_t s);

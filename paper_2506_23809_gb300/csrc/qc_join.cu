@@ -46,11 +46,12 @@ struct JLayout {
     size_t key1, val0, val1, table, sums, total;
 };
 
-JLayout jlayout(long long n, unsigned set_size) {
-    const long long m = 2 * std::max<long long>(n, 1);
+// sort space for m items and n_slots group sizes
+JLayout jlayout(long long m, unsigned long long n_slots) {
+    m = std::max<long long>(m, 2);
     const long long tiles = (m + kJTile - 1) / kJTile;
     const long long table_n = static_cast<long long>(kJBins) * tiles;
-    const long long scan_n = std::max<long long>(table_n, 2LL * set_size);
+    const long long scan_n = std::max<long long>(table_n, static_cast<long long>(n_slots));
     JLayout L{};
     size_t off = 0;
     L.key1 = off; off = align256(off + static_cast<size_t>(m) * 4);
@@ -143,38 +144,56 @@ __global__ void __launch_bounds__(256) join_gather_kernel(const ulonglong2* __re
     }
 }
 
+// A batch's entries: the molecule from the sorted key (slot_base: each molecule's first slot
+// key, then the sentinel), the spin from the key's place in the molecule's two sets.
+__global__ void __launch_bounds__(256) join_gather_batch_kernel(const qc::MolParams* __restrict__ mols,
+                                                                const unsigned* __restrict__ slot_base, int n_mol,
+                                                                const unsigned* __restrict__ skey,
+                                                                const unsigned* __restrict__ srow, long long m,
+                                                                ulonglong2* __restrict__ gent) {
+    const unsigned sentinel = slot_base[n_mol];
+    for (long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < m;
+         p += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const unsigned k = skey[p];
+        if (k >= sentinel) continue;
+        int lo = 0, hi = n_mol;  // largest molecule with slot_base <= k
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (slot_base[mid] <= k) lo = mid; else hi = mid;
+        }
+        const unsigned size = (slot_base[lo + 1] - slot_base[lo]) / 2u;
+        const unsigned row = srow[p];
+        gent[p] = make_ulonglong2(spin_string(mols[lo].tp.keys[row], k - slot_base[lo] < size ? 1 : 0), row);
+    }
+}
+
 int bits_for(unsigned long long v) {  // bits to hold 0..v
     int b = 1;
     while (b < 64 && (v >> b) != 0ULL) ++b;
     return b;
 }
 
-}  // namespace
-
-size_t qc::join_workspace_bytes(long long n, unsigned set_size) { return jlayout(n, set_size).total; }
-
-cudaError_t qc::launch_join_index(const TableParams& tp, unsigned set_size, void* ws, unsigned* jkey,
-                                  unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s) {
-    const long long n = tp.n;
-    if (n <= 0) return cudaSuccess;
-    const long long m = 2 * n;
-    const JLayout L = jlayout(n, set_size);
+// Group starts (exclusive prefix of the n_slots sizes) and the stable sort of m (key, value)
+// items by key, values from val_in or (val_in null) the item index modulo n_half.  Returns
+// the sorted arrays (in the workspace or in jkey, which the sort uses as a buffer).
+cudaError_t join_sort(unsigned* jkey, const unsigned* val_in, long long n_half, long long m,
+                      unsigned long long n_slots, unsigned* jlen, unsigned* jstart, void* ws,
+                      const unsigned** skey, const unsigned** sval, cudaStream_t s) {
+    const JLayout L = jlayout(m, n_slots);
     unsigned char* W = static_cast<unsigned char*>(ws);
     unsigned* key1 = reinterpret_cast<unsigned*>(W + L.key1);
     unsigned* val0 = reinterpret_cast<unsigned*>(W + L.val0);
     unsigned* val1 = reinterpret_cast<unsigned*>(W + L.val1);
     unsigned* table = reinterpret_cast<unsigned*>(W + L.table);
     unsigned* sums = reinterpret_cast<unsigned*>(W + L.sums);
-    // group starts
-    cudaError_t e = cudaMemcpyAsync(jstart, jlen, 2 * static_cast<size_t>(set_size) * sizeof(unsigned),
-                                    cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = qc::exclusive_scan_u32(jstart, 2LL * set_size, sums, s);
-    // stable LSD sort of (slot key, row) over the bits of the largest key (the sentinel 2 * size)
-    const int passes = (bits_for(2ULL * set_size) + kJBits - 1) / kJBits;
+    cudaError_t e = cudaMemcpyAsync(jstart, jlen, n_slots * sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = qc::exclusive_scan_u32(jstart, static_cast<long long>(n_slots), sums, s);
+    // LSD passes over the bits of the largest key (the sentinel n_slots)
+    const int passes = (bits_for(n_slots) + kJBits - 1) / kJBits;
     const long long tiles = (m + kJTile - 1) / kJTile;
     const unsigned blocks = static_cast<unsigned>((tiles + kJWarps - 1) / kJWarps);
     const unsigned* src_k = jkey;
-    const unsigned* src_v = nullptr;
+    const unsigned* src_v = val_in;
     unsigned* dk[2] = {key1, jkey};
     unsigned* dv[2] = {val0, val1};
     for (int p = 0; p < passes && e == cudaSuccess; ++p) {
@@ -182,16 +201,50 @@ cudaError_t qc::launch_join_index(const TableParams& tp, unsigned set_size, void
         e = cudaGetLastError();
         if (e == cudaSuccess) e = qc::exclusive_scan_u32(table, static_cast<long long>(kJBins) * tiles, sums, s);
         if (e == cudaSuccess) {
-            join_scatter_kernel<<<blocks, 32 * kJWarps, 0, s>>>(src_k, src_v, n, dk[p & 1], dv[p & 1], m,
+            join_scatter_kernel<<<blocks, 32 * kJWarps, 0, s>>>(src_k, src_v, n_half, dk[p & 1], dv[p & 1], m,
                                                                p * kJBits, tiles, table);
             e = cudaGetLastError();
         }
         src_k = dk[p & 1];
         src_v = dv[p & 1];
     }
+    *skey = src_k;
+    *sval = src_v;
+    return e;
+}
+
+}  // namespace
+
+size_t qc::join_workspace_bytes(long long n, unsigned set_size) { return jlayout(2 * n, 2ULL * set_size).total; }
+
+cudaError_t qc::launch_join_index(const TableParams& tp, unsigned set_size, void* ws, unsigned* jkey,
+                                  unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s) {
+    const long long n = tp.n;
+    if (n <= 0) return cudaSuccess;
+    const long long m = 2 * n;
+    const unsigned* skey = nullptr;
+    const unsigned* sval = nullptr;
+    cudaError_t e = join_sort(jkey, nullptr, n, m, 2ULL * set_size, jlen, jstart, ws, &skey, &sval, s);
     if (e == cudaSuccess) {
         const unsigned gblocks = static_cast<unsigned>(std::min<long long>((m + 255) / 256, 8192));
-        join_gather_kernel<<<gblocks, 256, 0, s>>>(tp.keys, src_k, src_v, m, set_size, gent);
+        join_gather_kernel<<<gblocks, 256, 0, s>>>(tp.keys, skey, sval, m, set_size, gent);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+size_t qc::join_batch_workspace_bytes(long long m, unsigned long long n_slots) { return jlayout(m, n_slots).total; }
+
+cudaError_t qc::launch_join_batch(const MolParams* mols, const unsigned* slot_base, int n_mol, long long m,
+                                  unsigned long long n_slots, void* ws, unsigned* jkey, unsigned* jval,
+                                  unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    const unsigned* skey = nullptr;
+    const unsigned* sval = nullptr;
+    cudaError_t e = join_sort(jkey, jval, 0, m, n_slots, jlen, jstart, ws, &skey, &sval, s);
+    if (e == cudaSuccess) {
+        const unsigned gblocks = static_cast<unsigned>(std::min<long long>((m + 255) / 256, 8192));
+        join_gather_batch_kernel<<<gblocks, 256, 0, s>>>(mols, slot_base, n_mol, skey, sval, m, gent);
         e = cudaGetLastError();
     }
     return e;

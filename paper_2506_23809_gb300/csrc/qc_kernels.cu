@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(256) build_table_kernel(TableParams tp, int n_
                                                           unsigned long long* bset, Counters* ctr,
                                                           unsigned* jkey, unsigned* jlen) {
     const long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (r < tp.n) build_one(tp, n_orb, na, nb, T, slots, filter, aset, bset, ctr, r, jkey, jlen);
+    if (r < tp.n) build_one(tp, n_orb, na, nb, T, slots, filter, aset, bset, ctr, r, jkey, jlen, 0u,
+                            2u * (tp.set_mask + 1u));
 }
 
 template <int PREC, int U, bool FILTER, int LEAN, bool JOIN>

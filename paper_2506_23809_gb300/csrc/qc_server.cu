@@ -119,7 +119,7 @@ struct qc_server {
     std::map<uint64_t, std::unique_ptr<Resident>> residents;  // by molecule key
     uint64_t next_ticket = 1;
     int active = 0;                      // admitted and not finished
-    long long quantum = 10000000000LL;   // enumerated pairs per wave (0: no slicing)
+    long long quantum = 1000000000000LL;  // enumerated pairs per wave (0: no slicing)
     int oldest_pct = 50;                 // share of a wave guaranteed to the oldest request
     bool last_wave_sliced = false;       // the last wave ran a slice of a long request
     bool stop = false;

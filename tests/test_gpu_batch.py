@@ -41,14 +41,17 @@ def _dev(B, keys, counts, psi):
     return (B.keys_to_tensor(keys), torch.from_numpy(counts).cuda(), torch.from_numpy(psi).cuda())
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_batch_equals_single_and_oracle(B, orc, prec):
+@pytest.mark.parametrize("prec,join", [(0, 1), (1, 1), (0, 2), (1, 2)], ids=["fp64", "fp32c", "fp64_join", "fp32c_join"])
+def test_batch_equals_single_and_oracle(B, orc, prec, join):
+    """join 2: every molecule takes the sample-space join, in the batch (one shared index)
+    as alone; join 1: none does."""
     import torch
     mols = _molecules()
     handles, singles, ins, outs = [], [], [], []
     try:
         for n, ne, ints, keys, counts, psi in mols:
             h = B.qc_eloc_create(ints.h, ints.eri, 0.0, n, ne, prec)
+            B.qc_eloc_set_option(h, B.QC_OPT_JOIN, join)
             handles.append(h)
             kt, ct, pt = _dev(B, keys, counts, psi)
             e, _ = B.qc_eloc_eval(h, kt, ct, pt)
@@ -62,6 +65,8 @@ def test_batch_equals_single_and_oracle(B, orc, prec):
             B.qc_batch_eval(batch)
             sums = B.qc_batch_summaries(batch)
             first = [o.cpu().numpy().copy() for o in outs]
+            if join == 2:
+                assert all(B.qc_eloc_last_config(h)["kernel"] in (4, 5) for h in handles)
             for m, (e1, s1) in enumerate(singles):
                 assert np.array_equal(first[m].view(np.uint64), e1.view(np.uint64)), f"molecule {m}"
                 assert sums[m]["n_hits"] == s1["n_hits"] and sums[m]["n_pairs"] == s1["n_pairs"]
