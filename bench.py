@@ -94,6 +94,18 @@ def _plain_launches(cfg, n_table):
     return n
 
 
+def _batched_launches(specs):
+    """Kernels of one batched step: the batch build, the batch kernel and two reduction
+    passes, and for the molecules that take the join (16384 rows up) one shared index: a
+    3-kernel scan, per 11-bit radix pass a histogram, a 3-kernel scan and a scatter, and the
+    gather."""
+    n = 4
+    slots = sum(2 * (1 << max(0, (2 * sp["n_u"] - 1).bit_length())) for sp in specs if sp["n_u"] >= 16384)
+    if slots:
+        n += 3 + 5 * (-(-slots.bit_length() // 11)) + 1
+    return n
+
+
 def _source_hash():
     h = hashlib.sha256()
     for f in ("qc_kernels.cu", "qc_device.cuh", "qc_internal.h"):
@@ -531,7 +543,8 @@ def run_batched(args):
                        "autotuned": best, "launch": cfg},
             "ms": {"plain_per_molecule_launches": t_plain, "batched_eager": t_eager,
                    "batched_eager_autotuned": t_tuned, "batched_graph_autotuned": t_graph},
-            "speedup_vs_plain": t_plain / t_graph, "max_rel_diff_vs_plain": diff}
+            "speedup_vs_plain": t_plain / t_graph, "max_rel_diff_vs_plain": diff,
+            "gpu_launches": _batched_launches(specs) * args.steps}
     print(json.dumps(line), flush=True)
     return 0
 
