@@ -163,6 +163,44 @@ def test_join_deterministic(B):
     assert np.array_equal(r[0].view(np.uint64), r[1].view(np.uint64))
 
 
+@pytest.mark.parametrize("join", [1, 2], ids=["enumeration", "join"])
+def test_join_caller_table_and_invalid_row(B, orc, join):
+    """Sample-space mode against a caller's table: samples half in the table and half not
+    (a sample whose spin strings have no group in the table), with the join forced on and
+    off; then a table row with a wrong electron count, which the join index leaves out of
+    every group -- the other samples' connected sets and E_loc are unchanged."""
+    K = 26
+    ints = I.make_integrals(K, 52, 3101)
+    allk = I.rank_weighted_samples(K, 7, 7, 5000, seed=3102)
+    rng = np.random.default_rng(3103)
+    in_tab = np.zeros(len(allk), bool)
+    in_tab[rng.choice(len(allk), 3500, replace=False)] = True
+    tkeys, tpsi = allk[in_tab], I.lognormal_psi(int(in_tab.sum()), 3104)
+    pick = np.sort(np.concatenate([np.flatnonzero(~in_tab)[:700], np.flatnonzero(in_tab)[:700]]))
+    skeys = allk[pick]
+    spsi = I.lognormal_psi(len(skeys), 3105)
+    counts = I.zipf_counts(len(skeys), 50 * len(skeys), 3106)
+    g = run_gpu(B, ints, 52, 14, skeys, counts, spsi, table=(tkeys, tpsi), opts={10: join})
+    assert g["cfg"]["kernel"] in ((2, 3) if join == 1 else (4, 5))
+    want, det = orc.eloc(ints.h, ints.eri, 0.0, 52, skeys, spsi, tkeys, tpsi, details=True)
+    assert_sets_equal(g, det)
+    assert_eloc_close(g["eloc"], want)
+    assert g["summary"]["status"] == 0
+    # a table row with one electron too many (an empty orbital filled): flagged, in no group
+    bad = tkeys.copy()
+    r = 1234
+    occ = int(bad[r, 0])
+    free = next(b for b in range(52) if not (occ >> b) & 1)
+    bad[r, 0] = np.uint64(occ | (1 << free))
+    order = np.lexsort((bad[:, 0], bad[:, 1]))
+    bad, bpsi = bad[order], tpsi[order]
+    g2 = run_gpu(B, ints, 52, 14, skeys, counts, spsi, table=(bad, bpsi), opts={10: join})
+    assert g2["summary"]["status"] == -4
+    want2, det2 = orc.eloc(ints.h, ints.eri, 0.0, 52, skeys, spsi, bad, bpsi, details=True)
+    assert_sets_equal(g2, det2)
+    assert_eloc_close(g2["eloc"], want2)
+
+
 def test_exact_ground_state_constant_eloc(B, orc):
     """N=8, 4 electrons, psi = exact ground state of the sector: E_loc = E0 everywhere
     psi is not negligible (FP64 path)."""
