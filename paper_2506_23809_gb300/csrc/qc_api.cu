@@ -119,7 +119,8 @@ qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int 
     for (int k = 0; k < K; ++k)
         for (int l = 0; l < K; ++l) {
             J[k * K + l] = eri[((static_cast<size_t>(k) * K + k) * K + l) * K + l];  // (kk|ll)
-            X[k * K + l] = eri[((static_cast<size_t>(k) * K + l) * K + l) * K + k];  // (kl|lk)
+            // same-spin pair term of the diagonal: (kk|ll) - (kl|lk)
+            X[k * K + l] = J[k * K + l] - eri[((static_cast<size_t>(k) * K + l) * K + l) * K + k];
         }
     const size_t K3 = KK * K;
     std::vector<double> Jt(K3), Xt(K3);

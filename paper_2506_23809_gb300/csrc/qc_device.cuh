@@ -526,6 +526,15 @@ __device__ __forceinline__ unsigned decode(unsigned code, const SysParams& sp,
     return i | (a << 8) | (j << 16) | (b << 24);
 }
 
+// x or -x, by flipping the sign bit with an integer operation (the FP64 pipe, 1/64 of the
+// FP32 rate on this GPU, is kept for the arithmetic that needs it)
+__device__ __forceinline__ double with_sign(double v, bool neg) {
+    return __hiloint2double(__double2hiint(v) ^ (neg ? static_cast<int>(0x80000000u) : 0), __double2loint(v));
+}
+__device__ __forceinline__ float with_sign(float v, bool neg) {
+    return __int_as_float(__float_as_int(v) ^ (neg ? static_cast<int>(0x80000000u) : 0));
+}
+
 // Stage 2 -- single i -> a (Slater-Condon): h_ai + sum_{k occ} (ai|kk) - sum_{k occ, same
 // spin} (ak|ki), phase <x'| a+_a a_i |x> = (-1)^{P(i) + P(a) + [i < a]}, P = occupied below
 // (read from the prefix-parity mask px).
@@ -555,7 +564,7 @@ __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 px, con
         for (q = 0; q + 1 < os; q += 2) { g0 += xt[occS[q]]; g1 += xt[occS[q + 1]]; }
         if (q < os) g0 += xt[occS[q]];
         const double f = ((f0 + f1) + (f2 + f3)) - (g0 + g1);
-        h64 = neg ? -f : f;
+        h64 = with_sign(f, neg);
     } else {
         float f0 = sp.h32[ka * K + ki], f1 = 0.f, f2 = 0.f, f3 = 0.f;
         const float* jt = sp.Jt32 + rowk;
@@ -571,7 +580,7 @@ __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 px, con
         for (q = 0; q + 1 < os; q += 2) { g0 += xt[occS[q]]; g1 += xt[occS[q + 1]]; }
         if (q < os) g0 += xt[occS[q]];
         const float f = ((f0 + f1) + (f2 + f3)) - (g0 + g1);
-        h32 = neg ? -f : f;
+        h32 = with_sign(f, neg);
     }
     sneg = neg;
 }
@@ -592,11 +601,11 @@ __device__ __forceinline__ void double_element(unsigned orbs, ulonglong2 px, con
     if (PREC == QC_FP64) {
         double e = sp.eri[d];
         if (same) e -= sp.eri[((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki];  // (aj|bi)
-        h64 = neg ? -e : e;
+        h64 = with_sign(e, neg);
     } else {
         float e = sp.eri32[d];
         if (same) e -= sp.eri32[((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki];
-        h32 = neg ? -e : e;
+        h32 = with_sign(e, neg);
     }
     // exported convention sorts the emptied and the filled pair
     sneg = neg != ((((i > j) ? 1 : 0) + ((a > b) ? 1 : 0)) & 1);
@@ -651,26 +660,34 @@ __device__ __forceinline__ bool sample_setup(const SysParams& sp, ulonglong2 x, 
     As = A;
     Bs = B;
     __syncwarp();
-    // diagonal: sum_p h_pp + 1/2 sum_{p,q occ} [(pp|qq) - d(sp,sq) (pq|qp)]  (FP64)
+    // diagonal: sum_p h_pp + 1/2 sum_{p,q occ} [(pp|qq) - d(sp,sq) (pq|qp)]  (FP64).  The
+    // n_occ^2 ordered pairs of occupied spatial orbitals (positions 0 .. oa - 1 alpha, then
+    // beta) are spread over the 32 lanes, one load and one add each: X holds the same-spin
+    // term (kk|ll) - (kl|lk), J the other (for p = q the same-spin term is 0)
     const int K = sp.K;
-    double ed = 0.0;
-    for (int idx = lane; idx < sp.oa + sp.ob; idx += 32) {
-        const bool isA = idx < sp.oa;
-        const int k = isA ? occA[idx] : occB[idx - sp.oa];
-        double sj = 0.0, sx = 0.0;
-        for (int q = 0; q < sp.oa; ++q) {
-            const int l = occA[q];
-            sj += sp.J[k * K + l];
-            if (isA) sx += sp.X[k * K + l];
-        }
-        for (int q = 0; q < sp.ob; ++q) {
-            const int l = occB[q];
-            sj += sp.J[k * K + l];
-            if (!isA) sx += sp.X[k * K + l];
-        }
-        ed += sp.h[k * K + k] + 0.5 * (sj - sx);
+    const int no = sp.oa + sp.ob;
+    double e0 = 0.0, e1 = 0.0;
+    for (int p = lane; p < no; p += 32) {
+        const int k = p < sp.oa ? occA[p] : occB[p - sp.oa];
+        e1 += sp.h[k * K + k];
     }
-    ediag = warp_sum(ed) + sp.e_core;
+    if (no > 0) {
+        const int q32 = 32 / no, r32 = 32 - q32 * no;
+        int p = lane / no, r = lane - (lane / no) * no;
+        for (int t = lane; t < no * no; t += 32) {
+            const bool pa = p < sp.oa, ra = r < sp.oa;
+            const int k = pa ? occA[p] : occB[p - sp.oa];
+            const int l = ra ? occA[r] : occB[r - sp.oa];
+            e0 += (pa == ra ? sp.X : sp.J)[k * K + l];
+            r += r32;
+            p += q32;
+            if (r >= no) {
+                r -= no;
+                ++p;
+            }
+        }
+    }
+    ediag = warp_sum(fma(0.5, e0, e1)) + sp.e_core;
     return true;
 }
 

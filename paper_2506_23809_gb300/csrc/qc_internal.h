@@ -28,7 +28,7 @@ struct SysParams {
     const float* h32;    // K*K  FP32 (FP32 precision)
     const float* eri32;  // K^4  FP32 (FP32 precision)
     const double* J;     // K*K  (kk|ll)  FP64
-    const double* X;     // K*K  (kl|lk)  FP64
+    const double* X;     // K*K  (kk|ll) - (kl|lk)  FP64 (the diagonal's same-spin pair term)
     const double* Jt;    // K^3  [a][i][k] = (ai|kk)  FP64 (single excitations)
     const double* Xt;    // K^3  [a][i][k] = (ak|ki)  FP64
     const float* Jt32;   // K^3  FP32 copies (FP32 precision)

@@ -70,7 +70,8 @@ __global__ void static_prep_kernel(const double* __restrict__ eri, int K, double
         Xt[t] = eri[((static_cast<size_t>(p) * K + k) * K + k) * K + i];  // (pk|ki)
         if (p == 0) {
             J[i * K + k] = eri[((static_cast<size_t>(i) * K + i) * K + k) * K + k];  // (ii|kk)
-            X[i * K + k] = eri[((static_cast<size_t>(i) * K + k) * K + k) * K + i];  // (ik|ki)
+            // same-spin pair term of the diagonal: (ii|kk) - (ik|ki)
+            X[i * K + k] = J[i * K + k] - eri[((static_cast<size_t>(i) * K + k) * K + k) * K + i];
         }
     }
     if (blockIdx.x == 0 && threadIdx.x < 128) {
