@@ -130,6 +130,18 @@ qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int 
                 Jt[(static_cast<size_t>(p) * K + i) * K + k] = eri[((static_cast<size_t>(p) * K + i) * K + k) * K + k];  // (pi|kk)
                 Xt[(static_cast<size_t>(p) * K + i) * K + k] = eri[((static_cast<size_t>(p) * K + k) * K + k) * K + i];  // (pk|ki)
             }
+    // singles against the Aufbau reference (spatial orbitals below na / nb occupied)
+    std::vector<double> Fref(2 * KK);
+    for (int s = 0; s < 2; ++s)
+        for (int a = 0; a < K; ++a)
+            for (int i = 0; i < K; ++i) {
+                double f = h[a * K + i];
+                const size_t row = (static_cast<size_t>(a) * K + i) * K;
+                for (int k = 0; k < H->na; ++k) f += Jt[row + k];
+                for (int k = 0; k < H->nb; ++k) f += Jt[row + k];
+                for (int k = 0; k < (s == 0 ? H->na : H->nb); ++k) f -= Xt[row + k];
+                Fref[(static_cast<size_t>(s) * K + a) * K + i] = f;
+            }
     std::vector<unsigned long long> T(128);
     unsigned long long seed = 0x51c0de5eedULL;
     for (auto& t : T) t = splitmix64(seed);
@@ -151,6 +163,8 @@ qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int 
         QC_TRY(cudaMemcpy(H->d_Jt, Jt.data(), K3 * sizeof(double), cudaMemcpyHostToDevice), "copy Jt");
         QC_TRY(cudaMalloc(&H->d_Xt, K3 * sizeof(double)), "cudaMalloc Xt");
         QC_TRY(cudaMemcpy(H->d_Xt, Xt.data(), K3 * sizeof(double), cudaMemcpyHostToDevice), "copy Xt");
+        QC_TRY(cudaMalloc(&H->d_Fref, 2 * KK * sizeof(double)), "cudaMalloc Fref");
+        QC_TRY(cudaMemcpy(H->d_Fref, Fref.data(), 2 * KK * sizeof(double), cudaMemcpyHostToDevice), "copy Fref");
         QC_TRY(cudaMalloc(&H->d_eri, K4 * sizeof(double)), "cudaMalloc eri");
         QC_TRY(cudaMemcpy(H->d_eri, eri, K4 * sizeof(double), cudaMemcpyHostToDevice), "copy eri");
     } else {
@@ -209,6 +223,9 @@ qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int 
     sp.X = H->d_X;
     sp.Jt = H->d_Jt;
     sp.Xt = H->d_Xt;
+    sp.Fref = H->d_Fref;
+    sp.refA = H->na >= 64 ? ~0ULL : (1ULL << H->na) - 1ULL;
+    sp.refB = H->nb >= 64 ? ~0ULL : (1ULL << H->nb) - 1ULL;
     sp.Jt32 = H->d_Jt32;
     sp.Xt32 = H->d_Xt32;
     *out = H;
@@ -223,6 +240,7 @@ qc_status qc_eloc_destroy(qc_eloc* H) {
     free_dev(H->d_X);
     free_dev(H->d_Jt);
     free_dev(H->d_Xt);
+    free_dev(H->d_Fref);
     free_dev(H->d_Jt32);
     free_dev(H->d_Xt32);
     free_dev(H->d_h32);

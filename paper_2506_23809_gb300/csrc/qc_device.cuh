@@ -50,6 +50,21 @@ __device__ __forceinline__ ulonglong2 prefix_parity(ulonglong2 x) {
     return p;
 }
 
+// Spatial occupation string of one spin (0 alpha, 1 beta) of an interleaved key: bit k is
+// spin orbital 2k + spin.
+__device__ __forceinline__ unsigned long long gather_even(unsigned long long w) {
+    w &= 0x5555555555555555ULL;
+    w = (w | (w >> 1)) & 0x3333333333333333ULL;
+    w = (w | (w >> 2)) & 0x0F0F0F0F0F0F0F0FULL;
+    w = (w | (w >> 4)) & 0x00FF00FF00FF00FFULL;
+    w = (w | (w >> 8)) & 0x0000FFFF0000FFFFULL;
+    w = (w | (w >> 16)) & 0x00000000FFFFFFFFULL;
+    return w;
+}
+__device__ __forceinline__ unsigned long long spin_string(ulonglong2 k, int spin) {
+    return gather_even(k.x >> spin) | (gather_even(k.y >> spin) << 32);
+}
+
 __device__ __forceinline__ int pbit(ulonglong2 p, int k) {
     const unsigned long long w = (k < 64) ? p.x : p.y;
     return static_cast<int>((w >> (k & 63)) & 1ULL);
@@ -540,7 +555,8 @@ __device__ __forceinline__ float with_sign(float v, bool neg) {
 // (read from the prefix-parity mask px).
 template <int PREC>
 __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 px, const SysParams& sp,
-                                               const unsigned char* __restrict__ wl, double& h64,
+                                               const unsigned char* __restrict__ wl,
+                                               const unsigned long long* __restrict__ dref, double& h64,
                                                float& h32, bool& sneg) {
     const int i = orbs & 255u, a = (orbs >> 8) & 255u;
     const int K = sp.K, ki = i >> 1, ka = a >> 1, s = i & 1;
@@ -548,22 +564,51 @@ __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 px, con
     const unsigned char* occA = wl;
     const unsigned char* occB = wl + 128;
     const bool neg = (pbit(px, i) ^ pbit(px, a) ^ (i < a ? 1 : 0)) != 0;
-    // sum over the occupied orbitals of both spins, four independent partial sums
     if (PREC == QC_FP64) {
-        double f0 = sp.h[ka * K + ki], f1 = 0.0, f2 = 0.0, f3 = 0.0;
         const double* jt = sp.Jt + rowk;
         const double* xt = sp.Xt + rowk;
-        const unsigned char* occS = s == 0 ? occA : occB;
         const int os = s == 0 ? sp.oa : sp.ob;
-        int q = 0;
-        for (; q + 1 < sp.oa; q += 2) { f0 += jt[occA[q]]; f1 += jt[occA[q + 1]]; }
-        if (q < sp.oa) f0 += jt[occA[q]];
-        for (q = 0; q + 1 < sp.ob; q += 2) { f2 += jt[occB[q]]; f3 += jt[occB[q + 1]]; }
-        if (q < sp.ob) f2 += jt[occB[q]];
-        double g0 = 0.0, g1 = 0.0;
-        for (q = 0; q + 1 < os; q += 2) { g0 += xt[occS[q]]; g1 += xt[occS[q + 1]]; }
-        if (q < os) g0 += xt[occS[q]];
-        const double f = ((f0 + f1) + (f2 + f3)) - (g0 + g1);
+        // x differs from the reference determinant in a few orbitals (dref: the spatial
+        // orbitals x fills and empties against it, alpha then beta): start from the
+        // reference's sum and correct by those, when that is the shorter sum (the same for
+        // every lane of a batch: one sample)
+        unsigned long long aP = 0, aM = 0, bP = 0, bM = 0;
+        int nd = 1 << 30;
+        if (dref != nullptr) {
+            aP = dref[0];
+            aM = dref[1];
+            bP = dref[2];
+            bM = dref[3];
+            nd = __popcll(aP | bP) + __popcll(aM | bM) + __popcll(s ? bP : aP) + __popcll(s ? bM : aM);
+        }
+        double f;
+        if (nd < sp.oa + sp.ob + os) {
+            double f0 = sp.Fref[(static_cast<size_t>(s) * K + ka) * K + ki], f1 = 0.0, f2 = 0.0, f3 = 0.0;
+            for (unsigned long long m = aP | bP; m; m &= m - 1ULL) {
+                const int k = __ffsll(m) - 1;
+                f1 += ((aP >> k) & (bP >> k) & 1ULL) ? 2.0 * jt[k] : jt[k];
+            }
+            for (unsigned long long m = aM | bM; m; m &= m - 1ULL) {
+                const int k = __ffsll(m) - 1;
+                f2 -= ((aM >> k) & (bM >> k) & 1ULL) ? 2.0 * jt[k] : jt[k];
+            }
+            for (unsigned long long m = s ? bP : aP; m; m &= m - 1ULL) f3 -= xt[__ffsll(m) - 1];
+            for (unsigned long long m = s ? bM : aM; m; m &= m - 1ULL) f0 += xt[__ffsll(m) - 1];
+            f = (f0 + f3) + (f1 + f2);
+        } else {
+            // sum over the occupied orbitals of both spins, four independent partial sums
+            double f0 = sp.h[ka * K + ki], f1 = 0.0, f2 = 0.0, f3 = 0.0;
+            const unsigned char* occS = s == 0 ? occA : occB;
+            int q = 0;
+            for (; q + 1 < sp.oa; q += 2) { f0 += jt[occA[q]]; f1 += jt[occA[q + 1]]; }
+            if (q < sp.oa) f0 += jt[occA[q]];
+            for (q = 0; q + 1 < sp.ob; q += 2) { f2 += jt[occB[q]]; f3 += jt[occB[q + 1]]; }
+            if (q < sp.ob) f2 += jt[occB[q]];
+            double g0 = 0.0, g1 = 0.0;
+            for (q = 0; q + 1 < os; q += 2) { g0 += xt[occS[q]]; g1 += xt[occS[q + 1]]; }
+            if (q < os) g0 += xt[occS[q]];
+            f = ((f0 + f1) + (f2 + f3)) - (g0 + g1);
+        }
         h64 = with_sign(f, neg);
     } else {
         float f0 = sp.h32[ka * K + ki], f1 = 0.f, f2 = 0.f, f3 = 0.f;
@@ -819,11 +864,12 @@ constexpr int kCandCap = 160;  // >= 31 + 32 * 4 (the largest U with a single fl
 constexpr size_t kWarpQueues = 4 * kCandCap + 64 * 8;  // candidate queue + hit queue
 
 constexpr int kSingleCap = 64;  // join: the hit queue of scanned singles (uint2)
+constexpr size_t kOccBytes = 288;  // per warp: occupation lists (4 x 64 B), reference masks (32 B)
 __host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filter, bool lean = false,
                                                   bool join = false) {
     // hash lists (u32) and, for the two single lists, their compaction maps (u16)
     const size_t lists = filter ? 4 * list_words(sp, lean) + 2 * static_cast<size_t>(sp.nsa + sp.nsb) : 0;
-    return (256 + kWarpQueues + (join ? 8 * kSingleCap : 0) + lists + 15) / 16 * 16;
+    return (kOccBytes + kWarpQueues + (join ? 8 * kSingleCap : 0) + lists + 15) / 16 * 16;
 }
 
 
@@ -842,10 +888,13 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                                            const uint32_t* filt, int c = 0, int C = 1) {
     const unsigned long long* T64 = reinterpret_cast<const unsigned long long*>(smem + kOffT);
     const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
-    uint32_t* q = reinterpret_cast<uint32_t*>(wl + 256);
-    uint2* hq = reinterpret_cast<uint2*>(wl + 256 + 4 * kCandCap);
+    uint32_t* q = reinterpret_cast<uint32_t*>(wl + kOccBytes);
+    uint2* hq = reinterpret_cast<uint2*>(wl + kOccBytes + 4 * kCandCap);
     uint2* hs = hq + 64;  // join kernels only: scanned singles
-    uint32_t* H = reinterpret_cast<uint32_t*>(wl + 256 + kWarpQueues + (JOIN ? 8 * kSingleCap : 0));
+    uint32_t* H = reinterpret_cast<uint32_t*>(wl + kOccBytes + kWarpQueues + (JOIN ? 8 * kSingleCap : 0));
+    // the FP64 singles' differences against the reference determinant (set after set-up)
+    unsigned long long* dref = (PREC == QC_FP64 && sp.Fref != nullptr)
+                                   ? reinterpret_cast<unsigned long long*>(wl + 256) : nullptr;
     const bool lean = FILTER && (LEAN == 1 || (LEAN == 2 && ep.lean != 0));
     // list offsets inside H: 0 zero | SA | SB | PAo | PAv | PBo | PBv, or in the lean layout
     // 0 zero | SA | SB | occupied alpha | empty alpha | occupied beta | empty beta
@@ -868,6 +917,12 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     if (!sample_setup(sp, x, lane, wl, T64, hx, ediag, As, Bs, hxa)) {
         if (c == 0) invalid_sample(ep, s, lane);  // reported once, by the first chunk
         return;
+    }
+    if (dref != nullptr && lane == 0) {
+        dref[0] = As & ~sp.refA;
+        dref[1] = sp.refA & ~As;
+        dref[2] = Bs & ~sp.refB;
+        dref[3] = sp.refB & ~Bs;
     }
     const double2 psix = ep.psi[s];
     const float2 ip32 = inv_psi32(psix);
@@ -896,7 +951,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         if (v)
             verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc, [&](double& h64, float& h32, bool& sneg) {
                 if ((e.x >> 16) == 0xFFFFu)
-                    single_element<PREC>(e.x, prefix_parity(x), sp, wl, h64, h32, sneg);
+                    single_element<PREC>(e.x, prefix_parity(x), sp, wl, dref, h64, h32, sneg);
                 else
                     double_element<PREC>(e.x, prefix_parity(x), sp, h64, h32, sneg);
             });

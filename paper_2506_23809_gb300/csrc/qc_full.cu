@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(32 * kExpWarps, 4) eloc_export_kernel(const __
                             double h64 = 0.0;
                             float h32 = 0.f;
                             bool sneg = false;
-                            single_element<PREC>(orbs, px, sp, wl, h64, h32, sneg);
+                            single_element<PREC>(orbs, px, sp, wl, nullptr, h64, h32, sneg);
                             __stcs(out.elems + pos, PREC == QC_FP64 ? h64 : static_cast<double>(h32));
                         }
                     }

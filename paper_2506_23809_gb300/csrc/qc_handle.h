@@ -20,6 +20,7 @@ struct qc_eloc {
     double* d_X = nullptr;
     double* d_Jt = nullptr;
     double* d_Xt = nullptr;
+    double* d_Fref = nullptr;
     float* d_Jt32 = nullptr;
     float* d_Xt32 = nullptr;
     float* d_h32 = nullptr;

@@ -33,6 +33,11 @@ struct SysParams {
     const double* Xt;    // K^3  [a][i][k] = (ak|ki)  FP64
     const float* Jt32;   // K^3  FP32 copies (FP32 precision)
     const float* Xt32;
+    // single excitations relative to a reference determinant (FP64 precision; NULL: none):
+    // Fref[s][a][i] = h_ai + sum_{k in ref, both spins} (ai|kk) - sum_{k in ref, spin s} (ak|ki)
+    // for the Aufbau strings refA, refB (spatial orbitals 0 .. na - 1, 0 .. nb - 1)
+    const double* Fref;  // 2*K*K
+    unsigned long long refA, refB;
 };
 
 // The lookup table: sorted unique keys, their psi, and the device hash index over them.

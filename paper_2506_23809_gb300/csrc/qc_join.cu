@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "qc_device.cuh"
 #include "qc_eloc.h"
 #include "qc_internal.h"
 
@@ -116,20 +117,6 @@ __global__ void __launch_bounds__(32 * kJWarps) join_scatter_kernel(const unsign
     }
 }
 
-// Spatial string of one spin from an interleaved key: bits 2k + spin, packed.
-__device__ __forceinline__ unsigned long long gather_even(unsigned long long w) {
-    w &= 0x5555555555555555ULL;
-    w = (w | (w >> 1)) & 0x3333333333333333ULL;
-    w = (w | (w >> 2)) & 0x0F0F0F0F0F0F0F0FULL;
-    w = (w | (w >> 4)) & 0x00FF00FF00FF00FFULL;
-    w = (w | (w >> 8)) & 0x0000FFFF0000FFFFULL;
-    w = (w | (w >> 16)) & 0x00000000FFFFFFFFULL;
-    return w;
-}
-__device__ __forceinline__ unsigned long long spin_string(ulonglong2 k, int spin) {
-    return gather_even(k.x >> spin) | (gather_even(k.y >> spin) << 32);
-}
-
 __global__ void __launch_bounds__(256) join_gather_kernel(const ulonglong2* __restrict__ keys,
                                                           const unsigned* __restrict__ skey,
                                                           const unsigned* __restrict__ srow, long long m,
@@ -140,7 +127,7 @@ __global__ void __launch_bounds__(256) join_gather_kernel(const ulonglong2* __re
         if (k >= 2u * set_size) continue;  // rows that failed validation: past every group
         const unsigned row = srow[p];
         // alpha groups list beta strings and the other way round
-        gent[p] = make_ulonglong2(spin_string(keys[row], k < set_size ? 1 : 0), row);
+        gent[p] = make_ulonglong2(qc::spin_string(keys[row], k < set_size ? 1 : 0), row);
     }
 }
 
@@ -163,7 +150,7 @@ __global__ void __launch_bounds__(256) join_gather_batch_kernel(const qc::MolPar
         }
         const unsigned size = (slot_base[lo + 1] - slot_base[lo]) / 2u;
         const unsigned row = srow[p];
-        gent[p] = make_ulonglong2(spin_string(mols[lo].tp.keys[row], k - slot_base[lo] < size ? 1 : 0), row);
+        gent[p] = make_ulonglong2(qc::spin_string(mols[lo].tp.keys[row], k - slot_base[lo] < size ? 1 : 0), row);
     }
 }
 
