@@ -85,12 +85,13 @@ def _dist():
 def _plain_launches(cfg, n_table):
     """Kernels of one plain evaluation: table build, main kernel, two reduction passes, and
     with the sample-space join its index: a 3-kernel scan of the group sizes, per 11-bit
-    radix pass a histogram, a 3-kernel scan and a scatter, and the gather."""
+    radix pass a histogram, a 3-kernel scan and a scatter, the gather, and the heavy-first
+    sample order (a key kernel and one radix pass)."""
     n = 4
     if cfg["kernel"] in (4, 5):
         size = 1 << max(0, (2 * max(n_table, 1) - 1).bit_length())  # hash sets: next_pow2(2n) slots
         passes = -(-(2 * size).bit_length() // 11)
-        n += 3 + 5 * passes + 1
+        n += 3 + 5 * passes + 1 + 6
     return n
 
 

@@ -550,9 +550,11 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     const size_t jo_len = a256(2 * static_cast<size_t>(nt) * 4);
     const size_t jo_start = jo_len + a256(2 * nbuckets * 4);
     const size_t jo_ent = jo_start + a256(2 * nbuckets * 4);
-    const size_t jo_ws = jo_ent + a256(2 * static_cast<size_t>(nt) * 16);
+    const size_t jo_ord = jo_ent + a256(2 * static_cast<size_t>(nt) * 16);  // order, then two scratch arrays
+    const size_t jo_ws = jo_ord + 3 * a256(static_cast<size_t>(nt) * 4);
     unsigned* jkey = nullptr;
     unsigned* jlen = nullptr;
+    const unsigned* join_order = nullptr;
     if (join) {
         const size_t need = jo_ws + qc::join_workspace_bytes(nt, static_cast<unsigned>(nbuckets));
         if (need > H->join_cap) {
@@ -571,9 +573,20 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     if (join) {
         unsigned* jstart = reinterpret_cast<unsigned*>(H->d_join + jo_start);
         ulonglong2* gent = reinterpret_cast<ulonglong2*>(H->d_join + jo_ent);
+        // the samples are the table rows: order them heavy first by their own groups' sizes
+        unsigned* order = nullptr;
+        unsigned* pa = nullptr;
+        unsigned* pb = nullptr;
+        if (own_table) {
+            order = reinterpret_cast<unsigned*>(H->d_join + jo_ord);
+            pa = reinterpret_cast<unsigned*>(H->d_join + jo_ord + a256(static_cast<size_t>(nt) * 4));
+            pb = reinterpret_cast<unsigned*>(H->d_join + jo_ord + 2 * a256(static_cast<size_t>(nt) * 4));
+            QC_CHK(cudaMemsetAsync(pa, 0, 2 * a256(static_cast<size_t>(nt) * 4), s), "memset sample order sizes");
+        }
         QC_CHK(qc::launch_join_index(tp, static_cast<unsigned>(nbuckets), H->d_join + jo_ws, jkey, jlen, jstart,
-                                     gent, s),
+                                     gent, s, order, pa, pb),
                "join index launch");
+        join_order = order;
         tp.jstart = jstart;
         tp.jlen = jlen;
         tp.gent = gent;
@@ -595,6 +608,7 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     ep.mode = H->mode;
     ep.lean = cfg.lean;
     ep.chunks = cfg.chunks;
+    ep.order = join_order;
     if (cfg.chunks > 1 && n_u > 0) {
         const size_t recs = static_cast<size_t>(n_u) * cfg.chunks;
         if (recs > H->cpart_cap) {

@@ -97,6 +97,7 @@ struct EvalParams {
     int pad_;
     void* cpart;                  // chunks > 1: ChunkRec[n_u * chunks]
     unsigned* cticket;            // chunks > 1: per-sample count of finished chunks (zeroed)
+    const unsigned* order;        // the order warps take samples in (NULL: index order)
 };
 
 // One excitation chunk's share of a sample (chunks > 1): the warp sums of its hits.
@@ -197,8 +198,11 @@ int reduce_blocks(long long n);
 // sample-space join index over an n-row table whose slot keys K0 wrote (qc_join.cu):
 // jkey[0, 2n) slot keys (alpha rows, then beta rows offset by the set size), jlen counts
 size_t join_workspace_bytes(long long n, unsigned set_size);
+// with order (the table is the sample set): also the heavy-first order of the samples (pa, pb:
+// n entries each of scratch)
 cudaError_t launch_join_index(const TableParams& tp, unsigned set_size, void* ws, unsigned* jkey,
-                              unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s);
+                              unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s,
+                              unsigned* order = nullptr, unsigned* pa = nullptr, unsigned* pb = nullptr);
 // a batch's join index: m sort items (every molecule's 2n keys, values written by K0),
 // n_slots group sizes (slot_base[M] = n_slots, the sentinel key); entries in one gent array
 size_t join_batch_workspace_bytes(long long m, unsigned long long n_slots);

@@ -117,10 +117,13 @@ __global__ void __launch_bounds__(32 * kJWarps) join_scatter_kernel(const unsign
     }
 }
 
+// (with pa: each row's own alpha- and beta-group sizes into pa / pb, for the sample order)
 __global__ void __launch_bounds__(256) join_gather_kernel(const ulonglong2* __restrict__ keys,
                                                           const unsigned* __restrict__ skey,
                                                           const unsigned* __restrict__ srow, long long m,
-                                                          unsigned set_size, ulonglong2* __restrict__ gent) {
+                                                          unsigned set_size, ulonglong2* __restrict__ gent,
+                                                          const unsigned* __restrict__ jlen, unsigned* pa,
+                                                          unsigned* pb) {
     for (long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < m;
          p += static_cast<long long>(gridDim.x) * blockDim.x) {
         const unsigned k = skey[p];
@@ -128,6 +131,7 @@ __global__ void __launch_bounds__(256) join_gather_kernel(const ulonglong2* __re
         const unsigned row = srow[p];
         // alpha groups list beta strings and the other way round
         gent[p] = make_ulonglong2(qc::spin_string(keys[row], k < set_size ? 1 : 0), row);
+        if (pa != nullptr) (k < set_size ? pa : pb)[row] = jlen[k];
     }
 }
 
@@ -151,6 +155,24 @@ __global__ void __launch_bounds__(256) join_gather_batch_kernel(const qc::MolPar
         const unsigned size = (slot_base[lo + 1] - slot_base[lo]) / 2u;
         const unsigned row = srow[p];
         gent[p] = make_ulonglong2(qc::spin_string(mols[lo].tp.keys[row], k - slot_base[lo] < size ? 1 : 0), row);
+    }
+}
+
+// Sort key of the heavy-first sample order: 255 - (8 log2 of the sizes of the sample's own
+// alpha and beta groups, in eighths of an octave); integer arithmetic only.
+__global__ void __launch_bounds__(256) order_key_kernel(const unsigned* __restrict__ pa,
+                                                        const unsigned* __restrict__ pb, long long n,
+                                                        unsigned* __restrict__ key) {
+    for (long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+         r += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const unsigned v = pa[r] + pb[r];
+        unsigned bucket = 0;
+        if (v != 0u) {
+            const unsigned b = 31u - static_cast<unsigned>(__clz(v));
+            const unsigned frac = b >= 3u ? (v >> (b - 3u)) & 7u : (v << (3u - b)) & 7u;
+            bucket = 8u * b + frac;
+        }
+        key[r] = 255u - (bucket > 255u ? 255u : bucket);
     }
 }
 
@@ -205,17 +227,42 @@ cudaError_t join_sort(unsigned* jkey, const unsigned* val_in, long long n_half, 
 size_t qc::join_workspace_bytes(long long n, unsigned set_size) { return jlayout(2 * n, 2ULL * set_size).total; }
 
 cudaError_t qc::launch_join_index(const TableParams& tp, unsigned set_size, void* ws, unsigned* jkey,
-                                  unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s) {
+                                  unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s,
+                                  unsigned* order, unsigned* pa, unsigned* pb) {
     const long long n = tp.n;
     if (n <= 0) return cudaSuccess;
     const long long m = 2 * n;
     const unsigned* skey = nullptr;
     const unsigned* sval = nullptr;
     cudaError_t e = join_sort(jkey, nullptr, n, m, 2ULL * set_size, jlen, jstart, ws, &skey, &sval, s);
+    const unsigned gblocks = static_cast<unsigned>(std::min<long long>((m + 255) / 256, 8192));
     if (e == cudaSuccess) {
-        const unsigned gblocks = static_cast<unsigned>(std::min<long long>((m + 255) / 256, 8192));
-        join_gather_kernel<<<gblocks, 256, 0, s>>>(tp.keys, skey, sval, m, set_size, gent);
+        join_gather_kernel<<<gblocks, 256, 0, s>>>(tp.keys, skey, sval, m, set_size, gent, jlen,
+                                                   order ? pa : nullptr, pb);
         e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && order != nullptr) {
+        // heavy-first sample order: one stable 8-bit pass over the priority keys (the sort
+        // buffers are free once the gather has run)
+        const JLayout L = jlayout(m, 2ULL * set_size);
+        unsigned char* W = static_cast<unsigned char*>(ws);
+        unsigned* okey = reinterpret_cast<unsigned*>(W + L.key1);
+        unsigned* okey2 = reinterpret_cast<unsigned*>(W + L.val0);
+        unsigned* table = reinterpret_cast<unsigned*>(W + L.table);
+        unsigned* sums = reinterpret_cast<unsigned*>(W + L.sums);
+        order_key_kernel<<<std::min<unsigned>(gblocks, 4096u), 256, 0, s>>>(pa, pb, n, okey);
+        e = cudaGetLastError();
+        const long long tiles = (n + kJTile - 1) / kJTile;
+        const unsigned blocks = static_cast<unsigned>((tiles + kJWarps - 1) / kJWarps);
+        if (e == cudaSuccess) {
+            join_hist_kernel<<<blocks, 32 * kJWarps, 0, s>>>(okey, n, 0, tiles, table);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = qc::exclusive_scan_u32(table, static_cast<long long>(kJBins) * tiles, sums, s);
+        if (e == cudaSuccess) {
+            join_scatter_kernel<<<blocks, 32 * kJWarps, 0, s>>>(okey, nullptr, n, okey2, order, n, 0, tiles, table);
+            e = cudaGetLastError();
+        }
     }
     return e;
 }

@@ -93,9 +93,11 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
         if (lane == 0) it = atomicAdd(&ep.ctr->next, 1ULL);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= items) break;
-        const unsigned long long s = it / C;
+        const unsigned long long q = it / C;
+        // heavy samples first when the host gave an order: the launch then ends on light ones
+        const unsigned long long s = ep.order != nullptr ? static_cast<unsigned long long>(__ldg(ep.order + q)) : q;
         run_sample<PREC, U, FILTER, LEAN, JOIN>(sp, tp, ep, static_cast<long long>(s), lane, smem, wl, filt,
-                                                static_cast<int>(it - s * C), static_cast<int>(C));
+                                                static_cast<int>(it - q * C), static_cast<int>(C));
     }
 }
 
