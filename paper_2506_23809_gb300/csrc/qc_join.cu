@@ -64,24 +64,26 @@ JLayout jlayout(long long m, unsigned long long n_slots) {
     return L;
 }
 
+// One block per tile of kJTile items: the tile's digit counts, table[d * tiles + t].
 __global__ void __launch_bounds__(32 * kJWarps) join_hist_kernel(const unsigned* __restrict__ key, long long m,
                                                                  int shift, long long tiles,
                                                                  unsigned* __restrict__ table) {
-    __shared__ unsigned hist[kJWarps][kJBins];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = lane; d < kJBins; d += 32) hist[warp][d] = 0u;
-    __syncwarp();
-    const long long t = static_cast<long long>(blockIdx.x) * kJWarps + warp;
-    if (t >= tiles) return;  // warp-uniform; no block-wide barrier
+    __shared__ unsigned hist[kJBins];
+    for (int d = threadIdx.x; d < kJBins; d += blockDim.x) hist[d] = 0u;
+    __syncthreads();
+    const long long t = blockIdx.x;
     const long long i0 = t * kJTile;
     const long long i1 = i0 + kJTile < m ? i0 + kJTile : m;
-    for (long long i = i0 + lane; i < i1; i += 32) atomicAdd(&hist[warp][(key[i] >> shift) & (kJBins - 1)], 1u);
-    __syncwarp();
-    for (int d = lane; d < kJBins; d += 32) table[static_cast<long long>(d) * tiles + t] = hist[warp][d];
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) atomicAdd(&hist[(key[i] >> shift) & (kJBins - 1)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kJBins; d += blockDim.x) table[static_cast<long long>(d) * tiles + t] = hist[d];
 }
 
-// Stable scatter of a tile in index order; the first pass takes the row from the index
-// (item i < n is row i's alpha key, item n + i its beta key).
+// Stable scatter of one tile per block: each warp takes a contiguous quarter of the tile,
+// counts its digits, and the block turns the tile's offsets into per-warp bases (warps in
+// tile order); then every warp walks its quarter in index order (__match_any_sync ranks
+// equal digits within a step of 32).  The first pass takes the row from the index (item
+// i < n is row i's alpha key, item n + i its beta key).
 __global__ void __launch_bounds__(32 * kJWarps) join_scatter_kernel(const unsigned* __restrict__ key_in,
                                                                     const unsigned* __restrict__ val_in,
                                                                     long long n, unsigned* __restrict__ key_out,
@@ -89,14 +91,26 @@ __global__ void __launch_bounds__(32 * kJWarps) join_scatter_kernel(const unsign
                                                                     int shift, long long tiles,
                                                                     const unsigned* __restrict__ offs) {
     __shared__ unsigned run[kJWarps][kJBins];
+    constexpr int kSub = kJTile / kJWarps;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long t = static_cast<long long>(blockIdx.x) * kJWarps + warp;
-    if (t >= tiles) return;
-    for (int d = lane; d < kJBins; d += 32) run[warp][d] = offs[static_cast<long long>(d) * tiles + t];
-    __syncwarp();
+    const long long t = blockIdx.x;
+    for (int d = threadIdx.x; d < kJWarps * kJBins; d += blockDim.x) (&run[0][0])[d] = 0u;
+    __syncthreads();
+    const long long i0 = t * kJTile + static_cast<long long>(warp) * kSub;
+    long long i1 = i0 + kSub;
+    if (i1 > m) i1 = m;
+    for (long long i = i0 + lane; i < i1; i += 32) atomicAdd(&run[warp][(key_in[i] >> shift) & (kJBins - 1)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kJBins; d += blockDim.x) {
+        unsigned base = offs[static_cast<long long>(d) * tiles + t];
+        for (int w = 0; w < kJWarps; ++w) {
+            const unsigned c = run[w][d];
+            run[w][d] = base;
+            base += c;
+        }
+    }
+    __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    const long long i0 = t * kJTile;
-    const long long i1 = i0 + kJTile < m ? i0 + kJTile : m;
     for (long long b = i0; b < i1; b += 32) {
         const long long i = b + lane;
         const bool v = i < i1;
@@ -200,7 +214,7 @@ cudaError_t join_sort(unsigned* jkey, const unsigned* val_in, long long n_half, 
     // LSD passes over the bits of the largest key (the sentinel n_slots)
     const int passes = (bits_for(n_slots) + kJBits - 1) / kJBits;
     const long long tiles = (m + kJTile - 1) / kJTile;
-    const unsigned blocks = static_cast<unsigned>((tiles + kJWarps - 1) / kJWarps);
+    const unsigned blocks = static_cast<unsigned>(tiles);  // one block per tile
     const unsigned* src_k = jkey;
     const unsigned* src_v = val_in;
     unsigned* dk[2] = {key1, jkey};
@@ -253,7 +267,7 @@ cudaError_t qc::launch_join_index(const TableParams& tp, unsigned set_size, void
         order_key_kernel<<<std::min<unsigned>(gblocks, 4096u), 256, 0, s>>>(pa, pb, n, okey);
         e = cudaGetLastError();
         const long long tiles = (n + kJTile - 1) / kJTile;
-        const unsigned blocks = static_cast<unsigned>((tiles + kJWarps - 1) / kJWarps);
+        const unsigned blocks = static_cast<unsigned>(tiles);  // one block per tile
         if (e == cudaSuccess) {
             join_hist_kernel<<<blocks, 32 * kJWarps, 0, s>>>(okey, n, 0, tiles, table);
             e = cudaGetLastError();
