@@ -70,6 +70,7 @@ struct qc_batch {
     long long j_items = 0;
     unsigned long long j_slots = 0;
     size_t jo_val = 0, jo_start = 0, jo_ent = 0, jo_ws = 0, jo_base = 0, ja_len = 0;
+    size_t jo_rbase = 0, jo_order = 0, jo_pab = 0;  // rows heavy first per molecule, and their scratch
     // launch shape
     int unroll = 4, warps = 0, chunk = 1;
     long long chunk_pairs = qc::kDefaultChunkPairs;  // excitation chunks (<= 0: one warp per sample)
@@ -188,9 +189,12 @@ qc_status prepare(qc_batch* B) {
         join = B->join = false;  // sort keys, values and entry positions are 32-bit
         std::fill(jm.begin(), jm.end(), 0);
     }
-    std::vector<unsigned> slot_base(M + 1, 0u);
+    std::vector<unsigned> slot_base(M + 1, 0u), row_base(M + 1, 0u);
     if (join)
-        for (int m = 0; m < M; ++m) slot_base[m + 1] = slot_base[m] + static_cast<unsigned>(jm[m] ? 2 * lay[m].nb : 0);
+        for (int m = 0; m < M; ++m) {
+            slot_base[m + 1] = slot_base[m] + static_cast<unsigned>(jm[m] ? 2 * lay[m].nb : 0);
+            row_base[m + 1] = row_base[m] + static_cast<unsigned>(jm[m] ? B->in[m].n_u : 0);
+        }
     if (join) {
         B->ja_len = off;
         off = align256(off + static_cast<size_t>(slot_base[M]) * 4);
@@ -215,6 +219,10 @@ qc_status prepare(qc_batch* B) {
         B->jo_start = jo; jo = align256(jo + static_cast<size_t>(ns) * 4);
         B->jo_ent = jo; jo = align256(jo + static_cast<size_t>(std::max<long long>(mi, 1)) * 16);
         B->jo_base = jo; jo = align256(jo + static_cast<size_t>(M + 1) * 4);
+        B->jo_rbase = jo; jo = align256(jo + static_cast<size_t>(M + 1) * 4);
+        const size_t rows = static_cast<size_t>(std::max<long long>(mi / 2, 1));
+        B->jo_order = jo; jo = align256(jo + rows * 4);
+        B->jo_pab = jo; jo = align256(jo + 2 * align256(rows * 4));
         B->jo_ws = jo; jo = align256(jo + qc::join_batch_workspace_bytes(mi, ns));
         if (jo > B->join_cap) {
             if (B->d_join) cudaFree(B->d_join);
@@ -229,7 +237,9 @@ qc_status prepare(qc_batch* B) {
         B->j_slots = ns;
         cudaError_t e = cudaMemcpy(B->d_join + B->jo_base, slot_base.data(), (M + 1) * sizeof(unsigned),
                                    cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return bcuda(B, e, "copy join slot bases");
+        if (e == cudaSuccess)
+            e = cudaMemcpy(B->d_join + B->jo_rbase, row_base.data(), (M + 1) * sizeof(unsigned), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bcuda(B, e, "copy join slot and row bases");
     }
     for (int m = 0; m < M; ++m) {
         const Lay& L = lay[m];
@@ -286,6 +296,9 @@ qc_status prepare(qc_batch* B) {
         P.ep.chunks = L.chunks;
         P.ep.cpart = L.cpart ? static_cast<void*>(A + L.cpart) : nullptr;
         P.ep.cticket = L.ctick ? reinterpret_cast<unsigned*>(A + L.ctick) : nullptr;
+        // a joining molecule's rows are handed out heavy first (the order the batch's join
+        // index builds each step)
+        P.ep.order = jm[m] ? reinterpret_cast<const unsigned*>(B->d_join + B->jo_order) + row_base[m] : nullptr;
         if (P.ep.chunks > 1 && !P.ep.cpart) P.ep.chunks = 1;
         P.active_warps = act[m];
         P.warp_stride = stride[m];
@@ -342,14 +355,21 @@ qc_status enqueue(qc_batch* B, qc_eloc_summary* sums_host, cudaStream_t s, bool 
     if (timed) QB(cudaEventRecord(B->ev[0], s), "cudaEventRecord");
     QB(cudaMemsetAsync(B->d_arena, 0, B->arena_bytes, s), "memset arena");
     QB(qc::launch_build_batch(B->d_mols, B->d_work, B->d_key_off, B->n_mol, B->n_keys, s), "batch build");
-    if (B->join)
+    if (B->join) {
+        const size_t rows = static_cast<size_t>(std::max<long long>(B->j_items / 2, 1));
+        unsigned* pa = reinterpret_cast<unsigned*>(B->d_join + B->jo_pab);
+        unsigned* pb = reinterpret_cast<unsigned*>(B->d_join + B->jo_pab + align256(rows * 4));
+        QB(cudaMemsetAsync(pa, 0, 2 * align256(rows * 4), s), "memset join order sizes");
         QB(qc::launch_join_batch(B->d_mols, reinterpret_cast<const unsigned*>(B->d_join + B->jo_base), B->n_mol,
                                  B->j_items, B->j_slots, B->d_join + B->jo_ws, reinterpret_cast<unsigned*>(B->d_join),
                                  reinterpret_cast<unsigned*>(B->d_join + B->jo_val),
                                  reinterpret_cast<unsigned*>(B->d_arena + B->ja_len),
                                  reinterpret_cast<unsigned*>(B->d_join + B->jo_start),
-                                 reinterpret_cast<ulonglong2*>(B->d_join + B->jo_ent), s),
+                                 reinterpret_cast<ulonglong2*>(B->d_join + B->jo_ent), s,
+                                 reinterpret_cast<const unsigned*>(B->d_join + B->jo_rbase),
+                                 reinterpret_cast<unsigned*>(B->d_join + B->jo_order), pa, pb),
            "batch join index");
+    }
     if (timed) QB(cudaEventRecord(B->ev[1], s), "cudaEventRecord");
     if (B->n_run > 0) {
         qc::BatchParams bp{};

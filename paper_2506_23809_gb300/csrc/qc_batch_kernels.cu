@@ -123,7 +123,10 @@ __global__ void __launch_bounds__(MAXT) eloc_batch_kernel(const __grid_constant_
                 const unsigned long long i1 = i0 + bp.chunk < n_run ? i0 + bp.chunk : n_run;
                 for (unsigned long long it = i0; it < i1; ++it) {
                     const unsigned long long q = it / C;
-                    const long long s = r0 + static_cast<long long>(q);
+                    // a joining molecule's rows heavy first (slices cut the same order)
+                    const long long s = mp.ep.order != nullptr
+                                            ? static_cast<long long>(__ldg(mp.ep.order + r0 + static_cast<long long>(q)))
+                                            : r0 + static_cast<long long>(q);
                     const int c = static_cast<int>(it - q * C);
                     if (mp.ep.lean)
                         run_sample<PREC, U, true, 1, JOIN>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));

@@ -206,9 +206,13 @@ cudaError_t launch_join_index(const TableParams& tp, unsigned set_size, void* ws
 // a batch's join index: m sort items (every molecule's 2n keys, values written by K0),
 // n_slots group sizes (slot_base[M] = n_slots, the sentinel key); entries in one gent array
 size_t join_batch_workspace_bytes(long long m, unsigned long long n_slots);
+// with order: also each joining molecule's rows heavy first (row_base: the molecules' first
+// rows in order / pa / pb, m / 2 rows in all)
 cudaError_t launch_join_batch(const MolParams* mols, const unsigned* slot_base, int n_mol, long long m,
                               unsigned long long n_slots, void* ws, unsigned* jkey, unsigned* jval,
-                              unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s);
+                              unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s,
+                              const unsigned* row_base = nullptr, unsigned* order = nullptr,
+                              unsigned* pa = nullptr, unsigned* pb = nullptr);
 // in-place exclusive prefix sum of n u32 (qc_dedup.cu); sums: (n / 4096 + 2) u32 of scratch
 cudaError_t exclusive_scan_u32(unsigned* a, long long n, unsigned* sums, cudaStream_t s);
 // message returned by qc_eloc_last_error(NULL) on this thread (qc_api.cu)

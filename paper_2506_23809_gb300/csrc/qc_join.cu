@@ -155,7 +155,10 @@ __global__ void __launch_bounds__(256) join_gather_batch_kernel(const qc::MolPar
                                                                 const unsigned* __restrict__ slot_base, int n_mol,
                                                                 const unsigned* __restrict__ skey,
                                                                 const unsigned* __restrict__ srow, long long m,
-                                                                ulonglong2* __restrict__ gent) {
+                                                                ulonglong2* __restrict__ gent,
+                                                                const unsigned* __restrict__ row_base,
+                                                                const unsigned* __restrict__ jlen, unsigned* pa,
+                                                                unsigned* pb) {
     const unsigned sentinel = slot_base[n_mol];
     for (long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < m;
          p += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -169,24 +172,46 @@ __global__ void __launch_bounds__(256) join_gather_batch_kernel(const qc::MolPar
         const unsigned size = (slot_base[lo + 1] - slot_base[lo]) / 2u;
         const unsigned row = srow[p];
         gent[p] = make_ulonglong2(qc::spin_string(mols[lo].tp.keys[row], k - slot_base[lo] < size ? 1 : 0), row);
+        if (pa != nullptr) (k - slot_base[lo] < size ? pa : pb)[row_base[lo] + row] = jlen[k];
     }
 }
 
 // Sort key of the heavy-first sample order: 255 - (8 log2 of the sizes of the sample's own
 // alpha and beta groups, in eighths of an octave); integer arithmetic only.
+__device__ __forceinline__ unsigned order_priority_key(unsigned v) {
+    unsigned bucket = 0;
+    if (v != 0u) {
+        const unsigned b = 31u - static_cast<unsigned>(__clz(v));
+        const unsigned frac = b >= 3u ? (v >> (b - 3u)) & 7u : (v << (3u - b)) & 7u;
+        bucket = 8u * b + frac;
+    }
+    return 255u - (bucket > 255u ? 255u : bucket);
+}
+
 __global__ void __launch_bounds__(256) order_key_kernel(const unsigned* __restrict__ pa,
                                                         const unsigned* __restrict__ pb, long long n,
                                                         unsigned* __restrict__ key) {
     for (long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+         r += static_cast<long long>(gridDim.x) * blockDim.x)
+        key[r] = order_priority_key(pa[r] + pb[r]);
+}
+
+// A batch's rows (row_base: each joining molecule's first row in pa / pb): key = molecule
+// index << 8 | priority, value = the row within its molecule, so one stable sort gives every
+// molecule's rows heavy first, molecule after molecule.
+__global__ void __launch_bounds__(256) order_key_batch_kernel(const unsigned* __restrict__ row_base, int n_mol,
+                                                              const unsigned* __restrict__ pa,
+                                                              const unsigned* __restrict__ pb, long long n,
+                                                              unsigned* __restrict__ key, unsigned* __restrict__ val) {
+    for (long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
          r += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const unsigned v = pa[r] + pb[r];
-        unsigned bucket = 0;
-        if (v != 0u) {
-            const unsigned b = 31u - static_cast<unsigned>(__clz(v));
-            const unsigned frac = b >= 3u ? (v >> (b - 3u)) & 7u : (v << (3u - b)) & 7u;
-            bucket = 8u * b + frac;
+        int lo = 0, hi = n_mol;  // largest molecule with row_base <= r
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (row_base[mid] <= static_cast<unsigned>(r)) lo = mid; else hi = mid;
         }
-        key[r] = 255u - (bucket > 255u ? 255u : bucket);
+        key[r] = (static_cast<unsigned>(lo) << 8) | order_priority_key(pa[r] + pb[r]);
+        val[r] = static_cast<unsigned>(r) - row_base[lo];
     }
 }
 
@@ -195,6 +220,11 @@ int bits_for(unsigned long long v) {  // bits to hold 0..v
     while (b < 64 && (v >> b) != 0ULL) ++b;
     return b;
 }
+
+cudaError_t radix_pairs(unsigned* key0, const unsigned* val_in, long long n_half, long long m,
+                        unsigned long long max_key, unsigned* key1, unsigned* val0, unsigned* val1,
+                        unsigned* table, unsigned* sums, const unsigned** skey, const unsigned** sval,
+                        cudaStream_t s);
 
 // Group starts (exclusive prefix of the n_slots sizes) and the stable sort of m (key, value)
 // items by key, values from val_in or (val_in null) the item index modulo n_half.  Returns
@@ -211,8 +241,19 @@ cudaError_t join_sort(unsigned* jkey, const unsigned* val_in, long long n_half, 
     unsigned* sums = reinterpret_cast<unsigned*>(W + L.sums);
     cudaError_t e = cudaMemcpyAsync(jstart, jlen, n_slots * sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = qc::exclusive_scan_u32(jstart, static_cast<long long>(n_slots), sums, s);
-    // LSD passes over the bits of the largest key (the sentinel n_slots)
-    const int passes = (bits_for(n_slots) + kJBits - 1) / kJBits;
+    if (e == cudaSuccess) e = radix_pairs(jkey, val_in, n_half, m, n_slots, key1, val0, val1, table, sums, skey, sval, s);
+    return e;
+}
+
+// Stable LSD sort of m (key, value) items by key (keys up to max_key), values from val_in or
+// (val_in null) the item index modulo n_half; key0 is overwritten (a buffer of the passes).
+cudaError_t radix_pairs(unsigned* key0, const unsigned* val_in, long long n_half, long long m,
+                        unsigned long long max_key, unsigned* key1, unsigned* val0, unsigned* val1,
+                        unsigned* table, unsigned* sums, const unsigned** skey, const unsigned** sval,
+                        cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    unsigned* jkey = key0;
+    const int passes = (bits_for(max_key) + kJBits - 1) / kJBits;
     const long long tiles = (m + kJTile - 1) / kJTile;
     const unsigned blocks = static_cast<unsigned>(tiles);  // one block per tile
     const unsigned* src_k = jkey;
@@ -285,15 +326,34 @@ size_t qc::join_batch_workspace_bytes(long long m, unsigned long long n_slots) {
 
 cudaError_t qc::launch_join_batch(const MolParams* mols, const unsigned* slot_base, int n_mol, long long m,
                                   unsigned long long n_slots, void* ws, unsigned* jkey, unsigned* jval,
-                                  unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s) {
+                                  unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s,
+                                  const unsigned* row_base, unsigned* order, unsigned* pa, unsigned* pb) {
     if (m <= 0) return cudaSuccess;
     const unsigned* skey = nullptr;
     const unsigned* sval = nullptr;
     cudaError_t e = join_sort(jkey, jval, 0, m, n_slots, jlen, jstart, ws, &skey, &sval, s);
+    const unsigned gblocks = static_cast<unsigned>(std::min<long long>((m + 255) / 256, 8192));
     if (e == cudaSuccess) {
-        const unsigned gblocks = static_cast<unsigned>(std::min<long long>((m + 255) / 256, 8192));
-        join_gather_batch_kernel<<<gblocks, 256, 0, s>>>(mols, slot_base, n_mol, skey, sval, m, gent);
+        join_gather_batch_kernel<<<gblocks, 256, 0, s>>>(mols, slot_base, n_mol, skey, sval, m, gent, row_base, jlen,
+                                                         order ? pa : nullptr, pb);
         e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && order != nullptr) {
+        // every joining molecule's rows heavy first: keys and values into the sort's input
+        // buffers (free once the gather has run), one stable sort, the values into order
+        const long long R = m / 2;
+        const JLayout L = jlayout(m, n_slots);
+        unsigned char* W = static_cast<unsigned char*>(ws);
+        order_key_batch_kernel<<<std::min<unsigned>(gblocks, 4096u), 256, 0, s>>>(row_base, n_mol, pa, pb, R, jkey,
+                                                                                 jval);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = radix_pairs(jkey, jval, R, R, (static_cast<unsigned long long>(n_mol) << 8) | 255ULL,
+                            reinterpret_cast<unsigned*>(W + L.key1), reinterpret_cast<unsigned*>(W + L.val0),
+                            reinterpret_cast<unsigned*>(W + L.val1), reinterpret_cast<unsigned*>(W + L.table),
+                            reinterpret_cast<unsigned*>(W + L.sums), &skey, &sval, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(order, sval, static_cast<size_t>(R) * sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
     }
     return e;
 }
