@@ -262,6 +262,10 @@ void admit(qc_server* S, std::unique_lock<std::mutex>& lk) {
 
 void run_wave(qc_server* S, Lane& L, int lane_index, int prec, const std::vector<Request*>& take);
 
+// The largest remaining work a wave admits beside its oldest request, as a multiple of the
+// oldest's remaining work.
+constexpr double kWaveSpread = 4.0;
+
 // Launch one wave on a free lane: requests of one precision, about `quantum` enumerated
 // pairs in all -- the oldest request first with at least `oldest_pct` percent of it, then
 // the others by least remaining work; a request that does not fit whole runs a slice of
@@ -311,8 +315,15 @@ void launch_wave(qc_server* S, Lane& L, int lane_index) {
     const double reserve = std::min(work_left(oldest), 0.01 * S->oldest_pct * Q);
     double room = Q - reserve;
     std::vector<Request*> take{oldest};
+    // a request far larger than the oldest would hold the wave's short requests back until it
+    // ends: it waits for a wave of its own (on the next free lane) instead
+    const double cap = kWaveSpread * std::max(work_left(oldest), 1.0);
     for (size_t i = 1; i < cand.size(); ++i) {
         Request* r = cand[i];
+        if (work_left(r) > cap && r->next_row == 0) {
+            keep.push_back(r);
+            continue;
+        }
         long long rows = rows_left(r);
         if (rows > 0 && work_left(r) > room)
             rows = std::max<long long>(0, static_cast<long long>(room / static_cast<double>(r->pairs_per_row)));
