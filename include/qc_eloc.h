@@ -344,7 +344,8 @@ qc_status qc_batch_autotune(qc_batch* batch, void* stream, int iters, int64_t* b
  * ("waves") on `n_streams` streams.  A wave holds about `quantum` enumerated pairs
  * (QC_SRV_OPT_QUANTUM, default 1e12): the oldest request with a guaranteed share of it
  * (QC_SRV_OPT_OLDEST_PCT, default half), the
- * others least remaining work first; a request that does not fit whole runs a slice of its
+ * others least remaining work first (none with more than 4x the oldest's remaining work,
+ * which waits for a wave of its own); a request that does not fit whole runs a slice of its
  * rows (against its whole sample table) and joins the next wave, and after a wave that ran
  * a slice the ready short requests (at most half a quantum) get a wave of their own, so
  * requests that arrive while a long one runs are served between its slices.  A request that can never fit the

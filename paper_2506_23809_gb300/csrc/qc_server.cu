@@ -9,7 +9,9 @@
 //   * waves -- admitted requests whose inputs are on the device join the next wave, one
 //     qc_batch launch on one of several streams; a wave holds about `quantum` enumerated
 //     pairs: the oldest request first (a guaranteed share of the quantum), then the others with
-//     the least remaining work first.  A request too long for the room left runs a slice of
+//     the least remaining work first, none with more than kWaveSpread times the oldest's
+//     remaining work (it would hold the wave's short requests until it ends; it waits for a
+//     wave of its own).  A request too long for the room left runs a slice of
 //     its rows against its whole sample table and comes back for the next wave, so a long
 //     request never holds the GPU for more than a wave while short ones wait; after a wave
 //     that ran a slice, the short requests that are ready (at most half a quantum each) get
