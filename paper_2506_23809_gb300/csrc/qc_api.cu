@@ -314,6 +314,34 @@ qc_status qc_eloc_set_option(qc_eloc* H, int option, int64_t value) {
 
 namespace qc {
 
+// The join index of an n_table-row table in one allocation: sort keys, group sizes and
+// starts, entries, the sample order with its two scratch arrays, then the sort's workspace.
+JoinLayout join_layout(long long n_table) {
+    auto a256 = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t nt = static_cast<size_t>(std::max<long long>(n_table, 1));
+    const size_t nb = static_cast<size_t>(table_buckets(n_table));
+    JoinLayout L{};
+    L.len = a256(2 * nt * 4);
+    L.start = L.len + a256(2 * nb * 4);
+    L.ent = L.start + a256(2 * nb * 4);
+    L.ord = L.ent + a256(2 * nt * 16);
+    L.ws = L.ord + 3 * a256(nt * 4);
+    L.total = L.ws + join_workspace_bytes(static_cast<long long>(nt), static_cast<unsigned>(nb));
+    return L;
+}
+
+qc_status ensure_join(qc_eloc* H, long long n_table) {
+    const size_t need = join_layout(n_table).total;
+    if (need > H->join_cap) {
+        free_dev(H->d_join);
+        H->join_cap = 0;
+        cudaError_t e = cudaMalloc(&H->d_join, need);
+        if (e != cudaSuccess) return cuda_fail(H, e, "cudaMalloc join index");
+        H->join_cap = need;
+    }
+    return QC_OK;
+}
+
 // Workspace growth: bucket table for n_table keys, filter of 2^fw words, partials.
 qc_status ensure_workspace(qc_eloc* H, long long n_u, long long n_table, int fw) {
     const size_t entries = 2 * static_cast<size_t>(table_buckets(n_table));
@@ -472,7 +500,9 @@ qc_status qc_eloc_reserve(qc_eloc* H, int64_t n_u_max, int64_t n_table_max) {
     const long long nt = std::max<long long>(n_table_max, n_u_max);
     qc_status s = choose_config(H, std::max<long long>(n_u_max, 1), nt, c, fw);
     if (s != QC_OK) return s;
-    return ensure_workspace(H, n_u_max, nt, fw);
+    s = ensure_workspace(H, n_u_max, nt, fw);
+    if (s == QC_OK && c.join && nt > 0) s = qc::ensure_join(H, nt);  // the sample-space join's index
+    return s;
 }
 
 qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* counts, const double* psi,
@@ -549,22 +579,14 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     // join index regions: slot keys, group sizes and starts, entries (strings, rows), sort space
     const bool join = cfg.join && nt > 0;
     auto a256 = [](size_t v) { return (v + 255) / 256 * 256; };
-    const size_t jo_len = a256(2 * static_cast<size_t>(nt) * 4);
-    const size_t jo_start = jo_len + a256(2 * nbuckets * 4);
-    const size_t jo_ent = jo_start + a256(2 * nbuckets * 4);
-    const size_t jo_ord = jo_ent + a256(2 * static_cast<size_t>(nt) * 16);  // order, then two scratch arrays
-    const size_t jo_ws = jo_ord + 3 * a256(static_cast<size_t>(nt) * 4);
+    const qc::JoinLayout JL = qc::join_layout(nt);
+    const size_t jo_len = JL.len, jo_start = JL.start, jo_ent = JL.ent, jo_ord = JL.ord, jo_ws = JL.ws;
     unsigned* jkey = nullptr;
     unsigned* jlen = nullptr;
     const unsigned* join_order = nullptr;
     if (join) {
-        const size_t need = jo_ws + qc::join_workspace_bytes(nt, static_cast<unsigned>(nbuckets));
-        if (need > H->join_cap) {
-            free_dev(H->d_join);
-            H->join_cap = 0;
-            QC_CHK(cudaMalloc(&H->d_join, need), "cudaMalloc join index");
-            H->join_cap = need;
-        }
+        st = qc::ensure_join(H, nt);
+        if (st != QC_OK) return st;
         jkey = reinterpret_cast<unsigned*>(H->d_join);
         jlen = reinterpret_cast<unsigned*>(H->d_join + jo_len);
         QC_CHK(cudaMemsetAsync(jlen, 0, 2 * nbuckets * sizeof(unsigned), s), "memset join sizes");

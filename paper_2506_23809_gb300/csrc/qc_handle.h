@@ -62,6 +62,12 @@ struct qc_eloc {
 namespace qc {
 // grow the handle's workspace for n_u samples, an n_table-row table and 2^fw filter words
 qc_status ensure_workspace(qc_eloc* H, long long n_u, long long n_table, int fw);
+// the sample-space join's index for an n_table-row table: layout and growth
+struct JoinLayout {
+    size_t len, start, ent, ord, ws, total;
+};
+JoinLayout join_layout(long long n_table);
+qc_status ensure_join(qc_eloc* H, long long n_table);
 // kernel choice and launch shape for n_u samples against an n_table-row table
 qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, LaunchCfg& c, int& fw);
 // point a batch at another set of handles, reusing its device allocations

@@ -201,6 +201,32 @@ def test_join_caller_table_and_invalid_row(B, orc, join):
     assert_eloc_close(g2["eloc"], want2)
 
 
+def test_reserve_then_eval_allocates_nothing(B):
+    """After qc_eloc_reserve, an evaluation within the reserved sizes -- here one that takes
+    the sample-space join (20,000 rows) -- allocates no device memory."""
+    import torch
+    K = 26
+    ints = I.make_integrals(K, 52, 3201)
+    keys = I.rank_weighted_samples(K, 7, 7, 20000, seed=3202)
+    counts = I.zipf_counts(20000, 400000, 3203)
+    psi = I.lognormal_psi(20000, 3204)
+    h = B.qc_eloc_create(ints.h, ints.eri, 0.0, 52, 14)
+    try:
+        kt = B.keys_to_tensor(keys)
+        ct = torch.from_numpy(counts).cuda()
+        pt = torch.from_numpy(psi).cuda()
+        out = torch.empty(len(keys), dtype=torch.complex128, device="cuda")
+        B.qc_eloc_reserve(h, len(keys), len(keys))
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        B.qc_eloc_eval(h, kt, ct, pt, eloc=out)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert B.qc_eloc_last_config(h)["kernel"] in (4, 5)
+    finally:
+        B.qc_eloc_destroy(h)
+
+
 def test_exact_ground_state_constant_eloc(B, orc):
     """N=8, 4 electrons, psi = exact ground state of the sector: E_loc = E0 everywhere
     psi is not negligible (FP64 path)."""
