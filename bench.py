@@ -108,10 +108,16 @@ def _batched_launches(specs):
 
 
 def _source_hash():
+    """Hash of the main kernel's sources without their comments and whitespace: a profile's
+    counters stay attached to the code they were taken on, not to its comments."""
+    import re
     h = hashlib.sha256()
     for f in ("qc_kernels.cu", "qc_device.cuh", "qc_internal.h"):
-        with open(os.path.join(ROOT, "paper_2506_23809_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2506_23809_gb300", "csrc", f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -339,8 +339,9 @@ __device__ __forceinline__ void build_one(const TableParams& tp, int n_orb, int 
 //   [kOffLut]   colex pair table: p = C(hi, 2) + lo  ->  lo | hi << 8   (p < 2016)
 //   [kOffDiv]   single-excitation index -> occupied position, per spin (u8, < 1024 each)
 //   [kOffVar]   filter words (filtered kernel only), then one region per warp:
-//               occA[64] virA[64] occB[64] virB[64] (u8) | candidate queue (u32) |
-//               single-hit and double-hit queues (uint2) | hash lists (u32, filtered only)
+//               occA[64] virA[64] occB[64] virB[64] (u8) | reference-determinant masks (4 x
+//               u64) | candidate queue (u32) | hit queue (uint2) | scanned-singles queue
+//               (uint2, join only) | hash lists (u32) and single-list maps (u16), filtered only
 constexpr size_t kOffBar = 0;
 constexpr size_t kOffT = 16;
 constexpr size_t kOffLut = kOffT + 128 * 8;
