@@ -46,7 +46,7 @@ OPS_PER_PAIR = 7
 ALU_LANES = 16
 # Nominal dense FP64 rate of the part, GFLOP/s (the gradient contraction's bound).
 FP64_NOMINAL_GFLOPS = 1250.0
-PROFILE_JSON = os.path.join(ROOT, "profiles", "eloc_main_n52_e14_u100k.json")
+PROFILE_DIR = os.path.join(ROOT, "profiles")  # eloc_main_<workload>.json: ncu counters of the main kernel
 
 
 def _args():
@@ -408,8 +408,9 @@ def run_ours(args):
     main_s = statistics.mean(main_ms) / 1e3
     achieved = pairs_rank * OPS_PER_PAIR / main_s
     traffic = issue = None
-    if os.path.exists(PROFILE_JSON):
-        with open(PROFILE_JSON) as f:
+    profile_json = os.path.join(PROFILE_DIR, f"eloc_main_{args.workload}.json")
+    if os.path.exists(profile_json):
+        with open(profile_json) as f:
             prof = json.load(f)
         if prof.get("source_hash") == _source_hash() and prof.get("workload") == args.workload:
             traffic = prof.get("dram_bytes_per_launch")
