@@ -12,6 +12,10 @@ function names the paper passage it follows:
   * ``h_slater_condon``/``slater_condon`` -- Slater-Condon rules (Sec. III-B (ii));
   * ``eloc``           -- Eq. 5 by excitation enumeration + binary search in the table;
   * ``eloc_pairwise``  -- Eq. 5 by an all-pairs scan of the table (no enumeration);
+  * ``hit_lists`` / ``hit_lists_pairwise`` -- every hit of every sample as phase * (row + 1),
+                          from the enumeration or from the scan, for pair-by-pair parity;
+  * ``magnitudes``     -- per sample, the sum over hits of |psi(x')/psi(x)| times the absolute
+                          integral terms of <x|H|x'>: the scale of an element's rounding error;
   * ``reduce``         -- Eq. 1 count-weighted mean and variance (two-pass);
   * ``grad``           -- Eq. 4 gradient weights and 2 Re contraction with d ln Psi* rows;
   * ``dedup``          -- the unique-sample table of Sec. IV-C-4 (sorted unique keys with
@@ -70,6 +74,10 @@ def _load():
     lib.orc_eloc.restype = i64
     lib.orc_pairwise.argtypes = [P, P, f64, i32, P, P, i64, P, P, i64, P, P, P, P, i32]
     lib.orc_pairwise.restype = i64
+    lib.orc_eloc_lists.argtypes = [P, P, f64, i32, P, P, i64, P, P, i64, i32, P, P, P, P, i32]
+    lib.orc_eloc_lists.restype = i64
+    lib.orc_pairwise_lists.argtypes = [P, P, f64, i32, P, P, i64, P, P, i64, P, P, P, i32]
+    lib.orc_pairwise_lists.restype = i64
     lib.orc_reduce.argtypes = [P, P, i64, P]
     lib.orc_reduce.restype = i32
     lib.orc_connected_union.argtypes = [i32, P, i64, P, i64]
@@ -201,6 +209,77 @@ def eloc_pairwise(h, eri, e_core, n_orb, samples, psi, table_keys=None, table_ps
     if details:
         return out, dict(hits=hits, rowsum=rows, signsum=signs)
     return out
+
+
+def _table(samples, psi, table_keys, table_psi):
+    if table_keys is not None:
+        table_keys = _keys(table_keys)
+        return table_keys, _cplx(table_psi), table_keys.shape[0]
+    return None, None, 0
+
+
+def _sorted_lists(off, lst):
+    """Each sample's entries sorted by table row (|entry|): rows are unique within a
+    sample, so this is the canonical form of its hit set."""
+    n = len(off) - 1
+    seg = np.repeat(np.arange(n), np.diff(off))
+    order = np.lexsort((np.abs(lst), seg))
+    return lst[order]
+
+
+def hit_lists(h, eri, e_core, n_orb, samples, psi, table_keys=None, table_psi=None,
+              mode=SAMPLE, nthreads=0):
+    """Every hit of every sample, from the enumeration of Eq. 5: returns (off int64[n_u + 1],
+    entries int64[off[-1]]) with sample r's hits at off[r]:off[r + 1] as phase * (row + 1),
+    sorted by row.  The phase is that of the ``details`` signsum (<x'| a+ a+ a a |x> with
+    the emptied and the filled spin orbitals each in ascending order)."""
+    h, eri = _ints(h, eri)
+    samples = _keys(samples)
+    psi = _cplx(psi)
+    _, det = eloc(h, eri, e_core, n_orb, samples, psi, table_keys, table_psi, mode=mode,
+                  nthreads=nthreads, details=True)
+    off = np.zeros(samples.shape[0] + 1, dtype=np.int64)
+    off[1:] = np.cumsum(det["hits"].astype(np.int64))
+    lst = np.zeros(max(int(off[-1]), 1), dtype=np.int64)
+    tk, tp, n_t = _table(samples, psi, table_keys, table_psi)
+    out = np.zeros(samples.shape[0], dtype=np.complex128)
+    _load().orc_eloc_lists(_p(h), _p(eri), float(e_core), n_orb, _p(samples), _p(psi), samples.shape[0],
+                           _p(tk), _p(tp), n_t, int(mode), _p(out), _p(off), _p(lst), None, int(nthreads))
+    return off, _sorted_lists(off, lst[:off[-1]])
+
+
+def hit_lists_pairwise(h, eri, e_core, n_orb, samples, psi, table_keys=None, table_psi=None,
+                       nthreads=0):
+    """The same lists from the all-pairs scan of the table (no enumeration)."""
+    h, eri = _ints(h, eri)
+    samples = _keys(samples)
+    psi = _cplx(psi)
+    _, det = eloc_pairwise(h, eri, e_core, n_orb, samples, psi, table_keys, table_psi,
+                           nthreads=nthreads, details=True)
+    off = np.zeros(samples.shape[0] + 1, dtype=np.int64)
+    off[1:] = np.cumsum(det["hits"].astype(np.int64))
+    lst = np.zeros(max(int(off[-1]), 1), dtype=np.int64)
+    tk, tp, n_t = _table(samples, psi, table_keys, table_psi)
+    out = np.zeros(samples.shape[0], dtype=np.complex128)
+    _load().orc_pairwise_lists(_p(h), _p(eri), float(e_core), n_orb, _p(samples), _p(psi), samples.shape[0],
+                               _p(tk), _p(tp), n_t, _p(out), _p(off), _p(lst), int(nthreads))
+    return off, _sorted_lists(off, lst[:off[-1]])
+
+
+def magnitudes(h, eri, e_core, n_orb, samples, psi, table_keys=None, table_psi=None,
+               mode=SAMPLE, nthreads=0):
+    """Per sample, sum over its hits x' of |psi(x')/psi(x)| times the sum of the absolute
+    values of the integral terms of <x|H|x'> (|h_ai| + sum_j |<aj|ij>| + |<aj|ji>| for a
+    single, |<ab|ij>| + |<ab|ji>| for a double): float64[n_u]."""
+    h, eri = _ints(h, eri)
+    samples = _keys(samples)
+    psi = _cplx(psi)
+    tk, tp, n_t = _table(samples, psi, table_keys, table_psi)
+    out = np.zeros(samples.shape[0], dtype=np.complex128)
+    mag = np.zeros(samples.shape[0], dtype=np.float64)
+    _load().orc_eloc_lists(_p(h), _p(eri), float(e_core), n_orb, _p(samples), _p(psi), samples.shape[0],
+                           _p(tk), _p(tp), n_t, int(mode), _p(out), None, None, _p(mag), int(nthreads))
+    return mag
 
 
 def reduce(eloc_vals, counts):

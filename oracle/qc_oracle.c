@@ -26,6 +26,11 @@
  *     every m to be in the caller's table.
  *   - orc_pairwise: the same sum found by scanning every (n, m) pair of the table and
  *     keeping those that differ by one or two electrons (no enumeration).
+ *   - orc_eloc_lists / orc_pairwise_lists: the same two sums, also listing every hit of a
+ *     sample as phase * (table row + 1), so that connected sets and phases can be compared
+ *     pair by pair; orc_eloc_lists can also return, per sample, the sum over its hits of
+ *     |psi(m)/psi(n)| times the absolute integral terms of <n|H|m> (the scale of a
+ *     lower-precision element's rounding error).
  *   - orc_reduce: Eq. 1, the count-weighted mean of E_loc, and its weighted variance.
  *   - orc_grad: Eq. 4, the energy gradient 2 Re < d_theta ln Psi*(n) (E_loc - <E>) >_n as
  *     a count-weighted sample average, given the rows d_theta ln Psi*(n_i).
@@ -229,6 +234,38 @@ static double slater_condon(const ints_t *ig, int n_orb, const det_t *bra, const
     return (double)ph * asym_so(ig, a, b, i, j);
 }
 
+/* Sum of the absolute values of the integral terms that make up an off-diagonal element
+ * <bra|H|ket> in the Slater-Condon rules above (no cancellation between them): for a single
+ * i -> a, |h_ai| + sum over occupied j of |<aj|ij>| + |<aj|ji>|; for a double (i, j) ->
+ * (a, b), |<ab|ij>| + |<ab|ji>|; 0 for the diagonal and for unconnected pairs.  It is the
+ * scale of the rounding error of an element formed in a lower precision (a forward-error
+ * bound of its terms' sum), not a matrix element. */
+static double slater_condon_mag(const ints_t *ig, int n_orb, const det_t *bra, const det_t *ket) {
+    if (count_all(bra, n_orb) != count_all(ket, n_orb)) return 0.0;
+    if (count_spin(bra, n_orb, 0) != count_spin(ket, n_orb, 0)) return 0.0;
+    int holes[2], parts[2], nh = 0, np = 0, ndiff = 0;
+    for (int m = 0; m < n_orb; ++m) {
+        int b = bit_get(bra, m), k = bit_get(ket, m);
+        if (b != k) {
+            ++ndiff;
+            if (ndiff > 4) return 0.0;
+            if (k) holes[nh++] = m; else parts[np++] = m;
+        }
+    }
+    if (ndiff == 2) {
+        int i = holes[0], a = parts[0];
+        double v = fabs(h_so(ig, a, i));
+        for (int j = 0; j < n_orb; ++j)
+            if (bit_get(ket, j)) v += fabs(phys_so(ig, a, j, i, j)) + fabs(phys_so(ig, a, j, j, i));
+        return v;
+    }
+    if (ndiff == 4) {
+        int i = holes[0], j = holes[1], a = parts[0], b = parts[1];
+        return fabs(phys_so(ig, a, b, i, j)) + fabs(phys_so(ig, a, b, j, i));
+    }
+    return 0.0;
+}
+
 double orc_slater_condon(const double *h, const double *eri, double e_core, int n_orb,
                          const uint64_t *bra, const uint64_t *ket, int *phase) {
     ints_t In = {h, eri, n_orb / 2, e_core};
@@ -259,6 +296,8 @@ typedef struct {
     const det_t *tab; const double complex *tpsi; int64_t ntab; int mode;
     const det_t *x; double complex inv_ref; double complex psi_x;
     double complex acc; uint64_t pairs, hits, missing, rowsum; int64_t signsum;
+    int64_t *list; int64_t lpos;  /* per-pair output: phase * (row + 1) of each hit, or NULL */
+    int want_mag; double mag;     /* sum over hits of slater_condon_mag * |psi(x')/psi(x)| */
 } eloc_ctx;
 
 static void visit(eloc_ctx *c, const det_t *xp) {
@@ -274,6 +313,8 @@ static void visit(eloc_ctx *c, const det_t *xp) {
     c->hits++;
     c->rowsum += (uint64_t)(row + 1);
     c->signsum += (int64_t)ph * (row + 1);
+    if (c->list) c->list[c->lpos++] = (int64_t)ph * (row + 1);
+    if (c->want_mag) c->mag += slater_condon_mag(c->ig, c->n_orb, c->x, xp) * cabs(c->tpsi[row] / c->psi_x);
 }
 
 /* For each sample x: E_loc(x) = <x|H|x> + sum over every single and double excitation
@@ -283,11 +324,12 @@ static void visit(eloc_ctx *c, const det_t *xp) {
  * Outputs (any may be NULL except eloc): eloc complex[n_u]; per-sample pair count,
  * hit count, sum of (row+1) and sum of phase*(row+1) over hits.
  * Returns the number of samples whose E_loc is NaN. */
-int64_t orc_eloc(const double *h, const double *eri, double e_core, int n_orb,
-                 const uint64_t *samples, const double *psi, int64_t n_u,
-                 const uint64_t *table_keys, const double *table_psi, int64_t n_table,
-                 int mode, double *eloc, uint64_t *pairs_out, uint32_t *hits_out,
-                 uint64_t *rowsum_out, int64_t *signsum_out, int nthreads) {
+static int64_t eloc_enum(const double *h, const double *eri, double e_core, int n_orb,
+                         const uint64_t *samples, const double *psi, int64_t n_u,
+                         const uint64_t *table_keys, const double *table_psi, int64_t n_table,
+                         int mode, double *eloc, uint64_t *pairs_out, uint32_t *hits_out,
+                         uint64_t *rowsum_out, int64_t *signsum_out, const int64_t *list_off,
+                         int64_t *list_out, double *mag_out, int nthreads) {
     ints_t In = {h, eri, n_orb / 2, e_core};
     const det_t *S = (const det_t *)samples;
     const double complex *P = (const double complex *)psi;
@@ -306,6 +348,8 @@ int64_t orc_eloc(const double *h, const double *eri, double e_core, int n_orb,
         memset(&c, 0, sizeof c);
         c.ig = &In; c.n_orb = n_orb; c.tab = T; c.tpsi = TP; c.ntab = NT; c.mode = mode;
         c.x = &S[r]; c.psi_x = P[r];
+        if (list_off && list_out) c.list = list_out + list_off[r];
+        c.want_mag = mag_out != NULL;
         const det_t x = S[r];
         int N = n_orb;
         /* singles: p occupied -> a empty, same spin */
@@ -346,17 +390,42 @@ int64_t orc_eloc(const double *h, const double *eri, double e_core, int n_orb,
         if (hits_out) hits_out[r] = (uint32_t)c.hits;
         if (rowsum_out) rowsum_out[r] = c.rowsum;
         if (signsum_out) signsum_out[r] = c.signsum;
+        if (mag_out) mag_out[r] = c.mag;
     }
     return nbad;
 }
 
+int64_t orc_eloc(const double *h, const double *eri, double e_core, int n_orb,
+                 const uint64_t *samples, const double *psi, int64_t n_u,
+                 const uint64_t *table_keys, const double *table_psi, int64_t n_table,
+                 int mode, double *eloc, uint64_t *pairs_out, uint32_t *hits_out,
+                 uint64_t *rowsum_out, int64_t *signsum_out, int nthreads) {
+    return eloc_enum(h, eri, e_core, n_orb, samples, psi, n_u, table_keys, table_psi, n_table, mode, eloc,
+                     pairs_out, hits_out, rowsum_out, signsum_out, NULL, NULL, NULL, nthreads);
+}
+
+/* orc_eloc with two more outputs.  list_off[r] (int64, caller-computed from the hit counts
+ * of a previous call) is where sample r's hits start in list_out; each hit writes
+ * phase * (table row + 1) there, in the order the enumeration visits them.  mag_out[r]
+ * (may be NULL) is the sum over sample r's hits of slater_condon_mag times
+ * |psi(x')/psi(x)|. */
+int64_t orc_eloc_lists(const double *h, const double *eri, double e_core, int n_orb,
+                       const uint64_t *samples, const double *psi, int64_t n_u,
+                       const uint64_t *table_keys, const double *table_psi, int64_t n_table,
+                       int mode, double *eloc, const int64_t *list_off, int64_t *list_out,
+                       double *mag_out, int nthreads) {
+    return eloc_enum(h, eri, e_core, n_orb, samples, psi, n_u, table_keys, table_psi, n_table, mode, eloc,
+                     NULL, NULL, NULL, NULL, list_off, list_out, mag_out, nthreads);
+}
+
 /* Same sum by an O(n_u * n_table) scan: y is connected to x when they hold the same
  * number of alpha and of beta electrons and differ in exactly 2 or 4 spin orbitals. */
-int64_t orc_pairwise(const double *h, const double *eri, double e_core, int n_orb,
-                     const uint64_t *samples, const double *psi, int64_t n_u,
-                     const uint64_t *table_keys, const double *table_psi, int64_t n_table,
-                     double *eloc, uint32_t *hits_out, uint64_t *rowsum_out,
-                     int64_t *signsum_out, int nthreads) {
+static int64_t pairwise_scan(const double *h, const double *eri, double e_core, int n_orb,
+                             const uint64_t *samples, const double *psi, int64_t n_u,
+                             const uint64_t *table_keys, const double *table_psi, int64_t n_table,
+                             double *eloc, uint32_t *hits_out, uint64_t *rowsum_out,
+                             int64_t *signsum_out, const int64_t *list_off, int64_t *list_out,
+                             int nthreads) {
     ints_t In = {h, eri, n_orb / 2, e_core};
     const det_t *S = (const det_t *)samples;
     const double complex *P = (const double complex *)psi;
@@ -384,6 +453,7 @@ int64_t orc_pairwise(const double *h, const double *eri, double e_core, int n_or
             int ph;
             double hv = slater_condon(&In, n_orb, &x, y, &ph);
             acc += hv * (TP[t] / P[r]);
+            if (list_off && list_out) list_out[list_off[r] + (int64_t)hits] = (int64_t)ph * (t + 1);
             hits++; rs += (uint64_t)(t + 1); ss += (int64_t)ph * (t + 1);
         }
         int ph;
@@ -396,6 +466,25 @@ int64_t orc_pairwise(const double *h, const double *eri, double e_core, int n_or
         if (signsum_out) signsum_out[r] = ss;
     }
     return nbad;
+}
+
+int64_t orc_pairwise(const double *h, const double *eri, double e_core, int n_orb,
+                     const uint64_t *samples, const double *psi, int64_t n_u,
+                     const uint64_t *table_keys, const double *table_psi, int64_t n_table,
+                     double *eloc, uint32_t *hits_out, uint64_t *rowsum_out,
+                     int64_t *signsum_out, int nthreads) {
+    return pairwise_scan(h, eri, e_core, n_orb, samples, psi, n_u, table_keys, table_psi, n_table, eloc,
+                         hits_out, rowsum_out, signsum_out, NULL, NULL, nthreads);
+}
+
+/* orc_pairwise writing each sample's hits as phase * (table row + 1) from list_off[r] on,
+ * in table order. */
+int64_t orc_pairwise_lists(const double *h, const double *eri, double e_core, int n_orb,
+                           const uint64_t *samples, const double *psi, int64_t n_u,
+                           const uint64_t *table_keys, const double *table_psi, int64_t n_table,
+                           double *eloc, const int64_t *list_off, int64_t *list_out, int nthreads) {
+    return pairwise_scan(h, eri, e_core, n_orb, samples, psi, n_u, table_keys, table_psi, n_table, eloc,
+                         NULL, NULL, NULL, list_off, list_out, nthreads);
 }
 
 /* ---------------------------------------------------------------------------------
