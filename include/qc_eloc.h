@@ -84,6 +84,7 @@ typedef int qc_status;
 #define QC_FLAG_NEG_COUNT  0x20u
 #define QC_FLAG_TABLE_FULL 0x40u
 #define QC_FLAG_TIMEOUT    0x80u
+#define QC_FLAG_LIST_FULL  0x100u  /* a hit list position fell outside hit_list_cap */
 
 /* precision */
 #define QC_FP64        0   /* every floating-point step in FP64 */
@@ -119,6 +120,8 @@ typedef int qc_status;
                                    up to the order of accumulation */
 #define QC_OPT_SCAN_COST    11  /* join: a group is scanned when its rows x this / 4 are at most
                                    the excitations it replaces; 0 the default */
+#define QC_OPT_COUNT_WORK   12  /* 1: the local-energy kernel counts the work it does (read with
+                                   qc_eloc_work); costs global atomics, so off (0) in timed runs */
 
 typedef struct qc_eloc qc_eloc;
 
@@ -144,13 +147,27 @@ typedef struct {
  *   hit_rowsum  device uint64[n_u]: sum over hits of (table row + 1)
  *   hit_signsum device int64[n_u]:  sum over hits of phase * (table row + 1), where the
  *               phase is <x'| a+_i a+_j a_b a_a |x> with a < b the spin orbitals emptied
- *               and i < j those filled (+-1; for a single, <x'| a+_i a_a |x>). */
+ *               and i < j those filled (+-1; for a single, <x'| a+_i a_a |x>).
+ * Pair-by-pair diagnostics (the connected set of Eq. 5 restricted to the table, with the
+ * phase of every element), written where each hit is resolved; both NULL or both given:
+ *   hit_cursor  device int64[n_u], read and written: on entry, the position in hit_list of
+ *               sample i's first hit (e.g. the exclusive prefix sum of the hit_count of an
+ *               earlier evaluation of the same inputs); on exit, one past its last
+ *   hit_list    device int64[hit_list_cap]: phase * (table row + 1) of each hit of sample i
+ *               at positions entry cursor .. exit cursor - 1, in no particular order
+ *   hit_list_cap entries of hit_list; a hit whose position falls outside it is not written
+ *               and sets QC_FLAG_LIST_FULL (status QC_ERR_CAPACITY)
+ * The lists cost an atomic add per 32 hits and a store per hit: for tests and debugging,
+ * not for timed runs. */
 typedef struct {
     double*          eloc;
     qc_eloc_summary* summary;
     uint32_t*        hit_count;
     uint64_t*        hit_rowsum;
     int64_t*         hit_signsum;
+    int64_t*         hit_cursor;
+    int64_t*         hit_list;
+    int64_t          hit_list_cap;
 } qc_eloc_out;
 
 /* Create a handle for one Hamiltonian.  n_orb: even, 2..128.  n_elec: even, S_z = 0
@@ -391,6 +408,14 @@ qc_status qc_server_destroy(qc_server* server);  /* finishes queued work first *
  *   l2_gather_gbs  random 16-byte loads from a 4 MB table resident in L2, GB/s, or NULL
  * Allocates and frees about 4 MB of device memory. */
 qc_status qc_probe_peaks(double* alu_ops_per_s, double* l2_gather_gbs, void* stream);
+
+/* Work counts of the last evaluation with QC_OPT_COUNT_WORK = 1 (the units of the local-energy
+ * kernel's roofline; no counterpart in the paper).  Waits for that evaluation's stream.
+ * work8 = {samples set up, join table rows scanned (16-byte entries), excitations tested
+ * against the shared-memory Bloom filter, candidates probed in the bucket table (16-byte
+ * buckets), hits that are single excitations, same-spin doubles, opposite-spin doubles,
+ * CTAs that copied the filter}. */
+qc_status qc_eloc_work(qc_eloc* handle, uint64_t* work8);
 
 /* Launch shape of the last evaluation on this handle: {kernel (1 direct, 2 filtered,
  * 3 filtered with pair lists formed on the fly), grid CTAs, warps per CTA, unroll, dynamic

@@ -25,6 +25,8 @@ QC_OPT_LEAN = 8
 QC_OPT_CHUNK_PAIRS = 9
 QC_OPT_JOIN = 10
 QC_OPT_SCAN_COST = 11
+QC_OPT_COUNT_WORK = 12
+WORK_FIELDS = ("samples", "scan_rows", "tests", "probes", "hits_single", "hits_same", "hits_ab", "ctas")
 QC_SRV_OPT_QUANTUM = 1
 QC_SRV_OPT_OLDEST_PCT = 2
 STATUS_NAMES = {0: "QC_OK", 1: "QC_PENDING", -1: "QC_ERR_ARG", -2: "QC_ERR_UNSORTED", -3: "QC_ERR_DUP",
@@ -54,7 +56,8 @@ class qc_eloc_summary(ctypes.Structure):
 
 class qc_eloc_out(ctypes.Structure):
     _fields_ = [("eloc", ctypes.c_void_p), ("summary", ctypes.c_void_p), ("hit_count", ctypes.c_void_p),
-                ("hit_rowsum", ctypes.c_void_p), ("hit_signsum", ctypes.c_void_p)]
+                ("hit_rowsum", ctypes.c_void_p), ("hit_signsum", ctypes.c_void_p),
+                ("hit_cursor", ctypes.c_void_p), ("hit_list", ctypes.c_void_p), ("hit_list_cap", ctypes.c_int64)]
 
 
 _lib = None
@@ -87,6 +90,8 @@ def load_library(path: str = LIB_PATH):
     lib.qc_eloc_timings.restype = i32
     lib.qc_eloc_last_config.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.qc_eloc_last_config.restype = i32
+    lib.qc_eloc_work.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.qc_eloc_work.restype = i32
     lib.qc_eloc_eval_static.argtypes = [P, P, f64, i32, i32, P, P, P, i64, P, P, P]
     lib.qc_eloc_eval_static.restype = i32
     lib.qc_eloc_grad.argtypes = [P, P, P, i64, P, i64, P, P, P]
@@ -188,6 +193,13 @@ def qc_eloc_last_config(handle: QcHandle) -> dict:
                 filter_log2w=int(c[5]), chunks=int(c[6]))
 
 
+def qc_eloc_work(handle: QcHandle) -> dict:
+    """Work counts of the last evaluation made with QC_OPT_COUNT_WORK = 1 (waits for it)."""
+    w = (ctypes.c_uint64 * 8)()
+    _check(load_library().qc_eloc_work(handle.ptr, w), handle.ptr)
+    return {k: int(v) for k, v in zip(WORK_FIELDS, w)}
+
+
 def _dptr(t, name, dtype_ok, shape_last=None):
     if t is None:
         return None
@@ -203,11 +215,13 @@ def _dptr(t, name, dtype_ok, shape_last=None):
 
 
 def qc_eloc_eval(handle: QcHandle, samples, counts, psi, table_keys=None, table_psi=None,
-                 eloc=None, diagnostics: bool = False, summary: bool = True, stream=None):
+                 eloc=None, diagnostics: bool = False, summary: bool = True, stream=None,
+                 hit_cursor=None, hit_list=None):
     """Enqueue one evaluation.  Returns (eloc complex128[n_u], diag) where diag is None or
     a dict of per-sample hit_count / hit_rowsum / hit_signsum tensors.  The summary is
     written into ``handle.summary_buf``; read it with ``qc_eloc_summary_read`` after the
-    stream has passed the call."""
+    stream has passed the call.  ``hit_cursor`` (int64[n_u], each sample's first position)
+    and ``hit_list`` (int64) receive the pair-by-pair lists (qc_eloc_out in the header)."""
     import torch
     lib = load_library()
     key_types = (torch.int64, torch.uint64)
@@ -226,6 +240,14 @@ def qc_eloc_eval(handle: QcHandle, samples, counts, psi, table_keys=None, table_
         out.hit_count = diag["hit_count"].data_ptr()
         out.hit_rowsum = diag["hit_rowsum"].data_ptr()
         out.hit_signsum = diag["hit_signsum"].data_ptr()
+    if (hit_cursor is None) != (hit_list is None):
+        raise ValueError("hit_cursor and hit_list go together")
+    if hit_list is not None:
+        if hit_cursor.numel() < n_u:
+            raise ValueError("hit_cursor needs one entry per sample")
+        out.hit_cursor = _dptr(hit_cursor, "hit_cursor", (torch.int64,)).value
+        out.hit_list = _dptr(hit_list, "hit_list", (torch.int64,)).value
+        out.hit_list_cap = int(hit_list.numel())
     s = _dptr(samples, "samples", key_types, 2)
     c = _dptr(counts, "counts", (torch.int64,))
     p = _dptr(psi, "psi", psi_types)

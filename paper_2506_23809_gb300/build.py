@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libqc_eloc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["qc_api.cu", "qc_batch.cu", "qc_server.cu", "qc_kernels.cu", "qc_batch_kernels.cu", "qc_static.cu", "qc_grad.cu", "qc_dedup.cu", "qc_full.cu", "qc_probe.cu", "qc_join.cu"]
+UNITS = ["qc_api.cu", "qc_batch.cu", "qc_server.cu", "qc_kernels.cu", "qc_kernels_diag.cu", "qc_batch_kernels.cu", "qc_static.cu", "qc_grad.cu", "qc_dedup.cu", "qc_full.cu", "qc_probe.cu", "qc_join.cu"]
 
 
 def _nvcc() -> str:

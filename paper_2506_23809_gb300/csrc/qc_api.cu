@@ -256,6 +256,7 @@ qc_status qc_eloc_destroy(qc_eloc* H) {
     free_dev(H->d_cpart);
     free_dev(H->d_cticket);
     free_dev(H->d_join);
+    free_dev(H->d_work);
     for (auto& ev : H->ev)
         if (ev) cudaEventDestroy(ev);
     delete H;
@@ -302,6 +303,7 @@ qc_status qc_eloc_set_option(qc_eloc* H, int option, int64_t value) {
             if (value < 0 || value > 1024) return fail(H, QC_ERR_ARG, "QC_OPT_SCAN_COST: 0..1024");
             H->opt_scan_cost = static_cast<int>(value);
             return QC_OK;
+        case QC_OPT_COUNT_WORK: H->opt_count_work = value ? 1 : 0; return QC_OK;
         case QC_OPT_GRID:
             if (value < 0 || value > (1 << 20)) return fail(H, QC_ERR_ARG, "QC_OPT_GRID: 0..2^20");
             H->opt_grid = static_cast<int>(value);
@@ -525,6 +527,12 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
         (nt > 0 && (misaligned(tk) || misaligned(tpsi))))
         return fail(H, QC_ERR_ARG, "device arrays must be 16-byte aligned");
     if (counts && (reinterpret_cast<uintptr_t>(counts) & 7u)) return fail(H, QC_ERR_ARG, "counts must be 8-byte aligned");
+    if ((out->hit_cursor == nullptr) != (out->hit_list == nullptr))
+        return fail(H, QC_ERR_ARG, "hit_cursor and hit_list go together");
+    if (out->hit_list != nullptr &&
+        (out->hit_list_cap < 0 || (reinterpret_cast<uintptr_t>(out->hit_list) & 7u) ||
+         (reinterpret_cast<uintptr_t>(out->hit_cursor) & 7u)))
+        return fail(H, QC_ERR_ARG, "hit_list / hit_cursor must be 8-byte aligned, hit_list_cap >= 0");
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != H->device) return fail(H, QC_ERR_ARG, "handle belongs to another device");
@@ -627,6 +635,16 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     ep.hit_count = out->hit_count;
     ep.hit_rowsum = reinterpret_cast<unsigned long long*>(out->hit_rowsum);
     ep.hit_signsum = reinterpret_cast<long long*>(out->hit_signsum);
+    ep.hit_cursor = reinterpret_cast<long long*>(out->hit_cursor);
+    ep.hit_list = reinterpret_cast<long long*>(out->hit_list);
+    ep.hit_list_cap = out->hit_list != nullptr ? out->hit_list_cap : 0;
+    if (H->opt_count_work) {
+        if (!H->d_work) QC_CHK(cudaMalloc(&H->d_work, sizeof(qc::WorkCounters)), "cudaMalloc work counters");
+        QC_CHK(cudaMemsetAsync(H->d_work, 0, sizeof(qc::WorkCounters), s), "memset work counters");
+        ep.work = H->d_work;
+        H->work_stream = s;
+        H->work_recorded = true;
+    }
     ep.ctr = H->d_ctr;
     ep.T = H->d_T;
     ep.mode = H->mode;
@@ -673,6 +691,19 @@ qc_status qc_eloc_timings(qc_eloc* H, float* ms3) {
         e = cudaEventElapsedTime(&ms3[i], H->ev[i], H->ev[i + 1]);
         if (e != cudaSuccess) return cuda_fail(H, e, "cudaEventElapsedTime");
     }
+    return QC_OK;
+}
+
+qc_status qc_eloc_work(qc_eloc* H, uint64_t* work8) {
+    if (!H || !work8) return QC_ERR_ARG;
+    if (!H->work_recorded) return fail(H, QC_ERR_ARG, "no evaluation counted its work (set QC_OPT_COUNT_WORK first)");
+    qc::WorkCounters w{};
+    cudaError_t e = cudaMemcpyAsync(&w, H->d_work, sizeof(w), cudaMemcpyDeviceToHost, H->work_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(H->work_stream);
+    if (e != cudaSuccess) return cuda_fail(H, e, "work counters copy");
+    const unsigned long long v[8] = {w.samples, w.scan_rows, w.tests, w.probes, w.hits_single, w.hits_same, w.hits_ab,
+                                     w.ctas};
+    for (int i = 0; i < 8; ++i) work8[i] = v[i];
     return QC_OK;
 }
 

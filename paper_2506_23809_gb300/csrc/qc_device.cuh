@@ -428,12 +428,13 @@ __device__ __forceinline__ void add_hit(double h64, float h32, long long row, bo
 
 // Stage 2 common part: issue the loads of the stored key and psi of a stage-1 row, let
 // `element` load the integrals meanwhile, then confirm the key (exact walk on a
-// fingerprint collision) and add the hit.
+// fingerprint collision) and add the hit.  Returns phase * (row + 1) of the hit added, or
+// 0 when the key is not in the table.
 template <int PREC, typename Element>
-__device__ __forceinline__ void verify_and_add(uint2 e, ulonglong2 x, unsigned long long hx,
-                                               const TableParams& tp, int mode,
-                                               const unsigned long long* __restrict__ T64,
-                                               float2 ip32, Acc& acc, Element element) {
+__device__ __forceinline__ long long verify_and_add(uint2 e, ulonglong2 x, unsigned long long hx,
+                                                    const TableParams& tp, int mode,
+                                                    const unsigned long long* __restrict__ T64,
+                                                    float2 ip32, Acc& acc, Element element) {
     unsigned long long h;
     const ulonglong2 xp = excite(e.x, x, hx, T64, h);
     const ulonglong2 key = __ldg(tp.keys + e.y);
@@ -448,7 +449,25 @@ __device__ __forceinline__ void verify_and_add(uint2 e, ulonglong2 x, unsigned l
         if (row >= 0) pp = __ldg(tp.psi + row);
         else if (mode == QC_FULL) acc.missing++;
     }
-    if (row >= 0) add_hit<PREC>(h64, h32, row, sneg, pp, ip32, acc);
+    if (row < 0) return 0;
+    add_hit<PREC>(h64, h32, row, sneg, pp, ip32, acc);
+    return sneg ? -(row + 1) : row + 1;
+}
+
+// Pair-by-pair diagnostics: the lanes' hits of one resolution batch (ent: phase * (row + 1),
+// 0 for none) go to sample s's list at the positions its cursor hands out, one atomic add
+// per batch; a position beyond the list's capacity is not written and is flagged.
+__device__ __forceinline__ void list_hits(const EvalParams& ep, long long s, long long ent, int lane) {
+    const unsigned m = __ballot_sync(QC_FULLMASK, ent != 0);
+    if (m == 0u) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(ep.hit_cursor + s), __popc(m));
+    base = __shfl_sync(QC_FULLMASK, base, 0);
+    if (ent != 0) {
+        const unsigned long long pos = base + static_cast<unsigned long long>(__popc(m & lanemask_lt()));
+        if (pos < static_cast<unsigned long long>(ep.hit_list_cap)) ep.hit_list[pos] = ent;
+        else atomicOr(&ep.ctr->flags, QC_FLAG_LIST_FULL);
+    }
 }
 
 // Sample-space join.  Kinds of scanned groups (low bits of a scan descriptor's kind; an
@@ -881,8 +900,10 @@ __host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filt
 // stored, 1 they are formed on the fly from per-orbital values (less shared memory per
 // warp, so more warps fit for large orbital counts), 2 as ep.lean says.  Both layouts give
 // the same hash values in the same order, so the same results.  JOIN: the sample-space join
-// is taken when the table carries its index (false compiles it out).
-template <int PREC, int U, bool FILTER, int LEAN, bool JOIN = true>
+// is taken when the table carries its index (false compiles it out).  DIAG: the pair-by-pair
+// hit lists and the work counters are written when the launch asks for them (false compiles
+// them out: the checks alone cost the timed kernel a third of its speed).
+template <int PREC, int U, bool FILTER, int LEAN, bool JOIN = true, bool DIAG = false>
 __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParams& tp,
                                            const EvalParams& ep, long long s, int lane,
                                            unsigned char* smem, unsigned char* wl,
@@ -919,6 +940,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         if (c == 0) invalid_sample(ep, s, lane);  // reported once, by the first chunk
         return;
     }
+    if (DIAG && ep.work != nullptr && lane == 0 && c == 0) atomicAdd(&ep.work->samples, 1ULL);
     if (dref != nullptr && lane == 0) {
         dref[0] = As & ~sp.refA;
         dref[1] = sp.refA & ~As;
@@ -949,13 +971,27 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         nq -= n;
         __syncwarp();
         if (FILTER && v) e.x = decode(e.x, sp, wl, smem, IA, IB);
+        long long ent = 0;
         if (v)
-            verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc, [&](double& h64, float& h32, bool& sneg) {
+            ent = verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc, [&](double& h64, float& h32, bool& sneg) {
                 if ((e.x >> 16) == 0xFFFFu)
                     single_element<PREC>(e.x, prefix_parity(x), sp, wl, dref, h64, h32, sneg);
                 else
                     double_element<PREC>(e.x, prefix_parity(x), sp, h64, h32, sneg);
             });
+        if (DIAG && ep.hit_list != nullptr) list_hits(ep, s, ent, lane);
+        if (DIAG && ep.work != nullptr) {
+            const bool sgl = (e.x >> 16) == 0xFFFFu;
+            const bool same = !sgl && ((e.x ^ (e.x >> 16)) & 1u) == 0u;
+            const unsigned m1 = __ballot_sync(QC_FULLMASK, ent != 0 && sgl);
+            const unsigned m2 = __ballot_sync(QC_FULLMASK, ent != 0 && same);
+            const unsigned m3 = __ballot_sync(QC_FULLMASK, ent != 0 && !sgl && !same);
+            if (lane == 0) {
+                if (m1) atomicAdd(&ep.work->hits_single, static_cast<unsigned long long>(__popc(m1)));
+                if (m2) atomicAdd(&ep.work->hits_same, static_cast<unsigned long long>(__popc(m2)));
+                if (m3) atomicAdd(&ep.work->hits_ab, static_cast<unsigned long long>(__popc(m3)));
+            }
+        }
     };
 
     // Scan state of the join (the first phase of the main loop, before any candidate is
@@ -974,7 +1010,10 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         q[lane] = gst;
         q[32 + lane] = inc - gln;
         q[64 + lane] = kind;
-        if (lane == 31) q[102] = inc;
+        if (lane == 31) {
+            q[102] = inc;
+            if (DIAG && ep.work != nullptr && inc != 0u) atomicAdd(&ep.work->scan_rows, static_cast<unsigned long long>(inc));
+        }
         __syncwarp();
     };
     unsigned long long* qx = reinterpret_cast<unsigned long long*>(q + 96);
@@ -1225,6 +1264,8 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                         }
                         umask |= (v ? 1u : 0u) << k;
                     }
+                    if (DIAG && FILTER && ep.work != nullptr && lane == 0)
+                        atomicAdd(&ep.work->tests, static_cast<unsigned long long>(__popc(umask)) * n2);
                     need_outer = false;
                 }
                 // steps over this block of U outer entries until its inner list ends or the
@@ -1285,6 +1326,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 const int n = qn < 32 ? qn : 32;
                 const bool v = lane < n;
                 const unsigned code = v ? q[lane] : 0u;
+                if (DIAG && ep.work != nullptr && lane == 0) atomicAdd(&ep.work->probes, static_cast<unsigned long long>(n));
                 __syncwarp();
                 for (int t = lane; t < qn - n; t += 32) q[t] = q[n + t];
                 qn -= n;
@@ -1448,7 +1490,7 @@ __device__ __forceinline__ void reduce_pass2_body(const EvalParams& ep, double* 
         else if (f & QC_FLAG_DUP) st = QC_ERR_DUP;
         else if (f & QC_FLAG_NELEC) st = QC_ERR_NELEC;
         else if (f & QC_FLAG_NEG_COUNT) st = QC_ERR_COUNTS;
-        else if (f & QC_FLAG_TABLE_FULL) st = QC_ERR_CAPACITY;
+        else if (f & (QC_FLAG_TABLE_FULL | QC_FLAG_LIST_FULL)) st = QC_ERR_CAPACITY;
         else if (f & QC_FLAG_TIMEOUT) st = QC_ERR_TIMEOUT;
         else if (f & QC_FLAG_MISSING) st = QC_ERR_MISSING;
         else if (f & QC_FLAG_ZERO_PSI) st = QC_ERR_ZERO_PSI;

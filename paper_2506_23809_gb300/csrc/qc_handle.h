@@ -50,6 +50,10 @@ struct qc_eloc {
     int opt_lean = 0;  // 0 auto, 1 stored pair lists, 2 formed on the fly
     int opt_join = 0;  // 0 auto, 1 off, 2 on (sample-space mode, filtered kernel)
     int opt_scan_cost = 0;  // 0 default, else 4 x the cost of a scanned row in enumerated pairs
+    int opt_count_work = 0;  // QC_OPT_COUNT_WORK
+    qc::WorkCounters* d_work = nullptr;
+    cudaStream_t work_stream = nullptr;  // stream of the last evaluation that counted work
+    bool work_recorded = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool ev_recorded = false;
     int sm_count = 0;

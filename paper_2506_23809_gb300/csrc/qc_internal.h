@@ -80,6 +80,19 @@ struct Counters {
     unsigned long long next;  // next sample a warp of the local-energy kernel takes
 };
 
+// Work the local-energy kernel did in one launch (QC_OPT_COUNT_WORK; diagnostics, off in
+// timed runs): the units the roofline's algorithmic bytes and operations are counted in.
+struct WorkCounters {
+    unsigned long long samples;      // samples set up (valid electron counts)
+    unsigned long long scan_rows;    // join: table rows scanned (one 16-byte entry each)
+    unsigned long long tests;        // excitations tested against the shared-memory filter
+    unsigned long long probes;       // candidates probed in the bucket table
+    unsigned long long hits_single;  // hits resolved: single excitations
+    unsigned long long hits_same;    //   same-spin doubles
+    unsigned long long hits_ab;      //   opposite-spin doubles
+    unsigned long long ctas;         // CTAs that copied the filter into shared memory
+};
+
 struct EvalParams {
     const ulonglong2* samples;
     const double2* psi;
@@ -89,6 +102,10 @@ struct EvalParams {
     uint32_t* hit_count;
     unsigned long long* hit_rowsum;
     long long* hit_signsum;
+    long long* hit_cursor;        // pair-by-pair diagnostics (NULL: off): per-sample list cursor
+    long long* hit_list;          //   phase * (row + 1) of every hit
+    long long hit_list_cap;
+    WorkCounters* work;           // QC_OPT_COUNT_WORK (NULL: off)
     Counters* ctr;
     const unsigned long long* T;  // 128 entries of the linear key hash
     int mode;                     // 0 SAMPLE, 1 FULL
@@ -177,6 +194,10 @@ cudaError_t launch_build_table(const TableParams& tp, int n_orb, int na, int nb,
                                unsigned* jkey = nullptr, unsigned* jlen = nullptr);
 cudaError_t launch_eloc_main(const SysParams& sp, const TableParams& tp, const EvalParams& ep,
                              const LaunchCfg& cfg, cudaStream_t s);
+// the same kernels with the hit lists and work counters compiled in (qc_kernels_diag.cu)
+cudaError_t launch_eloc_main_diag(const SysParams& sp, const TableParams& tp, const EvalParams& ep,
+                                  const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t prepare_kernels_diag(size_t max_smem);
 cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk,
                           void* summary_dev, long long pairs_per_sample, cudaStream_t s);
 int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem, int lean = 0, int join = 0);

@@ -43,13 +43,14 @@ def test_struct_layout_matches_binding(tmp_path):
     from paper_2506_23809_gb300 import binding as B
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "qc_eloc.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(qc_eloc_summary), '
-                   'offsetof(qc_eloc_summary, status), sizeof(qc_eloc_out), offsetof(qc_eloc_out, hit_signsum));return 0;}\n')
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(qc_eloc_summary), '
+                   'offsetof(qc_eloc_summary, status), sizeof(qc_eloc_out), offsetof(qc_eloc_out, hit_signsum), '
+                   'offsetof(qc_eloc_out, hit_list_cap));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert vals == [ctypes.sizeof(B.qc_eloc_summary), B.qc_eloc_summary.status.offset,
-                    ctypes.sizeof(B.qc_eloc_out), B.qc_eloc_out.hit_signsum.offset]
+                    ctypes.sizeof(B.qc_eloc_out), B.qc_eloc_out.hit_signsum.offset, B.qc_eloc_out.hit_list_cap.offset]
 
 
 def test_header_compiles_as_c_and_cpp(tmp_path):

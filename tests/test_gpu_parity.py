@@ -1,8 +1,10 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
-Bar (Eq. 5 / Eq. 1): connected sets, table rows and fermionic phases bit-exact (per-sample
-hit count, sum of rows, phase-weighted sum of rows); E_loc within 1e-6 relative for the
-FP64 path; |Delta E| <= 1e-5 Ha on the count-weighted energy for the FP32-compensated path.
+Bar (Eq. 5 / Eq. 1): connected sets, table rows and fermionic phases bit-exact, compared
+pair by pair (every hit of every sample as phase * (row + 1), written by the kernel where
+the hit is resolved, against the oracle's lists); E_loc within 1e-6 relative for the FP64
+path; for the FP32-compensated path |Delta E| <= 1e-5 Ha on the count-weighted energy and,
+per sample, the forward-error bound of its FP32 terms (``fp32c_bound``).
 """
 import numpy as np
 import pytest
@@ -13,6 +15,20 @@ pytestmark = pytest.mark.gpu
 
 RTOL_FP64 = 1e-6     # relative, per-sample E_loc and energy (FP64 path)
 ATOL_FP32C = 1e-5    # Ha, count-weighted energy (FP32-compensated path)
+U32 = 2.0 ** -24     # unit roundoff of FP32
+
+
+def fp32c_bound(n_elec, mag):
+    """Per-sample bound on |E_loc(FP32-compensated) - E_loc(FP64 oracle)|.  Each term
+    <x|H|x'> psi(x')/psi(x) is formed from FP32 integrals and FP32 ratios: the element from at
+    most 1 + 3 n_elec / 2 stored integrals summed in FP32 (singles; doubles one or two), each
+    stored with relative error <= u, the summation adding at most its length times u of the
+    sum of their magnitudes; the ratio from psi(x') and 1/psi(x) rounded to FP32 and a complex
+    product (<= 6 u); the term's own product (u); the TwoSum accumulation is exact up to u of
+    the lane's sum.  Bounded by (n_elec + 16) u times the oracle's magnitude sum (sum over hits
+    of |psi(x')/psi(x)| times the absolute integral terms of the element).  The diagonal and the
+    final combination are FP64 (1e-12 relative is left for them)."""
+    return (n_elec + 16) * U32 * mag
 
 
 @pytest.fixture(scope="module")
@@ -26,8 +42,32 @@ def B():
     return binding
 
 
+def sort_lists(off, lst):
+    """Each sample's entries ordered by table row (the canonical form of a hit set)."""
+    n = len(off) - 1
+    seg = np.repeat(np.arange(n), np.diff(off))
+    return lst[np.lexsort((np.abs(lst), seg))]
+
+
+def gpu_lists(B, h, kt, ct, pt, tk, tp, hit_count):
+    """Pair-by-pair lists of one evaluation: cursors from the hit counts of a previous
+    evaluation of the same inputs, then every hit as phase * (row + 1).  Returns (off, sorted
+    entries, status); the exit cursors must be exactly the next sample's start."""
+    import torch
+    cnt = hit_count.to(torch.int64)
+    off = torch.zeros(len(cnt) + 1, dtype=torch.int64, device=cnt.device)
+    off[1:] = torch.cumsum(cnt, 0)
+    cursor = off[:-1].clone()
+    lst = torch.full((max(int(off[-1].item()), 1),), 0, dtype=torch.int64, device=cnt.device)
+    eloc, _ = B.qc_eloc_eval(h, kt, ct, pt, tk, tp, hit_cursor=cursor, hit_list=lst)
+    st = B.qc_eloc_summary_read(h)["status"]
+    o = off.cpu().numpy()
+    assert np.array_equal(cursor.cpu().numpy(), o[1:]), "a sample's list length differs from its hit count"
+    return o, sort_lists(o, lst.cpu().numpy()[:o[-1]]), st, eloc.cpu().numpy()
+
+
 def run_gpu(B, ints, n_orb, n_elec, keys, counts, psi, table=None, prec=0, mode=0, opts=None,
-            diag=True, e_core=0.0):
+            diag=True, e_core=0.0, lists=False):
     import torch
     h = B.qc_eloc_create(ints.h, ints.eri, e_core, n_orb, n_elec, prec, mode)
     try:
@@ -40,14 +80,19 @@ def run_gpu(B, ints, n_orb, n_elec, keys, counts, psi, table=None, prec=0, mode=
         if table is not None:
             tk = B.keys_to_tensor(table[0])
             tp = torch.from_numpy(np.ascontiguousarray(table[1], dtype=np.complex128)).cuda()
-        eloc, d = B.qc_eloc_eval(h, kt, ct, pt, tk, tp, diagnostics=diag)
+        eloc, d = B.qc_eloc_eval(h, kt, ct, pt, tk, tp, diagnostics=diag or lists)
         summ = B.qc_eloc_summary_read(h)
         cfg = B.qc_eloc_last_config(h)
         out = dict(eloc=eloc.cpu().numpy(), summary=summ, cfg=cfg)
-        if diag:
+        if diag or lists:
             out["hits"] = d["hit_count"].cpu().numpy().view(np.uint32)
             out["rowsum"] = d["hit_rowsum"].cpu().numpy().view(np.uint64)
             out["signsum"] = d["hit_signsum"].cpu().numpy()
+        if lists:
+            out["list_off"], out["list"], st, e2 = gpu_lists(B, h, kt, ct, pt, tk, tp, d["hit_count"])
+            assert st == summ["status"]
+            # writing the lists leaves the evaluation bitwise unchanged
+            assert np.array_equal(e2.view(np.uint64), out["eloc"].view(np.uint64))
         return out
     finally:
         B.qc_eloc_destroy(h)
@@ -60,12 +105,39 @@ def assert_sets_equal(g, det, rows=None):
     assert np.array_equal(g["signsum"][sel], det["signsum"]), "fermionic phases differ"
 
 
+def assert_lists_equal(g, want, rows=None):
+    """Pair by pair: every sample's (row, phase) list equals the oracle's.  want = (off,
+    entries) from oracle.hit_lists for the selected rows (all rows when rows is None)."""
+    woff, wl = want
+    goff, gl = g["list_off"], g["list"]
+    if rows is None:
+        assert np.array_equal(goff, woff), "hit counts differ"
+        assert np.array_equal(gl, wl), "hit lists (rows or phases) differ"
+        return
+    for k, r in enumerate(rows):
+        a = gl[goff[r]:goff[r + 1]]
+        b = wl[woff[k]:woff[k + 1]]
+        assert np.array_equal(a, b), f"hit list of sample {r} differs"
+
+
 def assert_eloc_close(got, want, rtol=RTOL_FP64):
     ok = np.isfinite(want)
     assert np.array_equal(np.isfinite(got), ok)
     err = np.abs(got[ok] - want[ok]) / np.maximum(1.0, np.abs(want[ok]))
     assert err.max(initial=0.0) <= rtol, f"max rel err {err.max():.3e}"
     return err.max(initial=0.0)
+
+
+def assert_fp32c_per_sample(orc, ints, n_orb, n_elec, keys, psi, got, want, table=(None, None), mode=0):
+    """Per-sample error of the FP32-compensated path against the FP64 oracle within
+    fp32c_bound; returns (|error| per sample, largest error / bound)."""
+    mag = orc.magnitudes(ints.h, ints.eri, 0.0, n_orb, keys, psi, table[0], table[1], mode=mode)
+    ok = np.isfinite(want)
+    assert np.array_equal(np.isfinite(got), ok)
+    per = np.abs(got[ok] - want[ok])
+    bound = fp32c_bound(n_elec, mag[ok]) + 1e-12 * np.abs(want[ok])
+    assert np.all(per <= bound), f"per-sample error {per.max():.3e} above its bound"
+    return per, float((per / bound).max(initial=0.0))
 
 
 KERNELS = [dict(), {2: 1}, {2: 2, 5: 1}, {2: 2, 5: 2}, {2: 2, 5: 4}, {2: 2, 4: 3, 6: 5}, {2: 1, 4: 1, 6: 7},
@@ -79,9 +151,10 @@ KERNELS = [dict(), {2: 1}, {2: 2, 5: 1}, {2: 2, 5: 2}, {2: 2, 5: 4}, {2: 2, 4: 3
 def test_tiny_sample_mode(B, orc, opts):
     """N=14, 6 electrons, 1,000 uniform samples (204 pairs each), every kernel variant."""
     ints, s = I.make_workload("n14_e6_u1k")
-    g = run_gpu(B, ints, 14, 6, s.keys, s.counts, s.psi, opts=opts)
+    g = run_gpu(B, ints, 14, 6, s.keys, s.counts, s.psi, opts=opts, lists=True)
     want, det = orc.eloc(ints.h, ints.eri, 0.0, 14, s.keys, s.psi, details=True)
     assert_sets_equal(g, det)
+    assert_lists_equal(g, orc.hit_lists(ints.h, ints.eri, 0.0, 14, s.keys, s.psi))
     assert_eloc_close(g["eloc"], want)
     m, var, w, n = orc.reduce(want, s.counts)
     sm = g["summary"]
@@ -91,8 +164,7 @@ def test_tiny_sample_mode(B, orc, opts):
     assert abs(sm["energy"] - m) <= RTOL_FP64 * abs(m)
     assert abs(sm["var"] - var) <= RTOL_FP64 * max(1.0, var)
     # the all-pairs scan (no enumeration) finds the same connected set
-    _, pdet = orc.eloc_pairwise(ints.h, ints.eri, 0.0, 14, s.keys, s.psi, details=True)
-    assert np.array_equal(g["hits"], pdet["hits"]) and np.array_equal(g["signsum"], pdet["signsum"])
+    assert_lists_equal(g, orc.hit_lists_pairwise(ints.h, ints.eri, 0.0, 14, s.keys, s.psi))
 
 
 @pytest.mark.parametrize("n,ne,nu,prec", [(76, 20, 3000, 1), (128, 64, 24, 0), (52, 14, 2000, 0)])
@@ -106,23 +178,28 @@ def test_lean_lists_equal_stored(B, orc, n, ne, nu, prec):
     counts = I.zipf_counts(nu, 40 * nu, 992 + n)
     psi = I.lognormal_psi(nu, 993 + n)
     a = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={8: 1, 10: 1})
-    b = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={8: 2, 10: 1})
+    b = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={8: 2, 10: 1}, lists=True)
     assert a["cfg"]["kernel"] == 2 and b["cfg"]["kernel"] == 3
     assert b["cfg"]["warps"] >= a["cfg"]["warps"] and b["cfg"]["filter_log2w"] == a["cfg"]["filter_log2w"]
     assert np.array_equal(a["eloc"].view(np.uint64), b["eloc"].view(np.uint64))
     assert np.array_equal(a["hits"], b["hits"]) and np.array_equal(a["signsum"], b["signsum"])
     want, det = orc.eloc(ints.h, ints.eri, 0.0, n, keys, psi, details=True)
     assert_sets_equal(b, det)
+    assert_lists_equal(b, orc.hit_lists(ints.h, ints.eri, 0.0, n, keys, psi))
     if prec == 0:
         assert_eloc_close(b["eloc"], want)
 
 
 @pytest.mark.parametrize("n,ne,nu,prec,opts", [(52, 14, 3000, 0, {}), (76, 20, 3000, 1, {}),
                                                (52, 14, 3000, 0, {11: 1}), (52, 14, 3000, 0, {11: 64}),
+                                               (52, 14, 2000, 0, {11: 1024}),
+                                               (76, 20, 2000, 0, {}), (76, 20, 2000, 1, {11: 1}),
+                                               (76, 20, 2000, 1, {11: 1024}),
                                                (76, 20, 2000, 1, {8: 2, 5: 2}), (52, 14, 3000, 0, {9: 2000}),
-                                               (40, 8, 1500, 0, {}), (128, 64, 24, 0, {})],
-                         ids=["n52", "n76_fp32c", "n52_scan_all", "n52_enum_most", "n76_lean_u2", "n52_chunks",
-                              "n40", "n128"])
+                                               (40, 8, 1500, 0, {}), (128, 64, 24, 0, {}), (128, 40, 200, 1, {})],
+                         ids=["n52", "n76_fp32c", "n52_scan_all", "n52_enum_more", "n52_enum_most", "n76_fp64",
+                              "n76_scan_all", "n76_enum_most", "n76_lean_u2", "n52_chunks", "n40", "n128",
+                              "n128_fp32c"])
 def test_join_equals_enumeration(B, orc, n, ne, nu, prec, opts):
     """The sample-space join (QC_OPT_JOIN 2: short row groups scanned, long ones enumerated)
     finds the same connected set with the same rows and phases as plain enumeration
@@ -135,19 +212,20 @@ def test_join_equals_enumeration(B, orc, n, ne, nu, prec, opts):
     keys = I.rank_weighted_samples(K, na, ne - na, nu, seed=1991 + n)
     counts = I.zipf_counts(nu, 40 * nu, 1992 + n)
     psi = I.lognormal_psi(nu, 1993 + n)
-    a = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={2: 2, 10: 1, **opts})
-    b = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={2: 2, 10: 2, **opts})
+    a = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={2: 2, 10: 1, **opts}, lists=True)
+    b = run_gpu(B, ints, n, ne, keys, counts, psi, prec=prec, opts={2: 2, 10: 2, **opts}, lists=True)
     assert a["cfg"]["kernel"] in (2, 3) and b["cfg"]["kernel"] in (4, 5)
-    assert np.array_equal(a["hits"], b["hits"]) and np.array_equal(a["rowsum"], b["rowsum"])
-    assert np.array_equal(a["signsum"], b["signsum"])
+    assert np.array_equal(a["list_off"], b["list_off"]) and np.array_equal(a["list"], b["list"])
     want, det = orc.eloc(ints.h, ints.eri, 0.0, n, keys, psi, details=True)
     assert_sets_equal(b, det)
+    assert_lists_equal(b, orc.hit_lists(ints.h, ints.eri, 0.0, n, keys, psi))
     if prec == 0:
         assert_eloc_close(b["eloc"], want)
         assert_eloc_close(b["eloc"], a["eloc"], rtol=1e-12)
     else:
         m, _, _, _ = orc.reduce(want, counts)
         assert abs(b["summary"]["energy"] - m) <= ATOL_FP32C
+        assert_fp32c_per_sample(orc, ints, n, ne, keys, psi, b["eloc"], want)
     assert b["summary"]["status"] == 0 and b["summary"]["n_hits"] == a["summary"]["n_hits"]
 
 
@@ -180,10 +258,11 @@ def test_join_caller_table_and_invalid_row(B, orc, join):
     skeys = allk[pick]
     spsi = I.lognormal_psi(len(skeys), 3105)
     counts = I.zipf_counts(len(skeys), 50 * len(skeys), 3106)
-    g = run_gpu(B, ints, 52, 14, skeys, counts, spsi, table=(tkeys, tpsi), opts={10: join})
+    g = run_gpu(B, ints, 52, 14, skeys, counts, spsi, table=(tkeys, tpsi), opts={10: join}, lists=True)
     assert g["cfg"]["kernel"] in ((2, 3) if join == 1 else (4, 5))
     want, det = orc.eloc(ints.h, ints.eri, 0.0, 52, skeys, spsi, tkeys, tpsi, details=True)
     assert_sets_equal(g, det)
+    assert_lists_equal(g, orc.hit_lists(ints.h, ints.eri, 0.0, 52, skeys, spsi, tkeys, tpsi))
     assert_eloc_close(g["eloc"], want)
     assert g["summary"]["status"] == 0
     # a table row with one electron too many (an empty orbital filled): flagged, in no group
@@ -194,10 +273,13 @@ def test_join_caller_table_and_invalid_row(B, orc, join):
     bad[r, 0] = np.uint64(occ | (1 << free))
     order = np.lexsort((bad[:, 0], bad[:, 1]))
     bad, bpsi = bad[order], tpsi[order]
-    g2 = run_gpu(B, ints, 52, 14, skeys, counts, spsi, table=(bad, bpsi), opts={10: join})
+    g2 = run_gpu(B, ints, 52, 14, skeys, counts, spsi, table=(bad, bpsi), opts={10: join}, lists=True)
     assert g2["summary"]["status"] == -4
     want2, det2 = orc.eloc(ints.h, ints.eri, 0.0, 52, skeys, spsi, bad, bpsi, details=True)
     assert_sets_equal(g2, det2)
+    # the oracle has no electron-count check of table rows: the bad row's key has no
+    # connected sample with the right count, so both lists leave it out
+    assert_lists_equal(g2, orc.hit_lists(ints.h, ints.eri, 0.0, 52, skeys, spsi, bad, bpsi))
     assert_eloc_close(g2["eloc"], want2)
 
 
@@ -251,12 +333,15 @@ def test_full_mode(B, orc, prec):
     pick = np.sort(rng.choice(len(basis), 120, replace=False))
     keys, psi = basis[pick], tpsi[pick]
     counts = I.multinomial_counts(120, 10_000, 64)
-    g = run_gpu(B, ints, 12, 6, keys, counts, psi, table=(basis, tpsi), prec=prec, mode=1)
+    g = run_gpu(B, ints, 12, 6, keys, counts, psi, table=(basis, tpsi), prec=prec, mode=1, lists=True)
     want, det = orc.eloc(ints.h, ints.eri, 0.0, 12, keys, psi, basis, tpsi, mode=orc.FULL, details=True)
     assert_sets_equal(g, det)
+    assert_lists_equal(g, orc.hit_lists(ints.h, ints.eri, 0.0, 12, keys, psi, basis, tpsi, mode=orc.FULL))
     assert np.all(det["hits"] == det["pairs"])
     if prec == 0:
         assert_eloc_close(g["eloc"], want)
+    else:
+        assert_fp32c_per_sample(orc, ints, 12, 6, keys, psi, g["eloc"], want, (basis, tpsi), mode=orc.FULL)
     m, var, w, n = orc.reduce(want, counts)
     tol = RTOL_FP64 * abs(m) if prec == 0 else ATOL_FP32C
     assert abs(g["summary"]["energy"] - m) <= tol
@@ -285,9 +370,10 @@ def test_medium_n52_and_shards(B, orc):
     keys = I.rank_weighted_samples(26, 7, 7, 3000, seed=5202)
     counts = I.zipf_counts(3000, 300_000, 5203)
     psi = I.lognormal_psi(3000, 5204)
-    g = run_gpu(B, ints, 52, 14, keys, counts, psi)
+    g = run_gpu(B, ints, 52, 14, keys, counts, psi, lists=True)
     want, det = orc.eloc(ints.h, ints.eri, 0.0, 52, keys, psi, details=True)
     assert_sets_equal(g, det)
+    assert_lists_equal(g, orc.hit_lists(ints.h, ints.eri, 0.0, 52, keys, psi))
     assert_eloc_close(g["eloc"], want)
     assert g["summary"]["n_pairs"] == 3000 * 25137
     m, var, w, n = orc.reduce(want, counts)
@@ -315,12 +401,14 @@ def test_full_size_n52_sampled(B, orc):
     (which looks x' up in the whole table), plus exact structural totals and run-to-run
     determinism."""
     ints, s = I.make_workload("n52_e14_u100k")
-    g = run_gpu(B, ints, 52, 14, s.keys, s.counts, s.psi)
+    g = run_gpu(B, ints, 52, 14, s.keys, s.counts, s.psi, lists=True)
     g2 = run_gpu(B, ints, 52, 14, s.keys, s.counts, s.psi)
+    assert g["cfg"]["kernel"] in (4, 5)
     assert np.array_equal(g["eloc"].view(np.uint64), g2["eloc"].view(np.uint64))
     rows = np.sort(np.random.default_rng(7).choice(s.n_u, 512, replace=False))
     want, det = orc.eloc(ints.h, ints.eri, 0.0, 52, s.keys[rows], s.psi[rows], s.keys, s.psi, details=True)
     assert_sets_equal(g, det, rows)
+    assert_lists_equal(g, orc.hit_lists(ints.h, ints.eri, 0.0, 52, s.keys[rows], s.psi[rows], s.keys, s.psi), rows)
     assert_eloc_close(g["eloc"][rows], want)
     sm = g["summary"]
     assert sm["n_pairs"] == 100_000 * 25137 and sm["w"] == 10_000_000 and sm["status"] == 0
@@ -337,15 +425,41 @@ def test_precision_form_n76(B, orc):
     keys = I.rank_weighted_samples(38, 10, 10, 4000, seed=7602)
     counts = I.zipf_counts(4000, 400_000, 7603)
     psi = I.lognormal_psi(4000, 7604)
-    g = run_gpu(B, ints, 76, 20, keys, counts, psi, prec=1)
+    g = run_gpu(B, ints, 76, 20, keys, counts, psi, prec=1, lists=True)
     want, det = orc.eloc(ints.h, ints.eri, 0.0, 76, keys, psi, details=True)
     assert_sets_equal(g, det)
+    assert_lists_equal(g, orc.hit_lists(ints.h, ints.eri, 0.0, 76, keys, psi))
     m, var, w, n = orc.reduce(want, counts)
     err_total = abs(g["summary"]["energy"] - m)
-    per = np.abs(g["eloc"] - want)
-    print(f"FP32-comp N=76: |dE| total {err_total:.2e} Ha, per-sample max {per.max():.2e}, rms {np.sqrt((per**2).mean()):.2e}")
+    per, frac = assert_fp32c_per_sample(orc, ints, 76, 20, keys, psi, g["eloc"], want)
+    print(f"FP32-comp N=76: |dE| total {err_total:.2e} Ha, per-sample max {per.max():.2e}, "
+          f"rms {np.sqrt((per**2).mean()):.2e}, max error / bound {frac:.3f}")
     assert err_total <= ATOL_FP32C
     assert g["summary"]["n_pairs"] == 4000 * 112980
+
+
+@pytest.mark.slow
+def test_full_size_n76_sampled(B, orc):
+    """The precision-form workload at full size (N=76, 20 e, 2e5 samples, FP32 integrals and
+    terms, FP64 diagonal and reduction) in its default launch (the sample-space join): the
+    hit lists of 512 sampled rows pair by pair against the oracle, every sample's E_loc
+    within its FP32 forward-error bound, and the count-weighted energy within 1e-5 Ha of the
+    FP64 oracle's over all 2e5 samples."""
+    ints, s = I.make_workload("n76_e20_u200k")
+    g = run_gpu(B, ints, 76, 20, s.keys, s.counts, s.psi, prec=1, lists=True)
+    assert g["cfg"]["kernel"] in (4, 5) and g["summary"]["status"] == 0
+    rows = np.sort(np.random.default_rng(76).choice(s.n_u, 512, replace=False))
+    assert_lists_equal(g, orc.hit_lists(ints.h, ints.eri, 0.0, 76, s.keys[rows], s.psi[rows], s.keys, s.psi), rows)
+    want, mag = orc.eloc_and_magnitudes(ints.h, ints.eri, 0.0, 76, s.keys, s.psi)
+    per = np.abs(g["eloc"] - want)
+    bound = fp32c_bound(20, mag) + 1e-12 * np.abs(want)
+    assert np.all(per <= bound), f"per-sample error {per.max():.3e} above its bound"
+    m, var, w, n = orc.reduce(want, s.counts)
+    err_total = abs(g["summary"]["energy"] - m)
+    print(f"FP32-comp N=76 full size: |dE| total {err_total:.2e} Ha, per-sample max {per.max():.2e}, "
+          f"rms {np.sqrt((per ** 2).mean()):.2e}, max error / bound {(per / bound).max():.3f}")
+    assert err_total <= ATOL_FP32C
+    assert g["summary"]["n_pairs"] == s.n_u * 112980 and g["summary"]["w"] == 20_000_000
 
 
 @pytest.mark.parametrize("K,ne,n_u", [(2, 2, 4), (64, 4, 300), (64, 64, 24), (20, 20, 500)])
@@ -360,10 +474,14 @@ def test_shapes_edge(B, orc, K, ne, n_u):
     n = len(keys)
     psi = I.lognormal_psi(n, 300 + K)
     counts = I.multinomial_counts(n, 50 * n, 400 + K)
-    for opts in ({}, {2: 1}):
-        g = run_gpu(B, ints, 2 * K, ne, keys, counts, psi, opts=opts)
+    wl = orc.hit_lists(ints.h, ints.eri, 0.0, 2 * K, keys, psi)
+    for opts in ({}, {2: 1}, {2: 2, 10: 2}):
+        if 10 in opts and K == 2:
+            continue
+        g = run_gpu(B, ints, 2 * K, ne, keys, counts, psi, opts=opts, lists=True)
         want, det = orc.eloc(ints.h, ints.eri, 0.0, 2 * K, keys, psi, details=True)
         assert_sets_equal(g, det)
+        assert_lists_equal(g, wl)
         assert_eloc_close(g["eloc"], want)
 
 
@@ -433,7 +551,7 @@ def test_excitation_chunks(B, orc, prec):
     bad_keys[7, 0] ^= np.uint64(1)             # one electron too many or too few
     order = np.lexsort((bad_keys[:, 0], bad_keys[:, 1]))
     bad_keys, psi_b, counts_b = bad_keys[order], psi[order], counts[order]
-    a = run_gpu(B, ints, 52, 14, bad_keys, counts_b, psi_b, prec=prec, opts={9: 4000})
+    a = run_gpu(B, ints, 52, 14, bad_keys, counts_b, psi_b, prec=prec, opts={9: 4000}, lists=True)
     b = run_gpu(B, ints, 52, 14, bad_keys, counts_b, psi_b, prec=prec, opts={9: 4000})
     one = run_gpu(B, ints, 52, 14, bad_keys, counts_b, psi_b, prec=prec, opts={9: -1})
     assert a["cfg"]["chunks"] == 7 and one["cfg"]["chunks"] == 1
@@ -450,5 +568,7 @@ def test_excitation_chunks(B, orc, prec):
     want, det = orc.eloc(ints.h, ints.eri, 0.0, 52, bad_keys, psi_b, details=True)
     ok = np.isfinite(want) & fin
     assert np.array_equal(a["hits"][ok], det["hits"][ok]) and np.array_equal(a["signsum"][ok], det["signsum"][ok])
+    okr = np.flatnonzero(ok)
+    assert_lists_equal(a, orc.hit_lists(ints.h, ints.eri, 0.0, 52, bad_keys[okr], psi_b[okr], bad_keys, psi_b), okr)
     if prec == 0:
         assert_eloc_close(a["eloc"][ok], want[ok])
