@@ -266,11 +266,12 @@ def hit_lists_pairwise(h, eri, e_core, n_orb, samples, psi, table_keys=None, tab
     return off, _sorted_lists(off, lst[:off[-1]])
 
 
-def magnitudes(h, eri, e_core, n_orb, samples, psi, table_keys=None, table_psi=None,
-               mode=SAMPLE, nthreads=0):
-    """Per sample, sum over its hits x' of |psi(x')/psi(x)| times the sum of the absolute
-    values of the integral terms of <x|H|x'> (|h_ai| + sum_j |<aj|ij>| + |<aj|ji>| for a
-    single, |<ab|ij>| + |<ab|ji>| for a double): float64[n_u]."""
+def eloc_and_magnitudes(h, eri, e_core, n_orb, samples, psi, table_keys=None, table_psi=None,
+                        mode=SAMPLE, nthreads=0):
+    """E_loc as ``eloc`` and, from the same pass, per sample the sum over its hits x' of
+    |psi(x')/psi(x)| times the sum of the absolute values of the integral terms of <x|H|x'>
+    (|h_ai| + sum_j |<aj|ij>| + |<aj|ji>| for a single, |<ab|ij>| + |<ab|ji>| for a double):
+    (complex128[n_u], float64[n_u])."""
     h, eri = _ints(h, eri)
     samples = _keys(samples)
     psi = _cplx(psi)
@@ -279,7 +280,13 @@ def magnitudes(h, eri, e_core, n_orb, samples, psi, table_keys=None, table_psi=N
     mag = np.zeros(samples.shape[0], dtype=np.float64)
     _load().orc_eloc_lists(_p(h), _p(eri), float(e_core), n_orb, _p(samples), _p(psi), samples.shape[0],
                            _p(tk), _p(tp), n_t, int(mode), _p(out), None, None, _p(mag), int(nthreads))
-    return mag
+    return out, mag
+
+
+def magnitudes(h, eri, e_core, n_orb, samples, psi, table_keys=None, table_psi=None,
+               mode=SAMPLE, nthreads=0):
+    """The magnitude sums of ``eloc_and_magnitudes`` alone: float64[n_u]."""
+    return eloc_and_magnitudes(h, eri, e_core, n_orb, samples, psi, table_keys, table_psi, mode, nthreads)[1]
 
 
 def reduce(eloc_vals, counts):
