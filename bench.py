@@ -34,11 +34,23 @@ if ROOT not in sys.path:
 
 METRIC = "connected matrix elements/sec and E_loc samples/sec vs L2/HBM roofline; serve p50/p99"
 UNIT = "connected matrix elements/s"
-# Algorithmic integer (ALU-pipe) operations per enumerated pair in the main kernel: form
-# the excitation's hash (1 XOR), derive the filter word offset (1), shift the filter word to
-# its three bit positions (3), combine them (1) and test the result (1).  The word itself
-# is read through the load/store pipe and is not counted.
-OPS_PER_PAIR = 7
+# The roofline of the local-energy kernel is computed from the work it did in one launch,
+# counted on the device (QC_OPT_COUNT_WORK, one untimed evaluation after the timed steps):
+#   ALU operations = 7 x filter tests: form the excitation's hash (1 XOR), derive the filter
+#     word offset (1), shift the word to its three bit positions (3), combine (1), test (1);
+#     the word itself is read through the load/store pipe and is not counted;
+#   L2 bytes = 16 per scanned table row (the join's entry) + 16 per bucket probe
+#     + per hit 16 (stored key) + 16 (psi(x')) + its integrals, e bytes each (8 FP64, 4 FP32):
+#       single 1 + 3 n_elec / 2 (h_ai, (ai|kk) over the occupied k, (ak|ki) over the same spin),
+#       same-spin double 2, opposite-spin double 1
+#     + per sample 16 (x) + 16 (psi(x)) + 16 (E_loc written) + 8 per spin-string set lookup
+#       (one per single excitation, 2 o v)
+#     + per CTA the Bloom filter copied into shared memory (4 x 2^fw).
+# achieved = that work / the kernel's mean event-timed duration over the timed steps; the
+# peaks are the derived ALU peak (SMs x 4 x 16 lanes x max clock) with the library's measured
+# ALU probe beside it, and the measured L2 gather probe (random 16-byte loads from an
+# L2-resident table).  The resource with the larger fraction is reported as the bound.
+OPS_PER_TEST = 7
 # Lanes of the integer ALU pipe per SM sub-partition.  ncu reports the ALU pipe at 61.4 %
 # of its peak while the SM issues 2.44 of 4 instructions per cycle: a 32-lane pipe would
 # need more ALU instructions than were issued in total, so the pipe is 16 lanes wide
@@ -112,7 +124,7 @@ def _source_hash():
     counters stay attached to the code they were taken on, not to its comments."""
     import re
     h = hashlib.sha256()
-    for f in ("qc_kernels.cu", "qc_device.cuh", "qc_internal.h"):
+    for f in ("qc_kernels.cu", "qc_main_kernel.cuh", "qc_device.cuh", "qc_internal.h"):
         with open(os.path.join(ROOT, "paper_2506_23809_gb300", "csrc", f), encoding="utf-8") as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
@@ -190,9 +202,21 @@ def _make_workload(name, world):
                                  counts=(kind, total * world), seed=spec["seed"])
 
 
-def _cpu_baseline(ints, s, spec, target_s, pairs_per_sample):
+def work_l2_bytes(w, n_elec, n_orb, elem_bytes, filter_log2w):
+    """Algorithmic L2 bytes of one local-energy launch from its work counts (see the table at
+    the top of this file)."""
+    o = n_elec // 2
+    v = n_orb // 2 - o
+    return (16 * w["scan_rows"] + 16 * w["probes"]
+            + (32 + elem_bytes * (1 + 3 * n_elec // 2)) * w["hits_single"]
+            + (32 + 2 * elem_bytes) * w["hits_same"] + (32 + elem_bytes) * w["hits_ab"]
+            + (48 + 8 * 2 * o * v) * w["samples"] + (4 << filter_log2w) * w["ctas"])
+
+
+def _cpu_baseline(ints, s, spec, target_s, pairs_per_sample, gpu_eloc=None):
     """The oracle, as it stands, on a bounded seeded sample of rows (each looks its
-    excitations up in the whole table), all host cores."""
+    excitations up in the whole table), all host cores.  With gpu_eloc, also the error of
+    the GPU's E_loc against the oracle's on those rows."""
     import numpy as np
     import oracle
     oracle.build()
@@ -200,24 +224,34 @@ def _cpu_baseline(ints, s, spec, target_s, pairs_per_sample):
     rng = np.random.default_rng(12345)
     perm = rng.permutation(s.n_u)
 
+    last = {}
+
     def run(rows, threads):
         sel = np.sort(perm[:rows])
         t = time.perf_counter()
-        oracle.eloc(ints.h, ints.eri, 0.0, spec["n_orb"], s.keys[sel], s.psi[sel], s.keys, s.psi,
-                    nthreads=threads)
-        return time.perf_counter() - t
+        e = oracle.eloc(ints.h, ints.eri, 0.0, spec["n_orb"], s.keys[sel], s.psi[sel], s.keys, s.psi,
+                        nthreads=threads)
+        dt = time.perf_counter() - t
+        last["sel"], last["eloc"] = sel, e
+        return dt
 
     probe = min(s.n_u, 4 * cores)
     t0 = run(probe, cores)
     rows = int(min(s.n_u, max(probe, probe * target_s / max(t0, 1e-6))))
     t1 = run(rows, cores)
+    err = None
+    if gpu_eloc is not None:
+        d = np.abs(gpu_eloc[last["sel"]] - last["eloc"])
+        err = {"rows": int(rows), "max_abs_ha": float(d.max()), "rms_abs_ha": float(np.sqrt((d ** 2).mean())),
+               "max_rel": float((d / np.maximum(1.0, np.abs(last["eloc"]))).max())}
     # one thread, on a sample sized for about a tenth of the all-core time
     rows1 = int(min(s.n_u, max(4, rows * 0.1 / cores)))
     t2 = run(rows1, 1)
-    return {"value": rows * pairs_per_sample / t1, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{rows} seeded random rows of the {s.n_u}-row table (all rows looked up in the "
-                      f"whole table), {t1:.1f} s on {cores} threads; single thread: {rows1} rows, {t2:.2f} s",
-            "samples_per_s": rows / t1, "value_1_thread": rows1 * pairs_per_sample / t2}
+    out = {"value": rows * pairs_per_sample / t1, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{rows} seeded random rows of the {s.n_u}-row table (all rows looked up in the "
+                     f"whole table), {t1:.1f} s on {cores} threads; single thread: {rows1} rows, {t2:.2f} s",
+           "samples_per_s": rows / t1, "value_1_thread": rows1 * pairs_per_sample / t2}
+    return out, err
 
 
 def run_reference(args):
@@ -301,23 +335,30 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     B.qc_eloc_reserve(h, n_rank, s.n_u)
 
-    def step():
-        B.qc_eloc_eval(h, keys, cnt, psi, tk, tp, eloc=eloc, stream=stream)
+    enqueue_s = []
 
+    def step():
+        t = time.perf_counter()
+        B.qc_eloc_eval(h, keys, cnt, psi, tk, tp, eloc=eloc, stream=stream)
+        enqueue_s.append(time.perf_counter() - t)
+
+    # the clock sampler starts before the warm-up, which keeps the GPU busy (no idle gap, so
+    # no clock ramp-up inside the timed region) and gives the sampler its first samples
+    sampler = ClockSampler(local)
+    sampler.start()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
+    enqueue_s.clear()
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    step_ms, main_ms, table_ms, red_ms = [], [], [], []
+    step_ms, main_ms, table_ms, red_ms, host_ms = [], [], [], [], []
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     t_wall = time.perf_counter()
     for k in range(args.steps):
+        t_h = time.perf_counter()
         flush.fill_(float(k))
         ev0.record(stream)
         step()
@@ -325,6 +366,7 @@ def run_ours(args):
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
         t3 = B.qc_eloc_timings(h)
+        host_ms.append(1e3 * (time.perf_counter() - t_h))
         table_ms.append(t3[0])
         main_ms.append(t3[1])
         red_ms.append(t3[2])
@@ -384,13 +426,16 @@ def run_ours(args):
         for _ in range(max(1, args.warmup)):
             e2e_step()
         torch.cuda.synchronize()
-        e_ms = []
+        e_ms, e_host = [], []
         for k in range(args.steps):
             flush.fill_(float(k))
+            stream.synchronize()
+            t_h = time.perf_counter()
             ev0.record(stream)
             e2e_step()
             ev1.record(stream)
-            ev1.synchronize()
+            ev1.synchronize()        # the caller can use E_loc from here on
+            e_host.append(time.perf_counter() - t_h)
             e_ms.append(ev0.elapsed_time(ev1))
         et = sum(e_ms) / 1e3
         if pg:
@@ -398,15 +443,23 @@ def run_ours(args):
             pg.all_reduce(v, op=pg.ReduceOp.MAX)
             et = float(v.item())
         e2e = {"value": pairs_all * args.steps / et, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * et / args.steps}
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * et / args.steps,
+               # host wall clock from the first copy's enqueue to E_loc usable on the host
+               "host_ms_per_step": 1e3 * statistics.median(e_host)}
 
-    # ---- roofline of the dominant kernel (the local-energy kernel) ----
+    # ---- roofline of the dominant kernel (the local-energy kernel), from counted work ----
     peaks, peak_src = _measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = props.multi_processor_count * 4 * ALU_LANES * sm_max * 1e6  # ALU pipe, ops/s
+    peak_ops = props.multi_processor_count * 4 * ALU_LANES * sm_max * 1e6  # ALU pipe, ops/s (derived)
     main_s = statistics.mean(main_ms) / 1e3
-    achieved = pairs_rank * OPS_PER_PAIR / main_s
+    B.qc_eloc_set_option(h, B.QC_OPT_COUNT_WORK, 1)
+    B.qc_eloc_eval(h, keys, cnt, psi, tk, tp, eloc=eloc, stream=stream)   # untimed: counts the work
+    work = B.qc_eloc_work(h)
+    B.qc_eloc_set_option(h, B.QC_OPT_COUNT_WORK, 0)
+    elem = 8 if prec == B.QC_FP64 else 4
+    ops = OPS_PER_TEST * work["tests"]
+    l2_bytes = work_l2_bytes(work, spec["n_elec"], spec["n_orb"], elem, cfg["filter_log2w"])
     traffic = issue = None
     profile_json = os.path.join(PROFILE_DIR, f"eloc_main_{args.workload}.json")
     if os.path.exists(profile_json):
@@ -415,34 +468,40 @@ def run_ours(args):
         if prof.get("source_hash") == _source_hash() and prof.get("workload") == args.workload:
             traffic = prof.get("dram_bytes_per_launch")
             issue = prof.get("issue_active_frac")
-    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
-                "frac": achieved / peak_ops, "traffic": traffic,
+    probe = {}
+    try:  # measured ceilings (probes of the library, after the timed region)
+        probe = B.qc_probe_peaks()
+    except Exception as ex:  # noqa: BLE001 -- a probe failure must not lose the bench line
+        probe = {"error": str(ex)}
+    l2_peak = probe.get("l2_gather_gbs")
+    alu = {"ops": ops, "achieved_gops": ops / main_s / 1e9, "peak_gops": peak_ops / 1e9,
+           "frac": ops / main_s / peak_ops,
+           "peak_basis": f"{props.multi_processor_count} SMs x 4 sub-partitions x {ALU_LANES} ALU lanes x "
+                         f"{sm_max:.0f} MHz ({peak_src} sm_max_mhz)",
+           "probe_gops": probe.get("alu_ops_per_s", 0.0) / 1e9 or None}
+    l2 = {"bytes": l2_bytes, "achieved_gbs": l2_bytes / main_s / 1e9, "peak_gbs": l2_peak,
+          "frac": (l2_bytes / main_s / 1e9 / l2_peak) if l2_peak else None,
+          "peak_basis": "measured: qc_probe_peaks random 16-byte loads from a 4 MB L2-resident table"}
+    use_l2 = l2["frac"] is not None and l2["frac"] > alu["frac"]
+    roofline = {"bound": "l2" if use_l2 else "alu",
+                "achieved": l2["achieved_gbs"] if use_l2 else alu["achieved_gops"],
+                "peak": l2["peak_gbs"] if use_l2 else alu["peak_gops"],
+                "unit": "GB/s" if use_l2 else "Gop/s",
+                "frac": l2["frac"] if use_l2 else alu["frac"], "traffic": traffic,
                 "kernel": {1: "eloc_main_kernel (unfiltered)", 2: "eloc_main_kernel (filtered)",
                            3: "eloc_main_kernel (filtered, lean lists)",
                            4: "eloc_main_kernel (sample-space join)",
                            5: "eloc_main_kernel (sample-space join, lean lists)"}.get(cfg["kernel"], "eloc_main_kernel"),
-                "ops_per_pair": OPS_PER_PAIR,
-                "peak_basis": f"{props.multi_processor_count} SMs x 4 sub-partitions x {ALU_LANES} ALU lanes x {sm_max:.0f} MHz "
-                              f"({peak_src} sm_max_mhz)",
-                "kernel_ms": 1e3 * main_s, "kernel_pairs_per_s": pairs_rank / main_s,
+                "kernel_ms": 1e3 * main_s, "counted_work": work, "alu": alu, "l2": l2,
+                "formula": "alu: 7 x tests; l2: bench.work_l2_bytes(counted_work); achieved = work / kernel_ms",
                 "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                # the yardstick credits every connected pair with the filter test's ALU
-                # operations; the join resolves most pairs by scanning table rows instead, so
-                # the kernel runs fewer operations than credited -- the measured share of issue
-                # slots (ncu, same kernel sources) is the utilisation beside it
+                # ncu's share of issue slots that issued (same kernel sources): the kernel is
+                # bound by issue and latency rather than by either unit
                 "issue_active_frac": issue}
-    try:  # measured ceilings beside the derived one (probes of the library, after the timed region)
-        probe = B.qc_probe_peaks()
-        roofline["alu_probe_gops"] = probe["alu_ops_per_s"] / 1e9
-        roofline["alu_probe_frac_of_peak"] = probe["alu_ops_per_s"] / peak_ops
-        roofline["l2_gather_probe_gbs"] = probe["l2_gather_gbs"]
-        # the candidates that reach the bucket table: 16 B each, per launch
-    except Exception as ex:  # noqa: BLE001 -- a probe failure must not lose the bench line
-        roofline["probe_error"] = str(ex)
 
-    cpu = None
+    cpu = err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline(ints, s, spec, args.cpu_seconds, pairs_per_sample)
+        cpu, err = _cpu_baseline(ints, s, spec, args.cpu_seconds, pairs_per_sample, eloc.cpu().numpy())
 
     clocks = sampler.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -460,6 +519,13 @@ def run_ours(args):
                          "reduce": statistics.mean(red_ms)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": _plain_launches(cfg, int(s.n_u)) * args.steps, "clocks": clocks, "wall_s_timed": wall,
+            # host wall clock of one timed step (flush, enqueue, wait, phase timings) and of the
+            # qc_eloc_eval call alone (argument checks, launch set-up, enqueue)
+            "host_ms_per_step": 1e3 * wall / args.steps, "host_ms_step_median": statistics.median(host_ms),
+            "host_ms_step_max": max(host_ms), "enqueue_ms": 1e3 * statistics.median(enqueue_s),
+            "error_vs_oracle": err,
+            "value_basis": "structural connected pairs: samples x pairs per sample (every S_z-conserving "
+                           "single and double), however the kernel resolves them",
             "hits_per_step": int(summ["n_hits"]), "status": int(summ["status"])}
     if rank == 0:
         print(json.dumps(line), flush=True)

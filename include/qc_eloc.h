@@ -122,6 +122,11 @@ typedef int qc_status;
                                    the excitations it replaces; 0 the default */
 #define QC_OPT_COUNT_WORK   12  /* 1: the local-energy kernel counts the work it does (read with
                                    qc_eloc_work); costs global atomics, so off (0) in timed runs */
+#define QC_OPT_WAIT_LIMIT   13  /* test hook: iteration limit of each CTA's first wait for its copy
+                                   of the Bloom filter (-1, the default: 2^24).  When it runs out
+                                   the CTA sets QC_FLAG_TIMEOUT, waits for the copy with the
+                                   default limit (so nothing is left in flight) and leaves without
+                                   evaluating samples; the summary's status is QC_ERR_TIMEOUT */
 
 typedef struct qc_eloc qc_eloc;
 
@@ -296,8 +301,9 @@ qc_status qc_eloc_grad(qc_eloc* handle, const double* eloc, const int64_t* count
  * and eri (K^4) in the layouts above, samples / counts / psi as for qc_eloc_eval, and
  * eloc (complex128[n_u]).  summary may be host or device memory, or NULL.  The library's
  * own working memory (hash index, filter, integral tables, counters, reduction partials)
- * lives in one file-scope device array of QC_STATIC_SCRATCH_MB (about 8.4 MB) that every
- * GPU loading this library holds until the process exits.
+ * lives in one file-scope device array of QC_STATIC_SCRATCH_MB (about 8.4 MB): a GPU holds
+ * it from the moment the library's device code is loaded there (with lazy module loading,
+ * the first call on that device) until the process exits.
  *
  * Limits: n_u <= QC_STATIC_MAX_SAMPLES and n_orb <= QC_STATIC_MAX_ORB; larger sizes
  * return QC_ERR_CAPACITY without touching the GPU.  Errors of this call are read with
@@ -416,6 +422,12 @@ qc_status qc_probe_peaks(double* alu_ops_per_s, double* l2_gather_gbs, void* str
  * buckets), hits that are single excitations, same-spin doubles, opposite-spin doubles,
  * CTAs that copied the filter}. */
 qc_status qc_eloc_work(qc_eloc* handle, uint64_t* work8);
+
+/* Test hook (no counterpart in the paper): the library's next `after` device allocations
+ * (handles, their workspaces, batches, gradient partials) succeed and the one after them
+ * fails as if the device were out of memory, so that error paths can be tested on the host
+ * without exhausting a shared GPU.  A negative value turns it off (the default).  Process-wide. */
+qc_status qc_test_fail_alloc(int64_t after);
 
 /* Launch shape of the last evaluation on this handle: {kernel (1 direct, 2 filtered,
  * 3 filtered with pair lists formed on the fly), grid CTAs, warps per CTA, unroll, dynamic

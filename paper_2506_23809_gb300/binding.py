@@ -26,6 +26,7 @@ QC_OPT_CHUNK_PAIRS = 9
 QC_OPT_JOIN = 10
 QC_OPT_SCAN_COST = 11
 QC_OPT_COUNT_WORK = 12
+QC_OPT_WAIT_LIMIT = 13
 WORK_FIELDS = ("samples", "scan_rows", "tests", "probes", "hits_single", "hits_same", "hits_ab", "ctas")
 QC_SRV_OPT_QUANTUM = 1
 QC_SRV_OPT_OLDEST_PCT = 2
@@ -92,6 +93,8 @@ def load_library(path: str = LIB_PATH):
     lib.qc_eloc_last_config.restype = i32
     lib.qc_eloc_work.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
     lib.qc_eloc_work.restype = i32
+    lib.qc_test_fail_alloc.argtypes = [i64]
+    lib.qc_test_fail_alloc.restype = i32
     lib.qc_eloc_eval_static.argtypes = [P, P, f64, i32, i32, P, P, P, i64, P, P, P]
     lib.qc_eloc_eval_static.restype = i32
     lib.qc_eloc_grad.argtypes = [P, P, P, i64, P, i64, P, P, P]
@@ -191,6 +194,12 @@ def qc_eloc_last_config(handle: QcHandle) -> dict:
     _check(load_library().qc_eloc_last_config(handle.ptr, c), handle.ptr)
     return dict(kernel=int(c[0]), grid=int(c[1]), warps=int(c[2]), unroll=int(c[3]), smem=int(c[4]),
                 filter_log2w=int(c[5]), chunks=int(c[6]))
+
+
+def qc_test_fail_alloc(after: int):
+    """Test hook: the library's next `after` device allocations succeed, the one after fails
+    as out-of-memory (negative: off)."""
+    _check(load_library().qc_test_fail_alloc(int(after)), None)
 
 
 def qc_eloc_work(handle: QcHandle) -> dict:
@@ -384,10 +393,18 @@ def qc_eloc_eval_static(h, eri, e_core: float, n_orb: int, n_elec: int, samples,
     Returns the status code; raises QcError with the library's message on failure."""
     import torch
     lib = load_library()
-    for name, t in (("h", h), ("eri", eri)):
+    K = int(n_orb) // 2
+    for name, t, n in (("h", h, K * K), ("eri", eri, K ** 4)):
         if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
             raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+        if t.numel() < n:
+            raise ValueError(f"{name} needs {n} entries for n_orb = {n_orb}")
     n_u = samples.shape[0]
+    for name, t in (("counts", counts), ("psi", psi), ("eloc", eloc)):
+        if t.shape[0] < n_u:
+            raise ValueError(f"{name} has fewer rows than samples ({t.shape[0]} < {n_u})")
+    if summary is not None and (summary.is_cuda or summary.numel() < ctypes.sizeof(qc_eloc_summary)):
+        raise ValueError("summary must be host memory of at least sizeof(qc_eloc_summary) bytes")
     if stream is None:
         stream = torch.cuda.current_stream(samples.device)
     st = lib.qc_eloc_eval_static(ctypes.c_void_p(h.data_ptr()), ctypes.c_void_p(eri.data_ptr()),
@@ -395,7 +412,7 @@ def qc_eloc_eval_static(h, eri, e_core: float, n_orb: int, n_elec: int, samples,
                                  _dptr(samples, "samples", (torch.int64, torch.uint64), 2),
                                  _dptr(counts, "counts", (torch.int64,)),
                                  _dptr(psi, "psi", (torch.complex128, torch.float64)), int(n_u),
-                                 ctypes.c_void_p(eloc.data_ptr()),
+                                 _dptr(eloc, "eloc", (torch.complex128,)),
                                  None if summary is None else ctypes.c_void_p(summary.data_ptr()),
                                  ctypes.c_void_p(stream.cuda_stream))
     if st != QC_OK:

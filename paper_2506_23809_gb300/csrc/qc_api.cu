@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -72,9 +73,20 @@ void free_dev(T*& p) {
 
 bool prepared_devices[64] = {};
 
+// qc_test_fail_alloc: allocations left before the injected failure (negative: none injected)
+std::atomic<long long> g_fail_after{-1};
+
 }  // namespace
 
 void qc::set_handleless_error(const std::string& msg) { g_create_error = msg; }
+
+cudaError_t qc::dev_alloc(void** p, size_t bytes) {
+    if (g_fail_after.load(std::memory_order_relaxed) >= 0 && g_fail_after.fetch_sub(1) == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;  // injected: nothing was asked of the device
+    }
+    return cudaMalloc(p, bytes);
+}
 
 extern "C" {
 
@@ -152,44 +164,44 @@ qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int 
         cudaError_t r_ = (call);                                    \
         if (r_ != cudaSuccess) return cleanup(cuda_fail(nullptr, r_, what)); \
     } while (0)
-    QC_TRY(cudaMalloc(&H->d_h, KK * sizeof(double)), "cudaMalloc h");
+    QC_TRY(qc::dev_alloc(&H->d_h, KK * sizeof(double)), "cudaMalloc h");
     QC_TRY(cudaMemcpy(H->d_h, h, KK * sizeof(double), cudaMemcpyHostToDevice), "copy h");
-    QC_TRY(cudaMalloc(&H->d_J, KK * sizeof(double)), "cudaMalloc J");
+    QC_TRY(qc::dev_alloc(&H->d_J, KK * sizeof(double)), "cudaMalloc J");
     QC_TRY(cudaMemcpy(H->d_J, J.data(), KK * sizeof(double), cudaMemcpyHostToDevice), "copy J");
-    QC_TRY(cudaMalloc(&H->d_X, KK * sizeof(double)), "cudaMalloc X");
+    QC_TRY(qc::dev_alloc(&H->d_X, KK * sizeof(double)), "cudaMalloc X");
     QC_TRY(cudaMemcpy(H->d_X, X.data(), KK * sizeof(double), cudaMemcpyHostToDevice), "copy X");
     if (precision == QC_FP64) {
-        QC_TRY(cudaMalloc(&H->d_Jt, K3 * sizeof(double)), "cudaMalloc Jt");
+        QC_TRY(qc::dev_alloc(&H->d_Jt, K3 * sizeof(double)), "cudaMalloc Jt");
         QC_TRY(cudaMemcpy(H->d_Jt, Jt.data(), K3 * sizeof(double), cudaMemcpyHostToDevice), "copy Jt");
-        QC_TRY(cudaMalloc(&H->d_Xt, K3 * sizeof(double)), "cudaMalloc Xt");
+        QC_TRY(qc::dev_alloc(&H->d_Xt, K3 * sizeof(double)), "cudaMalloc Xt");
         QC_TRY(cudaMemcpy(H->d_Xt, Xt.data(), K3 * sizeof(double), cudaMemcpyHostToDevice), "copy Xt");
-        QC_TRY(cudaMalloc(&H->d_Fref, 2 * KK * sizeof(double)), "cudaMalloc Fref");
+        QC_TRY(qc::dev_alloc(&H->d_Fref, 2 * KK * sizeof(double)), "cudaMalloc Fref");
         QC_TRY(cudaMemcpy(H->d_Fref, Fref.data(), 2 * KK * sizeof(double), cudaMemcpyHostToDevice), "copy Fref");
-        QC_TRY(cudaMalloc(&H->d_eri, K4 * sizeof(double)), "cudaMalloc eri");
+        QC_TRY(qc::dev_alloc(&H->d_eri, K4 * sizeof(double)), "cudaMalloc eri");
         QC_TRY(cudaMemcpy(H->d_eri, eri, K4 * sizeof(double), cudaMemcpyHostToDevice), "copy eri");
     } else {
         std::vector<float> h32(KK), e32(K4);
         for (size_t i = 0; i < KK; ++i) h32[i] = static_cast<float>(h[i]);
         for (size_t i = 0; i < K4; ++i) e32[i] = static_cast<float>(eri[i]);
-        QC_TRY(cudaMalloc(&H->d_h32, KK * sizeof(float)), "cudaMalloc h32");
+        QC_TRY(qc::dev_alloc(&H->d_h32, KK * sizeof(float)), "cudaMalloc h32");
         QC_TRY(cudaMemcpy(H->d_h32, h32.data(), KK * sizeof(float), cudaMemcpyHostToDevice), "copy h32");
         std::vector<float> jt32(K3), xt32(K3);
         for (size_t i = 0; i < K3; ++i) {
             jt32[i] = static_cast<float>(Jt[i]);
             xt32[i] = static_cast<float>(Xt[i]);
         }
-        QC_TRY(cudaMalloc(&H->d_Jt32, K3 * sizeof(float)), "cudaMalloc Jt32");
+        QC_TRY(qc::dev_alloc(&H->d_Jt32, K3 * sizeof(float)), "cudaMalloc Jt32");
         QC_TRY(cudaMemcpy(H->d_Jt32, jt32.data(), K3 * sizeof(float), cudaMemcpyHostToDevice), "copy Jt32");
-        QC_TRY(cudaMalloc(&H->d_Xt32, K3 * sizeof(float)), "cudaMalloc Xt32");
+        QC_TRY(qc::dev_alloc(&H->d_Xt32, K3 * sizeof(float)), "cudaMalloc Xt32");
         QC_TRY(cudaMemcpy(H->d_Xt32, xt32.data(), K3 * sizeof(float), cudaMemcpyHostToDevice), "copy Xt32");
-        QC_TRY(cudaMalloc(&H->d_eri32, K4 * sizeof(float)), "cudaMalloc eri32");
+        QC_TRY(qc::dev_alloc(&H->d_eri32, K4 * sizeof(float)), "cudaMalloc eri32");
         QC_TRY(cudaMemcpy(H->d_eri32, e32.data(), K4 * sizeof(float), cudaMemcpyHostToDevice), "copy eri32");
     }
-    QC_TRY(cudaMalloc(&H->d_T, 128 * sizeof(unsigned long long)), "cudaMalloc T");
+    QC_TRY(qc::dev_alloc(&H->d_T, 128 * sizeof(unsigned long long)), "cudaMalloc T");
     QC_TRY(cudaMemcpy(H->d_T, T.data(), 128 * sizeof(unsigned long long), cudaMemcpyHostToDevice), "copy T");
-    QC_TRY(cudaMalloc(&H->d_ctr, sizeof(qc::Counters)), "cudaMalloc counters");
+    QC_TRY(qc::dev_alloc(&H->d_ctr, sizeof(qc::Counters)), "cudaMalloc counters");
     QC_TRY(cudaMemset(H->d_ctr, 0, sizeof(qc::Counters)), "memset counters");
-    QC_TRY(cudaMalloc(&H->d_sum, sizeof(qc_eloc_summary)), "cudaMalloc summary");
+    QC_TRY(qc::dev_alloc(&H->d_sum, sizeof(qc_eloc_summary)), "cudaMalloc summary");
     if (H->device >= 0 && H->device < 64 && !prepared_devices[H->device]) {
         QC_TRY(qc::prepare_kernels(H->smem_optin), "cudaFuncSetAttribute");
         prepared_devices[H->device] = true;
@@ -304,6 +316,10 @@ qc_status qc_eloc_set_option(qc_eloc* H, int option, int64_t value) {
             H->opt_scan_cost = static_cast<int>(value);
             return QC_OK;
         case QC_OPT_COUNT_WORK: H->opt_count_work = value ? 1 : 0; return QC_OK;
+        case QC_OPT_WAIT_LIMIT:
+            if (value >= 0x7fffffff) return fail(H, QC_ERR_ARG, "QC_OPT_WAIT_LIMIT: -1 or 0..2^31-2");
+            H->opt_wait_limit = value < 0 ? 0 : static_cast<int>(value) + 1;
+            return QC_OK;
         case QC_OPT_GRID:
             if (value < 0 || value > (1 << 20)) return fail(H, QC_ERR_ARG, "QC_OPT_GRID: 0..2^20");
             H->opt_grid = static_cast<int>(value);
@@ -337,7 +353,7 @@ qc_status ensure_join(qc_eloc* H, long long n_table) {
     if (need > H->join_cap) {
         free_dev(H->d_join);
         H->join_cap = 0;
-        cudaError_t e = cudaMalloc(&H->d_join, need);
+        cudaError_t e = qc::dev_alloc(&H->d_join, need);
         if (e != cudaSuccess) return cuda_fail(H, e, "cudaMalloc join index");
         H->join_cap = need;
     }
@@ -350,7 +366,7 @@ qc_status ensure_workspace(qc_eloc* H, long long n_u, long long n_table, int fw)
     if (entries > H->slots_cap) {
         free_dev(H->d_slots);
         H->slots_cap = 0;
-        cudaError_t e = cudaMalloc(&H->d_slots, entries * sizeof(unsigned long long));
+        cudaError_t e = qc::dev_alloc(&H->d_slots, entries * sizeof(unsigned long long));
         if (e != cudaSuccess) return cuda_fail(H, e, "cudaMalloc hash table");
         H->slots_cap = entries;
     }
@@ -359,7 +375,7 @@ qc_status ensure_workspace(qc_eloc* H, long long n_u, long long n_table, int fw)
         if (se > H->sets_cap) {
             free_dev(H->d_sets);
             H->sets_cap = 0;
-            cudaError_t e = cudaMalloc(&H->d_sets, 2 * se * sizeof(unsigned long long));
+            cudaError_t e = qc::dev_alloc(&H->d_sets, 2 * se * sizeof(unsigned long long));
             if (e != cudaSuccess) return cuda_fail(H, e, "cudaMalloc spin-string sets");
             H->sets_cap = se;
         }
@@ -368,7 +384,7 @@ qc_status ensure_workspace(qc_eloc* H, long long n_u, long long n_table, int fw)
     if (words > H->filter_cap) {
         free_dev(H->d_filter);
         H->filter_cap = 0;
-        cudaError_t e = cudaMalloc(&H->d_filter, words * sizeof(uint32_t));
+        cudaError_t e = qc::dev_alloc(&H->d_filter, words * sizeof(uint32_t));
         if (e != cudaSuccess) return cuda_fail(H, e, "cudaMalloc filter");
         H->filter_cap = words;
     }
@@ -376,7 +392,7 @@ qc_status ensure_workspace(qc_eloc* H, long long n_u, long long n_table, int fw)
     if (nblk > H->part_cap) {
         free_dev(H->d_part);
         H->part_cap = 0;
-        cudaError_t e = cudaMalloc(&H->d_part, static_cast<size_t>(nblk) * 4 * sizeof(double));
+        cudaError_t e = qc::dev_alloc(&H->d_part, static_cast<size_t>(nblk) * 4 * sizeof(double));
         if (e != cudaSuccess) return cuda_fail(H, e, "cudaMalloc partials");
         H->part_cap = nblk;
     }
@@ -639,13 +655,14 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     ep.hit_list = reinterpret_cast<long long*>(out->hit_list);
     ep.hit_list_cap = out->hit_list != nullptr ? out->hit_list_cap : 0;
     if (H->opt_count_work) {
-        if (!H->d_work) QC_CHK(cudaMalloc(&H->d_work, sizeof(qc::WorkCounters)), "cudaMalloc work counters");
+        if (!H->d_work) QC_CHK(qc::dev_alloc(&H->d_work, sizeof(qc::WorkCounters)), "cudaMalloc work counters");
         QC_CHK(cudaMemsetAsync(H->d_work, 0, sizeof(qc::WorkCounters), s), "memset work counters");
         ep.work = H->d_work;
         H->work_stream = s;
         H->work_recorded = true;
     }
     ep.ctr = H->d_ctr;
+    ep.wait_limit = H->opt_wait_limit;
     ep.T = H->d_T;
     ep.mode = H->mode;
     ep.lean = cfg.lean;
@@ -656,13 +673,13 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
         if (recs > H->cpart_cap) {
             free_dev(H->d_cpart);
             H->cpart_cap = 0;
-            QC_CHK(cudaMalloc(&H->d_cpart, recs * sizeof(qc::ChunkRec)), "cudaMalloc chunk records");
+            QC_CHK(qc::dev_alloc(&H->d_cpart, recs * sizeof(qc::ChunkRec)), "cudaMalloc chunk records");
             H->cpart_cap = recs;
         }
         if (static_cast<size_t>(n_u) > H->cticket_cap) {
             free_dev(H->d_cticket);
             H->cticket_cap = 0;
-            QC_CHK(cudaMalloc(&H->d_cticket, static_cast<size_t>(n_u) * sizeof(unsigned)), "cudaMalloc chunk tickets");
+            QC_CHK(qc::dev_alloc(&H->d_cticket, static_cast<size_t>(n_u) * sizeof(unsigned)), "cudaMalloc chunk tickets");
             H->cticket_cap = static_cast<size_t>(n_u);
         }
         QC_CHK(cudaMemsetAsync(H->d_cticket, 0, static_cast<size_t>(n_u) * sizeof(unsigned), s), "memset tickets");
@@ -691,6 +708,11 @@ qc_status qc_eloc_timings(qc_eloc* H, float* ms3) {
         e = cudaEventElapsedTime(&ms3[i], H->ev[i], H->ev[i + 1]);
         if (e != cudaSuccess) return cuda_fail(H, e, "cudaEventElapsedTime");
     }
+    return QC_OK;
+}
+
+qc_status qc_test_fail_alloc(int64_t after) {
+    g_fail_after.store(after < 0 ? -1 : static_cast<long long>(after));
     return QC_OK;
 }
 

@@ -205,7 +205,7 @@ qc_status prepare(qc_batch* B) {
         B->d_arena = nullptr;
         B->arena_cap = 0;
         const size_t cap = align256(off + off / 2);
-        cudaError_t e = cudaMalloc(&B->d_arena, cap);
+        cudaError_t e = qc::dev_alloc(&B->d_arena, cap);
         if (e != cudaSuccess) return bcuda(B, e, "cudaMalloc batch arena");
         B->arena_cap = cap;
     }
@@ -229,7 +229,7 @@ qc_status prepare(qc_batch* B) {
             B->d_join = nullptr;
             B->join_cap = 0;
             const size_t cap = align256(jo + jo / 2);
-            cudaError_t e = cudaMalloc(&B->d_join, cap);
+            cudaError_t e = qc::dev_alloc(&B->d_join, cap);
             if (e != cudaSuccess) return bcuda(B, e, "cudaMalloc batch join index");
             B->join_cap = cap;
         }
@@ -419,11 +419,11 @@ cudaError_t batch_alloc(qc_batch* B, int n_mol) {
     B->d_key_off = nullptr;
     B->d_sums = nullptr;
     B->mol_cap = 0;
-    cudaError_t e = cudaMalloc(&B->d_mols, n_mol * sizeof(qc::MolParams));
-    if (e == cudaSuccess) e = cudaMalloc(&B->d_work, n_mol * sizeof(qc::MolWork));
-    if (e == cudaSuccess) e = cudaMalloc(&B->d_key_off, (n_mol + 1) * sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc(&B->d_sums, n_mol * sizeof(qc_eloc_summary));
-    if (e == cudaSuccess) e = cudaMalloc(&B->d_order, n_mol * sizeof(int));
+    cudaError_t e = qc::dev_alloc(&B->d_mols, n_mol * sizeof(qc::MolParams));
+    if (e == cudaSuccess) e = qc::dev_alloc(&B->d_work, n_mol * sizeof(qc::MolWork));
+    if (e == cudaSuccess) e = qc::dev_alloc(&B->d_key_off, (n_mol + 1) * sizeof(long long));
+    if (e == cudaSuccess) e = qc::dev_alloc(&B->d_sums, n_mol * sizeof(qc_eloc_summary));
+    if (e == cudaSuccess) e = qc::dev_alloc(&B->d_order, n_mol * sizeof(int));
     if (e == cudaSuccess) B->mol_cap = n_mol;
     return e;
 }

@@ -143,7 +143,7 @@ extern "C" qc_status qc_eloc_grad(qc_eloc* H, const double* eloc, const int64_t*
                 if (H->d_gpart) cudaFree(H->d_gpart);
                 H->d_gpart = nullptr;
                 H->gpart_cap = 0;
-                e = cudaMalloc(&H->d_gpart, need * sizeof(double));
+                e = qc::dev_alloc(&H->d_gpart, need * sizeof(double));
                 if (e == cudaSuccess) H->gpart_cap = need;
             }
             if (e == cudaSuccess) {

@@ -51,6 +51,7 @@ struct qc_eloc {
     int opt_join = 0;  // 0 auto, 1 off, 2 on (sample-space mode, filtered kernel)
     int opt_scan_cost = 0;  // 0 default, else 4 x the cost of a scanned row in enumerated pairs
     int opt_count_work = 0;  // QC_OPT_COUNT_WORK
+    int opt_wait_limit = 0;  // QC_OPT_WAIT_LIMIT + 1 (0: the kernel's default)
     qc::WorkCounters* d_work = nullptr;
     cudaStream_t work_stream = nullptr;  // stream of the last evaluation that counted work
     bool work_recorded = false;

@@ -106,6 +106,8 @@ struct EvalParams {
     long long* hit_list;          //   phase * (row + 1) of every hit
     long long hit_list_cap;
     WorkCounters* work;           // QC_OPT_COUNT_WORK (NULL: off)
+    int wait_limit;               // QC_OPT_WAIT_LIMIT + 1 for the first filter-copy wait (0: the default)
+    int pad2_;
     Counters* ctr;
     const unsigned long long* T;  // 128 entries of the linear key hash
     int mode;                     // 0 SAMPLE, 1 FULL
@@ -238,5 +240,12 @@ cudaError_t launch_join_batch(const MolParams* mols, const unsigned* slot_base, 
 cudaError_t exclusive_scan_u32(unsigned* a, long long n, unsigned* sums, cudaStream_t s);
 // message returned by qc_eloc_last_error(NULL) on this thread (qc_api.cu)
 void set_handleless_error(const std::string& msg);
+// Device allocations of the handle, batch and gradient paths go through here, so that a test
+// can make one of them fail on the host (qc_test_fail_alloc) and check the error paths.
+cudaError_t dev_alloc(void** p, size_t bytes);
+template <typename T>
+inline cudaError_t dev_alloc(T** p, size_t bytes) {
+    return dev_alloc(reinterpret_cast<void**>(p), bytes);
+}
 
 }  // namespace qc

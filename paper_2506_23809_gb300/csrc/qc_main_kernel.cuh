@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ 
     fill_cta_tables(sp, ep.T, smem);
     if constexpr (FILTER) {
         bool ready = false;
-        for (unsigned it = 0; it < kWaitLimit; ++it) {
+        const unsigned limit = ep.wait_limit > 0 ? static_cast<unsigned>(ep.wait_limit - 1) : kWaitLimit;
+        for (unsigned it = 0; it < limit; ++it) {
             if (mbar_try_wait(bar, 0)) {
                 ready = true;
                 break;

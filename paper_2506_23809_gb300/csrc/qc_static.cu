@@ -7,8 +7,10 @@
 // request loop that must never block on the allocator.  Such a caller hands in device
 // buffers for every input and output; the library supplies the rest from the array below.
 //
-// The array (kStaticBytes, about 8.4 MB) is created by the CUDA runtime on every GPU that
-// loads this library and stays there until the process exits.  Every call shares it, so
+// The array (kStaticBytes, about 8.4 MB) is created by the CUDA runtime on a GPU when the
+// library's device code is loaded there -- with lazy module loading (the default since CUDA
+// 12.2) at the first call on that device that needs it, which the set-up below forces -- and
+// it stays there until the process exits.  Every call shares it, so
 // two calls that overlap on the GPU (different streams, or different host threads) race
 // on it; the array keeps whatever the last call left, and each call clears the parts that
 // must start at zero.

@@ -41,7 +41,7 @@ def test_source_hash_ignores_comments_not_code(tmp_path, monkeypatch):
     b = _bench()
     csrc = tmp_path / "paper_2506_23809_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    for f in ("qc_kernels.cu", "qc_device.cuh", "qc_internal.h"):
+    for f in ("qc_kernels.cu", "qc_main_kernel.cuh", "qc_device.cuh", "qc_internal.h"):
         shutil.copy(os.path.join(ROOT, "paper_2506_23809_gb300", "csrc", f), csrc / f)
     monkeypatch.setattr(b, "ROOT", str(tmp_path))
     h0 = b._source_hash()
@@ -51,3 +51,19 @@ def test_source_hash_ignores_comments_not_code(tmp_path, monkeypatch):
     assert b._source_hash() == h0
     dev.write_text(text.replace("kCandCap = 160", "kCandCap = 192", 1))
     assert b._source_hash() != h0
+
+
+def test_work_l2_bytes_formula():
+    """The roofline's algorithmic bytes from counted work, term by term (N=52, 14 e: o = 7,
+    v = 19, 2 o v = 266 spin-string lookups per sample; FP64 elements)."""
+    b = _bench()
+    zero = dict(samples=0, scan_rows=0, tests=0, probes=0, hits_single=0, hits_same=0, hits_ab=0, ctas=0)
+    assert b.work_l2_bytes(zero, 14, 52, 8, 14) == 0
+    cases = [("scan_rows", 16), ("probes", 16), ("hits_single", 32 + 8 * 22), ("hits_same", 48), ("hits_ab", 40),
+             ("samples", 48 + 8 * 266), ("ctas", 4 << 14), ("tests", 0)]
+    for k, per in cases:
+        w = dict(zero)
+        w[k] = 3
+        assert b.work_l2_bytes(w, 14, 52, 8, 14) == 3 * per, k
+    w = dict(zero, hits_single=1, hits_same=1, hits_ab=1)
+    assert b.work_l2_bytes(w, 20, 76, 4, 15) == (32 + 4 * 31) + (32 + 8) + (32 + 4)
