@@ -407,8 +407,8 @@ __device__ __forceinline__ ulonglong2 excite(unsigned orbs, ulonglong2 x, unsign
 }
 
 // Add one hit: <x|H|x'> (phase included) times psi(x') [FP64], or times psi(x')/psi(x)
-// [FP32, compensated], plus the diagnostics of the exported phase convention.
-template <int PREC>
+// [FP32, compensated], plus (DIAG) the per-sample digests of the exported phase convention.
+template <int PREC, bool DIAG>
 __device__ __forceinline__ void add_hit(double h64, float h32, long long row, bool sneg, double2 pp,
                                         float2 ip32, Acc& acc) {
     if (PREC == QC_FP64) {
@@ -422,15 +422,17 @@ __device__ __forceinline__ void add_hit(double h64, float h32, long long row, bo
         two_sum_acc(acc.si, acc.ci, __fmul_rn(h32, ri));
     }
     acc.hits++;
-    acc.rowsum += static_cast<unsigned long long>(row + 1);
-    acc.signsum += sneg ? -(row + 1) : (row + 1);
+    if (DIAG) {
+        acc.rowsum += static_cast<unsigned long long>(row + 1);
+        acc.signsum += sneg ? -(row + 1) : (row + 1);
+    }
 }
 
 // Stage 2 common part: issue the loads of the stored key and psi of a stage-1 row, let
 // `element` load the integrals meanwhile, then confirm the key (exact walk on a
 // fingerprint collision) and add the hit.  Returns phase * (row + 1) of the hit added, or
 // 0 when the key is not in the table.
-template <int PREC, typename Element>
+template <int PREC, bool DIAG, typename Element>
 __device__ __forceinline__ long long verify_and_add(uint2 e, ulonglong2 x, unsigned long long hx,
                                                     const TableParams& tp, int mode,
                                                     const unsigned long long* __restrict__ T64,
@@ -450,7 +452,7 @@ __device__ __forceinline__ long long verify_and_add(uint2 e, ulonglong2 x, unsig
         else if (mode == QC_FULL) acc.missing++;
     }
     if (row < 0) return 0;
-    add_hit<PREC>(h64, h32, row, sneg, pp, ip32, acc);
+    add_hit<PREC, DIAG>(h64, h32, row, sneg, pp, ip32, acc);
     return sneg ? -(row + 1) : row + 1;
 }
 
@@ -799,7 +801,7 @@ __device__ __forceinline__ void write_sample(const EvalParams& ep, long long s, 
 // excitation chunks per sample (C > 1) each chunk stores its warp sums; the warp that
 // finishes the last chunk of the sample adds the C records in chunk order (the result does
 // not depend on which warp finishes last) and writes the outputs.
-template <int PREC>
+template <int PREC, bool DIAG, bool FILTER>
 __device__ __forceinline__ void sample_finish(const EvalParams& ep, long long s, int lane,
                                               double ediag, double2 psix, Acc& acc, int c = 0, int C = 1) {
     double sre, sim;
@@ -811,9 +813,11 @@ __device__ __forceinline__ void sample_finish(const EvalParams& ep, long long s,
         sim = warp_sum(static_cast<double>(acc.si) + static_cast<double>(acc.ci));
     }
     const unsigned long long hits = warp_sum_u64(acc.hits);
-    const unsigned long long rows = warp_sum_u64(acc.rowsum);
-    const long long sgn = static_cast<long long>(warp_sum_u64(static_cast<unsigned long long>(acc.signsum)));
-    const unsigned long long miss = warp_sum_u64(acc.missing);
+    // the digests exist in the diagnostic kernels only; missing x' only without the filter
+    // (the accurate-energy kernel)
+    const unsigned long long rows = DIAG ? warp_sum_u64(acc.rowsum) : 0ULL;
+    const long long sgn = DIAG ? static_cast<long long>(warp_sum_u64(static_cast<unsigned long long>(acc.signsum))) : 0LL;
+    const unsigned long long miss = FILTER ? 0ULL : warp_sum_u64(acc.missing);
     if (lane != 0) return;
     if (C <= 1) {
         write_sample<PREC>(ep, s, ediag, psix, sre, sim, hits, rows, sgn, miss);
@@ -884,7 +888,21 @@ constexpr int kCandCap = 160;  // >= 31 + 32 * 4 (the largest U with a single fl
 constexpr size_t kWarpQueues = 4 * kCandCap + 64 * 8;  // candidate queue + hit queue
 
 constexpr int kSingleCap = 64;  // join: the hit queue of scanned singles (uint2)
-constexpr size_t kOccBytes = 288;  // per warp: occupation lists (4 x 64 B), reference masks (32 B)
+// The current sample's constants, kept in the warp's shared memory rather than registers (the
+// main loop reads them only in its hit and finish stages).
+struct WarpSample {
+    ulonglong2 x;             // the sample
+    ulonglong2 px;            // prefix parity of x (the phases of its excitations)
+    double2 psix;             // psi(x)
+    unsigned long long hx;    // linear hash of x
+    double ediag;             // <x|H|x>
+    float2 ip32;              // 1/psi(x) in FP32 (precision form)
+    unsigned long long pad;
+};
+constexpr size_t kOffWarpSample = 288;
+// per warp: occupation lists (4 x 64 B), reference masks (32 B), the sample's constants
+constexpr size_t kOccBytes = kOffWarpSample + sizeof(WarpSample);
+static_assert(kOccBytes % 16 == 0, "warp regions stay 16-byte aligned");
 __host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filter, bool lean = false,
                                                   bool join = false) {
     // hash lists (u32) and, for the two single lists, their compaction maps (u16)
@@ -947,8 +965,21 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         dref[2] = Bs & ~sp.refB;
         dref[3] = sp.refB & ~Bs;
     }
-    const double2 psix = ep.psi[s];
-    const float2 ip32 = inv_psi32(psix);
+    // the sample's constants go to the warp's shared memory: the hit and finish stages read
+    // them there, so the enumeration and scan states keep their registers
+    WarpSample* wsp = reinterpret_cast<WarpSample*>(wl + kOffWarpSample);
+    if (lane == 0) {
+        WarpSample w;
+        w.x = x;
+        w.px = prefix_parity(x);
+        w.psix = ep.psi[s];
+        w.hx = hx;
+        w.ediag = ediag;
+        w.ip32 = inv_psi32(w.psix);
+        w.pad = 0ULL;
+        *wsp = w;
+    }
+    __syncwarp();
     Acc acc{};
     int qn = 0, nh = 0;
     // sample-space join: short groups of table rows are scanned (the scan state, first phase
@@ -972,13 +1003,17 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         __syncwarp();
         if (FILTER && v) e.x = decode(e.x, sp, wl, smem, IA, IB);
         long long ent = 0;
-        if (v)
-            ent = verify_and_add<PREC>(e, x, hx, tp, ep.mode, T64, ip32, acc, [&](double& h64, float& h32, bool& sneg) {
+        if (v) {
+            const ulonglong2 xs = wsp->x, px = wsp->px;
+            ent = verify_and_add<PREC, DIAG>(e, xs, wsp->hx, tp, ep.mode, T64,
+                                             PREC == QC_FP64 ? make_float2(0.f, 0.f) : wsp->ip32, acc,
+                                             [&](double& h64, float& h32, bool& sneg) {
                 if ((e.x >> 16) == 0xFFFFu)
-                    single_element<PREC>(e.x, prefix_parity(x), sp, wl, dref, h64, h32, sneg);
+                    single_element<PREC>(e.x, px, sp, wl, dref, h64, h32, sneg);
                 else
-                    double_element<PREC>(e.x, prefix_parity(x), sp, h64, h32, sneg);
+                    double_element<PREC>(e.x, px, sp, h64, h32, sneg);
             });
+        }
         if (DIAG && ep.hit_list != nullptr) list_hits(ep, s, ent, lane);
         if (DIAG && ep.work != nullptr) {
             const bool sgl = (e.x >> 16) == 0xFFFFu;
@@ -1135,12 +1170,11 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     int cls = -1, oo = 0, n1 = 0, io = 0, n2 = 0, u0 = 0, w0 = 0;
     bool done = false, need_class = true, need_outer = true;
     bool pairs = false;  // lean layout, same-spin doubles: list entries are formed from pairs
-    // outer hash values and their copies shifted for the filter word offset (>> 3): XOR
-    // commutes with the shift, so the offset costs one LOP3 per test
-    uint32_t hu[U], hu3[U];
+    // outer hash values (the low 32 bits of x's hash XOR the outer entry)
+    uint32_t hu[U];
     unsigned umask = 0;
 #pragma unroll
-    for (int k = 0; k < U; ++k) hu[k] = hu3[k] = 0u;
+    for (int k = 0; k < U; ++k) hu[k] = 0u;
     bool scanning = join;
     unsigned sbase = 0u;  // next row of the current scan chunk
     while (true) {
@@ -1260,7 +1294,6 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                                 }
                             }
                             hu[k] = hx32 ^ e;
-                            hu3[k] = hu[k] >> 3;
                         }
                         umask |= (v ? 1u : 0u) << k;
                     }
@@ -1285,15 +1318,16 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                             hw = H[io + w];
                         }
                     }
-                    const uint32_t hw3 = hw >> 3;
                     const unsigned ccode = cbase | static_cast<unsigned>(w);
 #pragma unroll
                     for (int k = 0; k < U; ++k) {
                         bool pass;
                         if (FILTER) {
-                            const uint32_t word = *reinterpret_cast<const uint32_t*>(
-                                reinterpret_cast<const unsigned char*>(filt) + ((hu3[k] ^ hw3) & wmask4));
+                            // the hash's low bits g pick the filter word (bits 5.., a byte offset
+                            // of g >> 3 masked to whole words) and its three bits
                             const uint32_t g = hu[k] ^ hw;
+                            const uint32_t word = *reinterpret_cast<const uint32_t*>(
+                                reinterpret_cast<const unsigned char*>(filt) + ((g >> 3) & wmask4));
                             const uint32_t t = __funnelshift_r(word, word, g) &
                                                __funnelshift_r(word, word, g >> 27) &
                                                __funnelshift_r(word, word, g >> 22);
@@ -1357,7 +1391,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     } else {
                         item = decode(code, sp, wl, smem, IA, IB);
                         unsigned long long h;
-                        excite(item, x, hx, T64, h);
+                        excite(item, wsp->x, wsp->hx, T64, h);
                         g = static_cast<unsigned>(h);
                     }
                     row = probe_fp(g, tp);
@@ -1374,7 +1408,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         }
         if (done) break;
     }
-    sample_finish<PREC>(ep, s, lane, ediag, psix, acc, c, C);
+    sample_finish<PREC, DIAG, FILTER>(ep, s, lane, wsp->ediag, wsp->psix, acc, c, C);
     __syncwarp();
 }
 

@@ -62,8 +62,11 @@ cudaError_t launch_build_table(const TableParams& tp, int n_orb, int na, int nb,
 cudaError_t launch_eloc_main(const SysParams& sp, const TableParams& tp, const EvalParams& ep,
                              const LaunchCfg& c, cudaStream_t s) {
     if (ep.n_u <= 0) return cudaSuccess;
-    // hit lists or work counters asked for: the diagnostic instantiations (qc_kernels_diag.cu)
-    if (ep.hit_list != nullptr || ep.work != nullptr) return launch_eloc_main_diag(sp, tp, ep, c, s);
+    // per-sample digests, hit lists or work counters asked for: the diagnostic instantiations
+    // (qc_kernels_diag.cu)
+    if (ep.hit_count != nullptr || ep.hit_rowsum != nullptr || ep.hit_signsum != nullptr || ep.hit_list != nullptr ||
+        ep.work != nullptr)
+        return launch_eloc_main_diag(sp, tp, ep, c, s);
     return launch_main_variant<false>(sp, tp, ep, c, s);
 }
 

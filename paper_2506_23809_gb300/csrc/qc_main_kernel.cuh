@@ -12,7 +12,7 @@
 namespace qc {
 
 template <int PREC, int U, bool FILTER, int LEAN, bool JOIN, bool DIAG>
-__global__ void __launch_bounds__(640) eloc_main_kernel(const __grid_constant__ SysParams sp,
+__global__ void __launch_bounds__(32 * kFilteredMaxWarps) eloc_main_kernel(const __grid_constant__ SysParams sp,
                                                         const __grid_constant__ TableParams tp,
                                                         const __grid_constant__ EvalParams ep) {
     static_assert(31 + 32 * U <= kCandCap, "candidate queue too small for U");
