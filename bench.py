@@ -72,10 +72,11 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--form", default="plain", choices=["plain", "batched", "serve", "grad", "dedup", "full"],
+    p.add_argument("--form", default="plain", choices=["plain", "batched", "serve", "grad", "dedup", "full", "sweep"],
                    help="plain: one molecule per step (the default benchmark); batched: many "
                         "molecules in one persistent launch; serve: Poisson request arrivals")
     p.add_argument("--n-mol", type=int, default=64, help="batched form: molecules")
+    p.add_argument("--systems", default="", help="sweep form: comma-separated subset of the paper's systems")
     p.add_argument("--n-par", type=int, default=4096, help="grad form: parameters (columns of d ln Psi*)")
     p.add_argument("--chunk", type=int, default=10000, help="full form: samples per export/apply chunk")
     p.add_argument("--requests", type=int, default=48, help="serve form: requests")
@@ -903,6 +904,91 @@ def run_full(args):
     return 0
 
 
+def run_sweep(args):
+    """The paper's molecular shapes (N2, PH3, LiCl of Table I; Fe2S2, H50, C6H6 of Sec. IV-B)
+    with seeded synthetic integrals and rank-weighted samples: one plain step per system
+    (FP64, the library's default launch), timed like the default benchmark, beside the oracle
+    on the host cores over a bounded sample of rows.  One JSON line per system, then a
+    summary line."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2506_23809_gb300 import binding as B
+    from paper_2506_23809_gb300 import build
+    from paper_2506_23809_gb300 import inputs as I
+    build.build()
+    B.load_library()
+    oracle.build()
+    torch.cuda.set_device(0)
+    prec = B.QC_FP64 if args.precision == "fp64" else B.QC_FP32_COMP
+    cores = len(os.sched_getaffinity(0))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows_out = []
+    names = [n for n, _, _ in I.PAPER_SYSTEMS] if not args.systems else args.systems.split(",")
+    for name in names:
+        spec, ints, s = I.paper_system_workload(name)
+        h = B.qc_eloc_create(ints.h, ints.eri, 0.0, spec["n_orb"], spec["n_elec"], prec)
+        B.qc_eloc_set_option(h, B.QC_OPT_TIMING, 1)
+        kd = B.keys_to_tensor(s.keys)
+        cd = torch.from_numpy(s.counts).cuda()
+        pd = torch.from_numpy(s.psi).cuda()
+        el = torch.empty(s.n_u, dtype=torch.complex128, device="cuda")
+        B.qc_eloc_reserve(h, s.n_u, s.n_u)
+        for _ in range(args.warmup):
+            B.qc_eloc_eval(h, kd, cd, pd, eloc=el, stream=stream)
+        torch.cuda.synchronize()
+        ms, main = [], []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            B.qc_eloc_eval(h, kd, cd, pd, eloc=el, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            main.append(B.qc_eloc_timings(h)[1])
+        summ = B.qc_eloc_summary_read(h, stream)
+        cfg = B.qc_eloc_last_config(h)
+        P = B.qc_eloc_pairs_per_sample(h)
+        got = el.cpu().numpy()
+        B.qc_eloc_destroy(h)
+        step_s = statistics.mean(ms) / 1e3
+        # the oracle on a bounded seeded sample of rows (each looked up in the whole table)
+        rng = np.random.default_rng(spec["seed"])
+        n_cpu = int(min(s.n_u, max(2 * cores, args.cpu_seconds * 3e8 / max(P, 1) / 4)))
+        if args.no_cpu_baseline:
+            n_cpu = 2
+        sel = np.sort(rng.choice(s.n_u, n_cpu, replace=False))
+        t = time.perf_counter()
+        want = oracle.eloc(ints.h, ints.eri, 0.0, spec["n_orb"], s.keys[sel], s.psi[sel], s.keys, s.psi,
+                           nthreads=cores)
+        t_cpu = time.perf_counter() - t
+        err = np.abs(got[sel] - want) / np.maximum(1.0, np.abs(want))
+        line = {"metric": METRIC, "form": "sweep", "system": name, "value": s.n_u * P / step_s, "unit": UNIT,
+                "samples_per_s": s.n_u / step_s, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * step_s, "main_ms": statistics.mean(main), "higher_is_better": True,
+                "dtype": "f64" if prec == B.QC_FP64 else "f32+f64",
+                "data": "synthetic (seeded integrals of the system's size, rank-weighted unique samples)",
+                "config": {"workload": f"paper_shape_{name}", "n_orb": spec["n_orb"], "n_elec": spec["n_elec"],
+                           "n_u": s.n_u, "pairs_per_sample": P, "launch": cfg,
+                           "l2": "256 MB buffer written between timed steps"},
+                "hits_per_step": int(summ["n_hits"]), "status": int(summ["status"]),
+                "max_rel_err_vs_oracle": float(err.max()),
+                "cpu_baseline": {"value": n_cpu * P / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "samples_per_s": n_cpu / t_cpu,
+                                 "sample": f"{n_cpu} seeded random rows of the {s.n_u}-row table, {t_cpu:.1f} s"}}
+        rows_out.append(line)
+        print(json.dumps(line), flush=True)
+    print(json.dumps({"form": "sweep", "summary": [
+        {"system": r["system"], "n_orb": r["config"]["n_orb"], "n_elec": r["config"]["n_elec"],
+         "n_u": r["config"]["n_u"], "ms_per_step": r["ms_per_step"], "samples_per_s": r["samples_per_s"],
+         "pairs_per_s": r["value"], "oracle_pairs_per_s": r["cpu_baseline"]["value"],
+         "max_rel_err": r["max_rel_err_vs_oracle"]} for r in rows_out]}), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -917,6 +1003,8 @@ def main():
         return run_dedup(args)
     if args.form == "full":
         return run_full(args)
+    if args.form == "sweep":
+        return run_sweep(args)
     return run_ours(args)
 
 

@@ -26,7 +26,7 @@ __all__ = [
     "Integrals", "SampleSet", "make_integrals", "aufbau_key", "pack_occupations",
     "sort_keys", "sector_keys", "uniform_samples", "rank_weighted_samples",
     "multinomial_counts", "zipf_counts", "lognormal_psi", "WORKLOADS", "make_workload",
-    "batched_molecule_specs", "serving_request_specs",
+    "batched_molecule_specs", "serving_request_specs", "PAPER_SYSTEMS", "paper_system_workload",
 ]
 
 
@@ -282,6 +282,28 @@ WORKLOADS = {
     "n76_e20_u200k": dict(n_orb=76, n_elec=20, rank=76, n_u=200_000, sampler="rank",
                           counts=("zipf", 20_000_000), seed=7601),
 }
+
+
+# The paper's molecular shapes (spin orbitals, electrons): N2, PH3 and LiCl of Table I; Fe2S2,
+# H50 and C6H6 of Sec. IV-B (C6H6's electron count is not given: half filling).  Their
+# integrals are not available; each gets seeded synthetic integrals of its size (rank N), and
+# up to 1e5 rank-weighted unique samples -- at most half of a small sector.
+PAPER_SYSTEMS = [("N2", 20, 14), ("PH3", 24, 18), ("LiCl", 28, 20), ("Fe2S2", 40, 30), ("H50", 100, 50),
+                 ("C6H6", 120, 60)]
+
+
+def paper_system_workload(name: str, n_u_max: int = 100_000):
+    """(spec dict, Integrals, SampleSet) of one paper-shaped system: Zipf counts summing to
+    100 per sample, lognormal complex psi."""
+    n_orb, n_elec = {n: (a, b) for n, a, b in PAPER_SYSTEMS}[name]
+    K, o = n_orb // 2, n_elec // 2
+    n_u = min(n_u_max, math.comb(K, o) ** 2 // 2)
+    seed = 9000 + n_orb
+    ints = make_integrals(K, n_orb, seed)
+    keys = rank_weighted_samples(K, o, o, n_u, seed=seed + 1)
+    s = SampleSet(keys=keys, counts=zipf_counts(n_u, 100 * n_u, seed + 2), psi=lognormal_psi(n_u, seed + 3),
+                  meta=dict(name=name))
+    return dict(name=name, n_orb=n_orb, n_elec=n_elec, n_u=n_u, seed=seed), ints, s
 
 
 def make_workload(name: str = None, *, n_orb: int = None, n_elec: int = None, rank: int = None,
