@@ -122,6 +122,10 @@ typedef int qc_status;
                                    the excitations it replaces; 0 the default */
 #define QC_OPT_COUNT_WORK   12  /* 1: the local-energy kernel counts the work it does (read with
                                    qc_eloc_work); costs global atomics, so off (0) in timed runs */
+#define QC_OPT_ALPHA_SLOTS  14  /* join: slots of the per-warp alpha single list (the alpha' groups
+                                   too long to scan); 0 auto (all alpha singles, or fewer when that
+                                   fits more warps), else that many (at least 1): a sample with more
+                                   long alpha' groups enumerates them in segments */
 #define QC_OPT_WAIT_LIMIT   13  /* test hook: iteration limit of each CTA's first wait for its copy
                                    of the Bloom filter (-1, the default: 2^24).  When it runs out
                                    the CTA sets QC_FLAG_TIMEOUT, waits for the copy with the

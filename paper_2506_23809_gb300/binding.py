@@ -27,6 +27,7 @@ QC_OPT_JOIN = 10
 QC_OPT_SCAN_COST = 11
 QC_OPT_COUNT_WORK = 12
 QC_OPT_WAIT_LIMIT = 13
+QC_OPT_ALPHA_SLOTS = 14
 WORK_FIELDS = ("samples", "scan_rows", "tests", "probes", "hits_single", "hits_same", "hits_ab", "ctas")
 QC_SRV_OPT_QUANTUM = 1
 QC_SRV_OPT_OLDEST_PCT = 2

@@ -316,6 +316,10 @@ qc_status qc_eloc_set_option(qc_eloc* H, int option, int64_t value) {
             H->opt_scan_cost = static_cast<int>(value);
             return QC_OK;
         case QC_OPT_COUNT_WORK: H->opt_count_work = value ? 1 : 0; return QC_OK;
+        case QC_OPT_ALPHA_SLOTS:
+            if (value < 0 || value > 4096) return fail(H, QC_ERR_ARG, "QC_OPT_ALPHA_SLOTS: 0..4096");
+            H->opt_alpha_slots = static_cast<int>(value);
+            return QC_OK;
         case QC_OPT_WAIT_LIMIT:
             if (value >= 0x7fffffff) return fail(H, QC_ERR_ARG, "QC_OPT_WAIT_LIMIT: -1 or 0..2^31-2");
             H->opt_wait_limit = value < 0 ? 0 : static_cast<int>(value) + 1;
@@ -413,7 +417,7 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
     // build, a few microseconds per launch, outweighs what it saves); built with U = 4
     // (its sort keys are 32-bit: both sets' slots and the sentinel below 2^32)
     const bool join = kernel == 2 && H->mode == QC_SAMPLE && H->opt_prefilter && H->na > 0 && H->nb > 0 &&
-                      table_buckets(n_table) <= (1ULL << 30) &&
+                      n_table > 0 && table_buckets(n_table) <= (1ULL << 30) &&
                       (H->opt_join == 2 || (H->opt_join == 0 && n_table >= qc::kJoinMinRows));
     if (kernel == 2) {
         // filter sized for ~16 bits per key, 2^10..2^15 words; then as many warps as fit,
@@ -428,18 +432,24 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
             want = ceil_log2(static_cast<unsigned long long>(std::max<long long>(n_table, 1)) / 2 + 1);
             want = std::min(15, std::max(10, want));
         }
-        int best_fw = 0, best_w = 0, best_lean = 0;
+        int best_fw = 0, best_w = 0, best_lean = 0, best_acap = 0;
+        // with the join the alpha list may get fewer slots than alpha singles (filled in
+        // segments) when that fits more warps; the full list on a tie
+        const int acaps[3] = {H->opt_alpha_slots, 64, 32};
+        for (int ai = 0; ai < (join ? (H->opt_alpha_slots ? 1 : 3) : 1); ++ai)
         for (int ln = 0; ln < 2; ++ln) {
             if ((H->opt_lean == 1 && ln == 1) || (H->opt_lean == 2 && ln == 0)) continue;
-            const size_t wb =
-                qc::filtered_smem_bytes(sp, 1, want, ln, join) - qc::filtered_smem_bytes(sp, 0, want, ln, join);
+            const int acap = acaps[ai];
+            if (acap > 0 && acap >= sp.nsa) continue;
+            const size_t wb = qc::filtered_smem_bytes(sp, 1, want, ln, join, acap) -
+                              qc::filtered_smem_bytes(sp, 0, want, ln, join, acap);
             int f = want, w = 0;
             if (join && H->opt_fw == 0) {
                 const int min_f = std::min(want, std::max(10, ceil_log2(static_cast<unsigned long long>(
                                                                    std::max<long long>(n_table, 1)) * 5 / 32 + 1)));
                 int bf = 0, bw = 0;
                 for (int g = want; g >= min_f; --g) {
-                    const size_t base = qc::filtered_smem_bytes(sp, 0, g, ln, join);
+                    const size_t base = qc::filtered_smem_bytes(sp, 0, g, ln, join, acap);
                     if (base + wb > H->smem_optin) continue;
                     const int fit = static_cast<int>((H->smem_optin - base) / wb);
                     const int wg = std::min(qc::kFilteredMaxWarps, H->opt_warps ? H->opt_warps : fit);
@@ -452,7 +462,7 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
                 w = bw;
             } else {
                 for (; f >= 5; --f) {
-                    const size_t base = qc::filtered_smem_bytes(sp, 0, f, ln, join);
+                    const size_t base = qc::filtered_smem_bytes(sp, 0, f, ln, join, acap);
                     if (base + wb > H->smem_optin) continue;
                     const int fit = static_cast<int>((H->smem_optin - base) / wb);
                     w = std::min(qc::kFilteredMaxWarps, H->opt_warps ? H->opt_warps : fit);
@@ -466,11 +476,13 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
                 best_fw = f;
                 best_w = w;
                 best_lean = ln;
+                best_acap = acap;
             }
         }
         fw = best_fw;
         warps = best_w;
         lean = best_lean;
+        c.acap = best_acap;
         if (warps < 1) {
             if (H->opt_kernel == 2) return fail(H, QC_ERR_CAPACITY, "filtered kernel does not fit shared memory");
             kernel = 1;
@@ -482,14 +494,15 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
     c.lean = lean;
     c.join = kernel == 2 && join;
     c.unroll = c.join ? 4 : (H->opt_unroll ? H->opt_unroll : 4);
+    if (!c.join) c.acap = 0;
     if (kernel == 2) {
         c.warps = warps;
-        c.smem = qc::filtered_smem_bytes(sp, warps, fw, lean, c.join);
+        c.smem = qc::filtered_smem_bytes(sp, warps, fw, lean, c.join, c.acap);
     } else {
         c.warps = std::min(qc::kFilteredMaxWarps, H->opt_warps ? H->opt_warps : 16);
         c.smem = qc::direct_smem_bytes(sp, c.warps);
     }
-    int per_sm = qc::max_active_ctas(c.kernel, H->precision, c.unroll, 32 * c.warps, c.smem, c.lean, c.join);
+    int per_sm = qc::max_active_ctas(c.kernel, H->precision, c.unroll, 32 * c.warps, c.smem, c.lean, c.join, c.acap > 0);
     if (per_sm < 1) return fail(H, QC_ERR_CAPACITY, "main kernel cannot be resident with this shape");
     long long grid = H->opt_grid ? H->opt_grid : static_cast<long long>(per_sm) * H->sm_count;
     const long long cp = H->opt_chunk_pairs == 0 ? qc::kDefaultChunkPairs : H->opt_chunk_pairs;
@@ -639,6 +652,7 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
         tp.jlen = jlen;
         tp.gent = gent;
         tp.scan_cost = H->opt_scan_cost ? H->opt_scan_cost : qc::kDefaultScanCost;
+        tp.alpha_cap = cfg.acap;
     }
     if (H->opt_timing) QC_CHK(cudaEventRecord(H->ev[1], s), "cudaEventRecord");
 

@@ -118,7 +118,7 @@ qc_status prepare(qc_batch* B) {
     struct Lay { size_t slots, filter, sets, ctr, part, sum, cpart, ctick; unsigned long long nb; int fw, chunks; };
     std::vector<Lay> lay(M);
     const size_t fixed0 = qc::smem_fixed_bytes();
-    const int wcap = B->warps > 0 ? std::min(B->warps, qc::kFilteredMaxWarps) : 16;  // 16: the spill-free bound
+    const int wcap = B->warps > 0 ? std::min(B->warps, qc::kBatchMaxWarps) : 16;  // 16: 128 registers
     // the join, per molecule as its handle would decide (so that a molecule's results are
     // the same in a batch as alone); the batch shares one index build over those molecules
     std::vector<char> jm(M, 0);
@@ -130,7 +130,7 @@ qc_status prepare(qc_batch* B) {
         join = join || jm[m];
     }
     B->join = join;
-    std::vector<int> act(M), lean(M);
+    std::vector<int> act(M), lean(M), acap(M);
     std::vector<unsigned> stride(M);
     for (int m = 0; m < M; ++m) {
         const long long n = std::max<long long>(B->in[m].n_u, 1);
@@ -140,8 +140,17 @@ qc_status prepare(qc_batch* B) {
         // leaves fewer than 8 warps, in the list layout that fits more warps
         int fw = 0, w = 0;
         lean[m] = 0;
+        acap[m] = 0;
+        // a joining molecule's alpha list may get fewer slots (enumerated in segments) when
+        // that fits more warps; the full list on a tie
+        const int nsa = B->handles[m]->sp.nsa;
+        const int caps[3] = {0, 64, 32};
+        for (int ci = 0; ci < (jm[m] ? 3 : 1); ++ci)
         for (int ln = 0; ln < 2; ++ln) {
-            const unsigned st = static_cast<unsigned>((qc::batch_warp_bytes(B->handles[m]->sp, ln, join) + 15) / 16 * 16);
+            const int cap = caps[ci];
+            if (cap > 0 && cap >= nsa) continue;
+            const unsigned st =
+                static_cast<unsigned>((qc::batch_warp_bytes(B->handles[m]->sp, ln, join, cap) + 15) / 16 * 16);
             int f = filter_log2(n), ww = 0;
             for (; f >= 5; --f) {
                 const size_t base = fixed0 + (static_cast<size_t>(4) << f);
@@ -155,6 +164,7 @@ qc_status prepare(qc_batch* B) {
                 w = ww;
                 lean[m] = ln;
                 stride[m] = st;
+                acap[m] = cap;
             }
         }
         if (w < 1) return bfail(B, QC_ERR_CAPACITY, "a molecule of the batch does not fit shared memory");
@@ -282,6 +292,7 @@ qc_status prepare(qc_batch* B) {
             P.tp.jlen = reinterpret_cast<const unsigned*>(A + B->ja_len) + slot_base[m];
             P.tp.gent = reinterpret_cast<const ulonglong2*>(B->d_join + B->jo_ent);
             P.tp.scan_cost = H->opt_scan_cost ? H->opt_scan_cost : qc::kDefaultScanCost;
+            P.tp.alpha_cap = acap[m];
         }
         P.ep = qc::EvalParams{};
         P.ep.samples = reinterpret_cast<const ulonglong2*>(I.samples);
@@ -535,7 +546,7 @@ qc_status qc_batch_set_inputs(qc_batch* B, int mol, const uint64_t* samples, con
 qc_status qc_batch_set_config(qc_batch* B, int unroll, int warps, int chunk) {
     if (!B) return QC_ERR_ARG;
     if (unroll != 0 && unroll != 2 && unroll != 4) return bfail(B, QC_ERR_ARG, "unroll: 0, 2 or 4");
-    if (warps < 0 || warps > qc::kFilteredMaxWarps) return bfail(B, QC_ERR_ARG, "warps: 0..20");
+    if (warps < 0 || warps > qc::kBatchMaxWarps) return bfail(B, QC_ERR_ARG, "warps: 0..20");
     if (chunk < 0 || chunk > 1024) return bfail(B, QC_ERR_ARG, "chunk: 0..1024");
     B->unroll = unroll ? unroll : 4;
     B->warps = warps;

@@ -128,17 +128,22 @@ __global__ void __launch_bounds__(MAXT) eloc_batch_kernel(const __grid_constant_
                                             ? static_cast<long long>(__ldg(mp.ep.order + r0 + static_cast<long long>(q)))
                                             : r0 + static_cast<long long>(q);
                     const int c = static_cast<int>(it - q * C);
+                    // a joining molecule's alpha list may be capped (mp.tp.alpha_cap): segments
                     if (mp.ep.lean)
-                        run_sample<PREC, U, true, 1, JOIN>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));
+                        run_sample<PREC, U, true, 1, JOIN, false, JOIN>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c,
+                                                                         static_cast<int>(C));
                     else
-                        run_sample<PREC, U, true, 0, JOIN>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c, static_cast<int>(C));
+                        run_sample<PREC, U, true, 0, JOIN, false, JOIN>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c,
+                                                                         static_cast<int>(C));
                 }
             }
         }
     }
 }
 
-size_t batch_warp_bytes(const SysParams& sp, bool lean, bool join) { return main_warp_bytes(sp, true, lean, join); }
+size_t batch_warp_bytes(const SysParams& sp, bool lean, bool join, int acap) {
+    return main_warp_bytes(sp, true, lean, join, acap);
+}
 
 cudaError_t launch_build_batch(const MolParams* mols, const MolWork* work, const long long* key_off,
                                int n_mol, long long n_keys, cudaStream_t s) {

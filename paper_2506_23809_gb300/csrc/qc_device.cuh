@@ -348,11 +348,20 @@ constexpr size_t kOffLut = kOffT + 128 * 8;
 constexpr size_t kOffDiv = kOffLut + kPairLut * 2;
 constexpr size_t kOffVar = ((kOffDiv + 2 * 1024 + 127) / 128) * 128;
 
+// Slots of a warp's alpha single list.  Without the join it holds every alpha single that
+// passes the spin-string prefilter.  With the sample-space join it holds only the alpha
+// singles whose alpha' group is too long to scan (enumerated as classes 0 and 4); the host
+// may give it fewer slots than there are alpha singles (acap > 0) when that fits more warps,
+// and a sample with more long alpha' groups than slots enumerates them in segments.
+__host__ __device__ inline int alpha_slots(const SysParams& sp, int acap) {
+    return acap > 0 && acap < sp.nsa ? acap : sp.nsa;
+}
+
 // u32 words of a warp's hash lists: the zero entry, the two single lists, then either the
 // four pair lists (occupied and empty pairs per spin) or, in the lean layout, only the
 // per-orbital values they are built from (a pair's value is the XOR of two of them).
-__host__ __device__ inline size_t list_words(const SysParams& sp, bool lean = false) {
-    return static_cast<size_t>(1 + sp.nsa + sp.nsb) +
+__host__ __device__ inline size_t list_words(const SysParams& sp, bool lean = false, int acap = 0) {
+    return static_cast<size_t>(1 + alpha_slots(sp, acap) + sp.nsb) +
            static_cast<size_t>(lean ? sp.oa + sp.va + sp.ob + sp.vb : sp.npoa + sp.npva + sp.npob + sp.npvb);
 }
 
@@ -897,16 +906,23 @@ struct WarpSample {
     unsigned long long hx;    // linear hash of x
     double ediag;             // <x|H|x>
     float2 ip32;              // 1/psi(x) in FP32 (precision form)
+    unsigned long long as, bs, hxa;  // join: x's alpha and beta spatial strings, alpha part of hx
+    unsigned a_next;          // join: first alpha single not yet in an alpha-list segment
+    unsigned a_seen;          // join: alpha singles below this were classified (short groups scanned)
     unsigned long long pad;
 };
 constexpr size_t kOffWarpSample = 288;
 // per warp: occupation lists (4 x 64 B), reference masks (32 B), the sample's constants
 constexpr size_t kOccBytes = kOffWarpSample + sizeof(WarpSample);
 static_assert(kOccBytes % 16 == 0, "warp regions stay 16-byte aligned");
+// join: the kernel has the join's queue of scanned singles; acap: the alpha list's slots
+// (alpha_slots; 0 for all)
 __host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filter, bool lean = false,
-                                                  bool join = false) {
+                                                  bool join = false, int acap = 0) {
     // hash lists (u32) and, for the two single lists, their compaction maps (u16)
-    const size_t lists = filter ? 4 * list_words(sp, lean) + 2 * static_cast<size_t>(sp.nsa + sp.nsb) : 0;
+    const size_t lists = filter ? 4 * list_words(sp, lean, acap) +
+                                      2 * static_cast<size_t>(alpha_slots(sp, acap) + sp.nsb)
+                                : 0;
     return (kOccBytes + kWarpQueues + (join ? 8 * kSingleCap : 0) + lists + 15) / 16 * 16;
 }
 
@@ -920,8 +936,10 @@ __host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filt
 // the same hash values in the same order, so the same results.  JOIN: the sample-space join
 // is taken when the table carries its index (false compiles it out).  DIAG: the pair-by-pair
 // hit lists and the work counters are written when the launch asks for them (false compiles
-// them out: the checks alone cost the timed kernel a third of its speed).
-template <int PREC, int U, bool FILTER, int LEAN, bool JOIN = true, bool DIAG = false>
+// them out: the checks alone cost the timed kernel a third of its speed).  SEG: the join's
+// alpha list may have fewer slots than alpha singles (tp.alpha_cap) and is then enumerated in
+// segments (false compiles the segments out: 2% of the kernel's time when no list is capped).
+template <int PREC, int U, bool FILTER, int LEAN, bool JOIN = true, bool DIAG = false, bool SEG = false>
 __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParams& tp,
                                            const EvalParams& ep, long long s, int lane,
                                            unsigned char* smem, unsigned char* wl,
@@ -937,13 +955,18 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                                    ? reinterpret_cast<unsigned long long*>(wl + 256) : nullptr;
     const bool lean = FILTER && (LEAN == 1 || (LEAN == 2 && ep.lean != 0));
     // list offsets inside H: 0 zero | SA | SB | PAo | PAv | PBo | PBv, or in the lean layout
-    // 0 zero | SA | SB | occupied alpha | empty alpha | occupied beta | empty beta
-    const int oSA = 1, oSB = oSA + sp.nsa, oPAo = oSB + sp.nsb;
+    // 0 zero | SA | SB | occupied alpha | empty alpha | occupied beta | empty beta; with the
+    // join the alpha list may have fewer slots (tp.alpha_cap), filled in segments
+    const bool join_lists = JOIN && FILTER && tp.jlen != nullptr;
+    const int nA = alpha_slots(sp, SEG && join_lists ? tp.alpha_cap : 0);
+    const int oSA = 1, oSB = oSA + nA, oPAo = oSB + sp.nsb;
     const int oPAv = oPAo + (lean ? sp.oa : sp.npoa);
     const int oPBo = oPAv + (lean ? sp.va : sp.npva);
     const int oPBv = oPBo + (lean ? sp.ob : sp.npob);
-    unsigned short* IA = FILTER ? reinterpret_cast<unsigned short*>(H + list_words(sp, lean)) : nullptr;
-    unsigned short* IB = FILTER ? IA + sp.nsa : nullptr;
+    unsigned short* IA =
+        FILTER ? reinterpret_cast<unsigned short*>(H + list_words(sp, lean, SEG && join_lists ? tp.alpha_cap : 0))
+               : nullptr;
+    unsigned short* IB = FILTER ? IA + nA : nullptr;
     int nsa2 = sp.nsa, nsb2 = sp.nsb;  // single-list lengths after the spin-string prefilter
     const uint32_t wmask4 = FILTER ? ((1u << tp.fw) - 1u) << 2 : 0u;
     const unsigned ltmask = lanemask_lt();
@@ -976,6 +999,11 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         w.hx = hx;
         w.ediag = ediag;
         w.ip32 = inv_psi32(w.psix);
+        w.as = As;
+        w.bs = Bs;
+        w.hxa = hxa;
+        w.a_next = 0u;
+        w.a_seen = 0u;
         w.pad = 0ULL;
         *wsp = w;
     }
@@ -1032,9 +1060,10 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     // Scan state of the join (the first phase of the main loop, before any candidate is
     // queued, so it owns the candidate queue's space): a chunk of up to 32 groups of table
     // rows, one per lane -- start, exclusive row offset and kind in q[0..95] -- scanned as one
-    // list of q[102] rows, 32 per step; x's spin strings and alpha hash in q[96..101], the
-    // next alpha single excitation to classify in q[103] (shared memory keeps the scan state
-    // out of the registers of the enumeration loop).
+    // list of q[102] rows, 32 per step; the next alpha single excitation to classify in q[103]
+    // (shared memory keeps the scan state out of the registers of the enumeration loop).  When
+    // the alpha list is full, the enumeration runs over that segment and the scan state is
+    // entered again for the remaining alpha singles (classes 0 and 4 only).
     auto store_chunk = [&](unsigned gst, unsigned gln, unsigned kind) {
         unsigned inc = gln;
 #pragma unroll
@@ -1051,7 +1080,6 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         }
         __syncwarp();
     };
-    unsigned long long* qx = reinterpret_cast<unsigned long long*>(q + 96);
 
     if (FILTER) {
         const unsigned char* occA = wl;
@@ -1109,12 +1137,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
             }
             enumA = __shfl_sync(QC_FULLMASK, en, 0);
             enumB = __shfl_sync(QC_FULLMASK, en, 1);
-            if (lane == 0) {
-                qx[0] = As;
-                qx[1] = Bs;
-                qx[2] = hxa;
-                q[103] = 0u;
-            }
+            if (lane == 0) q[103] = 0u;
             store_chunk(gst, c == 0 ? gln : 0u, kind);  // later chunks classify but scan nothing
             nsa2 = 0;  // the alpha' groups are classified in the scan state
         } else {
@@ -1176,6 +1199,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
 #pragma unroll
     for (int k = 0; k < U; ++k) hu[k] = 0u;
     bool scanning = join;
+    bool seg2 = false;    // join: a later segment of the alpha list (classes 0 and 4 only)
     unsigned sbase = 0u;  // next row of the current scan chunk
     while (true) {
         if (scanning) {
@@ -1199,7 +1223,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     const unsigned kd = q[64 + g];
                     const ulonglong2 e = __ldg(tp.gent + q[g] + (v - q[32 + g]));
                     const unsigned kk = kd & 3u;
-                    const unsigned long long ref = kk == kScanBeta ? qx[0] : qx[1];
+                    const unsigned long long ref = kk == kScanBeta ? wsp->as : wsp->bs;
                     const unsigned long long dm = e.x ^ ref;
                     const int d = __popcll(dm);
                     sgl = kk == kScanAlpha ? d == 2 : (kk == kScanAlphaP && d == 0);
@@ -1222,37 +1246,53 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 const unsigned char* occA = wl;
                 const unsigned char* virA = wl + 64;
                 const int t = st0 + lane;
-                bool keep = false;
+                const int a_next = SEG ? static_cast<int>(wsp->a_next) : 0;
+                const int a_seen = SEG ? static_cast<int>(wsp->a_seen) : 0;
+                bool lng = false;
                 uint32_t hv32 = 0u;
-                unsigned gst = 0u, gln = 0u, kd = 0u;
-                if (t < sp.nsa) {
+                unsigned gst = 0u, gln = 0u, kd = 0u, len = 0u, start = 0u;
+                // singles below a_next are in an earlier segment; between a_next and a_seen only
+                // their long groups are left (the short ones were scanned)
+                if (t < sp.nsa && t >= a_next) {
                     const int oi = divA[t];
                     const int ki = occA[oi], ka = virA[t - oi * sp.va];
                     const unsigned long long tm = T64[2 * ki] ^ T64[2 * ka];
                     hv32 = static_cast<uint32_t>(tm);
-                    const unsigned sl = set_slot(tp.aset, tp.set_mask, qx[0] ^ (1ULL << ki) ^ (1ULL << ka), qx[2] ^ tm);
-                    unsigned len = 0u, start = 0u;
+                    const unsigned sl = set_slot(tp.aset, tp.set_mask, wsp->as ^ (1ULL << ki) ^ (1ULL << ka), wsp->hxa ^ tm);
                     if (sl != kNoSlot) {
                         len = __ldg(tp.jlen + sl);
                         start = __ldg(tp.jstart + sl);
                     }
-                    if (static_cast<long long>(len) * tp.scan_cost <= 4LL * (nsb2 + 1)) {
-                        gst = start;
-                        gln = len;
-                        kd = kScanAlphaP | (static_cast<unsigned>(ki) << 8) | (static_cast<unsigned>(ka) << 16);
-                    } else {
-                        keep = true;
-                    }
+                    lng = static_cast<long long>(len) * tp.scan_cost > 4LL * (nsb2 + 1);
+                    kd = kScanAlphaP | (static_cast<unsigned>(ki) << 8) | (static_cast<unsigned>(ka) << 16);
                 }
-                const unsigned m = __ballot_sync(QC_FULLMASK, keep);
+                // a long group joins the alpha list while it has room; the first that does not
+                // fit ends this segment's classification (a_next), and short groups are
+                // scanned once (t >= a_seen)
+                const unsigned m = __ballot_sync(QC_FULLMASK, lng);
+                const int pos = nsa2 + __popc(m & ltmask);
+                const bool keep = lng && pos < nA;
                 if (keep) {
-                    const int pos = nsa2 + __popc(m & ltmask);
                     H[oSA + pos] = hv32;
                     IA[pos] = static_cast<unsigned short>(t);
+                } else if (!lng && t >= a_seen) {
+                    gst = start;
+                    gln = len;
                 }
-                nsa2 += __popc(m);
-                __syncwarp();
-                if (lane == 0) q[103] = static_cast<unsigned>(st0 + 32);
+                nsa2 = min(nA, nsa2 + __popc(m));
+                if (SEG) {
+                    const unsigned md = __ballot_sync(QC_FULLMASK, lng && !keep);
+                    __syncwarp();
+                    if (lane == 0) {
+                        const int end = min(st0 + 32, sp.nsa);
+                        wsp->a_next = static_cast<unsigned>(md ? st0 + __ffs(md) - 1 : end);
+                        wsp->a_seen = static_cast<unsigned>(max(a_seen, end));
+                        q[103] = static_cast<unsigned>(md ? sp.nsa : st0 + 32);
+                    }
+                } else {
+                    __syncwarp();
+                    if (lane == 0) q[103] = static_cast<unsigned>(st0 + 32);
+                }
                 store_chunk(gst, c == 0 ? gln : 0u, kd);
                 sbase = 0u;
             } else {
@@ -1268,7 +1308,8 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     else if (cls == 3) { oo = oPBo; n1 = sp.npob; io = oPBv; n2 = sp.npvb; }
                     else if (cls == 4) { oo = oSA; n1 = nsa2; io = oSB; n2 = nsb2; }
                 } while (cls < 5 && (n1 == 0 || n2 == 0 || (cls < 2 ? c != 0 : c * U >= n1) ||
-                                     ((cls == 1 || cls == 3) && !enumA) || (cls == 2 && !enumB)));
+                                     ((cls == 1 || cls == 3) && !enumA) || (cls == 2 && !enumB) ||
+                                     (SEG && seg2 && cls >= 1 && cls <= 3)));
                 done = cls >= 5;
                 pairs = lean && (cls == 2 || cls == 3);
                 // excitation chunk c of C: the singles in chunk 0, outer blocks c, c + C, ...
@@ -1406,7 +1447,23 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 break;
             }
         }
-        if (done) break;
+        if (done) {
+            // join: long alpha' groups that did not fit the alpha list: classify and enumerate
+            // the next segment (the queues are empty here)
+            if (!(SEG && join && static_cast<int>(wsp->a_next) < sp.nsa)) break;
+            scanning = true;
+            seg2 = true;
+            done = false;
+            need_class = true;
+            cls = -1;
+            nsa2 = 0;
+            sbase = 0u;
+            if (lane == 0) {
+                q[102] = 0u;
+                q[103] = wsp->a_next / 32u * 32u;
+            }
+            __syncwarp();
+        }
     }
     sample_finish<PREC, DIAG, FILTER>(ep, s, lane, wsp->ediag, wsp->psix, acc, c, C);
     __syncwarp();

@@ -52,6 +52,7 @@ struct qc_eloc {
     int opt_scan_cost = 0;  // 0 default, else 4 x the cost of a scanned row in enumerated pairs
     int opt_count_work = 0;  // QC_OPT_COUNT_WORK
     int opt_wait_limit = 0;  // QC_OPT_WAIT_LIMIT + 1 (0: the kernel's default)
+    int opt_alpha_slots = 0;  // QC_OPT_ALPHA_SLOTS (0: auto)
     qc::WorkCounters* d_work = nullptr;
     cudaStream_t work_stream = nullptr;  // stream of the last evaluation that counted work
     bool work_recorded = false;

@@ -15,6 +15,8 @@ constexpr int kPairLut = 2016;   // C(64, 2): colex pair index -> (i, j), i < j 
 // registers a thread, which it fits without spills since the sample's constants moved to
 // shared memory; 24 warps beat 20 (96 registers) by 6% at N=52 (measured: 2.81 / 3.00 ms)
 constexpr int kFilteredMaxWarps = 24;
+// Warps per CTA of the batch kernel at most (its launch bounds: 512 or 640 threads)
+constexpr int kBatchMaxWarps = 20;
 
 // One Hamiltonian (Eq. 2) resident on the device.
 struct SysParams {
@@ -66,6 +68,7 @@ struct TableParams {
     const unsigned* jlen;
     const ulonglong2* gent;
     int scan_cost;  // a group is scanned when len * scan_cost <= 4 * (pairs it replaces)
+    int alpha_cap;  // join: slots of the per-warp alpha single list (0: all alpha singles)
 };
 
 // Counters and flags of one evaluation (device memory, zeroed at the start of a call).
@@ -189,6 +192,7 @@ struct LaunchCfg {
     int lean;     // filtered kernel: pair hash lists formed on the fly
     int chunks;   // excitation chunks per sample
     int join;     // filtered kernel: sample-space join (short row groups scanned)
+    int acap;     // join: slots of the per-warp alpha single list (0: all)
 };
 
 // host-side launchers (qc_kernels.cu)
@@ -205,7 +209,8 @@ cudaError_t launch_eloc_main_diag(const SysParams& sp, const TableParams& tp, co
 cudaError_t prepare_kernels_diag(size_t max_smem);
 cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk,
                           void* summary_dev, long long pairs_per_sample, cudaStream_t s);
-int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem, int lean = 0, int join = 0);
+int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem, int lean = 0, int join = 0,
+                    int seg = 0);
 // batch: build every molecule's table in one launch (key_off: prefix of table sizes, device)
 cudaError_t launch_build_batch(const MolParams* mols, const MolWork* work, const long long* key_off,
                                int n_mol, long long n_keys, cudaStream_t s);
@@ -214,10 +219,11 @@ cudaError_t launch_eloc_batch(const BatchParams& bp, int precision, int unroll, 
 cudaError_t launch_reduce_batch(const MolParams* mols, const MolWork* work, int n_mol, int max_blocks,
                                 cudaStream_t s);
 int max_active_batch(int precision, int unroll, int threads, size_t smem, bool join = false);
-size_t batch_warp_bytes(const SysParams& sp, bool lean, bool join = false);
+// join: the batch kernel has the join's queues; acap: the molecule's alpha list slots (0: all)
+size_t batch_warp_bytes(const SysParams& sp, bool lean, bool join, int acap);
 cudaError_t prepare_batch_kernels(size_t max_smem, size_t* dyn_limit);
 cudaError_t prepare_kernels(size_t max_smem);
-size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw, bool lean = false, bool join = false);
+size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw, bool lean = false, bool join = false, int acap = 0);
 size_t direct_smem_bytes(const SysParams& sp, int warps);
 size_t smem_fixed_bytes();  // CTA tables at the head of the main kernels' dynamic shared memory
 int reduce_blocks(long long n);

@@ -18,8 +18,9 @@ int reduce_blocks(long long n) {
 
 size_t smem_fixed_bytes() { return kOffVar; }
 
-size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw, bool lean, bool join) {
-    return kOffVar + (static_cast<size_t>(4) << fw) + static_cast<size_t>(warps) * main_warp_bytes(sp, true, lean, join);
+size_t filtered_smem_bytes(const SysParams& sp, int warps, int fw, bool lean, bool join, int acap) {
+    return kOffVar + (static_cast<size_t>(4) << fw) +
+           static_cast<size_t>(warps) * main_warp_bytes(sp, true, lean, join, join ? acap : 0);
 }
 size_t direct_smem_bytes(const SysParams& sp, int warps) {
     return kOffVar + static_cast<size_t>(warps) * main_warp_bytes(sp, false);
@@ -80,9 +81,9 @@ cudaError_t launch_reduce(const EvalParams& ep, double* partials, int nblk, void
     return cudaGetLastError();
 }
 
-int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem, int lean, int join) {
-    const void* f = precision == QC_FP64 ? main_kernel_ptr<QC_FP64, false>(kernel, unroll, lean, join)
-                                         : main_kernel_ptr<QC_FP32_COMP, false>(kernel, unroll, lean, join);
+int max_active_ctas(int kernel, int precision, int unroll, int threads, size_t smem, int lean, int join, int seg) {
+    const void* f = precision == QC_FP64 ? main_kernel_ptr<QC_FP64, false>(kernel, unroll, lean, join, seg)
+                                         : main_kernel_ptr<QC_FP32_COMP, false>(kernel, unroll, lean, join, seg);
     int n = 0;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) == cudaSuccess ? n : 0;
 }

@@ -11,7 +11,7 @@
 
 namespace qc {
 
-template <int PREC, int U, bool FILTER, int LEAN, bool JOIN, bool DIAG>
+template <int PREC, int U, bool FILTER, int LEAN, bool JOIN, bool DIAG, bool SEG = false>
 __global__ void __launch_bounds__(32 * kFilteredMaxWarps) eloc_main_kernel(const __grid_constant__ SysParams sp,
                                                         const __grid_constant__ TableParams tp,
                                                         const __grid_constant__ EvalParams ep) {
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(32 * kFilteredMaxWarps) eloc_main_kernel(const
     }
     if (DIAG && ep.work != nullptr && threadIdx.x == 0) atomicAdd(&ep.work->ctas, 1ULL);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * main_warp_bytes(sp, FILTER, LEAN == 1, JOIN);
+    unsigned char* wl = smem + kOffVar + fbytes + static_cast<size_t>(warp) * main_warp_bytes(sp, FILTER, LEAN == 1, JOIN, SEG ? tp.alpha_cap : 0);
     // samples go to warps as they come free: one cursor for the grid, so a warp that drew
     // cheap samples takes more of them and the launch ends with little tail
     // with C excitation chunks per sample a work item is (sample, chunk): item = s * C + c
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(32 * kFilteredMaxWarps) eloc_main_kernel(const
         const unsigned long long q = it / C;
         // heavy samples first when the host gave an order: the launch then ends on light ones
         const unsigned long long s = ep.order != nullptr ? static_cast<unsigned long long>(__ldg(ep.order + q)) : q;
-        run_sample<PREC, U, FILTER, LEAN, JOIN, DIAG>(sp, tp, ep, static_cast<long long>(s), lane, smem, wl, filt,
+        run_sample<PREC, U, FILTER, LEAN, JOIN, DIAG, SEG>(sp, tp, ep, static_cast<long long>(s), lane, smem, wl, filt,
                                                 static_cast<int>(it - q * C), static_cast<int>(C));
     }
 }
@@ -83,7 +83,8 @@ template <int PREC, int LEAN, bool DIAG>
 static void launch_filtered(const SysParams& sp, const TableParams& tp, const EvalParams& ep, const LaunchCfg& c,
                             cudaStream_t s) {
     const dim3 grid(c.grid), block(32 * c.warps);
-    if (c.join) eloc_main_kernel<PREC, 4, true, LEAN, true, DIAG><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    if (c.join && c.acap > 0) eloc_main_kernel<PREC, 4, true, LEAN, true, DIAG, true><<<grid, block, c.smem, s>>>(sp, tp, ep);
+    else if (c.join) eloc_main_kernel<PREC, 4, true, LEAN, true, DIAG><<<grid, block, c.smem, s>>>(sp, tp, ep);
     else if (c.unroll == 1) eloc_main_kernel<PREC, 1, true, LEAN, false, DIAG><<<grid, block, c.smem, s>>>(sp, tp, ep);
     else if (c.unroll == 2) eloc_main_kernel<PREC, 2, true, LEAN, false, DIAG><<<grid, block, c.smem, s>>>(sp, tp, ep);
     else eloc_main_kernel<PREC, 4, true, LEAN, false, DIAG><<<grid, block, c.smem, s>>>(sp, tp, ep);
@@ -102,16 +103,18 @@ static cudaError_t launch_main_p(const SysParams& sp, const TableParams& tp, con
     return cudaGetLastError();
 }
 
-// the join is built with U = 4 only
+// the join is built with U = 4 only; seg: its alpha list is capped (enumerated in segments)
 template <int PREC, bool DIAG>
-static const void* main_kernel_ptr(int kernel, int unroll, int lean, int join) {
+static const void* main_kernel_ptr(int kernel, int unroll, int lean, int join, int seg = 0) {
     if (kernel != 2) return (const void*)eloc_main_kernel<PREC, 1, false, 0, false, DIAG>;
     if (lean) {
+        if (join && seg) return (const void*)eloc_main_kernel<PREC, 4, true, 1, true, DIAG, true>;
         if (join) return (const void*)eloc_main_kernel<PREC, 4, true, 1, true, DIAG>;
         if (unroll == 1) return (const void*)eloc_main_kernel<PREC, 1, true, 1, false, DIAG>;
         if (unroll == 2) return (const void*)eloc_main_kernel<PREC, 2, true, 1, false, DIAG>;
         return (const void*)eloc_main_kernel<PREC, 4, true, 1, false, DIAG>;
     }
+    if (join && seg) return (const void*)eloc_main_kernel<PREC, 4, true, 0, true, DIAG, true>;
     if (join) return (const void*)eloc_main_kernel<PREC, 4, true, 0, true, DIAG>;
     if (unroll == 1) return (const void*)eloc_main_kernel<PREC, 1, true, 0, false, DIAG>;
     if (unroll == 2) return (const void*)eloc_main_kernel<PREC, 2, true, 0, false, DIAG>;
@@ -133,9 +136,9 @@ static cudaError_t prepare_variant(size_t max_smem) {
         for (int kernel = 1; kernel <= 2; ++kernel)
             for (int unroll : {1, 2, 4})
                 for (int lean = 0; lean < 2; ++lean)
-                    for (int join = 0; join < 2; ++join) {
-                        const void* f = prec == QC_FP64 ? main_kernel_ptr<QC_FP64, DIAG>(kernel, unroll, lean, join)
-                                                        : main_kernel_ptr<QC_FP32_COMP, DIAG>(kernel, unroll, lean, join);
+                    for (int join = 0; join < 3; ++join) {
+                        const void* f = prec == QC_FP64 ? main_kernel_ptr<QC_FP64, DIAG>(kernel, unroll, lean, join > 0, join == 2)
+                                                        : main_kernel_ptr<QC_FP32_COMP, DIAG>(kernel, unroll, lean, join > 0, join == 2);
                         const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
                         if (r != cudaSuccess) e = r;
                     }

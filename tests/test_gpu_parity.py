@@ -196,10 +196,14 @@ def test_lean_lists_equal_stored(B, orc, n, ne, nu, prec):
                                                (76, 20, 2000, 0, {}), (76, 20, 2000, 1, {11: 1}),
                                                (76, 20, 2000, 1, {11: 1024}),
                                                (76, 20, 2000, 1, {8: 2, 5: 2}), (52, 14, 3000, 0, {9: 2000}),
-                                               (40, 8, 1500, 0, {}), (128, 64, 24, 0, {}), (128, 40, 200, 1, {})],
+                                               (40, 8, 1500, 0, {}), (128, 64, 24, 0, {}), (128, 40, 200, 1, {}),
+                                               (52, 14, 3000, 0, {14: 1, 11: 1024}), (52, 14, 3000, 0, {14: 4}),
+                                               (76, 20, 2000, 1, {14: 3, 11: 64}), (76, 20, 2000, 0, {14: 8, 9: 3000}),
+                                               (128, 40, 200, 0, {14: 5})],
                          ids=["n52", "n76_fp32c", "n52_scan_all", "n52_enum_more", "n52_enum_most", "n76_fp64",
                               "n76_scan_all", "n76_enum_most", "n76_lean_u2", "n52_chunks", "n40", "n128",
-                              "n128_fp32c"])
+                              "n128_fp32c", "n52_alpha_seg1", "n52_alpha_seg4", "n76_alpha_seg3", "n76_alpha_seg8_chunks",
+                              "n128_alpha_seg5"])
 def test_join_equals_enumeration(B, orc, n, ne, nu, prec, opts):
     """The sample-space join (QC_OPT_JOIN 2: short row groups scanned, long ones enumerated)
     finds the same connected set with the same rows and phases as plain enumeration
