@@ -1271,15 +1271,15 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 // scanned once (t >= a_seen)
                 const unsigned m = __ballot_sync(QC_FULLMASK, lng);
                 const int pos = nsa2 + __popc(m & ltmask);
-                const bool keep = lng && pos < nA;
+                const bool keep = SEG ? (lng && pos < nA) : lng;
                 if (keep) {
                     H[oSA + pos] = hv32;
                     IA[pos] = static_cast<unsigned short>(t);
-                } else if (!lng && t >= a_seen) {
+                } else if (!lng && (!SEG || t >= a_seen)) {
                     gst = start;
                     gln = len;
                 }
-                nsa2 = min(nA, nsa2 + __popc(m));
+                nsa2 = SEG ? min(nA, nsa2 + __popc(m)) : nsa2 + __popc(m);
                 if (SEG) {
                     const unsigned md = __ballot_sync(QC_FULLMASK, lng && !keep);
                     __syncwarp();
