@@ -553,11 +553,14 @@ def run_batched(args):
     from paper_2506_23809_gb300 import inputs as I
     build.build()
     B.load_library()
-    torch.cuda.set_device(0)
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
     specs = I.batched_molecule_specs(args.n_mol)
     # the batched form computes in the precision form (FP32 terms, compensated sums, FP64
     # diagonal and reduction) unless --precision fp64 is given explicitly
     prec = B.QC_FP64 if "--precision" in sys.argv and args.precision == "fp64" else B.QC_FP32_COMP
+    if world > 1:
+        return _run_batched_plan(args, specs, prec, world, rank, local)
     handles, dev, outs = [], [], []
     total_pairs = 0
     for sp in specs:
@@ -621,6 +624,90 @@ def run_batched(args):
             "speedup_vs_plain": t_plain / t_graph, "max_rel_diff_vs_plain": diff,
             "gpu_launches": _batched_launches(specs) * args.steps}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def _batched_molecule(I, sp):
+    K = sp["n_orb"] // 2
+    ints = I.make_integrals(K, sp["n_orb"], sp["seed"])
+    keys = I.rank_weighted_samples(K, sp["n_elec"] // 2, sp["n_elec"] // 2, sp["n_u"], seed=sp["seed"] + 1)
+    return ints, keys, I.zipf_counts(sp["n_u"], 100 * sp["n_u"], sp["seed"] + 2), I.lognormal_psi(sp["n_u"], sp["seed"] + 3)
+
+
+def _run_batched_plan(args, specs, prec, world, rank, local):
+    """The batched workload over N GPUs with a cost-weighted plan (Alg. 2's split with
+    measured costs): rank 0 times every molecule once and spreads that over its rows by hit
+    count, the plan (row ranges of molecules per rank) is broadcast, and each rank runs its
+    pieces as one batched step (autotuned, replayed as a CUDA graph).  The pieces' Eq. 1
+    partials are gathered and combined per molecule: 32 bytes per piece, the one exchange."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_23809_gb300 import binding as B
+    from paper_2506_23809_gb300 import inputs as I
+    from paper_2506_23809_gb300 import shards
+    dev = torch.device("cuda", local)
+    dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.Stream()
+    plan = [None]
+    if rank == 0:
+        handles, inputs = [], []
+        for sp in specs:
+            ints, keys, counts, psi = _batched_molecule(I, sp)
+            handles.append(B.qc_eloc_create(ints.h, ints.eri, 0.0, sp["n_orb"], sp["n_elec"], prec))
+            inputs.append((B.keys_to_tensor(keys, dev), torch.from_numpy(counts).to(dev), torch.from_numpy(psi).to(dev),
+                           torch.empty(sp["n_u"], dtype=torch.complex128, device=dev)))
+        with torch.cuda.stream(stream):
+            costs = shards.calibrate_row_costs(B, handles, inputs, stream)
+        plan = [shards.plan_pieces(costs, world)]
+        for h in handles:
+            B.qc_eloc_destroy(h)
+        del inputs
+    dist.broadcast_object_list(plan, src=0)
+    plan = plan[0]
+    mine = plan[rank]
+    mols = sorted({m for m, _, _ in mine})
+    handles, inputs = {}, {}
+    for m in mols:
+        sp = specs[m]
+        ints, keys, counts, psi = _batched_molecule(I, sp)
+        handles[m] = B.qc_eloc_create(ints.h, ints.eri, 0.0, sp["n_orb"], sp["n_elec"], prec)
+        inputs[m] = (B.keys_to_tensor(keys, dev), torch.from_numpy(counts).to(dev), torch.from_numpy(psi).to(dev),
+                     torch.empty(sp["n_u"], dtype=torch.complex128, device=dev))
+    with torch.cuda.stream(stream):
+        batch, _ = shards.evaluate_pieces(B, handles, inputs, mine, stream, autotune=True, graph=True)
+        for _ in range(args.warmup):
+            B.qc_batch_graph_launch(batch, stream)
+        stream.synchronize()
+        dist.barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            B.qc_batch_graph_launch(batch, stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        sums = B.qc_batch_summaries(batch, stream)
+    t = torch.tensor([ev0.elapsed_time(ev1) / args.steps], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    parts = [(m, shards.partials(sm)) for (m, _, _), sm in zip(mine, sums)]
+    gathered = [None] * world
+    dist.all_gather_object(gathered, parts)
+    energies = shards.combine_pieces(len(specs), [x for g in gathered for x in g])
+    B.qc_batch_destroy(batch)
+    for h in handles.values():
+        B.qc_eloc_destroy(h)
+    total_pairs = sum(sp["n_u"] * _pairs(sp["n_orb"], sp["n_elec"]) for sp in specs)
+    ms = float(t.item())
+    if rank == 0:
+        line = {"metric": METRIC, "form": "batched", "value": total_pairs / (ms / 1e3), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "strong", "dtype": "f32+f64" if prec == B.QC_FP32_COMP else "f64",
+                "config": {"workload": f"batched_{len(specs)}_molecules", "parallelism": f"cost-weighted plan x{world}",
+                           "pieces_per_rank": [len(p) for p in plan]},
+                "energy_checksum": float(sum(E.real for _, E, _ in energies)),
+                "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
     return 0
 
 

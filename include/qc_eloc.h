@@ -344,6 +344,14 @@ qc_status qc_batch_destroy(qc_batch* batch);
 const char* qc_batch_last_error(const qc_batch* batch);
 qc_status qc_batch_set_inputs(qc_batch* batch, int mol, const uint64_t* samples, const int64_t* counts,
                               const double* psi, int64_t n_u, double* eloc);
+/* One piece of a molecule for replicas that share its work (Alg. 2's cost-weighted split of
+ * the unique samples): the next steps evaluate only rows [r0, r1) of the molecule's samples
+ * (by row index, against its whole sample table; r1 < 0: to the end) and reduce Eq. 1 over
+ * those rows only, so its summary holds the piece's partials -- W, sum c E (sum_ce_re/im)
+ * and var -- which combine across pieces into the molecule's energy.  E_loc of each row is
+ * bitwise the same as in a whole-molecule step.  (0, n_u) restores the whole molecule.
+ * Call after qc_batch_set_inputs; QC_ERR_ARG on a bad range. */
+qc_status qc_batch_set_rows(qc_batch* batch, int mol, int64_t r0, int64_t r1);
 /* launch shape: unroll 0|2|4 (0 = 4), warps 0..20 (0 = 16, the widest CTA without register spills), samples a warp
  * takes per fetch 0..1024 (0 = 1) */
 qc_status qc_batch_set_config(qc_batch* batch, int unroll, int warps, int chunk);

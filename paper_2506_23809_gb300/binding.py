@@ -122,9 +122,10 @@ def load_library(path: str = LIB_PATH):
     lib.qc_batch_timings.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
     lib.qc_batch_autotune.argtypes = [P, P, i32, ctypes.POINTER(ctypes.c_int64)]
     lib.qc_batch_set_chunk_pairs.argtypes = [P, i64]
+    lib.qc_batch_set_rows.argtypes = [P, i32, i64, i64]
     for f in ("qc_batch_create", "qc_batch_destroy", "qc_batch_set_inputs", "qc_batch_set_config",
               "qc_batch_config", "qc_batch_eval", "qc_batch_graph_launch", "qc_batch_timings", "qc_batch_autotune",
-              "qc_batch_set_chunk_pairs"):
+              "qc_batch_set_chunk_pairs", "qc_batch_set_rows"):
         getattr(lib, f).restype = i32
     _lib = lib
     return lib
@@ -477,6 +478,12 @@ def qc_batch_set_inputs(batch: QcBatch, mol: int, samples, counts, psi, eloc):
         int(samples.shape[0]), _dptr(eloc, "eloc", (torch.complex128, torch.float64)))
     _bcheck(st, batch)
     batch.keep += [samples, counts, psi, eloc]
+
+
+def qc_batch_set_rows(batch: QcBatch, mol: int, r0: int, r1: int = -1):
+    """Evaluate only rows [r0, r1) of molecule `mol` and reduce Eq. 1 over them (a replica's
+    piece; the molecule's summary then holds the piece's partials)."""
+    _bcheck(load_library().qc_batch_set_rows(batch.ptr, int(mol), int(r0), int(r1)), batch)
 
 
 def qc_batch_set_config(batch: QcBatch, unroll=0, warps=0, chunk=0):

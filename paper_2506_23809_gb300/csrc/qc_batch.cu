@@ -33,6 +33,9 @@ struct BatchInput {
     int64_t r0 = 0, r1 = -1;  // r1 < 0: all rows
     bool reduce = true;
     qc::Counters* ctr = nullptr;  // null: the batch's own counters, zeroed every step
+    // a replica's piece (qc_batch_set_rows): rows [r0, r1) by row index, in row order, with
+    // the Eq. 1 reduction over those rows only (the summary holds the piece's partials)
+    bool piece = false;
 };
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -263,7 +266,8 @@ qc_status prepare(qc_batch* B) {
         W.ctr = I.ctr ? I.ctr : reinterpret_cast<qc::Counters*>(A + L.ctr);
         W.part = reinterpret_cast<double*>(A + L.part);
         W.sum = B->d_sums + m;
-        W.nblk = I.reduce ? qc::reduce_blocks(I.n_u) : 0;
+        const long long red_rows = I.piece ? (I.r1 < 0 ? I.n_u : I.r1) - I.r0 : I.n_u;
+        W.nblk = I.reduce ? qc::reduce_blocks(red_rows) : 0;
         W.jkey = W.jval = W.jlen = nullptr;
         W.jbase = W.jsent = 0u;
         if (jm[m]) {
@@ -309,12 +313,15 @@ qc_status prepare(qc_batch* B) {
         P.ep.cticket = L.ctick ? reinterpret_cast<unsigned*>(A + L.ctick) : nullptr;
         // a joining molecule's rows are handed out heavy first (the order the batch's join
         // index builds each step)
-        P.ep.order = jm[m] ? reinterpret_cast<const unsigned*>(B->d_join + B->jo_order) + row_base[m] : nullptr;
+        P.ep.order = jm[m] && !I.piece ? reinterpret_cast<const unsigned*>(B->d_join + B->jo_order) + row_base[m]
+                                         : nullptr;
         if (P.ep.chunks > 1 && !P.ep.cpart) P.ep.chunks = 1;
         P.active_warps = act[m];
         P.warp_stride = stride[m];
         P.r0 = I.r0;
         P.r1 = I.r1 < 0 ? I.n_u : I.r1;
+        P.red_lo = I.piece ? P.r0 : 0;
+        P.red_hi = I.piece ? P.r1 : I.n_u;
     }
     // launch shape: the widest CTA any molecule uses, all the dynamic shared memory
     int warps = 1;
@@ -469,6 +476,7 @@ qc_status qc::batch_set_slice(qc_batch* B, int mol, long long r0, long long r1, 
     I.r1 = r1;
     I.reduce = reduce;
     I.ctr = ctr;
+    I.piece = false;
     B->dirty = true;
     drop_graph(B);
     return QC_OK;
@@ -538,6 +546,22 @@ qc_status qc_batch_set_inputs(qc_batch* B, int mol, const uint64_t* samples, con
     I.psi = psi;
     I.n_u = n_u;
     I.eloc = eloc;
+    B->dirty = true;
+    drop_graph(B);
+    return QC_OK;
+}
+
+qc_status qc_batch_set_rows(qc_batch* B, int mol, int64_t r0, int64_t r1) {
+    if (!B) return QC_ERR_ARG;
+    if (mol < 0 || mol >= B->n_mol) return bfail(B, QC_ERR_ARG, "mol out of range");
+    BatchInput& I = B->in[mol];
+    if (r1 < 0) r1 = I.n_u;
+    if (r0 < 0 || r1 < r0 || r1 > I.n_u) return bfail(B, QC_ERR_ARG, "rows must satisfy 0 <= r0 <= r1 <= n_u");
+    I.r0 = r0;
+    I.r1 = r1;
+    I.reduce = true;
+    I.ctr = nullptr;
+    I.piece = !(r0 == 0 && r1 == I.n_u);
     B->dirty = true;
     drop_graph(B);
     return QC_OK;

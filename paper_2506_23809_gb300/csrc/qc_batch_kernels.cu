@@ -30,14 +30,16 @@ __global__ void __launch_bounds__(kRedThreads) reduce_batch_pass1(const MolParam
                                                                   const MolWork* __restrict__ work) {
     const MolWork& W = work[blockIdx.y];
     if (blockIdx.x >= static_cast<unsigned>(W.nblk)) return;  // block-uniform
-    reduce_pass1_body(mols[blockIdx.y].ep, W.part, blockIdx.x, W.nblk);
+    const MolParams& P = mols[blockIdx.y];
+    reduce_pass1_body(P.ep, W.part, blockIdx.x, W.nblk, P.red_lo, P.red_hi);
 }
 __global__ void __launch_bounds__(kRedThreads) reduce_batch_pass2(const MolParams* __restrict__ mols,
                                                                   const MolWork* __restrict__ work) {
     const MolParams& P = mols[blockIdx.y];
     const MolWork& W = work[blockIdx.y];
     if (blockIdx.x >= static_cast<unsigned>(W.nblk)) return;  // block-uniform
-    reduce_pass2_body(P.ep, W.part, static_cast<qc_eloc_summary*>(W.sum), P.sp.pairs, blockIdx.x, W.nblk);
+    reduce_pass2_body(P.ep, W.part, static_cast<qc_eloc_summary*>(W.sum), P.sp.pairs, blockIdx.x, W.nblk, P.red_lo,
+                      P.red_hi);
 }
 
 // K4: many molecules in one persistent launch, one molecule after another.  Every CTA

@@ -1488,17 +1488,17 @@ __device__ __forceinline__ Tv block_sum(Tv v, Tv* sh) {
     return r;
 }
 
-// Pass 1 of one molecule, as block `bid` of `nblk`: W, sum c E and the count of finite
-// samples; the last block to finish writes the mean.
+// Pass 1 of one molecule over its rows [lo, hi), as block `bid` of `nblk`: W, sum c E and the
+// count of finite samples; the last block to finish writes the mean.
 __device__ __forceinline__ void reduce_pass1_body(const EvalParams& ep, double* part, unsigned bid,
-                                                  unsigned nblk) {
+                                                  unsigned nblk, long long lo, long long hi) {
     __shared__ double shd[kRedThreads];
     __shared__ long long shl[kRedThreads];
     __shared__ bool last;
     long long w = 0, used = 0;
     double sr = 0.0, si = 0.0;
     bool neg = false;
-    for (long long i = static_cast<long long>(bid) * kRedThreads + threadIdx.x; i < ep.n_u;
+    for (long long i = lo + static_cast<long long>(bid) * kRedThreads + threadIdx.x; i < hi;
          i += static_cast<long long>(nblk) * kRedThreads) {
         const double2 e = ep.eloc[i];
         const long long c = ep.counts[i];
@@ -1548,14 +1548,16 @@ __device__ __forceinline__ void reduce_pass1_body(const EvalParams& ep, double* 
     }
 }
 
-// Pass 2 of one molecule: sum c |E - Ebar|^2; the last block writes the summary.
+// Pass 2 of one molecule over its rows [lo, hi): sum c |E - Ebar|^2; the last block writes the
+// summary.
 __device__ __forceinline__ void reduce_pass2_body(const EvalParams& ep, double* part, qc_eloc_summary* out,
-                                                  long long pairs_per_sample, unsigned bid, unsigned nblk) {
+                                                  long long pairs_per_sample, unsigned bid, unsigned nblk,
+                                                  long long lo, long long hi) {
     __shared__ double shd[kRedThreads];
     __shared__ bool last;
     const double mr = ep.ctr->mean_re, mi = ep.ctr->mean_im;
     double v = 0.0;
-    for (long long i = static_cast<long long>(bid) * kRedThreads + threadIdx.x; i < ep.n_u;
+    for (long long i = lo + static_cast<long long>(bid) * kRedThreads + threadIdx.x; i < hi;
          i += static_cast<long long>(nblk) * kRedThreads) {
         const double2 e = ep.eloc[i];
         const long long c = ep.counts[i];
@@ -1593,7 +1595,7 @@ __device__ __forceinline__ void reduce_pass2_body(const EvalParams& ep, double* 
         out->sum_ce_re = c->sce_re;
         out->sum_ce_im = c->sce_im;
         out->n_used = c->used;
-        out->n_pairs = static_cast<unsigned long long>(ep.n_u - static_cast<long long>(c->invalid)) *
+        out->n_pairs = static_cast<unsigned long long>(hi - lo - static_cast<long long>(c->invalid)) *
                        static_cast<unsigned long long>(pairs_per_sample);
         out->n_hits = c->hits;
         out->n_missing = c->missing;

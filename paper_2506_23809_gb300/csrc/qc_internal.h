@@ -174,6 +174,7 @@ struct MolParams {
     int active_warps;    // warps of a CTA that work on this molecule's samples (the rest idle)
     unsigned warp_stride;  // this molecule's per-warp shared-memory region
     long long r0, r1;      // rows evaluated by this launch (the table holds all n_u rows)
+    long long red_lo, red_hi;  // rows the Eq. 1 reduction runs over
 };
 struct BatchParams {
     const MolParams* mols;

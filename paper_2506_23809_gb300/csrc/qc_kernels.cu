@@ -38,11 +38,11 @@ __global__ void __launch_bounds__(256) build_table_kernel(TableParams tp, int n_
 }
 
 __global__ void __launch_bounds__(kRedThreads) reduce_pass1(EvalParams ep, double* part) {
-    reduce_pass1_body(ep, part, blockIdx.x, gridDim.x);
+    reduce_pass1_body(ep, part, blockIdx.x, gridDim.x, 0, ep.n_u);
 }
 __global__ void __launch_bounds__(kRedThreads) reduce_pass2(EvalParams ep, double* part,
                                                             qc_eloc_summary* out, long long pairs_per_sample) {
-    reduce_pass2_body(ep, part, out, pairs_per_sample, blockIdx.x, gridDim.x);
+    reduce_pass2_body(ep, part, out, pairs_per_sample, blockIdx.x, gridDim.x, 0, ep.n_u);
 }
 
 // ------------------------------------------------------------------------------------

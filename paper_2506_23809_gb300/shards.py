@@ -49,7 +49,8 @@ def allgather_combine(part: np.ndarray, dist, device=None) -> tuple[float, compl
 
 
 # ---------------------------------------------------------------------------------------
-# Cost-weighted plans across replicas (many molecules, uneven sizes)
+# Cost-weighted plans across replicas (many molecules, uneven sizes): Alg. 2 balances the
+# unique samples of partitions by predicted counts; here molecules are cut by measured cost
 # ---------------------------------------------------------------------------------------
 def job_cost(n_rows: int, pairs_per_sample: int, per_sample: float = 4096.0) -> float:
     """Estimated work of n_rows samples of one molecule: every sample enumerates the same
@@ -89,6 +90,98 @@ def plan_replicas(jobs, n_replicas: int, per_sample: float = 4096.0, min_rows: i
     for p in plan:
         p.sort()
     return plan
+
+
+def row_costs_from_timing(ms: float, hits) -> np.ndarray:
+    """Per-row cost (ms) of one molecule from a measured evaluation: its device time `ms`
+    spread over the rows in proportion to (mean hits + the row's hits) -- every row pays its
+    set-up and scans, and the rows near the reference determinant find many more hits."""
+    h = np.asarray(hits, dtype=np.float64)
+    if h.size == 0:
+        return h
+    w = h.mean() + h + 1e-9
+    return float(ms) * w / w.sum()
+
+
+def plan_pieces(row_costs, n_replicas: int):
+    """Cost-weighted plan over replicas (Alg. 2's split, with costs instead of sample counts):
+    row_costs is one array of per-row costs per molecule.  A molecule whose cost exceeds a
+    fair share (total / n_replicas) is cut into contiguous row ranges of about equal cost;
+    pieces then go longest first to the least-loaded replica.  Returns, per replica, a sorted
+    list of (molecule, row0, row1); every row of every molecule is in exactly one piece."""
+    if n_replicas < 1:
+        raise ValueError("n_replicas >= 1")
+    costs = [np.asarray(c, dtype=np.float64) for c in row_costs]
+    totals = [float(c.sum()) for c in costs]
+    share = sum(totals) / n_replicas if sum(totals) > 0 else 0.0
+    pieces = []           # (cost, molecule, r0, r1)
+    for j, (c, tot) in enumerate(zip(costs, totals)):
+        n = c.size
+        if n == 0:
+            continue
+        if share > 0 and tot > share and n > 1:
+            k = min(n, int(np.ceil(tot / share)))
+            cum = np.cumsum(c)
+            cuts = [0] + [int(np.searchsorted(cum, tot * q / k, side="left")) + 1 for q in range(1, k)] + [n]
+            cuts = sorted(set(min(max(x, 0), n) for x in cuts))
+            for r0, r1 in zip(cuts, cuts[1:]):
+                if r1 > r0:
+                    pieces.append((float(c[r0:r1].sum()), j, r0, r1))
+        else:
+            pieces.append((tot, j, 0, n))
+    pieces.sort(key=lambda t: (-t[0], t[1], t[2]))
+    load = [0.0] * n_replicas
+    plan = [[] for _ in range(n_replicas)]
+    for c, j, r0, r1 in pieces:
+        r = min(range(n_replicas), key=lambda i: (load[i], i))
+        load[r] += c
+        plan[r].append((j, r0, r1))
+    for p in plan:
+        p.sort()
+    return plan
+
+
+def combine_pieces(n_mol: int, pieces):
+    """Per-molecule (W, Ebar, var) from the partials of its pieces: pieces is a list of
+    (molecule, partials) with partials as returned by ``partials``."""
+    per = [[] for _ in range(n_mol)]
+    for m, part in pieces:
+        per[m].append(part)
+    return [combine(p) if p else (0.0, complex(np.nan, np.nan), float("nan")) for p in per]
+
+
+def calibrate_row_costs(binding, handles, inputs, stream=None):
+    """Per-row costs of every molecule for plan_pieces, from one timed evaluation each on this
+    device: its main-kernel time spread over its rows by their hit counts."""
+    import torch
+    out = []
+    for h, (keys, counts, psi, eloc) in zip(handles, inputs):
+        binding.qc_eloc_set_option(h, binding.QC_OPT_TIMING, 1)
+        _, d = binding.qc_eloc_eval(h, keys, counts, psi, eloc=eloc, diagnostics=True, stream=stream)
+        ms = binding.qc_eloc_timings(h)[1]
+        out.append(row_costs_from_timing(ms, d["hit_count"].to(torch.int64).cpu().numpy()))
+    return out
+
+
+def evaluate_pieces(binding, handles, inputs, pieces, stream=None, autotune=False, graph=False):
+    """One replica's share of a plan as one batched step: a batch entry per piece (its
+    molecule's handle and whole sample set; only the piece's rows are evaluated and reduced).
+    inputs[m] = (keys, counts, psi, eloc) device tensors of molecule m; E_loc of the piece's
+    rows lands in eloc.  Returns (the batch, [(molecule, partials)] per piece); the caller
+    destroys the batch."""
+    batch = binding.qc_batch_create([handles[m] for m, _, _ in pieces])
+    for i, (m, r0, r1) in enumerate(pieces):
+        keys, counts, psi, eloc = inputs[m]
+        binding.qc_batch_set_inputs(batch, i, keys, counts, psi, eloc)
+        binding.qc_batch_set_rows(batch, i, r0, r1)
+    if autotune:
+        binding.qc_batch_autotune(batch, stream, iters=2)
+    if graph:
+        binding.qc_batch_graph_launch(batch, stream)
+    else:
+        binding.qc_batch_eval(batch, stream)
+    sums = binding.qc_batch_summaries(batch, stream)
+    return batch, [(m, partials(sm)) for (m, _, _), sm in zip(pieces, sums)]
 
 
 def predicted_unique(sample_counts, density_prev) -> np.ndarray:

@@ -116,3 +116,95 @@ def test_density_prediction():
     d = density([50, 0, 30], [100, 0, 30])
     assert np.allclose(d, [0.5, 0.0, 1.0])
     assert np.allclose(predicted_unique([200, 10, 60], d), [100.0, 0.0, 60.0])
+
+
+# ---------------------------------------------------------------------------------------
+# a cost-weighted plan over two gloo ranks (the oracle stands in for the device kernel)
+# ---------------------------------------------------------------------------------------
+PLAN_MOLS = [(20, 6, 2400, 8601), (16, 6, 600, 8602), (24, 8, 900, 8603), (14, 6, 300, 8604)]
+
+
+def _plan_inputs():
+    from paper_2506_23809_gb300 import inputs as I
+    mols = []
+    for n, ne, nu, seed in PLAN_MOLS:
+        K = n // 2
+        ints = I.make_integrals(K, n, seed)
+        keys = I.rank_weighted_samples(K, ne // 2, ne // 2, nu, seed=seed + 1)
+        mols.append((n, ne, ints, keys, I.zipf_counts(nu, 20 * nu, seed + 2), I.lognormal_psi(nu, seed + 3)))
+    return mols
+
+
+def _plan(mols):
+    """The plan every rank derives from the same costs (per-row costs from the oracle's hit
+    counts and a fixed time per molecule: the inputs plan_pieces takes on the device)."""
+    import oracle
+    costs = []
+    for n, ne, ints, keys, counts, psi in mols:
+        _, det = oracle.eloc(ints.h, ints.eri, 0.0, n, keys, psi, details=True, nthreads=1)
+        costs.append(shards.row_costs_from_timing(float(len(keys)), det["hits"]))
+    return shards.plan_pieces(costs, 2)
+
+
+def _plan_worker(rank, world, port, out_path):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    mols = _plan_inputs()
+    plan = _plan(mols)
+    mine = []
+    for m, r0, r1 in plan[rank]:
+        n, ne, ints, keys, counts, psi = mols[m]
+        el = oracle.eloc(ints.h, ints.eri, 0.0, n, keys[r0:r1], psi[r0:r1], keys, psi, nthreads=1)
+        mo, var, w, _ = oracle.reduce(el, counts[r0:r1])
+        mine.append((m, [w, w * mo.real, w * mo.imag, w * var]))
+    got = [None] * world
+    dist.all_gather_object(got, mine)
+    res = shards.combine_pieces(len(mols), [x for g in got for x in g])
+    if rank == 0:
+        np.save(out_path, np.array([[W, E.real, E.imag, V] for W, E, V in res]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_plan_pieces_cover_and_balance():
+    rng = np.random.default_rng(5)
+    costs = [rng.random(n) * s for n, s in ((5000, 5.0), (300, 1.0), (1200, 1.0), (40, 1.0), (1, 1.0))]
+    total = sum(c.sum() for c in costs)
+    for n_rep in (1, 2, 3, 8):
+        plan = shards.plan_pieces(costs, n_rep)
+        seen = {j: [] for j in range(len(costs))}
+        for rep in plan:
+            for j, r0, r1 in rep:
+                seen[j].append((r0, r1))
+        for j, c in enumerate(costs):
+            rs = sorted(seen[j])
+            assert rs[0][0] == 0 and rs[-1][1] == c.size and all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
+        loads = [sum(costs[j][r0:r1].sum() for j, r0, r1 in rep) for rep in plan]
+        # a piece is at most about a fair share: no replica carries more than two shares
+        assert max(loads) <= 2.0 * total / n_rep + 1e-9
+        if n_rep == 2:
+            assert max(loads) <= 1.10 * total / 2
+
+
+def test_two_gloo_ranks_run_a_plan(tmp_path, orc):
+    import multiprocessing as mp
+    port = _free_port()
+    out = str(tmp_path / "plan.npy")
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_plan_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    got = np.load(out)
+    mols = _plan_inputs()
+    plan = _plan(mols)
+    assert sum(len(p) for p in plan) > len(mols)          # a molecule is cut across the ranks
+    for m, (n, ne, ints, keys, counts, psi) in enumerate(mols):
+        el = orc.eloc(ints.h, ints.eri, 0.0, n, keys, psi)
+        mo, var, w, _ = orc.reduce(el, counts)
+        W, er, ei, V = got[m]
+        assert W == w and abs(complex(er, ei) - mo) <= 1e-12 * abs(mo) and abs(V - var) <= 1e-10 * var
