@@ -80,7 +80,8 @@ def _args():
     p.add_argument("--n-par", type=int, default=4096, help="grad form: parameters (columns of d ln Psi*)")
     p.add_argument("--chunk", type=int, default=10000, help="full form: samples per export/apply chunk")
     p.add_argument("--requests", type=int, default=48, help="serve form: requests")
-    p.add_argument("--rate", type=float, default=20.0, help="serve form: arrivals per second")
+    p.add_argument("--rates", default="", help="serve form: comma-separated arrival rates per second "
+                                                "(default: 0.3, 0.7 and 1.5 x the plain capacity)")
     p.add_argument("--quantum", type=float, default=1e12,
                    help="serve form: enumerated pairs per wave (0: one wave takes every ready request)")
     p.add_argument("--oldest-pct", type=int, default=50,
@@ -110,11 +111,16 @@ def _plain_launches(cfg, n_table):
 
 def _batched_launches(specs):
     """Kernels of one batched step: the batch build, the batch kernel and two reduction
-    passes, and for the molecules that take the join (16384 rows up) one shared index: a
+    passes, and for the molecules that take the join (join_by_default: 16384 rows up, or 2e8
+    rows x pairs per sample, or 512 rows at 50000 pairs per sample) one shared index: a
     3-kernel scan, per 11-bit radix pass a histogram, a 3-kernel scan and a scatter, and the
     gather."""
     n = 4
-    slots = sum(2 * (1 << max(0, (2 * sp["n_u"] - 1).bit_length())) for sp in specs if sp["n_u"] >= 16384)
+
+    def joins(sp):
+        p = _pairs(sp["n_orb"], sp["n_elec"]) if "n_orb" in sp else 0
+        return sp["n_u"] >= 16384 or sp["n_u"] * p >= 200_000_000 or (p >= 50_000 and sp["n_u"] >= 512)
+    slots = sum(2 * (1 << max(0, (2 * sp["n_u"] - 1).bit_length())) for sp in specs if joins(sp))
     if slots:
         n += 3 + 5 * (-(-slots.bit_length() // 11)) + 1
     return n
@@ -712,8 +718,15 @@ def _run_batched_plan(args, specs, prec, world, rank, local):
 
 
 def run_serve(args):
-    """Poisson arrivals of requests with their own molecules (N 28..128) and sample sets;
-    latency percentiles and throughput of the server against plain sequential launches."""
+    """Poisson arrivals of requests with their own molecules (the serving spec: N even in
+    28..128, half filling +-4 electrons, lognormal unique-sample counts clipped to 1e3..1e6,
+    rank-N integrals), at three arrival rates set against the measured capacity of plain
+    per-request evaluation (the last above it, so the GPU saturates).  Two arms see the same
+    arrivals: the server (continuous batching) and a live plain FIFO -- one worker thread that
+    creates a handle, uploads, evaluates, reads E_loc back and destroys the handle, request
+    after request in arrival order.  Latency = completion - arrival; sustained throughput =
+    the requests' structural pairs over each arm's busy span."""
+    import queue
     import threading
 
     import numpy as np
@@ -725,78 +738,130 @@ def run_serve(args):
     build.build()
     B.load_library()
     torch.cuda.set_device(0)
-    specs = I.serving_request_specs(args.requests, args.rate)
+    specs = I.serving_request_specs(args.requests, 1.0)     # arrival times at one request per second
+    t_gen = time.perf_counter()
     reqs = []
     for sp in specs:
-        n_u = min(sp["n_u"], 200_000)   # generation cost on the host bounds the largest sets
         K = sp["n_orb"] // 2
-        ints = I.make_integrals(K, min(sp["n_orb"], 64), sp["seed"])
-        keys = I.rank_weighted_samples(K, sp["n_elec"] // 2, sp["n_elec"] // 2, n_u, seed=sp["seed"] + 1)
+        ints = I.make_integrals(K, sp["n_orb"], sp["seed"])
+        keys = I.rank_weighted_samples(K, sp["n_elec"] // 2, sp["n_elec"] // 2, sp["n_u"], seed=sp["seed"] + 1)
         reqs.append(dict(t=sp["t_arrive"], n_orb=sp["n_orb"], n_elec=sp["n_elec"], ints=ints, keys=keys,
-                         counts=I.zipf_counts(n_u, 100 * n_u, sp["seed"] + 2), psi=I.lognormal_psi(n_u, sp["seed"] + 3),
-                         pairs=n_u * _pairs(sp["n_orb"], sp["n_elec"])))
+                         counts=I.zipf_counts(sp["n_u"], 100 * sp["n_u"], sp["seed"] + 2),
+                         psi=I.lognormal_psi(sp["n_u"], sp["seed"] + 3),
+                         pairs=sp["n_u"] * _pairs(sp["n_orb"], sp["n_elec"])))
+    t_gen = time.perf_counter() - t_gen
+    n = len(reqs)
     total_pairs = sum(r["pairs"] for r in reqs)
-    # plain: one handle and one evaluation per request, back to back (integral upload
-    # included); its latencies under the same arrivals follow from FIFO service times
-    service = []
-    t0 = time.perf_counter()
-    for r in reqs:
-        ts = time.perf_counter()
+    base_t = np.array([r["t"] for r in reqs])
+
+    def plain_one(r):
         h = B.qc_eloc_create(r["ints"].h, r["ints"].eri, 0.0, r["n_orb"], r["n_elec"])
         e, _ = B.qc_eloc_eval(h, B.keys_to_tensor(r["keys"]), torch.from_numpy(r["counts"]).cuda(),
                               torch.from_numpy(r["psi"]).cuda())
-        e.cpu()
+        out = e.cpu().numpy()
+        summ = B.qc_eloc_summary_read(h)
         B.qc_eloc_destroy(h)
-        service.append(time.perf_counter() - ts)
-    t_plain = time.perf_counter() - t0
-    free_at, plain_lat = 0.0, []
-    for r, sv in zip(reqs, service):
-        begin = max(free_at, r["t"])
-        free_at = begin + sv
-        plain_lat.append(1e3 * (free_at - r["t"]))
-    srv = B.qc_server_create(0, 160 << 30, max_slots=64, n_streams=2)
-    B.qc_server_set_option(srv, B.QC_SRV_OPT_QUANTUM, int(args.quantum))
-    B.qc_server_set_option(srv, B.QC_SRV_OPT_OLDEST_PCT, int(args.oldest_pct))
-    done = {}
-    tickets = [None] * len(reqs)
-    start = time.perf_counter()
+        return out, summ
 
-    def client():
-        for i, r in enumerate(reqs):
-            delay = r["t"] - (time.perf_counter() - start)
-            if delay > 0:
-                time.sleep(delay)
-            tickets[i] = B.qc_eloc_submit(srv, r["ints"].h, r["ints"].eri, 0.0, r["n_orb"], r["n_elec"],
-                                          r["keys"], r["counts"], r["psi"], mol_key=i + 1)
-    th = threading.Thread(target=client)
-    th.start()
-    while len(done) < len(reqs):
-        for i, t in enumerate(tickets):
-            if t is not None and i not in done:
-                out = B.qc_eloc_poll(srv, t, 1000)
-                if out is not None:
-                    done[i] = out[0]
-        time.sleep(0.0005)
-    th.join()
-    t_all = time.perf_counter() - start
-    B.qc_server_destroy(srv)
-    lat = np.array([done[i]["t_done"] - done[i]["t_submit"] for i in range(len(reqs))]) * 1e3
-    ok = all(done[i]["status"] == 0 for i in done)
-    line = {"metric": METRIC, "form": "serve", "value": total_pairs / t_all, "unit": UNIT, "n_gpus": 1,
-            "higher_is_better": True, "dtype": "f64",
-            "config": {"workload": f"serve_{args.requests}_requests_poisson_{args.rate}_per_s",
-                       "requests": len(reqs), "rate_per_s": args.rate, "budget_gb": 160,
+    # warm-up (kernel loading, allocator pools), then capacity: every request back to back
+    plain_one(min(reqs, key=lambda r: len(r["keys"])))
+    torch.cuda.synchronize()
+    service = []
+    for r in reqs:
+        t0 = time.perf_counter()
+        plain_one(r)
+        service.append(time.perf_counter() - t0)
+    capacity = n / sum(service)                         # requests per second, plain
+    rates = [float(x) for x in args.rates.split(",")] if args.rates else \
+        [0.3 * capacity, 0.7 * capacity, 1.5 * capacity]
+
+    def plain_live(t_arr):
+        q = queue.Queue()
+        done = np.zeros(n)
+        start = time.perf_counter()
+
+        def client():
+            for i in np.argsort(t_arr, kind="stable"):
+                d = start + t_arr[i] - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                q.put(int(i))
+            q.put(None)
+        th = threading.Thread(target=client)
+        th.start()
+        t_first = None
+        while True:
+            i = q.get()
+            if i is None:
+                break
+            if t_first is None:
+                t_first = time.perf_counter() - start
+            plain_one(reqs[i])
+            done[i] = time.perf_counter() - start
+        th.join()
+        lat = 1e3 * (done - t_arr)
+        return lat, total_pairs / (done.max() - t_first), done.max()
+
+    def served(t_arr):
+        srv = B.qc_server_create(0, 160 << 30, max_slots=64, n_streams=2)
+        B.qc_server_set_option(srv, B.QC_SRV_OPT_QUANTUM, int(args.quantum))
+        B.qc_server_set_option(srv, B.QC_SRV_OPT_OLDEST_PCT, int(args.oldest_pct))
+        res = {}
+        tickets = [None] * n
+        start = time.perf_counter()
+
+        def client():
+            for i in np.argsort(t_arr, kind="stable"):
+                d = start + t_arr[i] - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                r = reqs[i]
+                tickets[i] = B.qc_eloc_submit(srv, r["ints"].h, r["ints"].eri, 0.0, r["n_orb"], r["n_elec"],
+                                              r["keys"], r["counts"], r["psi"], mol_key=i + 1,
+                                              borrow_integrals=True)
+        th = threading.Thread(target=client)
+        th.start()
+        while len(res) < n:
+            for i, t in enumerate(tickets):
+                if t is not None and i not in res:
+                    out = B.qc_eloc_poll(srv, t, 1000)
+                    if out is not None:
+                        res[i] = out[0]
+            time.sleep(0.0005)
+        th.join()
+        B.qc_server_destroy(srv)
+        lat = np.array([res[i]["t_done"] - res[i]["t_submit"] for i in range(n)]) * 1e3
+        span = max(res[i]["t_done"] for i in range(n)) - min(res[i]["t_submit"] for i in range(n))
+        stages = {k: float(np.median([1e3 * (res[i][b] - res[i][a]) for i in range(n)]))
+                  for k, a, b in (("submit_to_admit", "t_submit", "t_admit"), ("admit_to_start", "t_admit", "t_start"),
+                                  ("start_to_done", "t_start", "t_done"))}
+        served.stages = stages
+        return lat, total_pairs / span, all(res[i]["status"] == 0 for i in range(n))
+
+    per_rate = []
+    for rate in rates:
+        t_arr = base_t / rate
+        lp, thr_p, _ = plain_live(t_arr)
+        ls, thr_s, ok = served(t_arr)
+        per_rate.append({"rate_per_s": rate, "load_vs_plain_capacity": rate / capacity,
+                         "served_ms": {"p50": float(np.percentile(ls, 50)), "p99": float(np.percentile(ls, 99)),
+                                       "max": float(ls.max())},
+                         "plain_fifo_live_ms": {"p50": float(np.percentile(lp, 50)),
+                                                "p99": float(np.percentile(lp, 99)), "max": float(lp.max())},
+                         "served_sustained_pairs_per_s": thr_s, "plain_sustained_pairs_per_s": thr_p,
+                         "served_median_stage_ms": served.stages, "all_ok": bool(ok)})
+        print(json.dumps({"form": "serve", "progress": per_rate[-1]}), file=sys.stderr, flush=True)
+    sat = per_rate[-1]
+    line = {"metric": METRIC, "form": "serve", "value": sat["served_sustained_pairs_per_s"], "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
+            "config": {"workload": f"serve_{n}_requests_poisson_3_rates", "requests": n, "budget_gb": 160,
                        "wave_quantum_pairs": int(args.quantum), "oldest_share_pct": int(args.oldest_pct),
-                       "streams": 2,
-                       "n_orb_range": [min(r["n_orb"] for r in reqs), max(r["n_orb"] for r in reqs)],
-                       "max_samples": int(max(len(r["keys"]) for r in reqs)), "pairs_total": int(total_pairs)},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max())},
-            "plain_fifo_latency_ms": {"p50": float(np.percentile(plain_lat, 50)),
-                                      "p99": float(np.percentile(plain_lat, 99))},
-            "wall_s": {"served_including_arrival_gaps": t_all, "plain_sequential": t_plain,
-                       "arrival_span": reqs[-1]["t"]},
-            "all_ok": bool(ok)}
+                       "streams": 2, "n_orb_range": [min(r["n_orb"] for r in reqs), max(r["n_orb"] for r in reqs)],
+                       "n_u_range": [int(min(len(r["keys"]) for r in reqs)), int(max(len(r["keys"]) for r in reqs))],
+                       "samples_total": int(sum(len(r["keys"]) for r in reqs)), "pairs_total": int(total_pairs),
+                       "integral_rank": "N", "input_generation_s": t_gen},
+            "plain_capacity_req_per_s": capacity, "plain_back_to_back_s": float(sum(service)),
+            "rates": per_rate}
     print(json.dumps(line), flush=True)
     return 0
 

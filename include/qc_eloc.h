@@ -112,7 +112,8 @@ typedef int qc_status;
                                    more warps), 1 stored pair lists, 2 pair lists formed on the
                                    fly from per-orbital values (same results, less shared memory) */
 #define QC_OPT_JOIN         10  /* sample-space mode, filtered kernel: 0 auto (on from 16384
-                                   table rows), 1 off, 2 on.  On,
+                                   table rows, from 2e8 table rows x connected pairs per sample,
+                                   or from 512 rows when a sample has 50000 pairs), 1 off, 2 on.  On,
                                    the table rows are also grouped by alpha string and by beta
                                    string (a per-evaluation index); a short group that can hold
                                    connected keys is scanned row by row, the excitations into a
@@ -390,12 +391,14 @@ qc_status qc_batch_autotune(qc_batch* batch, void* stream, int iters, int64_t* b
  * any mix: the batch runs the single-molecule per-sample code, and a sliced request's
  * Eq. 1 reduction runs once, over all of its rows, with its last slice. */
 typedef struct qc_server qc_server;
+#define QC_JOB_BORROW_INTEGRALS 1  /* qc_eloc_job.flags: h and eri stay valid until the ticket
+                                      is polled done, so submit does not copy them */
 typedef struct {
     const double* h;       /* host FP64 integrals as for qc_eloc_create: copied at submit   */
-    const double* eri;     /* unless the molecule (mol_key) is resident                     */
+    const double* eri;     /* unless the molecule (mol_key) is resident or flags borrows them */
     double e_core;
     int n_orb, n_elec, precision;  /* QC_FP64 | QC_FP32_COMP; sample-space mode             */
-    int pad;
+    int flags;             /* QC_JOB_BORROW_INTEGRALS or 0                                  */
     uint64_t mol_key;      /* nonzero: keep this Hamiltonian resident under this key        */
     const uint64_t* samples;  /* host uint64[n_u][2], sorted unique; with counts and psi,   */
     const int64_t* counts;    /* valid until the ticket is polled done                      */

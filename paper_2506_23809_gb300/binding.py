@@ -541,7 +541,7 @@ def qc_batch_set_chunk_pairs(batch: QcBatch, chunk_pairs: int):
 class qc_eloc_job(ctypes.Structure):
     _fields_ = [("h", ctypes.c_void_p), ("eri", ctypes.c_void_p), ("e_core", ctypes.c_double),
                 ("n_orb", ctypes.c_int), ("n_elec", ctypes.c_int), ("precision", ctypes.c_int),
-                ("pad", ctypes.c_int), ("mol_key", ctypes.c_uint64), ("samples", ctypes.c_void_p),
+                ("flags", ctypes.c_int), ("mol_key", ctypes.c_uint64), ("samples", ctypes.c_void_p),
                 ("counts", ctypes.c_void_p), ("psi", ctypes.c_void_p), ("n_u", ctypes.c_int64),
                 ("eloc_out", ctypes.c_void_p)]
 
@@ -585,9 +585,15 @@ def qc_server_create(device: int = 0, budget_bytes: int = 160 << 30, max_slots: 
     return QcServer(out, {})
 
 
+QC_JOB_BORROW_INTEGRALS = 1
+
+
 def qc_eloc_submit(server: QcServer, h, eri, e_core: float, n_orb: int, n_elec: int, keys, counts, psi,
-                   precision: int = QC_FP64, mol_key: int = 0, want_eloc: bool = True) -> int:
-    """Queue one request (host numpy inputs); returns its ticket."""
+                   precision: int = QC_FP64, mol_key: int = 0, want_eloc: bool = True,
+                   borrow_integrals: bool = False) -> int:
+    """Queue one request (host numpy inputs); returns its ticket.  With borrow_integrals the
+    server reads h and eri when it admits the request instead of copying them at submit (they
+    are kept alive here until the ticket is polled)."""
     h = np.ascontiguousarray(h, dtype=np.float64)
     eri = np.ascontiguousarray(eri, dtype=np.float64)
     keys = np.ascontiguousarray(keys, dtype=np.uint64)
@@ -595,14 +601,15 @@ def qc_eloc_submit(server: QcServer, h, eri, e_core: float, n_orb: int, n_elec: 
     psi = np.ascontiguousarray(psi, dtype=np.complex128)
     out = np.empty(len(keys), dtype=np.complex128) if want_eloc else None
     j = qc_eloc_job(h=h.ctypes.data, eri=eri.ctypes.data, e_core=float(e_core), n_orb=int(n_orb),
-                    n_elec=int(n_elec), precision=int(precision), pad=0, mol_key=int(mol_key),
+                    n_elec=int(n_elec), precision=int(precision),
+                    flags=QC_JOB_BORROW_INTEGRALS if borrow_integrals else 0, mol_key=int(mol_key),
                     samples=keys.ctypes.data, counts=counts.ctypes.data, psi=psi.ctypes.data, n_u=len(keys),
                     eloc_out=None if out is None else out.ctypes.data)
     t = ctypes.c_uint64()
     st = _server_lib().qc_eloc_submit(server.ptr, ctypes.byref(j), ctypes.byref(t))
     if st != QC_OK:
         raise QcError(st, "qc_eloc_submit refused the request")
-    server.keep[t.value] = (keys, counts, psi, out)
+    server.keep[t.value] = (keys, counts, psi, out, h, eri)
     return t.value
 
 

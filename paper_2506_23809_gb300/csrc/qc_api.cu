@@ -413,12 +413,12 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
     int warps = 0;
     int lean = 0;
     // the join needs the spin-string sets and strings that are never empty (no spin without
-    // electrons); by default taken from qc::kJoinMinRows table rows up (below that its index
+    // electrons); by default taken when qc::join_by_default says so (below that its index
     // build, a few microseconds per launch, outweighs what it saves); built with U = 4
     // (its sort keys are 32-bit: both sets' slots and the sentinel below 2^32)
     const bool join = kernel == 2 && H->mode == QC_SAMPLE && H->opt_prefilter && H->na > 0 && H->nb > 0 &&
                       n_table > 0 && table_buckets(n_table) <= (1ULL << 30) &&
-                      (H->opt_join == 2 || (H->opt_join == 0 && n_table >= qc::kJoinMinRows));
+                      (H->opt_join == 2 || (H->opt_join == 0 && qc::join_by_default(n_table, sp.pairs)));
     if (kernel == 2) {
         // filter sized for ~16 bits per key, 2^10..2^15 words; then as many warps as fit,
         // shrinking the filter while that leaves fewer than 8.  With the join, which sends

@@ -88,6 +88,10 @@ struct qc_batch {
     // timing of the last eager evaluation
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool timed = false;
+    // non-null (the serving form's lanes): the arena and the join index grow stream-ordered on
+    // this stream and the parameter blocks are copied on it, so a wave's set-up never waits for
+    // work on other streams (a plain cudaFree waits for the whole device)
+    cudaStream_t alloc_stream = nullptr;
     std::string err;
 };
 
@@ -112,6 +116,13 @@ int filter_log2(long long n) {
 // fill the parameter blocks and order the molecules by estimated running time, longest
 // first, so that the small ones fill the tail of the launch.
 qc_status prepare(qc_batch* B) {
+    // host-to-device copies of the parameter blocks: on the allocation stream when the batch
+    // has one (ordered after its stream-ordered allocations; pageable sources are staged
+    // before the call returns), else synchronous
+    auto h2d = [B](void* dst, const void* src, size_t bytes) {
+        return B->alloc_stream ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, B->alloc_stream)
+                               : cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
     const int M = B->n_mol;
     B->red_blocks = 1;
     std::vector<qc::MolParams> mp(M);
@@ -129,7 +140,7 @@ qc_status prepare(qc_batch* B) {
     for (int m = 0; m < M; ++m) {
         const qc_eloc* H = B->handles[m];
         jm[m] = H->opt_prefilter && H->na > 0 && H->nb > 0 &&
-                (H->opt_join == 2 || (H->opt_join == 0 && B->in[m].n_u >= qc::kJoinMinRows));
+                (H->opt_join == 2 || (H->opt_join == 0 && qc::join_by_default(B->in[m].n_u, H->sp.pairs)));
         join = join || jm[m];
     }
     B->join = join;
@@ -213,12 +224,17 @@ qc_status prepare(qc_batch* B) {
         off = align256(off + static_cast<size_t>(slot_base[M]) * 4);
     }
     if (off > B->arena_cap) {
-        // grow with headroom: a reallocation (cudaFree) waits for the whole device
-        if (B->d_arena) cudaFree(B->d_arena);
+        // grow with headroom: a reallocation (cudaFree) waits for the whole device, unless
+        // the batch allocates stream-ordered
+        if (B->d_arena) {
+            if (B->alloc_stream) cudaFreeAsync(B->d_arena, B->alloc_stream);
+            else cudaFree(B->d_arena);
+        }
         B->d_arena = nullptr;
         B->arena_cap = 0;
         const size_t cap = align256(off + off / 2);
-        cudaError_t e = qc::dev_alloc(&B->d_arena, cap);
+        cudaError_t e = B->alloc_stream ? cudaMallocAsync(reinterpret_cast<void**>(&B->d_arena), cap, B->alloc_stream)
+                                        : qc::dev_alloc(&B->d_arena, cap);
         if (e != cudaSuccess) return bcuda(B, e, "cudaMalloc batch arena");
         B->arena_cap = cap;
     }
@@ -238,20 +254,22 @@ qc_status prepare(qc_batch* B) {
         B->jo_pab = jo; jo = align256(jo + 2 * align256(rows * 4));
         B->jo_ws = jo; jo = align256(jo + qc::join_batch_workspace_bytes(mi, ns));
         if (jo > B->join_cap) {
-            if (B->d_join) cudaFree(B->d_join);
+            if (B->d_join) {
+                if (B->alloc_stream) cudaFreeAsync(B->d_join, B->alloc_stream);
+                else cudaFree(B->d_join);
+            }
             B->d_join = nullptr;
             B->join_cap = 0;
             const size_t cap = align256(jo + jo / 2);
-            cudaError_t e = qc::dev_alloc(&B->d_join, cap);
+            cudaError_t e = B->alloc_stream ? cudaMallocAsync(reinterpret_cast<void**>(&B->d_join), cap, B->alloc_stream)
+                                            : qc::dev_alloc(&B->d_join, cap);
             if (e != cudaSuccess) return bcuda(B, e, "cudaMalloc batch join index");
             B->join_cap = cap;
         }
         B->j_items = mi;
         B->j_slots = ns;
-        cudaError_t e = cudaMemcpy(B->d_join + B->jo_base, slot_base.data(), (M + 1) * sizeof(unsigned),
-                                   cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(B->d_join + B->jo_rbase, row_base.data(), (M + 1) * sizeof(unsigned), cudaMemcpyHostToDevice);
+        cudaError_t e = h2d(B->d_join + B->jo_base, slot_base.data(), (M + 1) * sizeof(unsigned));
+        if (e == cudaSuccess) e = h2d(B->d_join + B->jo_rbase, row_base.data(), (M + 1) * sizeof(unsigned));
         if (e != cudaSuccess) return bcuda(B, e, "copy join slot and row bases");
     }
     for (int m = 0; m < M; ++m) {
@@ -344,14 +362,14 @@ qc_status prepare(qc_batch* B) {
     B->n_keys = key_off[M];
     cudaError_t e;
     if (!order.empty()) {
-        e = cudaMemcpy(B->d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice);
+        e = h2d(B->d_order, order.data(), order.size() * sizeof(int));
         if (e != cudaSuccess) return bcuda(B, e, "copy run order");
     }
-    e = cudaMemcpy(B->d_mols, mp.data(), M * sizeof(qc::MolParams), cudaMemcpyHostToDevice);
+    e = h2d(B->d_mols, mp.data(), M * sizeof(qc::MolParams));
     if (e != cudaSuccess) return bcuda(B, e, "copy molecule parameters");
-    e = cudaMemcpy(B->d_work, mw.data(), M * sizeof(qc::MolWork), cudaMemcpyHostToDevice);
+    e = h2d(B->d_work, mw.data(), M * sizeof(qc::MolWork));
     if (e != cudaSuccess) return bcuda(B, e, "copy molecule workspaces");
-    e = cudaMemcpy(B->d_key_off, key_off.data(), (M + 1) * sizeof(long long), cudaMemcpyHostToDevice);
+    e = h2d(B->d_key_off, key_off.data(), (M + 1) * sizeof(long long));
     if (e != cudaSuccess) return bcuda(B, e, "copy key offsets");
     B->dirty = false;
     B->warps_used = warps;
@@ -479,6 +497,14 @@ qc_status qc::batch_set_slice(qc_batch* B, int mol, long long r0, long long r1, 
     I.piece = false;
     B->dirty = true;
     drop_graph(B);
+    return QC_OK;
+}
+
+// The serving form's lanes: grow the batch's device buffers stream-ordered on `s` (the lane
+// stream its waves run on) and copy the parameter blocks there.
+qc_status qc::batch_set_alloc_stream(qc_batch* B, cudaStream_t s) {
+    if (!B) return QC_ERR_ARG;
+    B->alloc_stream = s;
     return QC_OK;
 }
 

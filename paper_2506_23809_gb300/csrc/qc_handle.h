@@ -80,4 +80,6 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, LaunchCfg&
 qc_status batch_retarget(qc_batch* B, qc_eloc* const* handles, int n_mol);
 // one slice of a molecule's rows per step (the serving form's long requests)
 qc_status batch_set_slice(qc_batch* B, int mol, long long r0, long long r1, bool reduce, Counters* ctr);
+// grow the batch's device buffers stream-ordered on s and copy its parameter blocks there
+qc_status batch_set_alloc_stream(qc_batch* B, cudaStream_t s);
 }  // namespace qc

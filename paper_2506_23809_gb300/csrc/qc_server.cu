@@ -18,6 +18,10 @@
 //     a wave of their own before the next slice;
 //   * completion -- found by polling CUDA events (no blocking device waits); results are
 //     copied to the caller's host buffers and the request's memory is released.
+// Admission (creating a Hamiltonian and uploading a request's inputs, the slow host-side
+// part) runs on a thread of its own, so waves keep being launched and retired meanwhile;
+// each lane's batch grows its device buffers stream-ordered on the lane's stream, so a
+// wave's set-up never waits for another lane's wave.
 // Because a batch runs the single-molecule per-sample code, and a sliced request's Eq. 1
 // reduction runs once over all of its rows in its last wave, a request's E_loc and energy
 // are bitwise the same alone and in any mix.
@@ -56,6 +60,7 @@ struct Resident {  // a molecule's Hamiltonian kept on the device
     size_t bytes = 0;
     int users = 0;        // requests in flight using it
     double last_use = 0.0;
+    bool evaluating = false;  // a wave runs on the handle's own workspace (single-molecule path)
 };
 
 struct Request {
@@ -79,6 +84,7 @@ struct Request {
 struct Wave {
     std::vector<Request*> reqs;
     int stream = 0;  // index into the wave streams; its batch, summaries and event
+    bool single = false;  // one whole request through the single-molecule path
 };
 
 struct Lane {  // one wave stream with the objects reused by its waves
@@ -113,6 +119,7 @@ struct qc_server {
     std::vector<Lane> lanes;
     std::mutex mu;
     std::condition_variable cv_submit;   // wakes the scheduler
+    std::condition_variable cv_admit;    // wakes the admission thread (a submit, or memory freed)
     std::condition_variable cv_done;     // wakes pollers
     std::deque<Request*> pending;        // submitted, not admitted
     std::vector<Request*> ready;         // admitted, inputs on the device, not launched
@@ -126,6 +133,7 @@ struct qc_server {
     bool last_wave_sliced = false;       // the last wave ran a slice of a long request
     bool stop = false;
     std::thread worker;
+    std::thread admitter;
     cudaError_t fatal = cudaSuccess;
 };
 
@@ -150,6 +158,7 @@ void finish_request(qc_server* S, Request* r, cudaStream_t s) {
     S->used -= r->bytes;
     S->active--;
     r->done = true;
+    S->cv_admit.notify_all();  // memory and a slot came free
 }
 
 // Evict unused resident Hamiltonians, least recently used first, until `need` fits.
@@ -171,10 +180,10 @@ bool make_room(qc_server* S, size_t need) {
 }
 
 // Admit pending requests in arrival order while memory and slots allow.  Called by the
-// scheduler thread with the lock held; the lock is released while a new Hamiltonian is
-// created and while a request's inputs are copied to the device, so submit and poll do not
-// wait for those copies.  Only the scheduler thread admits, so a molecule created here is
-// complete before a later request for it is admitted.
+// admission thread with the lock held; the lock is released while a new Hamiltonian is
+// created and while a request's inputs are copied to the device, so submit, poll and the
+// scheduler do not wait for those copies.  Only the admission thread admits, so a molecule
+// created here is complete before a later request for it is admitted.
 void admit(qc_server* S, std::unique_lock<std::mutex>& lk) {
     while (!S->pending.empty() && S->active < S->max_slots) {
         Request* r = S->pending.front();
@@ -220,9 +229,11 @@ void admit(qc_server* S, std::unique_lock<std::mutex>& lk) {
         // ---- outside the lock: the Hamiltonian and the inputs go to the device ----
         qc_status st = QC_OK;
         qc_eloc* made = nullptr;
-        if (create)
-            st = qc_eloc_create(r->h.data(), r->eri.data(), j.e_core, j.n_orb, j.n_elec, j.precision, QC_SAMPLE,
-                                &made);
+        if (create) {
+            const bool own = !r->h.empty();  // copied at submit, else borrowed from the caller
+            st = qc_eloc_create(own ? r->h.data() : j.h, own ? r->eri.data() : j.eri, j.e_core, j.n_orb, j.n_elec,
+                                j.precision, QC_SAMPLE, &made);
+        }
         r->h.clear();
         r->h.shrink_to_fit();
         r->eri.clear();
@@ -259,6 +270,7 @@ void admit(qc_server* S, std::unique_lock<std::mutex>& lk) {
         }
         r->pairs_per_row = std::max<long long>(1, qc_eloc_pairs_per_sample(res->handle));
         S->ready.push_back(r);
+        S->cv_submit.notify_all();
     }
 }
 
@@ -351,14 +363,50 @@ void launch_wave(qc_server* S, Lane& L, int lane_index) {
     run_wave(S, L, lane_index, prec, take);
 }
 
-// Launch `take` (with their row slices set) as one batch on lane L.
+// Launch `take` (with their row slices set) as one batch on lane L.  A wave of one whole
+// request whose Hamiltonian no other wave is using runs the single-molecule path on that
+// handle's own workspace instead: the widest launch shape, and E_loc exactly the handle API's.
 void run_wave(qc_server* S, Lane& L, int lane_index, int prec, const std::vector<Request*>& take) {
+    if (take.size() == 1 && take[0]->next_row == 0 && take[0]->slice_end == take[0]->job.n_u &&
+        !take[0]->res->evaluating) {
+        Request* r = take[0];
+        qc_eloc_out out{};
+        out.eloc = r->d_eloc;
+        out.summary = L.sums;
+        const double t0 = now_s();
+        cudaError_t e = cudaEventRecord(L.ev, S->upload);   // after the request's uploads
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(L.stream, L.ev, 0);
+        qc_status st = QC_ERR_CUDA;
+        if (e == cudaSuccess)
+            st = qc_eloc_eval(r->res->handle, r->d_keys, r->d_counts, r->d_psi, r->job.n_u, nullptr, nullptr, 0,
+                              &out, L.stream);
+        if (st == QC_OK) e = cudaEventRecord(L.ev, L.stream);
+        if (st != QC_OK || e != cudaSuccess) {
+            r->result.status = st != QC_OK ? st : QC_ERR_CUDA;
+            finish_request(S, r, L.stream);
+            S->cv_done.notify_all();
+            return;
+        }
+        if (r->result.t_start == 0.0) r->result.t_start = t0;
+        r->res->evaluating = true;
+        Wave w;
+        w.reqs = take;
+        w.stream = lane_index;
+        w.single = true;
+        L.busy = true;
+        S->waves.push_back(w);
+        return;
+    }
     std::vector<qc_eloc*> hs;
     for (Request* r : take) hs.push_back(r->res->handle);
     qc_status st = QC_OK;
     qc_batch*& B = L.batch[prec];
-    if (!B) st = qc_batch_create(hs.data(), static_cast<int>(hs.size()), &B);
-    else st = qc::batch_retarget(B, hs.data(), static_cast<int>(hs.size()));
+    if (!B) {
+        st = qc_batch_create(hs.data(), static_cast<int>(hs.size()), &B);
+        if (st == QC_OK) st = qc::batch_set_alloc_stream(B, L.stream);
+    } else {
+        st = qc::batch_retarget(B, hs.data(), static_cast<int>(hs.size()));
+    }
     for (size_t m = 0; m < take.size() && st == QC_OK; ++m) {
         Request* r = take[m];
         st = qc_batch_set_inputs(B, static_cast<int>(m), r->d_keys, r->d_counts, r->d_psi, r->job.n_u, r->d_eloc);
@@ -417,6 +465,7 @@ bool retire(qc_server* S) {
             r->result.status = e == cudaSuccess ? L.sums[m].status : QC_ERR_CUDA;
             r->result.t_done = now_s();
             (void)t;
+            if (it->single && r->res) r->res->evaluating = false;  // its handle's workspace is free
             finish_request(S, r, L.stream);
         }
         L.busy = false;
@@ -426,16 +475,27 @@ bool retire(qc_server* S) {
     return any;
 }
 
+// The admission thread: admits whatever fits whenever a request is submitted or memory
+// and slots come free.
+void admission(qc_server* S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (true) {
+        admit(S, lk);
+        if (S->stop && S->pending.empty()) break;
+        S->cv_admit.wait_for(lk, std::chrono::milliseconds(50));
+    }
+}
+
 void scheduler(qc_server* S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     while (true) {
         if (retire(S)) S->cv_done.notify_all();
-        admit(S, lk);
         // continuous batching: every free lane takes the requests that are ready now
         for (size_t i = 0; i < S->lanes.size() && !S->ready.empty(); ++i)
             if (!S->lanes[i].busy) launch_wave(S, S->lanes[i], static_cast<int>(i));
-        if (S->stop && S->pending.empty() && S->ready.empty() && S->waves.empty()) break;
+        if (S->stop && S->pending.empty() && S->ready.empty() && S->waves.empty() && S->active == 0) break;
         if (S->waves.empty() && S->ready.empty())
             S->cv_submit.wait_for(lk, std::chrono::milliseconds(50));
         else {
@@ -474,6 +534,7 @@ qc_status qc_server_create(int device, uint64_t budget_bytes, int max_slots, int
         return QC_ERR_CUDA;
     }
     S->worker = std::thread(scheduler, S);
+    S->admitter = std::thread(admission, S);
     *out = S;
     return QC_OK;
 }
@@ -484,29 +545,35 @@ qc_status qc_eloc_submit(qc_server* S, const qc_eloc_job* job, uint64_t* ticket)
         (job->n_elec & 1) || job->n_u < 0 || (job->n_u > 0 && (!job->samples || !job->counts || !job->psi)) ||
         !job->h || !job->eri || (job->precision != QC_FP64 && job->precision != QC_FP32_COMP))
         return QC_ERR_ARG;
+    const double t_call = now_s();  // latency counts from the call, copies included
+    if (job->flags & ~QC_JOB_BORROW_INTEGRALS) return QC_ERR_ARG;
     auto r = std::make_unique<Request>();
     r->job = *job;
     r->bytes = request_bytes(job->n_u);
     const size_t ham = hamiltonian_bytes(job->n_orb, job->precision);
     if (r->bytes + ham > S->budget) return QC_ERR_BUDGET;
-    std::lock_guard<std::mutex> lk(S->mu);
+    std::unique_lock<std::mutex> lk(S->mu);
     if (S->stop) return QC_ERR_ARG;
     auto rit = job->mol_key ? S->residents.find(job->mol_key) : S->residents.end();
     if (rit != S->residents.end()) {  // resident: pin it until this request finishes
         r->res = rit->second.get();
         r->res->users++;
-    } else {  // the caller may free its integrals after submit
+    } else if (!(job->flags & QC_JOB_BORROW_INTEGRALS)) {
+        // the caller may free its integrals after submit: copy them, outside the lock
+        lk.unlock();
         const size_t K = static_cast<size_t>(job->n_orb / 2);
         r->h.assign(job->h, job->h + K * K);
         r->eri.assign(job->eri, job->eri + K * K * K * K);
+        lk.lock();
+        if (S->stop) return QC_ERR_ARG;
     }
     r->ticket = S->next_ticket++;
-    r->result.t_submit = now_s();
+    r->result.t_submit = t_call;
     *ticket = r->ticket;
     Request* raw = r.release();
     S->all[raw->ticket] = raw;
     S->pending.push_back(raw);
-    S->cv_submit.notify_all();
+    S->cv_admit.notify_all();
     return QC_OK;
 }
 
@@ -550,7 +617,9 @@ qc_status qc_server_destroy(qc_server* S) {
         std::lock_guard<std::mutex> lk(S->mu);
         S->stop = true;
         S->cv_submit.notify_all();
+        S->cv_admit.notify_all();
     }
+    if (S->admitter.joinable()) S->admitter.join();
     if (S->worker.joinable()) S->worker.join();
     cudaSetDevice(S->device);
     for (auto& kv : S->all) delete kv.second;
