@@ -74,6 +74,7 @@ typedef int qc_status;
 #define QC_ERR_TIMEOUT   -10   /* a bounded device wait ran out */
 #define QC_ERR_CAPACITY  -11   /* size beyond a compiled or reserved limit */
 #define QC_ERR_COUNTS    -12   /* negative count */
+#define QC_ERR_BOUNDS    -13   /* an index failed its bounds check (QC_CHECKED builds only) */
 
 /* device-detected condition bits in qc_eloc_summary.flags */
 #define QC_FLAG_UNSORTED   0x01u
@@ -85,6 +86,8 @@ typedef int qc_status;
 #define QC_FLAG_TABLE_FULL 0x40u
 #define QC_FLAG_TIMEOUT    0x80u
 #define QC_FLAG_LIST_FULL  0x100u  /* a hit list position fell outside hit_list_cap */
+#define QC_FLAG_BOUNDS     0x200u  /* QC_CHECKED builds: an integral, table or list index was
+                                      out of range (the access was skipped) */
 
 /* precision */
 #define QC_FP64        0   /* every floating-point step in FP64 */

@@ -15,6 +15,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqc_eloc.so")
+LIB_CHECKED_PATH = os.path.join(HERE, "libqc_eloc_checked.so")
 
 QC_OK, QC_PENDING = 0, 1
 QC_FP64, QC_FP32_COMP = 0, 1
@@ -34,7 +35,7 @@ QC_SRV_OPT_OLDEST_PCT = 2
 STATUS_NAMES = {0: "QC_OK", 1: "QC_PENDING", -1: "QC_ERR_ARG", -2: "QC_ERR_UNSORTED", -3: "QC_ERR_DUP",
                 -4: "QC_ERR_NELEC", -5: "QC_ERR_OOM", -6: "QC_ERR_BUDGET", -7: "QC_ERR_CUDA",
                 -8: "QC_ERR_ZERO_PSI", -9: "QC_ERR_MISSING", -10: "QC_ERR_TIMEOUT",
-                -11: "QC_ERR_CAPACITY", -12: "QC_ERR_COUNTS"}
+                -11: "QC_ERR_CAPACITY", -12: "QC_ERR_COUNTS", -13: "QC_ERR_BOUNDS"}
 
 
 class QcError(RuntimeError):

@@ -3,6 +3,11 @@
 Each .cu under csrc/ compiles to an object in _build/ (in parallel), then one shared
 library is linked next to this file.  ``-Xptxas -v`` output is kept in
 _build/ptxas_<unit>.log for register / spill / shared-memory checks.
+
+``build(checked=True)`` makes libqc_eloc_checked.so from the same sources with QC_CHECKED
+defined: every table, integral and work-list index in the kernels is then bounds-checked
+(an index out of range sets QC_FLAG_BOUNDS and the call returns QC_ERR_BOUNDS).  It is a
+testing build; the product library has no such checks.
 """
 from __future__ import annotations
 
@@ -16,6 +21,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libqc_eloc.so")
+LIB_CHECKED = os.path.join(HERE, "libqc_eloc_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = ["qc_api.cu", "qc_batch.cu", "qc_server.cu", "qc_kernels.cu", "qc_kernels_diag.cu", "qc_batch_kernels.cu", "qc_static.cu", "qc_grad.cu", "qc_dedup.cu", "qc_full.cu", "qc_probe.cu", "qc_join.cu"]
 
@@ -33,25 +39,29 @@ def _sources():
     return srcs
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(s) <= t for s in _sources())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    out = os.path.join(BUILD, "checked") if checked else BUILD
+    os.makedirs(out, exist_ok=True)
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-Xptxas", "-v"]
+    if checked:
+        common += ["-DQC_CHECKED"]
     procs = []
     objs = []
     for u in UNITS:
-        obj = os.path.join(BUILD, u.replace(".cu", ".o"))
-        log = os.path.join(BUILD, f"ptxas_{u.replace('.cu', '')}.log")
+        obj = os.path.join(out, u.replace(".cu", ".o"))
+        log = os.path.join(out, f"ptxas_{u.replace('.cu', '')}.log")
         objs.append(obj)
         cmd = [nvcc] + common + ["-c", os.path.join(CSRC, u), "-o", obj]
         f = open(log, "w")
@@ -71,11 +81,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         msg = "\n".join(f"--- {u} ---\n{t}" for u, t in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -236,6 +236,7 @@ qc_status qc_eloc_create(const double* h, const double* eri, double e_core, int 
     sp.Jt = H->d_Jt;
     sp.Xt = H->d_Xt;
     sp.Fref = H->d_Fref;
+    sp.err = &H->d_ctr->flags;
     sp.refA = H->na >= 64 ? ~0ULL : (1ULL << H->na) - 1ULL;
     sp.refB = H->nb >= 64 ? ~0ULL : (1ULL << H->nb) - 1ULL;
     sp.Jt32 = H->d_Jt32;
@@ -596,6 +597,7 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     tp.keys = tk;
     tp.psi = tpsi;
     tp.n = nt;
+    tp.err = &H->d_ctr->flags;
     tp.slots = H->d_slots;
     tp.nb_mask = static_cast<unsigned>(table_buckets(nt) - 1);
     tp.filter = (cfg.kernel == 2) ? H->d_filter : nullptr;

@@ -298,10 +298,12 @@ qc_status prepare(qc_batch* B) {
         B->red_blocks = std::max(B->red_blocks, W.nblk);
         qc::MolParams& P = mp[m];
         P.sp = H->sp;
+        P.sp.err = &W.ctr->flags;
         P.tp = qc::TableParams{};
         P.tp.keys = reinterpret_cast<const ulonglong2*>(I.samples);
         P.tp.psi = reinterpret_cast<const double2*>(I.psi);
         P.tp.n = I.n_u;
+        P.tp.err = &W.ctr->flags;
         P.tp.slots = W.slots;
         P.tp.nb_mask = static_cast<unsigned>(L.nb - 1);
         P.tp.filter = W.filter;

@@ -31,6 +31,24 @@ namespace qc {
 
 #define QC_FULLMASK 0xffffffffu
 
+// Bounds checks of the QC_CHECKED build (a library compiled with -DQC_CHECKED): every integral,
+// table and list index goes through QC_IX(i, n, err); out of [0, n) it sets QC_FLAG_BOUNDS in
+// *err and yields 0, so the access stays inside the array and nothing traps.  In the normal
+// build QC_IX(i, n, err) is i.
+#ifdef QC_CHECKED
+__device__ __forceinline__ long long checked_index(long long i, long long n, unsigned* err) {
+    if (i >= 0 && i < n) return i;
+    if (err != nullptr) atomicOr(err, QC_FLAG_BOUNDS);
+    return 0;
+}
+#define QC_IX(i, n, err) (::qc::checked_index(static_cast<long long>(i), static_cast<long long>(n), (err)))
+#else
+#define QC_IX(i, n, err) (i)
+#endif
+#define QC_K2(sp) (static_cast<long long>((sp).K) * (sp).K)
+#define QC_K3(sp) (QC_K2(sp) * (sp).K)
+#define QC_K4(sp) (QC_K2(sp) * QC_K2(sp))
+
 // ------------------------------------------------------------------------------------
 // small device helpers
 // ------------------------------------------------------------------------------------
@@ -169,17 +187,17 @@ __device__ __forceinline__ long long table_find(const TableParams& tp, ulonglong
     unsigned b = home_bucket(g, tp.nb_mask);
     const ulonglong2* buckets = reinterpret_cast<const ulonglong2*>(tp.slots);
     for (unsigned it = 0; it <= tp.nb_mask; ++it) {
-        const ulonglong2 e = __ldg(buckets + b);
+        const ulonglong2 e = __ldg(buckets + QC_IX(b, tp.nb_mask + 1LL, tp.err));
         if (e.x == 0ULL) return -1;
         if (static_cast<unsigned>(e.x >> 32) == g) {
             const long long r = static_cast<long long>(static_cast<unsigned>(e.x)) - 1;
-            const ulonglong2 k = __ldg(tp.keys + r);
+            const ulonglong2 k = __ldg(tp.keys + QC_IX(r, tp.n, tp.err));
             if (k.x == key.x && k.y == key.y) return r;
         }
         if (e.y == 0ULL) return -1;
         if (static_cast<unsigned>(e.y >> 32) == g) {
             const long long r = static_cast<long long>(static_cast<unsigned>(e.y)) - 1;
-            const ulonglong2 k = __ldg(tp.keys + r);
+            const ulonglong2 k = __ldg(tp.keys + QC_IX(r, tp.n, tp.err));
             if (k.x == key.x && k.y == key.y) return r;
         }
         b = (b + 1u) & tp.nb_mask;
@@ -194,7 +212,7 @@ __device__ __forceinline__ long long probe_fp(unsigned g, const TableParams& tp)
     unsigned b = home_bucket(g, tp.nb_mask);
     const ulonglong2* buckets = reinterpret_cast<const ulonglong2*>(tp.slots);
     for (unsigned it = 0; it <= tp.nb_mask; ++it) {
-        const ulonglong2 e = __ldg(buckets + b);
+        const ulonglong2 e = __ldg(buckets + QC_IX(b, tp.nb_mask + 1LL, tp.err));
         if (e.x == 0ULL) return -1;
         if (static_cast<unsigned>(e.x >> 32) == g) return static_cast<long long>(static_cast<unsigned>(e.x)) - 1;
         if (e.y == 0ULL) return -1;
@@ -232,7 +250,7 @@ __device__ __forceinline__ unsigned set_slot(const unsigned long long* __restric
                                              unsigned long long v, unsigned long long h) {
     unsigned b = static_cast<unsigned>(h >> 32) & mask;
     for (unsigned it = 0; it <= mask; ++it) {
-        const unsigned long long e = __ldg(set + b);
+        const unsigned long long e = __ldg(set + (b & mask));
         if (e == v) return b;
         if (e == 0ULL) return kNoSlot;
         b = (b + 1u) & mask;
@@ -257,10 +275,10 @@ __device__ __forceinline__ void build_one(const TableParams& tp, int n_orb, int 
                                           Counters* ctr, long long r, unsigned* jkey = nullptr,
                                           unsigned* jlen = nullptr, unsigned jbase = 0u, unsigned jsent = 0u,
                                           unsigned* jval = nullptr) {
-    const ulonglong2 key = tp.keys[r];
+    const ulonglong2 key = tp.keys[QC_IX(r, tp.n, tp.err)];
     unsigned flags = 0;
     if (r > 0) {
-        const ulonglong2 prev = tp.keys[r - 1];
+        const ulonglong2 prev = tp.keys[QC_IX(r - 1, tp.n, tp.err)];
         const bool eq = prev.x == key.x && prev.y == key.y;
         const bool gt = (prev.y > key.y) || (prev.y == key.y && prev.x > key.x);
         if (eq) flags |= QC_FLAG_DUP;
@@ -448,8 +466,8 @@ __device__ __forceinline__ long long verify_and_add(uint2 e, ulonglong2 x, unsig
                                                     float2 ip32, Acc& acc, Element element) {
     unsigned long long h;
     const ulonglong2 xp = excite(e.x, x, hx, T64, h);
-    const ulonglong2 key = __ldg(tp.keys + e.y);
-    double2 pp = __ldg(tp.psi + e.y);
+    const ulonglong2 key = __ldg(tp.keys + QC_IX(e.y, tp.n, tp.err));
+    double2 pp = __ldg(tp.psi + QC_IX(e.y, tp.n, tp.err));
     double h64 = 0.0;
     float h32 = 0.f;
     bool sneg = false;
@@ -457,7 +475,7 @@ __device__ __forceinline__ long long verify_and_add(uint2 e, ulonglong2 x, unsig
     long long row = e.y;
     if (key.x != xp.x || key.y != xp.y) {
         row = table_find(tp, xp, static_cast<unsigned>(h));
-        if (row >= 0) pp = __ldg(tp.psi + row);
+        if (row >= 0) pp = __ldg(tp.psi + QC_IX(row, tp.n, tp.err));
         else if (mode == QC_FULL) acc.missing++;
     }
     if (row < 0) return 0;
@@ -540,19 +558,20 @@ __device__ __forceinline__ unsigned decode(unsigned code, const SysParams& sp,
     int w = static_cast<int>(code & 4095u);
     // singles lists may be compacted by the spin-string prefilter: map back
     if (IA != nullptr) {
-        if (cls == 4u) { u = IA[u]; w = IB[w]; }
-        else if (cls == 0u) w = IA[w];
-        else if (cls == 1u) w = IB[w];
+        if (cls == 4u) { u = IA[QC_IX(u, sp.nsa, sp.err)]; w = IB[QC_IX(w, sp.nsb, sp.err)]; }
+        else if (cls == 0u) w = IA[QC_IX(w, sp.nsa, sp.err)];
+        else if (cls == 1u) w = IB[QC_IX(w, sp.nsb, sp.err)];
     }
     unsigned i, a, j = 255u, b = 255u;
     if (cls == 4u) {
-        const int io = divA[u], jo = divB[w];
-        i = 2u * occA[io];
-        a = 2u * virA[u - io * sp.va];
-        j = 2u * occB[jo] + 1u;
-        b = 2u * virB[w - jo * sp.vb] + 1u;
+        const int io = divA[QC_IX(u, sp.nsa, sp.err)], jo = divB[QC_IX(w, sp.nsb, sp.err)];
+        i = 2u * occA[QC_IX(io, sp.oa, sp.err)];
+        a = 2u * virA[QC_IX(u - io * sp.va, sp.va, sp.err)];
+        j = 2u * occB[QC_IX(jo, sp.ob, sp.err)] + 1u;
+        b = 2u * virB[QC_IX(w - jo * sp.vb, sp.vb, sp.err)] + 1u;
     } else if (cls >= 2u) {
-        const unsigned po = lut[u], pv = lut[w];
+        const unsigned po = lut[QC_IX(u, cls == 2u ? sp.npoa : sp.npob, sp.err)];
+        const unsigned pv = lut[QC_IX(w, cls == 2u ? sp.npva : sp.npvb, sp.err)];
         const unsigned char* occ = cls == 2u ? occA : occB;
         const unsigned char* vir = cls == 2u ? virA : virB;
         const unsigned s = cls - 2u;
@@ -565,9 +584,9 @@ __device__ __forceinline__ unsigned decode(unsigned code, const SysParams& sp,
         const unsigned char* occ = cls == 0u ? occA : occB;
         const unsigned char* vir = cls == 0u ? virA : virB;
         const int vv = cls == 0u ? sp.va : sp.vb;
-        const int io = dv[w];
-        i = 2u * occ[io] + cls;
-        a = 2u * vir[w - io * vv] + cls;
+        const int io = dv[QC_IX(w, cls == 0u ? sp.nsa : sp.nsb, sp.err)];
+        i = 2u * occ[QC_IX(io, cls == 0u ? sp.oa : sp.ob, sp.err)] + cls;
+        a = 2u * vir[QC_IX(w - io * vv, vv, sp.err)] + cls;
     }
     return i | (a << 8) | (j << 16) | (b << 24);
 }
@@ -591,7 +610,7 @@ __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 px, con
                                                float& h32, bool& sneg) {
     const int i = orbs & 255u, a = (orbs >> 8) & 255u;
     const int K = sp.K, ki = i >> 1, ka = a >> 1, s = i & 1;
-    const size_t rowk = (static_cast<size_t>(ka) * K + ki) * K;
+    const size_t rowk = QC_IX((static_cast<size_t>(ka) * K + ki) * K, QC_K3(sp) - K + 1, sp.err);
     const unsigned char* occA = wl;
     const unsigned char* occB = wl + 128;
     const bool neg = (pbit(px, i) ^ pbit(px, a) ^ (i < a ? 1 : 0)) != 0;
@@ -614,7 +633,8 @@ __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 px, con
         }
         double f;
         if (nd < sp.oa + sp.ob + os) {
-            double f0 = sp.Fref[(static_cast<size_t>(s) * K + ka) * K + ki], f1 = 0.0, f2 = 0.0, f3 = 0.0;
+            double f0 = sp.Fref[QC_IX((static_cast<size_t>(s) * K + ka) * K + ki, 2 * QC_K2(sp), sp.err)], f1 = 0.0,
+                   f2 = 0.0, f3 = 0.0;
             for (unsigned long long m = aP | bP; m; m &= m - 1ULL) {
                 const int k = __ffsll(m) - 1;
                 f1 += ((aP >> k) & (bP >> k) & 1ULL) ? 2.0 * jt[k] : jt[k];
@@ -628,7 +648,7 @@ __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 px, con
             f = (f0 + f3) + (f1 + f2);
         } else {
             // sum over the occupied orbitals of both spins, four independent partial sums
-            double f0 = sp.h[ka * K + ki], f1 = 0.0, f2 = 0.0, f3 = 0.0;
+            double f0 = sp.h[QC_IX(ka * K + ki, QC_K2(sp), sp.err)], f1 = 0.0, f2 = 0.0, f3 = 0.0;
             const unsigned char* occS = s == 0 ? occA : occB;
             int q = 0;
             for (; q + 1 < sp.oa; q += 2) { f0 += jt[occA[q]]; f1 += jt[occA[q + 1]]; }
@@ -642,7 +662,7 @@ __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 px, con
         }
         h64 = with_sign(f, neg);
     } else {
-        float f0 = sp.h32[ka * K + ki], f1 = 0.f, f2 = 0.f, f3 = 0.f;
+        float f0 = sp.h32[QC_IX(ka * K + ki, QC_K2(sp), sp.err)], f1 = 0.f, f2 = 0.f, f3 = 0.f;
         const float* jt = sp.Jt32 + rowk;
         const float* xt = sp.Xt32 + rowk;
         const unsigned char* occS = s == 0 ? occA : occB;
@@ -669,18 +689,18 @@ __device__ __forceinline__ void double_element(unsigned orbs, ulonglong2 px, con
                                                double& h64, float& h32, bool& sneg) {
     const int i = orbs & 255u, a = (orbs >> 8) & 255u, j = (orbs >> 16) & 255u, b = orbs >> 24;
     const int K = sp.K, ki = i >> 1, ka = a >> 1, kj = j >> 1, kb = b >> 1;
-    const size_t d = ((static_cast<size_t>(ka) * K + ki) * K + kb) * K + kj;  // (ai|bj)
+    const size_t d = QC_IX(((static_cast<size_t>(ka) * K + ki) * K + kb) * K + kj, QC_K4(sp), sp.err);  // (ai|bj)
     const int par = (pbit(px, i) ^ pbit(px, j) ^ pbit(px, a) ^ pbit(px, b)) + (i < j) + (i < b) +
                     (j < b) + (i < a) + (j < a) + (b < a);
     const bool neg = (par & 1) != 0;
     const bool same = (i & 1) == (j & 1);
     if (PREC == QC_FP64) {
         double e = sp.eri[d];
-        if (same) e -= sp.eri[((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki];  // (aj|bi)
+        if (same) e -= sp.eri[QC_IX(((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki, QC_K4(sp), sp.err)];  // (aj|bi)
         h64 = with_sign(e, neg);
     } else {
         float e = sp.eri32[d];
-        if (same) e -= sp.eri32[((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki];
+        if (same) e -= sp.eri32[QC_IX(((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki, QC_K4(sp), sp.err)];
         h32 = with_sign(e, neg);
     }
     // exported convention sorts the emptied and the filled pair
@@ -720,10 +740,10 @@ __device__ __forceinline__ bool sample_setup(const SysParams& sp, ulonglong2 x, 
     for (int k = lane; k < sp.K; k += 32) {
         const unsigned long long lowm = (1ULL << k) - 1ULL;
         const int ca = __popcll(A & lowm), cb = __popcll(B & lowm);
-        if ((A >> k) & 1ULL) occA[ca] = static_cast<unsigned char>(k);
-        else virA[k - ca] = static_cast<unsigned char>(k);
-        if ((B >> k) & 1ULL) occB[cb] = static_cast<unsigned char>(k);
-        else virB[k - cb] = static_cast<unsigned char>(k);
+        if ((A >> k) & 1ULL) occA[QC_IX(ca, 64, sp.err)] = static_cast<unsigned char>(k);
+        else virA[QC_IX(k - ca, 64, sp.err)] = static_cast<unsigned char>(k);
+        if ((B >> k) & 1ULL) occB[QC_IX(cb, 64, sp.err)] = static_cast<unsigned char>(k);
+        else virB[QC_IX(k - cb, 64, sp.err)] = static_cast<unsigned char>(k);
     }
     // linear hash of x: XOR of T over set bits (lane l: bits l, l+32, l+64, l+96)
     unsigned long long hv = 0;
@@ -745,7 +765,7 @@ __device__ __forceinline__ bool sample_setup(const SysParams& sp, ulonglong2 x, 
     double e0 = 0.0, e1 = 0.0;
     for (int p = lane; p < no; p += 32) {
         const int k = p < sp.oa ? occA[p] : occB[p - sp.oa];
-        e1 += sp.h[k * K + k];
+        e1 += sp.h[QC_IX(k * K + k, QC_K2(sp), sp.err)];
     }
     if (no > 0) {
         const int q32 = 32 / no, r32 = 32 - q32 * no;
@@ -754,7 +774,7 @@ __device__ __forceinline__ bool sample_setup(const SysParams& sp, ulonglong2 x, 
             const bool pa = p < sp.oa, ra = r < sp.oa;
             const int k = pa ? occA[p] : occB[p - sp.oa];
             const int l = ra ? occA[r] : occB[r - sp.oa];
-            e0 += (pa == ra ? sp.X : sp.J)[k * K + l];
+            e0 += (pa == ra ? sp.X : sp.J)[QC_IX(k * K + l, QC_K2(sp), sp.err)];
             r += r32;
             p += q32;
             if (r >= no) {
@@ -796,7 +816,7 @@ __device__ __forceinline__ void write_sample(const EvalParams& ep, long long s, 
         e.x = ediag + sre;
         e.y = sim;
     }
-    ep.eloc[s] = e;
+    ep.eloc[QC_IX(s, ep.n_u, &ep.ctr->flags)] = e;
     if (ep.hit_count) ep.hit_count[s] = static_cast<uint32_t>(hits);
     if (ep.hit_rowsum) ep.hit_rowsum[s] = rows;
     if (ep.hit_signsum) ep.hit_signsum[s] = sgn;
@@ -967,6 +987,8 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         FILTER ? reinterpret_cast<unsigned short*>(H + list_words(sp, lean, SEG && join_lists ? tp.alpha_cap : 0))
                : nullptr;
     unsigned short* IB = FILTER ? IA + nA : nullptr;
+    const int nH = FILTER ? static_cast<int>(list_words(sp, lean, SEG && join_lists ? tp.alpha_cap : 0)) : 0;
+    (void)nH;  // the list's length, for the checked build's bounds checks
     int nsa2 = sp.nsa, nsb2 = sp.nsb;  // single-list lengths after the spin-string prefilter
     const uint32_t wmask4 = FILTER ? ((1u << tp.fw) - 1u) << 2 : 0u;
     const unsigned ltmask = lanemask_lt();
@@ -974,7 +996,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     const unsigned char* divB = divA + 1024;
 
 
-    const ulonglong2 x = ep.samples[s];
+    const ulonglong2 x = ep.samples[QC_IX(s, ep.n_u, sp.err)];
     unsigned long long hx, As, Bs, hxa;
     double ediag;
     if (!sample_setup(sp, x, lane, wl, T64, hx, ediag, As, Bs, hxa)) {
@@ -995,7 +1017,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         WarpSample w;
         w.x = x;
         w.px = prefix_parity(x);
-        w.psix = ep.psi[s];
+        w.psix = ep.psi[QC_IX(s, ep.n_u, sp.err)];
         w.hx = hx;
         w.ediag = ediag;
         w.ip32 = inv_psi32(w.psix);
@@ -1108,8 +1130,8 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
             const unsigned m = __ballot_sync(QC_FULLMASK, keep);
             if (keep) {
                 const int pos = nsb2 + __popc(m & ltmask);
-                H[oSB + pos] = hv32;
-                IB[pos] = static_cast<unsigned short>(t);
+                H[QC_IX(oSB + pos, nH, sp.err)] = hv32;
+                IB[QC_IX(pos, sp.nsb, sp.err)] = static_cast<unsigned short>(t);
             }
             nsb2 += __popc(m);
         }
@@ -1122,12 +1144,12 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 const unsigned off = lane == 0 ? 0u : tp.set_mask + 1u;
                 const unsigned sl = lane == 0 ? set_slot(tp.aset, tp.set_mask, As, hxa)
                                               : set_slot(tp.bset, tp.set_mask, Bs, hxb);
-                const unsigned len = sl != kNoSlot ? __ldg(tp.jlen + off + sl) : 0u;
+                const unsigned len = sl != kNoSlot ? __ldg(tp.jlen + QC_IX(off + sl, 2LL * (tp.set_mask + 1LL), tp.err)) : 0u;
                 const long long pairs = lane == 0 ? static_cast<long long>(nsb2) + static_cast<long long>(sp.npob) * sp.npvb
                                                   : static_cast<long long>(sp.npoa) * sp.npva;
                 if (len > 0u) {
                     if (static_cast<long long>(len) * tp.scan_cost <= 4 * pairs) {
-                        gst = __ldg(tp.jstart + off + sl);
+                        gst = __ldg(tp.jstart + QC_IX(off + sl, 2LL * (tp.set_mask + 1LL), tp.err));
                         gln = len;
                     } else {
                         en = true;
@@ -1157,8 +1179,8 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 const unsigned m = __ballot_sync(QC_FULLMASK, keep);
                 if (keep) {
                     const int pos = nsa2 + __popc(m & ltmask);
-                    H[oSA + pos] = hv32;
-                    IA[pos] = static_cast<unsigned short>(t);
+                    H[QC_IX(oSA + pos, nH, sp.err)] = hv32;
+                    IA[QC_IX(pos, nA, sp.err)] = static_cast<unsigned short>(t);
                 }
                 nsa2 += __popc(m);
             }
@@ -1221,7 +1243,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 unsigned code = 0u, row = 0u;
                 if (v < stotal) {
                     const unsigned kd = q[64 + g];
-                    const ulonglong2 e = __ldg(tp.gent + q[g] + (v - q[32 + g]));
+                    const ulonglong2 e = __ldg(tp.gent + QC_IX(q[g] + (v - q[32 + g]), 2 * tp.n, tp.err));
                     const unsigned kk = kd & 3u;
                     const unsigned long long ref = kk == kScanBeta ? wsp->as : wsp->bs;
                     const unsigned long long dm = e.x ^ ref;
@@ -1234,8 +1256,8 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     }
                 }
                 const unsigned md = __ballot_sync(QC_FULLMASK, dbl), ms = __ballot_sync(QC_FULLMASK, sgl);
-                if (dbl) hq[nh + __popc(md & ltmask)] = make_uint2(code, row);
-                if (sgl) hs[ns + __popc(ms & ltmask)] = make_uint2(code, row);
+                if (dbl) hq[QC_IX(nh + __popc(md & ltmask), 64, sp.err)] = make_uint2(code, row);
+                if (sgl) hs[QC_IX(ns + __popc(ms & ltmask), kSingleCap, sp.err)] = make_uint2(code, row);
                 nh += __popc(md);
                 ns += __popc(ms);
                 sbase += 32u;
@@ -1260,8 +1282,8 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     hv32 = static_cast<uint32_t>(tm);
                     const unsigned sl = set_slot(tp.aset, tp.set_mask, wsp->as ^ (1ULL << ki) ^ (1ULL << ka), wsp->hxa ^ tm);
                     if (sl != kNoSlot) {
-                        len = __ldg(tp.jlen + sl);
-                        start = __ldg(tp.jstart + sl);
+                        len = __ldg(tp.jlen + QC_IX(sl, tp.set_mask + 1LL, tp.err));
+                        start = __ldg(tp.jstart + QC_IX(sl, tp.set_mask + 1LL, tp.err));
                     }
                     lng = static_cast<long long>(len) * tp.scan_cost > 4LL * (nsb2 + 1);
                     kd = kScanAlphaP | (static_cast<unsigned>(ki) << 8) | (static_cast<unsigned>(ka) << 16);
@@ -1273,8 +1295,8 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 const int pos = nsa2 + __popc(m & ltmask);
                 const bool keep = SEG ? (lng && pos < nA) : lng;
                 if (keep) {
-                    H[oSA + pos] = hv32;
-                    IA[pos] = static_cast<unsigned short>(t);
+                    H[QC_IX(oSA + pos, nH, sp.err)] = hv32;
+                    IA[QC_IX(pos, nA, sp.err)] = static_cast<unsigned short>(t);
                 } else if (!lng && (!SEG || t >= a_seen)) {
                     gst = start;
                     gln = len;
@@ -1329,9 +1351,9 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                             if (v) {
                                 if (pairs) {
                                     const unsigned pp = lut[u0 + k];
-                                    e = H[oo + (pp & 255u)] ^ H[oo + (pp >> 8)];
+                                    e = H[QC_IX(oo + (pp & 255u), nH, sp.err)] ^ H[QC_IX(oo + (pp >> 8), nH, sp.err)];
                                 } else {
-                                    e = H[oo + u0 + k];
+                                    e = H[QC_IX(oo + u0 + k, nH, sp.err)];
                                 }
                             }
                             hu[k] = hx32 ^ e;
@@ -1354,9 +1376,9 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     if (FILTER && wv) {
                         if (LEAN != 0 && pairs) {
                             const unsigned pp = lut[w];
-                            hw = H[io + (pp & 255u)] ^ H[io + (pp >> 8)];
+                            hw = H[QC_IX(io + (pp & 255u), nH, sp.err)] ^ H[QC_IX(io + (pp >> 8), nH, sp.err)];
                         } else {
-                            hw = H[io + w];
+                            hw = H[QC_IX(io + w, nH, sp.err)];
                         }
                     }
                     const unsigned ccode = cbase | static_cast<unsigned>(w);
@@ -1368,7 +1390,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                             // of g >> 3 masked to whole words) and its three bits
                             const uint32_t g = hu[k] ^ hw;
                             const uint32_t word = *reinterpret_cast<const uint32_t*>(
-                                reinterpret_cast<const unsigned char*>(filt) + ((g >> 3) & wmask4));
+                                reinterpret_cast<const unsigned char*>(filt) + QC_IX((g >> 3) & wmask4, 4LL << tp.fw, sp.err));
                             const uint32_t t = __funnelshift_r(word, word, g) &
                                                __funnelshift_r(word, word, g >> 27) &
                                                __funnelshift_r(word, word, g >> 22);
@@ -1377,7 +1399,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                             pass = ((vm >> k) & 1u) != 0u;
                         }
                         const unsigned m = __ballot_sync(QC_FULLMASK, pass);
-                        if (pass) q[qn + __popc(m & ltmask)] = ccode + (static_cast<unsigned>(k) << 12);
+                        if (pass) q[QC_IX(qn + __popc(m & ltmask), kCandCap, sp.err)] = ccode + (static_cast<unsigned>(k) << 12);
                         qn += __popc(m);
                     }
                     w0 += 32;
@@ -1421,11 +1443,11 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                         uint32_t ho, hi;
                         if (LEAN != 0 && lean && (cc == 2u || cc == 3u)) {
                             const unsigned pu = lut[u], pw = lut[w];
-                            ho = H[ob + (pu & 255u)] ^ H[ob + (pu >> 8)];
-                            hi = H[ib + (pw & 255u)] ^ H[ib + (pw >> 8)];
+                            ho = H[QC_IX(ob + (pu & 255u), nH, sp.err)] ^ H[QC_IX(ob + (pu >> 8), nH, sp.err)];
+                            hi = H[QC_IX(ib + (pw & 255u), nH, sp.err)] ^ H[QC_IX(ib + (pw >> 8), nH, sp.err)];
                         } else {
-                            ho = H[ob + u];
-                            hi = H[ib + w];
+                            ho = H[QC_IX(ob + u, nH, sp.err)];
+                            hi = H[QC_IX(ib + w, nH, sp.err)];
                         }
                         g = hx32 ^ ho ^ hi;
                         item = code;
@@ -1440,7 +1462,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 }
                 const bool hit = row >= 0;
                 const unsigned mh = __ballot_sync(QC_FULLMASK, hit);
-                if (hit) hq[nh + __popc(mh & ltmask)] = make_uint2(item, static_cast<unsigned>(row));
+                if (hit) hq[QC_IX(nh + __popc(mh & ltmask), 64, sp.err)] = make_uint2(item, static_cast<unsigned>(row));
                 nh += __popc(mh);
                 __syncwarp();
             } else {
@@ -1584,6 +1606,7 @@ __device__ __forceinline__ void reduce_pass2_body(const EvalParams& ep, double* 
         else if (f & QC_FLAG_NELEC) st = QC_ERR_NELEC;
         else if (f & QC_FLAG_NEG_COUNT) st = QC_ERR_COUNTS;
         else if (f & (QC_FLAG_TABLE_FULL | QC_FLAG_LIST_FULL)) st = QC_ERR_CAPACITY;
+        else if (f & QC_FLAG_BOUNDS) st = QC_ERR_BOUNDS;
         else if (f & QC_FLAG_TIMEOUT) st = QC_ERR_TIMEOUT;
         else if (f & QC_FLAG_MISSING) st = QC_ERR_MISSING;
         else if (f & QC_FLAG_ZERO_PSI) st = QC_ERR_ZERO_PSI;

@@ -43,6 +43,7 @@ struct SysParams {
     // for the Aufbau strings refA, refB (spatial orbitals 0 .. na - 1, 0 .. nb - 1)
     const double* Fref;  // 2*K*K
     unsigned long long refA, refB;
+    unsigned* err;       // QC_CHECKED builds: flags word a failed bounds check sets (QC_FLAG_BOUNDS)
 };
 
 // The lookup table: sorted unique keys, their psi, and the device hash index over them.
@@ -69,6 +70,7 @@ struct TableParams {
     const ulonglong2* gent;
     int scan_cost;  // a group is scanned when len * scan_cost <= 4 * (pairs it replaces)
     int alpha_cap;  // join: slots of the per-warp alpha single list (0: all alpha singles)
+    unsigned* err;  // QC_CHECKED builds: flags word a failed bounds check sets (QC_FLAG_BOUNDS)
 };
 
 // Counters and flags of one evaluation (device memory, zeroed at the start of a call).

@@ -155,6 +155,7 @@ extern "C" qc_status qc_eloc_eval_static(const double* h, const double* eri, dou
     sp.Xt = reinterpret_cast<double*>(S + kOffXt);
     unsigned long long* T = reinterpret_cast<unsigned long long*>(S + kOffTab);
     Counters* ctr = reinterpret_cast<Counters*>(S + kOffCtr);
+    sp.err = &ctr->flags;
     double* part = reinterpret_cast<double*>(S + kOffPart);
     uint32_t* filter = reinterpret_cast<uint32_t*>(S + kOffFilter);
     unsigned long long* slots = reinterpret_cast<unsigned long long*>(S + kOffSlots);
@@ -197,6 +198,7 @@ extern "C" qc_status qc_eloc_eval_static(const double* h, const double* eri, dou
     tp.keys = reinterpret_cast<const ulonglong2*>(samples);
     tp.psi = reinterpret_cast<const double2*>(psi);
     tp.n = n_u;
+    tp.err = &ctr->flags;
     tp.slots = slots;
     tp.nb_mask = static_cast<unsigned>(next_pow2_u(2ULL * static_cast<unsigned long long>(nt)) - 1);
     tp.filter = cfg.kernel == 2 ? filter : nullptr;
