@@ -415,22 +415,33 @@ struct Acc {
     unsigned long long missing;
 };
 
-// x' = x with spin orbitals (i, j) emptied and (a, b) filled (j = b = 255: a single), and
-// its linear hash h, updated from that of x by the four orbitals' entries of T.
-__device__ __forceinline__ ulonglong2 excite(unsigned orbs, ulonglong2 x, unsigned long long hx,
-                                             const unsigned long long* __restrict__ T64,
-                                             unsigned long long& h) {
+// x' = x with spin orbitals (i, j) emptied and (a, b) filled (j = b = 255: a single).
+__device__ __forceinline__ ulonglong2 excited_key(unsigned orbs, ulonglong2 x) {
     const int i = orbs & 255u, a = (orbs >> 8) & 255u, j = (orbs >> 16) & 255u, b = orbs >> 24;
     ulonglong2 xp = x;
     flip(xp, i);
     flip(xp, a);
-    h = hx ^ T64[i] ^ T64[a];
     if (j != 255) {
         flip(xp, j);
         flip(xp, b);
-        h ^= T64[j] ^ T64[b];
     }
     return xp;
+}
+
+// The linear hash of that x', updated from that of x by the four orbitals' entries of T.
+__device__ __forceinline__ unsigned long long excited_hash(unsigned orbs, unsigned long long hx,
+                                                           const unsigned long long* __restrict__ T64) {
+    const int i = orbs & 255u, a = (orbs >> 8) & 255u, j = (orbs >> 16) & 255u, b = orbs >> 24;
+    unsigned long long h = hx ^ T64[i] ^ T64[a];
+    if (j != 255) h ^= T64[j] ^ T64[b];
+    return h;
+}
+
+__device__ __forceinline__ ulonglong2 excite(unsigned orbs, ulonglong2 x, unsigned long long hx,
+                                             const unsigned long long* __restrict__ T64,
+                                             unsigned long long& h) {
+    h = excited_hash(orbs, hx, T64);
+    return excited_key(orbs, x);
 }
 
 // Add one hit: <x|H|x'> (phase included) times psi(x') [FP64], or times psi(x')/psi(x)
@@ -457,16 +468,17 @@ __device__ __forceinline__ void add_hit(double h64, float h32, long long row, bo
 
 // Stage 2 common part: issue the loads of the stored key and psi of a stage-1 row, let
 // `element` load the integrals meanwhile, then confirm the key (exact walk on a
-// fingerprint collision) and add the hit.  Returns phase * (row + 1) of the hit added, or
-// 0 when the key is not in the table.
+// fingerprint collision) and add the hit.  A row found by the join's scan is exact (its
+// group fixes one spin string and the scan compared the other), so its key is not loaded.
+// Returns phase * (row + 1) of the hit added, or 0 when the key is not in the table.
 template <int PREC, bool DIAG, typename Element>
-__device__ __forceinline__ long long verify_and_add(uint2 e, ulonglong2 x, unsigned long long hx,
+__device__ __forceinline__ long long verify_and_add(uint2 e, bool exact, ulonglong2 x, unsigned long long hx,
                                                     const TableParams& tp, int mode,
                                                     const unsigned long long* __restrict__ T64,
                                                     float2 ip32, Acc& acc, Element element) {
-    unsigned long long h;
-    const ulonglong2 xp = excite(e.x, x, hx, T64, h);
-    const ulonglong2 key = __ldg(tp.keys + QC_IX(e.y, tp.n, tp.err));
+    const ulonglong2 xp = excited_key(e.x, x);
+    ulonglong2 key = xp;
+    if (!exact) key = __ldg(tp.keys + QC_IX(e.y, tp.n, tp.err));
     double2 pp = __ldg(tp.psi + QC_IX(e.y, tp.n, tp.err));
     double h64 = 0.0;
     float h32 = 0.f;
@@ -474,7 +486,7 @@ __device__ __forceinline__ long long verify_and_add(uint2 e, ulonglong2 x, unsig
     element(h64, h32, sneg);
     long long row = e.y;
     if (key.x != xp.x || key.y != xp.y) {
-        row = table_find(tp, xp, static_cast<unsigned>(h));
+        row = table_find(tp, xp, static_cast<unsigned>(excited_hash(e.x, hx, T64)));
         if (row >= 0) pp = __ldg(tp.psi + QC_IX(row, tp.n, tp.err));
         else if (mode == QC_FULL) acc.missing++;
     }
@@ -610,7 +622,8 @@ __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 px, con
                                                float& h32, bool& sneg) {
     const int i = orbs & 255u, a = (orbs >> 8) & 255u;
     const int K = sp.K, ki = i >> 1, ka = a >> 1, s = i & 1;
-    const size_t rowk = QC_IX((static_cast<size_t>(ka) * K + ki) * K, QC_K3(sp) - K + 1, sp.err);
+    // K <= 64: every integral index fits 32 bits (K^4 <= 2^24)
+    const unsigned rowk = QC_IX((static_cast<unsigned>(ka) * K + ki) * K, QC_K3(sp) - K + 1, sp.err);
     const unsigned char* occA = wl;
     const unsigned char* occB = wl + 128;
     const bool neg = (pbit(px, i) ^ pbit(px, a) ^ (i < a ? 1 : 0)) != 0;
@@ -633,7 +646,7 @@ __device__ __forceinline__ void single_element(unsigned orbs, ulonglong2 px, con
         }
         double f;
         if (nd < sp.oa + sp.ob + os) {
-            double f0 = sp.Fref[QC_IX((static_cast<size_t>(s) * K + ka) * K + ki, 2 * QC_K2(sp), sp.err)], f1 = 0.0,
+            double f0 = sp.Fref[QC_IX((static_cast<unsigned>(s) * K + ka) * K + ki, 2 * QC_K2(sp), sp.err)], f1 = 0.0,
                    f2 = 0.0, f3 = 0.0;
             for (unsigned long long m = aP | bP; m; m &= m - 1ULL) {
                 const int k = __ffsll(m) - 1;
@@ -689,18 +702,19 @@ __device__ __forceinline__ void double_element(unsigned orbs, ulonglong2 px, con
                                                double& h64, float& h32, bool& sneg) {
     const int i = orbs & 255u, a = (orbs >> 8) & 255u, j = (orbs >> 16) & 255u, b = orbs >> 24;
     const int K = sp.K, ki = i >> 1, ka = a >> 1, kj = j >> 1, kb = b >> 1;
-    const size_t d = QC_IX(((static_cast<size_t>(ka) * K + ki) * K + kb) * K + kj, QC_K4(sp), sp.err);  // (ai|bj)
+    // K <= 64: the index fits 32 bits (K^4 <= 2^24)
+    const unsigned d = QC_IX(((static_cast<unsigned>(ka) * K + ki) * K + kb) * K + kj, QC_K4(sp), sp.err);  // (ai|bj)
     const int par = (pbit(px, i) ^ pbit(px, j) ^ pbit(px, a) ^ pbit(px, b)) + (i < j) + (i < b) +
                     (j < b) + (i < a) + (j < a) + (b < a);
     const bool neg = (par & 1) != 0;
     const bool same = (i & 1) == (j & 1);
     if (PREC == QC_FP64) {
         double e = sp.eri[d];
-        if (same) e -= sp.eri[QC_IX(((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki, QC_K4(sp), sp.err)];  // (aj|bi)
+        if (same) e -= sp.eri[QC_IX(((static_cast<unsigned>(ka) * K + kj) * K + kb) * K + ki, QC_K4(sp), sp.err)];  // (aj|bi)
         h64 = with_sign(e, neg);
     } else {
         float e = sp.eri32[d];
-        if (same) e -= sp.eri32[QC_IX(((static_cast<size_t>(ka) * K + kj) * K + kb) * K + ki, QC_K4(sp), sp.err)];
+        if (same) e -= sp.eri32[QC_IX(((static_cast<unsigned>(ka) * K + kj) * K + kb) * K + ki, QC_K4(sp), sp.err)];
         h32 = with_sign(e, neg);
     }
     // exported convention sorts the emptied and the filled pair
@@ -1051,11 +1065,12 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         if (lane < nq - n) Q[lane] = Q[n + lane];
         nq -= n;
         __syncwarp();
+        const bool exact = JOIN && FILTER && (e.x >> 24) >= kCodeSingleA;  // found by the join's scan
         if (FILTER && v) e.x = decode(e.x, sp, wl, smem, IA, IB);
         long long ent = 0;
         if (v) {
             const ulonglong2 xs = wsp->x, px = wsp->px;
-            ent = verify_and_add<PREC, DIAG>(e, xs, wsp->hx, tp, ep.mode, T64,
+            ent = verify_and_add<PREC, DIAG>(e, exact, xs, wsp->hx, tp, ep.mode, T64,
                                              PREC == QC_FP64 ? make_float2(0.f, 0.f) : wsp->ip32, acc,
                                              [&](double& h64, float& h32, bool& sneg) {
                 if ((e.x >> 16) == 0xFFFFu)
