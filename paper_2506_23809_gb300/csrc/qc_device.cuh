@@ -1034,7 +1034,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         w.psix = ep.psi[QC_IX(s, ep.n_u, sp.err)];
         w.hx = hx;
         w.ediag = ediag;
-        w.ip32 = inv_psi32(w.psix);
+        w.ip32 = PREC == QC_FP64 ? make_float2(0.f, 0.f) : inv_psi32(w.psix);
         w.as = As;
         w.bs = Bs;
         w.hxa = hxa;
@@ -1243,40 +1243,43 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
             const unsigned stotal = q[102];
             const int st0 = static_cast<int>(q[103]);
             if (sbase < stotal) {
-                // 32 rows of the chunk: each lane finds its row's group by a binary search over
-                // the offsets.  A row connects to x when the popcount of its string of the
-                // other spin against x's is 2 or 4 (x's alpha group: a beta single or beta-beta
-                // double), 4 (x's beta group: an alpha-alpha double) or 0 or 2 (an alpha'
-                // group: the alpha single or an alpha-beta double).  Singles and doubles go to
-                // separate queues, so that hit batches do not mix the two element paths.
-                const unsigned v = sbase + lane;
-                int g = 0;
+                // steps of 32 rows of the chunk, while both hit queues have room for another
+                // step: each lane finds its row's group by a binary search over the offsets.  A
+                // row connects to x when the popcount of its string of the other spin against
+                // x's is 2 or 4 (x's alpha group: a beta single or beta-beta double), 4 (x's beta
+                // group: an alpha-alpha double) or 0 or 2 (an alpha' group: the alpha single or
+                // an alpha-beta double).  Singles and doubles go to separate queues, so that hit
+                // batches do not mix the two element paths.
+                do {
+                    const unsigned v = sbase + lane;
+                    int g = 0;
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (q[32 + g + step] <= v) g += step;
-                bool dbl = false, sgl = false;
-                unsigned code = 0u, row = 0u;
-                if (v < stotal) {
-                    const unsigned kd = q[64 + g];
-                    const ulonglong2 e = __ldg(tp.gent + QC_IX(q[g] + (v - q[32 + g]), 2 * tp.n, tp.err));
-                    const unsigned kk = kd & 3u;
-                    const unsigned long long ref = kk == kScanBeta ? wsp->as : wsp->bs;
-                    const unsigned long long dm = e.x ^ ref;
-                    const int d = __popcll(dm);
-                    sgl = kk == kScanAlpha ? d == 2 : (kk == kScanAlphaP && d == 0);
-                    dbl = kk == kScanAlphaP ? d == 2 : d == 4;
-                    if (sgl || dbl) {
-                        code = scan_code(kd, d, dm & ref, dm & e.x);
-                        row = static_cast<unsigned>(e.y);
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (q[32 + g + step] <= v) g += step;
+                    bool dbl = false, sgl = false;
+                    unsigned code = 0u, row = 0u;
+                    if (v < stotal) {
+                        const unsigned kd = q[64 + g];
+                        const ulonglong2 e = __ldg(tp.gent + QC_IX(q[g] + (v - q[32 + g]), 2 * tp.n, tp.err));
+                        const unsigned kk = kd & 3u;
+                        const unsigned long long ref = kk == kScanBeta ? wsp->as : wsp->bs;
+                        const unsigned long long dm = e.x ^ ref;
+                        const int d = __popcll(dm);
+                        sgl = kk == kScanAlpha ? d == 2 : (kk == kScanAlphaP && d == 0);
+                        dbl = kk == kScanAlphaP ? d == 2 : d == 4;
+                        if (sgl || dbl) {
+                            code = scan_code(kd, d, dm & ref, dm & e.x);
+                            row = static_cast<unsigned>(e.y);
+                        }
                     }
-                }
-                const unsigned md = __ballot_sync(QC_FULLMASK, dbl), ms = __ballot_sync(QC_FULLMASK, sgl);
-                if (dbl) hq[QC_IX(nh + __popc(md & ltmask), 64, sp.err)] = make_uint2(code, row);
-                if (sgl) hs[QC_IX(ns + __popc(ms & ltmask), kSingleCap, sp.err)] = make_uint2(code, row);
-                nh += __popc(md);
-                ns += __popc(ms);
-                sbase += 32u;
-                __syncwarp();
+                    const unsigned md = __ballot_sync(QC_FULLMASK, dbl), ms = __ballot_sync(QC_FULLMASK, sgl);
+                    if (dbl) hq[QC_IX(nh + __popc(md & ltmask), 64, sp.err)] = make_uint2(code, row);
+                    if (sgl) hs[QC_IX(ns + __popc(ms & ltmask), kSingleCap, sp.err)] = make_uint2(code, row);
+                    nh += __popc(md);
+                    ns += __popc(ms);
+                    sbase += 32u;
+                    __syncwarp();
+                } while (sbase < stotal && nh < 32 && ns < 32);
             } else if (st0 < sp.nsa) {
                 // the next 32 alpha' = single excitations of x's alpha string: a long group
                 // joins the lists of classes 0 and 4, a short one becomes a scan descriptor
