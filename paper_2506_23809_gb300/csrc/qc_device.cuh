@@ -466,20 +466,19 @@ __device__ __forceinline__ void add_hit(double h64, float h32, long long row, bo
     }
 }
 
-// Stage 2 common part: issue the loads of the stored key and psi of a stage-1 row, let
-// `element` load the integrals meanwhile, then confirm the key (exact walk on a
-// fingerprint collision) and add the hit.  A row found by the join's scan is exact (its
-// group fixes one spin string and the scan compared the other), so its key is not loaded.
-// Returns phase * (row + 1) of the hit added, or 0 when the key is not in the table.
+// Stage 2 common part: with the stored key and psi of a stage-1 row already on their way
+// (the caller issues those loads before decoding the excitation), let `element` load the
+// integrals, then confirm the key (exact walk on a fingerprint collision) and add the hit.
+// A row found by the join's scan is exact (its group fixes one spin string and the scan
+// compared the other), so its key is not loaded.  Returns phase * (row + 1) of the hit
+// added, or 0 when the key is not in the table.
 template <int PREC, bool DIAG, typename Element>
-__device__ __forceinline__ long long verify_and_add(uint2 e, bool exact, ulonglong2 x, unsigned long long hx,
-                                                    const TableParams& tp, int mode,
+__device__ __forceinline__ long long verify_and_add(uint2 e, bool exact, ulonglong2 key, double2 pp, ulonglong2 x,
+                                                    unsigned long long hx, const TableParams& tp, int mode,
                                                     const unsigned long long* __restrict__ T64,
                                                     float2 ip32, Acc& acc, Element element) {
     const ulonglong2 xp = excited_key(e.x, x);
-    ulonglong2 key = xp;
-    if (!exact) key = __ldg(tp.keys + QC_IX(e.y, tp.n, tp.err));
-    double2 pp = __ldg(tp.psi + QC_IX(e.y, tp.n, tp.err));
+    if (exact) key = xp;
     double h64 = 0.0;
     float h32 = 0.f;
     bool sneg = false;
@@ -524,15 +523,18 @@ constexpr unsigned kCodeSingleA = 5u, kCodeSingleB = 6u, kCodeDoubleAA = 7u, kCo
 // filled its bits set only in x's string and only in the row's.
 __device__ __forceinline__ unsigned scan_code(unsigned kind, int d, unsigned long long emptied,
                                               unsigned long long filled) {
-    const unsigned e0 = static_cast<unsigned>(__ffsll(emptied) - 1) & 63u;
-    const unsigned f0 = static_cast<unsigned>(__ffsll(filled) - 1) & 63u;
+    // the highest bits; at d == 2 the strings differ in one orbital each way, so these are
+    // the only ones
+    const unsigned e1 = static_cast<unsigned>(63 - __clzll(emptied)) & 63u;
+    const unsigned f1 = static_cast<unsigned>(63 - __clzll(filled)) & 63u;
     if ((kind & 3u) == kScanAlphaP) {
         const unsigned ki = (kind >> 8) & 63u, ka = (kind >> 16) & 63u;
         if (d == 0) return (kCodeSingleA << 24) | ki | (ka << 6);
-        return (kCodeDoubleAB << 24) | ki | (ka << 6) | (e0 << 12) | (f0 << 18);
+        return (kCodeDoubleAB << 24) | ki | (ka << 6) | (e1 << 12) | (f1 << 18);
     }
-    if (d == 2) return (kCodeSingleB << 24) | e0 | (f0 << 6);  // x's alpha group only
-    const unsigned e1 = static_cast<unsigned>(63 - __clzll(emptied)), f1 = static_cast<unsigned>(63 - __clzll(filled));
+    if (d == 2) return (kCodeSingleB << 24) | e1 | (f1 << 6);  // x's alpha group only
+    const unsigned e0 = static_cast<unsigned>(__ffsll(emptied) - 1) & 63u;
+    const unsigned f0 = static_cast<unsigned>(__ffsll(filled) - 1) & 63u;
     const unsigned cls = (kind & 3u) == kScanAlpha ? kCodeDoubleBB : kCodeDoubleAA;
     return (cls << 24) | e0 | (e1 << 6) | (f0 << 12) | (f1 << 18);
 }
@@ -1066,11 +1068,18 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         nq -= n;
         __syncwarp();
         const bool exact = JOIN && FILTER && (e.x >> 24) >= kCodeSingleA;  // found by the join's scan
+        // the row's psi and (unless exact) stored key load while the excitation is decoded
+        ulonglong2 key = make_ulonglong2(0ULL, 0ULL);
+        double2 pp = make_double2(0.0, 0.0);
+        if (v) {
+            if (!exact) key = __ldg(tp.keys + QC_IX(e.y, tp.n, tp.err));
+            pp = __ldg(tp.psi + QC_IX(e.y, tp.n, tp.err));
+        }
         if (FILTER && v) e.x = decode(e.x, sp, wl, smem, IA, IB);
         long long ent = 0;
         if (v) {
             const ulonglong2 xs = wsp->x, px = wsp->px;
-            ent = verify_and_add<PREC, DIAG>(e, exact, xs, wsp->hx, tp, ep.mode, T64,
+            ent = verify_and_add<PREC, DIAG>(e, exact, key, pp, xs, wsp->hx, tp, ep.mode, T64,
                                              PREC == QC_FP64 ? make_float2(0.f, 0.f) : wsp->ip32, acc,
                                              [&](double& h64, float& h32, bool& sneg) {
                 if ((e.x >> 16) == 0xFFFFu)
