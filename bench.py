@@ -40,7 +40,8 @@ UNIT = "connected matrix elements/s"
 #     word offset (1), shift the word to its three bit positions (3), combine (1), test (1);
 #     the word itself is read through the load/store pipe and is not counted;
 #   L2 bytes = 16 per scanned table row (the join's entry) + 16 per bucket probe
-#     + per hit 16 (stored key) + 16 (psi(x')) + its integrals, e bytes each (8 FP64, 4 FP32):
+#     + per hit 16 (psi(x')) + 16 (the stored key, which a hit found by the join's scan does not
+#     load: its entry already matched) + its integrals, e bytes each (8 FP64, 4 FP32):
 #       single 1 + 3 n_elec / 2 (h_ai, (ai|kk) over the occupied k, (ak|ki) over the same spin),
 #       same-spin double 2, opposite-spin double 1
 #     + per sample 16 (x) + 16 (psi(x)) + 16 (E_loc written) + 8 per spin-string set lookup
@@ -217,7 +218,8 @@ def work_l2_bytes(w, n_elec, n_orb, elem_bytes, filter_log2w):
     return (16 * w["scan_rows"] + 16 * w["probes"]
             + (32 + elem_bytes * (1 + 3 * n_elec // 2)) * w["hits_single"]
             + (32 + 2 * elem_bytes) * w["hits_same"] + (32 + elem_bytes) * w["hits_ab"]
-            + (48 + 8 * 2 * o * v) * w["samples"] + (4 << filter_log2w) * w["ctas"])
+            + (48 + 8 * 2 * o * v) * w["samples"] + (4 << filter_log2w) * w["ctas"]
+            - 16 * w.get("hits_scanned", 0))
 
 
 def _cpu_baseline(ints, s, spec, target_s, pairs_per_sample, gpu_eloc=None):

@@ -435,11 +435,13 @@ qc_status qc_probe_peaks(double* alu_ops_per_s, double* l2_gather_gbs, void* str
 
 /* Work counts of the last evaluation with QC_OPT_COUNT_WORK = 1 (the units of the local-energy
  * kernel's roofline; no counterpart in the paper).  Waits for that evaluation's stream.
- * work8 = {samples set up, join table rows scanned (16-byte entries), excitations tested
- * against the shared-memory Bloom filter, candidates probed in the bucket table (16-byte
- * buckets), hits that are single excitations, same-spin doubles, opposite-spin doubles,
- * CTAs that copied the filter}. */
-qc_status qc_eloc_work(qc_eloc* handle, uint64_t* work8);
+ * Writes the first min(n_fields, QC_WORK_FIELDS) of {samples set up, join table rows scanned
+ * (16-byte entries), excitations tested against the shared-memory Bloom filter, candidates
+ * probed in the bucket table (16-byte buckets), hits that are single excitations, same-spin
+ * doubles, opposite-spin doubles, CTAs that copied the filter, hits found by the join's scans
+ * (of all kinds; their keys are not loaded again)} to work.  QC_ERR_ARG if n_fields < 1. */
+#define QC_WORK_FIELDS 9
+qc_status qc_eloc_work(qc_eloc* handle, uint64_t* work, int n_fields);
 
 /* Test hook (no counterpart in the paper): the library's next `after` device allocations
  * (handles, their workspaces, batches, gradient partials) succeed and the one after them

@@ -29,7 +29,8 @@ QC_OPT_SCAN_COST = 11
 QC_OPT_COUNT_WORK = 12
 QC_OPT_WAIT_LIMIT = 13
 QC_OPT_ALPHA_SLOTS = 14
-WORK_FIELDS = ("samples", "scan_rows", "tests", "probes", "hits_single", "hits_same", "hits_ab", "ctas")
+WORK_FIELDS = ("samples", "scan_rows", "tests", "probes", "hits_single", "hits_same", "hits_ab", "ctas",
+               "hits_scanned")
 QC_SRV_OPT_QUANTUM = 1
 QC_SRV_OPT_OLDEST_PCT = 2
 STATUS_NAMES = {0: "QC_OK", 1: "QC_PENDING", -1: "QC_ERR_ARG", -2: "QC_ERR_UNSORTED", -3: "QC_ERR_DUP",
@@ -93,7 +94,7 @@ def load_library(path: str = LIB_PATH):
     lib.qc_eloc_timings.restype = i32
     lib.qc_eloc_last_config.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.qc_eloc_last_config.restype = i32
-    lib.qc_eloc_work.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.qc_eloc_work.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), i32]
     lib.qc_eloc_work.restype = i32
     lib.qc_test_fail_alloc.argtypes = [i64]
     lib.qc_test_fail_alloc.restype = i32
@@ -207,8 +208,8 @@ def qc_test_fail_alloc(after: int):
 
 def qc_eloc_work(handle: QcHandle) -> dict:
     """Work counts of the last evaluation made with QC_OPT_COUNT_WORK = 1 (waits for it)."""
-    w = (ctypes.c_uint64 * 8)()
-    _check(load_library().qc_eloc_work(handle.ptr, w), handle.ptr)
+    w = (ctypes.c_uint64 * len(WORK_FIELDS))()
+    _check(load_library().qc_eloc_work(handle.ptr, w, len(WORK_FIELDS)), handle.ptr)
     return {k: int(v) for k, v in zip(WORK_FIELDS, w)}
 
 

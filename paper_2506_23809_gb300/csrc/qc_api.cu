@@ -732,16 +732,16 @@ qc_status qc_test_fail_alloc(int64_t after) {
     return QC_OK;
 }
 
-qc_status qc_eloc_work(qc_eloc* H, uint64_t* work8) {
-    if (!H || !work8) return QC_ERR_ARG;
+qc_status qc_eloc_work(qc_eloc* H, uint64_t* work, int n_fields) {
+    if (!H || !work || n_fields < 1) return QC_ERR_ARG;
     if (!H->work_recorded) return fail(H, QC_ERR_ARG, "no evaluation counted its work (set QC_OPT_COUNT_WORK first)");
     qc::WorkCounters w{};
     cudaError_t e = cudaMemcpyAsync(&w, H->d_work, sizeof(w), cudaMemcpyDeviceToHost, H->work_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(H->work_stream);
     if (e != cudaSuccess) return cuda_fail(H, e, "work counters copy");
-    const unsigned long long v[8] = {w.samples, w.scan_rows, w.tests, w.probes, w.hits_single, w.hits_same, w.hits_ab,
-                                     w.ctas};
-    for (int i = 0; i < 8; ++i) work8[i] = v[i];
+    const unsigned long long v[QC_WORK_FIELDS] = {w.samples, w.scan_rows, w.tests, w.probes, w.hits_single,
+                                                  w.hits_same, w.hits_ab, w.ctas, w.hits_scanned};
+    for (int i = 0; i < n_fields && i < QC_WORK_FIELDS; ++i) work[i] = v[i];
     return QC_OK;
 }
 

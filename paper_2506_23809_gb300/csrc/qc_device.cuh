@@ -1095,10 +1095,12 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
             const unsigned m1 = __ballot_sync(QC_FULLMASK, ent != 0 && sgl);
             const unsigned m2 = __ballot_sync(QC_FULLMASK, ent != 0 && same);
             const unsigned m3 = __ballot_sync(QC_FULLMASK, ent != 0 && !sgl && !same);
+            const unsigned m4 = __ballot_sync(QC_FULLMASK, ent != 0 && exact);
             if (lane == 0) {
                 if (m1) atomicAdd(&ep.work->hits_single, static_cast<unsigned long long>(__popc(m1)));
                 if (m2) atomicAdd(&ep.work->hits_same, static_cast<unsigned long long>(__popc(m2)));
                 if (m3) atomicAdd(&ep.work->hits_ab, static_cast<unsigned long long>(__popc(m3)));
+                if (m4) atomicAdd(&ep.work->hits_scanned, static_cast<unsigned long long>(__popc(m4)));
             }
         }
     };
@@ -1576,16 +1578,23 @@ __device__ __forceinline__ void reduce_pass1_body(const EvalParams& ep, double* 
         last = (atomicAdd(&ep.ctr->ticket, 1u) == nblk - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {
+        // the last block adds the partials: thread t those of blocks t, t + 256, ..., then a
+        // fixed tree over the threads (the same order on every run)
         __threadfence();
         double tr = 0.0, ti = 0.0;
         long long tw = 0, tu = 0;
-        for (unsigned b = 0; b < nblk; ++b) {
+        for (unsigned b = threadIdx.x; b < nblk; b += kRedThreads) {
             tr += __ldcg(part + 4 * b + 0);
             ti += __ldcg(part + 4 * b + 1);
             tw += __double_as_longlong(__ldcg(part + 4 * b + 2));
             tu += __double_as_longlong(__ldcg(part + 4 * b + 3));
         }
+        tr = block_sum<double>(tr, shd);
+        ti = block_sum<double>(ti, shd);
+        tw = block_sum<long long>(tw, shl);
+        tu = block_sum<long long>(tu, shl);
+        if (threadIdx.x != 0) return;
         Counters* c = ep.ctr;
         c->w = tw;
         c->used = static_cast<unsigned long long>(tu);
@@ -1621,10 +1630,12 @@ __device__ __forceinline__ void reduce_pass2_body(const EvalParams& ep, double* 
         last = (atomicAdd(&ep.ctr->ticket, 1u) == nblk - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {
         __threadfence();
         double tv = 0.0;
-        for (unsigned b = 0; b < nblk; ++b) tv += __ldcg(part + 4 * b);
+        for (unsigned b = threadIdx.x; b < nblk; b += kRedThreads) tv += __ldcg(part + 4 * b);
+        tv = block_sum<double>(tv, shd);
+        if (threadIdx.x != 0) return;
         Counters* c = ep.ctr;
         const unsigned f = c->flags;
         int st = QC_OK;

@@ -99,6 +99,7 @@ struct WorkCounters {
     unsigned long long hits_same;    //   same-spin doubles
     unsigned long long hits_ab;      //   opposite-spin doubles
     unsigned long long ctas;         // CTAs that copied the filter into shared memory
+    unsigned long long hits_scanned; // hits found by the join's scans (any kind; exact, no key load)
 };
 
 struct EvalParams {

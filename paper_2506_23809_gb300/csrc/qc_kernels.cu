@@ -10,7 +10,8 @@
 namespace qc {
 
 int reduce_blocks(long long n) {
-    long long b = (n + kRedThreads * 8 - 1) / (kRedThreads * 8);
+    // two rows per thread: enough blocks that every SM has a few (latency-bound loads)
+    long long b = (n + kRedThreads * 2 - 1) / (kRedThreads * 2);
     if (b < 1) b = 1;
     if (b > 1024) b = 1024;
     return static_cast<int>(b);

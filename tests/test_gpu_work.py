@@ -70,6 +70,11 @@ def test_work_counters(B, orc, opts, kind):
     assert (w["hits_single"], w["hits_same"], w["hits_ab"]) == (n1, n2, n3)
     assert n1 + n2 + n3 == summ["n_hits"]
     assert w["samples"] == 3000 and w["ctas"] == cfg["grid"]
+    # hits found by the join's scans: none without the join, some but not all with it
+    if kind in ("join", "join_lean"):
+        assert 0 < w["hits_scanned"] < summ["n_hits"]
+    else:
+        assert w["hits_scanned"] == 0
     pairs = summ["n_pairs"]
     if kind == "direct":
         assert w["tests"] == 0 and w["probes"] == pairs and w["scan_rows"] == 0
