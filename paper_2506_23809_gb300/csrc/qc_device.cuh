@@ -1106,12 +1106,13 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     };
 
     // Scan state of the join (the first phase of the main loop, before any candidate is
-    // queued, so it owns the candidate queue's space): a chunk of up to 32 groups of table
-    // rows, one per lane -- start, exclusive row offset and kind in q[0..95] -- scanned as one
-    // list of q[102] rows, 32 per step; the next alpha single excitation to classify in q[103]
-    // (shared memory keeps the scan state out of the registers of the enumeration loop).  When
-    // the alpha list is full, the enumeration runs over that segment and the scan state is
-    // entered again for the remaining alpha singles (classes 0 and 4 only).
+    // queued, so it owns the candidate queue's space): a chunk of up to 32 non-empty groups of
+    // table rows -- start, exclusive row offset and kind in q[0..95], packed to the front (an
+    // unused entry's offset is 0xFFFFFFFF) -- scanned as one list of q[102] rows, 32 per step;
+    // the next alpha single excitation to classify in q[103] (shared memory keeps the scan state
+    // out of the registers of the enumeration loop).  When the alpha list is full, the
+    // enumeration runs over that segment and the scan state is entered again for the remaining
+    // alpha singles (classes 0 and 4 only).
     auto store_chunk = [&](unsigned gst, unsigned gln, unsigned kind) {
         unsigned inc = gln;
 #pragma unroll
@@ -1119,9 +1120,14 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
             const unsigned y = __shfl_up_sync(QC_FULLMASK, inc, o);
             if (lane >= o) inc += y;
         }
-        q[lane] = gst;
-        q[32 + lane] = inc - gln;
-        q[64 + lane] = kind;
+        const unsigned ne = __ballot_sync(QC_FULLMASK, gln != 0u);
+        const int pos = __popc(ne & ltmask);
+        if (lane >= __popc(ne)) q[32 + lane] = 0xFFFFFFFFu;
+        if (gln != 0u) {
+            q[pos] = gst;
+            q[32 + pos] = inc - gln;
+            q[64 + pos] = kind;
+        }
         if (lane == 31) {
             q[102] = inc;
             if (DIAG && ep.work != nullptr && inc != 0u) atomicAdd(&ep.work->scan_rows, static_cast<unsigned long long>(inc));
@@ -1255,25 +1261,29 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
             const int st0 = static_cast<int>(q[103]);
             if (sbase < stotal) {
                 // steps of 32 rows of the chunk, while both hit queues have room for another
-                // step: each lane finds its row's group by a binary search over the offsets.  A
+                // step.  Lane l's row sbase + l lies in group g = (the groups starting at or
+                // before sbase) - 1 + (the groups starting at window positions 1..l): one ballot
+                // over the groups' offsets and one OR-reduction of their start positions.  A
                 // row connects to x when the popcount of its string of the other spin against
                 // x's is 2 or 4 (x's alpha group: a beta single or beta-beta double), 4 (x's beta
                 // group: an alpha-alpha double) or 0 or 2 (an alpha' group: the alpha single or
                 // an alpha-beta double).  Singles and doubles go to separate queues, so that hit
                 // batches do not mix the two element paths.
+                const unsigned offj = q[32 + lane];  // group lane's first row in the chunk
+                const unsigned long long ras = wsp->as, rbs = wsp->bs;
+                const unsigned lemask = ltmask | (1u << lane);
                 do {
                     const unsigned v = sbase + lane;
-                    int g = 0;
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1)
-                        if (q[32 + g + step] <= v) g += step;
+                    const unsigned rel = offj - sbase;
+                    const unsigned starts = __reduce_or_sync(QC_FULLMASK, rel - 1u < 31u ? 1u << rel : 0u);
+                    const int g = __popc(__ballot_sync(QC_FULLMASK, offj <= sbase)) - 1 + __popc(starts & lemask);
                     bool dbl = false, sgl = false;
                     unsigned code = 0u, row = 0u;
                     if (v < stotal) {
                         const unsigned kd = q[64 + g];
                         const ulonglong2 e = __ldg(tp.gent + QC_IX(q[g] + (v - q[32 + g]), 2 * tp.n, tp.err));
                         const unsigned kk = kd & 3u;
-                        const unsigned long long ref = kk == kScanBeta ? wsp->as : wsp->bs;
+                        const unsigned long long ref = kk == kScanBeta ? ras : rbs;
                         const unsigned long long dm = e.x ^ ref;
                         const int d = __popcll(dm);
                         sgl = kk == kScanAlpha ? d == 2 : (kk == kScanAlphaP && d == 0);
