@@ -568,13 +568,18 @@ __device__ __forceinline__ unsigned decode(unsigned code, const SysParams& sp,
         const unsigned sb = cls - kCodeDoubleAA;
         return (2u * k0 + sb) | ((2u * k2 + sb) << 8) | ((2u * k1 + sb) << 16) | ((2u * k3 + sb) << 24);
     }
-    int u = static_cast<int>((code >> 12) & 4095u);
-    int w = static_cast<int>(code & 4095u);
-    // singles lists may be compacted by the spin-string prefilter: map back
-    if (IA != nullptr) {
-        if (cls == 4u) { u = IA[QC_IX(u, sp.nsa, sp.err)]; w = IB[QC_IX(w, sp.nsb, sp.err)]; }
-        else if (cls == 0u) w = IA[QC_IX(w, sp.nsa, sp.err)];
-        else if (cls == 1u) w = IB[QC_IX(w, sp.nsb, sp.err)];
+    const int u = static_cast<int>((code >> 12) & 4095u);
+    const int w = static_cast<int>(code & 4095u);
+    // the filtered kernel's single lists are compacted by the spin-string prefilter; their maps
+    // IA / IB hold each entry's spatial orbitals (occupied | empty << 8)
+    if (IA != nullptr && (cls <= 1u || cls == 4u)) {
+        if (cls == 4u) {
+            const unsigned pa = IA[QC_IX(u, sp.nsa, sp.err)], pb = IB[QC_IX(w, sp.nsb, sp.err)];
+            return (2u * (pa & 255u)) | ((2u * (pa >> 8)) << 8) | ((2u * (pb & 255u) + 1u) << 16) |
+                   ((2u * (pb >> 8) + 1u) << 24);
+        }
+        const unsigned p = cls == 0u ? IA[QC_IX(w, sp.nsa, sp.err)] : IB[QC_IX(w, sp.nsb, sp.err)];
+        return (2u * (p & 255u) + cls) | ((2u * (p >> 8) + cls) << 8) | 0xFFFF0000u;
     }
     unsigned i, a, j = 255u, b = 255u;
     if (cls == 4u) {
@@ -1151,11 +1156,13 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
             const int t = t0 + lane;
             bool keep = false;
             uint32_t hv32 = 0u;
+            unsigned pk = 0u;  // the single's spatial orbitals, occupied | empty << 8
             if (t < sp.nsb) {
                 const int io = divB[t];
                 const int ki = occB[io], ka = virB[t - io * sp.vb];
                 const unsigned long long tm = T64[2 * ki + 1] ^ T64[2 * ka + 1];
                 hv32 = static_cast<uint32_t>(tm);
+                pk = static_cast<unsigned>(ki) | (static_cast<unsigned>(ka) << 8);
                 keep = tp.bset == nullptr ||
                        set_contains(tp.bset, tp.set_mask, Bs ^ (1ULL << ki) ^ (1ULL << ka), hxb ^ tm);
             }
@@ -1163,7 +1170,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
             if (keep) {
                 const int pos = nsb2 + __popc(m & ltmask);
                 H[QC_IX(oSB + pos, nH, sp.err)] = hv32;
-                IB[QC_IX(pos, sp.nsb, sp.err)] = static_cast<unsigned short>(t);
+                IB[QC_IX(pos, sp.nsb, sp.err)] = static_cast<unsigned short>(pk);
             }
             nsb2 += __popc(m);
         }
@@ -1200,11 +1207,13 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 const int t = t0 + lane;
                 bool keep = false;
                 uint32_t hv32 = 0u;
+                unsigned pk = 0u;
                 if (t < sp.nsa) {
                     const int io = divA[t];
                     const int ki = occA[io], ka = virA[t - io * sp.va];
                     const unsigned long long tm = T64[2 * ki] ^ T64[2 * ka];
                     hv32 = static_cast<uint32_t>(tm);
+                    pk = static_cast<unsigned>(ki) | (static_cast<unsigned>(ka) << 8);
                     keep = tp.aset == nullptr ||
                            set_contains(tp.aset, tp.set_mask, As ^ (1ULL << ki) ^ (1ULL << ka), hxa ^ tm);
                 }
@@ -1212,7 +1221,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 if (keep) {
                     const int pos = nsa2 + __popc(m & ltmask);
                     H[QC_IX(oSA + pos, nH, sp.err)] = hv32;
-                    IA[QC_IX(pos, nA, sp.err)] = static_cast<unsigned short>(t);
+                    IA[QC_IX(pos, nA, sp.err)] = static_cast<unsigned short>(pk);
                 }
                 nsa2 += __popc(m);
             }
@@ -1335,7 +1344,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 const bool keep = SEG ? (lng && pos < nA) : lng;
                 if (keep) {
                     H[QC_IX(oSA + pos, nH, sp.err)] = hv32;
-                    IA[QC_IX(pos, nA, sp.err)] = static_cast<unsigned short>(t);
+                    IA[QC_IX(pos, nA, sp.err)] = static_cast<unsigned short>((kd >> 8) & 0xFFFFu);
                 } else if (!lng && (!SEG || t >= a_seen)) {
                     gst = start;
                     gln = len;
