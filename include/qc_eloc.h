@@ -384,7 +384,8 @@ qc_status qc_batch_autotune(qc_batch* batch, void* stream, int iters, int64_t* b
  * (QC_SRV_OPT_QUANTUM, default 1e12): the oldest request with a guaranteed share of it
  * (QC_SRV_OPT_OLDEST_PCT, default half), the
  * others least remaining work first (none with more than 4x the oldest's remaining work,
- * which waits for a wave of its own); a request that does not fit whole runs a slice of its
+ * which waits for a wave of its own), and the wave's sample rows stay within
+ * QC_SRV_OPT_WAVE_ROWS unless it holds one request; a request that does not fit whole runs a slice of its
  * rows (against its whole sample table) and joins the next wave, and after a wave that ran
  * a slice the ready short requests (at most half a quantum) get a wave of their own, so
  * requests that arrive while a long one runs are served between its slices.  A request that can never fit the
@@ -422,6 +423,10 @@ qc_status qc_eloc_poll(qc_server* server, uint64_t ticket, qc_eloc_result* resul
 qc_status qc_server_stats(qc_server* server, uint64_t* stats4);
 #define QC_SRV_OPT_QUANTUM    1  /* enumerated pairs per wave, >= 0 (0: no slicing, one wave takes all) */
 #define QC_SRV_OPT_OLDEST_PCT 2  /* percent of a wave guaranteed to the oldest request, 1..100 (50) */
+#define QC_SRV_OPT_WAVE_ROWS  3  /* sample rows a wave of several requests may hold, >= 0 (65536; 0:
+                                    no limit): a longer request runs in a wave of its own, as the
+                                    plain launch would, instead of delaying the requests batched
+                                    with it until all of them are done */
 qc_status qc_server_set_option(qc_server* server, int option, int64_t value);
 qc_status qc_server_destroy(qc_server* server);  /* finishes queued work first */
 

@@ -33,6 +33,7 @@ WORK_FIELDS = ("samples", "scan_rows", "tests", "probes", "hits_single", "hits_s
                "hits_scanned")
 QC_SRV_OPT_QUANTUM = 1
 QC_SRV_OPT_OLDEST_PCT = 2
+QC_SRV_OPT_WAVE_ROWS = 3
 STATUS_NAMES = {0: "QC_OK", 1: "QC_PENDING", -1: "QC_ERR_ARG", -2: "QC_ERR_UNSORTED", -3: "QC_ERR_DUP",
                 -4: "QC_ERR_NELEC", -5: "QC_ERR_OOM", -6: "QC_ERR_BUDGET", -7: "QC_ERR_CUDA",
                 -8: "QC_ERR_ZERO_PSI", -9: "QC_ERR_MISSING", -10: "QC_ERR_TIMEOUT",

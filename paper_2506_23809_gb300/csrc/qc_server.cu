@@ -11,7 +11,10 @@
 //     pairs: the oldest request first (a guaranteed share of the quantum), then the others with
 //     the least remaining work first, none with more than kWaveSpread times the oldest's
 //     remaining work (it would hold the wave's short requests until it ends; it waits for a
-//     wave of its own).  A request too long for the room left runs a slice of
+//     wave of its own), and the wave's rows stay within `wave_rows` (a batch returns its
+//     requests when all of them are done, so a long request batched with another would wait
+//     for it: past that size a request runs alone, as the plain launch would, and batching
+//     is kept for the short requests whose launch costs it saves).  A request too long for the room left runs a slice of
 //     its rows against its whole sample table and comes back for the next wave, so a long
 //     request never holds the GPU for more than a wave while short ones wait; after a wave
 //     that ran a slice, the short requests that are ready (at most half a quantum each) get
@@ -130,6 +133,7 @@ struct qc_server {
     int active = 0;                      // admitted and not finished
     long long quantum = 1000000000000LL;  // enumerated pairs per wave (0: no slicing)
     int oldest_pct = 50;                 // share of a wave guaranteed to the oldest request
+    long long wave_rows = 1LL << 16;     // sample rows a wave of several requests may hold (0: any)
     bool last_wave_sliced = false;       // the last wave ran a slice of a long request
     bool stop = false;
     std::thread worker;
@@ -307,13 +311,15 @@ void launch_wave(qc_server* S, Lane& L, int lane_index) {
                              [&](const Request* a, const Request* b) { return work_left(a) < work_left(b); });
             std::vector<Request*> take;
             double room = Q;
+            long long rows_in = 0;
             for (Request* r : small) {
-                if (!take.empty() && work_left(r) > room) {
+                if (!take.empty() && (work_left(r) > room || (S->wave_rows > 0 && rows_in + rows_left(r) > S->wave_rows))) {
                     rest.push_back(r);
                     continue;
                 }
                 r->slice_end = r->job.n_u;
                 room -= work_left(r);
+                rows_in += rows_left(r);
                 take.push_back(r);
             }
             for (Request* r : rest) keep.push_back(r);
@@ -332,9 +338,10 @@ void launch_wave(qc_server* S, Lane& L, int lane_index) {
     // a request far larger than the oldest would hold the wave's short requests back until it
     // ends: it waits for a wave of its own (on the next free lane) instead
     const double cap = kWaveSpread * std::max(work_left(oldest), 1.0);
+    long long rows_in = rows_left(oldest);
     for (size_t i = 1; i < cand.size(); ++i) {
         Request* r = cand[i];
-        if (work_left(r) > cap && r->next_row == 0) {
+        if ((work_left(r) > cap && r->next_row == 0) || (S->wave_rows > 0 && rows_in + rows_left(r) > S->wave_rows)) {
             keep.push_back(r);
             continue;
         }
@@ -347,6 +354,7 @@ void launch_wave(qc_server* S, Lane& L, int lane_index) {
         }
         r->slice_end = r->next_row + rows;
         room -= static_cast<double>(rows) * static_cast<double>(r->pairs_per_row);
+        rows_in += rows;
         take.push_back(r);
     }
     {
@@ -597,6 +605,7 @@ qc_status qc_server_set_option(qc_server* S, int option, int64_t value) {
     std::lock_guard<std::mutex> lk(S->mu);
     if (option == QC_SRV_OPT_QUANTUM && value >= 0) S->quantum = value;
     else if (option == QC_SRV_OPT_OLDEST_PCT && value >= 1 && value <= 100) S->oldest_pct = static_cast<int>(value);
+    else if (option == QC_SRV_OPT_WAVE_ROWS && value >= 0) S->wave_rows = value;
     else return QC_ERR_ARG;
     return QC_OK;
 }
