@@ -182,8 +182,10 @@ __device__ __forceinline__ unsigned home_bucket(unsigned g, unsigned nb_mask) {
 }
 
 // Returns the table row of key (low hash bits g), or -1.  Buckets hold two 64-bit entries
-// (fingerprint << 32 | row + 1); an empty entry ends the probe sequence.
-__device__ __forceinline__ long long table_find(const TableParams& tp, ulonglong2 key, unsigned g) {
+// (fingerprint << 32 | row + 1); an empty entry ends the probe sequence.  Called only on a
+// fingerprint collision (about 0.2% of hits), so it is kept out of line: its loop would
+// otherwise sit in the middle of the hit stage's code.
+static __device__ __noinline__ long long table_find(const TableParams& tp, ulonglong2 key, unsigned g) {
     unsigned b = home_bucket(g, tp.nb_mask);
     const ulonglong2* buckets = reinterpret_cast<const ulonglong2*>(tp.slots);
     for (unsigned it = 0; it <= tp.nb_mask; ++it) {
@@ -900,7 +902,7 @@ __device__ __forceinline__ void sample_finish(const EvalParams& ep, long long s,
     write_sample<PREC>(ep, s, ediag, psix, re, im, th, tr, ts, tm);
 }
 
-__device__ __forceinline__ void invalid_sample(const EvalParams& ep, long long s, int lane) {
+static __device__ __noinline__ void invalid_sample(const EvalParams& ep, long long s, int lane) {
     if (lane == 0) {
         double2 e;
         e.x = __longlong_as_double(0x7ff8000000000000LL);
