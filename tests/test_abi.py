@@ -82,3 +82,11 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
     assert so.qc_eloc_eval(None, None, None, None, 0, None, None, 0, None, None) == -1
     so.qc_eloc_destroy.argtypes = [ctypes.c_void_p]
     assert so.qc_eloc_destroy(None) == 0
+    # the work counters, a batch's row piece and a server option refuse a NULL object too
+    so.qc_eloc_work.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    w = (ctypes.c_uint64 * 9)()
+    assert so.qc_eloc_work(None, w, 9) == -1
+    so.qc_batch_set_rows.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64]
+    assert so.qc_batch_set_rows(None, 0, 0, 0) == -1
+    so.qc_server_set_option.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]
+    assert so.qc_server_set_option(None, 3, 5) == -1

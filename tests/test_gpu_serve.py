@@ -83,6 +83,35 @@ def test_alone_equals_in_the_mix_and_handle_api(B, orc):
         B.qc_server_destroy(srv)
 
 
+def test_wave_rows_cap_leaves_results_unchanged(B):
+    """QC_SRV_OPT_WAVE_ROWS only decides which requests share a wave: with no cap, the default
+    and a cap below every request's rows (each request alone, on the single-molecule path) the
+    same requests give bitwise the same E_loc and energies; a negative cap is refused."""
+    specs = [(28, 10, 1500, 2201), (20, 8, 700, 2301), (40, 12, 900, 2401), (24, 8, 2500, 2501)]
+    mols = [_mol(n, ne, nu, sd) for n, ne, nu, sd in specs]
+    runs = []
+    for cap in (0, -1, 100):
+        srv = B.qc_server_create(0, 8 << 30, max_slots=16, n_streams=2)
+        try:
+            if cap >= 0:
+                B.qc_server_set_option(srv, B.QC_SRV_OPT_WAVE_ROWS, cap)
+            tickets = [B.qc_eloc_submit(srv, ints.h, ints.eri, 0.0, n, ne, keys, counts, psi, mol_key=k + 1)
+                       for k, ((n, ne, nu, sd), (ints, keys, counts, psi)) in enumerate(zip(specs, mols))]
+            runs.append([_wait(B, srv, t) for t in tickets])
+        finally:
+            B.qc_server_destroy(srv)
+    for k in range(len(specs)):
+        for r in runs[1:]:
+            assert r[k][0]["status"] == 0 and r[k][0]["e_re"] == runs[0][k][0]["e_re"]
+            assert np.array_equal(r[k][1].view(np.uint64), runs[0][k][1].view(np.uint64)), k
+    srv = B.qc_server_create(0, 1 << 30, max_slots=4, n_streams=1)
+    try:
+        with pytest.raises(B.QcError):
+            B.qc_server_set_option(srv, B.QC_SRV_OPT_WAVE_ROWS, -5)
+    finally:
+        B.qc_server_destroy(srv)
+
+
 def test_budget_refusal_and_eviction(B):
     ints, keys, counts, psi = _mol(24, 8, 500, 1701)
     srv = B.qc_server_create(0, 1 << 20, max_slots=4, n_streams=1)
