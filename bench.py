@@ -402,7 +402,7 @@ def run_ours(args):
         pg.all_reduce(c)
         pairs_all, samples_all = int(c[0].item()), int(c[1].item())
         # Eq. 1 across ranks: gather (W, sum cE, W * var) and combine
-        W, Ebar, var = shards.allgather_combine(shards.partials(summ), pg, device=dev)
+        W, Ebar, var = shards.allgather_combine(shards.partials(summ), pg, device=dev, status=int(summ["status"]))
     else:
         W, Ebar, var = summ["w"], summ["energy"], summ["var"]
     value = pairs_all * args.steps / t_max

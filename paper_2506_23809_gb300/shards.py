@@ -38,14 +38,32 @@ def combine(parts) -> tuple[float, complex, float]:
     return float(W), ebar, float(var)
 
 
-def allgather_combine(part: np.ndarray, dist, device=None) -> tuple[float, complex, float]:
+class RankFailure(RuntimeError):
+    """A rank reported a failed evaluation (a nonzero qc_eloc status) at the exchange step."""
+
+    def __init__(self, statuses):
+        bad = {r: s for r, s in enumerate(statuses) if s != 0}
+        super().__init__(f"ranks reported failed evaluations (rank: status): {bad}")
+        self.statuses = list(statuses)
+
+
+def allgather_combine(part: np.ndarray, dist, device=None, status: int = 0) -> tuple[float, complex, float]:
     """Gather every rank's partials with torch.distributed (gloo on CPU tensors, NCCL on
-    CUDA tensors) and combine them; every rank gets the same result."""
+    CUDA tensors) and combine them; every rank gets the same result.  Each rank also sends
+    the status of its evaluation: if any rank's is nonzero, every rank raises RankFailure
+    instead of combining (a rank whose kernel ran out of a bounded wait, say, must not
+    contribute its partial sums).  A rank that never reaches the exchange (it died) ends the
+    others' collective with the process group's error or timeout."""
     import torch
-    t = torch.as_tensor(np.asarray(part, dtype=np.float64), device=device)
+    v = np.append(np.asarray(part, dtype=np.float64).reshape(4), float(status))
+    t = torch.as_tensor(v, device=device)
     out = [torch.empty_like(t) for _ in range(dist.get_world_size())]
     dist.all_gather(out, t)
-    return combine(torch.stack(out).cpu().numpy())
+    g = torch.stack(out).cpu().numpy()
+    statuses = [int(s) for s in g[:, 4]]
+    if any(s != 0 for s in statuses):
+        raise RankFailure(statuses)
+    return combine(g[:, :4])
 
 
 # ---------------------------------------------------------------------------------------

@@ -208,3 +208,71 @@ def test_two_gloo_ranks_run_a_plan(tmp_path, orc):
         mo, var, w, _ = orc.reduce(el, counts)
         W, er, ei, V = got[m]
         assert W == w and abs(complex(er, ei) - mo) <= 1e-12 * abs(mo) and abs(V - var) <= 1e-10 * var
+
+
+def _failing_worker(rank, world, port, out_dir, mode):
+    """Rank 1 fails: 'status' -- its evaluation reports a nonzero status at the exchange;
+    'dies' -- it raises before the exchange and exits.  Every surviving rank records what
+    its exchange step raised, and how long it took."""
+    import datetime
+    import time
+
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    part = np.array([10.0 + rank, 1.0, 0.5, 2.0])
+    if mode == "dies" and rank == 1:
+        raise RuntimeError("rank 1 fails before the exchange")
+    status = -10 if (mode == "status" and rank == 1) else 0   # QC_ERR_TIMEOUT
+    t0 = time.time()
+    try:
+        shards.allgather_combine(part, dist, status=status)
+        what = "combined"
+    except shards.RankFailure as ex:
+        what = "RankFailure " + " ".join(str(s) for s in ex.statuses)
+    except RuntimeError as ex:  # the process group's error when a peer is gone
+        what = "RuntimeError " + str(ex).splitlines()[0][:80]
+    with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
+        f.write(f"{what}\n{time.time() - t0:.3f}\n")
+
+
+def _run_failing(tmp_path, mode):
+    import multiprocessing as mp
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, str(tmp_path), mode)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    codes = [p.exitcode for p in procs]
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+    out = {}
+    for r in range(2):
+        path = tmp_path / f"rank{r}.txt"
+        if path.exists():
+            what, dt = path.read_text().splitlines()
+            out[r] = (what, float(dt))
+    return codes, out
+
+
+def test_a_failed_rank_status_reaches_every_rank(tmp_path):
+    """A rank whose evaluation failed (here a bounded device wait that ran out) reports its
+    status at the exchange step: every rank raises RankFailure naming it, and none combines
+    partial sums that include the failed rank's."""
+    codes, out = _run_failing(tmp_path, "status")
+    assert codes == [0, 0]
+    for r in range(2):
+        assert out[r][0] == "RankFailure 0 -10", out[r]
+
+
+def test_a_rank_that_dies_is_detected(tmp_path):
+    """A rank that raises before the exchange step and exits: the surviving rank's collective
+    ends with the process group's error (the peer closed its connection, or the 10 s
+    timeout) rather than hanging, so it can stop before its next launch."""
+    codes, out = _run_failing(tmp_path, "dies")
+    assert codes[1] != 0 and 1 not in out
+    assert codes[0] == 0 and out[0][0].startswith("RuntimeError"), out
+    assert out[0][1] < 60.0
