@@ -864,7 +864,7 @@ __device__ __forceinline__ void sample_finish(const EvalParams& ep, long long s,
         sre = warp_sum(static_cast<double>(acc.sr) + static_cast<double>(acc.cr));
         sim = warp_sum(static_cast<double>(acc.si) + static_cast<double>(acc.ci));
     }
-    const unsigned long long hits = warp_sum_u64(acc.hits);
+    const unsigned long long hits = __reduce_add_sync(QC_FULLMASK, acc.hits);
     // the digests exist in the diagnostic kernels only; missing x' only without the filter
     // (the accurate-energy kernel)
     const unsigned long long rows = DIAG ? warp_sum_u64(acc.rowsum) : 0ULL;
@@ -1228,27 +1228,38 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 nsa2 += __popc(m);
             }
         }
+        // the same-spin pair lists serve classes 2 (alpha) and 3 (beta) alone, which the join
+        // enumerates only when x's beta (alpha) group is too long to scan
+        const bool needA = !join || enumB, needB = !join || enumA;
         if (lean) {
-            for (int t = lane; t < sp.oa; t += 32) H[oPAo + t] = static_cast<uint32_t>(T64[2 * occA[t]]);
-            for (int t = lane; t < sp.va; t += 32) H[oPAv + t] = static_cast<uint32_t>(T64[2 * virA[t]]);
-            for (int t = lane; t < sp.ob; t += 32) H[oPBo + t] = static_cast<uint32_t>(T64[2 * occB[t] + 1]);
-            for (int t = lane; t < sp.vb; t += 32) H[oPBv + t] = static_cast<uint32_t>(T64[2 * virB[t] + 1]);
+            if (needA) {
+                for (int t = lane; t < sp.oa; t += 32) H[oPAo + t] = static_cast<uint32_t>(T64[2 * occA[t]]);
+                for (int t = lane; t < sp.va; t += 32) H[oPAv + t] = static_cast<uint32_t>(T64[2 * virA[t]]);
+            }
+            if (needB) {
+                for (int t = lane; t < sp.ob; t += 32) H[oPBo + t] = static_cast<uint32_t>(T64[2 * occB[t] + 1]);
+                for (int t = lane; t < sp.vb; t += 32) H[oPBv + t] = static_cast<uint32_t>(T64[2 * virB[t] + 1]);
+            }
         } else {
-            for (int t = lane; t < sp.npoa; t += 32) {
-                const unsigned p = lut[t];
-                H[oPAo + t] = static_cast<uint32_t>(T64[2 * occA[p & 255u]] ^ T64[2 * occA[p >> 8]]);
+            if (needA) {
+                for (int t = lane; t < sp.npoa; t += 32) {
+                    const unsigned p = lut[t];
+                    H[oPAo + t] = static_cast<uint32_t>(T64[2 * occA[p & 255u]] ^ T64[2 * occA[p >> 8]]);
+                }
+                for (int t = lane; t < sp.npva; t += 32) {
+                    const unsigned p = lut[t];
+                    H[oPAv + t] = static_cast<uint32_t>(T64[2 * virA[p & 255u]] ^ T64[2 * virA[p >> 8]]);
+                }
             }
-            for (int t = lane; t < sp.npva; t += 32) {
-                const unsigned p = lut[t];
-                H[oPAv + t] = static_cast<uint32_t>(T64[2 * virA[p & 255u]] ^ T64[2 * virA[p >> 8]]);
-            }
-            for (int t = lane; t < sp.npob; t += 32) {
-                const unsigned p = lut[t];
-                H[oPBo + t] = static_cast<uint32_t>(T64[2 * occB[p & 255u] + 1] ^ T64[2 * occB[p >> 8] + 1]);
-            }
-            for (int t = lane; t < sp.npvb; t += 32) {
-                const unsigned p = lut[t];
-                H[oPBv + t] = static_cast<uint32_t>(T64[2 * virB[p & 255u] + 1] ^ T64[2 * virB[p >> 8] + 1]);
+            if (needB) {
+                for (int t = lane; t < sp.npob; t += 32) {
+                    const unsigned p = lut[t];
+                    H[oPBo + t] = static_cast<uint32_t>(T64[2 * occB[p & 255u] + 1] ^ T64[2 * occB[p >> 8] + 1]);
+                }
+                for (int t = lane; t < sp.npvb; t += 32) {
+                    const unsigned p = lut[t];
+                    H[oPBv + t] = static_cast<uint32_t>(T64[2 * virB[p & 255u] + 1] ^ T64[2 * virB[p >> 8] + 1]);
+                }
             }
         }
         __syncwarp();
