@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(kRedThreads) reduce_batch_pass2(const MolParam
 // MAXT: the launch bound.  The per-molecule parameters live in shared memory, not in the
 // constant bank, so the sample code needs more registers than in the single-molecule
 // kernel: 512 threads (16 warps, 128 registers) keep it free of spills, 640 threads (20
-// warps, 96 registers) trade a few spills for more warps.
+// warps, 96 registers) trade a few spills for more warps (768 threads would spill 80-170
+// bytes a thread).
 // JOIN: the molecules' tables carry the sample-space join index (built with U = 4 only).
 template <int PREC, int U, int MAXT, bool JOIN>
 __global__ void __launch_bounds__(MAXT) eloc_batch_kernel(const __grid_constant__ BatchParams bp) {
@@ -130,13 +131,11 @@ __global__ void __launch_bounds__(MAXT) eloc_batch_kernel(const __grid_constant_
                                             ? static_cast<long long>(__ldg(mp.ep.order + r0 + static_cast<long long>(q)))
                                             : r0 + static_cast<long long>(q);
                     const int c = static_cast<int>(it - q * C);
-                    // a joining molecule's alpha list may be capped (mp.tp.alpha_cap): segments
-                    if (mp.ep.lean)
-                        run_sample<PREC, U, true, 1, JOIN, false, JOIN>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c,
-                                                                         static_cast<int>(C));
-                    else
-                        run_sample<PREC, U, true, 0, JOIN, false, JOIN>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c,
-                                                                         static_cast<int>(C));
+                    // a joining molecule's alpha list may be capped (mp.tp.alpha_cap): segments.
+                    // One copy of the sample code takes either list layout (ep.lean), so the
+                    // kernel holds it once
+                    run_sample<PREC, U, true, 2, JOIN, false, JOIN>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c,
+                                                                     static_cast<int>(C));
                 }
             }
         }
