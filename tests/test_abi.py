@@ -39,6 +39,17 @@ def test_exports_match_header(lib):
     assert exported == names
 
 
+def test_checked_build_exports_the_same_abi(lib):
+    """The bounds-checked testing build (QC_CHECKED) compiles from the same sources and
+    exports exactly the same functions as the product library."""
+    from paper_2506_23809_gb300 import build
+    path = build.build(checked=True)
+    assert path != lib[1]
+    ctypes.CDLL(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    assert sorted(set(re.findall(r"\b(qc_\w+)$", out, flags=re.M))) == _declared()
+
+
 def test_struct_layout_matches_binding(tmp_path):
     from paper_2506_23809_gb300 import binding as B
     src = tmp_path / "sz.c"
