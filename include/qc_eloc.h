@@ -183,7 +183,8 @@ typedef struct {
     int64_t          hit_list_cap;
 } qc_eloc_out;
 
-/* Create a handle for one Hamiltonian.  n_orb: even, 2..128.  n_elec: even, S_z = 0
+/* Create a handle for one Hamiltonian, the second-quantized H of Eq. 2 (Sec. II-A) given by
+ * its one- and two-electron integrals h_pq and (pq|rs).  n_orb: even, 2..128.  n_elec: even, S_z = 0
  * (n_elec/2 electrons of each spin), 0 < n_elec < n_orb.  h, eri: host FP64 (layout
  * above), copied to the device.  e_core: constant added to every diagonal element.
  * precision: QC_FP64 | QC_FP32_COMP.  mode: QC_SAMPLE | QC_FULL.  Uses the current CUDA
@@ -207,7 +208,11 @@ qc_status qc_eloc_set_option(qc_eloc* handle, int option, int64_t value);
  * o_a v_a o_b v_b (o occupied, v empty spatial orbitals per spin). */
 int64_t qc_eloc_pairs_per_sample(const qc_eloc* handle);
 
-/* Evaluate E_loc for n_u samples on `stream` (a cudaStream_t, NULL = legacy default).
+/* Evaluate E_loc(x) = sum_x' <x|H|x'> psi(x') / psi(x) (Eq. 5, Sec. III-B) for n_u samples,
+ * x' running over x and every single and double excitation of x: QC_SAMPLE keeps the x'
+ * present in the table (the "sample space" energy of Sec. IV-C-4), QC_FULL needs them all;
+ * then the count-weighted energy and variance of Eq. 1 (Sec. II-A) into out->summary.
+ * Runs on `stream` (a cudaStream_t, NULL = legacy default).
  *   samples  device uint64[n_u][2]   bitstrings to evaluate
  *   counts   device int64[n_u]       sample counts (>= 0)
  *   psi      device complex128[n_u]  psi(x), (re, im) interleaved
