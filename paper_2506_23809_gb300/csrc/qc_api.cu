@@ -636,18 +636,20 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
     if (join) {
         unsigned* jstart = reinterpret_cast<unsigned*>(H->d_join + jo_start);
         ulonglong2* gent = reinterpret_cast<ulonglong2*>(H->d_join + jo_ent);
-        // the samples are the table rows: order them heavy first by their own groups' sizes
+        // samples heavy first by the sizes of their own groups: the table's rows, or a caller's
+        // samples no more numerous than its rows (the order's buffers hold one entry per row)
         unsigned* order = nullptr;
         unsigned* pa = nullptr;
         unsigned* pb = nullptr;
-        if (own_table) {
+        if (own_table || n_u <= nt) {
             order = reinterpret_cast<unsigned*>(H->d_join + jo_ord);
             pa = reinterpret_cast<unsigned*>(H->d_join + jo_ord + a256(static_cast<size_t>(nt) * 4));
             pb = reinterpret_cast<unsigned*>(H->d_join + jo_ord + 2 * a256(static_cast<size_t>(nt) * 4));
             QC_CHK(cudaMemsetAsync(pa, 0, 2 * a256(static_cast<size_t>(nt) * 4), s), "memset sample order sizes");
         }
         QC_CHK(qc::launch_join_index(tp, static_cast<unsigned>(nbuckets), H->d_join + jo_ws, jkey, jlen, jstart,
-                                     gent, s, order, pa, pb),
+                                     gent, s, order, pa, pb,
+                                     own_table ? nullptr : reinterpret_cast<const ulonglong2*>(samples), n_u, H->d_T),
                "join index launch");
         join_order = order;
         tp.jstart = jstart;

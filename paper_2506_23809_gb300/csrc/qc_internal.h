@@ -245,9 +245,13 @@ int reduce_blocks(long long n);
 size_t join_workspace_bytes(long long n, unsigned set_size);
 // with order (the table is the sample set): also the heavy-first order of the samples (pa, pb:
 // n entries each of scratch)
+// with order and samples (not the table's rows; n_samples <= tp.n, T the key hash's table): the
+// heavy-first order of those samples, their groups looked up in the table's sets
 cudaError_t launch_join_index(const TableParams& tp, unsigned set_size, void* ws, unsigned* jkey,
                               unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s,
-                              unsigned* order = nullptr, unsigned* pa = nullptr, unsigned* pb = nullptr);
+                              unsigned* order = nullptr, unsigned* pa = nullptr, unsigned* pb = nullptr,
+                              const ulonglong2* samples = nullptr, long long n_samples = 0,
+                              const unsigned long long* T = nullptr);
 // a batch's join index: m sort items (every molecule's 2n keys, values written by K0),
 // n_slots group sizes (slot_base[M] = n_slots, the sentinel key); entries in one gent array
 size_t join_batch_workspace_bytes(long long m, unsigned long long n_slots);

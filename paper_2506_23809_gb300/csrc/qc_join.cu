@@ -176,6 +176,37 @@ __global__ void __launch_bounds__(256) join_gather_batch_kernel(const qc::MolPar
     }
 }
 
+// Samples that are not the table's rows (a caller's table, e.g. one rank's rows against the
+// whole sample set): each sample's own alpha- and beta-group sizes in the table, looked up by
+// its spin strings in the table's sets (0 for a string the table does not hold), into pa / pb.
+__global__ void __launch_bounds__(256) sample_group_sizes_kernel(const qc::TableParams tp,
+                                                                 const ulonglong2* __restrict__ samples,
+                                                                 long long n_u,
+                                                                 const unsigned long long* __restrict__ T,
+                                                                 unsigned set_size,
+                                                                 const unsigned* __restrict__ jlen,
+                                                                 unsigned* __restrict__ pa,
+                                                                 unsigned* __restrict__ pb) {
+    for (long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; r < n_u;
+         r += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const ulonglong2 key = samples[r];
+        unsigned long long ha = 0, hb = 0;  // the alpha and beta parts of the key's linear hash
+        for (unsigned long long w = key.x; w; w &= w - 1ULL) {
+            const int bit = __ffsll(w) - 1;
+            if (bit & 1) hb ^= __ldg(T + bit); else ha ^= __ldg(T + bit);
+        }
+        for (unsigned long long w = key.y; w; w &= w - 1ULL) {
+            const int bit = __ffsll(w) - 1;
+            if (bit & 1) hb ^= __ldg(T + 64 + bit); else ha ^= __ldg(T + 64 + bit);
+        }
+        const unsigned long long sa = qc::spin_string(key, 0), sb = qc::spin_string(key, 1);
+        const unsigned la = sa != 0ULL ? qc::set_slot(tp.aset, tp.set_mask, sa, ha) : qc::kNoSlot;
+        const unsigned lb = sb != 0ULL ? qc::set_slot(tp.bset, tp.set_mask, sb, hb) : qc::kNoSlot;
+        pa[r] = la != qc::kNoSlot ? __ldg(jlen + la) : 0u;
+        pb[r] = lb != qc::kNoSlot ? __ldg(jlen + set_size + lb) : 0u;
+    }
+}
+
 // Sort key of the heavy-first sample order: 255 - (8 log2 of the sizes of the sample's own
 // alpha and beta groups, in eighths of an octave); integer arithmetic only.
 __device__ __forceinline__ unsigned order_priority_key(unsigned v) {
@@ -283,20 +314,27 @@ size_t qc::join_workspace_bytes(long long n, unsigned set_size) { return jlayout
 
 cudaError_t qc::launch_join_index(const TableParams& tp, unsigned set_size, void* ws, unsigned* jkey,
                                   unsigned* jlen, unsigned* jstart, ulonglong2* gent, cudaStream_t s,
-                                  unsigned* order, unsigned* pa, unsigned* pb) {
-    const long long n = tp.n;
-    if (n <= 0) return cudaSuccess;
-    const long long m = 2 * n;
+                                  unsigned* order, unsigned* pa, unsigned* pb, const ulonglong2* samples,
+                                  long long n_samples, const unsigned long long* T) {
+    if (tp.n <= 0) return cudaSuccess;
+    const long long m = 2 * tp.n;
     const unsigned* skey = nullptr;
     const unsigned* sval = nullptr;
-    cudaError_t e = join_sort(jkey, nullptr, n, m, 2ULL * set_size, jlen, jstart, ws, &skey, &sval, s);
+    cudaError_t e = join_sort(jkey, nullptr, tp.n, m, 2ULL * set_size, jlen, jstart, ws, &skey, &sval, s);
     const unsigned gblocks = static_cast<unsigned>(std::min<long long>((m + 255) / 256, 8192));
     if (e == cudaSuccess) {
         join_gather_kernel<<<gblocks, 256, 0, s>>>(tp.keys, skey, sval, m, set_size, gent, jlen,
-                                                   order ? pa : nullptr, pb);
+                                                   order != nullptr && samples == nullptr ? pa : nullptr, pb);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && order != nullptr) {
+    // the samples to order: the table's rows, or a caller's samples (their groups looked up)
+    const long long n = samples != nullptr ? n_samples : tp.n;
+    if (e == cudaSuccess && order != nullptr && samples != nullptr && n > 0) {
+        const unsigned sblocks = static_cast<unsigned>(std::min<long long>((n + 255) / 256, 8192));
+        sample_group_sizes_kernel<<<sblocks, 256, 0, s>>>(tp, samples, n, T, set_size, jlen, pa, pb);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && order != nullptr && n > 0) {
         // heavy-first sample order: one stable 8-bit pass over the priority keys (the sort
         // buffers are free once the gather has run)
         const JLayout L = jlayout(m, 2ULL * set_size);
