@@ -399,6 +399,28 @@ def test_medium_n52_and_shards(B, orc):
     assert W == w and abs(E - m) <= RTOL_FP64 * abs(m)
 
 
+def test_join_shards_equal_the_whole_bitwise(B, orc):
+    """With the sample-space join, rows evaluated against a caller's table (two shards of the
+    sample set, each ordered heavy first by its groups looked up in the table's sets) give
+    bitwise the E_loc of the same rows in one evaluation of the whole set (ordered by the
+    table's own group sizes): the order schedules samples, it never changes a sample's sum."""
+    ints = I.make_integrals(26, 52, 5301)
+    keys = I.rank_weighted_samples(26, 7, 7, 4000, seed=5302)
+    counts = I.zipf_counts(4000, 400_000, 5303)
+    psi = I.lognormal_psi(4000, 5304)
+    whole = run_gpu(B, ints, 52, 14, keys, counts, psi, opts={10: 2}, diag=False)
+    assert whole["cfg"]["kernel"] in (4, 5)
+    for lo, hi in ((0, 1500), (1500, 4000)):
+        gs = run_gpu(B, ints, 52, 14, keys[lo:hi], counts[lo:hi], psi[lo:hi], table=(keys, psi), opts={10: 2},
+                     diag=False)
+        # the same kernel form and shape; the grid follows the rows and never enters a sum
+        assert {k: v for k, v in gs["cfg"].items() if k != "grid"} == \
+            {k: v for k, v in whole["cfg"].items() if k != "grid"}
+        assert np.array_equal(gs["eloc"].view(np.uint64), whole["eloc"][lo:hi].view(np.uint64)), (lo, hi)
+    want = orc.eloc(ints.h, ints.eri, 0.0, 52, keys[:300], psi[:300], keys, psi)
+    assert_eloc_close(whole["eloc"][:300], want)
+
+
 def test_full_size_n52_sampled(B, orc):
     """The benchmark workload (N=52, 14 e, 1e5 samples, Zipf counts summing to 1e7) in the
     launch configuration the benchmark uses: 512 sampled rows checked against the oracle
