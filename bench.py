@@ -45,7 +45,7 @@ UNIT = "connected matrix elements/s"
 #       single 1 + 3 n_elec / 2 (h_ai, (ai|kk) over the occupied k, (ak|ki) over the same spin),
 #       same-spin double 2, opposite-spin double 1
 #     + per sample 16 (x) + 16 (psi(x)) + 16 (E_loc written) + 8 per spin-string set lookup
-#       (one per single excitation, 2 o v)
+#       (one per single excitation, 2 o v, and one per beta' the join's beta' phase classifies)
 #     + per CTA the Bloom filter copied into shared memory (4 x 2^fw).
 # achieved = that work / the kernel's mean event-timed duration over the timed steps; the
 # peaks are the derived ALU peak (SMs x 4 x 16 lanes x max clock) with the library's measured
@@ -223,7 +223,7 @@ def work_l2_bytes(w, n_elec, n_orb, elem_bytes, filter_log2w):
             + (32 + elem_bytes * (1 + 3 * n_elec // 2)) * w["hits_single"]
             + (32 + 2 * elem_bytes) * w["hits_same"] + (32 + elem_bytes) * w["hits_ab"]
             + (48 + 8 * 2 * o * v) * w["samples"] + (4 << filter_log2w) * w["ctas"]
-            - 16 * w.get("hits_scanned", 0))
+            - 16 * w.get("hits_scanned", 0) + 8 * w.get("beta_looked", 0))
 
 
 def _cpu_baseline(ints, s, spec, target_s, pairs_per_sample, gpu_eloc=None):

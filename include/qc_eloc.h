@@ -124,6 +124,14 @@ typedef int qc_status;
                                    up to the order of accumulation */
 #define QC_OPT_SCAN_COST    11  /* join: a group is scanned when its rows x this / 4 are at most
                                    the excitations it replaces; 0 the default */
+#define QC_OPT_BETA_COST    15  /* join, launches whose alpha list is capped (QC_OPT_ALPHA_SLOTS,
+                                   or the automatic choice at large orbital counts): for a sample
+                                   with at least 8 alpha' groups too long to scan in the list's
+                                   first segment, the group of a beta' (a single excitation of its
+                                   beta string in the table) is scanned for the rows of long alpha'
+                                   groups when its rows x this / 4 are at most that number, instead
+                                   of enumerating the beta' against each of them; 0 the default
+                                   (8), -1 never, else 1..1024.  Same connected set either way */
 #define QC_OPT_COUNT_WORK   12  /* 1: the local-energy kernel counts the work it does (read with
                                    qc_eloc_work); costs global atomics, so off (0) in timed runs */
 #define QC_OPT_ALPHA_SLOTS  14  /* join: slots of the per-warp alpha single list (the alpha' groups
@@ -449,8 +457,10 @@ qc_status qc_probe_peaks(double* alu_ops_per_s, double* l2_gather_gbs, void* str
  * (16-byte entries), excitations tested against the shared-memory Bloom filter, candidates
  * probed in the bucket table (16-byte buckets), hits that are single excitations, same-spin
  * doubles, opposite-spin doubles, CTAs that copied the filter, hits found by the join's scans
- * (of all kinds; their keys are not loaded again)} to work.  QC_ERR_ARG if n_fields < 1. */
-#define QC_WORK_FIELDS 9
+ * (of all kinds; their keys are not loaded again), beta' = beta single excitations looked up
+ * in the table's beta set by the join's beta' phase (8-byte slots), beta' groups that phase
+ * scans} to work.  QC_ERR_ARG if n_fields < 1. */
+#define QC_WORK_FIELDS 11
 qc_status qc_eloc_work(qc_eloc* handle, uint64_t* work, int n_fields);
 
 /* Test hook (no counterpart in the paper): the library's next `after` device allocations

@@ -26,11 +26,12 @@ QC_OPT_LEAN = 8
 QC_OPT_CHUNK_PAIRS = 9
 QC_OPT_JOIN = 10
 QC_OPT_SCAN_COST = 11
+QC_OPT_BETA_COST = 15
 QC_OPT_COUNT_WORK = 12
 QC_OPT_WAIT_LIMIT = 13
 QC_OPT_ALPHA_SLOTS = 14
 WORK_FIELDS = ("samples", "scan_rows", "tests", "probes", "hits_single", "hits_same", "hits_ab", "ctas",
-               "hits_scanned")
+               "hits_scanned", "beta_looked", "beta_groups")
 QC_SRV_OPT_QUANTUM = 1
 QC_SRV_OPT_OLDEST_PCT = 2
 QC_SRV_OPT_WAVE_ROWS = 3

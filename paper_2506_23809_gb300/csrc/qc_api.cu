@@ -316,6 +316,10 @@ qc_status qc_eloc_set_option(qc_eloc* H, int option, int64_t value) {
             if (value < 0 || value > 1024) return fail(H, QC_ERR_ARG, "QC_OPT_SCAN_COST: 0..1024");
             H->opt_scan_cost = static_cast<int>(value);
             return QC_OK;
+        case QC_OPT_BETA_COST:
+            if (value < -1 || value > 1024) return fail(H, QC_ERR_ARG, "QC_OPT_BETA_COST: -1..1024");
+            H->opt_beta_cost = static_cast<int>(value);
+            return QC_OK;
         case QC_OPT_COUNT_WORK: H->opt_count_work = value ? 1 : 0; return QC_OK;
         case QC_OPT_ALPHA_SLOTS:
             if (value < 0 || value > 4096) return fail(H, QC_ERR_ARG, "QC_OPT_ALPHA_SLOTS: 0..4096");
@@ -656,6 +660,7 @@ qc_status qc_eloc_eval(qc_eloc* H, const uint64_t* samples, const int64_t* count
         tp.jlen = jlen;
         tp.gent = gent;
         tp.scan_cost = H->opt_scan_cost ? H->opt_scan_cost : qc::kDefaultScanCost;
+        tp.beta_cost = qc::beta_cost_of(H->opt_beta_cost);
         tp.alpha_cap = cfg.acap;
     }
     if (H->opt_timing) QC_CHK(cudaEventRecord(H->ev[1], s), "cudaEventRecord");
@@ -742,7 +747,8 @@ qc_status qc_eloc_work(qc_eloc* H, uint64_t* work, int n_fields) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(H->work_stream);
     if (e != cudaSuccess) return cuda_fail(H, e, "work counters copy");
     const unsigned long long v[QC_WORK_FIELDS] = {w.samples, w.scan_rows, w.tests, w.probes, w.hits_single,
-                                                  w.hits_same, w.hits_ab, w.ctas, w.hits_scanned};
+                                                  w.hits_same, w.hits_ab, w.ctas, w.hits_scanned,
+                                                  w.beta_looked, w.beta_groups};
     for (int i = 0; i < n_fields && i < QC_WORK_FIELDS; ++i) work[i] = v[i];
     return QC_OK;
 }

@@ -316,6 +316,7 @@ qc_status prepare(qc_batch* B) {
             P.tp.jlen = reinterpret_cast<const unsigned*>(A + B->ja_len) + slot_base[m];
             P.tp.gent = reinterpret_cast<const ulonglong2*>(B->d_join + B->jo_ent);
             P.tp.scan_cost = H->opt_scan_cost ? H->opt_scan_cost : qc::kDefaultScanCost;
+            P.tp.beta_cost = qc::beta_cost_of(H->opt_beta_cost);
             P.tp.alpha_cap = acap[m];
         }
         P.ep = qc::EvalParams{};

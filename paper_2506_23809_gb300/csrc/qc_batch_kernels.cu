@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(MAXT) eloc_batch_kernel(const __grid_constant_
                     // a joining molecule's alpha list may be capped (mp.tp.alpha_cap): segments.
                     // One copy of the sample code takes either list layout (ep.lean), so the
                     // kernel holds it once
-                    run_sample<PREC, U, true, 2, JOIN, false, JOIN>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c,
+                    run_sample<PREC, U, true, 2, JOIN, false, JOIN, JOIN>(mp.sp, mp.tp, mp.ep, s, lane, smem, wl, filt, c,
                                                                      static_cast<int>(C));
                 }
             }

@@ -513,16 +513,22 @@ __device__ __forceinline__ void list_hits(const EvalParams& ep, long long s, lon
 }
 
 // Sample-space join.  Kinds of scanned groups (low bits of a scan descriptor's kind; an
-// alpha' group also carries its excitation ki << 8 | ka << 16), and the classes of the hits
-// it finds: their codes pack four spatial orbitals, 6 bits each.
+// alpha' or beta' group also carries its excitation ki << 8 | ka << 16, a beta' group in bit 2
+// whether x's beta single is taken from it), and the classes of the hits it finds: their codes
+// pack four spatial orbitals, 6 bits each.  Odd kinds scan beta strings against x's, even ones
+// alpha strings.
+constexpr unsigned kScanBetaP = 0u;   // rows of a beta' = single excitation of x's beta string
 constexpr unsigned kScanAlpha = 1u;   // rows sharing x's alpha string (beta strings scanned)
 constexpr unsigned kScanBeta = 2u;    // rows sharing x's beta string (alpha strings scanned)
 constexpr unsigned kScanAlphaP = 3u;  // rows of an alpha' = single excitation of x's alpha string
 constexpr unsigned kCodeSingleA = 5u, kCodeSingleB = 6u, kCodeDoubleAA = 7u, kCodeDoubleBB = 8u,
                    kCodeDoubleAB = 9u;
+// beta' groups are scanned only for samples with at least this many long alpha' groups
+constexpr int kMinLongAlpha = 8;
 
 // Code of a scanned hit: d is the popcount of the scanned string against x's, emptied and
-// filled its bits set only in x's string and only in the row's.
+// filled its bits set only in x's string and only in the row's (BETA: beta' groups exist).
+template <bool BETA>
 __device__ __forceinline__ unsigned scan_code(unsigned kind, int d, unsigned long long emptied,
                                               unsigned long long filled) {
     // the highest bits; at d == 2 the strings differ in one orbital each way, so these are
@@ -533,6 +539,11 @@ __device__ __forceinline__ unsigned scan_code(unsigned kind, int d, unsigned lon
         const unsigned ki = (kind >> 8) & 63u, ka = (kind >> 16) & 63u;
         if (d == 0) return (kCodeSingleA << 24) | ki | (ka << 6);
         return (kCodeDoubleAB << 24) | ki | (ka << 6) | (e1 << 12) | (f1 << 18);
+    }
+    if (BETA && (kind & 3u) == kScanBetaP) {  // the beta orbitals in the kind, the alpha ones scanned
+        const unsigned kj = (kind >> 8) & 63u, kb = (kind >> 16) & 63u;
+        if (d == 0) return (kCodeSingleB << 24) | kj | (kb << 6);
+        return (kCodeDoubleAB << 24) | e1 | (f1 << 6) | (kj << 12) | (kb << 18);
     }
     if (d == 2) return (kCodeSingleB << 24) | e1 | (f1 << 6);  // x's alpha group only
     const unsigned e0 = static_cast<unsigned>(__ffsll(emptied) - 1) & 63u;
@@ -952,7 +963,8 @@ struct WarpSample {
     unsigned long long as, bs, hxa;  // join: x's alpha and beta spatial strings, alpha part of hx
     unsigned a_next;          // join: first alpha single not yet in an alpha-list segment
     unsigned a_seen;          // join: alpha singles below this were classified (short groups scanned)
-    unsigned long long pad;
+    unsigned athr;            // join, segments: an alpha' group is long when its len exceeds this
+    unsigned pad;
 };
 constexpr size_t kOffWarpSample = 288;
 // per warp: occupation lists (4 x 64 B), reference masks (32 B), the sample's constants
@@ -982,11 +994,17 @@ __host__ __device__ inline size_t main_warp_bytes(const SysParams& sp, bool filt
 // them out: the checks alone cost the timed kernel a third of its speed).  SEG: the join's
 // alpha list may have fewer slots than alpha singles (tp.alpha_cap) and is then enumerated in
 // segments (false compiles the segments out: 2% of the kernel's time when no list is capped).
-template <int PREC, int U, bool FILTER, int LEAN, bool JOIN = true, bool DIAG = false, bool SEG = false>
+// BETA: the join's beta' phase (with SEG only, and run only when the alpha list is capped, as
+// in the single-molecule kernel with segments; false compiles it out: compiled into the kernel
+// without segments, it made that kernel 5% slower at 52 spin orbitals with the phase switched
+// off, more than the phase saved there with it on).
+template <int PREC, int U, bool FILTER, int LEAN, bool JOIN = true, bool DIAG = false, bool SEG = false,
+          bool BETA = false>
 __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParams& tp,
                                            const EvalParams& ep, long long s, int lane,
                                            unsigned char* smem, unsigned char* wl,
                                            const uint32_t* filt, int c = 0, int C = 1) {
+    static_assert(!BETA || (JOIN && SEG), "the beta' phase runs in the join kernels with segments");
     const unsigned long long* T64 = reinterpret_cast<const unsigned long long*>(smem + kOffT);
     const unsigned short* lut = reinterpret_cast<const unsigned short*>(smem + kOffLut);
     uint32_t* q = reinterpret_cast<uint32_t*>(wl + kOccBytes);
@@ -1049,7 +1067,8 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
         w.hxa = hxa;
         w.a_next = 0u;
         w.a_seen = 0u;
-        w.pad = 0ULL;
+        w.athr = 0u;
+        w.pad = 0u;
         *wsp = w;
     }
     __syncwarp();
@@ -1119,7 +1138,15 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
     // the next alpha single excitation to classify in q[103] (shared memory keeps the scan state
     // out of the registers of the enumeration loop).  When the alpha list is full, the
     // enumeration runs over that segment and the scan state is entered again for the remaining
-    // alpha singles (classes 0 and 4 only).
+    // alpha singles (classes 0 and 4 only).  In the kernels with the beta' phase (BETA), after
+    // the first segment's last alpha' chunk, a
+    // sample with at least kMinLongAlpha long alpha' groups in it classifies its beta' (the
+    // prefiltered beta singles, q[101] the next one, q[100] those kept): a beta' group short
+    // against the number of those groups is scanned for the rows of long alpha' groups (alpha-
+    // beta doubles, told by the row's alpha-group size in its entry against the sample's alpha'
+    // threshold, which stays that of the full beta list; and x's beta single when class 1 is
+    // enumerated) and leaves the beta list, which classes 1 and 4 of every segment then
+    // enumerate compacted.
     auto store_chunk = [&](unsigned gst, unsigned gln, unsigned kind) {
         unsigned inc = gln;
 #pragma unroll
@@ -1200,7 +1227,16 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
             }
             enumA = __shfl_sync(QC_FULLMASK, en, 0);
             enumB = __shfl_sync(QC_FULLMASK, en, 1);
-            if (lane == 0) q[103] = 0u;
+            if (lane == 0) {
+                q[103] = 0u;
+                if (BETA) {
+                    q[100] = 0u;  // beta' phase: entries kept in the beta single list
+                    q[101] = 0u;  // beta' phase: next entry to classify
+                    // len * scan_cost > 4 (nsb2 + 1), as len > floor(4 (nsb2 + 1) / scan_cost), by
+                    // the beta list before the beta' phase
+                    wsp->athr = 4u * static_cast<unsigned>(nsb2 + 1) / static_cast<unsigned>(tp.scan_cost);
+                }
+            }
             store_chunk(gst, c == 0 ? gln : 0u, kind);  // later chunks classify but scan nothing
             nsa2 = 0;  // the alpha' groups are classified in the scan state
         } else {
@@ -1275,6 +1311,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
 #pragma unroll
     for (int k = 0; k < U; ++k) hu[k] = 0u;
     bool scanning = join;
+    bool bph = false;     // join: the beta' phase of the scan state is due
     bool seg2 = false;    // join: a later segment of the alpha list (classes 0 and 4 only)
     unsigned sbase = 0u;  // next row of the current scan chunk
     while (true) {
@@ -1293,6 +1330,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 // batches do not mix the two element paths.
                 const unsigned offj = q[32 + lane];  // group lane's first row in the chunk
                 const unsigned long long ras = wsp->as, rbs = wsp->bs;
+                const unsigned lthr = BETA ? wsp->athr : 0u;
                 const unsigned lemask = ltmask | (1u << lane);
                 do {
                     const unsigned v = sbase + lane;
@@ -1305,13 +1343,23 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                         const unsigned kd = q[64 + g];
                         const ulonglong2 e = __ldg(tp.gent + QC_IX(q[g] + (v - q[32 + g]), 2 * tp.n, tp.err));
                         const unsigned kk = kd & 3u;
-                        const unsigned long long ref = kk == kScanBeta ? ras : rbs;
+                        const unsigned long long ref = (BETA ? (kk & 1u) == 0u : kk == kScanBeta) ? ras : rbs;
                         const unsigned long long dm = e.x ^ ref;
                         const int d = __popcll(dm);
-                        sgl = kk == kScanAlpha ? d == 2 : (kk == kScanAlphaP && d == 0);
-                        dbl = kk == kScanAlphaP ? d == 2 : d == 4;
+                        if (BETA) {
+                            // an alpha' or beta' group: its single at d == 0, alpha-beta doubles
+                            // at d == 2 (a beta' group's only where the row's alpha' group is long)
+                            const bool prime = kk == kScanAlphaP || kk == kScanBetaP;
+                            sgl = prime ? d == 0 && (kd & (kk == kScanAlphaP ? 3u : 4u)) != 0u
+                                        : (kk == kScanAlpha && d == 2);
+                            dbl = prime ? d == 2 && (kk == kScanAlphaP || static_cast<unsigned>(e.y >> 32) > lthr)
+                                        : d == 4;
+                        } else {
+                            sgl = kk == kScanAlpha ? d == 2 : (kk == kScanAlphaP && d == 0);
+                            dbl = kk == kScanAlphaP ? d == 2 : d == 4;
+                        }
                         if (sgl || dbl) {
-                            code = scan_code(kd, d, dm & ref, dm & e.x);
+                            code = scan_code<BETA>(kd, d, dm & ref, dm & e.x);
                             row = static_cast<unsigned>(e.y);
                         }
                     }
@@ -1346,7 +1394,7 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                         len = __ldg(tp.jlen + QC_IX(sl, tp.set_mask + 1LL, tp.err));
                         start = __ldg(tp.jstart + QC_IX(sl, tp.set_mask + 1LL, tp.err));
                     }
-                    lng = static_cast<long long>(len) * tp.scan_cost > 4LL * (nsb2 + 1);
+                    lng = BETA ? len > wsp->athr : static_cast<long long>(len) * tp.scan_cost > 4LL * (nsb2 + 1);
                     kd = kScanAlphaP | (static_cast<unsigned>(ki) << 8) | (static_cast<unsigned>(ka) << 16);
                 }
                 // a long group joins the alpha list while it has room; the first that does not
@@ -1363,8 +1411,13 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                     gln = len;
                 }
                 nsa2 = SEG ? min(nA, nsa2 + __popc(m)) : nsa2 + __popc(m);
+                // after the first segment's last chunk: the beta' phase (judged by the long alpha'
+                // groups of that segment when the list is full; the later segments enumerate the
+                // same compacted beta list)
+                bool whole = st0 + 32 >= sp.nsa;
                 if (SEG) {
                     const unsigned md = __ballot_sync(QC_FULLMASK, lng && !keep);
+                    whole = (whole || md != 0u) && !seg2;
                     __syncwarp();
                     if (lane == 0) {
                         const int end = min(st0 + 32, sp.nsa);
@@ -1375,6 +1428,59 @@ __device__ __forceinline__ void run_sample(const SysParams& sp, const TableParam
                 } else {
                     __syncwarp();
                     if (lane == 0) q[103] = static_cast<unsigned>(st0 + 32);
+                }
+                bph = BETA && whole && tp.alpha_cap > 0 && tp.beta_cost > 0 && nsa2 >= kMinLongAlpha && nsb2 > 0;
+                store_chunk(gst, c == 0 ? gln : 0u, kd);
+                sbase = 0u;
+            } else if (BETA && bph) {
+                // the next 32 beta' of the beta single list: a group with len beta_cost <= 4
+                // (long alpha' groups) becomes a scan descriptor, the others stay in the list
+                // (compacted in place: every entry of the chunk is read before any is written)
+                const int tb = static_cast<int>(q[101]);
+                const int kept0 = static_cast<int>(q[100]);
+                const int t = tb + lane;
+                bool keep = false;
+                uint32_t hv32 = 0u;
+                unsigned short pk = 0;
+                unsigned gst = 0u, gln = 0u, kd = 0u;
+                if (t < nsb2) {
+                    hv32 = H[QC_IX(oSB + t, nH, sp.err)];
+                    pk = IB[QC_IX(t, sp.nsb, sp.err)];
+                    const unsigned kj = pk & 255u, kb = static_cast<unsigned>(pk) >> 8;
+                    const unsigned long long tm = T64[2 * kj + 1] ^ T64[2 * kb + 1];
+                    const unsigned sl = set_slot(tp.bset, tp.set_mask, wsp->bs ^ (1ULL << kj) ^ (1ULL << kb),
+                                                 wsp->hx ^ wsp->hxa ^ tm);
+                    const long long jo = static_cast<long long>(tp.set_mask) + 1LL + sl;
+                    const unsigned len =
+                        sl != kNoSlot ? __ldg(tp.jlen + QC_IX(jo, 2LL * (tp.set_mask + 1LL), tp.err)) : 0u;
+                    keep = !(len > 0u && static_cast<long long>(len) * tp.beta_cost <= 4LL * nsa2);
+                    if (!keep) {
+                        gst = __ldg(tp.jstart + QC_IX(jo, 2LL * (tp.set_mask + 1LL), tp.err));
+                        gln = len;
+                        // bit 2: x's beta single is taken from the group (class 1 is enumerated)
+                        kd = kScanBetaP | (enumA ? 4u : 0u) | (kj << 8) | (kb << 16);
+                    }
+                }
+                const unsigned m = __ballot_sync(QC_FULLMASK, keep);
+                if (DIAG && ep.work != nullptr && lane == 0 && c == 0) {
+                    const int nv = min(32, nsb2 - tb);
+                    atomicAdd(&ep.work->beta_looked, static_cast<unsigned long long>(nv));
+                    atomicAdd(&ep.work->beta_groups, static_cast<unsigned long long>(nv - __popc(m)));
+                }
+                __syncwarp();
+                if (keep) {
+                    const int pos = kept0 + __popc(m & ltmask);
+                    H[QC_IX(oSB + pos, nH, sp.err)] = hv32;
+                    IB[QC_IX(pos, sp.nsb, sp.err)] = pk;
+                }
+                const int kept = kept0 + __popc(m);
+                if (lane == 0) {
+                    q[100] = static_cast<unsigned>(kept);
+                    q[101] = static_cast<unsigned>(tb + 32);
+                }
+                if (tb + 32 >= nsb2) {
+                    bph = false;
+                    nsb2 = kept;
                 }
                 store_chunk(gst, c == 0 ? gln : 0u, kd);
                 sbase = 0u;

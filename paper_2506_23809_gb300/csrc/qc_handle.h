@@ -50,6 +50,7 @@ struct qc_eloc {
     int opt_lean = 0;  // 0 auto, 1 stored pair lists, 2 formed on the fly
     int opt_join = 0;  // 0 auto, 1 off, 2 on (sample-space mode, filtered kernel)
     int opt_scan_cost = 0;  // 0 default, else 4 x the cost of a scanned row in enumerated pairs
+    int opt_beta_cost = 0;  // QC_OPT_BETA_COST: 0 default, -1 never, else its factor
     int opt_count_work = 0;  // QC_OPT_COUNT_WORK
     int opt_wait_limit = 0;  // QC_OPT_WAIT_LIMIT + 1 (0: the kernel's default)
     int opt_alpha_slots = 0;  // QC_OPT_ALPHA_SLOTS (0: auto)

@@ -69,6 +69,7 @@ struct TableParams {
     const unsigned* jlen;
     const ulonglong2* gent;
     int scan_cost;  // a group is scanned when len * scan_cost <= 4 * (pairs it replaces)
+    int beta_cost;  // a beta' group is scanned when len * beta_cost <= 4 * (long alpha' groups); 0 never
     int alpha_cap;  // join: slots of the per-warp alpha single list (0: all alpha singles)
     unsigned* err;  // QC_CHECKED builds: flags word a failed bounds check sets (QC_FLAG_BOUNDS)
 };
@@ -100,6 +101,8 @@ struct WorkCounters {
     unsigned long long hits_ab;      //   opposite-spin doubles
     unsigned long long ctas;         // CTAs that copied the filter into shared memory
     unsigned long long hits_scanned; // hits found by the join's scans (any kind; exact, no key load)
+    unsigned long long beta_looked;  // join: beta' looked up in the beta set for the beta' phase
+    unsigned long long beta_groups;  // join: beta' groups the beta' phase scans
 };
 
 struct EvalParams {
@@ -144,6 +147,11 @@ constexpr long long kDefaultChunkPairs = 0;
 // Sample-space join: a group of table rows is scanned when len * kDefaultScanCost / 4 is at
 // most the number of excitations that scanning it replaces.
 constexpr int kDefaultScanCost = 4;
+// The join's beta' phase: a beta' group is scanned for the rows of long alpha' groups when
+// len * kDefaultBetaCost / 4 is at most their number (a scanned row costs about twice a
+// filter test and its share of false-positive probes).
+constexpr int kDefaultBetaCost = 8;
+inline int beta_cost_of(int opt) { return opt == 0 ? kDefaultBetaCost : opt < 0 ? 0 : opt; }
 constexpr long long kJoinMinRows = 16384;  // the join's default: tables from this many rows, or
 // from kJoinMinPairRows table rows x connected pairs per sample, or from kJoinBigRows rows when
 // a sample has at least kJoinBigPairs connected pairs (measured break-even: about 2e8 pair-rows

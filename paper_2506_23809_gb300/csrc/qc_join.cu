@@ -22,9 +22,14 @@
 //              order of a group -- and with it the order of accumulation -- is the same on
 //              every run
 //   J3 gather: each entry's row and the row's string of the other spin (16 bytes, so one
-//              load brings the kernel both)
+//              load brings the kernel both); the alpha entries leave each row's alpha-group
+//              size in a per-row array
+//   J4 mark:   each beta entry's row word gets the row's alpha-group size in its high 32
+//              bits (the kernel's scan of a beta' group keeps the rows of long alpha' groups
+//              by it, without a lookup)
 // Traffic per row: 8 B read (hist) + 8 B read + 8 B written (scatter) per pass and key half,
-// then 16 B read, 16 B written; a few tens of microseconds at 10^5 rows.
+// then 16 B read, 16 B written (gather) and 12 B read, 8 B written (mark); a few tens of
+// microseconds at 10^5 rows.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,7 +49,7 @@ constexpr int kJBins = 1 << kJBits;
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct JLayout {
-    size_t key1, val0, val1, table, sums, total;
+    size_t key1, val0, val1, table, sums, alen, total;
 };
 
 // sort space for m items and n_slots group sizes
@@ -60,6 +65,7 @@ JLayout jlayout(long long m, unsigned long long n_slots) {
     L.val1 = off; off = align256(off + static_cast<size_t>(m) * 4);
     L.table = off; off = align256(off + static_cast<size_t>(table_n) * 4);
     L.sums = off; off = align256(off + static_cast<size_t>(scan_n / 4096 + 2) * 4 + 4096);
+    L.alen = off; off = align256(off + static_cast<size_t>(m / 2 + 1) * 4);
     L.total = off;
     return L;
 }
@@ -131,13 +137,14 @@ __global__ void __launch_bounds__(32 * kJWarps) join_scatter_kernel(const unsign
     }
 }
 
-// (with pa: each row's own alpha- and beta-group sizes into pa / pb, for the sample order)
+// (alen: each row's alpha-group size, from its alpha entry; with pa: each row's own alpha-
+// and beta-group sizes into pa / pb, for the sample order)
 __global__ void __launch_bounds__(256) join_gather_kernel(const ulonglong2* __restrict__ keys,
                                                           const unsigned* __restrict__ skey,
                                                           const unsigned* __restrict__ srow, long long m,
                                                           unsigned set_size, ulonglong2* __restrict__ gent,
-                                                          const unsigned* __restrict__ jlen, unsigned* pa,
-                                                          unsigned* pb) {
+                                                          const unsigned* __restrict__ jlen, unsigned* __restrict__ alen,
+                                                          unsigned* pa, unsigned* pb) {
     for (long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < m;
          p += static_cast<long long>(gridDim.x) * blockDim.x) {
         const unsigned k = skey[p];
@@ -145,8 +152,33 @@ __global__ void __launch_bounds__(256) join_gather_kernel(const ulonglong2* __re
         const unsigned row = srow[p];
         // alpha groups list beta strings and the other way round
         gent[p] = make_ulonglong2(qc::spin_string(keys[row], k < set_size ? 1 : 0), row);
+        if (k < set_size) alen[row] = jlen[k];
         if (pa != nullptr) (k < set_size ? pa : pb)[row] = jlen[k];
     }
+}
+
+// J4: the beta entries' row words get the row's alpha-group size in their high half.
+__global__ void __launch_bounds__(256) join_mark_kernel(const unsigned* __restrict__ skey,
+                                                        const unsigned* __restrict__ srow, long long m,
+                                                        unsigned set_size, ulonglong2* __restrict__ gent,
+                                                        const unsigned* __restrict__ alen) {
+    for (long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < m;
+         p += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const unsigned k = skey[p];
+        if (k < set_size || k >= 2u * set_size) continue;
+        const unsigned row = srow[p];
+        gent[p].y = static_cast<unsigned long long>(row) | (static_cast<unsigned long long>(alen[row]) << 32);
+    }
+}
+
+// The molecule of a batch's sorted slot key k: the largest one with slot_base <= k.
+__device__ __forceinline__ int batch_molecule(const unsigned* __restrict__ slot_base, int n_mol, unsigned k) {
+    int lo = 0, hi = n_mol;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (slot_base[mid] <= k) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
 // A batch's entries: the molecule from the sorted key (slot_base: each molecule's first slot
@@ -157,22 +189,42 @@ __global__ void __launch_bounds__(256) join_gather_batch_kernel(const qc::MolPar
                                                                 const unsigned* __restrict__ srow, long long m,
                                                                 ulonglong2* __restrict__ gent,
                                                                 const unsigned* __restrict__ row_base,
-                                                                const unsigned* __restrict__ jlen, unsigned* pa,
+                                                                const unsigned* __restrict__ jlen,
+                                                                unsigned* __restrict__ alen, unsigned* pa,
                                                                 unsigned* pb) {
     const unsigned sentinel = slot_base[n_mol];
     for (long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < m;
          p += static_cast<long long>(gridDim.x) * blockDim.x) {
         const unsigned k = skey[p];
         if (k >= sentinel) continue;
-        int lo = 0, hi = n_mol;  // largest molecule with slot_base <= k
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (slot_base[mid] <= k) lo = mid; else hi = mid;
-        }
+        const int lo = batch_molecule(slot_base, n_mol, k);
         const unsigned size = (slot_base[lo + 1] - slot_base[lo]) / 2u;
         const unsigned row = srow[p];
-        gent[p] = make_ulonglong2(qc::spin_string(mols[lo].tp.keys[row], k - slot_base[lo] < size ? 1 : 0), row);
-        if (pa != nullptr) (k - slot_base[lo] < size ? pa : pb)[row_base[lo] + row] = jlen[k];
+        const bool alpha = k - slot_base[lo] < size;
+        gent[p] = make_ulonglong2(qc::spin_string(mols[lo].tp.keys[row], alpha ? 1 : 0), row);
+        if (alpha) alen[row_base[lo] + row] = jlen[k];
+        if (pa != nullptr) (alpha ? pa : pb)[row_base[lo] + row] = jlen[k];
+    }
+}
+
+// J4 of a batch: the beta entries' row words get the row's alpha-group size.
+__global__ void __launch_bounds__(256) join_mark_batch_kernel(const unsigned* __restrict__ slot_base, int n_mol,
+                                                              const unsigned* __restrict__ skey,
+                                                              const unsigned* __restrict__ srow, long long m,
+                                                              ulonglong2* __restrict__ gent,
+                                                              const unsigned* __restrict__ row_base,
+                                                              const unsigned* __restrict__ alen) {
+    const unsigned sentinel = slot_base[n_mol];
+    for (long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < m;
+         p += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const unsigned k = skey[p];
+        if (k >= sentinel) continue;
+        const int lo = batch_molecule(slot_base, n_mol, k);
+        const unsigned size = (slot_base[lo + 1] - slot_base[lo]) / 2u;
+        if (k - slot_base[lo] < size) continue;
+        const unsigned row = srow[p];
+        gent[p].y = static_cast<unsigned long long>(row) |
+                    (static_cast<unsigned long long>(alen[row_base[lo] + row]) << 32);
     }
 }
 
@@ -322,9 +374,14 @@ cudaError_t qc::launch_join_index(const TableParams& tp, unsigned set_size, void
     const unsigned* sval = nullptr;
     cudaError_t e = join_sort(jkey, nullptr, tp.n, m, 2ULL * set_size, jlen, jstart, ws, &skey, &sval, s);
     const unsigned gblocks = static_cast<unsigned>(std::min<long long>((m + 255) / 256, 8192));
+    unsigned* alen = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(ws) + jlayout(m, 2ULL * set_size).alen);
     if (e == cudaSuccess) {
-        join_gather_kernel<<<gblocks, 256, 0, s>>>(tp.keys, skey, sval, m, set_size, gent, jlen,
+        join_gather_kernel<<<gblocks, 256, 0, s>>>(tp.keys, skey, sval, m, set_size, gent, jlen, alen,
                                                    order != nullptr && samples == nullptr ? pa : nullptr, pb);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        join_mark_kernel<<<gblocks, 256, 0, s>>>(skey, sval, m, set_size, gent, alen);
         e = cudaGetLastError();
     }
     // the samples to order: the table's rows, or a caller's samples (their groups looked up)
@@ -371,9 +428,14 @@ cudaError_t qc::launch_join_batch(const MolParams* mols, const unsigned* slot_ba
     const unsigned* sval = nullptr;
     cudaError_t e = join_sort(jkey, jval, 0, m, n_slots, jlen, jstart, ws, &skey, &sval, s);
     const unsigned gblocks = static_cast<unsigned>(std::min<long long>((m + 255) / 256, 8192));
+    unsigned* alen = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(ws) + jlayout(m, n_slots).alen);
     if (e == cudaSuccess) {
         join_gather_batch_kernel<<<gblocks, 256, 0, s>>>(mols, slot_base, n_mol, skey, sval, m, gent, row_base, jlen,
-                                                         order ? pa : nullptr, pb);
+                                                         alen, order ? pa : nullptr, pb);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        join_mark_batch_kernel<<<gblocks, 256, 0, s>>>(slot_base, n_mol, skey, sval, m, gent, row_base, alen);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && order != nullptr) {

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(32 * kFilteredMaxWarps) eloc_main_kernel(const
         // heavy samples first when the host gave an order: the launch then ends on light ones
         const unsigned long long s =
             ep.order != nullptr ? static_cast<unsigned long long>(__ldg(ep.order + QC_IX(q, ep.n_u, sp.err))) : q;
-        run_sample<PREC, U, FILTER, LEAN, JOIN, DIAG, SEG>(sp, tp, ep, static_cast<long long>(s), lane, smem, wl, filt,
+        run_sample<PREC, U, FILTER, LEAN, JOIN, DIAG, SEG, SEG>(sp, tp, ep, static_cast<long long>(s), lane, smem, wl, filt,
                                                 static_cast<int>(it - q * C), static_cast<int>(C));
     }
 }

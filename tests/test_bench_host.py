@@ -58,10 +58,11 @@ def test_work_l2_bytes_formula():
     v = 19, 2 o v = 266 spin-string lookups per sample; FP64 elements)."""
     b = _bench()
     zero = dict(samples=0, scan_rows=0, tests=0, probes=0, hits_single=0, hits_same=0, hits_ab=0, ctas=0,
-                hits_scanned=0)
+                hits_scanned=0, beta_looked=0, beta_groups=0)
     assert b.work_l2_bytes(zero, 14, 52, 8, 14) == 0
     cases = [("scan_rows", 16), ("probes", 16), ("hits_single", 32 + 8 * 22), ("hits_same", 48), ("hits_ab", 40),
-             ("samples", 48 + 8 * 266), ("ctas", 4 << 14), ("tests", 0), ("hits_scanned", -16)]
+             ("samples", 48 + 8 * 266), ("ctas", 4 << 14), ("tests", 0), ("hits_scanned", -16),
+             ("beta_looked", 8), ("beta_groups", 0)]
     for k, per in cases:
         w = dict(zero)
         w[k] = 3

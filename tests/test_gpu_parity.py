@@ -443,6 +443,52 @@ def test_full_size_n52_sampled(B, orc):
     assert abs(sm["energy"] - m) <= 1e-12 * abs(m) and abs(sm["var"] - var) <= 1e-10 * var
 
 
+def test_beta_phase_same_set_n52(B, orc):
+    """The join's beta' phase (for a sample with many alpha' groups too long to scan, a beta'
+    group is scanned for the rows of those groups instead of enumerating the beta' against
+    each of them; in the launches with a capped alpha list, here 132 of the 133 slots) finds
+    the same connected set: at the N=52 workload every sample's hit list with the phase
+    equals its list without it, pair by pair, 256 sampled rows equal the oracle's, and E_loc
+    agrees to rounding (only the order of accumulation differs)."""
+    ints, s = I.make_workload("n52_e14_u100k")
+    seg = {B.QC_OPT_ALPHA_SLOTS: 7 * 19 - 1}
+    on = run_gpu(B, ints, 52, 14, s.keys, s.counts, s.psi, lists=True, diag=False, opts=seg)
+    off = run_gpu(B, ints, 52, 14, s.keys, s.counts, s.psi, lists=True, diag=False,
+                  opts={**seg, B.QC_OPT_BETA_COST: -1})
+    rows = np.sort(np.random.default_rng(52).choice(s.n_u, 256, replace=False))
+    assert_lists_equal(on, orc.hit_lists(ints.h, ints.eri, 0.0, 52, s.keys[rows], s.psi[rows], s.keys, s.psi), rows)
+    assert on["cfg"] == off["cfg"] and on["cfg"]["kernel"] in (4, 5)
+    assert np.array_equal(on["list_off"], off["list_off"]), "hit counts differ"
+    assert np.array_equal(on["list"], off["list"]), "hit lists differ"
+    err = np.abs(on["eloc"] - off["eloc"]) / np.maximum(1.0, np.abs(off["eloc"]))
+    assert err.max() <= 1e-12, f"max rel difference {err.max():.3e}"
+
+
+@pytest.mark.parametrize("prec,slots", [(0, 132), (1, 132), (0, 8), (1, 8)])
+def test_beta_phase_forced(B, orc, prec, slots):
+    """The beta' phase on most samples of a 20,000-row N=52 table (join on, groups judged long
+    at a quarter of the default length, every beta' group of up to 4 x the long alpha' groups
+    scanned; 132 alpha slots, or 8, where the phase follows the first of several alpha-list
+    segments): the hit
+    lists of all rows equal those of the filtered enumeration without the join, and 300
+    sampled rows equal the oracle's."""
+    K = 26
+    ints = I.make_integrals(K, 52, 5401)
+    keys = I.rank_weighted_samples(K, 7, 7, 20000, seed=5402)
+    counts = I.zipf_counts(20000, 200_000, 5403)
+    psi = I.lognormal_psi(20000, 5404)
+    forced = {B.QC_OPT_JOIN: 2, B.QC_OPT_SCAN_COST: 16, B.QC_OPT_BETA_COST: 1, B.QC_OPT_ALPHA_SLOTS: slots}
+    a = run_gpu(B, ints, 52, 14, keys, counts, psi, prec=prec, lists=True, diag=False, opts=forced)
+    b = run_gpu(B, ints, 52, 14, keys, counts, psi, prec=prec, lists=True, diag=False, opts={B.QC_OPT_JOIN: 1})
+    assert a["cfg"]["kernel"] in (4, 5) and b["cfg"]["kernel"] in (2, 3)
+    assert np.array_equal(a["list_off"], b["list_off"]) and np.array_equal(a["list"], b["list"])
+    rows = np.sort(np.random.default_rng(54).choice(20000, 300, replace=False))
+    assert_lists_equal(a, orc.hit_lists(ints.h, ints.eri, 0.0, 52, keys[rows], psi[rows], keys, psi), rows)
+    if prec == 0:
+        want = orc.eloc(ints.h, ints.eri, 0.0, 52, keys[rows], psi[rows], keys, psi)
+        assert_eloc_close(a["eloc"][rows], want)
+
+
 def test_precision_form_n76(B, orc):
     """FP32 integrals and FP32 x FP32 terms with TwoSum accumulation; diagonal and the
     reduction in FP64.  N=76, 20 electrons, 4,000 samples: error against the FP64 oracle

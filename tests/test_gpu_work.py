@@ -87,12 +87,65 @@ def test_work_counters(B, orc, opts, kind):
         assert w["scan_rows"] > 0 and w["tests"] < pairs
 
 
+def _spin_strings(keys, K, spin):
+    """Each key's alpha (spin 0) or beta (spin 1) string as a K-bit integer."""
+    out = np.zeros(len(keys), dtype=np.uint64)
+    for k in range(K):
+        b = 2 * k + spin
+        out |= ((keys[:, b // 64] >> np.uint64(b % 64)) & np.uint64(1)) << np.uint64(k)
+    return out
+
+
+def _single_strings(S, K, o):
+    """All o (K - o) single excitations of each K-bit string with o bits set."""
+    occ = np.stack([((S >> np.uint64(k)) & np.uint64(1)) == 1 for k in range(K)], axis=1)
+    oi = np.argsort(~occ, axis=1, kind="stable")[:, :o].astype(np.uint64)
+    vi = np.argsort(occ, axis=1, kind="stable")[:, :K - o].astype(np.uint64)
+    one = np.uint64(1)
+    return np.stack([S ^ (one << oi[:, i]) ^ (one << vi[:, a]) for i in range(o) for a in range(K - o)], axis=1)
+
+
+def _beta_phase_counts(keys, K, o, cap, scan_cost=4, beta_cost=8, min_long=8):
+    """(beta' looked up, beta' groups scanned) by the join's beta' phase over all samples of
+    an own table, from the group sizes: a sample's alpha' group is long when len x scan_cost
+    > 4 (beta' in the table + 1); with at least min_long long ones in the first segment of
+    the alpha list (cap slots), each of its beta' is looked up and its group scanned when
+    len x beta_cost <= 4 (long alpha' groups in that segment)."""
+    def group_len(X, u, c):
+        p = np.minimum(np.searchsorted(u, X), len(u) - 1)
+        return np.where(u[p] == X, c[p], 0)
+    A, Bs = _spin_strings(keys, K, 0), _spin_strings(keys, K, 1)
+    (ua, ca), (ub, cb) = np.unique(A, return_counts=True), np.unique(Bs, return_counts=True)
+    looked = groups = 0
+    for lo in range(0, len(keys), 20000):
+        La = group_len(_single_strings(A[lo:lo + 20000], K, o), ua, ca)
+        Lb = group_len(_single_strings(Bs[lo:lo + 20000], K, o), ub, cb)
+        nb = (Lb > 0).sum(1)
+        nla = np.minimum((La * scan_cost > 4 * (nb + 1)[:, None]).sum(1), cap)
+        run = (nla >= min_long) & (nb > 0)
+        looked += int(nb[run].sum())
+        groups += int(((Lb > 0) & (Lb * beta_cost <= 4 * nla[:, None]))[run].sum())
+    return looked, groups
+
+
 def test_work_counters_full_size_n52(B):
-    """The benchmark workload's counts are deterministic (the same on every run) and the
-    hits add up to the summary's."""
+    """The benchmark workload's counts are deterministic (the same on every run) and the hits
+    add up to the summary's; its default launch (no alpha-list segments) has no beta'
+    phase, and with a capped alpha list (132 of 133 slots) the phase looks up and scans
+    exactly the beta' the group sizes call for (none with the phase off)."""
     ints, s = I.make_workload("n52_e14_u100k")
     w1, s1, _ = _run(B, ints, 52, 14, s, {})
     w2, _, _ = _run(B, ints, 52, 14, s, {})
     assert w1 == w2
     assert w1["hits_single"] + w1["hits_same"] + w1["hits_ab"] == s1["n_hits"]
     assert w1["samples"] == 100_000
+    assert w1["beta_looked"] == 0 and w1["beta_groups"] == 0
+    seg = {B.QC_OPT_ALPHA_SLOTS: 7 * 19 - 1}
+    w3, s3, _ = _run(B, ints, 52, 14, s, seg)
+    looked, groups = _beta_phase_counts(s.keys, 26, 7, cap=7 * 19 - 1)
+    assert 0 < groups < looked
+    assert (w3["beta_looked"], w3["beta_groups"]) == (looked, groups)
+    w4, s4, _ = _run(B, ints, 52, 14, s, {**seg, B.QC_OPT_BETA_COST: -1})
+    assert w4["beta_looked"] == 0 and w4["beta_groups"] == 0
+    assert s4["n_hits"] == s3["n_hits"] == s1["n_hits"]
+    assert w4["tests"] > w3["tests"] and w4["scan_rows"] < w3["scan_rows"]

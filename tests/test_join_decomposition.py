@@ -12,7 +12,16 @@ with the same electron count whose occupations differ in one or two electrons --
 sample sets with the structure of the benchmark's (rank-weighted, a few large groups) and
 uniform ones.  The CUDA kernels implement this decomposition; their connected sets are
 compared with the oracle's in the GPU parity tests.
+
+The kernels split the work further -- short groups scanned, the excitations into long ones
+enumerated, and (beta' phase) the groups of some beta' = single excitations of beta scanned
+for the rows of long alpha' groups instead of enumerating those beta' against them -- and the
+second test checks, at the level of sets, that every rule combination finds each connected
+row exactly once.
 """
+from collections import Counter
+from itertools import combinations
+
 import numpy as np
 import pytest
 
@@ -75,3 +84,85 @@ def test_join_groups_give_the_connected_set(K, na, nb, n, kind, seed):
     got = _join(A, Bs, K)
     assert got == want
     assert sum(len(s) for s in want) > 0
+
+
+def _split(A, Bs, K, o, scan_cost, beta_cost, min_long, cap):
+    """Each sample's rows as the kernels find them, as a multiset: the scan-or-enumerate rule
+    per group (rows x scan_cost / 4 against the excitations replaced), the alpha list capped
+    at cap slots (the beta' phase follows its first segment), and the beta' phase (with at
+    least min_long long alpha' in that segment, a beta' group is scanned when its rows x
+    beta_cost / 4 are at most their number, keeping rows whose alpha group is long and x's beta
+    single when class 1 is enumerated; the other beta' stay in the enumerated list).  Filter
+    and bucket probe stand as exact membership."""
+    ga, gb = {}, {}
+    for r, (a, b) in enumerate(zip(A, Bs)):
+        ga.setdefault(a, []).append(r)
+        gb.setdefault(b, []).append(r)
+    row_of = {(a, b): r for r, (a, b) in enumerate(zip(A, Bs))}
+
+    def singles(s):
+        occ = [k for k in range(K) if s >> k & 1]
+        vir = [k for k in range(K) if not s >> k & 1]
+        return [s ^ (1 << i) ^ (1 << v) for i in occ for v in vir]
+
+    def doubles(s):
+        occ = [k for k in range(K) if s >> k & 1]
+        vir = [k for k in range(K) if not s >> k & 1]
+        return [s ^ (1 << i) ^ (1 << j) ^ (1 << u) ^ (1 << v) for i, j in combinations(occ, 2)
+                for u, v in combinations(vir, 2)]
+
+    npairs = (o * (o - 1) // 2) * ((K - o) * (K - o - 1) // 2)
+    out = []
+    for a, b in zip(A, Bs):
+        found = Counter()
+        bp = [b1 for b1 in singles(b) if b1 in gb]            # the prefiltered beta list
+        la, lb = len(ga.get(a, [])), len(gb.get(b, []))
+        enum_a = la > 0 and la * scan_cost > 4 * (len(bp) + npairs)
+        enum_b = lb > 0 and lb * scan_cost > 4 * npairs
+        if la > 0 and not enum_a:                             # x's alpha group scanned
+            found.update(r for r in ga[a] if _pc(Bs[r] ^ b) in (2, 4))
+        if lb > 0 and not enum_b:                             # x's beta group scanned
+            found.update(r for r in gb[b] if _pc(A[r] ^ a) == 4)
+        athr = 4 * (len(bp) + 1)
+        long_a = []
+        for a1 in singles(a):                                 # alpha' groups
+            if a1 not in ga:
+                continue
+            if len(ga[a1]) * scan_cost > athr:
+                long_a.append(a1)
+            else:
+                found.update(r for r in ga[a1] if _pc(Bs[r] ^ b) in (0, 2))
+        first = min(len(long_a), cap)                         # long alpha' in the first segment
+        blist = bp
+        if beta_cost > 0 and first >= min_long and bp:        # the beta' phase
+            blist = []
+            for b1 in bp:
+                if len(gb[b1]) * beta_cost <= 4 * first:
+                    for r in gb[b1]:
+                        d = _pc(A[r] ^ a)
+                        if (d == 0 and enum_a) or (d == 2 and len(ga[A[r]]) * scan_cost > athr):
+                            found[r] += 1
+                else:
+                    blist.append(b1)
+        for a1 in long_a:                                     # class 0 and class 4
+            found.update(row_of[k] for k in [(a1, b)] + [(a1, b1) for b1 in blist] if k in row_of)
+        if enum_a:                                            # classes 1 and 3
+            found.update(row_of[k] for k in [(a, b1) for b1 in blist] + [(a, b2) for b2 in doubles(b)]
+                         if k in row_of)
+        if enum_b:                                            # class 2
+            found.update(row_of[k] for k in [(a2, b) for a2 in doubles(a)] if k in row_of)
+        out.append(found)
+    return out
+
+
+@pytest.mark.parametrize("scan_cost,beta_cost,min_long,cap", [(4, 8, 8, 10 ** 9), (16, 1, 8, 4), (64, 1, 2, 3),
+                                                              (64, 4, 1, 1), (4, 0, 8, 2), (1, 1, 1, 5)])
+def test_split_with_beta_phase_finds_each_pair_once(scan_cost, beta_cost, min_long, cap):
+    K, o = 10, 3
+    keys = I.rank_weighted_samples(K, o, o, 1200, seed=21)
+    A, Bs = _strings(keys, K)
+    want = _brute(A, Bs)
+    got = _split(A, Bs, K, o, scan_cost, beta_cost, min_long, cap)
+    for r, (g, w) in enumerate(zip(got, want)):
+        assert max(g.values(), default=1) == 1, f"sample {r}: a row found twice"
+        assert set(g) == w, f"sample {r}: connected set differs"
