@@ -136,8 +136,9 @@ typedef int qc_status;
                                    qc_eloc_work); costs global atomics, so off (0) in timed runs */
 #define QC_OPT_ALPHA_SLOTS  14  /* join: slots of the per-warp alpha single list (the alpha' groups
                                    too long to scan); 0 auto (all alpha singles, or fewer when that
-                                   fits more warps), else that many (at least 1): a sample with more
-                                   long alpha' groups enumerates them in segments */
+                                   fits more warps), else that many (at least 1; the full list from
+                                   the number of alpha singles up): a sample with more long alpha'
+                                   groups enumerates them in segments */
 #define QC_OPT_WAIT_LIMIT   13  /* test hook: iteration limit of each CTA's first wait for its copy
                                    of the Bloom filter (-1, the default: 2^24).  When it runs out
                                    the CTA sets QC_FLAG_TIMEOUT, waits for the copy with the

@@ -444,8 +444,9 @@ qc_status choose_config(qc_eloc* H, long long n_u, long long n_table, qc::Launch
         for (int ai = 0; ai < (join ? (H->opt_alpha_slots ? 1 : 3) : 1); ++ai)
         for (int ln = 0; ln < 2; ++ln) {
             if ((H->opt_lean == 1 && ln == 1) || (H->opt_lean == 2 && ln == 0)) continue;
-            const int acap = acaps[ai];
-            if (acap > 0 && acap >= sp.nsa) continue;
+            // a capacity of at least the alpha singles is the full list
+            const int acap = acaps[ai] >= sp.nsa ? 0 : acaps[ai];
+            if (ai > 0 && acap == 0) continue;  // an automatic candidate that caps nothing
             const size_t wb = qc::filtered_smem_bytes(sp, 1, want, ln, join, acap) -
                               qc::filtered_smem_bytes(sp, 0, want, ln, join, acap);
             int f = want, w = 0;

@@ -557,6 +557,38 @@ def test_shapes_edge(B, orc, K, ne, n_u):
         assert_eloc_close(g["eloc"], want)
 
 
+def test_options_out_of_range_refused(B):
+    """Every option value outside its documented range is refused with QC_ERR_ARG and leaves
+    the handle usable; the documented ends of the ranges are accepted."""
+    ints = I.make_integrals(8, 16, 4401)
+    h = B.qc_eloc_create(ints.h, ints.eri, 0.0, 16, 8)
+    try:
+        bad = [(B.QC_OPT_UNROLL, 3), (B.QC_OPT_LEAN, 3), (B.QC_OPT_JOIN, 3), (B.QC_OPT_JOIN, -1),
+               (B.QC_OPT_SCAN_COST, -1), (B.QC_OPT_SCAN_COST, 1025), (B.QC_OPT_BETA_COST, -2),
+               (B.QC_OPT_BETA_COST, 1025), (B.QC_OPT_ALPHA_SLOTS, -1), (B.QC_OPT_ALPHA_SLOTS, 4097),
+               (B.QC_OPT_CHUNK_PAIRS, -2), (B.QC_OPT_GRID, -1), (99, 0)]
+        for opt, v in bad:
+            with pytest.raises(B.QcError) as ei:
+                B.qc_eloc_set_option(h, opt, v)
+            assert ei.value.status == -1, (opt, v)
+        good = [(B.QC_OPT_BETA_COST, -1), (B.QC_OPT_BETA_COST, 0), (B.QC_OPT_BETA_COST, 1024),
+                (B.QC_OPT_SCAN_COST, 0), (B.QC_OPT_SCAN_COST, 1024), (B.QC_OPT_ALPHA_SLOTS, 4096),
+                (B.QC_OPT_JOIN, 2), (B.QC_OPT_UNROLL, 4)]
+        for opt, v in good:
+            B.qc_eloc_set_option(h, opt, v)
+        # still evaluates, and correctly
+        keys = I.rank_weighted_samples(8, 4, 4, 300, seed=4402)
+        psi = I.lognormal_psi(300, 4403)
+        import torch
+        e, _ = B.qc_eloc_eval(h, B.keys_to_tensor(keys), torch.ones(300, dtype=torch.int64, device="cuda"),
+                              torch.from_numpy(psi).cuda())
+        assert B.qc_eloc_summary_read(h)["status"] == 0 and np.all(np.isfinite(e.cpu().numpy()))
+        # more alpha slots than alpha singles is the full list: the join kernel, not a fallback
+        assert B.qc_eloc_last_config(h)["kernel"] in (4, 5)
+    finally:
+        B.qc_eloc_destroy(h)
+
+
 def test_degenerate_inputs(B, orc):
     import torch
     ints, s = I.make_workload("n14_e6_u1k")
