@@ -102,7 +102,7 @@ typedef int qc_status;
 #define QC_OPT_TIMING        1  /* 1: record per-phase CUDA events (qc_eloc_timings) */
 #define QC_OPT_KERNEL        2  /* 0 auto, 1 direct probe of every x', 2 filtered */
 #define QC_OPT_FILTER_LOG2W  3  /* 0 auto, else log2 of filter 32-bit words (5..15) */
-#define QC_OPT_WARPS         4  /* 0 auto, else warps per CTA of the main kernel (<= 24) */
+#define QC_OPT_WARPS         4  /* 0 auto, else warps per CTA of the main kernel, 1..24 */
 #define QC_OPT_UNROLL        5  /* 0 auto, else outer entries per inner pass (1, 2, 4) */
 #define QC_OPT_GRID          6  /* 0 auto, else CTAs of the main kernel */
 #define QC_OPT_PREFILTER     7  /* 1 (default): drop single excitations whose new spin string no

@@ -291,7 +291,7 @@ qc_status qc_eloc_set_option(qc_eloc* H, int option, int64_t value) {
             H->opt_fw = static_cast<int>(value);
             return QC_OK;
         case QC_OPT_WARPS:
-            if (value < 0 || value > 32) return fail(H, QC_ERR_ARG, "QC_OPT_WARPS: 0..32");
+            if (value < 0 || value > qc::kFilteredMaxWarps) return fail(H, QC_ERR_ARG, "QC_OPT_WARPS: 0..24");
             H->opt_warps = static_cast<int>(value);
             return QC_OK;
         case QC_OPT_UNROLL:

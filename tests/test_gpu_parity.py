@@ -566,14 +566,15 @@ def test_options_out_of_range_refused(B):
         bad = [(B.QC_OPT_UNROLL, 3), (B.QC_OPT_LEAN, 3), (B.QC_OPT_JOIN, 3), (B.QC_OPT_JOIN, -1),
                (B.QC_OPT_SCAN_COST, -1), (B.QC_OPT_SCAN_COST, 1025), (B.QC_OPT_BETA_COST, -2),
                (B.QC_OPT_BETA_COST, 1025), (B.QC_OPT_ALPHA_SLOTS, -1), (B.QC_OPT_ALPHA_SLOTS, 4097),
-               (B.QC_OPT_CHUNK_PAIRS, -2), (B.QC_OPT_GRID, -1), (99, 0)]
+               (B.QC_OPT_CHUNK_PAIRS, -2), (B.QC_OPT_GRID, -1), (B.QC_OPT_WARPS, 25), (B.QC_OPT_KERNEL, 3),
+               (B.QC_OPT_FILTER_LOG2W, 4), (B.QC_OPT_FILTER_LOG2W, 16), (99, 0)]
         for opt, v in bad:
             with pytest.raises(B.QcError) as ei:
                 B.qc_eloc_set_option(h, opt, v)
             assert ei.value.status == -1, (opt, v)
         good = [(B.QC_OPT_BETA_COST, -1), (B.QC_OPT_BETA_COST, 0), (B.QC_OPT_BETA_COST, 1024),
                 (B.QC_OPT_SCAN_COST, 0), (B.QC_OPT_SCAN_COST, 1024), (B.QC_OPT_ALPHA_SLOTS, 4096),
-                (B.QC_OPT_JOIN, 2), (B.QC_OPT_UNROLL, 4)]
+                (B.QC_OPT_JOIN, 2), (B.QC_OPT_UNROLL, 4), (B.QC_OPT_WARPS, 24), (B.QC_OPT_WARPS, 0)]
         for opt, v in good:
             B.qc_eloc_set_option(h, opt, v)
         # still evaluates, and correctly
