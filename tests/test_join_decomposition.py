@@ -93,7 +93,8 @@ def _split(A, Bs, K, o, scan_cost, beta_cost, min_long, cap):
     least min_long long alpha' in that segment, a beta' group is scanned when its rows x
     beta_cost / 4 are at most their number, keeping rows whose alpha group is long and x's beta
     single when class 1 is enumerated; the other beta' stay in the enumerated list).  Filter
-    and bucket probe stand as exact membership."""
+    and bucket probe stand as exact membership.  Also returns the work as the kernel counts it:
+    rows scanned, excitations filter-tested, beta' looked up and beta' groups scanned."""
     ga, gb = {}, {}
     for r, (a, b) in enumerate(zip(A, Bs)):
         ga.setdefault(a, []).append(r)
@@ -113,6 +114,7 @@ def _split(A, Bs, K, o, scan_cost, beta_cost, min_long, cap):
 
     npairs = (o * (o - 1) // 2) * ((K - o) * (K - o - 1) // 2)
     out = []
+    work = Counter()
     for a, b in zip(A, Bs):
         found = Counter()
         bp = [b1 for b1 in singles(b) if b1 in gb]            # the prefiltered beta list
@@ -121,8 +123,10 @@ def _split(A, Bs, K, o, scan_cost, beta_cost, min_long, cap):
         enum_b = lb > 0 and lb * scan_cost > 4 * npairs
         if la > 0 and not enum_a:                             # x's alpha group scanned
             found.update(r for r in ga[a] if _pc(Bs[r] ^ b) in (2, 4))
+            work["scan_rows"] += la
         if lb > 0 and not enum_b:                             # x's beta group scanned
             found.update(r for r in gb[b] if _pc(A[r] ^ a) == 4)
+            work["scan_rows"] += lb
         athr = 4 * (len(bp) + 1)
         long_a = []
         for a1 in singles(a):                                 # alpha' groups
@@ -132,12 +136,16 @@ def _split(A, Bs, K, o, scan_cost, beta_cost, min_long, cap):
                 long_a.append(a1)
             else:
                 found.update(r for r in ga[a1] if _pc(Bs[r] ^ b) in (0, 2))
+                work["scan_rows"] += len(ga[a1])
         first = min(len(long_a), cap)                         # long alpha' in the first segment
         blist = bp
         if beta_cost > 0 and first >= min_long and bp:        # the beta' phase
             blist = []
+            work["beta_looked"] += len(bp)
             for b1 in bp:
                 if len(gb[b1]) * beta_cost <= 4 * first:
+                    work["beta_groups"] += 1
+                    work["scan_rows"] += len(gb[b1])
                     for r in gb[b1]:
                         d = _pc(A[r] ^ a)
                         if (d == 0 and enum_a) or (d == 2 and len(ga[A[r]]) * scan_cost > athr):
@@ -146,13 +154,17 @@ def _split(A, Bs, K, o, scan_cost, beta_cost, min_long, cap):
                     blist.append(b1)
         for a1 in long_a:                                     # class 0 and class 4
             found.update(row_of[k] for k in [(a1, b)] + [(a1, b1) for b1 in blist] if k in row_of)
+            work["tests"] += 1 + len(blist)
         if enum_a:                                            # classes 1 and 3
-            found.update(row_of[k] for k in [(a, b1) for b1 in blist] + [(a, b2) for b2 in doubles(b)]
-                         if k in row_of)
+            cands = [(a, b1) for b1 in blist] + [(a, b2) for b2 in doubles(b)]
+            found.update(row_of[k] for k in cands if k in row_of)
+            work["tests"] += len(cands)
         if enum_b:                                            # class 2
-            found.update(row_of[k] for k in [(a2, b) for a2 in doubles(a)] if k in row_of)
+            cands = [(a2, b) for a2 in doubles(a)]
+            found.update(row_of[k] for k in cands if k in row_of)
+            work["tests"] += len(cands)
         out.append(found)
-    return out
+    return out, work
 
 
 @pytest.mark.parametrize("scan_cost,beta_cost,min_long,cap", [(4, 8, 8, 10 ** 9), (16, 1, 8, 4), (64, 1, 2, 3),
@@ -162,7 +174,23 @@ def test_split_with_beta_phase_finds_each_pair_once(scan_cost, beta_cost, min_lo
     keys = I.rank_weighted_samples(K, o, o, 1200, seed=21)
     A, Bs = _strings(keys, K)
     want = _brute(A, Bs)
-    got = _split(A, Bs, K, o, scan_cost, beta_cost, min_long, cap)
+    got, _ = _split(A, Bs, K, o, scan_cost, beta_cost, min_long, cap)
     for r, (g, w) in enumerate(zip(got, want)):
         assert max(g.values(), default=1) == 1, f"sample {r}: a row found twice"
         assert set(g) == w, f"sample {r}: connected set differs"
+
+
+@pytest.mark.parametrize("scan_cost,beta_cost,min_long,cap", [(4, 8, 8, 10 ** 9), (16, 1, 8, 4), (64, 1, 2, 3),
+                                                              (64, 4, 1, 1), (4, 0, 8, 2), (1, 1, 1, 5)])
+def test_work_model_equals_the_rules_row_by_row(scan_cost, beta_cost, min_long, cap):
+    """The vectorised model of the join's work from group sizes (which the GPU work-counter
+    tests hold the kernel's counters to) equals the row-by-row emulation of the rules above:
+    scanned rows, filter tests, beta' look-ups and scanned beta' groups."""
+    from join_model import join_work
+    K, o = 10, 3
+    keys = I.rank_weighted_samples(K, o, o, 1200, seed=21)
+    A, Bs = _strings(keys, K)
+    _, work = _split(A, Bs, K, o, scan_cost, beta_cost, min_long, cap)
+    model = join_work(keys, K, o, cap, scan_cost=scan_cost, beta_cost=beta_cost, min_long=min_long)
+    assert model == {k: work[k] for k in ("tests", "scan_rows", "beta_looked", "beta_groups")}
+    assert model["tests"] > 0 and model["scan_rows"] > 0
