@@ -101,16 +101,17 @@ def _dist():
     return world, rank, local
 
 
-def _plain_launches(cfg, n_table):
+def _plain_launches(cfg, n_table, caller_table=False):
     """Kernels of one plain evaluation: table build, main kernel, two reduction passes, and
     with the sample-space join its index: a 3-kernel scan of the group sizes, per 11-bit
-    radix pass a histogram, a 3-kernel scan and a scatter, the gather, and the heavy-first
-    sample order (a key kernel and one radix pass)."""
+    radix pass a histogram, a 3-kernel scan and a scatter, the gather and the mark pass, and
+    the heavy-first sample order (a key kernel and one radix pass; against a caller's table,
+    first a look-up of the samples' group sizes)."""
     n = 4
     if cfg["kernel"] in (4, 5):
         size = 1 << max(0, (2 * max(n_table, 1) - 1).bit_length())  # hash sets: next_pow2(2n) slots
         passes = -(-(2 * size).bit_length() // 11)
-        n += 3 + 5 * passes + 1 + 6
+        n += 3 + 5 * passes + 2 + 6 + (1 if caller_table else 0)
     return n
 
 
@@ -118,8 +119,9 @@ def _batched_launches(specs):
     """Kernels of one batched step: the batch build, the batch kernel and two reduction
     passes, and for the molecules that take the join (join_by_default: 16384 rows up, or 2e8
     rows x pairs per sample, or 512 rows at 50000 pairs per sample) one shared index: a
-    3-kernel scan, per 11-bit radix pass a histogram, a 3-kernel scan and a scatter, and the
-    gather."""
+    3-kernel scan, per 11-bit radix pass a histogram, a 3-kernel scan and a scatter, the
+    gather and the mark pass; then the rows heavy first, molecule by molecule: a key kernel
+    and one radix sort of keys up to (molecules << 8) | 255."""
     n = 4
 
     def joins(sp):
@@ -127,7 +129,8 @@ def _batched_launches(specs):
         return sp["n_u"] >= 16384 or sp["n_u"] * p >= 200_000_000 or (p >= 50_000 and sp["n_u"] >= 512)
     slots = sum(2 * (1 << max(0, (2 * sp["n_u"] - 1).bit_length())) for sp in specs if joins(sp))
     if slots:
-        n += 3 + 5 * (-(-slots.bit_length() // 11)) + 1
+        n += 3 + 5 * (-(-slots.bit_length() // 11)) + 2
+        n += 1 + 5 * (-(-((len(specs) << 8) | 255).bit_length() // 11))
     return n
 
 
@@ -531,7 +534,8 @@ def run_ours(args):
             "phase_ms": {"table": statistics.mean(table_ms), "main": statistics.mean(main_ms),
                          "reduce": statistics.mean(red_ms)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": _plain_launches(cfg, int(s.n_u)) * args.steps, "clocks": clocks, "wall_s_timed": wall,
+            "gpu_launches": _plain_launches(cfg, int(s.n_u), caller_table=world > 1) * args.steps, "clocks": clocks,
+            "wall_s_timed": wall,
             # host wall clock of one timed step (flush, enqueue, wait, phase timings) and of the
             # qc_eloc_eval call alone (argument checks, launch set-up, enqueue)
             "host_ms_per_step": 1e3 * wall / args.steps, "host_ms_step_median": statistics.median(host_ms),

@@ -20,12 +20,14 @@ def test_plain_launch_counts():
     assert b._plain_launches({"kernel": 2}, 1000) == 4
     assert b._plain_launches({"kernel": 3}, 10 ** 6) == 4
     # with the join at 1e5 rows: sets of 2^18 slots, keys up to 2^20 -> two 11-bit passes:
-    # group-start scan 3 + 2 x (hist + scan 3 + scatter) + gather + order (key + 5)
-    assert b._plain_launches({"kernel": 4}, 100_000) == 4 + 3 + 10 + 1 + 6
+    # group-start scan 3 + 2 x (hist + scan 3 + scatter) + gather + mark + order (key + 5)
+    assert b._plain_launches({"kernel": 4}, 100_000) == 4 + 3 + 10 + 2 + 6
+    # against a caller's table the samples' group sizes are looked up first
+    assert b._plain_launches({"kernel": 4}, 100_000, caller_table=True) == 4 + 3 + 10 + 2 + 6 + 1
     # 2^20 slots per set (5e5 rows): keys up to 2^21 (22 bits) -> still two passes;
     # 2^21 slots (1e6 rows): keys up to 2^22 (23 bits) -> three
-    assert b._plain_launches({"kernel": 5}, 500_000) == 24
-    assert b._plain_launches({"kernel": 5}, 1_000_000) == 29
+    assert b._plain_launches({"kernel": 5}, 500_000) == 25
+    assert b._plain_launches({"kernel": 5}, 1_000_000) == 30
 
 
 def test_batched_launch_counts():
@@ -34,7 +36,12 @@ def test_batched_launch_counts():
     assert b._batched_launches(small) == 4          # no molecule takes the join
     big = small + [{"n_u": 20000}, {"n_u": 100000}]
     n = b._batched_launches(big)
-    assert n in (4 + 3 + 10 + 1, 4 + 3 + 15 + 1)    # one shared index, two or three passes
+    # one shared index (two or three passes, gather, mark), then the order of four molecules'
+    # rows: a key kernel and one pass over keys up to (4 << 8) | 255 (11 bits)
+    assert n in (4 + 3 + 10 + 2 + 6, 4 + 3 + 15 + 2 + 6)
+    # 64 molecules: keys up to (64 << 8) | 255 (15 bits) -> two order passes
+    many = big + [{"n_u": 1000}] * 60
+    assert b._batched_launches(many) - b._batched_launches(big) == 5
 
 
 def test_source_hash_ignores_comments_not_code(tmp_path, monkeypatch):
