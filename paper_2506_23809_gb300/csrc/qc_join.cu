@@ -9,7 +9,9 @@
 // a few groups: the rows sharing x's alpha string, those sharing its beta string, and the
 // rows of each alpha' group.  The local-energy kernel scans a short group row by row (one
 // popcount of the other spin's string difference decides the connection) and enumerates the
-// excitations into a long one through the filter and the bucket table.
+// excitations into a long one through the filter and the bucket table.  An alpha-beta double
+// also lies in the group of its beta' (a single excitation of beta), so for a sample with many
+// long alpha' groups the kernel may scan short beta' groups for their rows instead.
 //
 // Built once per evaluation after K0, which leaves each row's slot in the alpha and beta
 // spin-string sets as a sort key (alpha rows first, beta rows offset by the set size) and
